@@ -1,0 +1,180 @@
+"""MLMC / MLQMC / FMG-MLMC estimators and sample-size control (Sec. 2.2-2.5).
+
+TEST INFRASTRUCTURE ONLY (see the oracle package docstring).
+
+  * telescoping sum E[Q_L] = sum_l E[Y_l], Y_0 = Q_0, Y_l = Q^f_l - Q^c_l (Eq. 2-3),
+    the same sample omega for both terms of a level, independent samples
+    across levels (Eq. 5);
+  * MSE split  sum_l V_l/N_l <= eps^2/2,  bias^2 <= eps^2/2 (Sec. 2.3);
+  * optimal N_l minimising sum_l N_l C_l under the variance constraint (Sec.
+    2.3 states the problem, not the answer): by Lagrange multipliers
+    N_l = (2/eps^2) sqrt(V_l/C_l) sum_k sqrt(V_k C_k), rounded up;
+  * Richardson bias estimate |E[Y_L]| / (2^alpha - 1) (Algorithm 1);
+  * MLQMC (Algorithm 2): R independently shifted point sets per level; the
+    level estimate is the mean over shifts and its variance the sample
+    variance of the R shift means divided by R; while sum_l V[Y^_l] > eps^2/2
+    double N_l on the level maximising V[Y^_l] / (N_l C_l).
+
+Sums are exact-rounded (math.fsum), the plainest correct reduction.
+"""
+import math
+
+import numpy as np
+
+from . import kl as _kl
+from . import lib as _lib
+
+
+def optimal_samples(V, C, eps):
+    """N_l = ceil((2/eps^2) sqrt(V_l/C_l) sum_k sqrt(V_k C_k))."""
+    V = np.asarray(V, float)
+    C = np.asarray(C, float)
+    total = float(np.sum(np.sqrt(V * C)))
+    return np.ceil(2.0 / eps ** 2 * np.sqrt(V / C) * total).astype(np.int64)
+
+
+def cost_model(n_cells):
+    """Deterministic cost per sample: finest cells x 4/3 (all FMG grids)."""
+    return np.asarray(n_cells, float) * 4.0 / 3.0
+
+
+class LevelAccumulator:
+    """Per-level sums of Y, Y^2, Q^f, Q^c over the samples seen so far."""
+
+    def __init__(self, nlev):
+        self.Y = [[] for _ in range(nlev)]
+        self.Qf = [[] for _ in range(nlev)]
+        self.Qc = [[] for _ in range(nlev)]
+
+    def add(self, l, y, qf, qc):
+        self.Y[l].extend(np.asarray(y).tolist())
+        self.Qf[l].extend(np.asarray(qf).tolist())
+        self.Qc[l].extend(np.asarray(qc).tolist())
+
+    def N(self, l):
+        return len(self.Y[l])
+
+    def mean(self, l):
+        return math.fsum(self.Y[l]) / len(self.Y[l])
+
+    def var(self, l):
+        n = len(self.Y[l])
+        m = self.mean(l)
+        return math.fsum((y - m) ** 2 for y in self.Y[l]) / (n - 1)
+
+
+def fit_rate(values, start=1):
+    """Least-squares slope of -log2|values_l| against l for l >= start."""
+    l = np.arange(start, len(values))
+    v = np.abs(np.asarray(values[start:], float))
+    if len(l) < 2 or np.any(v <= 0):
+        return float("nan")
+    A = np.stack([l, np.ones_like(l)], axis=1).astype(float)
+    slope = np.linalg.lstsq(A, np.log2(v), rcond=None)[0][0]
+    return float(-slope)
+
+
+def mlmc(sampler, L, eps, n_pilot, cost, max_rounds=50):
+    """Algorithm 1 / 3 for a fixed finest level L.
+    sampler(l, first, n) -> (Y, Qf, Qc) for samples first..first+n-1 of level l."""
+    acc = LevelAccumulator(L + 1)
+    dN = np.full(L + 1, n_pilot, np.int64)
+    rounds = 0
+    while np.any(dN > 0) and rounds < max_rounds:
+        for l in range(L + 1):
+            if dN[l] > 0:
+                y, qf, qc = sampler(l, acc.N(l), int(dN[l]))
+                acc.add(l, y, qf, qc)
+        V = np.array([acc.var(l) for l in range(L + 1)])
+        Nopt = optimal_samples(V, cost, eps)
+        dN = np.maximum(0, Nopt - np.array([acc.N(l) for l in range(L + 1)]))
+        rounds += 1
+    return _report(acc, L, eps, cost, rounds)
+
+
+def _report(acc, L, eps, cost, rounds):
+    means = np.array([acc.mean(l) for l in range(L + 1)])
+    V = np.array([acc.var(l) for l in range(L + 1)])
+    N = np.array([acc.N(l) for l in range(L + 1)])
+    alpha = fit_rate(means, 1)
+    beta = fit_rate(V, 1)
+    bias = abs(means[L]) / (2.0 ** alpha - 1.0) if np.isfinite(alpha) and alpha > 0 else float("nan")
+    return dict(estimate=math.fsum(means), means=means, V=V, N=N,
+                var_estimator=float(np.sum(V / N)), alpha=alpha, beta=beta,
+                bias=bias, rounds=rounds, cost=float(np.sum(N * cost)), acc=acc)
+
+
+def mlqmc(sampler, L, eps, n_pilot, R, cost, max_rounds=200):
+    """Algorithm 2 for a fixed L.  sampler(l, first, n, r) -> (Y, Qf, Qc) for
+    points first..first+n-1 of shift r on level l."""
+    Ys = [[[] for _ in range(R)] for _ in range(L + 1)]
+    N = np.full(L + 1, n_pilot, np.int64)
+    for l in range(L + 1):
+        for r in range(R):
+            Ys[l][r].extend(np.asarray(sampler(l, 0, n_pilot, r)[0]).tolist())
+
+    def level_stats(l):
+        m = np.array([math.fsum(Ys[l][r]) / len(Ys[l][r]) for r in range(R)])
+        mean = math.fsum(m) / R
+        var_hat = math.fsum((m - mean) ** 2) / (R * (R - 1))
+        return mean, var_hat
+
+    rounds = 0
+    while rounds < max_rounds:
+        stats = [level_stats(l) for l in range(L + 1)]
+        Vhat = np.array([s[1] for s in stats])
+        if Vhat.sum() <= eps ** 2 / 2:
+            break
+        l = int(np.argmax(Vhat / (N * cost)))
+        for r in range(R):
+            Ys[l][r].extend(np.asarray(sampler(l, int(N[l]), int(N[l]), r)[0]).tolist())
+        N[l] *= 2
+        rounds += 1
+    stats = [level_stats(l) for l in range(L + 1)]
+    means = np.array([s[0] for s in stats])
+    Vhat = np.array([s[1] for s in stats])
+    alpha = fit_rate(means, 1)
+    bias = abs(means[L]) / (2.0 ** alpha - 1.0) if np.isfinite(alpha) and alpha > 0 else float("nan")
+    return dict(estimate=math.fsum(means), means=means, Vhat=Vhat, N=N,
+                var_estimator=float(Vhat.sum()), alpha=alpha, bias=bias, rounds=rounds,
+                cost=float(np.sum(N * R * cost)))
+
+
+class FMGSampler:
+    """Samples of one FMG-MLMC level: points -> KL field -> FMG -> (Q^f, Q^c).
+
+    levels[l] = n_l (finest grid of level l); basis: a KLBasis (or anything
+    with level_basis(n)); seed: the Philox key for MC points and QMC shifts."""
+
+    def __init__(self, levels, basis, seed, prm=None, n0=4, qmc_dirnums=None,
+                 n_shifts=0, nthreads=0):
+        self.levels, self.basis, self.seed = list(levels), basis, seed
+        self.prm = prm or _lib.params()
+        self.n0 = n0
+        self.B = [basis.level_basis(n) for n in self.levels]
+        self.V = qmc_dirnums
+        self.shifts = None
+        if qmc_dirnums is not None:
+            M = self.B[0].shape[1]
+            self.shifts = [_lib.sobol_shifts(seed, l, n_shifts, M) for l in range(len(levels))]
+        self.nthreads = nthreads
+        self.solves = [0] * len(levels)
+
+    def points(self, l, first, n, r=None):
+        M = self.B[l].shape[1]
+        if r is None:
+            return _lib.mc_normals(self.seed, l, first, n, M)
+        _, xi = _lib.sobol_points(self.V, first, n, self.shifts[l][r:r + 1], want_xi=True)
+        return xi[0]
+
+    def solve(self, l, xi):
+        n = self.levels[l]
+        K = _kl.synthesize(self.B[l], xi).reshape(-1, n, n)
+        qf, qc, _, _ = _lib.fmg_solve_batch(K, self.prm, self.n0, nthreads=self.nthreads)
+        self.solves[l] += len(qf)
+        return qf, qc
+
+    def __call__(self, l, first, n, r=None):
+        qf, qc = self.solve(l, self.points(l, first, n, r))
+        y = qf if l == 0 else qf - qc
+        return y, qf, qc
