@@ -1,0 +1,336 @@
+"""Benchmark: seconds to RMSE <= eps on E[outflux] with FMG-MLMC on one GB300.
+
+Workload (default): five MLMC levels 16x16 .. 256x256, 128 KL modes of the
+exponential covariance (sigma^2 = 1, lambda = 0.3), Case II boundary data
+(p = 1 west, 0 east), FMG from 4x4 with 2 V(2,2) cycles per stage, MC points,
+sample sizes from the optimal rule for RMSE 1e-3.  One step = one complete
+mlmc_estimate call (points, KL synthesis, FMG solves, level sums, controller
+rounds) from an empty estimator to RMSE <= eps; the KL basis is resident in
+HBM before the timed region.  L2 is flushed (a 512 MiB write) between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="fmg_mlmc5")
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--qmc", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="budget of the oracle's bounded timing sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+METRIC = "seconds to RMSE<=1e-3 on E[outflux], plain FP64 vs chosen form; smoother HBM GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p.get("bf16_tflops"), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_level_seconds(wl, budget_s, levels=None):
+    """Seconds per sample of the oracle on each level, on all host cores,
+    from a bounded sample (about budget_s seconds in total)."""
+    from oracle import kl as okl
+    from oracle import mlmc as omlmc
+    cores = os.cpu_count() or 1
+    basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32 if wl.M <= 128 else 0)
+    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, nthreads=cores)
+    per = []
+    share = budget_s / len(wl.levels)
+    counts = []
+    for l, n in enumerate(wl.levels):
+        k = max(cores, 16)
+        t0 = time.perf_counter()
+        s(l, 0, k)
+        dt = time.perf_counter() - t0
+        # grow the sample to about `share` seconds (at most 64x the first)
+        k2 = int(min(64 * k, max(k, k * share / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        s(l, k, k2)
+        dt = time.perf_counter() - t0
+        per.append(dt / k2)
+        counts.append(k2)
+    return np.array(per), cores, counts
+
+
+# ------------------------------------------------------------------ native
+def flush_l2(buf):
+    buf.fill_(1.0)
+
+
+def run_native(args, wl, eps):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1910_04727_gb300 as fm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    fm.load_library()
+    # replicas: each rank runs its own estimate with its own seed
+    ctx = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
+                     pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
+                     n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank)
+    theta, captured = ctx.kl_basis_build(q=wl.kl_q)
+    n_ref = wl.n_ref
+    flush = torch.empty(512 << 20 >> 2, dtype=torch.float32, device="cuda")
+
+    def estimate():
+        return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+
+    for _ in range(args.warmup):
+        estimate()
+    torch.cuda.synchronize()
+
+    # timed region: K estimates, each from an empty estimator
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, results = [], []
+    ctx.profile_begin()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        r = estimate()
+        stop.record()
+        torch.cuda.synchronize()
+        times.append(start.elapsed_time(stop) / 1e3)
+        results.append(r)
+    torch.cuda.synchronize()
+    prof = ctx.profile_end()
+    clk = clocks.stop()
+    t_total = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API from pinned host memory: basis upload,
+    # estimate, result read-back
+    B_host = torch.empty((n_ref * n_ref, wl.M), dtype=torch.float64).pin_memory()
+    ctx2 = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
+                      pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
+                      n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank)
+    # the basis the native path built, staged to pinned host memory outside the timing
+    ctx.kl_basis_get(B_host)
+    e2e_times, rounds = [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.kl_basis_set_host_ptr(B_host.data_ptr())
+        r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+        e2e_times.append(time.perf_counter() - t0)
+        rounds.append(r["rounds"])
+    ctx2.close()
+    h2d = B_host.numel() * 8
+    d2h = int(np.mean(rounds)) * len(wl.levels) * (wl.n_shifts if args.qmc else 1) * 128
+
+    hbm, bf16, src = peaks()
+    # dominant kernel family by event-timed device time
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    fam, st = dom
+    per_launch_ms = st["ms"] / st["launches"]
+    if fam == "kl_gemm_exp":
+        roof = {"bound": "alu", "kernel": fam, "achieved": st["flops"] / (st["ms"] / 1e3) / 1e12,
+                "unit": "TFLOP/s FP64", "peak": None, "frac": None, "traffic": None}
+    else:
+        ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src}
+    roof["launches"] = st["launches"]
+    roof["avg_launch_ms"] = per_launch_ms
+    families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                    "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in prof.items()}
+    total_launches = int(sum(v["launches"] for v in prof.values()))
+
+    ests = [r["estimate"] for r in results]
+    out = {
+        "metric": METRIC,
+        "value": t_total / args.steps,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded Philox KL coefficients, KL basis built on the GPU)",
+        "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
+                   "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
+                   "fmg": "4x4 exact, nu0=%d V(%d,%d) RB-GS" % (wl.nu0, wl.nu1, wl.nu2),
+                   "form": "plain FP64", "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "captured_variance": captured},
+        "estimate": float(np.mean(ests)),
+        "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in results]))),
+        "N_per_level": [int(x) for x in results[-1]["N"]],
+        "roofline": roof,
+        "kernel_families": families,
+        "gpu_launches": total_launches,
+        "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds)
+        N = results[-1]["N"]
+        t_cpu = float(np.sum(per * N))
+        out["cpu_baseline"] = {"value": t_cpu, "unit": "s", "cores": cores, "kind": "oracle",
+                               "sample": "oracle FMG-MLMC samples per level %s timed on %d threads; "
+                                         "seconds per sample x the GPU run's N_l (extrapolated)"
+                                         % (counts, cores)}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, wl, eps):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # the oracle's time to RMSE: per-level seconds per sample x the optimal
+    # N_l of the target eps, N_l from the oracle's own pilot variances
+    from oracle import mlmc as omlmc
+    from oracle import kl as okl
+    times = []
+    budget = max(5.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    cores = os.cpu_count() or 1
+    basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32 if wl.M <= 128 else 0)
+    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, nthreads=cores)
+    cost = omlmc.cost_model(np.array(wl.levels) ** 2)
+    V = None
+    for step in range(args.warmup + args.steps):
+        per, var = [], []
+        for l in range(len(wl.levels)):
+            k = max(cores, int(64 / (1 << l)))
+            t0 = time.perf_counter()
+            y = s(l, step * 4096, k)[0]
+            per.append((time.perf_counter() - t0) / k)
+            var.append(np.var(y, ddof=1))
+        V = np.array(var) if V is None else 0.5 * (V + np.array(var))
+        N = omlmc.optimal_samples(V, cost, eps)
+        if step >= args.warmup:
+            times.append(float(np.sum(np.array(per) * N)))
+    value = float(np.mean(times))
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "eps": eps,
+                      "sampler": "mc", "form": "FP64 CPU oracle"},
+           "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                            "sample": "per step: a bounded batch per level timed on %d threads, "
+                                      "extrapolated to the optimal N_l of eps" % cores},
+           "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    wl = W.WORKLOADS[args.workload]
+    eps = args.eps if args.eps is not None else wl.eps
+    if args.impl == "reference":
+        run_reference(args, wl, eps)
+    else:
+        run_native(args, wl, eps)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * fmgmlmc.h - C ABI of the GB300 full-multigrid multilevel (quasi-) Monte
+ * Carlo library.
+ *
+ * Method: Liu, Li, Sun & Yu, "A full multigrid multilevel (quasi-) Monte
+ * Carlo method for the single-phase subsurface flow with random
+ * coefficients", arXiv 1910.04727.  The model problem is Eq. 1 on the unit
+ * square with the boundary data and QoI of Table 1, Case II (Dirichlet p_W /
+ * p_E on the west / east edges, no flow north and south, QoI = outflux
+ * through the east edge); the permeability is k = exp(g), g a Gaussian field
+ * with the exponential Matern covariance of Sec. 3.1, represented by its
+ * truncated KL expansion.  The MLMC levels (Sec. 2.2, Algorithm 1) share
+ * their grid hierarchy with the full multigrid solver (Sec. 2.5): one FMG
+ * solve of level l gives both Q^f_l and Q^c_l (Algorithm 3), the coarse
+ * coefficients coming from the fine ones by injection (Sec. 2.5).
+ *
+ * Conventions
+ *   - Every pointer named d_* is DEVICE memory owned by the caller; the
+ *     library never frees it and keeps no reference after the call returns.
+ *     Every other pointer is host memory owned by the caller.
+ *   - Grids are n x n cells, stored row-major with x fastest: cell (i, j)
+ *     (i = 0 at the west edge, j = 0 at the south edge) is element j*n + i.
+ *     A batch of S grids is S consecutive grids ([S][n][n]).
+ *   - Calls that take a cudaStream_t (passed as void*, NULL = the legacy
+ *     default stream) are asynchronous on that stream; the return status
+ *     covers argument checks and launch errors only.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef FMGMLMC_H
+#define FMGMLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fm_status;
+#define FM_OK 0
+#define FM_EINVAL 1        /* bad argument (message in fm_last_error) */
+#define FM_ENOMEM 2        /* device or host allocation failed */
+#define FM_ECUDA 3         /* a CUDA call failed */
+#define FM_ENOTCONV 4      /* a solve did not reach its tolerance */
+#define FM_ETIMEOUT 5      /* a bounded device wait ran out */
+#define FM_EUNSUPPORTED 6  /* valid request this build does not implement */
+
+#define FM_MAX_LEVELS 12
+
+/* Arithmetic of the solver. FP64: every step in FP64. */
+#define FM_PREC_FP64 0
+
+typedef struct fm_ctx fm_ctx;
+
+/* Problem and method parameters of one FMG-MLMC run. */
+typedef struct {
+    int32_t n_levels;     /* MLMC levels L + 1 (1 .. FM_MAX_LEVELS) */
+    int32_t n_level0;     /* finest grid of level 0; level l uses n_level0 << l */
+    int32_t n_coarsest;   /* coarsest FMG grid (the exact-solve grid); 4 */
+    int32_t M;            /* KL modes (1 .. 4096) */
+    double sigma2;        /* variance of g (Sec. 3.1) */
+    double lambda;        /* correlation length (Sec. 3.1) */
+    double pW, pE;        /* Dirichlet data on the west / east edges (Table 1) */
+    int32_t nu0;          /* V-cycles per FMG stage */
+    int32_t nu1, nu2;     /* pre- / post-smoothing red-black Gauss-Seidel sweeps */
+    int32_t precision;    /* FM_PREC_* */
+    int32_t n_shifts;     /* QMC digital shifts R */
+    uint64_t seed;        /* key of the Philox streams (MC points, QMC shifts) */
+    int64_t max_batch;    /* most samples per device batch (0: library's choice) */
+} fm_config;
+
+/* Parameters of one batched FMG solve. */
+typedef struct {
+    double pW, pE;        /* Dirichlet data */
+    int32_t n_coarsest;   /* coarsest grid (4) */
+    int32_t nu0, nu1, nu2;
+    int32_t precision;    /* FM_PREC_* */
+} fm_solve_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device.  Checks cfg, computes the
+ * Sobol' direction numbers for M dimensions and allocates the level-sum
+ * buffers.  *out is set only on FM_OK. */
+fm_status fm_create(const fm_config* cfg, fm_ctx** out);
+
+/* Release every device and host resource of ctx (NULL is a no-op). */
+void fm_destroy(fm_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed fm_create
+ * on this thread when ctx is NULL).  Valid until the next call. */
+const char* fm_last_error(const fm_ctx* ctx);
+
+/* ---------------------------------------------------------------- points */
+
+/* MC points (Sec. 2.3): d_xi[s*dim + k] = Phi^{-1}(u),
+ * u = ((w >> 11) + 1/2) 2^-53, where w is 64-bit word k of the Philox4x64-10
+ * stream keyed (seed, 1<<32 | level) at counter (k/4, first + s, 0, 0),
+ * lane k%4.  n samples; dim <= 4096.  Phi^{-1} is CUDA's normcdfinv. */
+fm_status mc_points(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, uint32_t dim,
+                    double* d_xi, void* stream);
+
+/* Randomized Sobol' points (Sec. 2.4 / 3.1): point index first + s (Gray-code
+ * order, x = XOR of the direction numbers selected by the bits of
+ * (n XOR n>>1)), XOR a digital shift per (level, shift r, dimension) drawn
+ * from the Philox stream (seed, 2<<32 | level) at counter (d/4, r, 0, 0),
+ * lane d%4, high 32 bits.  d_x (nullable) receives the uint32 points
+ * [n_shifts][n][dim]; d_xi (nullable) Phi^{-1}((x + 1/2) 2^-32) in the same
+ * layout.  dim <= the context's M. */
+fm_status sobol_points(fm_ctx* ctx, uint32_t level, uint32_t dim, uint64_t first, uint32_t n,
+                       uint32_t first_shift, uint32_t n_shifts, uint32_t* d_x, double* d_xi,
+                       void* stream);
+
+/* Host copy of the Sobol' direction numbers V[d*32 + b] (d < M, b < 32). */
+fm_status sobol_direction_numbers(const fm_ctx* ctx, uint32_t* V);
+
+/* ---------------------------------------------------------------- KL field */
+
+/* Install a KL basis (Sec. 3.1): basis_ref[c*M + k] = sqrt(theta_k) phi_k(x_c)
+ * at the cells c of the finest grid n_ref = n_level0 << (n_levels - 1).  Grid
+ * n of a coarser level samples the field at the finest-grid points that
+ * injection keeps (cell (i,j) of grid n -> cell (s i, s j) of grid n_ref,
+ * s = n_ref / n), so the coarse coefficients of level l and the fine ones of
+ * level l-1 coincide.  basis_ref is device memory if on_device, else host. */
+fm_status kl_basis_set(fm_ctx* ctx, const double* basis_ref, int32_t on_device);
+
+/* Build the KL basis of the exponential covariance sigma2 exp(-|x-y|/lambda)
+ * on the GPU by the Nystrom method: midpoint quadrature on a q x q grid
+ * (q = 0: smallest q >= 32 with q^2 >= 8 M), a dense symmetric eigensolve
+ * (cuSOLVER) of the weighted covariance matrix, and Nystrom interpolation
+ * of the top M eigenfunctions to the field points.  theta_out (nullable,
+ * host) receives the M eigenvalues, captured_out (nullable, host)
+ * sum_{k<=M} theta_k / (sigma2 meas(Omega)).  Synchronous. */
+fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, double* captured_out);
+
+/* Copy the installed basis of the finest grid (the layout kl_basis_set takes)
+ * to basis_ref_out: device memory if on_device, else host.  Synchronous. */
+fm_status kl_basis_get(const fm_ctx* ctx, double* basis_ref_out, int32_t on_device);
+
+/* Field synthesis (Sec. 3.1): d_K[s][c] = exp(sum_k B_l[c][k] d_xi[s*M + k])
+ * for the n samples of MLMC level `level` (grid n_level0 << level),
+ * FP64 throughout.  d_K is [n][N_l][N_l] doubles. */
+fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d_xi,
+                         double* d_K, void* stream);
+
+/* ---------------------------------------------------------------- solver */
+
+/* Full multigrid (Sec. 2.5) for n independent problems on an n_fine x n_fine
+ * grid with coefficients d_K [n][n_fine][n_fine]: coefficients coarsened by
+ * injection K^c[I][J] = K^f[2I][2J] down to the coarsest grid, exact solve
+ * there, then per finer grid bilinear interpolation of the previous stage's
+ * solution and nu0 V(nu1,nu2) cycles (red-black Gauss-Seidel, residual
+ * restricted by summing the 2x2 children, bilinear cell-centred
+ * prolongation).  Outputs: d_qf[s] outflux of the finest stage; d_qc[s]
+ * (nullable) outflux of the stage one grid coarser (the Q^c by-product;
+ * NaN if n_fine == n_coarsest); d_p (nullable) the finest solution
+ * [n][n_fine][n_fine].  n_fine must be n_coarsest times a power of two.
+ * Scratch is owned by the context. */
+fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
+                          const fm_solve_params* prm, double* d_qf, double* d_qc,
+                          double* d_p, void* stream);
+
+/* ---------------------------------------------------------------- MLMC */
+
+/* Running sums of one (level, shift) cell: Neumaier-compensated FP64 pairs
+ * (sum, compensation) of Y, Y^2, Q^f, Q^c, and the sample count.  Y = Q^f on
+ * level 0 and Q^f - Q^c above (Sec. 2.2). */
+typedef struct {
+    double sum_y[2];
+    double sum_y2[2];
+    double sum_qf[2];
+    double sum_qc[2];
+    double count;
+    double pad[7];
+} fm_level_sums;
+
+/* Draw samples first .. first+n-1 of level `level` (MC if shift < 0, else
+ * QMC shift `shift`), synthesise their fields, run the FMG solve and add Y,
+ * Y^2, Q^f, Q^c to *d_sums (device).  d_qf / d_qc (nullable, device [n])
+ * receive the per-sample QoIs.  Processes the samples in batches of at most
+ * the context's max_batch. */
+fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t first, uint32_t n,
+                            int32_t shift, fm_level_sums* d_sums, double* d_qf, double* d_qc,
+                            void* stream);
+
+typedef struct {
+    double eps;           /* target RMSE */
+    int32_t qmc;          /* 0: MLMC (Algorithm 1/3), 1: MLQMC (Algorithm 2) */
+    int64_t n_pilot;      /* initial samples per level (per shift for QMC) */
+    int32_t max_rounds;
+} fm_estimate_opts;
+
+typedef struct {
+    double estimate;                 /* sum_l mean(Y_l) */
+    double var_estimator;            /* sum_l V_l / N_l (MC) or sum_l Var(Y^_l) (QMC) */
+    double mean[FM_MAX_LEVELS];      /* mean(Y_l) */
+    double var[FM_MAX_LEVELS];       /* MC: V_l; QMC: variance of the level estimate */
+    int64_t N[FM_MAX_LEVELS];        /* samples per level (per shift for QMC) */
+    double alpha, beta;              /* fitted rates of |E Y_l| and V_l, l >= 1 */
+    double bias;                     /* |mean(Y_L)| / (2^alpha - 1) */
+    int32_t rounds;
+    double seconds;                  /* wall time of the call */
+} fm_result;
+
+/* The host controller (Algorithm 3 with the MC rule N_l = (2/eps^2)
+ * sqrt(V_l/C_l) sum_k sqrt(V_k C_k), or Algorithm 2's doubling rule for
+ * QMC), at the fixed finest level n_levels - 1, with the cost model
+ * C_l = (4/3) (n_level0 << l)^2.  Uses the default stream, synchronous. */
+fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Per-kernel-family timing for roofline reports (not part of the method).
+ * While a profile is open, the library records a CUDA event pair on the
+ * launching stream around every launch of the families in `family_mask`
+ * (bit f = family f, see fm_kernel_family_name) and notes the algorithmic
+ * bytes and flops of each launch. */
+fm_status fm_profile_begin(fm_ctx* ctx, uint32_t family_mask);
+
+typedef struct {
+    int32_t family;       /* family index */
+    int64_t launches;
+    double ms;            /* sum of event-timed launch durations */
+    double bytes;         /* sum of algorithmic bytes */
+    double flops;         /* sum of algorithmic flops */
+} fm_kernel_stat;
+
+/* Close the profile: synchronises the device, returns one entry per family
+ * with at least one launch (at most max_stats) and the count in *n_stats. */
+fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t max_stats, int32_t* n_stats);
+
+/* Name of kernel family f (NULL when out of range). */
+const char* fm_kernel_family_name(int32_t family);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMGMLMC_H */

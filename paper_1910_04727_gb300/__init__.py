@@ -1,0 +1,200 @@
+"""GB300 full-multigrid multilevel (quasi-) Monte Carlo (arXiv 1910.04727).
+
+A thin binding of the C ABI in include/fmgmlmc.h.  It only marshals
+arguments: every step of the method runs in the library's CUDA kernels.
+PyTorch provides device memory and the current stream.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FM_PREC_FP64, STATUS_NAMES
+
+__all__ = ["Context", "FmError", "FM_PREC_FP64", "load_library"]
+
+
+class FmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def load_library():
+    return _lib.load()
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One fm_ctx: the problem (levels, field, boundary data) and the solver settings."""
+
+    def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
+                 nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
+                 precision=FM_PREC_FP64):
+        self._L = _lib.load()
+        cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
+                            precision, n_shifts, seed, max_batch)
+        h = C.c_void_p()
+        st = self._L.fm_create(C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise FmError(st, self._L.fm_last_error(None).decode())
+        self._h = h
+        self.cfg = cfg
+        self.levels = [n_level0 << l for l in range(n_levels)]
+        self.M = M
+
+    def _check(self, st):
+        if st != 0:
+            raise FmError(st, self._L.fm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.fm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- points
+    def mc_points(self, level, first, n, dim=None, out=None):
+        dim = dim or self.M
+        out = out if out is not None else torch.empty((n, dim), dtype=torch.float64, device="cuda")
+        self._check(self._L.mc_points(self._h, level, first, n, dim, _ptr(out), _stream()))
+        return out
+
+    def sobol_points(self, level, first, n, first_shift=0, n_shifts=1, dim=None, want_x=True,
+                     want_xi=True):
+        dim = dim or self.M
+        x = torch.empty((n_shifts, n, dim), dtype=torch.int32, device="cuda") if want_x else None
+        xi = torch.empty((n_shifts, n, dim), dtype=torch.float64, device="cuda") if want_xi else None
+        self._check(self._L.sobol_points(self._h, level, dim, first, n, first_shift, n_shifts,
+                                         _ptr(x), _ptr(xi), _stream()))
+        return x, xi
+
+    def sobol_direction_numbers(self):
+        V = np.zeros((self.M, 32), np.uint32)
+        self._check(self._L.sobol_direction_numbers(self._h, V.ctypes.data_as(C.c_void_p)))
+        return V
+
+    # ----------------------------------------------------------- KL field
+    def kl_basis_set(self, B_ref):
+        """B_ref: [n_ref^2][M] float64 (numpy array or CUDA tensor)."""
+        if isinstance(B_ref, torch.Tensor):
+            t = B_ref.to(device="cuda", dtype=torch.float64).contiguous()
+            self._check(self._L.kl_basis_set(self._h, _ptr(t), 1))
+            torch.cuda.synchronize()
+        else:
+            a = np.ascontiguousarray(B_ref, dtype=np.float64)
+            self._check(self._L.kl_basis_set(self._h, a.ctypes.data_as(C.c_void_p), 0))
+
+    def kl_basis_build(self, q=0):
+        theta = np.zeros(self.M)
+        cap = C.c_double()
+        self._check(self._L.kl_basis_build(self._h, q, theta.ctypes.data_as(C.c_void_p),
+                                           C.byref(cap)))
+        return theta, cap.value
+
+    def kl_basis_get(self, out=None):
+        """The installed finest-grid basis [n_ref^2][M] (CUDA tensor, or into a
+        given CPU/CUDA float64 tensor)."""
+        n = self.levels[-1]
+        if out is None:
+            out = torch.empty((n * n, self.M), dtype=torch.float64, device="cuda")
+        on_dev = 1 if out.is_cuda else 0
+        self._check(self._L.kl_basis_get(self._h, C.c_void_p(out.data_ptr()), on_dev))
+        return out
+
+    def kl_basis_set_host_ptr(self, ptr):
+        """Install a basis from host memory at address ptr (e.g. pinned)."""
+        self._check(self._L.kl_basis_set(self._h, C.c_void_p(ptr), 0))
+
+    def kl_field_batch(self, level, xi, out=None):
+        n = xi.shape[0]
+        N = self.levels[level]
+        out = out if out is not None else torch.empty((n, N, N), dtype=torch.float64, device="cuda")
+        self._check(self._L.kl_field_batch(self._h, level, n, _ptr(xi), _ptr(out), _stream()))
+        return out
+
+    # ----------------------------------------------------------- solver
+    def solve_params(self, **over):
+        c = self.cfg
+        p = _lib.FmSolveParams(c.pW, c.pE, c.n_coarsest, c.nu0, c.nu1, c.nu2, c.precision)
+        for k, v in over.items():
+            setattr(p, k, v)
+        return p
+
+    def fmg_solve_batch(self, K, want_qc=True, want_p=False, **params):
+        """K: CUDA float64 [S][n][n]. Returns (qf, qc or None, p or None)."""
+        S, n = K.shape[0], K.shape[-1]
+        prm = self.solve_params(**params)
+        qf = torch.empty(S, dtype=torch.float64, device="cuda")
+        qc = torch.empty(S, dtype=torch.float64, device="cuda") if want_qc else None
+        p = torch.empty((S, n, n), dtype=torch.float64, device="cuda") if want_p else None
+        self._check(self._L.fmg_solve_batch(self._h, n, S, _ptr(K), C.byref(prm), _ptr(qf), _ptr(qc),
+                                            _ptr(p), _stream()))
+        return qf, qc, p
+
+    # ----------------------------------------------------------- MLMC
+    @staticmethod
+    def new_sums(count=1):
+        return torch.zeros((count, 16), dtype=torch.float64, device="cuda")
+
+    def mlmc_sample_level(self, level, first, n, shift=-1, sums=None, want_q=False):
+        qf = torch.empty(n, dtype=torch.float64, device="cuda") if want_q else None
+        qc = torch.empty(n, dtype=torch.float64, device="cuda") if want_q else None
+        self._check(self._L.mlmc_sample_level(self._h, level, first, n, shift, _ptr(sums), _ptr(qf),
+                                              _ptr(qc), _stream()))
+        return qf, qc
+
+    @staticmethod
+    def read_sums(sums):
+        """(mean, var, count, sum_qf, sum_qc) of one fm_level_sums row."""
+        s = sums.detach().cpu().numpy()
+        n = s[8]
+        sy, sy2 = s[0] + s[1], s[2] + s[3]
+        mean = sy / n
+        var = (sy2 - sy * sy / n) / (n - 1) if n > 1 else 0.0
+        return mean, var, n, s[4] + s[5], s[6] + s[7]
+
+    # ----------------------------------------------------------- profiling
+    def profile_begin(self, mask=0xFFFFFFFF):
+        self._check(self._L.fm_profile_begin(self._h, mask))
+
+    def profile_end(self):
+        """{family name: dict(launches, ms, bytes, flops)} since profile_begin."""
+        stats = (_lib.FmKernelStat * 32)()
+        n = C.c_int32()
+        self._check(self._L.fm_profile_end(self._h, stats, 32, C.byref(n)))
+        out = {}
+        for s in stats[:n.value]:
+            out[self._L.fm_kernel_family_name(s.family).decode()] = dict(
+                launches=s.launches, ms=s.ms, bytes=s.bytes, flops=s.flops)
+        return out
+
+    def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100):
+        torch.cuda.synchronize()
+        opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds)
+        res = _lib.FmResult()
+        self._check(self._L.mlmc_estimate(self._h, C.byref(opts), C.byref(res)))
+        L = len(self.levels)
+        return dict(estimate=res.estimate, var_estimator=res.var_estimator,
+                    means=np.array(res.mean[:L]), V=np.array(res.var[:L]),
+                    N=np.array(res.N[:L]), alpha=res.alpha, beta=res.beta, bias=res.bias,
+                    rounds=res.rounds, seconds=res.seconds)

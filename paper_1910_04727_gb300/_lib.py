@@ -1,0 +1,97 @@
+"""ctypes declarations of the C ABI in include/fmgmlmc.h.
+
+Loading fails loudly when the library has not been built: there is no
+fallback implementation.
+"""
+import ctypes as C
+import os
+
+from .build import LIB_PATH
+
+FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENOTCONV, FM_ETIMEOUT, FM_EUNSUPPORTED = range(7)
+FM_MAX_LEVELS = 12
+FM_PREC_FP64 = 0
+
+STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENOTCONV",
+                5: "FM_ETIMEOUT", 6: "FM_EUNSUPPORTED"}
+
+# every entry point declared in include/fmgmlmc.h
+EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_points",
+           "sobol_direction_numbers", "kl_basis_set", "kl_basis_build", "kl_basis_get", "kl_field_batch",
+           "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
+           "fm_profile_end", "fm_kernel_family_name"]
+
+
+class FmConfig(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_level0", C.c_int32), ("n_coarsest", C.c_int32),
+                ("M", C.c_int32), ("sigma2", C.c_double), ("lambda_", C.c_double),
+                ("pW", C.c_double), ("pE", C.c_double), ("nu0", C.c_int32), ("nu1", C.c_int32),
+                ("nu2", C.c_int32), ("precision", C.c_int32), ("n_shifts", C.c_int32),
+                ("seed", C.c_uint64), ("max_batch", C.c_int64)]
+
+
+class FmSolveParams(C.Structure):
+    _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("n_coarsest", C.c_int32),
+                ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class FmLevelSums(C.Structure):
+    _fields_ = [("sum_y", C.c_double * 2), ("sum_y2", C.c_double * 2), ("sum_qf", C.c_double * 2),
+                ("sum_qc", C.c_double * 2), ("count", C.c_double), ("pad", C.c_double * 7)]
+
+
+class FmEstimateOpts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("qmc", C.c_int32), ("n_pilot", C.c_int64),
+                ("max_rounds", C.c_int32)]
+
+
+class FmKernelStat(C.Structure):
+    _fields_ = [("family", C.c_int32), ("launches", C.c_int64), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class FmResult(C.Structure):
+    _fields_ = [("estimate", C.c_double), ("var_estimator", C.c_double),
+                ("mean", C.c_double * FM_MAX_LEVELS), ("var", C.c_double * FM_MAX_LEVELS),
+                ("N", C.c_int64 * FM_MAX_LEVELS), ("alpha", C.c_double), ("beta", C.c_double),
+                ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libfmgmlmc.so and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libfmgmlmc.so is not built (%s); run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    P, U32, U64, I32, I64, D = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "fm_create": (I32, [C.POINTER(FmConfig), C.POINTER(P)]),
+        "fm_destroy": (None, [P]),
+        "fm_last_error": (C.c_char_p, [P]),
+        "mc_points": (I32, [P, U32, U64, U32, U32, P, P]),
+        "sobol_points": (I32, [P, U32, U32, U64, U32, U32, U32, P, P, P]),
+        "sobol_direction_numbers": (I32, [P, P]),
+        "kl_basis_set": (I32, [P, P, I32]),
+        "kl_basis_build": (I32, [P, I32, P, P]),
+        "kl_basis_get": (I32, [P, P, I32]),
+        "kl_field_batch": (I32, [P, I32, U32, P, P, P]),
+        "fmg_solve_batch": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P, P]),
+        "mlmc_sample_level": (I32, [P, I32, U64, U32, I32, P, P, P, P]),
+        "mlmc_estimate": (I32, [P, C.POINTER(FmEstimateOpts), C.POINTER(FmResult)]),
+        "fm_profile_begin": (I32, [P, U32]),
+        "fm_profile_end": (I32, [P, P, I32, C.POINTER(I32)]),
+        "fm_kernel_family_name": (C.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L

@@ -1,0 +1,79 @@
+// Context lifetime and error reporting of the C ABI.
+#include <cstring>
+
+#include "common.cuh"
+
+namespace fm {
+
+static thread_local std::string g_create_error;
+
+void set_error(const fm_ctx* ctx, const std::string& msg) {
+    if (ctx) const_cast<fm_ctx*>(ctx)->last_error = msg;
+    else g_create_error = msg;
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
+    FM_CHECK_ARG(nullptr, cfg && out, "fm_create: null argument");
+    FM_CHECK_ARG(nullptr, cfg->n_levels >= 1 && cfg->n_levels <= FM_MAX_LEVELS, "fm_create: n_levels out of range");
+    FM_CHECK_ARG(nullptr, cfg->n_coarsest >= 2 && cfg->n_coarsest <= 4, "fm_create: n_coarsest must be 2..4");
+    int m = 0;
+    while ((cfg->n_coarsest << m) < cfg->n_level0) ++m;
+    FM_CHECK_ARG(nullptr, (cfg->n_coarsest << m) == cfg->n_level0,
+                 "fm_create: n_level0 must be n_coarsest times a power of two");
+    FM_CHECK_ARG(nullptr, ((int64_t)cfg->n_level0 << (cfg->n_levels - 1)) <= 8192, "fm_create: finest grid above 8192");
+    FM_CHECK_ARG(nullptr, cfg->M >= 1 && cfg->M <= 4096, "fm_create: M must be in [1, 4096]");
+    FM_CHECK_ARG(nullptr, cfg->sigma2 > 0 && cfg->lambda > 0, "fm_create: sigma2 and lambda must be positive");
+    FM_CHECK_ARG(nullptr, cfg->nu0 >= 1 && cfg->nu1 >= 0 && cfg->nu2 >= 0 && cfg->nu1 + cfg->nu2 >= 1,
+                 "fm_create: need nu0 >= 1 and nu1 + nu2 >= 1");
+    FM_CHECK_ARG(nullptr, cfg->precision == FM_PREC_FP64, "fm_create: unknown precision");
+    FM_CHECK_ARG(nullptr, cfg->n_shifts >= 0 && cfg->n_shifts <= 64, "fm_create: n_shifts must be in [0, 64]");
+    fm_ctx* ctx = new (std::nothrow) fm_ctx();
+    if (!ctx) {
+        set_error(nullptr, "fm_create: host allocation failed");
+        return FM_ENOMEM;
+    }
+    ctx->cfg = *cfg;
+    cudaGetDevice(&ctx->device);
+    if (sobol_direction_numbers_host((uint32_t)cfg->M, ctx->h_sobol_V) != 0) {
+        delete ctx;
+        set_error(nullptr, "fm_create: Sobol' direction numbers unavailable for this M");
+        return FM_EINVAL;
+    }
+    const size_t vbytes = ctx->h_sobol_V.size() * sizeof(uint32_t);
+    const size_t sums = (size_t)cfg->n_levels * (cfg->n_shifts > 0 ? cfg->n_shifts : 1);
+    if (cudaMalloc((void**)&ctx->d_sobol_V, vbytes) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_sums, sums * sizeof(fm_level_sums)) != cudaSuccess) {
+        fm_destroy(ctx);
+        set_error(nullptr, "fm_create: device allocation failed");
+        return FM_ENOMEM;
+    }
+    if (cudaMemcpy(ctx->d_sobol_V, ctx->h_sobol_V.data(), vbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        fm_destroy(ctx);
+        set_error(nullptr, "fm_create: copy of the direction numbers failed");
+        return FM_ECUDA;
+    }
+    *out = ctx;
+    return FM_OK;
+}
+
+extern "C" void fm_destroy(fm_ctx* ctx) {
+    if (!ctx) return;
+    for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->d_basis[l]);
+    cudaFree(ctx->d_sobol_V);
+    cudaFree(ctx->arena.base);
+    cudaFree(ctx->d_xi);
+    cudaFree(ctx->d_K);
+    cudaFree(ctx->d_q);
+    cudaFree(ctx->d_sums);
+    cudaFree(ctx->d_partials);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+extern "C" const char* fm_last_error(const fm_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}

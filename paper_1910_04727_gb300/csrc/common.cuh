@@ -1,0 +1,190 @@
+// Internal definitions shared by the translation units of libfmgmlmc.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fmgmlmc.h"
+
+namespace fm {
+
+// ------------------------------------------------------------------ Philox
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+// (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2, c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0),
+// with the key bumped by the Weyl constants between rounds.
+constexpr uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ULL;
+constexpr uint64_t kPhiloxM1 = 0xCA5A826395121157ULL;
+constexpr uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ULL;
+constexpr uint64_t kPhiloxW1 = 0xBB67AE8584CAA73BULL;
+
+// Stream purposes (high half of key[1]).
+constexpr uint64_t kPurposeMC = 1;
+constexpr uint64_t kPurposeShift = 2;
+constexpr uint64_t kPurposeSobolDir = 3;
+constexpr uint64_t kSobolDirSeed = 0x1910047270ULL;
+
+struct u64x4 {
+    uint64_t v[4];
+};
+
+__host__ __device__ inline void mulhilo64(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+#ifdef __CUDA_ARCH__
+    hi = __umul64hi(a, b);
+    lo = a * b;
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    hi = (uint64_t)(p >> 64);
+    lo = (uint64_t)p;
+#endif
+}
+
+__host__ __device__ inline u64x4 philox4x64(u64x4 c, uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(kPhiloxM0, c.v[0], hi0, lo0);
+        mulhilo64(kPhiloxM1, c.v[2], hi1, lo1);
+        u64x4 n = {{hi1 ^ c.v[1] ^ k0, lo1, hi0 ^ c.v[3] ^ k1, lo0}};
+        c = n;
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ errors
+#define FM_CUDA_TRY(ctx, expr)                                                        \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            fm::set_error((ctx), std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+            return FM_ECUDA;                                                          \
+        }                                                                             \
+    } while (0)
+
+#define FM_CHECK_ARG(ctx, cond, msg)                   \
+    do {                                               \
+        if (!(cond)) {                                 \
+            fm::set_error((ctx), std::string(msg));    \
+            return FM_EINVAL;                          \
+        }                                              \
+    } while (0)
+
+#define FM_TRY(expr)                 \
+    do {                             \
+        fm_status s_ = (expr);       \
+        if (s_ != FM_OK) return s_;  \
+    } while (0)
+
+void set_error(const fm_ctx* ctx, const std::string& msg);
+
+// ------------------------------------------------------------------ profiling
+enum Family {
+    kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
+    kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
+    kFamOutflux, kFamLevelSums, kFamilyCount
+};
+
+struct ProfRecord {
+    int family;
+    cudaEvent_t start, stop;
+    double bytes = 0.0, flops = 0.0;
+};
+
+struct Profiler {
+    bool active = false;
+    uint32_t mask = 0;
+    std::vector<ProfRecord> records;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+};
+
+// ------------------------------------------------------------------ arena
+// A grow-only device buffer the context hands out in 256-byte-aligned pieces.
+struct Arena {
+    char* base = nullptr;
+    size_t capacity = 0;
+    size_t used = 0;
+};
+
+}  // namespace fm
+
+struct fm_ctx {
+    fm_config cfg{};
+    int device = 0;
+    std::string last_error;
+    // KL basis per MLMC level: [n_l^2][M] FP64, row-subsets of the finest grid's basis.
+    double* d_basis[FM_MAX_LEVELS] = {};
+    bool basis_ready = false;
+    // Sobol' direction numbers [M][32] (device and host copies).
+    uint32_t* d_sobol_V = nullptr;
+    std::vector<uint32_t> h_sobol_V;
+    // scratch
+    fm::Arena arena;
+    double* d_xi = nullptr;          // points of the current batch
+    size_t xi_capacity = 0;
+    double* d_K = nullptr;           // fields of the current batch
+    size_t K_capacity = 0;
+    double* d_q = nullptr;           // Q^f, Q^c of the current batch
+    size_t q_capacity = 0;
+    fm_level_sums* d_sums = nullptr; // [n_levels][max(1, n_shifts)] for mlmc_estimate
+    double* d_partials = nullptr;    // per-block partial sums of the level-sum kernel
+    size_t partial_capacity = 0;
+    fm::Profiler prof;
+};
+
+namespace fm {
+
+// Grows *buf to hold `count` elements of T; previous contents are dropped.
+template <typename T>
+fm_status ensure(fm_ctx* ctx, T** buf, size_t* capacity, size_t count) {
+    if (*capacity >= count && *buf) return FM_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *capacity = 0;
+    if (cudaMalloc((void**)buf, sizeof(T) * count) != cudaSuccess) {
+        set_error(ctx, "device allocation of " + std::to_string(sizeof(T) * count) + " bytes failed");
+        return FM_ENOMEM;
+    }
+    *capacity = count;
+    return FM_OK;
+}
+
+inline int grid_of_level(const fm_ctx* ctx, int level) { return ctx->cfg.n_level0 << level; }
+inline int finest_grid(const fm_ctx* ctx) { return grid_of_level(ctx, ctx->cfg.n_levels - 1); }
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Event-pair timing around one launch of `family` (no-op unless profiling).
+int prof_start(fm_ctx* ctx, int family, cudaStream_t st);
+void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops);
+
+#define FM_TIMED(ctx, family, st, bytes, flops, ...)          \
+    do {                                                       \
+        const int pi_ = fm::prof_start((ctx), (family), (st)); \
+        __VA_ARGS__;                                           \
+        fm::prof_stop((ctx), pi_, (st), (bytes), (flops));     \
+    } while (0)
+
+// Samples per device batch for grid n (memory of the FMG hierarchy and field).
+int64_t batch_limit(const fm_ctx* ctx, int n);
+
+// FMG solve into caller-provided outputs (used by mlmc_sample_level too).
+fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
+                         const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
+                         cudaStream_t stream);
+
+// Level sums of a batch (mlmc.cu).
+fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc,
+                         int coarse, fm_level_sums* d_sums, cudaStream_t stream);
+
+// Host-side Sobol' direction numbers (points.cu).
+int sobol_direction_numbers_host(uint32_t dim, std::vector<uint32_t>& V);
+
+}  // namespace fm

@@ -1,0 +1,77 @@
+// Event-pair timing of kernel families for roofline reports.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fm {
+
+static const char* kFamilyNames[kFamilyCount] = {
+    "points", "kl_gemm_exp", "inject", "coefficients", "stage_rhs", "rbgs_smoother",
+    "residual_restrict", "prolong_correct", "fmg_interpolate", "coarse_inverse",
+    "coarse_solve", "outflux", "level_sums"};
+
+int prof_start(fm_ctx* ctx, int family, cudaStream_t st) {
+    Profiler& P = ctx->prof;
+    if (!P.active || !((P.mask >> family) & 1u)) return -1;
+    while (P.pool.size() < P.pool_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        P.pool.push_back(e);
+    }
+    ProfRecord r;
+    r.family = family;
+    r.start = P.pool[P.pool_used++];
+    r.stop = P.pool[P.pool_used++];
+    cudaEventRecord(r.start, st);
+    P.records.push_back(r);
+    return (int)P.records.size() - 1;
+}
+
+void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops) {
+    if (idx < 0) return;
+    ProfRecord& r = ctx->prof.records[idx];
+    cudaEventRecord(r.stop, st);
+    r.bytes = bytes;
+    r.flops = flops;
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" fm_status fm_profile_begin(fm_ctx* ctx, uint32_t family_mask) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_profile_begin: null context");
+    ctx->prof.active = true;
+    ctx->prof.mask = family_mask;
+    ctx->prof.records.clear();
+    ctx->prof.pool_used = 0;
+    return FM_OK;
+}
+
+extern "C" fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t max_stats,
+                                    int32_t* n_stats) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_profile_end: null context");
+    ctx->prof.active = false;
+    FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    fm_kernel_stat acc[kFamilyCount];
+    for (int f = 0; f < kFamilyCount; ++f) acc[f] = fm_kernel_stat{f, 0, 0.0, 0.0, 0.0};
+    for (const ProfRecord& r : ctx->prof.records) {
+        float ms = 0.0f;
+        FM_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, r.start, r.stop));
+        fm_kernel_stat& a = acc[r.family];
+        a.launches += 1;
+        a.ms += ms;
+        a.bytes += r.bytes;
+        a.flops += r.flops;
+    }
+    int out = 0;
+    for (int f = 0; f < kFamilyCount; ++f)
+        if (acc[f].launches > 0 && out < max_stats && stats) stats[out++] = acc[f];
+    if (n_stats) *n_stats = out;
+    ctx->prof.records.clear();
+    return FM_OK;
+}
+
+extern "C" const char* fm_kernel_family_name(int32_t family) {
+    return (family >= 0 && family < kFamilyCount) ? kFamilyNames[family] : nullptr;
+}

@@ -1,0 +1,57 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point include/fmgmlmc.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fmgmlmc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1910_04727_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_method_entry_points():
+    names = declared_functions()
+    for required in ("mlmc_sample_level", "fmg_solve_batch", "kl_field_batch", "sobol_points",
+                     "mlmc_estimate", "fm_create", "fm_destroy", "fm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_every_export(lib_path):
+    from paper_1910_04727_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_functions()
+    L = _lib.load(lib_path)
+    for n in _lib.EXPORTS:
+        assert getattr(L, n).argtypes is not None or n == "fm_destroy"
+
+
+def test_create_rejects_bad_config_without_touching_the_gpu(lib_path):
+    from paper_1910_04727_gb300 import _lib
+    L = _lib.load(lib_path)
+    cfg = _lib.FmConfig(0, 16, 4, 8, 1.0, 0.3, 1.0, 0.0, 2, 2, 2, 0, 0, 1, 0)   # n_levels = 0
+    h = ctypes.c_void_p()
+    assert L.fm_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.FM_EINVAL
+    assert b"n_levels" in L.fm_last_error(None)
+    cfg = _lib.FmConfig(2, 12, 4, 8, 1.0, 0.3, 1.0, 0.0, 2, 2, 2, 0, 0, 1, 0)    # 12 != 4*2^m
+    assert L.fm_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.FM_EINVAL
+    assert not h.value

@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: integer work (Sobol' points, direction numbers) bit-exact; FP64
+per-sample QoI within 1e-10 relative (the oracle and the kernels run the same
+algorithm in a different rounding order: FMA contraction, reduction order
+and the inverse-based coarsest solve differ at the 1e-15 level, amplified at
+most by the conditioning of the small FV systems); fields within 1e-13.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import kl as okl
+from oracle import lib as OL
+from oracle import mlmc as omlmc
+
+pytestmark = pytest.mark.gpu
+
+RTOL_Q = 1e-10
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import paper_1910_04727_gb300 as fm
+    fm.load_library()
+    return fm
+
+
+@pytest.fixture(scope="module")
+def small(fm):
+    """Three levels 8..32, 24 KL modes, the oracle's basis installed."""
+    basis = okl.KLBasis(32, 24, 1.0, 0.3, q=24)
+    ctx = fm.Context(3, 8, 24, sigma2=1.0, lam=0.3, n_shifts=4, seed=77)
+    ctx.kl_basis_set(basis.B_ref)
+    return ctx, basis
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+# ------------------------------------------------------------------ points
+def test_mc_points_match_oracle(small):
+    ctx, _ = small
+    for level, first, n, dim in [(0, 0, 257, 24), (2, 1000, 33, 7), (1, 2 ** 40, 5, 24)]:
+        xi = ctx.mc_points(level, first, n, dim).cpu().numpy()
+        ref = OL.mc_normals(77, level, first, n, dim)
+        np.testing.assert_allclose(xi, ref, rtol=1e-13, atol=1e-15)
+
+
+def test_sobol_direction_numbers_bit_exact(small):
+    ctx, _ = small
+    np.testing.assert_array_equal(ctx.sobol_direction_numbers(), OL.sobol_direction_numbers(24))
+
+
+def test_sobol_points_bit_exact_and_xi(small):
+    ctx, _ = small
+    V = OL.sobol_direction_numbers(24)
+    for level, first, n, s0, R in [(0, 0, 300, 0, 4), (2, 12345, 77, 2, 2)]:
+        x, xi = ctx.sobol_points(level, first, n, s0, R)
+        shifts = OL.sobol_shifts(77, level, s0 + R, 24)[s0:]
+        ref_x, ref_xi = OL.sobol_points(V, first, n, shifts, want_xi=True)
+        np.testing.assert_array_equal(x.cpu().numpy().view(np.uint32), ref_x)
+        np.testing.assert_allclose(xi.cpu().numpy(), ref_xi, rtol=1e-13, atol=1e-15)
+
+
+def test_empty_and_invalid_calls(fm, small):
+    ctx, _ = small
+    assert ctx.mc_points(0, 0, 0, 24).numel() == 0
+    with pytest.raises(fm.FmError, match="EINVAL"):
+        ctx.mc_points(0, 0, 4, 5000)
+    with pytest.raises(fm.FmError, match="EINVAL"):
+        ctx.sobol_points(0, 0, 4, dim=25)
+    K = torch.ones((0, 8, 8), dtype=torch.float64, device="cuda")
+    qf, qc, _ = ctx.fmg_solve_batch(K)
+    assert qf.numel() == 0
+    with pytest.raises(fm.FmError, match="n_fine"):
+        ctx.fmg_solve_batch(torch.ones((2, 12, 12), dtype=torch.float64, device="cuda"))
+
+
+# ------------------------------------------------------------------ KL field
+def test_kl_field_matches_oracle(small):
+    ctx, basis = small
+    xi = W.normals(67, 24, tag=50)
+    for level, n in enumerate([8, 16, 32]):
+        K = ctx.kl_field_batch(level, torch.tensor(xi, device="cuda")).cpu().numpy()
+        ref = okl.synthesize(basis.level_basis(n), xi).reshape(-1, n, n)
+        assert _rel(K, ref) < 1e-13
+
+
+# ------------------------------------------------------------------ solver
+@pytest.mark.parametrize("n,S", [(4, 5), (8, 37), (16, 33), (32, 129), (64, 19), (128, 7), (256, 3)])
+def test_fmg_solve_matches_oracle(small, n, S):
+    ctx, _ = small
+    K = W.smooth_lognormal_field(n, S=S, tag=60 + n)
+    qf, qc, p = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True)
+    rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(), want_p=True)
+    assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
+    if n > 4:
+        assert _rel(qc.cpu().numpy(), rc) < RTOL_Q
+    else:
+        assert np.all(np.isnan(qc.cpu().numpy()))
+    np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=1e-11)
+
+
+def test_fmg_other_parameters_match_oracle(small):
+    ctx, _ = small
+    K = W.smooth_lognormal_field(32, S=9, tag=70)
+    for kw in [dict(nu0=1, nu1=1, nu2=1), dict(nu0=3, nu1=2, nu2=1), dict(pW=100.0, pE=0.0),
+               dict(pW=3.0, pE=1.0), dict(n_coarsest=2)]:
+        qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), **kw)
+        rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params(**{k: v for k, v in kw.items() if k != "n_coarsest"}),
+                                          n0=kw.get("n_coarsest", 4))
+        assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
+        assert _rel(qc.cpu().numpy(), rc) < RTOL_Q
+
+
+def test_constant_field_exact_on_gpu(small):
+    ctx, _ = small
+    for n in (4, 16, 128):
+        qf, qc, p = ctx.fmg_solve_batch(torch.ones((3, n, n), dtype=torch.float64, device="cuda"),
+                                        want_p=True)
+        assert np.max(np.abs(qf.cpu().numpy() - 1)) < 1e-13
+        x = (np.arange(n) + 0.5) / n
+        np.testing.assert_allclose(p.cpu().numpy()[1], np.broadcast_to(1 - x, (n, n)), atol=1e-13)
+
+
+# ------------------------------------------------------------------ MLMC
+def test_sample_level_matches_oracle_mc_and_qmc(small):
+    ctx, basis = small
+    V = OL.sobol_direction_numbers(24)
+    osamp = omlmc.FMGSampler([8, 16, 32], basis, seed=77, qmc_dirnums=V, n_shifts=4)
+    for level in range(3):
+        for shift in (-1, 2):
+            sums = ctx.new_sums()
+            qf, qc = ctx.mlmc_sample_level(level, 50, 101, shift, sums=sums[0], want_q=True)
+            y, rf, rc = osamp(level, 50, 101, None if shift < 0 else shift)
+            assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
+            if level > 0:
+                assert _rel(qc.cpu().numpy(), rc) < RTOL_Q
+            mean, var, cnt, _, _ = ctx.read_sums(sums[0])
+            assert cnt == 101
+            assert abs(mean - np.mean(y)) < 1e-12 * max(1.0, abs(np.mean(y)))
+            assert abs(var - np.var(y, ddof=1)) < 1e-9 * np.var(y, ddof=1)
+
+
+def test_gpu_telescoping_identity_same_omega(small):
+    """Q^c of level l equals Q^f of level l-1 for the same KL coefficients."""
+    ctx, _ = small
+    xi = torch.tensor(W.normals(40, 24, tag=80), device="cuda")
+    q = []
+    for level in range(3):
+        K = ctx.kl_field_batch(level, xi)
+        q.append(ctx.fmg_solve_batch(K))
+    for level in (1, 2):
+        np.testing.assert_allclose(q[level][1].cpu().numpy(), q[level - 1][0].cpu().numpy(),
+                                   rtol=1e-13)
+
+
+def test_level_sums_are_deterministic(small):
+    ctx, _ = small
+    a, b = ctx.new_sums(), ctx.new_sums()
+    ctx.mlmc_sample_level(1, 0, 5000, -1, sums=a[0])
+    ctx.mlmc_sample_level(1, 0, 2500, -1, sums=b[0])
+    ctx.mlmc_sample_level(1, 2500, 2500, -1, sums=b[0])
+    torch.cuda.synchronize()
+    ma = ctx.read_sums(a[0])
+    mb = ctx.read_sums(b[0])
+    assert abs(ma[0] - mb[0]) < 1e-14 * abs(ma[0])
+    c = ctx.new_sums()
+    ctx.mlmc_sample_level(1, 0, 5000, -1, sums=c[0])
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
+
+
+def test_mlmc_estimate_matches_oracle_controller(fm):
+    levels = [8, 16, 32]
+    basis = okl.KLBasis(32, 16, 1.0, 0.3, q=24)
+    ctx = fm.Context(3, 8, 16, seed=91, n_shifts=4)
+    ctx.kl_basis_set(basis.B_ref)
+    eps = 6e-3
+    res = ctx.mlmc_estimate(eps, n_pilot=64)
+    ref = omlmc.mlmc(omlmc.FMGSampler(levels, basis, seed=91), 2, eps, 64,
+                     omlmc.cost_model(np.array(levels) ** 2))
+    assert res["var_estimator"] <= eps ** 2 / 2 * 1.001
+    if np.array_equal(res["N"], ref["N"]):
+        assert abs(res["estimate"] - ref["estimate"]) < 1e-10 * abs(ref["estimate"])
+    else:   # the sample-size rule may round one V_l differently (ceil at a tie)
+        assert np.max(np.abs(res["N"] - ref["N"]) / ref["N"]) < 0.01
+        assert abs(res["estimate"] - ref["estimate"]) < 3 * np.sqrt(ref["var_estimator"])
+    qres = ctx.mlmc_estimate(eps, qmc=True, n_pilot=16)
+    assert qres["var_estimator"] <= eps ** 2 / 2
+    assert abs(qres["estimate"] - ref["estimate"]) < 4 * np.sqrt(ref["var_estimator"] + qres["var_estimator"])
+
+
+def test_kl_basis_build_matches_oracle_spectrum(fm):
+    ctx = fm.Context(2, 16, 32, sigma2=1.0, lam=0.3)
+    theta, captured = ctx.kl_basis_build(q=24)
+    th, V, qpts, w, trace = okl.nystrom_eigs(24, 32, 1.0, 0.3)
+    np.testing.assert_allclose(theta, th, rtol=1e-10)
+    assert abs(captured - th.sum() / trace) < 1e-12
+    # the field covariance B B^T does not depend on the basis within degenerate pairs
+    B_or = okl.nystrom_basis(okl.field_points(32, 32), th, V, qpts, w, 1.0, 0.3)
+    xi = torch.eye(32, dtype=torch.float64, device="cuda")
+    # exp(B e_k) gives column k of the basis back through the field synthesis
+    Bg = torch.log(ctx.kl_field_batch(1, xi)).reshape(32, -1).T.cpu().numpy()
+    np.testing.assert_allclose(Bg @ Bg.T, B_or @ B_or.T, atol=1e-10)
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_level_sampled_against_oracle(fm):
+    """The 256 x 256 level of the five-level workload (128 modes) in the batch
+    shape the benchmark uses, sampled outputs checked one by one."""
+    wl = W.WORKLOADS["fmg_mlmc5"]
+    basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32)
+    ctx = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, seed=wl.seed)
+    ctx.kl_basis_set(basis.B_ref)
+    n = 1024
+    qf, qc = ctx.mlmc_sample_level(4, 0, n, -1, sums=ctx.new_sums()[0], want_q=True)
+    qf, qc = qf.cpu().numpy(), qc.cpu().numpy()
+    assert np.all(np.isfinite(qf)) and np.all(np.isfinite(qc))
+    picks = [0, 1, 511, 1023]
+    xi = OL.mc_normals(wl.seed, 4, 0, n, wl.M)[picks]
+    K = okl.synthesize(basis.level_basis(256), xi).reshape(-1, 256, 256)
+    rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params())
+    assert _rel(qf[picks], rf) < RTOL_Q
+    assert _rel(qc[picks], rc) < RTOL_Q
