@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle's bounded timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64_converged", "fp64_fmg2"])
+    ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     return ap.parse_args()
 
 
@@ -110,14 +112,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_level_seconds(wl, budget_s, levels=None):
+def oracle_params(converged):
+    from oracle import lib as olib
+    return olib.params(converged=converged, tol=1e-10, max_cycles=200)
+
+
+def oracle_level_seconds(wl, budget_s, converged):
     """Seconds per sample of the oracle on each level, on all host cores,
     from a bounded sample (about budget_s seconds in total)."""
     from oracle import kl as okl
     from oracle import mlmc as omlmc
     cores = os.cpu_count() or 1
     basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32 if wl.M <= 128 else 0)
-    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, nthreads=cores)
+    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, prm=oracle_params(converged), nthreads=cores)
     per = []
     share = budget_s / len(wl.levels)
     counts = []
@@ -141,6 +148,56 @@ def flush_l2(buf):
     buf.fill_(1.0)
 
 
+FORMS = {
+    # FP32 smoothing/transfers/coarsest solve inside FP64 iterative refinement
+    # of the stages giving Q^c and Q^f, to ||r|| <= 1e-10 ||b||
+    "mixed": dict(precision=1, converged=True),
+    # the same converged solves, every step in FP64
+    "fp64_converged": dict(precision=0, converged=True),
+    # the paper's fixed schedule: 2 V(2,2) cycles per FMG stage, FP64
+    "fp64_fmg2": dict(precision=0, converged=False),
+}
+
+
+def make_ctx(fm, wl, rank, form):
+    f = FORMS[form]
+    return fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
+                      pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
+                      n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank, precision=f["precision"],
+                      converged=f["converged"], tol=1e-10, max_cycles=200)
+
+
+def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=False, clocks=None,
+                   dist=None):
+    def estimate():
+        return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+
+    for _ in range(warmup):
+        estimate()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    if profile:
+        ctx.profile_begin()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, results = [], []
+    for _ in range(steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        r = estimate()
+        stop.record()
+        torch.cuda.synchronize()
+        times.append(start.elapsed_time(stop) / 1e3)
+        results.append(r)
+    prof = ctx.profile_end() if profile else None
+    clk = clocks.stop() if clocks else None
+    return times, results, prof, clk
+
+
 def run_native(args, wl, eps):
     import torch
     import torch.distributed as dist
@@ -154,42 +211,19 @@ def run_native(args, wl, eps):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     fm.load_library()
-    # replicas: each rank runs its own estimate with its own seed
-    ctx = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
-                     pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
-                     n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank)
-    theta, captured = ctx.kl_basis_build(q=wl.kl_q)
     n_ref = wl.n_ref
     flush = torch.empty(512 << 20 >> 2, dtype=torch.float32, device="cuda")
 
-    def estimate():
-        return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+    # replicas: each rank runs its own estimate with its own seed; the KL
+    # basis is built once on the GPU and installed in every form's context
+    ctx = make_ctx(fm, wl, rank, args.form)
+    theta, captured = ctx.kl_basis_build(q=wl.kl_q)
+    B_dev = ctx.kl_basis_get()
 
-    for _ in range(args.warmup):
-        estimate()
-    torch.cuda.synchronize()
-
-    # timed region: K estimates, each from an empty estimator
     clocks = ClockSampler(local)
-    clocks.start()
-    times, results = [], []
-    ctx.profile_begin()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush_l2(flush)
-        torch.cuda.synchronize()
-        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        start.record()
-        r = estimate()
-        stop.record()
-        torch.cuda.synchronize()
-        times.append(start.elapsed_time(stop) / 1e3)
-        results.append(r)
-    torch.cuda.synchronize()
-    prof = ctx.profile_end()
-    clk = clocks.stop()
+    times, results, prof, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
+                                               profile=True, clocks=clocks,
+                                               dist=dist if world > 1 else None)
     t_total = float(np.sum(times))
     if world > 1:
         t = torch.tensor([t_total], device="cuda")
@@ -197,14 +231,24 @@ def run_native(args, wl, eps):
         t_total = float(t.item())
         dist.barrier()
 
+    # the other forms of the same estimate, timed the same way
+    others = {}
+    for form in FORMS:
+        if form == args.form or args.only_chosen:
+            continue
+        c2 = make_ctx(fm, wl, rank, form)
+        c2.kl_basis_set(B_dev)
+        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush)
+        others[form] = {"value": float(np.mean(ts)), "unit": "s",
+                        "estimate": float(np.mean([r["estimate"] for r in rs])),
+                        "N_per_level": [int(x) for x in rs[-1]["N"]]}
+        c2.close()
+
     # end to end through the public API from pinned host memory: basis upload,
     # estimate, result read-back
     B_host = torch.empty((n_ref * n_ref, wl.M), dtype=torch.float64).pin_memory()
-    ctx2 = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
-                      pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
-                      n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank)
-    # the basis the native path built, staged to pinned host memory outside the timing
     ctx.kl_basis_get(B_host)
+    ctx2 = make_ctx(fm, wl, rank, args.form)
     e2e_times, rounds = [], []
     for _ in range(max(1, min(args.steps, 3))):
         flush_l2(flush)
@@ -220,20 +264,19 @@ def run_native(args, wl, eps):
 
     hbm, bf16, src = peaks()
     # dominant kernel family by event-timed device time
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    fam, st = dom
+    fam, st = max(prof.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = st["ms"] / st["launches"]
-    if fam == "kl_gemm_exp":
-        roof = {"bound": "alu", "kernel": fam, "achieved": st["flops"] / (st["ms"] / 1e3) / 1e12,
-                "unit": "TFLOP/s FP64", "peak": None, "frac": None, "traffic": None}
-    else:
-        ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": src}
+    ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None, "peak_source": src}
+    if fam in ("kl_gemm_exp", "fmg_resident"):
+        roof["bound"] = "alu"
+        roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is ALU/latency bound"
     roof["launches"] = st["launches"]
     roof["avg_launch_ms"] = per_launch_ms
     families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                    "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in prof.items()}
+                    "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3)} for k, v in prof.items()}
     total_launches = int(sum(v["launches"] for v in prof.values()))
 
     ests = [r["estimate"] for r in results]
@@ -248,17 +291,18 @@ def run_native(args, wl, eps):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32+f64" if FORMS[args.form]["precision"] == 1 else "f64",
         "data": "synthetic (seeded Philox KL coefficients, KL basis built on the GPU)",
         "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
                    "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
                    "fmg": "4x4 exact, nu0=%d V(%d,%d) RB-GS" % (wl.nu0, wl.nu1, wl.nu2),
-                   "form": "plain FP64", "l2": "flushed between steps (512 MiB write)",
+                   "form": args.form, "tol": 1e-10, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "captured_variance": captured},
         "estimate": float(np.mean(ests)),
         "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in results]))),
         "N_per_level": [int(x) for x in results[-1]["N"]],
+        "other_forms": others,
         "roofline": roof,
         "kernel_families": families,
         "gpu_launches": total_launches,
@@ -267,13 +311,15 @@ def run_native(args, wl, eps):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds)
+        conv = FORMS[args.form]["converged"]
+        per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds, conv)
         N = results[-1]["N"]
         t_cpu = float(np.sum(per * N))
         out["cpu_baseline"] = {"value": t_cpu, "unit": "s", "cores": cores, "kind": "oracle",
-                               "sample": "oracle FMG-MLMC samples per level %s timed on %d threads; "
-                                         "seconds per sample x the GPU run's N_l (extrapolated)"
-                                         % (counts, cores)}
+                               "sample": "oracle FMG-MLMC samples per level %s (%s) timed on %d "
+                                         "threads; seconds per sample x the GPU run's N_l "
+                                         "(extrapolated)" % (counts, "FP64 V-cycles to 1e-10" if conv
+                                                             else "2 V(2,2) per stage", cores)}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -293,7 +339,8 @@ def run_reference(args, wl, eps):
     budget = max(5.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
     cores = os.cpu_count() or 1
     basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32 if wl.M <= 128 else 0)
-    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, nthreads=cores)
+    conv = FORMS[args.form]["converged"]
+    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, prm=oracle_params(conv), nthreads=cores)
     cost = omlmc.cost_model(np.array(wl.levels) ** 2)
     V = None
     for step in range(args.warmup + args.steps):
@@ -314,7 +361,7 @@ def run_reference(args, wl, eps):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "eps": eps,
-                      "sampler": "mc", "form": "FP64 CPU oracle"},
+                      "sampler": "mc", "form": args.form, "implementation": "FP64 CPU oracle"},
            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                             "sample": "per step: a bounded batch per level timed on %d threads, "
                                       "extrapolated to the optimal N_l of eps" % cores},

@@ -48,8 +48,26 @@ typedef int32_t fm_status;
 
 #define FM_MAX_LEVELS 12
 
-/* Arithmetic of the solver. FP64: every step in FP64. */
+/* Arithmetic of the solver.
+ * FP64:  every step in FP64.
+ * MIXED: FP32 smoothing, restriction, prolongation and coarsest solve inside
+ *        an FP64 iterative-refinement loop on the stages that give Q^c and
+ *        Q^f; FP64 only for the finest-grid residual, the iterate those
+ *        stages update and the outflux.  Needs converged = 1. */
 #define FM_PREC_FP64 0
+#define FM_PREC_MIXED 1
+
+/* Arithmetic of the KL field synthesis.
+ * AUTO: FP64 in the FP64 form, BF16X3 in the mixed form.
+ * FP64: FP64 SIMT contraction.
+ * BF16: tcgen05 tensor cores, BF16 basis and coefficients, FP32 accumulation
+ *       (relative error of g about 2^-8).
+ * BF16X3: tcgen05 tensor cores on the split products hi*hi + hi*lo + lo*hi
+ *       (relative error of g about 2^-16). */
+#define FM_KL_AUTO 0
+#define FM_KL_FP64 1
+#define FM_KL_BF16 2
+#define FM_KL_BF16X3 3
 
 typedef struct fm_ctx fm_ctx;
 
@@ -65,10 +83,22 @@ typedef struct {
     int32_t nu0;          /* V-cycles per FMG stage */
     int32_t nu1, nu2;     /* pre- / post-smoothing red-black Gauss-Seidel sweeps */
     int32_t precision;    /* FM_PREC_* */
+    int32_t converged;    /* 0: nu0 V-cycles per stage; 1: the stages giving Q^c and Q^f
+                             iterate until ||b - A p||_2 <= tol ||b||_2 */
+    double tol;           /* relative residual target of converged stages */
+    int32_t max_cycles;   /* cycle cap of a converged stage */
+    int32_t kl_mode;      /* FM_KL_*: arithmetic of the field synthesis */
     int32_t n_shifts;     /* QMC digital shifts R */
     uint64_t seed;        /* key of the Philox streams (MC points, QMC shifts) */
     int64_t max_batch;    /* most samples per device batch (0: library's choice) */
 } fm_config;
+
+/* Kernel schedule of a batched FMG solve (same arithmetic, same result up
+ * to rounding order). */
+#define FM_KERNEL_AUTO 0       /* resident where the hierarchy fits, else levelwise */
+#define FM_KERNEL_LEVELWISE 1  /* one kernel per grid operation over all samples */
+#define FM_KERNEL_RESIDENT 2   /* one CTA per sample, hierarchy in shared memory
+                                  (n_fine <= 64 in FP64) */
 
 /* Parameters of one batched FMG solve. */
 typedef struct {
@@ -76,6 +106,13 @@ typedef struct {
     int32_t n_coarsest;   /* coarsest grid (4) */
     int32_t nu0, nu1, nu2;
     int32_t precision;    /* FM_PREC_* */
+    int32_t kernel;       /* FM_KERNEL_* */
+    int32_t converged;    /* 0: nu0 V-cycles on every stage (the end of a stage's
+                             cycles is its "exact" solution); 1: stages n_fine/2 and
+                             n_fine iterate to ||b - A p||_2 <= tol ||b||_2 */
+    double tol;
+    int32_t max_cycles;   /* cap per converged stage; a sample that reaches it gets
+                             status FM_ENOTCONV */
 } fm_solve_params;
 
 /* ---------------------------------------------------------------- context */
@@ -139,8 +176,9 @@ fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, double* capt
 fm_status kl_basis_get(const fm_ctx* ctx, double* basis_ref_out, int32_t on_device);
 
 /* Field synthesis (Sec. 3.1): d_K[s][c] = exp(sum_k B_l[c][k] d_xi[s*M + k])
- * for the n samples of MLMC level `level` (grid n_level0 << level),
- * FP64 throughout.  d_K is [n][N_l][N_l] doubles. */
+ * for the n samples of MLMC level `level` (grid n_level0 << level), in the
+ * context's kl_mode; d_K is [n][N_l][N_l] doubles.  The tensor-core forms
+ * report a device-side wait that ran out through fm_sync. */
 fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d_xi,
                          double* d_K, void* stream);
 
@@ -155,11 +193,13 @@ fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d
  * prolongation).  Outputs: d_qf[s] outflux of the finest stage; d_qc[s]
  * (nullable) outflux of the stage one grid coarser (the Q^c by-product;
  * NaN if n_fine == n_coarsest); d_p (nullable) the finest solution
- * [n][n_fine][n_fine].  n_fine must be n_coarsest times a power of two.
- * Scratch is owned by the context. */
+ * [n][n_fine][n_fine]; d_status (nullable) per-sample FM_OK / FM_ENOTCONV.
+ * n_fine must be n_coarsest times a power of two.  Scratch is owned by the
+ * context.  FM_PREC_MIXED and converged mode run on the resident schedule
+ * (n_fine <= 64). */
 fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                           const fm_solve_params* prm, double* d_qf, double* d_qc,
-                          double* d_p, void* stream);
+                          double* d_p, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------- MLMC */
 
@@ -208,6 +248,11 @@ typedef struct {
  * QMC), at the fixed finest level n_levels - 1, with the cost model
  * C_l = (4/3) (n_level0 << l)^2.  Uses the default stream, synchronous. */
 fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out);
+
+/* Synchronise the device and report device-side failures of earlier
+ * asynchronous calls on ctx: FM_ETIMEOUT if a bounded wait inside a kernel
+ * ran out (its output is then invalid), FM_ECUDA for a CUDA error. */
+fm_status fm_sync(fm_ctx* ctx);
 
 /* ---------------------------------------------------------------- profiling */
 

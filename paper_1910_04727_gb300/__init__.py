@@ -10,9 +10,9 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import FM_PREC_FP64, STATUS_NAMES
+from ._lib import FM_PREC_FP64, FM_PREC_MIXED, STATUS_NAMES
 
-__all__ = ["Context", "FmError", "FM_PREC_FP64", "load_library"]
+__all__ = ["Context", "FmError", "FM_PREC_FP64", "FM_PREC_MIXED", "load_library"]
 
 
 class FmError(RuntimeError):
@@ -44,10 +44,11 @@ class Context:
 
     def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
                  nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
-                 precision=FM_PREC_FP64):
+                 precision=FM_PREC_FP64, converged=False, tol=1e-10, max_cycles=100, kl_mode=0):
         self._L = _lib.load()
         cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
-                            precision, n_shifts, seed, max_batch)
+                            precision, int(bool(converged)), tol, max_cycles, kl_mode, n_shifts, seed,
+                            max_batch)
         h = C.c_void_p()
         st = self._L.fm_create(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -111,6 +112,10 @@ class Context:
                                            C.byref(cap)))
         return theta, cap.value
 
+    def sync(self):
+        """Synchronise and raise on device-side failures of earlier calls."""
+        self._check(self._L.fm_sync(self._h))
+
     def kl_basis_get(self, out=None):
         """The installed finest-grid basis [n_ref^2][M] (CUDA tensor, or into a
         given CPU/CUDA float64 tensor)."""
@@ -135,21 +140,23 @@ class Context:
     # ----------------------------------------------------------- solver
     def solve_params(self, **over):
         c = self.cfg
-        p = _lib.FmSolveParams(c.pW, c.pE, c.n_coarsest, c.nu0, c.nu1, c.nu2, c.precision)
+        p = _lib.FmSolveParams(c.pW, c.pE, c.n_coarsest, c.nu0, c.nu1, c.nu2, c.precision,
+                               _lib.FM_KERNEL_AUTO, c.converged, c.tol, c.max_cycles)
         for k, v in over.items():
             setattr(p, k, v)
         return p
 
-    def fmg_solve_batch(self, K, want_qc=True, want_p=False, **params):
-        """K: CUDA float64 [S][n][n]. Returns (qf, qc or None, p or None)."""
+    def fmg_solve_batch(self, K, want_qc=True, want_p=False, want_status=False, **params):
+        """K: CUDA float64 [S][n][n]. Returns (qf, qc or None, p or None[, status])."""
         S, n = K.shape[0], K.shape[-1]
         prm = self.solve_params(**params)
         qf = torch.empty(S, dtype=torch.float64, device="cuda")
         qc = torch.empty(S, dtype=torch.float64, device="cuda") if want_qc else None
         p = torch.empty((S, n, n), dtype=torch.float64, device="cuda") if want_p else None
+        st = torch.empty(S, dtype=torch.int32, device="cuda") if want_status else None
         self._check(self._L.fmg_solve_batch(self._h, n, S, _ptr(K), C.byref(prm), _ptr(qf), _ptr(qc),
-                                            _ptr(p), _stream()))
-        return qf, qc, p
+                                            _ptr(p), _ptr(st), _stream()))
+        return (qf, qc, p, st) if want_status else (qf, qc, p)
 
     # ----------------------------------------------------------- MLMC
     @staticmethod

@@ -11,6 +11,9 @@ from .build import LIB_PATH
 FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENOTCONV, FM_ETIMEOUT, FM_EUNSUPPORTED = range(7)
 FM_MAX_LEVELS = 12
 FM_PREC_FP64 = 0
+FM_PREC_MIXED = 1
+FM_KERNEL_AUTO, FM_KERNEL_LEVELWISE, FM_KERNEL_RESIDENT = 0, 1, 2
+FM_KL_AUTO, FM_KL_FP64, FM_KL_BF16, FM_KL_BF16X3 = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENOTCONV",
                 5: "FM_ETIMEOUT", 6: "FM_EUNSUPPORTED"}
@@ -19,21 +22,23 @@ STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "F
 EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_points",
            "sobol_direction_numbers", "kl_basis_set", "kl_basis_build", "kl_basis_get", "kl_field_batch",
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
-           "fm_profile_end", "fm_kernel_family_name"]
+           "fm_profile_end", "fm_kernel_family_name", "fm_sync"]
 
 
 class FmConfig(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("n_level0", C.c_int32), ("n_coarsest", C.c_int32),
                 ("M", C.c_int32), ("sigma2", C.c_double), ("lambda_", C.c_double),
                 ("pW", C.c_double), ("pE", C.c_double), ("nu0", C.c_int32), ("nu1", C.c_int32),
-                ("nu2", C.c_int32), ("precision", C.c_int32), ("n_shifts", C.c_int32),
-                ("seed", C.c_uint64), ("max_batch", C.c_int64)]
+                ("nu2", C.c_int32), ("precision", C.c_int32), ("converged", C.c_int32),
+                ("tol", C.c_double), ("max_cycles", C.c_int32), ("kl_mode", C.c_int32),
+                ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64)]
 
 
 class FmSolveParams(C.Structure):
     _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("n_coarsest", C.c_int32),
                 ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("kernel", C.c_int32), ("converged", C.c_int32),
+                ("tol", C.c_double), ("max_cycles", C.c_int32)]
 
 
 class FmLevelSums(C.Structure):
@@ -82,12 +87,13 @@ def load(path=None):
         "kl_basis_build": (I32, [P, I32, P, P]),
         "kl_basis_get": (I32, [P, P, I32]),
         "kl_field_batch": (I32, [P, I32, U32, P, P, P]),
-        "fmg_solve_batch": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P, P]),
+        "fmg_solve_batch": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P, P, P]),
         "mlmc_sample_level": (I32, [P, I32, U64, U32, I32, P, P, P, P]),
         "mlmc_estimate": (I32, [P, C.POINTER(FmEstimateOpts), C.POINTER(FmResult)]),
         "fm_profile_begin": (I32, [P, U32]),
         "fm_profile_end": (I32, [P, P, I32, C.POINTER(I32)]),
         "fm_kernel_family_name": (C.c_char_p, [I32]),
+        "fm_sync": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -29,8 +29,14 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
     FM_CHECK_ARG(nullptr, cfg->sigma2 > 0 && cfg->lambda > 0, "fm_create: sigma2 and lambda must be positive");
     FM_CHECK_ARG(nullptr, cfg->nu0 >= 1 && cfg->nu1 >= 0 && cfg->nu2 >= 0 && cfg->nu1 + cfg->nu2 >= 1,
                  "fm_create: need nu0 >= 1 and nu1 + nu2 >= 1");
-    FM_CHECK_ARG(nullptr, cfg->precision == FM_PREC_FP64, "fm_create: unknown precision");
+    FM_CHECK_ARG(nullptr, cfg->precision == FM_PREC_FP64 || cfg->precision == FM_PREC_MIXED,
+                 "fm_create: unknown precision");
+    FM_CHECK_ARG(nullptr, cfg->precision != FM_PREC_MIXED || cfg->converged,
+                 "fm_create: the mixed form refines to a tolerance (converged = 1)");
+    FM_CHECK_ARG(nullptr, !cfg->converged || (cfg->tol > 0 && cfg->max_cycles >= 1),
+                 "fm_create: converged mode needs tol > 0 and max_cycles >= 1");
     FM_CHECK_ARG(nullptr, cfg->n_shifts >= 0 && cfg->n_shifts <= 64, "fm_create: n_shifts must be in [0, 64]");
+    FM_CHECK_ARG(nullptr, cfg->kl_mode >= FM_KL_AUTO && cfg->kl_mode <= FM_KL_BF16X3, "fm_create: unknown kl_mode");
     fm_ctx* ctx = new (std::nothrow) fm_ctx();
     if (!ctx) {
         set_error(nullptr, "fm_create: host allocation failed");
@@ -71,7 +77,24 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     cudaFree(ctx->d_sums);
     cudaFree(ctx->d_partials);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->tc.basis[l]);
+    cudaFree(ctx->tc.xi);
+    cudaFree(ctx->tc.err);
     delete ctx;
+}
+
+extern "C" fm_status fm_sync(fm_ctx* ctx) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_sync: null context");
+    FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    if (ctx->tc.err) {
+        int e = 0;
+        FM_CUDA_TRY(ctx, cudaMemcpy(&e, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            set_error(ctx, "a bounded device-side wait of the tensor-core field synthesis ran out");
+            return FM_ETIMEOUT;
+        }
+    }
+    return FM_OK;
 }
 
 extern "C" const char* fm_last_error(const fm_ctx* ctx) {

@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of libfmgmlmc.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -88,7 +89,7 @@ void set_error(const fm_ctx* ctx, const std::string& msg);
 enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
-    kFamOutflux, kFamLevelSums, kFamilyCount
+    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamilyCount
 };
 
 struct ProfRecord {
@@ -111,6 +112,18 @@ struct Arena {
     char* base = nullptr;
     size_t capacity = 0;
     size_t used = 0;
+};
+
+// Tensor-core KL synthesis state (kl_tc.cu).
+struct TcState {
+    bool ready = false;
+    int split = 0, Mpad = 0, Kp = 0;
+    void* basis[FM_MAX_LEVELS] = {};   // BF16 [cells][Kp] per level
+    CUtensorMap mapA[FM_MAX_LEVELS];
+    CUtensorMap mapB;
+    void* xi = nullptr;                // BF16 [capacity][Kp]
+    size_t xi_capacity = 0, mapB_rows = 0;
+    int* err = nullptr;                // device flag: a bounded wait ran out
 };
 
 }  // namespace fm
@@ -137,6 +150,7 @@ struct fm_ctx {
     double* d_partials = nullptr;    // per-block partial sums of the level-sum kernel
     size_t partial_capacity = 0;
     fm::Profiler prof;
+    fm::TcState tc;
 };
 
 namespace fm {
@@ -178,7 +192,19 @@ int64_t batch_limit(const fm_ctx* ctx, int n);
 // FMG solve into caller-provided outputs (used by mlmc_sample_level too).
 fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
                          const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
-                         cudaStream_t stream);
+                         int32_t* d_status, cudaStream_t stream);
+
+// Sample-resident FMG (fmg_resident.cu); false if the grid does not fit.
+bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double* d_K,
+                         const fm_solve_params& prm, double* qf, double* qc, double* p_out,
+                         int32_t* status, cudaStream_t st);
+
+// Tensor-core KL synthesis (kl_tc.cu): install the BF16 basis, then fields.
+fm_status kl_tc_install(fm_ctx* ctx, int split);
+fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, double* d_K, cudaStream_t st);
+
+// KL arithmetic of the context: 1 FP64, 2 BF16, 3 BF16 split (bf16x3).
+int kl_mode_of(const fm_ctx* ctx);
 
 // Level sums of a batch (mlmc.cu).
 fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc,

@@ -1,16 +1,20 @@
 // Batched full multigrid for the Case II Darcy problem (Eq. 1, Table 1,
-// Sec. 2.5): one FMG hierarchy per sample, all samples of a batch advanced
-// level by level, every kernel covering every cell of every sample of one
-// grid (x fastest, so a warp touches consecutive cells of one row).
+// Sec. 2.5), level-wise schedule: one FMG hierarchy per sample, all samples
+// of a batch advanced together, every kernel covering every cell of every
+// (active) sample of one grid, x fastest so a warp touches consecutive cells
+// of one row.  Used for grids whose hierarchy does not fit in one CTA's
+// shared memory (n > 64); smaller grids take the resident schedule.
 //
 // Per grid k (n_k = n_coarsest << k) and sample the scratch holds
-//   K   coefficients (injected from the finer grid; the finest is the input)
+//   K   FP64 coefficients (injected from the finer grid; the finest is the input)
 //   Te  east-face transmissibility of each cell (2K on the east edge)
 //   Tn  north-face transmissibility (0 on the north edge)
 //   D   diagonal: sum of the four face transmissibilities (2K on the west edge)
 //   p   iterate, b right-hand side
-// and for the coarsest grid the inverse of its dense operator, so each exact
-// solve is one small matrix-vector product.
+// in the V-cycle type T (FP64, or FP32 in the mixed form), and for the
+// coarsest grid the inverse of its dense operator, so each exact solve is a
+// small matrix-vector product.  The mixed form adds FP64 p, Te, Tn, D on the
+// two refined grids (n/2 and n, which give Q^c and Q^f).
 #include <algorithm>
 #include <cmath>
 
@@ -24,6 +28,9 @@ inline unsigned blocks_for(size_t threads) { return (unsigned)((threads + kBlock
 
 __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
+// Sample of a flat thread index and whether it still iterates.
+__device__ __forceinline__ bool inactive(const int32_t* active, size_t s) { return active && !active[s]; }
+
 // K_c[J][I] = K_f[2J][2I] (Sec. 2.5, the lower-left child in 0-indexed form).
 __global__ void k_inject(int nc, size_t S, const double* __restrict__ Kf, double* __restrict__ Kc) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,9 +43,11 @@ __global__ void k_inject(int nc, size_t S, const double* __restrict__ Kf, double
 }
 
 // Face transmissibilities: harmonic mean inside, 2K on the Dirichlet edges,
-// none on the no-flow edges.
-__global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, double* __restrict__ Te,
-                               double* __restrict__ Tn, double* __restrict__ D) {
+// none on the no-flow edges; optional FP64 copies for refined grids.
+template <typename T>
+__global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T* __restrict__ Te,
+                               T* __restrict__ Tn, T* __restrict__ D, double* __restrict__ Te64,
+                               double* __restrict__ Tn64, double* __restrict__ D64) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)n * n;
     if (t >= S * cells) return;
@@ -49,14 +58,21 @@ __global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, do
     const double te = (i < n - 1) ? harmonic(k, K[t + 1]) : 2.0 * k;
     const double ts = (j > 0) ? harmonic(K[t - n], k) : 0.0;
     const double tn = (j < n - 1) ? harmonic(k, K[t + n]) : 0.0;
-    Te[t] = te;
-    Tn[t] = tn;
-    D[t] = tw + te + ts + tn;
+    const double d = tw + te + ts + tn;
+    Te[t] = (T)te;
+    Tn[t] = (T)tn;
+    D[t] = (T)d;
+    if (Te64) {
+        Te64[t] = te;
+        Tn64[t] = tn;
+        D64[t] = d;
+    }
 }
 
 // Right-hand side of a stage problem: the Dirichlet data moved to the rhs.
+template <typename T>
 __global__ void k_stage_rhs(int n, size_t S, const double* __restrict__ K, double pW, double pE,
-                            double* __restrict__ b) {
+                            T* __restrict__ b) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)n * n;
     if (t >= S * cells) return;
@@ -64,22 +80,24 @@ __global__ void k_stage_rhs(int n, size_t S, const double* __restrict__ K, doubl
     double v = 0.0;
     if (i == 0) v += 2.0 * K[t] * pW;
     if (i == n - 1) v += 2.0 * K[t] * pE;
-    b[t] = v;
+    b[t] = (T)v;
 }
 
 // One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == color.
-__global__ void k_rbgs_color(int n, size_t S, int color, const double* __restrict__ b,
-                             const double* __restrict__ Te, const double* __restrict__ Tn,
-                             const double* __restrict__ D, double* __restrict__ p) {
+template <typename T>
+__global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b, const T* __restrict__ Te,
+                             const T* __restrict__ Tn, const T* __restrict__ D, T* __restrict__ p,
+                             const int32_t* __restrict__ active) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t half = (size_t)n * n / 2;
     if (t >= S * half) return;
     const size_t s = t / half;
+    if (inactive(active, s)) return;
     const int h = (int)(t % half);
     const int j = h / (n / 2);
     const int i = 2 * (h % (n / 2)) + ((j + color) & 1);
     const size_t c = s * (size_t)n * n + (size_t)j * n + i;
-    double acc = b[c];
+    T acc = b[c];
     if (i > 0) acc += Te[c - 1] * p[c - 1];
     if (i < n - 1) acc += Te[c] * p[c + 1];
     if (j > 0) acc += Tn[c - n] * p[c - n];
@@ -87,10 +105,10 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const double* __restric
     p[c] = acc / D[c];
 }
 
-__device__ __forceinline__ double residual_at(int n, size_t c, int i, int j, const double* b,
-                                              const double* Te, const double* Tn, const double* D,
-                                              const double* p) {
-    double v = D[c] * p[c];
+template <typename T>
+__device__ __forceinline__ T residual_at(int n, size_t c, int i, int j, const T* b, const T* Te, const T* Tn,
+                                         const T* D, const T* p) {
+    T v = D[c] * p[c];
     if (i > 0) v -= Te[c - 1] * p[c - 1];
     if (i < n - 1) v -= Te[c] * p[c + 1];
     if (j > 0) v -= Tn[c - n] * p[c - n];
@@ -99,122 +117,145 @@ __device__ __forceinline__ double residual_at(int n, size_t c, int i, int j, con
 }
 
 // Fused residual + restriction: b_c = sum of the four fine residuals; p_c = 0.
-__global__ void k_residual_restrict(int nc, size_t S, const double* __restrict__ bf,
-                                    const double* __restrict__ Te, const double* __restrict__ Tn,
-                                    const double* __restrict__ D, const double* __restrict__ pf,
-                                    double* __restrict__ bc, double* __restrict__ pc) {
+template <typename T>
+__global__ void k_residual_restrict(int nc, size_t S, const T* __restrict__ bf, const T* __restrict__ Te,
+                                    const T* __restrict__ Tn, const T* __restrict__ D, const T* __restrict__ pf,
+                                    T* __restrict__ bc, T* __restrict__ pc, const int32_t* __restrict__ active) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)nc * nc;
     if (t >= S * cells) return;
     const size_t s = t / cells;
+    if (inactive(active, s)) return;
     const int C = (int)(t % cells);
     const int I = C % nc, J = C / nc, nf = 2 * nc;
     const size_t base = s * (size_t)nf * nf;
     const int i0 = 2 * I, j0 = 2 * J;
     const size_t c00 = base + (size_t)j0 * nf + i0;
-    const double r00 = residual_at(nf, c00, i0, j0, bf, Te, Tn, D, pf);
-    const double r10 = residual_at(nf, c00 + 1, i0 + 1, j0, bf, Te, Tn, D, pf);
-    const double r01 = residual_at(nf, c00 + nf, i0, j0 + 1, bf, Te, Tn, D, pf);
-    const double r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bf, Te, Tn, D, pf);
+    const T r00 = residual_at(nf, c00, i0, j0, bf, Te, Tn, D, pf);
+    const T r10 = residual_at(nf, c00 + 1, i0 + 1, j0, bf, Te, Tn, D, pf);
+    const T r01 = residual_at(nf, c00 + nf, i0, j0 + 1, bf, Te, Tn, D, pf);
+    const T r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bf, Te, Tn, D, pf);
     bc[t] = r00 + r10 + r01 + r11;
-    pc[t] = 0.0;
+    pc[t] = T(0);
 }
 
 // Coarse value with ghosts: mirror across the no-flow edges, 2g - u across
 // the Dirichlet edges (g = 0 for an error).
-__device__ __forceinline__ double coarse_ghost(int nc, const double* uc, int I, int J, double gW,
-                                               double gE) {
+template <typename U>
+__device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U gW, U gE) {
     J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
-    if (I < 0) return 2.0 * gW - uc[(size_t)J * nc];
-    if (I > nc - 1) return 2.0 * gE - uc[(size_t)J * nc + nc - 1];
+    if (I < 0) return U(2) * gW - uc[(size_t)J * nc];
+    if (I > nc - 1) return U(2) * gE - uc[(size_t)J * nc + nc - 1];
     return uc[(size_t)J * nc + I];
 }
 
-__device__ __forceinline__ double bilinear_at(int nc, const double* uc, int i, int j, double gW,
-                                              double gE) {
-    const int I = i >> 1, J = j >> 1;
-    const int Ix = (i & 1) ? I + 1 : I - 1;
-    const int Jy = (j & 1) ? J + 1 : J - 1;
-    return (9.0 * coarse_ghost(nc, uc, I, J, gW, gE) + 3.0 * coarse_ghost(nc, uc, Ix, J, gW, gE) +
-            3.0 * coarse_ghost(nc, uc, I, Jy, gW, gE) + 1.0 * coarse_ghost(nc, uc, Ix, Jy, gW, gE)) /
-           16.0;
-}
-
 // p_f += P e_c (add = 1, boundary values 0) or p_f = P u_c (add = 0, FMG start).
-__global__ void k_prolong(int nc, size_t S, const double* __restrict__ uc, double gW, double gE,
-                          int add, double* __restrict__ pf) {
+template <typename U>
+__global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE, int add, U* __restrict__ pf,
+                          const int32_t* __restrict__ active) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nf = 2 * nc;
     const size_t cells = (size_t)nf * nf;
     if (t >= S * cells) return;
     const size_t s = t / cells;
+    if (inactive(active, s)) return;
     const int c = (int)(t % cells);
-    const double v = bilinear_at(nc, uc + s * (size_t)nc * nc, c % nf, c / nf, gW, gE);
+    const int i = c % nf, j = c / nf;
+    const U* u = uc + s * (size_t)nc * nc;
+    const int I = i >> 1, J = j >> 1;
+    const int Ix = (i & 1) ? I + 1 : I - 1;
+    const int Jy = (j & 1) ? J + 1 : J - 1;
+    const U v = (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
+                 U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
+                U(16);
     pf[t] = add ? pf[t] + v : v;
 }
 
-// Inverse of the dense operator of the coarsest grid (m = n0^2 unknowns), by
-// Gauss-Jordan elimination on [A | I]; A is SPD so no pivoting is needed.
-// One thread per sample; m <= 16.
-__global__ void k_coarse_inverse(int n0, size_t S, const double* __restrict__ Te,
-                                 const double* __restrict__ Tn, const double* __restrict__ D,
-                                 double* __restrict__ Ainv) {
-    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+// Inverse of the dense operator of the coarsest grid (m = n0^2 <= 16
+// unknowns), Gauss-Jordan on [A | I] in FP64 (A is SPD, so no pivoting).
+// One warp per sample with [A | X] in shared memory: lane c < 16 owns column
+// c of A, lane 16 + c column c of X.
+constexpr int kInvWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kInvWarps) k_coarse_inverse(int n0, size_t S, const double* __restrict__ K,
+                                                                   T* __restrict__ Ainv) {
+    __shared__ double sh[kInvWarps][2][16][16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t s = (size_t)blockIdx.x * kInvWarps + warp;
+    if (s >= S) return;   // whole warps leave together
     const int m = n0 * n0;
-    double A[16][16], X[16][16];
-    const double* te = Te + s * m;
-    const double* tn = Tn + s * m;
-    const double* d = D + s * m;
-    for (int r = 0; r < m; ++r)
+    double(*A)[16] = sh[warp][0];
+    double(*X)[16] = sh[warp][1];
+    const double* k = K + s * m;
+    for (int r = lane; r < m; r += 32) {   // row r: the equation of cell r
         for (int c = 0; c < m; ++c) {
             A[r][c] = 0.0;
             X[r][c] = (r == c) ? 1.0 : 0.0;
         }
-    for (int c = 0; c < m; ++c) {
-        const int i = c % n0, j = c / n0;
-        A[c][c] = d[c];
-        if (i < n0 - 1) { A[c][c + 1] = -te[c]; A[c + 1][c] = -te[c]; }
-        if (j < n0 - 1) { A[c][c + n0] = -tn[c]; A[c + n0][c] = -tn[c]; }
+        const int i = r % n0, j = r / n0;
+        const double tw = (i > 0) ? harmonic(k[r - 1], k[r]) : 2.0 * k[r];
+        const double te = (i < n0 - 1) ? harmonic(k[r], k[r + 1]) : 2.0 * k[r];
+        const double ts = (j > 0) ? harmonic(k[r - n0], k[r]) : 0.0;
+        const double tn = (j < n0 - 1) ? harmonic(k[r], k[r + n0]) : 0.0;
+        A[r][r] = tw + te + ts + tn;
+        if (i > 0) A[r][r - 1] = -tw;
+        if (i < n0 - 1) A[r][r + 1] = -te;
+        if (j > 0) A[r][r - n0] = -ts;
+        if (j < n0 - 1) A[r][r + n0] = -tn;
     }
-    for (int k = 0; k < m; ++k) {
-        const double inv = 1.0 / A[k][k];
-        for (int c = 0; c < m; ++c) { A[k][c] *= inv; X[k][c] *= inv; }
-        for (int r = 0; r < m; ++r) {
-            if (r == k) continue;
-            const double f = A[r][k];
-            if (f == 0.0) continue;
-            for (int c = 0; c < m; ++c) { A[r][c] -= f * A[k][c]; X[r][c] -= f * X[k][c]; }
+    __syncwarp();
+    const bool ownA = lane < m, ownX = lane >= 16 && lane - 16 < m;
+    const int col = lane & 15;
+    for (int p = 0; p < m; ++p) {
+        const double piv = A[p][p];
+        double f[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) f[r] = (r < m) ? A[r][p] : 0.0;
+        __syncwarp();
+        // scale row p, then eliminate column p from every other row
+        if (ownA) A[p][col] /= piv;
+        if (ownX) X[p][col] /= piv;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (r >= m || r == p) continue;
+            if (ownA) A[r][col] -= f[r] * A[p][col];
+            if (ownX) X[r][col] -= f[r] * X[p][col];
         }
+        __syncwarp();
     }
-    double* out = Ainv + s * (size_t)m * m;
-    for (int r = 0; r < m; ++r)
-        for (int c = 0; c < m; ++c) out[r * m + c] = X[r][c];
+    T* out = Ainv + s * (size_t)m * m;
+    for (int e = lane; e < m * m; e += 32) out[e] = (T)X[e / m][e % m];
 }
 
 // p = A^{-1} b on the coarsest grid; one thread per (sample, unknown).
-__global__ void k_coarse_solve(int m, size_t S, const double* __restrict__ Ainv,
-                               const double* __restrict__ b, double* __restrict__ p) {
+template <typename T>
+__global__ void k_coarse_solve(int m, size_t S, const T* __restrict__ Ainv, const T* __restrict__ b,
+                               T* __restrict__ p, const int32_t* __restrict__ active) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S * m) return;
     const size_t s = t / m;
+    if (inactive(active, s)) return;
     const int r = (int)(t % m);
-    const double* row = Ainv + s * (size_t)m * m + (size_t)r * m;
-    const double* bs = b + s * m;
-    double acc = 0.0;
+    const T* row = Ainv + s * (size_t)m * m + (size_t)r * m;
+    const T* bs = b + s * m;
+    T acc = T(0);
     for (int c = 0; c < m; ++c) acc += row[c] * bs[c];
     p[t] = acc;
 }
 
 // Q = sum_j 2 K_(n-1,j) (p_(n-1,j) - pE), one warp per sample, shuffle reduction.
-__global__ void k_outflux(int n, size_t S, const double* __restrict__ K, const double* __restrict__ p,
-                          double pE, double* __restrict__ q) {
+template <typename P>
+__global__ void k_outflux(int n, size_t S, const double* __restrict__ K, const P* __restrict__ p, double pE,
+                          double* __restrict__ q) {
     const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x & 31;
     if (warp >= S) return;
     const size_t base = warp * (size_t)n * n + (n - 1);
     double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += 2.0 * K[base + (size_t)j * n] * (p[base + (size_t)j * n] - pE);
+    for (int j = lane; j < n; j += 32)
+        acc += 2.0 * K[base + (size_t)j * n] * ((double)p[base + (size_t)j * n] - pE);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) q[warp] = acc;
@@ -225,31 +266,126 @@ __global__ void k_fill(size_t count, double v, double* __restrict__ x) {
     if (t < count) x[t] = v;
 }
 
+// ------------------------------------------------------------------ refinement kernels
+// Per-sample convergence test of the stage problem, one CTA per sample:
+// active[s] = ||b - A p||_2 > tol ||b||_2 (FP64 sums), counted in *left.
+// Mixed form (p64 != null): the residual is formed in FP64 from the FP64
+// grid and written, rounded, into the FP32 rhs bT, with the FP32 correction
+// pT zeroed; FP64 form: the residual of the T grid itself.
+template <typename T>
+__global__ void k_stage_check(int n, size_t S, const double* __restrict__ K, double pW, double pE,
+                              const T* __restrict__ b, const T* __restrict__ Te, const T* __restrict__ Tn,
+                              const T* __restrict__ D, const T* __restrict__ p, const double* __restrict__ p64,
+                              const double* __restrict__ Te64, const double* __restrict__ Tn64,
+                              const double* __restrict__ D64, T* __restrict__ bT, T* __restrict__ pT,
+                              double tol, int32_t* __restrict__ active, int32_t* __restrict__ left) {
+    __shared__ double red[2][32];
+    const size_t s = blockIdx.x;
+    if (s >= S || inactive(active, s)) return;
+    const size_t base = s * (size_t)n * n;
+    double rr = 0.0, bb = 0.0;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const size_t g = base + c;
+        double f = 0.0;
+        if (i == 0) f += 2.0 * K[g] * pW;
+        if (i == n - 1) f += 2.0 * K[g] * pE;
+        double r;
+        if (p64) {
+            double v = D64[g] * p64[g];
+            if (i > 0) v -= Te64[g - 1] * p64[g - 1];
+            if (i < n - 1) v -= Te64[g] * p64[g + 1];
+            if (j > 0) v -= Tn64[g - n] * p64[g - n];
+            if (j < n - 1) v -= Tn64[g] * p64[g + n];
+            r = f - v;
+            bT[g] = (T)r;
+            pT[g] = T(0);
+        } else {
+            r = (double)residual_at(n, g, i, j, b, Te, Tn, D, p);
+        }
+        rr += r * r;
+        bb += f * f;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, off);
+        bb += __shfl_down_sync(0xffffffffu, bb, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = rr;
+        red[1][threadIdx.x >> 5] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b2 += red[1][w];
+        }
+        const bool done = a <= tol * tol * b2;
+        active[s] = done ? 0 : 1;
+        if (!done) atomicAdd(left, 1);
+    }
+}
+
+template <typename T>
+__global__ void k_ir_update(size_t cells, size_t S, const T* __restrict__ e, double* __restrict__ p64,
+                            const int32_t* __restrict__ active) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S * cells) return;
+    if (inactive(active, t / cells)) return;
+    p64[t] += (double)e[t];
+}
+
+template <typename T>
+__global__ void k_widen(size_t count, const T* __restrict__ x, double* __restrict__ y) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) y[t] = (double)x[t];
+}
+
+__global__ void k_status(size_t S, const int32_t* __restrict__ active, int32_t* __restrict__ status) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S && active[s]) status[s] = FM_ENOTCONV;
+}
+
 // ------------------------------------------------------------------ driver
+template <typename T>
 struct GridBufs {
     int n;
     const double* K;
-    double *Te, *Tn, *D, *p, *b;
+    T *Te, *Tn, *D, *p, *b;
+    double *p64, *Te64, *Tn64, *D64;   // refined grids of the mixed form only
 };
 
+template <typename T>
 struct Hierarchy {
     fm_ctx* ctx;
-    int m;   // finest index
+    int m;
     int n0;
     size_t S;
-    GridBufs g[FM_MAX_LEVELS + 8];
-    double* Ainv;
+    GridBufs<T> g[FM_MAX_LEVELS + 8];
+    T* Ainv;
+    int32_t* active;   // per-sample iterate flags of converged stages
+    int32_t* left;     // count of samples still iterating
 };
 
-static size_t hierarchy_doubles(int n_fine, int n0, size_t S) {
+static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool mixed, bool converged) {
     size_t total = 0;
-    for (int n = n0; n <= n_fine; n *= 2) total += (size_t)6 * n * n;  // K, Te, Tn, D, p, b
-    total += (size_t)n0 * n0 * n0 * n0;                                 // Ainv
-    return total * S;
+    int m = 0;
+    while ((n0 << m) < n_fine) ++m;
+    for (int k = 0; k <= m; ++k) {
+        const size_t c = (size_t)(n0 << k) * (n0 << k);
+        total += c * (8 + 5 * tsize) + 5 * 256;
+        if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
+    }
+    total += (size_t)n0 * n0 * n0 * n0 * tsize + 256;
+    if (converged) total += 4 * 2 + 2 * 256;
+    return total * S + 4096;
 }
 
 int64_t batch_limit(const fm_ctx* ctx, int n) {
-    const size_t per = hierarchy_doubles(n, std::max(ctx->cfg.n_coarsest, 4), 1) * sizeof(double) +
+    const bool mixed = ctx->cfg.precision == FM_PREC_MIXED;
+    const size_t per = hierarchy_bytes(n, std::max(ctx->cfg.n_coarsest, 4), 1, mixed ? 4 : 8, mixed, true) +
                        (size_t)n * n * sizeof(double) + (size_t)ctx->cfg.M * sizeof(double);
     const size_t budget = (size_t)8 << 30;   // 8 GiB of scratch per batch
     int64_t lim = (int64_t)(budget / per);
@@ -257,8 +393,10 @@ int64_t batch_limit(const fm_ctx* ctx, int n) {
     return std::max<int64_t>(lim, 1);
 }
 
-static fm_status carve(fm_ctx* ctx, Hierarchy& H, int n_fine, int n0, size_t S, const double* d_K) {
-    const size_t need = hierarchy_doubles(n_fine, n0, S) * sizeof(double) + 64 * 256;
+template <typename T>
+static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t S, const double* d_K,
+                       bool mixed, bool converged) {
+    const size_t need = hierarchy_bytes(n_fine, n0, S, sizeof(T), mixed, converged);
     if (ctx->arena.capacity < need) {
         if (ctx->arena.base) cudaFree(ctx->arena.base);
         ctx->arena.base = nullptr;
@@ -270,9 +408,9 @@ static fm_status carve(fm_ctx* ctx, Hierarchy& H, int n_fine, int n0, size_t S, 
         ctx->arena.capacity = need;
     }
     char* cur = ctx->arena.base;
-    auto take = [&](size_t count) {
-        double* p = reinterpret_cast<double*>(cur);
-        cur += ((count * sizeof(double) + 255) / 256) * 256;
+    auto take = [&](size_t bytes) {
+        char* p = cur;
+        cur += ((bytes + 255) / 256) * 256;
         return p;
     };
     H.ctx = ctx;
@@ -283,62 +421,111 @@ static fm_status carve(fm_ctx* ctx, Hierarchy& H, int n_fine, int n0, size_t S, 
     for (int k = 0; k <= H.m; ++k) {
         const int n = n0 << k;
         const size_t cnt = S * (size_t)n * n;
-        GridBufs& g = H.g[k];
+        GridBufs<T>& g = H.g[k];
         g.n = n;
-        g.K = (k == H.m) ? d_K : take(cnt);
-        g.Te = take(cnt);
-        g.Tn = take(cnt);
-        g.D = take(cnt);
-        g.p = take(cnt);
-        g.b = take(cnt);
+        g.K = (k == H.m) ? d_K : (double*)take(cnt * 8);
+        g.Te = (T*)take(cnt * sizeof(T));
+        g.Tn = (T*)take(cnt * sizeof(T));
+        g.D = (T*)take(cnt * sizeof(T));
+        g.p = (T*)take(cnt * sizeof(T));
+        g.b = (T*)take(cnt * sizeof(T));
+        g.p64 = g.Te64 = g.Tn64 = g.D64 = nullptr;
+        if (mixed && k >= H.m - 1) {
+            g.p64 = (double*)take(cnt * 8);
+            g.Te64 = (double*)take(cnt * 8);
+            g.Tn64 = (double*)take(cnt * 8);
+            g.D64 = (double*)take(cnt * 8);
+        }
     }
-    H.Ainv = take(S * (size_t)n0 * n0 * n0 * n0);
+    H.Ainv = (T*)take(S * (size_t)n0 * n0 * n0 * n0 * sizeof(T));
+    H.active = converged ? (int32_t*)take(S * 4) : nullptr;
+    H.left = converged ? (int32_t*)take(4) : nullptr;
     return FM_OK;
 }
 
-static void vcycle(const Hierarchy& H, int k, const fm_solve_params& prm, cudaStream_t st) {
+template <typename T>
+static void vcycle(const Hierarchy<T>& H, int k, const fm_solve_params& prm, const int32_t* active,
+                   cudaStream_t st) {
     fm_ctx* ctx = H.ctx;
     const size_t S = H.S;
-    const GridBufs& g = H.g[k];
+    const GridBufs<T>& g = H.g[k];
+    const double ts = sizeof(T);
     if (k == 0) {
         const int m = H.n0 * H.n0;
-        FM_TIMED(ctx, kFamCoarseSolve, st, (double)S * (m * m + 2 * m) * 8.0, 2.0 * S * m * m,
-                 k_coarse_solve<<<blocks_for(S * m), kBlock, 0, st>>>(m, S, H.Ainv, g.b, g.p));
+        FM_TIMED(ctx, kFamCoarseSolve, st, (double)S * (m * m + 2 * m) * ts, 2.0 * S * m * m,
+                 k_coarse_solve<T><<<blocks_for(S * m), kBlock, 0, st>>>(m, S, H.Ainv, g.b, g.p, active));
         return;
     }
     const int n = g.n;
     const size_t cells = S * (size_t)n * n;
     const size_t half = cells / 2;
     // algorithmic bytes of one colour: half of a single-pass sweep that reads
-    // p, b, Te, Tn, D and writes p (48 B per cell in FP64)
-    const double sweep_half_bytes = 24.0 * cells, sweep_half_flops = 5.0 * cells;
+    // p, b, Te, Tn, D and writes p (6 words per cell)
+    const double sweep_half_bytes = 3.0 * ts * cells, sweep_half_flops = 5.0 * cells;
     for (int it = 0; it < prm.nu1; ++it)
         for (int color = 0; color < 2; ++color)
             FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D, g.p));
-    const GridBufs& c = H.g[k - 1];
-    FM_TIMED(ctx, kFamResidualRestrict, st, 44.0 * cells, 10.0 * cells,
-             k_residual_restrict<<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
-                 c.n, S, g.b, g.Te, g.Tn, g.D, g.p, c.b, c.p));
-    vcycle(H, k - 1, prm, st);
-    FM_TIMED(ctx, kFamProlong, st, 18.0 * cells, 8.0 * cells,
-             k_prolong<<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, 0.0, 0.0, 1, g.p));
+                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D,
+                                                                          g.p, active));
+    const GridBufs<T>& c = H.g[k - 1];
+    FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
+             k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
+                 c.n, S, g.b, g.Te, g.Tn, g.D, g.p, c.b, c.p, active));
+    vcycle(H, k - 1, prm, active, st);
+    FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
+             k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, g.p, active));
     for (int it = 0; it < prm.nu2; ++it)
         for (int color = 0; color < 2; ++color)
             FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D, g.p));
+                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D,
+                                                                          g.p, active));
 }
 
-static void outflux(const Hierarchy& H, int k, double pE, double* q, cudaStream_t st) {
-    const GridBufs& g = H.g[k];
-    FM_TIMED(H.ctx, kFamOutflux, st, 16.0 * H.S * g.n, 3.0 * H.S * g.n,
-             k_outflux<<<blocks_for(H.S * 32), kBlock, 0, st>>>(g.n, H.S, g.K, g.p, pE, q));
+template <typename P>
+static void outflux(fm_ctx* ctx, int n, size_t S, const double* K, const P* p, double pE, double* q,
+                    cudaStream_t st) {
+    FM_TIMED(ctx, kFamOutflux, st, 16.0 * S * n, 3.0 * S * n,
+             k_outflux<P><<<blocks_for(S * 32), kBlock, 0, st>>>(n, S, K, p, pE, q));
 }
 
-static void fmg_batch(const Hierarchy& H, const fm_solve_params& prm, double* qf, double* qc,
-                      double* p_out, cudaStream_t st) {
+// Cycles of one refined stage until every sample passes its residual test.
+template <typename T>
+static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_params& prm, bool mixed,
+                              int32_t* status, cudaStream_t st) {
+    fm_ctx* ctx = H.ctx;
+    const GridBufs<T>& g = H.g[k];
+    const size_t S = H.S, cells = (size_t)g.n * g.n;
+    FM_CUDA_TRY(ctx, cudaMemsetAsync(H.active, 0xff, S * sizeof(int32_t), st));   // all active (-1)
+    int32_t left = 0;
+    for (int it = 0;; ++it) {
+        FM_CUDA_TRY(ctx, cudaMemsetAsync(H.left, 0, sizeof(int32_t), st));
+        FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * S * cells, 12.0 * S * cells,
+                 k_stage_check<T><<<(unsigned)S, kBlock, 0, st>>>(
+                     g.n, S, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64,
+                     g.b, g.p, prm.tol, H.active, H.left));
+        FM_CUDA_TRY(ctx, cudaMemcpyAsync(&left, H.left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        if (left == 0) break;
+        if (it >= prm.max_cycles) {
+            if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
+            break;
+        }
+        vcycle(H, k, prm, H.active, st);
+        if (mixed)
+            k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, st>>>(cells, S, g.p, g.p64, H.active);
+    }
+    return FM_OK;
+}
+
+template <typename T>
+static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, double* qf, double* qc,
+                           double* p_out, int32_t* status, cudaStream_t st) {
     fm_ctx* ctx = H.ctx;
     const size_t S = H.S;
+    const bool mixed = prm.precision == FM_PREC_MIXED;
+    const bool conv = prm.converged != 0;
+    const double ts = sizeof(T);
+    if (status) FM_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int32_t) * S, st));
     // coefficient hierarchy: inject, then faces and diagonals on every grid
     for (int k = H.m; k >= 1; --k) {
         const int nc = H.g[k - 1].n;
@@ -347,45 +534,85 @@ static void fmg_batch(const Hierarchy& H, const fm_solve_params& prm, double* qf
                  k_inject<<<blocks_for(cc), kBlock, 0, st>>>(nc, S, H.g[k].K, const_cast<double*>(H.g[k - 1].K)));
     }
     for (int k = 0; k <= H.m; ++k) {
-        const GridBufs& g = H.g[k];
+        const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
-        FM_TIMED(ctx, kFamCoefficients, st, 32.0 * cells, 16.0 * cells,
-                 k_coefficients<<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D));
+        FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts + (g.Te64 ? 24.0 : 0.0)) * cells, 16.0 * cells,
+                 k_coefficients<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D, g.Te64,
+                                                                         g.Tn64, g.D64));
     }
     {
         const int m = H.n0 * H.n0;
-        FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (3 * m + m * m) * 8.0, 2.0 * S * m * m * m,
-                 k_coarse_inverse<<<blocks_for(S), 64, 0, st>>>(H.n0, S, H.g[0].Te, H.g[0].Tn, H.g[0].D, H.Ainv));
+        FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (8 * m + ts * m * m), 2.0 * S * m * m * m,
+                 k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(H.n0, S, H.g[0].K, H.Ainv));
     }
-    // stage 0: exact solve of the coarsest stage problem
-    {
-        const GridBufs& g = H.g[0];
+    for (int k = 0; k <= H.m; ++k) {
+        const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
-        FM_TIMED(ctx, kFamStageRhs, st, 16.0 * cells, 2.0 * cells,
-                 k_stage_rhs<<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, prm.pW, prm.pE, g.b));
-        vcycle(H, 0, prm, st);
-        if (H.m == 1 && qc) outflux(H, 0, prm.pE, qc, st);
+        const bool refined = conv && k >= H.m - 1;
+        if (k > 0) {
+            const GridBufs<T>& c = H.g[k - 1];
+            if (mixed && refined && k == H.m && H.m >= 1) {
+                FM_TIMED(ctx, kFamFmgInterp, st, 10.0 * cells, 8.0 * cells,
+                         k_prolong<double><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p64, prm.pW, prm.pE, 0,
+                                                                                 g.p64, nullptr));
+            } else {
+                FM_TIMED(ctx, kFamFmgInterp, st, 1.25 * ts * cells, 8.0 * cells,
+                         k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, (T)prm.pW, (T)prm.pE, 0,
+                                                                            g.p, nullptr));
+            }
+        }
+        FM_TIMED(ctx, kFamStageRhs, st, (8.0 + ts) * cells, 2.0 * cells,
+                 k_stage_rhs<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, prm.pW, prm.pE, g.b));
+        if (k == 0) vcycle(H, 0, prm, nullptr, st);
+        if (!refined) {
+            if (k > 0)
+                for (int it = 0; it < prm.nu0; ++it) vcycle(H, k, prm, nullptr, st);
+        } else {
+            if (mixed && !(k == H.m && H.m >= 1))
+                k_widen<T><<<blocks_for(cells), kBlock, 0, st>>>(cells, g.p, g.p64);
+            FM_TRY(refine_stage(H, k, prm, mixed, status, st));
+        }
+        if (k == H.m - 1 && qc) {
+            if (mixed && refined) outflux(ctx, g.n, S, g.K, g.p64, prm.pE, qc, st);
+            else outflux(ctx, g.n, S, g.K, g.p, prm.pE, qc, st);
+        }
     }
-    for (int k = 1; k <= H.m; ++k) {
-        const GridBufs& g = H.g[k];
-        const size_t cells = S * (size_t)g.n * g.n;
-        FM_TIMED(ctx, kFamFmgInterp, st, 10.0 * cells, 8.0 * cells,
-                 k_prolong<<<blocks_for(cells), kBlock, 0, st>>>(H.g[k - 1].n, S, H.g[k - 1].p, prm.pW, prm.pE, 0, g.p));
-        FM_TIMED(ctx, kFamStageRhs, st, 16.0 * cells, 2.0 * cells,
-                 k_stage_rhs<<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, prm.pW, prm.pE, g.b));
-        for (int it = 0; it < prm.nu0; ++it) vcycle(H, k, prm, st);
-        if (k == H.m - 1 && qc) outflux(H, k, prm.pE, qc, st);
-    }
+    const GridBufs<T>& f = H.g[H.m];
+    const bool fine64 = mixed && conv;
     if (H.m == 0 && qc) k_fill<<<blocks_for(S), kBlock, 0, st>>>(S, std::nan(""), qc);
-    outflux(H, H.m, prm.pE, qf, st);
-    if (p_out)
-        cudaMemcpyAsync(p_out, H.g[H.m].p, sizeof(double) * S * H.g[H.m].n * H.g[H.m].n,
-                        cudaMemcpyDeviceToDevice, st);
+    if (fine64) outflux(ctx, f.n, S, f.K, f.p64, prm.pE, qf, st);
+    else outflux(ctx, f.n, S, f.K, f.p, prm.pE, qf, st);
+    if (p_out) {
+        const size_t cells = S * (size_t)f.n * f.n;
+        if (fine64)
+            FM_CUDA_TRY(ctx, cudaMemcpyAsync(p_out, f.p64, sizeof(double) * cells, cudaMemcpyDeviceToDevice, st));
+        else
+            k_widen<T><<<blocks_for(cells), kBlock, 0, st>>>(cells, f.p, p_out);
+    }
+    return FM_OK;
+}
+
+template <typename T>
+static fm_status levelwise(fm_ctx* ctx, int n_fine, int n0, uint32_t S, const double* d_K,
+                           const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
+                           int32_t* d_status, cudaStream_t st) {
+    const bool mixed = prm.precision == FM_PREC_MIXED;
+    const int64_t lim = batch_limit(ctx, n_fine);
+    for (uint64_t first = 0; first < S; first += (uint64_t)lim) {
+        const size_t cnt = (size_t)std::min<uint64_t>((uint64_t)lim, S - first);
+        const size_t off = first * (size_t)n_fine * n_fine;
+        Hierarchy<T> H;
+        FM_TRY(carve(ctx, H, n_fine, n0, cnt, d_K + off, mixed, prm.converged != 0));
+        FM_TRY(fmg_batch(H, prm, d_qf + first, d_qc ? d_qc + first : nullptr, d_p ? d_p + off : nullptr,
+                         d_status ? d_status + first : nullptr, st));
+        FM_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return FM_OK;
 }
 
 fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
                          const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
-                         cudaStream_t st) {
+                         int32_t* d_status, cudaStream_t st) {
     const int n0 = prm.n_coarsest;
     FM_CHECK_ARG(ctx, n0 >= 2 && n0 <= 4, "fmg_solve_batch: n_coarsest must be 2..4");
     FM_CHECK_ARG(ctx, n_fine >= n0 && n_fine <= 8192, "fmg_solve_batch: bad n_fine");
@@ -394,19 +621,28 @@ fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
     FM_CHECK_ARG(ctx, (n0 << m) == n_fine, "fmg_solve_batch: n_fine must be n_coarsest * 2^m");
     FM_CHECK_ARG(ctx, prm.nu0 >= 1 && prm.nu1 >= 0 && prm.nu2 >= 0 && prm.nu1 + prm.nu2 >= 1,
                  "fmg_solve_batch: need nu0 >= 1 and nu1 + nu2 >= 1");
-    FM_CHECK_ARG(ctx, prm.precision == FM_PREC_FP64, "fmg_solve_batch: unknown precision");
+    FM_CHECK_ARG(ctx, prm.precision == FM_PREC_FP64 || prm.precision == FM_PREC_MIXED,
+                 "fmg_solve_batch: unknown precision");
+    FM_CHECK_ARG(ctx, prm.precision != FM_PREC_MIXED || prm.converged,
+                 "fmg_solve_batch: the mixed form refines to a tolerance (converged = 1)");
+    FM_CHECK_ARG(ctx, !prm.converged || (prm.tol > 0 && prm.max_cycles >= 1),
+                 "fmg_solve_batch: converged mode needs tol > 0 and max_cycles >= 1");
     FM_CHECK_ARG(ctx, S == 0 || (d_K && d_qf), "fmg_solve_batch: null input or output");
+    FM_CHECK_ARG(ctx, prm.kernel >= FM_KERNEL_AUTO && prm.kernel <= FM_KERNEL_RESIDENT,
+                 "fmg_solve_batch: unknown kernel schedule");
     if (S == 0) return FM_OK;
-    const int64_t lim = batch_limit(ctx, n_fine);
-    for (uint64_t first = 0; first < S; first += (uint64_t)lim) {
-        const size_t cnt = (size_t)std::min<uint64_t>((uint64_t)lim, S - first);
-        const size_t off = first * (size_t)n_fine * n_fine;
-        Hierarchy H;
-        FM_TRY(carve(ctx, H, n_fine, n0, cnt, d_K + off));
-        fmg_batch(H, prm, d_qf + first, d_qc ? d_qc + first : nullptr, d_p ? d_p + off : nullptr, st);
-        FM_CUDA_TRY(ctx, cudaGetLastError());
+    if (prm.kernel != FM_KERNEL_LEVELWISE) {
+        if (fmg_resident_launch(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st)) {
+            FM_CUDA_TRY(ctx, cudaGetLastError());
+            return FM_OK;
+        }
+        FM_CHECK_ARG(ctx, prm.kernel == FM_KERNEL_AUTO,
+                     "fmg_solve_batch: the resident schedule needs the hierarchy in shared memory "
+                     "(n_fine <= 64)");
     }
-    return FM_OK;
+    if (prm.precision == FM_PREC_MIXED)
+        return levelwise<float>(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
+    return levelwise<double>(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
 }
 
 }  // namespace fm
@@ -415,8 +651,8 @@ using namespace fm;
 
 extern "C" fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                                      const fm_solve_params* prm, double* d_qf, double* d_qc,
-                                     double* d_p, void* stream) {
+                                     double* d_p, int32_t* d_status, void* stream) {
     FM_CHECK_ARG(ctx, ctx != nullptr, "fmg_solve_batch: null context");
     FM_CHECK_ARG(ctx, prm != nullptr, "fmg_solve_batch: null parameters");
-    return fmg_solve_impl(ctx, n_fine, n, d_K, *prm, d_qf, d_qc, d_p, as_stream(stream));
+    return fmg_solve_impl(ctx, n_fine, n, d_K, *prm, d_qf, d_qc, d_p, d_status, as_stream(stream));
 }

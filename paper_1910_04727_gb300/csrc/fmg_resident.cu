@@ -1,0 +1,544 @@
+// Sample-resident full multigrid: one CTA owns one sample at a time and keeps
+// its entire FMG hierarchy (Sec. 2.5) in shared memory.  HBM traffic is the
+// fine coefficient field in and two QoIs out, so small grids (the level-0
+// work of an MLMC run, hundreds of thousands of 16x16 .. 64x64 samples) run
+// at shared-memory speed instead of streaming every sweep through L2/HBM.
+// CTAs are persistent: each loops over samples blockIdx.x, +gridDim.x, ...
+//
+// Shared layout per grid k (n = n0 << k), type T of the V-cycle arithmetic:
+//   p    iterate (a correction inside iterative refinement)
+//   te   east-face transmissibility (2K on the east edge)
+//   tn   north-face transmissibility (0 on the north edge)
+//   tw   west-edge transmissibility 2K of each row (n values)
+//   dinv reciprocal diagonal (FP64 form only; FP32 divides on the fly)
+//   b    right-hand side.  In the FP64 form the finest grid has none: it only
+//        ever solves its stage problem, whose right-hand side (the Dirichlet
+//        data) is formed on the fly from tw, te, p_W and p_E.
+// Mixed form (T = float): the grids of the two refined stages (n_fine/2 and
+// n_fine, which give Q^c and Q^f) also hold FP64 p, te, tn, tw; the FP64
+// residual of the stage problem is the right-hand side of an FP32 V-cycle
+// for the correction, which is added to the FP64 iterate.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace fm {
+
+template <typename T>
+struct RGrid {
+    int n;
+    T *p, *te, *tn, *dinv, *tw, *b;   // dinv and b may be null
+};
+
+struct HGrid {
+    int n;
+    double *p, *te, *tn, *tw;
+};
+
+template <typename T>
+struct RLayout {
+    int m, n0;
+    RGrid<T> g[8];
+    HGrid h[2];      // mixed form: h[0] = grid m-1 (m >= 1), h[1] = grid m
+    T* ainv;         // inverse of the coarsest operator
+    T* work;         // Gauss-Jordan scratch
+    double* red;     // block-reduction scratch (80 doubles)
+    size_t bytes;
+};
+
+// Carve the shared buffer (or count its size when base == nullptr).
+template <typename T>
+__host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, int n0, bool mixed) {
+    RLayout<T> L;
+    L.n0 = n0;
+    L.m = 0;
+    while ((n0 << L.m) < n_fine) ++L.m;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base + off;
+        off += ((bytes + 15) / 16) * 16;
+        return p;
+    };
+    for (int k = 0; k <= L.m; ++k) {
+        const int n = n0 << k;
+        const size_t c = (size_t)n * n;
+        RGrid<T>& g = L.g[k];
+        g.n = n;
+        g.p = (T*)take(c * sizeof(T));
+        g.te = (T*)take(c * sizeof(T));
+        g.tn = (T*)take(c * sizeof(T));
+        g.tw = (T*)take(n * sizeof(T));
+        g.dinv = mixed ? nullptr : (T*)take(c * sizeof(T));
+        g.b = (mixed || k < L.m) ? (T*)take(c * sizeof(T)) : nullptr;
+    }
+    for (int q = 0; q < 2; ++q) {
+        const int k = L.m - 1 + q;
+        HGrid& h = L.h[q];
+        h.n = (k >= 0) ? (n0 << k) : 0;
+        h.p = h.te = h.tn = h.tw = nullptr;
+        if (!mixed || k < 0) continue;
+        const size_t c = (size_t)h.n * h.n;
+        h.p = (double*)take(c * 8);
+        h.te = (double*)take(c * 8);
+        h.tn = (double*)take(c * 8);
+        h.tw = (double*)take(h.n * 8);
+    }
+    L.ainv = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
+    L.work = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
+    L.red = (double*)take(80 * 8);
+    L.bytes = off;
+    return L;
+}
+
+__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// ------------------------------------------------------------------ setup
+// Face transmissibilities of grid n, K injected from the fine field at
+// stride s = n_fine / n (read from global memory; L1/L2 serve the reuse).
+template <typename T>
+__device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const double* __restrict__ Kf,
+                                    int n_fine) {
+    const int n = g.n, s = n_fine / n;
+    auto K = [&](int i, int j) { return __ldg(Kf + (size_t)(s * j) * n_fine + (size_t)s * i); };
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const double k = K(i, j);
+        const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
+        const double te = (i < n - 1) ? harm(k, K(i + 1, j)) : 2.0 * k;
+        const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
+        const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : 0.0;
+        g.te[c] = (T)te;
+        g.tn[c] = (T)tn;
+        if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
+        if (i == 0) g.tw[j] = (T)(2.0 * k);
+        if (h) {
+            h->te[c] = te;
+            h->tn[c] = tn;
+            if (i == 0) h->tw[j] = 2.0 * k;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ V-cycle pieces
+// Right-hand side of cell (i, j): stored, or the stage problem's Dirichlet data.
+template <typename T>
+__device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
+    if (g.b) return g.b[c];
+    T v = T(0);
+    if (i == 0) v += g.tw[j] * pW;
+    if (i == g.n - 1) v += g.te[c] * pE;
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_at(const RGrid<T>& g, int c, int i, int j) {
+    const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
+    const T ts = (j > 0) ? g.tn[c - g.n] : T(0);
+    return tw + g.te[c] + ts + g.tn[c];
+}
+
+template <typename T>
+__device__ __forceinline__ T divide_by_diag(const RGrid<T>& g, T acc, int c, int i, int j) {
+    if (g.dinv) return acc * g.dinv[c];
+    return acc / diag_at(g, c, i, j);
+}
+
+// Gauss-Jordan inverse of the coarsest operator, all threads of the CTA.
+// A is SPD, so no pivoting.
+template <typename T>
+__device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A) {
+    const int n = g.n, m = n * n;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        T v = T(0);
+        if (r == c) {
+            v = diag_at(g, r, r % n, r / n);
+        } else {
+            const int ri = r % n, rj = r / n, ci = c % n, cj = c / n;
+            if (rj == cj && ci == ri + 1) v = -g.te[r];
+            if (rj == cj && ci == ri - 1) v = -g.te[c];
+            if (ri == ci && cj == rj + 1) v = -g.tn[r];
+            if (ri == ci && cj == rj - 1) v = -g.tn[c];
+        }
+        A[e] = v;
+        ainv[e] = (r == c) ? T(1) : T(0);
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        const T piv = A[k * m + k];
+        __syncthreads();
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+            A[k * m + c] /= piv;
+            ainv[k * m + c] /= piv;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e / m, c = e % m;
+            if (r == k) continue;
+            const T f = A[r * m + k];   // column k is left alone until the next phase
+            if (c != k) A[e] -= f * A[k * m + c];
+            ainv[e] -= f * ainv[k * m + c];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            if (r != k) A[r * m + k] = T(0);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, const T* ainv, T pW, T pE) {
+    const int n = g.n, m = n * n;
+    T acc = T(0);
+    if (threadIdx.x < m)
+        for (int c = 0; c < m; ++c) acc += ainv[threadIdx.x * m + c] * rhs_at(g, c, c % n, c / n, pW, pE);
+    __syncthreads();
+    if (threadIdx.x < m) g.p[threadIdx.x] = acc;
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T pE) {
+    const int n = g.n, half = n * n / 2, hn = n / 2;
+    for (int color = 0; color < 2; ++color) {
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const int j = h / hn;
+            const int i = 2 * (h % hn) + ((j + color) & 1);
+            const int c = j * n + i;
+            T acc = rhs_at(g, c, i, j, pW, pE);
+            if (i > 0) acc += g.te[c - 1] * g.p[c - 1];
+            if (i < n - 1) acc += g.te[c] * g.p[c + 1];
+            if (j > 0) acc += g.tn[c - n] * g.p[c - n];
+            if (j < n - 1) acc += g.tn[c] * g.p[c + n];
+            g.p[c] = divide_by_diag(g, acc, c, i, j);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
+    const int n = g.n;
+    T v = diag_at(g, c, i, j) * g.p[c];
+    if (i > 0) v -= g.te[c - 1] * g.p[c - 1];
+    if (i < n - 1) v -= g.te[c] * g.p[c + 1];
+    if (j > 0) v -= g.tn[c - n] * g.p[c - n];
+    if (j < n - 1) v -= g.tn[c] * g.p[c + n];
+    return rhs_at(g, c, i, j, pW, pE) - v;
+}
+
+template <typename T>
+__device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, T pW, T pE) {
+    const int nc = cg.n, nf = f.n;
+    for (int C = threadIdx.x; C < nc * nc; C += blockDim.x) {
+        const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J, c0 = j0 * nf + i0;
+        const T r00 = resident_residual(f, c0, i0, j0, pW, pE);
+        const T r10 = resident_residual(f, c0 + 1, i0 + 1, j0, pW, pE);
+        const T r01 = resident_residual(f, c0 + nf, i0, j0 + 1, pW, pE);
+        const T r11 = resident_residual(f, c0 + nf + 1, i0 + 1, j0 + 1, pW, pE);
+        cg.b[C] = r00 + r10 + r01 + r11;
+        cg.p[C] = T(0);
+    }
+    __syncthreads();
+}
+
+template <typename U>
+__device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, U gW, U gE) {
+    J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
+    if (I < 0) return U(2) * gW - uc[J * nc];
+    if (I > nc - 1) return U(2) * gE - uc[J * nc + nc - 1];
+    return uc[J * nc + I];
+}
+
+// out (+)= bilinear interpolation of uc (nc x nc) onto the 2nc x 2nc grid.
+template <typename U>
+__device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, U gW, U gE, bool add) {
+    const int nf = 2 * nc;
+    for (int c = threadIdx.x; c < nf * nf; c += blockDim.x) {
+        const int i = c % nf, j = c / nf, I = i >> 1, J = j >> 1;
+        const int Ix = (i & 1) ? I + 1 : I - 1;
+        const int Jy = (j & 1) ? J + 1 : J - 1;
+        const U v = (U(9) * ghost(uc, nc, I, J, gW, gE) + U(3) * ghost(uc, nc, Ix, J, gW, gE) +
+                     U(3) * ghost(uc, nc, I, Jy, gW, gE) + U(1) * ghost(uc, nc, Ix, Jy, gW, gE)) /
+                    U(16);
+        out[c] = add ? out[c] + v : v;
+    }
+    __syncthreads();
+}
+
+// One V(nu1, nu2) cycle on grid k, iteratively: descend (smooth, restrict
+// the residual), exact coarsest solve, ascend (prolong the correction,
+// smooth).  pW/pE only enter through a grid without a stored rhs.
+template <typename T>
+__device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, T pW, T pE) {
+    for (int l = k; l >= 1; --l) {
+        for (int s = 0; s < nu1; ++s) resident_rbgs(L.g[l], pW, pE);
+        resident_restrict(L.g[l], L.g[l - 1], pW, pE);
+    }
+    resident_coarse_solve(L.g[0], L.ainv, pW, pE);
+    for (int l = 1; l <= k; ++l) {
+        resident_prolong(L.g[l - 1].p, L.g[l - 1].n, L.g[l].p, T(0), T(0), true);
+        for (int s = 0; s < nu2; ++s) resident_rbgs(L.g[l], pW, pE);
+    }
+}
+
+// Sum of a and b over the CTA; every thread gets the totals.
+__device__ __forceinline__ void block_sum2(double a, double b, double* red, double& A, double& B) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[warp] = a;
+        red[32 + warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            sa += red[w];
+            sb += red[32 + w];
+        }
+        red[64] = sa;
+        red[65] = sb;
+    }
+    __syncthreads();
+    A = red[64];
+    B = red[65];
+    __syncthreads();
+}
+
+// Stage problem of grid k written into its rhs: the Dirichlet data.
+template <typename T>
+__device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, T pW, T pE) {
+    for (int c = threadIdx.x; c < g.n * g.n; c += blockDim.x) {
+        const int i = c % g.n, j = c / g.n;
+        T v = T(0);
+        if (i == 0) v += g.tw[j] * pW;
+        if (i == g.n - 1) v += g.te[c] * pE;
+        g.b[c] = v;
+    }
+    __syncthreads();
+}
+
+// ||r||^2 and ||rhs||^2 of the stage problem on grid k (V-cycle type).
+template <typename T>
+__device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, double& rr, double& bb) {
+    double a = 0.0, b = 0.0;
+    for (int c = threadIdx.x; c < g.n * g.n; c += blockDim.x) {
+        const int i = c % g.n, j = c / g.n;
+        const double r = (double)resident_residual(g, c, i, j, pW, pE);
+        const double f = (double)rhs_at(g, c, i, j, pW, pE);
+        a += r * r;
+        b += f * f;
+    }
+    block_sum2(a, b, red, rr, bb);
+}
+
+// FP64 residual of the stage problem on h into the FP32 grid's rhs (the
+// correction equation), zero the correction; returns the norms.
+template <typename T>
+__device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW, double pE, double* red,
+                            double& rr, double& bb) {
+    const int n = h.n;
+    double a = 0.0, b = 0.0;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const double tw = (i > 0) ? h.te[c - 1] : h.tw[j];
+        const double ts = (j > 0) ? h.tn[c - n] : 0.0;
+        double f = 0.0;
+        if (i == 0) f += h.tw[j] * pW;
+        if (i == n - 1) f += h.te[c] * pE;
+        double v = (tw + h.te[c] + ts + h.tn[c]) * h.p[c];
+        if (i > 0) v -= h.te[c - 1] * h.p[c - 1];
+        if (i < n - 1) v -= h.te[c] * h.p[c + 1];
+        if (j > 0) v -= h.tn[c - n] * h.p[c - n];
+        if (j < n - 1) v -= h.tn[c] * h.p[c + n];
+        const double r = f - v;
+        g.b[c] = (T)r;
+        g.p[c] = T(0);
+        a += r * r;
+        b += f * f;
+    }
+    block_sum2(a, b, red, rr, bb);
+}
+
+// Q = sum_j te(n-1, j) (p(n-1, j) - pE); warp 0 reduces, valid in thread 0.
+template <typename P, typename Q>
+__device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, double pE) {
+    double acc = 0.0;
+    if (threadIdx.x < 32) {
+        for (int j = threadIdx.x; j < n; j += 32) {
+            const int c = j * n + n - 1;
+            acc += (double)te[c] * ((double)p[c] - pE);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    }
+    return acc;
+}
+
+struct ResidentArgs {
+    int n_fine, n0;
+    size_t S;
+    const double* K;
+    double pW, pE;
+    int nu0, nu1, nu2;
+    int converged, max_cycles;
+    double tol;
+    double *qf, *qc, *p_out;
+    int32_t* status;
+};
+
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const RLayout<T> L = resident_layout<T>(smem, a.n_fine, a.n0, MIXED);
+    const T tpW = (T)a.pW, tpE = (T)a.pE;
+    const int m = L.m;
+    for (size_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+        const double* Kf = a.K + s * (size_t)a.n_fine * a.n_fine;
+        for (int k = 0; k <= m; ++k) {
+            const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
+            resident_setup_grid(L.g[k], h, Kf, a.n_fine);
+        }
+        __syncthreads();
+        resident_coarse_inverse(L.g[0], L.ainv, L.work);
+        bool ok = true;
+        double q_coarse = NAN, q_fine = NAN;
+
+        for (int k = 0; k <= m; ++k) {
+            const RGrid<T>& g = L.g[k];
+            // the stages giving Q^c and Q^f are refined when converged
+            const bool refined = a.converged && k >= m - 1;
+            if (k > 0) {
+                if (MIXED && refined && k == m && m >= 1) {
+                    // FP64 interpolation of the refined stage m-1 solution
+                    resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.pW, a.pE, false);
+                } else {
+                    resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, tpW, tpE, false);
+                }
+            }
+            if (g.b) resident_stage_rhs(g, tpW, tpE);
+            if (k == 0) resident_coarse_solve(g, L.ainv, tpW, tpE);
+            if (!refined) {
+                if (k > 0)
+                    for (int it = 0; it < a.nu0; ++it) resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+            } else if (!MIXED) {
+                // FP64: V-cycles on the stage problem until the residual test passes
+                for (int it = 0;; ++it) {
+                    double rr, bb;
+                    stage_norms(g, tpW, tpE, L.red, rr, bb);
+                    if (rr <= a.tol * a.tol * bb) break;
+                    if (it >= a.max_cycles) {
+                        ok = false;
+                        break;
+                    }
+                    resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                }
+            } else {
+                // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
+                const HGrid& h = L.h[k - (m - 1)];
+                if (!(k == m && m >= 1)) {
+                    for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] = (double)g.p[c];
+                    __syncthreads();
+                }
+                for (int it = 0;; ++it) {
+                    double rr, bb;
+                    ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
+                    if (rr <= a.tol * a.tol * bb) break;
+                    if (it >= a.max_cycles) {
+                        ok = false;
+                        break;
+                    }
+                    resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
+                    for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] += (double)g.p[c];
+                    __syncthreads();
+                }
+            }
+            // outflux of the stage (the FP64 iterate in mixed refined stages)
+            if (k >= m - 1) {
+                double q;
+                if (MIXED && refined) {
+                    const HGrid& h = L.h[k - (m - 1)];
+                    q = outflux_of(h.te, h.p, h.n, a.pE);
+                } else {
+                    q = outflux_of(g.te, g.p, g.n, a.pE);
+                }
+                if (k == m) q_fine = q;
+                else q_coarse = q;
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            a.qf[s] = q_fine;
+            if (a.qc) a.qc[s] = q_coarse;
+            if (a.status) a.status[s] = ok ? FM_OK : FM_ENOTCONV;
+        }
+        if (a.p_out) {
+            const bool fine64 = MIXED && a.converged;
+            double* po = a.p_out + s * (size_t)a.n_fine * a.n_fine;
+            for (int c = threadIdx.x; c < a.n_fine * a.n_fine; c += blockDim.x)
+                po[c] = fine64 ? L.h[1].p[c] : (double)L.g[m].p[c];
+        }
+        __syncthreads();
+    }
+}
+
+size_t resident_smem_bytes(int n_fine, int n0, bool mixed) {
+    return mixed ? resident_layout<float>(nullptr, n_fine, n0, true).bytes
+                 : resident_layout<double>(nullptr, n_fine, n0, false).bytes;
+}
+
+constexpr size_t kResidentSmemMax = 227 * 1024;
+
+template <typename T, bool MIXED>
+static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st) {
+    const size_t smem = resident_smem_bytes(a.n_fine, a.n0, MIXED);
+    if (smem > kResidentSmemMax) return false;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_fmg_resident<T, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kResidentSmemMax);
+        attr_done = true;
+    }
+    const int threads = a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fmg_resident<T, MIXED>, threads, smem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const size_t grid = std::min<size_t>(a.S, (size_t)std::max(per_sm, 1) * sms);
+    const double cells = (double)a.S * a.n_fine * a.n_fine;
+    FM_TIMED(ctx, kFamResidentFmg, st, 8.0 * cells + 16.0 * a.S, 0.0,
+             k_fmg_resident<T, MIXED><<<(unsigned)grid, threads, smem, st>>>(a));
+    return true;
+}
+
+bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double* d_K,
+                         const fm_solve_params& prm, double* qf, double* qc, double* p_out,
+                         int32_t* status, cudaStream_t st) {
+    ResidentArgs a;
+    a.n_fine = n_fine;
+    a.n0 = n0;
+    a.S = S;
+    a.K = d_K;
+    a.pW = prm.pW;
+    a.pE = prm.pE;
+    a.nu0 = prm.nu0;
+    a.nu1 = prm.nu1;
+    a.nu2 = prm.nu2;
+    a.converged = prm.converged;
+    a.max_cycles = prm.max_cycles;
+    a.tol = prm.tol;
+    a.qf = qf;
+    a.qc = qc;
+    a.p_out = p_out;
+    a.status = status;
+    if (prm.precision == FM_PREC_MIXED) return launch_resident<float, true>(ctx, a, st);
+    return launch_resident<double, false>(ctx, a, st);
+}
+
+}  // namespace fm

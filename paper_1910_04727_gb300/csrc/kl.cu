@@ -125,8 +125,15 @@ static fm_status install_basis(fm_ctx* ctx, const double* d_Bref) {
         FM_CUDA_TRY(ctx, cudaGetLastError());
     }
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    const int mode = kl_mode_of(ctx);
+    if (mode == FM_KL_BF16 || mode == FM_KL_BF16X3) FM_TRY(kl_tc_install(ctx, mode == FM_KL_BF16X3));
     ctx->basis_ready = true;
     return FM_OK;
+}
+
+int kl_mode_of(const fm_ctx* ctx) {
+    if (ctx->cfg.kl_mode != FM_KL_AUTO) return ctx->cfg.kl_mode;
+    return ctx->cfg.precision == FM_PREC_MIXED ? FM_KL_BF16X3 : FM_KL_FP64;
 }
 
 }  // namespace fm
@@ -286,6 +293,9 @@ extern "C" fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, cons
     FM_CHECK_ARG(ctx, ctx->basis_ready, "kl_field_batch: no KL basis installed");
     FM_CHECK_ARG(ctx, n == 0 || (d_xi && d_K), "kl_field_batch: null pointer");
     if (n == 0) return FM_OK;
+    const int mode = kl_mode_of(ctx);
+    if (mode == FM_KL_BF16 || mode == FM_KL_BF16X3)
+        return kl_tc_field(ctx, level, n, d_xi, d_K, as_stream(stream));
     const int N = grid_of_level(ctx, level);
     const int cells = N * N;
     dim3 grid((cells + kTC - 1) / kTC, (n + kTS - 1) / kTS);

@@ -15,6 +15,7 @@
 namespace fm {
 
 constexpr int kSumBlock = 256;
+constexpr double kMaxSamplesPerLevel = 1e9;   // guard against a runaway sample-size rule
 constexpr int kSumItems = 2048;   // samples per block
 
 struct Pair {
@@ -101,6 +102,10 @@ static fm_solve_params solve_params(const fm_ctx* ctx) {
     p.nu1 = ctx->cfg.nu1;
     p.nu2 = ctx->cfg.nu2;
     p.precision = ctx->cfg.precision;
+    p.kernel = FM_KERNEL_AUTO;
+    p.converged = ctx->cfg.converged;
+    p.tol = ctx->cfg.tol;
+    p.max_cycles = ctx->cfg.max_cycles;
     return p;
 }
 
@@ -152,7 +157,7 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
         FM_TRY(kl_field_batch(ctx, level, cnt, ctx->d_xi, ctx->d_K, stream));
         double* qf = ctx->d_q;
         double* qc = ctx->d_q + cap;
-        FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, st));
+        FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, nullptr, st));
         if (d_sums) FM_TRY(level_sums_add(ctx, cnt, qf, qc, level > 0, d_sums, st));
         if (d_qf) FM_CUDA_TRY(ctx, cudaMemcpyAsync(d_qf + off, qf, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (d_qc) FM_CUDA_TRY(ctx, cudaMemcpyAsync(d_qc + off, qc, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -186,7 +191,7 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
     int rounds = 0;
 
     auto refresh = [&]() -> fm_status {
-        FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+        FM_TRY(fm_sync(ctx));
         FM_CUDA_TRY(ctx, cudaMemcpy(h.data(), ctx->d_sums, cells * sizeof(fm_level_sums), cudaMemcpyDeviceToHost));
         for (int l = 0; l <= L; ++l) {
             if (!opts->qmc) {
@@ -237,6 +242,12 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
             for (int l = 0; l <= L; ++l) tot += std::sqrt(var[l] * C[l]);
             for (int l = 0; l <= L; ++l) {
                 const double opt = std::ceil(2.0 / (opts->eps * opts->eps) * std::sqrt(var[l] / C[l]) * tot);
+                if (!std::isfinite(opt) || opt > kMaxSamplesPerLevel) {
+                    set_error(ctx, "mlmc_estimate: level " + std::to_string(l) + " would need " +
+                                       std::to_string(opt) + " samples (variance " + std::to_string(var[l]) +
+                                       "); beyond the per-level cap");
+                    return FM_ENOTCONV;
+                }
                 dN[l] = std::max<int64_t>(0, (int64_t)opt - N[l]);
             }
         }

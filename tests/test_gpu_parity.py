@@ -91,11 +91,18 @@ def test_kl_field_matches_oracle(small):
 
 
 # ------------------------------------------------------------------ solver
-@pytest.mark.parametrize("n,S", [(4, 5), (8, 37), (16, 33), (32, 129), (64, 19), (128, 7), (256, 3)])
-def test_fmg_solve_matches_oracle(small, n, S):
+LEVELWISE, RESIDENT = 1, 2
+CASES = [(4, 5, LEVELWISE), (8, 37, LEVELWISE), (16, 33, LEVELWISE), (32, 129, LEVELWISE),
+         (64, 19, LEVELWISE), (128, 7, LEVELWISE), (256, 3, LEVELWISE),
+         (4, 5, RESIDENT), (8, 37, RESIDENT), (16, 1000, RESIDENT), (32, 129, RESIDENT),
+         (64, 19, RESIDENT)]
+
+
+@pytest.mark.parametrize("n,S,kernel", CASES)
+def test_fmg_solve_matches_oracle(small, n, S, kernel):
     ctx, _ = small
     K = W.smooth_lognormal_field(n, S=S, tag=60 + n)
-    qf, qc, p = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True)
+    qf, qc, p = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, kernel=kernel)
     rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(), want_p=True)
     assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
     if n > 4:
@@ -105,12 +112,30 @@ def test_fmg_solve_matches_oracle(small, n, S):
     np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=1e-11)
 
 
-def test_fmg_other_parameters_match_oracle(small):
+def test_resident_schedule_rejects_grids_beyond_shared_memory(fm, small):
+    ctx, _ = small
+    K = torch.ones((2, 128, 128), dtype=torch.float64, device="cuda")
+    with pytest.raises(fm.FmError, match="shared memory"):
+        ctx.fmg_solve_batch(K, kernel=RESIDENT)
+
+
+def test_resident_and_levelwise_agree_on_kl_fields(small):
+    ctx, _ = small
+    xi = torch.tensor(W.normals(300, 24, tag=71), device="cuda")
+    K = ctx.kl_field_batch(2, xi)
+    a = ctx.fmg_solve_batch(K, kernel=LEVELWISE)
+    b = ctx.fmg_solve_batch(K, kernel=RESIDENT)
+    assert _rel(b[0].cpu().numpy(), a[0].cpu().numpy()) < 1e-12
+    assert _rel(b[1].cpu().numpy(), a[1].cpu().numpy()) < 1e-12
+
+
+@pytest.mark.parametrize("kernel", [LEVELWISE, RESIDENT])
+def test_fmg_other_parameters_match_oracle(small, kernel):
     ctx, _ = small
     K = W.smooth_lognormal_field(32, S=9, tag=70)
     for kw in [dict(nu0=1, nu1=1, nu2=1), dict(nu0=3, nu1=2, nu2=1), dict(pW=100.0, pE=0.0),
                dict(pW=3.0, pE=1.0), dict(n_coarsest=2)]:
-        qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), **kw)
+        qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), kernel=kernel, **kw)
         rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params(**{k: v for k, v in kw.items() if k != "n_coarsest"}),
                                           n0=kw.get("n_coarsest", 4))
         assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
@@ -227,3 +252,116 @@ def test_full_size_level_sampled_against_oracle(fm):
     rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params())
     assert _rel(qf[picks], rf) < RTOL_Q
     assert _rel(qc[picks], rc) < RTOL_Q
+
+
+# ------------------------------------------------------------------ converged / mixed
+RTOL_MIXED = 1e-8   # mixed path after refinement, against the converged FP64 oracle
+
+
+REFINED_CASES = [(8, RESIDENT), (16, RESIDENT), (32, RESIDENT), (64, RESIDENT),
+                 (8, LEVELWISE), (32, LEVELWISE), (128, LEVELWISE)]
+
+
+@pytest.mark.parametrize("n,kernel", REFINED_CASES)
+def test_converged_fp64_matches_converged_oracle(small, n, kernel):
+    ctx, _ = small
+    K = W.smooth_lognormal_field(n, S=23, tag=90 + n)
+    qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
+                                        converged=1, tol=1e-12, max_cycles=200, kernel=kernel)
+    rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
+                                       want_p=True)
+    assert int(st.abs().sum()) == 0
+    assert _rel(qf.cpu().numpy(), rf) < 1e-10
+    assert _rel(qc.cpu().numpy(), rc) < 1e-10
+
+
+@pytest.mark.parametrize("n,kernel", REFINED_CASES)
+def test_mixed_precision_matches_converged_oracle(fm, small, n, kernel):
+    ctx, _ = small
+    K = W.smooth_lognormal_field(n, S=41, tag=100 + n)
+    qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
+                                        precision=fm.FM_PREC_MIXED, converged=1, tol=1e-11,
+                                        max_cycles=200, kernel=kernel)
+    rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
+                                       want_p=True)
+    assert int(st.abs().sum()) == 0
+    assert _rel(qf.cpu().numpy(), rf) < RTOL_MIXED
+    assert _rel(qc.cpu().numpy(), rc) < RTOL_MIXED
+    np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=1e-8)
+
+
+def test_mixed_on_kl_fields_and_by_product(fm, small):
+    """Mixed form on KL fields: Q^c of level l equals the mixed Q^f of level l-1
+    (both refined to the same tolerance), and both match the FP64 converged form."""
+    ctx, _ = small
+    xi = torch.tensor(W.normals(200, 24, tag=110), device="cuda")
+    res = {}
+    for level in range(3):
+        K = ctx.kl_field_batch(level, xi)
+        res[level] = ctx.fmg_solve_batch(K, precision=fm.FM_PREC_MIXED, converged=1, tol=1e-11,
+                                         max_cycles=200)
+        ref = ctx.fmg_solve_batch(K, converged=1, tol=1e-12, max_cycles=200)
+        assert _rel(res[level][0].cpu().numpy(), ref[0].cpu().numpy()) < RTOL_MIXED
+    for level in (1, 2):
+        assert _rel(res[level][1].cpu().numpy(), res[level - 1][0].cpu().numpy()) < RTOL_MIXED
+
+
+@pytest.mark.parametrize("kernel", [LEVELWISE, RESIDENT])
+def test_converged_reports_non_convergence(fm, small, kernel):
+    ctx, _ = small
+    K = torch.tensor(W.smooth_lognormal_field(32, S=8, tag=120), device="cuda")
+    _, _, _, st = ctx.fmg_solve_batch(K, want_status=True, converged=1, tol=1e-15, max_cycles=1,
+                                      kernel=kernel)
+    assert np.all(st.cpu().numpy() == 4)   # FM_ENOTCONV
+    with pytest.raises(fm.FmError, match="converged"):
+        ctx.fmg_solve_batch(K, precision=fm.FM_PREC_MIXED, converged=0)
+
+
+# ------------------------------------------------------------------ tensor-core KL synthesis
+# Stated field error bounds (relative error of K = exp(g), i.e. |dg|):
+#   BF16X3 (hi*hi + hi*lo + lo*hi, FP32 accumulation): <= 5e-5
+#   BF16 (plain):                                      <= 4e-2
+KL_TOL = {3: 5e-5, 2: 4e-2}
+
+
+@pytest.mark.parametrize("kl_mode", [3, 2])
+def test_tensor_core_kl_field_error(fm, kl_mode):
+    basis = okl.KLBasis(32, 24, 1.0, 0.3, q=24)
+    ctx = fm.Context(3, 8, 24, sigma2=1.0, lam=0.3, seed=5, kl_mode=kl_mode)
+    ctx.kl_basis_set(basis.B_ref)
+    for level, n, S in [(0, 8, 300), (1, 16, 257), (2, 32, 513)]:
+        xi = W.normals(S, 24, tag=130 + level)
+        K = ctx.kl_field_batch(level, torch.tensor(xi, device="cuda"))
+        ctx.sync()
+        ref = okl.synthesize(basis.level_basis(n), xi).reshape(-1, n, n)
+        err = _rel(K.cpu().numpy(), ref)
+        print("kl_mode %d level %d: max relative field error %.3e" % (kl_mode, level, err))
+        assert err < KL_TOL[kl_mode]
+
+
+def test_tensor_core_kl_128_modes_full_level(fm):
+    """The five-level workload's 128-mode basis on its 256 x 256 level."""
+    wl = W.WORKLOADS["fmg_mlmc5"]
+    basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32)
+    ctx = fm.Context(len(wl.levels), wl.levels[0], wl.M, kl_mode=3)
+    ctx.kl_basis_set(basis.B_ref)
+    xi = W.normals(300, wl.M, tag=140)
+    for level in (0, 4):
+        n = wl.levels[level]
+        K = ctx.kl_field_batch(level, torch.tensor(xi, device="cuda"))
+        ctx.sync()
+        ref = okl.synthesize(basis.level_basis(n), xi).reshape(-1, n, n)
+        assert _rel(K.cpu().numpy(), ref) < KL_TOL[3]
+
+
+def test_tensor_core_fields_are_nested_across_levels(fm):
+    """Coarse rows of the same coefficients give bitwise the same field values
+    (the injected fine field equals the coarse level's field)."""
+    basis = okl.KLBasis(32, 24, 1.0, 0.3, q=24)
+    ctx = fm.Context(3, 8, 24, kl_mode=3)
+    ctx.kl_basis_set(basis.B_ref)
+    xi = torch.tensor(W.normals(260, 24, tag=150), device="cuda")
+    K2 = ctx.kl_field_batch(2, xi)
+    K1 = ctx.kl_field_batch(1, xi)
+    ctx.sync()
+    assert torch.equal(K2[:, ::2, ::2], K1)
