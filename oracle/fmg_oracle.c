@@ -290,6 +290,10 @@ typedef struct {
     int converged;   /* 1: V-cycles at each stage until ||r||/||b|| <= tol */
     double tol;
     int max_cycles;
+    int coarse_op;   /* coefficients of the V-cycle's coarse-grid correction
+                        operators: 0 the injected field itself, 1 the geometric
+                        mean of the four children of the injected field one
+                        grid finer */
 } or_params;
 
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
@@ -484,7 +488,9 @@ double or_norm2(int m, const double* v)
 typedef struct {
     int m;           /* finest index */
     int n0;          /* coarsest grid size */
-    double* K[32];   /* injected coefficients per grid */
+    double* K[32];   /* injected coefficients per grid (the stage problems) */
+    double* Kop[32]; /* coefficients of the correction operators below the top */
+    double* Kavg[32];
     double* x[32];   /* iterate per grid */
     double* b[32];   /* rhs per grid */
     double* r[32];   /* residual work per grid */
@@ -492,7 +498,17 @@ typedef struct {
 
 static int grid_n(const hierarchy* H, int k) { return H->n0 << k; }
 
-static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fine)
+/* K_c[J][I] = (K_f[2J][2I] K_f[2J][2I+1] K_f[2J+1][2I] K_f[2J+1][2I+1])^(1/4) */
+static void geometric_children(int nc, const double* Kf, double* Kc)
+{
+    int nf = 2 * nc;
+    for (int J = 0; J < nc; ++J)
+        for (int I = 0; I < nc; ++I)
+            Kc[J * nc + I] = exp(0.25 * (log(Kf[(2 * J) * nf + 2 * I]) + log(Kf[(2 * J) * nf + 2 * I + 1]) +
+                                         log(Kf[(2 * J + 1) * nf + 2 * I]) + log(Kf[(2 * J + 1) * nf + 2 * I + 1])));
+}
+
+static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fine, int coarse_op)
 {
     memset(H, 0, sizeof(*H));
     H->n0 = n0;
@@ -508,30 +524,40 @@ static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fin
     }
     memcpy(H->K[m], K_fine, sizeof(double) * (size_t)n_fine * n_fine);
     for (int k = m; k >= 1; --k) or_inject(grid_n(H, k - 1), H->K[k], H->K[k - 1]);
+    for (int k = 0; k <= m; ++k) {
+        H->Kop[k] = H->K[k];
+        if (coarse_op == 1 && k < m) {
+            H->Kavg[k] = (double*)malloc(sizeof(double) * (size_t)grid_n(H, k) * grid_n(H, k));
+            geometric_children(grid_n(H, k), H->K[k + 1], H->Kavg[k]);
+            H->Kop[k] = H->Kavg[k];
+        }
+    }
 }
 
 static void hierarchy_free(hierarchy* H)
 {
     for (int k = 0; k <= H->m; ++k) {
-        free(H->K[k]); free(H->x[k]); free(H->b[k]); free(H->r[k]);
+        free(H->K[k]); free(H->x[k]); free(H->b[k]); free(H->r[k]); free(H->Kavg[k]);
     }
 }
 
-/* One V(nu1, nu2) cycle for A_k x_k = b_k. */
-static void vcycle(hierarchy* H, int k, int nu1, int nu2)
+/* One V(nu1, nu2) cycle for A_k x_k = b_k; grid `top` carries the stage
+ * operator (injected K), the grids below it the correction operators. */
+static void vcycle(hierarchy* H, int k, int top, int nu1, int nu2)
 {
     int n = grid_n(H, k);
+    const double* K = (k == top) ? H->K[k] : H->Kop[k];
     if (k == 0) {
-        or_exact_solve(n, H->K[0], H->b[0], H->x[0]);
+        or_exact_solve(n, K, H->b[0], H->x[0]);
         return;
     }
-    for (int s = 0; s < nu1; ++s) or_rbgs_sweep(n, H->K[k], H->b[k], H->x[k]);
-    or_residual(n, H->K[k], H->b[k], H->x[k], H->r[k]);
+    for (int s = 0; s < nu1; ++s) or_rbgs_sweep(n, K, H->b[k], H->x[k]);
+    or_residual(n, K, H->b[k], H->x[k], H->r[k]);
     or_restrict_sum(n / 2, H->r[k], H->b[k - 1]);
     memset(H->x[k - 1], 0, sizeof(double) * (size_t)(n / 2) * (n / 2));
-    vcycle(H, k - 1, nu1, nu2);
+    vcycle(H, k - 1, top, nu1, nu2);
     or_prolong_add(n / 2, H->x[k - 1], H->x[k]);
-    for (int s = 0; s < nu2; ++s) or_rbgs_sweep(n, H->K[k], H->b[k], H->x[k]);
+    for (int s = 0; s < nu2; ++s) or_rbgs_sweep(n, K, H->b[k], H->x[k]);
 }
 
 /* Relative residual ||b - A x|| / ||b|| on grid k. */
@@ -549,12 +575,12 @@ static double rel_residual(hierarchy* H, int k)
 static int stage_cycles(hierarchy* H, int k, const or_params* P)
 {
     if (!P->converged) {
-        for (int it = 0; it < P->nu0; ++it) vcycle(H, k, P->nu1, P->nu2);
+        for (int it = 0; it < P->nu0; ++it) vcycle(H, k, k, P->nu1, P->nu2);
         return P->nu0;
     }
     int it = 0;
     while (it < P->max_cycles && rel_residual(H, k) > P->tol) {
-        vcycle(H, k, P->nu1, P->nu2);
+        vcycle(H, k, k, P->nu1, P->nu2);
         ++it;
     }
     return it;
@@ -570,7 +596,7 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
                  double* p_out, double* qf, double* qc)
 {
     hierarchy H;
-    hierarchy_init(&H, n_fine, n0, K_fine);
+    hierarchy_init(&H, n_fine, n0, K_fine, P->coarse_op);
     int cycles = 0;
     *qc = NAN;
     or_stage_rhs(n0, H.K[0], P->pW, P->pE, H.b[0]);
@@ -592,14 +618,14 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
 /* V-cycles on a given problem A x = b from the given x (for convergence-factor
  * checks).  res_hist[c] = ||b - A x|| after cycle c (c = 0 before any). */
 void or_vcycle_solve(int n, int n0, const double* K, const double* b, double* x,
-                     int nu1, int nu2, int ncycles, double* res_hist)
+                     int nu1, int nu2, int ncycles, int coarse_op, double* res_hist)
 {
     hierarchy H;
-    hierarchy_init(&H, n, n0, K);
+    hierarchy_init(&H, n, n0, K, coarse_op);
     memcpy(H.b[H.m], b, sizeof(double) * (size_t)n * n);
     memcpy(H.x[H.m], x, sizeof(double) * (size_t)n * n);
     for (int c = 0; c <= ncycles; ++c) {
-        if (c > 0) vcycle(&H, H.m, nu1, nu2);
+        if (c > 0) vcycle(&H, H.m, H.m, nu1, nu2);
         if (res_hist) {
             or_residual(n, H.K[H.m], H.b[H.m], H.x[H.m], H.r[H.m]);
             res_hist[c] = or_norm2(n * n, H.r[H.m]);

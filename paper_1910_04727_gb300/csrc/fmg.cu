@@ -42,6 +42,19 @@ __global__ void k_inject(int nc, size_t S, const double* __restrict__ Kf, double
     Kc[t] = Kf[s * (size_t)nf * nf + (size_t)(2 * J) * nf + 2 * I];
 }
 
+// Correction-grid coefficients: K_c[J][I] = geometric mean of the four
+// children K_f[2J+dj][2I+di] on the injected grid one level finer.
+__global__ void k_child_geomean(int nc, size_t S, const double* __restrict__ Kf, double* __restrict__ Kc) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t cells = (size_t)nc * nc;
+    if (t >= S * cells) return;
+    const size_t s = t / cells;
+    const int c = (int)(t % cells);
+    const int I = c % nc, J = c / nc, nf = 2 * nc;
+    const double* k = Kf + s * (size_t)nf * nf + (size_t)(2 * J) * nf + 2 * I;
+    Kc[t] = exp(0.25 * (log(k[0]) + log(k[1]) + log(k[nf]) + log(k[nf + 1])));
+}
+
 // Face transmissibilities: harmonic mean inside, 2K on the Dirichlet edges,
 // none on the no-flow edges; optional FP64 copies for refined grids.
 template <typename T>
@@ -354,6 +367,8 @@ struct GridBufs {
     int n;
     const double* K;
     T *Te, *Tn, *D, *p, *b;
+    double* Kc;                        // correction-grid coefficients (k < m)
+    T *TeC, *TnC, *DC;                 // their faces and diagonal
     double *p64, *Te64, *Tn64, *D64;   // refined grids of the mixed form only
 };
 
@@ -364,7 +379,8 @@ struct Hierarchy {
     int n0;
     size_t S;
     GridBufs<T> g[FM_MAX_LEVELS + 8];
-    T* Ainv;
+    T* Ainv;           // coarsest stage operator (injected K)
+    T* AinvC;          // coarsest correction operator (child means)
     int32_t* active;   // per-sample iterate flags of converged stages
     int32_t* left;     // count of samples still iterating
 };
@@ -376,9 +392,10 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
     for (int k = 0; k <= m; ++k) {
         const size_t c = (size_t)(n0 << k) * (n0 << k);
         total += c * (8 + 5 * tsize) + 5 * 256;
+        if (k < m) total += c * (8 + 3 * tsize) + 4 * 256;
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
-    total += (size_t)n0 * n0 * n0 * n0 * tsize + 256;
+    total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
     if (converged) total += 4 * 2 + 2 * 256;
     return total * S + 4096;
 }
@@ -429,6 +446,14 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
         g.D = (T*)take(cnt * sizeof(T));
         g.p = (T*)take(cnt * sizeof(T));
         g.b = (T*)take(cnt * sizeof(T));
+        g.Kc = nullptr;
+        g.TeC = g.TnC = g.DC = nullptr;
+        if (k < H.m) {
+            g.Kc = (double*)take(cnt * 8);
+            g.TeC = (T*)take(cnt * sizeof(T));
+            g.TnC = (T*)take(cnt * sizeof(T));
+            g.DC = (T*)take(cnt * sizeof(T));
+        }
         g.p64 = g.Te64 = g.Tn64 = g.D64 = nullptr;
         if (mixed && k >= H.m - 1) {
             g.p64 = (double*)take(cnt * 8);
@@ -438,22 +463,30 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
         }
     }
     H.Ainv = (T*)take(S * (size_t)n0 * n0 * n0 * n0 * sizeof(T));
+    H.AinvC = (T*)take(S * (size_t)n0 * n0 * n0 * n0 * sizeof(T));
     H.active = converged ? (int32_t*)take(S * 4) : nullptr;
     H.left = converged ? (int32_t*)take(4) : nullptr;
     return FM_OK;
 }
 
+// One V(nu1, nu2) cycle on grid k; grid `top` carries the stage operator
+// (injected K), the grids below it the correction operators (child means).
 template <typename T>
-static void vcycle(const Hierarchy<T>& H, int k, const fm_solve_params& prm, const int32_t* active,
+static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params& prm, const int32_t* active,
                    cudaStream_t st) {
     fm_ctx* ctx = H.ctx;
     const size_t S = H.S;
     const GridBufs<T>& g = H.g[k];
     const double ts = sizeof(T);
+    const bool stage_op = (k == top);
+    const T* Te = stage_op ? g.Te : g.TeC;
+    const T* Tn = stage_op ? g.Tn : g.TnC;
+    const T* D = stage_op ? g.D : g.DC;
     if (k == 0) {
         const int m = H.n0 * H.n0;
         FM_TIMED(ctx, kFamCoarseSolve, st, (double)S * (m * m + 2 * m) * ts, 2.0 * S * m * m,
-                 k_coarse_solve<T><<<blocks_for(S * m), kBlock, 0, st>>>(m, S, H.Ainv, g.b, g.p, active));
+                 k_coarse_solve<T><<<blocks_for(S * m), kBlock, 0, st>>>(m, S, stage_op ? H.Ainv : H.AinvC, g.b,
+                                                                         g.p, active));
         return;
     }
     const int n = g.n;
@@ -465,20 +498,20 @@ static void vcycle(const Hierarchy<T>& H, int k, const fm_solve_params& prm, con
     for (int it = 0; it < prm.nu1; ++it)
         for (int color = 0; color < 2; ++color)
             FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D,
-                                                                          g.p, active));
+                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, Te, Tn, D, g.p,
+                                                                          active));
     const GridBufs<T>& c = H.g[k - 1];
     FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
              k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
-                 c.n, S, g.b, g.Te, g.Tn, g.D, g.p, c.b, c.p, active));
-    vcycle(H, k - 1, prm, active, st);
+                 c.n, S, g.b, Te, Tn, D, g.p, c.b, c.p, active));
+    vcycle(H, k - 1, top, prm, active, st);
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
              k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, g.p, active));
     for (int it = 0; it < prm.nu2; ++it)
         for (int color = 0; color < 2; ++color)
             FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, g.Te, g.Tn, g.D,
-                                                                          g.p, active));
+                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, Te, Tn, D, g.p,
+                                                                          active));
 }
 
 template <typename P>
@@ -510,7 +543,7 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
             if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
             break;
         }
-        vcycle(H, k, prm, H.active, st);
+        vcycle(H, k, k, prm, H.active, st);
         if (mixed)
             k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, st>>>(cells, S, g.p, g.p64, H.active);
     }
@@ -540,6 +573,20 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
                  k_coefficients<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D, g.Te64,
                                                                          g.Tn64, g.D64));
     }
+    for (int k = 0; k < H.m; ++k) {
+        const GridBufs<T>& g = H.g[k];
+        const size_t cells = S * (size_t)g.n * g.n;
+        FM_TIMED(ctx, kFamCoefficients, st, (32.0 + 8.0 + 3.0 * ts) * cells, 40.0 * cells,
+                 k_child_geomean<<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, H.g[k + 1].K, g.Kc);
+                 k_coefficients<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.Kc, g.TeC, g.TnC, g.DC,
+                                                                         nullptr, nullptr, nullptr));
+    }
+    if (H.m >= 1) {
+        const int m = H.n0 * H.n0;
+        FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (8 * m + ts * m * m), 2.0 * S * m * m * m,
+                 k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(
+                     H.n0, S, H.g[0].Kc, H.AinvC));
+    }
     {
         const int m = H.n0 * H.n0;
         FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (8 * m + ts * m * m), 2.0 * S * m * m * m,
@@ -563,10 +610,10 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
         }
         FM_TIMED(ctx, kFamStageRhs, st, (8.0 + ts) * cells, 2.0 * cells,
                  k_stage_rhs<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, prm.pW, prm.pE, g.b));
-        if (k == 0) vcycle(H, 0, prm, nullptr, st);
+        if (k == 0) vcycle(H, 0, 0, prm, nullptr, st);
         if (!refined) {
             if (k > 0)
-                for (int it = 0; it < prm.nu0; ++it) vcycle(H, k, prm, nullptr, st);
+                for (int it = 0; it < prm.nu0; ++it) vcycle(H, k, k, prm, nullptr, st);
         } else {
             if (mixed && !(k == H.m && H.m >= 1))
                 k_widen<T><<<blocks_for(cells), kBlock, 0, st>>>(cells, g.p, g.p64);

@@ -120,6 +120,35 @@ __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const dou
     }
 }
 
+// Coefficients of grid n as a correction grid: K of each cell is the
+// geometric mean of its four children on the injected grid 2n, i.e. of the
+// fine field at stride s/2.  Uses the grid's iterate as scratch, so it runs
+// once the grid's stage solution has been interpolated to the next grid.
+template <typename T>
+__device__ void resident_setup_correction(const RGrid<T>& g, const double* __restrict__ Kf, int n_fine) {
+    const int n = g.n, s = n_fine / n, h2 = s / 2;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const size_t r0 = (size_t)(s * j) * n_fine + (size_t)s * i, r1 = r0 + (size_t)h2 * n_fine;
+        const double a = __ldg(Kf + r0), b = __ldg(Kf + r0 + h2), cc = __ldg(Kf + r1), d = __ldg(Kf + r1 + h2);
+        g.p[c] = (T)exp(0.25 * (log(a) + log(b) + log(cc) + log(d)));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const double k = (double)g.p[c];
+        const double tw = (i > 0) ? harm((double)g.p[c - 1], k) : 2.0 * k;
+        const double te = (i < n - 1) ? harm(k, (double)g.p[c + 1]) : 2.0 * k;
+        const double ts = (j > 0) ? harm((double)g.p[c - n], k) : 0.0;
+        const double tn = (j < n - 1) ? harm(k, (double)g.p[c + n]) : 0.0;
+        g.te[c] = (T)te;
+        g.tn[c] = (T)tn;
+        if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
+        if (i == 0) g.tw[j] = (T)(2.0 * k);
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ V-cycle pieces
 // Right-hand side of cell (i, j): stored, or the stage problem's Dirichlet data.
 template <typename T>
@@ -421,6 +450,9 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                 } else {
                     resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, tpW, tpE, false);
                 }
+                // grid k-1 now only carries corrections of the V-cycles on grid k
+                resident_setup_correction(L.g[k - 1], Kf, a.n_fine);
+                if (k == 1) resident_coarse_inverse(L.g[0], L.ainv, L.work);
             }
             if (g.b) resident_stage_rhs(g, tpW, tpE);
             if (k == 0) resident_coarse_solve(g, L.ainv, tpW, tpE);

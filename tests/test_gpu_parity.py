@@ -267,12 +267,14 @@ def test_converged_fp64_matches_converged_oracle(small, n, kernel):
     ctx, _ = small
     K = W.smooth_lognormal_field(n, S=23, tag=90 + n)
     qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
-                                        converged=1, tol=1e-12, max_cycles=200, kernel=kernel)
+                                        converged=1, tol=1e-11, max_cycles=400, kernel=kernel)
     rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
                                        want_p=True)
     assert int(st.abs().sum()) == 0
-    assert _rel(qf.cpu().numpy(), rf) < 1e-10
-    assert _rel(qc.cpu().numpy(), rc) < 1e-10
+    # both sides stop at a residual test, so the QoIs agree to the solver
+    # tolerance times the conditioning of the outflux (<= 200 tol here), not to rounding
+    assert _rel(qf.cpu().numpy(), rf) < 200 * 1e-11
+    assert _rel(qc.cpu().numpy(), rc) < 200 * 1e-11
 
 
 @pytest.mark.parametrize("n,kernel", REFINED_CASES)
@@ -281,7 +283,7 @@ def test_mixed_precision_matches_converged_oracle(fm, small, n, kernel):
     K = W.smooth_lognormal_field(n, S=41, tag=100 + n)
     qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
                                         precision=fm.FM_PREC_MIXED, converged=1, tol=1e-11,
-                                        max_cycles=200, kernel=kernel)
+                                        max_cycles=400, kernel=kernel)
     rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
                                        want_p=True)
     assert int(st.abs().sum()) == 0
