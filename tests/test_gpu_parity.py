@@ -267,14 +267,16 @@ def test_converged_fp64_matches_converged_oracle(small, n, kernel):
     ctx, _ = small
     K = W.smooth_lognormal_field(n, S=23, tag=90 + n)
     qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
-                                        converged=1, tol=1e-11, max_cycles=400, kernel=kernel)
+                                        converged=1, tol=1e-12, max_cycles=400, kernel=kernel)
     rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
                                        want_p=True)
     assert int(st.abs().sum()) == 0
     # both sides stop at a residual test, so the QoIs agree to the solver
-    # tolerance times the conditioning of the outflux (<= 200 tol here), not to rounding
-    assert _rel(qf.cpu().numpy(), rf) < 200 * 1e-11
-    assert _rel(qc.cpu().numpy(), rc) < 200 * 1e-11
+    # tolerance times the conditioning of the outflux, not to rounding; the
+    # residual is relative to ||b||, which lives on the boundary column only,
+    # so the bound grows with n: |dQ|/Q <= 10 n tol
+    assert _rel(qf.cpu().numpy(), rf) < 10 * n * 1e-12
+    assert _rel(qc.cpu().numpy(), rc) < 10 * n * 1e-12
 
 
 @pytest.mark.parametrize("n,kernel", REFINED_CASES)
@@ -282,7 +284,7 @@ def test_mixed_precision_matches_converged_oracle(fm, small, n, kernel):
     ctx, _ = small
     K = W.smooth_lognormal_field(n, S=41, tag=100 + n)
     qf, qc, p, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, want_status=True,
-                                        precision=fm.FM_PREC_MIXED, converged=1, tol=1e-11,
+                                        precision=fm.FM_PREC_MIXED, converged=1, tol=1e-12,
                                         max_cycles=400, kernel=kernel)
     rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300),
                                        want_p=True)
@@ -300,9 +302,9 @@ def test_mixed_on_kl_fields_and_by_product(fm, small):
     res = {}
     for level in range(3):
         K = ctx.kl_field_batch(level, xi)
-        res[level] = ctx.fmg_solve_batch(K, precision=fm.FM_PREC_MIXED, converged=1, tol=1e-11,
-                                         max_cycles=200)
-        ref = ctx.fmg_solve_batch(K, converged=1, tol=1e-12, max_cycles=200)
+        res[level] = ctx.fmg_solve_batch(K, precision=fm.FM_PREC_MIXED, converged=1, tol=1e-12,
+                                         max_cycles=400)
+        ref = ctx.fmg_solve_batch(K, converged=1, tol=1e-12, max_cycles=400)
         assert _rel(res[level][0].cpu().numpy(), ref[0].cpu().numpy()) < RTOL_MIXED
     for level in (1, 2):
         assert _rel(res[level][1].cpu().numpy(), res[level - 1][0].cpu().numpy()) < RTOL_MIXED
