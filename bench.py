@@ -165,7 +165,7 @@ def make_ctx(fm, wl, rank, form):
     return fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
                       pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
                       n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank, precision=f["precision"],
-                      converged=f["converged"], tol=1e-10, max_cycles=200)
+                      converged=f["converged"], tol=1e-10, qtol=1e-9, max_cycles=200)
 
 
 def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=False, clocks=None,
@@ -297,7 +297,7 @@ def run_native(args, wl, eps):
         "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
                    "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
                    "fmg": "4x4 exact, nu0=%d V(%d,%d) RB-GS" % (wl.nu0, wl.nu1, wl.nu2),
-                   "form": args.form, "tol": 1e-10, "l2": "flushed between steps (512 MiB write)",
+                   "form": args.form, "tol": 1e-10, "qtol": 1e-9, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "captured_variance": captured},
         "estimate": float(np.mean(ests)),

@@ -86,6 +86,8 @@ typedef struct {
     int32_t converged;    /* 0: nu0 V-cycles per stage; 1: the stages giving Q^c and Q^f
                              iterate until ||b - A p||_2 <= tol ||b||_2 */
     double tol;           /* relative residual target of converged stages */
+    double qtol;          /* converged stages also stop once an iteration changes the
+                             stage's outflux by <= qtol |Q| (0: residual test only) */
     int32_t max_cycles;   /* cycle cap of a converged stage */
     int32_t kl_mode;      /* FM_KL_*: arithmetic of the field synthesis */
     int32_t n_shifts;     /* QMC digital shifts R */
@@ -111,6 +113,7 @@ typedef struct {
                              cycles is its "exact" solution); 1: stages n_fine/2 and
                              n_fine iterate to ||b - A p||_2 <= tol ||b||_2 */
     double tol;
+    double qtol;          /* also stop once a cycle changes the outflux by <= qtol |Q| */
     int32_t max_cycles;   /* cap per converged stage; a sample that reaches it gets
                              status FM_ENOTCONV */
 } fm_solve_params;

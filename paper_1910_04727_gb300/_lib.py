@@ -30,7 +30,8 @@ class FmConfig(C.Structure):
                 ("M", C.c_int32), ("sigma2", C.c_double), ("lambda_", C.c_double),
                 ("pW", C.c_double), ("pE", C.c_double), ("nu0", C.c_int32), ("nu1", C.c_int32),
                 ("nu2", C.c_int32), ("precision", C.c_int32), ("converged", C.c_int32),
-                ("tol", C.c_double), ("max_cycles", C.c_int32), ("kl_mode", C.c_int32),
+                ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
+                ("kl_mode", C.c_int32),
                 ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64)]
 
 
@@ -38,7 +39,7 @@ class FmSolveParams(C.Structure):
     _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("n_coarsest", C.c_int32),
                 ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("converged", C.c_int32),
-                ("tol", C.c_double), ("max_cycles", C.c_int32)]
+                ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32)]
 
 
 class FmLevelSums(C.Structure):

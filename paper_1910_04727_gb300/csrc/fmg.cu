@@ -291,15 +291,17 @@ __global__ void k_stage_check(int n, size_t S, const double* __restrict__ K, dou
                               const T* __restrict__ D, const T* __restrict__ p, const double* __restrict__ p64,
                               const double* __restrict__ Te64, const double* __restrict__ Tn64,
                               const double* __restrict__ D64, T* __restrict__ bT, T* __restrict__ pT,
-                              double tol, int32_t* __restrict__ active, int32_t* __restrict__ left) {
-    __shared__ double red[2][32];
+                              double tol, double qtol, double* __restrict__ qprev,
+                              int32_t* __restrict__ active, int32_t* __restrict__ left) {
+    __shared__ double red[3][32];
     const size_t s = blockIdx.x;
     if (s >= S || inactive(active, s)) return;
     const size_t base = s * (size_t)n * n;
-    double rr = 0.0, bb = 0.0;
+    double rr = 0.0, bb = 0.0, qq = 0.0;
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int i = c % n, j = c / n;
         const size_t g = base + c;
+        if (i == n - 1) qq += 2.0 * K[g] * ((p64 ? p64[g] : (double)p[g]) - pE);
         double f = 0.0;
         if (i == 0) f += 2.0 * K[g] * pW;
         if (i == n - 1) f += 2.0 * K[g] * pE;
@@ -323,19 +325,24 @@ __global__ void k_stage_check(int n, size_t S, const double* __restrict__ K, dou
     for (int off = 16; off > 0; off >>= 1) {
         rr += __shfl_down_sync(0xffffffffu, rr, off);
         bb += __shfl_down_sync(0xffffffffu, bb, off);
+        qq += __shfl_down_sync(0xffffffffu, qq, off);
     }
     if ((threadIdx.x & 31) == 0) {
         red[0][threadIdx.x >> 5] = rr;
         red[1][threadIdx.x >> 5] = bb;
+        red[2][threadIdx.x >> 5] = qq;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b2 = 0.0;
+        double a = 0.0, b2 = 0.0, q = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             a += red[0][w];
             b2 += red[1][w];
+            q += red[2][w];
         }
-        const bool done = a <= tol * tol * b2;
+        // residual test, or an iteration that moved the outflux by <= qtol |Q|
+        const bool done = a <= tol * tol * b2 || (qtol > 0 && fabs(q - qprev[s]) <= qtol * fabs(q));
+        qprev[s] = q;
         active[s] = done ? 0 : 1;
         if (!done) atomicAdd(left, 1);
     }
@@ -383,6 +390,7 @@ struct Hierarchy {
     T* AinvC;          // coarsest correction operator (child means)
     int32_t* active;   // per-sample iterate flags of converged stages
     int32_t* left;     // count of samples still iterating
+    double* qprev;     // outflux of the previous iteration per sample
 };
 
 static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool mixed, bool converged) {
@@ -396,7 +404,7 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
     total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
-    if (converged) total += 4 * 2 + 2 * 256;
+    if (converged) total += 4 * 2 + 8 + 3 * 256;
     return total * S + 4096;
 }
 
@@ -466,6 +474,7 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
     H.AinvC = (T*)take(S * (size_t)n0 * n0 * n0 * n0 * sizeof(T));
     H.active = converged ? (int32_t*)take(S * 4) : nullptr;
     H.left = converged ? (int32_t*)take(4) : nullptr;
+    H.qprev = converged ? (double*)take(S * 8) : nullptr;
     return FM_OK;
 }
 
@@ -529,13 +538,14 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
     const GridBufs<T>& g = H.g[k];
     const size_t S = H.S, cells = (size_t)g.n * g.n;
     FM_CUDA_TRY(ctx, cudaMemsetAsync(H.active, 0xff, S * sizeof(int32_t), st));   // all active (-1)
+    FM_CUDA_TRY(ctx, cudaMemsetAsync(H.qprev, 0xff, S * sizeof(double), st));     // NaN
     int32_t left = 0;
     for (int it = 0;; ++it) {
         FM_CUDA_TRY(ctx, cudaMemsetAsync(H.left, 0, sizeof(int32_t), st));
         FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * S * cells, 12.0 * S * cells,
                  k_stage_check<T><<<(unsigned)S, kBlock, 0, st>>>(
                      g.n, S, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64,
-                     g.b, g.p, prm.tol, H.active, H.left));
+                     g.b, g.p, prm.tol, prm.qtol, H.qprev, H.active, H.left));
         FM_CUDA_TRY(ctx, cudaMemcpyAsync(&left, H.left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
         if (left == 0) break;

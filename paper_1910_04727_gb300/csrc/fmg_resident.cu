@@ -91,7 +91,10 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
     return L;
 }
 
-__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+template <typename C>
+__device__ __forceinline__ C harm(C a, C b) {
+    return C(2) * a * b / (a + b);
+}
 
 // ------------------------------------------------------------------ setup
 // Face transmissibilities of grid n, K injected from the fine field at
@@ -99,23 +102,37 @@ __device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b 
 template <typename T>
 __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const double* __restrict__ Kf,
                                     int n_fine) {
+    // FP64 faces where an FP64 copy is kept (or T is FP64); otherwise the
+    // FP32 correction-solver coefficients are formed in FP32
     const int n = g.n, s = n_fine / n;
     auto K = [&](int i, int j) { return __ldg(Kf + (size_t)(s * j) * n_fine + (size_t)s * i); };
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int i = c % n, j = c / n;
-        const double k = K(i, j);
-        const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
-        const double te = (i < n - 1) ? harm(k, K(i + 1, j)) : 2.0 * k;
-        const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
-        const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : 0.0;
-        g.te[c] = (T)te;
-        g.tn[c] = (T)tn;
-        if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
-        if (i == 0) g.tw[j] = (T)(2.0 * k);
-        if (h) {
-            h->te[c] = te;
-            h->tn[c] = tn;
-            if (i == 0) h->tw[j] = 2.0 * k;
+        if (h || sizeof(T) == 8) {
+            const double k = K(i, j);
+            const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
+            const double te = (i < n - 1) ? harm(k, K(i + 1, j)) : 2.0 * k;
+            const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
+            const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : 0.0;
+            g.te[c] = (T)te;
+            g.tn[c] = (T)tn;
+            if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
+            if (i == 0) g.tw[j] = (T)(2.0 * k);
+            if (h) {
+                h->te[c] = te;
+                h->tn[c] = tn;
+                if (i == 0) h->tw[j] = 2.0 * k;
+            }
+        } else {
+            const T k = (T)K(i, j);
+            const T tw = (i > 0) ? harm((T)K(i - 1, j), k) : T(2) * k;
+            const T te = (i < n - 1) ? harm(k, (T)K(i + 1, j)) : T(2) * k;
+            const T ts = (j > 0) ? harm((T)K(i, j - 1), k) : T(0);
+            const T tn = (j < n - 1) ? harm(k, (T)K(i, j + 1)) : T(0);
+            g.te[c] = te;
+            g.tn[c] = tn;
+            if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
+            if (i == 0) g.tw[j] = T(2) * k;
         }
     }
 }
@@ -131,20 +148,23 @@ __device__ void resident_setup_correction(const RGrid<T>& g, const double* __res
         const int i = c % n, j = c / n;
         const size_t r0 = (size_t)(s * j) * n_fine + (size_t)s * i, r1 = r0 + (size_t)h2 * n_fine;
         const double a = __ldg(Kf + r0), b = __ldg(Kf + r0 + h2), cc = __ldg(Kf + r1), d = __ldg(Kf + r1 + h2);
-        g.p[c] = (T)exp(0.25 * (log(a) + log(b) + log(cc) + log(d)));
+        if (sizeof(T) == 8)
+            g.p[c] = (T)exp(0.25 * (log(a) + log(b) + log(cc) + log(d)));
+        else   // FP32 correction coefficients of the mixed form
+            g.p[c] = (T)expf(0.25f * (logf((float)a) + logf((float)b) + logf((float)cc) + logf((float)d)));
     }
     __syncthreads();
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int i = c % n, j = c / n;
-        const double k = (double)g.p[c];
-        const double tw = (i > 0) ? harm((double)g.p[c - 1], k) : 2.0 * k;
-        const double te = (i < n - 1) ? harm(k, (double)g.p[c + 1]) : 2.0 * k;
-        const double ts = (j > 0) ? harm((double)g.p[c - n], k) : 0.0;
-        const double tn = (j < n - 1) ? harm(k, (double)g.p[c + n]) : 0.0;
-        g.te[c] = (T)te;
-        g.tn[c] = (T)tn;
-        if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
-        if (i == 0) g.tw[j] = (T)(2.0 * k);
+        const T k = g.p[c];
+        const T tw = (i > 0) ? harm(g.p[c - 1], k) : T(2) * k;
+        const T te = (i < n - 1) ? harm(k, g.p[c + 1]) : T(2) * k;
+        const T ts = (j > 0) ? harm(g.p[c - n], k) : T(0);
+        const T tn = (j < n - 1) ? harm(k, g.p[c + n]) : T(0);
+        g.te[c] = te;
+        g.tn[c] = tn;
+        if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
+        if (i == 0) g.tw[j] = T(2) * k;
     }
     __syncthreads();
 }
@@ -410,6 +430,17 @@ __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, dou
     return acc;
 }
 
+// Outflux broadcast to every thread of the CTA.
+template <typename P, typename Q>
+__device__ __forceinline__ double stage_outflux(const P* te, const Q* p, int n, double pE, double* red) {
+    const double q = outflux_of(te, p, n, pE);
+    if (threadIdx.x == 0) red[70] = q;
+    __syncthreads();
+    const double out = red[70];
+    __syncthreads();
+    return out;
+}
+
 struct ResidentArgs {
     int n_fine, n0;
     size_t S;
@@ -417,7 +448,7 @@ struct ResidentArgs {
     double pW, pE;
     int nu0, nu1, nu2;
     int converged, max_cycles;
-    double tol;
+    double tol, qtol;
     double *qf, *qc, *p_out;
     int32_t* status;
 };
@@ -460,11 +491,16 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                 if (k > 0)
                     for (int it = 0; it < a.nu0; ++it) resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
             } else if (!MIXED) {
-                // FP64: V-cycles on the stage problem until the residual test passes
+                // FP64: V-cycles on the stage problem until the residual or
+                // outflux-change test passes
+                double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
                     stage_norms(g, tpW, tpE, L.red, rr, bb);
+                    const double q = stage_outflux(g.te, g.p, g.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
+                    if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
+                    q_prev = q;
                     if (it >= a.max_cycles) {
                         ok = false;
                         break;
@@ -478,10 +514,14 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                     for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] = (double)g.p[c];
                     __syncthreads();
                 }
+                double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
                     ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
+                    const double q = stage_outflux(h.te, h.p, h.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
+                    if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
+                    q_prev = q;
                     if (it >= a.max_cycles) {
                         ok = false;
                         break;
@@ -565,6 +605,7 @@ bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double
     a.converged = prm.converged;
     a.max_cycles = prm.max_cycles;
     a.tol = prm.tol;
+    a.qtol = prm.qtol;
     a.qf = qf;
     a.qc = qc;
     a.p_out = p_out;

@@ -105,6 +105,7 @@ static fm_solve_params solve_params(const fm_ctx* ctx) {
     p.kernel = FM_KERNEL_AUTO;
     p.converged = ctx->cfg.converged;
     p.tol = ctx->cfg.tol;
+    p.qtol = ctx->cfg.qtol;
     p.max_cycles = ctx->cfg.max_cycles;
     return p;
 }

@@ -369,3 +369,21 @@ def test_tensor_core_fields_are_nested_across_levels(fm):
     K1 = ctx.kl_field_batch(1, xi)
     ctx.sync()
     assert torch.equal(K2[:, ::2, ::2], K1)
+
+
+@pytest.mark.parametrize("n,kernel", [(16, RESIDENT), (64, RESIDENT), (128, LEVELWISE)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_outflux_change_stopping_rule(fm, small, n, kernel, precision):
+    """Refinement that stops once an iteration moves Q by <= 1e-10 |Q| (the
+    residual target set out of reach) still lands within 1e-8 of the
+    converged FP64 oracle: the cycle contracts by rho < 0.8, so the
+    remaining error is below rho / (1 - rho) * 1e-10."""
+    ctx, _ = small
+    K = W.smooth_lognormal_field(n, S=17, tag=160 + n)
+    qf, qc, _, st = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_status=True,
+                                        precision=precision, converged=1, tol=1e-16, qtol=1e-10,
+                                        max_cycles=400, kernel=kernel)
+    rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300))
+    assert int(st.abs().sum()) == 0
+    assert _rel(qf.cpu().numpy(), rf) < RTOL_MIXED
+    assert _rel(qc.cpu().numpy(), rc) < RTOL_MIXED
