@@ -111,7 +111,9 @@ typedef struct {
     int32_t kernel;       /* FM_KERNEL_* */
     int32_t converged;    /* 0: nu0 V-cycles on every stage (the end of a stage's
                              cycles is its "exact" solution); 1: stages n_fine/2 and
-                             n_fine iterate to ||b - A p||_2 <= tol ||b||_2 */
+                             n_fine iterate to ||b - A p||_2 <= tol ||b||_2, testing
+                             after every nu0 V-cycles (in the mixed form: nu0 FP32
+                             V-cycles on the correction per FP64 residual) */
     double tol;
     double qtol;          /* also stop once a cycle changes the outflux by <= qtol |Q| */
     int32_t max_cycles;   /* cap per converged stage; a sample that reaches it gets

@@ -553,7 +553,7 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
             if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
             break;
         }
-        vcycle(H, k, k, prm, H.active, st);
+        for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, st);
         if (mixed)
             k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, st>>>(cells, S, g.p, g.p64, H.active);
     }

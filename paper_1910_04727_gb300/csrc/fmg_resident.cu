@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    for (int v = 0; v < a.nu0; ++v) resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
                 }
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
+                    // nu0 FP32 V-cycles on the correction equation per FP64 residual
+                    for (int v = 0; v < a.nu0; ++v) resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
                     for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] += (double)g.p[c];
                     __syncthreads();
                 }
