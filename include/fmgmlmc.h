@@ -206,6 +206,31 @@ fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double*
                           const fm_solve_params* prm, double* d_qf, double* d_qc,
                           double* d_p, int32_t* d_status, void* stream);
 
+/* The same FP64 fixed-cycle solve on the level-wise schedule as
+ * fmg_solve_batch, for callers that must not allocate device memory during a
+ * solve: code that runs under a memory budget fixed up front, inside a
+ * memory pool owned by someone else, or on a path where a cudaMalloc would
+ * stall the device or fail.  It allocates nothing (no cudaMalloc, cudaFree
+ * or allocating library routine; profiling must be off): its scratch is one
+ * static device array of 32 MiB that the library holds on every device that
+ * loads it until the process exits.  The paper has no counterpart; this is
+ * an interface for callers that cannot allocate.
+ *   - Inputs and outputs stay the caller's: d_K [n][n_fine][n_fine], d_qf
+ *     [n], d_qc [n] (nullable), as in fmg_solve_batch.
+ *   - prm must ask for FM_PREC_FP64 with converged = 0; prm->kernel is not
+ *     read.  A batch whose hierarchy needs more than 32 MiB (about 6 samples
+ *     of 256 x 256, 25 of 128 x 128, 100 of 64 x 64) is rejected with
+ *     FM_EINVAL and a message giving the bytes it needs: split it.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress) and keeps it; make that
+ *     first call before any stream capture.
+ *   - Every call uses the same array, which keeps whatever the last call left
+ *     in it; the solve writes every scratch entry before reading it.  Calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race
+ *     on the array: serialise them. */
+fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
+                                 const fm_solve_params* prm, double* d_qf, double* d_qc, void* stream);
+
 /* ---------------------------------------------------------------- MLMC */
 
 /* Running sums of one (level, shift) cell: Neumaier-compensated FP64 pairs

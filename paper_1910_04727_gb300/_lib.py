@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "F
 EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_points",
            "sobol_direction_numbers", "kl_basis_set", "kl_basis_build", "kl_basis_get", "kl_field_batch",
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
-           "fm_profile_end", "fm_kernel_family_name", "fm_sync"]
+           "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static"]
 
 
 class FmConfig(C.Structure):
@@ -95,6 +95,7 @@ def load(path=None):
         "fm_profile_end": (I32, [P, P, I32, C.POINTER(I32)]),
         "fm_kernel_family_name": (C.c_char_p, [I32]),
         "fm_sync": (I32, [P]),
+        "fmg_solve_batch_static": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -17,6 +17,7 @@
 // two refined grids (n/2 and n, which give Q^c and Q^f).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -702,9 +703,117 @@ fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
     return levelwise<double>(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// Scratch of fmg_solve_batch_static: one file-scope device array, present on
+// every device that loads the library for as long as the process lives.
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;   // 32 MiB
+static __device__ __align__(256) char g_static_scratch[kStaticScratchBytes];
+
+// Device address of the array on the current device.  Host code only sees a
+// stand-in symbol, so the address is asked for once per device, with that
+// device current, and kept.
+static char* static_scratch_address(fm_ctx* ctx, fm_status* status) {
+    static std::mutex mu;
+    static char* addr[128] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+        set_error(ctx, "fmg_solve_batch_static: no current CUDA device");
+        *status = FM_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(ctx, std::string("fmg_solve_batch_static: cudaGetSymbolAddress failed: ") +
+                               cudaGetErrorString(e));
+            *status = FM_ECUDA;
+            return nullptr;
+        }
+        addr[dev] = static_cast<char*>(p);
+    }
+    *status = FM_OK;
+    return addr[dev];
+}
+
+// The level-wise FP64 hierarchy of carve(), laid out in a caller-given buffer.
+static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine, int n0, size_t S,
+                       const double* d_K) {
+    char* cur = base;
+    auto take = [&](size_t bytes) {
+        char* p = cur;
+        cur += ((bytes + 255) / 256) * 256;
+        return p;
+    };
+    H.ctx = ctx;
+    H.n0 = n0;
+    H.S = S;
+    H.m = 0;
+    while ((n0 << H.m) < n_fine) ++H.m;
+    for (int k = 0; k <= H.m; ++k) {
+        const int n = n0 << k;
+        const size_t cnt = S * (size_t)n * n;
+        GridBufs<double>& g = H.g[k];
+        g.n = n;
+        g.K = (k == H.m) ? d_K : (double*)take(cnt * 8);
+        g.Te = (double*)take(cnt * 8);
+        g.Tn = (double*)take(cnt * 8);
+        g.D = (double*)take(cnt * 8);
+        g.p = (double*)take(cnt * 8);
+        g.b = (double*)take(cnt * 8);
+        g.Kc = nullptr;
+        g.TeC = g.TnC = g.DC = nullptr;
+        if (k < H.m) {
+            g.Kc = (double*)take(cnt * 8);
+            g.TeC = (double*)take(cnt * 8);
+            g.TnC = (double*)take(cnt * 8);
+            g.DC = (double*)take(cnt * 8);
+        }
+        g.p64 = g.Te64 = g.Tn64 = g.D64 = nullptr;
+    }
+    H.Ainv = (double*)take(S * (size_t)n0 * n0 * n0 * n0 * 8);
+    H.AinvC = (double*)take(S * (size_t)n0 * n0 * n0 * n0 * 8);
+    H.active = nullptr;
+    H.left = nullptr;
+    H.qprev = nullptr;
+}
+
 }  // namespace fm
 
 using namespace fm;
+
+extern "C" fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
+                                            const fm_solve_params* prm, double* d_qf, double* d_qc,
+                                            void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fmg_solve_batch_static: null context");
+    FM_CHECK_ARG(ctx, prm != nullptr, "fmg_solve_batch_static: null parameters");
+    const int n0 = prm->n_coarsest;
+    FM_CHECK_ARG(ctx, n0 >= 2 && n0 <= 4, "fmg_solve_batch_static: n_coarsest must be 2..4");
+    FM_CHECK_ARG(ctx, n_fine >= n0 && n_fine <= 8192, "fmg_solve_batch_static: bad n_fine");
+    int m = 0;
+    while ((n0 << m) < n_fine) ++m;
+    FM_CHECK_ARG(ctx, (n0 << m) == n_fine, "fmg_solve_batch_static: n_fine must be n_coarsest * 2^m");
+    FM_CHECK_ARG(ctx, prm->nu0 >= 1 && prm->nu1 >= 0 && prm->nu2 >= 0 && prm->nu1 + prm->nu2 >= 1,
+                 "fmg_solve_batch_static: need nu0 >= 1 and nu1 + nu2 >= 1");
+    FM_CHECK_ARG(ctx, prm->precision == FM_PREC_FP64 && !prm->converged,
+                 "fmg_solve_batch_static: only the FP64 fixed-cycle schedule (converged = 0)");
+    FM_CHECK_ARG(ctx, n == 0 || (d_K && d_qf), "fmg_solve_batch_static: null input or output");
+    if (n == 0) return FM_OK;
+    const size_t need = hierarchy_bytes(n_fine, n0, n, 8, false, false);
+    FM_CHECK_ARG(ctx, need <= kStaticScratchBytes,
+                 "fmg_solve_batch_static: " + std::to_string(n) + " samples of " + std::to_string(n_fine) + "x" +
+                     std::to_string(n_fine) + " need " + std::to_string(need) + " bytes of scratch; the static "
+                     "scratch holds " + std::to_string(kStaticScratchBytes) + " bytes: split the batch");
+    fm_status st = FM_OK;
+    char* base = static_scratch_address(ctx, &st);
+    if (!base) return st;
+    Hierarchy<double> H;
+    carve_into(ctx, H, base, n_fine, n0, n, d_K);
+    FM_TRY(fmg_batch(H, *prm, d_qf, d_qc, nullptr, nullptr, as_stream(stream)));
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
+}
 
 extern "C" fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                                      const fm_solve_params* prm, double* d_qf, double* d_qc,
