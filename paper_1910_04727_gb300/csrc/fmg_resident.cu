@@ -96,17 +96,28 @@ __device__ __forceinline__ C harm(C a, C b) {
     return C(2) * a * b / (a + b);
 }
 
+// All per-sample routines of the resident schedule, for one group of threads
+// that owns a sample: the whole CTA (WARP = false) or a single warp (WARP =
+// true, several samples per CTA, __syncwarp instead of CTA barriers).
+template <typename T, bool WARP>
+struct Res {
+    static __device__ __forceinline__ int rank() { return WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x; }
+    static __device__ __forceinline__ int size() { return WARP ? 32 : (int)blockDim.x; }
+    static __device__ __forceinline__ void sync() {
+        if (WARP) __syncwarp();
+        else __syncthreads();
+    }
+
 // ------------------------------------------------------------------ setup
 // Face transmissibilities of grid n, K injected from the fine field at
 // stride s = n_fine / n (read from global memory; L1/L2 serve the reuse).
-template <typename T>
-__device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const double* __restrict__ Kf,
+static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const double* __restrict__ Kf,
                                     int n_fine) {
     // FP64 faces where an FP64 copy is kept (or T is FP64); otherwise the
     // FP32 correction-solver coefficients are formed in FP32
     const int n = g.n, s = n_fine / n;
     auto K = [&](int i, int j) { return __ldg(Kf + (size_t)(s * j) * n_fine + (size_t)s * i); };
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         if (h || sizeof(T) == 8) {
             const double k = K(i, j);
@@ -141,10 +152,9 @@ __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const dou
 // geometric mean of its four children on the injected grid 2n, i.e. of the
 // fine field at stride s/2.  Uses the grid's iterate as scratch, so it runs
 // once the grid's stage solution has been interpolated to the next grid.
-template <typename T>
-__device__ void resident_setup_correction(const RGrid<T>& g, const double* __restrict__ Kf, int n_fine) {
+static __device__ void resident_setup_correction(const RGrid<T>& g, const double* __restrict__ Kf, int n_fine) {
     const int n = g.n, s = n_fine / n, h2 = s / 2;
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         const size_t r0 = (size_t)(s * j) * n_fine + (size_t)s * i, r1 = r0 + (size_t)h2 * n_fine;
         const double a = __ldg(Kf + r0), b = __ldg(Kf + r0 + h2), cc = __ldg(Kf + r1), d = __ldg(Kf + r1 + h2);
@@ -153,8 +163,8 @@ __device__ void resident_setup_correction(const RGrid<T>& g, const double* __res
         else   // FP32 correction coefficients of the mixed form
             g.p[c] = (T)expf(0.25f * (logf((float)a) + logf((float)b) + logf((float)cc) + logf((float)d)));
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    sync();
+    for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         const T k = g.p[c];
         const T tw = (i > 0) ? harm(g.p[c - 1], k) : T(2) * k;
@@ -166,13 +176,12 @@ __device__ void resident_setup_correction(const RGrid<T>& g, const double* __res
         if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
         if (i == 0) g.tw[j] = T(2) * k;
     }
-    __syncthreads();
+    sync();
 }
 
 // ------------------------------------------------------------------ V-cycle pieces
 // Right-hand side of cell (i, j): stored, or the stage problem's Dirichlet data.
-template <typename T>
-__device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
+static __device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
     if (g.b) return g.b[c];
     T v = T(0);
     if (i == 0) v += g.tw[j] * pW;
@@ -180,25 +189,22 @@ __device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, T pW
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T diag_at(const RGrid<T>& g, int c, int i, int j) {
+static __device__ __forceinline__ T diag_at(const RGrid<T>& g, int c, int i, int j) {
     const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
     const T ts = (j > 0) ? g.tn[c - g.n] : T(0);
     return tw + g.te[c] + ts + g.tn[c];
 }
 
-template <typename T>
-__device__ __forceinline__ T divide_by_diag(const RGrid<T>& g, T acc, int c, int i, int j) {
+static __device__ __forceinline__ T divide_by_diag(const RGrid<T>& g, T acc, int c, int i, int j) {
     if (g.dinv) return acc * g.dinv[c];
     return acc / diag_at(g, c, i, j);
 }
 
 // Gauss-Jordan inverse of the coarsest operator, all threads of the CTA.
 // A is SPD, so no pivoting.
-template <typename T>
-__device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A) {
+static __device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A) {
     const int n = g.n, m = n * n;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    for (int e = rank(); e < m * m; e += size()) {
         const int r = e / m, c = e % m;
         T v = T(0);
         if (r == c) {
@@ -213,45 +219,43 @@ __device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A) {
         A[e] = v;
         ainv[e] = (r == c) ? T(1) : T(0);
     }
-    __syncthreads();
+    sync();
     for (int k = 0; k < m; ++k) {
         const T piv = A[k * m + k];
-        __syncthreads();
-        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        sync();
+        for (int c = rank(); c < m; c += size()) {
             A[k * m + c] /= piv;
             ainv[k * m + c] /= piv;
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        sync();
+        for (int e = rank(); e < m * m; e += size()) {
             const int r = e / m, c = e % m;
             if (r == k) continue;
             const T f = A[r * m + k];   // column k is left alone until the next phase
             if (c != k) A[e] -= f * A[k * m + c];
             ainv[e] -= f * ainv[k * m + c];
         }
-        __syncthreads();
-        for (int r = threadIdx.x; r < m; r += blockDim.x)
+        sync();
+        for (int r = rank(); r < m; r += size())
             if (r != k) A[r * m + k] = T(0);
-        __syncthreads();
+        sync();
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, const T* ainv, T pW, T pE) {
+static __device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, const T* ainv, T pW, T pE) {
     const int n = g.n, m = n * n;
     T acc = T(0);
-    if (threadIdx.x < m)
-        for (int c = 0; c < m; ++c) acc += ainv[threadIdx.x * m + c] * rhs_at(g, c, c % n, c / n, pW, pE);
-    __syncthreads();
-    if (threadIdx.x < m) g.p[threadIdx.x] = acc;
-    __syncthreads();
+    if (rank() < m)
+        for (int c = 0; c < m; ++c) acc += ainv[rank() * m + c] * rhs_at(g, c, c % n, c / n, pW, pE);
+    sync();
+    if (rank() < m) g.p[rank()] = acc;
+    sync();
 }
 
-template <typename T>
-__device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T pE) {
+static __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T pE) {
     const int n = g.n, half = n * n / 2, hn = n / 2;
     for (int color = 0; color < 2; ++color) {
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+        for (int h = rank(); h < half; h += size()) {
             const int j = h / hn;
             const int i = 2 * (h % hn) + ((j + color) & 1);
             const int c = j * n + i;
@@ -262,12 +266,11 @@ __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T pE) {
             if (j < n - 1) acc += g.tn[c] * g.p[c + n];
             g.p[c] = divide_by_diag(g, acc, c, i, j);
         }
-        __syncthreads();
+        sync();
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
+static __device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
     const int n = g.n;
     T v = diag_at(g, c, i, j) * g.p[c];
     if (i > 0) v -= g.te[c - 1] * g.p[c - 1];
@@ -277,10 +280,9 @@ __device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, 
     return rhs_at(g, c, i, j, pW, pE) - v;
 }
 
-template <typename T>
-__device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, T pW, T pE) {
+static __device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, T pW, T pE) {
     const int nc = cg.n, nf = f.n;
-    for (int C = threadIdx.x; C < nc * nc; C += blockDim.x) {
+    for (int C = rank(); C < nc * nc; C += size()) {
         const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J, c0 = j0 * nf + i0;
         const T r00 = resident_residual(f, c0, i0, j0, pW, pE);
         const T r10 = resident_residual(f, c0 + 1, i0 + 1, j0, pW, pE);
@@ -289,11 +291,11 @@ __device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid
         cg.b[C] = r00 + r10 + r01 + r11;
         cg.p[C] = T(0);
     }
-    __syncthreads();
+    sync();
 }
 
 template <typename U>
-__device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, U gW, U gE) {
+static __device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, U gW, U gE) {
     J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
     if (I < 0) return U(2) * gW - uc[J * nc];
     if (I > nc - 1) return U(2) * gE - uc[J * nc + nc - 1];
@@ -302,9 +304,9 @@ __device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, U gW, U gE
 
 // out (+)= bilinear interpolation of uc (nc x nc) onto the 2nc x 2nc grid.
 template <typename U>
-__device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, U gW, U gE, bool add) {
+static __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, U gW, U gE, bool add) {
     const int nf = 2 * nc;
-    for (int c = threadIdx.x; c < nf * nf; c += blockDim.x) {
+    for (int c = rank(); c < nf * nf; c += size()) {
         const int i = c % nf, j = c / nf, I = i >> 1, J = j >> 1;
         const int Ix = (i & 1) ? I + 1 : I - 1;
         const int Jy = (j & 1) ? J + 1 : J - 1;
@@ -313,14 +315,13 @@ __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, U 
                     U(16);
         out[c] = add ? out[c] + v : v;
     }
-    __syncthreads();
+    sync();
 }
 
 // One V(nu1, nu2) cycle on grid k, iteratively: descend (smooth, restrict
 // the residual), exact coarsest solve, ascend (prolong the correction,
 // smooth).  pW/pE only enter through a grid without a stored rhs.
-template <typename T>
-__device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, T pW, T pE) {
+static __device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, T pW, T pE) {
     for (int l = k; l >= 1; --l) {
         for (int s = 0; s < nu1; ++s) resident_rbgs(L.g[l], pW, pE);
         resident_restrict(L.g[l], L.g[l - 1], pW, pE);
@@ -333,19 +334,24 @@ __device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, T 
 }
 
 // Sum of a and b over the CTA; every thread gets the totals.
-__device__ __forceinline__ void block_sum2(double a, double b, double* red, double& A, double& B) {
+static __device__ __forceinline__ void block_sum2(double a, double b, double* red, double& A, double& B) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, off);
         b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    if (WARP) {
+        A = __shfl_sync(0xffffffffu, a, 0);
+        B = __shfl_sync(0xffffffffu, b, 0);
+        return;
     }
     const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0) {
         red[warp] = a;
         red[32 + warp] = b;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    sync();
+    if (rank() == 0) {
         double sa = 0.0, sb = 0.0;
         for (int w = 0; w < nw; ++w) {
             sa += red[w];
@@ -354,30 +360,28 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* red, doub
         red[64] = sa;
         red[65] = sb;
     }
-    __syncthreads();
+    sync();
     A = red[64];
     B = red[65];
-    __syncthreads();
+    sync();
 }
 
 // Stage problem of grid k written into its rhs: the Dirichlet data.
-template <typename T>
-__device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, T pW, T pE) {
-    for (int c = threadIdx.x; c < g.n * g.n; c += blockDim.x) {
+static __device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, T pW, T pE) {
+    for (int c = rank(); c < g.n * g.n; c += size()) {
         const int i = c % g.n, j = c / g.n;
         T v = T(0);
         if (i == 0) v += g.tw[j] * pW;
         if (i == g.n - 1) v += g.te[c] * pE;
         g.b[c] = v;
     }
-    __syncthreads();
+    sync();
 }
 
 // ||r||^2 and ||rhs||^2 of the stage problem on grid k (V-cycle type).
-template <typename T>
-__device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, double& rr, double& bb) {
+static __device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, double& rr, double& bb) {
     double a = 0.0, b = 0.0;
-    for (int c = threadIdx.x; c < g.n * g.n; c += blockDim.x) {
+    for (int c = rank(); c < g.n * g.n; c += size()) {
         const int i = c % g.n, j = c / g.n;
         const double r = (double)resident_residual(g, c, i, j, pW, pE);
         const double f = (double)rhs_at(g, c, i, j, pW, pE);
@@ -389,12 +393,11 @@ __device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, double& 
 
 // FP64 residual of the stage problem on h into the FP32 grid's rhs (the
 // correction equation), zero the correction; returns the norms.
-template <typename T>
-__device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW, double pE, double* red,
+static __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW, double pE, double* red,
                             double& rr, double& bb) {
     const int n = h.n;
     double a = 0.0, b = 0.0;
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         const double tw = (i > 0) ? h.te[c - 1] : h.tw[j];
         const double ts = (j > 0) ? h.tn[c - n] : 0.0;
@@ -417,10 +420,10 @@ __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW, double
 
 // Q = sum_j te(n-1, j) (p(n-1, j) - pE); warp 0 reduces, valid in thread 0.
 template <typename P, typename Q>
-__device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, double pE) {
+static __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, double pE) {
     double acc = 0.0;
-    if (threadIdx.x < 32) {
-        for (int j = threadIdx.x; j < n; j += 32) {
+    if (rank() < 32) {
+        for (int j = rank(); j < n; j += 32) {
             const int c = j * n + n - 1;
             acc += (double)te[c] * ((double)p[c] - pE);
         }
@@ -432,14 +435,17 @@ __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, dou
 
 // Outflux broadcast to every thread of the CTA.
 template <typename P, typename Q>
-__device__ __forceinline__ double stage_outflux(const P* te, const Q* p, int n, double pE, double* red) {
+static __device__ __forceinline__ double stage_outflux(const P* te, const Q* p, int n, double pE, double* red) {
     const double q = outflux_of(te, p, n, pE);
-    if (threadIdx.x == 0) red[70] = q;
-    __syncthreads();
+    if (WARP) return __shfl_sync(0xffffffffu, q, 0);
+    if (rank() == 0) red[70] = q;
+    sync();
     const double out = red[70];
-    __syncthreads();
+    sync();
     return out;
 }
+
+};
 
 struct ResidentArgs {
     int n_fine, n0;
@@ -453,20 +459,35 @@ struct ResidentArgs {
     int32_t* status;
 };
 
-template <typename T, bool MIXED>
-__global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
+// Shared memory of one CTA: a layout table per group, then each group's data.
+template <typename T>
+__host__ __device__ inline size_t resident_slot_bytes() {
+    return ((sizeof(RLayout<T>) + 15) / 16) * 16;
+}
+
+template <typename T, bool MIXED, bool WARP>
+__global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
+    using R = Res<T, WARP>;
     extern __shared__ __align__(16) char smem[];
-    const RLayout<T> L = resident_layout<T>(smem, a.n_fine, a.n0, MIXED);
+    const int groups = WARP ? (int)(blockDim.x >> 5) : 1;
+    const int grp = WARP ? (int)(threadIdx.x >> 5) : 0;
+    RLayout<T>* slot = reinterpret_cast<RLayout<T>*>(smem + grp * resident_slot_bytes<T>());
+    const size_t data_bytes = resident_layout<T>(nullptr, a.n_fine, a.n0, MIXED).bytes;
+    char* data = smem + groups * resident_slot_bytes<T>() + grp * data_bytes;
+    if (R::rank() == 0) *slot = resident_layout<T>(data, a.n_fine, a.n0, MIXED);
+    R::sync();
+    const RLayout<T>& L = *slot;
     const T tpW = (T)a.pW, tpE = (T)a.pE;
     const int m = L.m;
-    for (size_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+    const size_t stride = (size_t)gridDim.x * groups;
+    for (size_t s = (size_t)blockIdx.x * groups + grp; s < a.S; s += stride) {
         const double* Kf = a.K + s * (size_t)a.n_fine * a.n_fine;
         for (int k = 0; k <= m; ++k) {
             const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
-            resident_setup_grid(L.g[k], h, Kf, a.n_fine);
+            R::resident_setup_grid(L.g[k], h, Kf, a.n_fine);
         }
-        __syncthreads();
-        resident_coarse_inverse(L.g[0], L.ainv, L.work);
+        R::sync();
+        R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
         bool ok = true;
         double q_coarse = NAN, q_fine = NAN;
 
@@ -477,27 +498,27 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
             if (k > 0) {
                 if (MIXED && refined && k == m && m >= 1) {
                     // FP64 interpolation of the refined stage m-1 solution
-                    resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.pW, a.pE, false);
+                    R::resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.pW, a.pE, false);
                 } else {
-                    resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, tpW, tpE, false);
+                    R::resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, tpW, tpE, false);
                 }
                 // grid k-1 now only carries corrections of the V-cycles on grid k
-                resident_setup_correction(L.g[k - 1], Kf, a.n_fine);
-                if (k == 1) resident_coarse_inverse(L.g[0], L.ainv, L.work);
+                R::resident_setup_correction(L.g[k - 1], Kf, a.n_fine);
+                if (k == 1) R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
             }
-            if (g.b) resident_stage_rhs(g, tpW, tpE);
-            if (k == 0) resident_coarse_solve(g, L.ainv, tpW, tpE);
+            if (g.b) R::resident_stage_rhs(g, tpW, tpE);
+            if (k == 0) R::resident_coarse_solve(g, L.ainv, tpW, tpE);
             if (!refined) {
                 if (k > 0)
-                    for (int it = 0; it < a.nu0; ++it) resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    for (int it = 0; it < a.nu0; ++it) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
             } else if (!MIXED) {
                 // FP64: V-cycles on the stage problem until the residual or
                 // outflux-change test passes
                 double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
-                    stage_norms(g, tpW, tpE, L.red, rr, bb);
-                    const double q = stage_outflux(g.te, g.p, g.n, a.pE, L.red);
+                    R::stage_norms(g, tpW, tpE, L.red, rr, bb);
+                    const double q = R::stage_outflux(g.te, g.p, g.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
                     q_prev = q;
@@ -505,20 +526,20 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    for (int v = 0; v < a.nu0; ++v) resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
                 }
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
                 const HGrid& h = L.h[k - (m - 1)];
                 if (!(k == m && m >= 1)) {
-                    for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] = (double)g.p[c];
-                    __syncthreads();
+                    for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] = (double)g.p[c];
+                    R::sync();
                 }
                 double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
-                    ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
-                    const double q = stage_outflux(h.te, h.p, h.n, a.pE, L.red);
+                    R::ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
+                    const double q = R::stage_outflux(h.te, h.p, h.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
                     q_prev = q;
@@ -527,9 +548,9 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                         break;
                     }
                     // nu0 FP32 V-cycles on the correction equation per FP64 residual
-                    for (int v = 0; v < a.nu0; ++v) resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
-                    for (int c = threadIdx.x; c < h.n * h.n; c += blockDim.x) h.p[c] += (double)g.p[c];
-                    __syncthreads();
+                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
+                    for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] += (double)g.p[c];
+                    R::sync();
                 }
             }
             // outflux of the stage (the FP64 iterate in mixed refined stages)
@@ -537,16 +558,16 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
                 double q;
                 if (MIXED && refined) {
                     const HGrid& h = L.h[k - (m - 1)];
-                    q = outflux_of(h.te, h.p, h.n, a.pE);
+                    q = R::outflux_of(h.te, h.p, h.n, a.pE);
                 } else {
-                    q = outflux_of(g.te, g.p, g.n, a.pE);
+                    q = R::outflux_of(g.te, g.p, g.n, a.pE);
                 }
                 if (k == m) q_fine = q;
                 else q_coarse = q;
-                __syncthreads();
+                R::sync();
             }
         }
-        if (threadIdx.x == 0) {
+        if (R::rank() == 0) {
             a.qf[s] = q_fine;
             if (a.qc) a.qc[s] = q_coarse;
             if (a.status) a.status[s] = ok ? FM_OK : FM_ENOTCONV;
@@ -554,10 +575,10 @@ __global__ void __launch_bounds__(512) k_fmg_resident(ResidentArgs a) {
         if (a.p_out) {
             const bool fine64 = MIXED && a.converged;
             double* po = a.p_out + s * (size_t)a.n_fine * a.n_fine;
-            for (int c = threadIdx.x; c < a.n_fine * a.n_fine; c += blockDim.x)
+            for (int c = R::rank(); c < a.n_fine * a.n_fine; c += R::size())
                 po[c] = fine64 ? L.h[1].p[c] : (double)L.g[m].p[c];
         }
-        __syncthreads();
+        R::sync();
     }
 }
 
@@ -568,26 +589,36 @@ size_t resident_smem_bytes(int n_fine, int n0, bool mixed) {
 
 constexpr size_t kResidentSmemMax = 227 * 1024;
 
-template <typename T, bool MIXED>
+// Grids up to 16 x 16 run one sample per warp (four per CTA, barriers are
+// __syncwarp); larger grids one sample per CTA.
+template <typename T, bool MIXED, bool WARP>
 static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st) {
-    const size_t smem = resident_smem_bytes(a.n_fine, a.n0, MIXED);
+    const int groups = WARP ? 4 : 1;
+    const size_t smem = groups * (resident_slot_bytes<T>() + resident_smem_bytes(a.n_fine, a.n0, MIXED));
     if (smem > kResidentSmemMax) return false;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_fmg_resident<T, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_fmg_resident<T, MIXED, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kResidentSmemMax);
         attr_done = true;
     }
-    const int threads = a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128);
+    const int threads = WARP ? 32 * groups : (a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fmg_resident<T, MIXED>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fmg_resident<T, MIXED, WARP>, threads, smem);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    const size_t grid = std::min<size_t>(a.S, (size_t)std::max(per_sm, 1) * sms);
+    const size_t need = (a.S + groups - 1) / groups;
+    const size_t grid = std::min<size_t>(need, (size_t)std::max(per_sm, 1) * sms);
     const double cells = (double)a.S * a.n_fine * a.n_fine;
     FM_TIMED(ctx, kFamResidentFmg, st, 8.0 * cells + 16.0 * a.S, 0.0,
-             k_fmg_resident<T, MIXED><<<(unsigned)grid, threads, smem, st>>>(a));
+             k_fmg_resident<T, MIXED, WARP><<<(unsigned)grid, threads, smem, st>>>(a));
     return true;
+}
+
+template <typename T, bool MIXED>
+static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st) {
+    if (a.n_fine <= 16) return launch_resident<T, MIXED, true>(ctx, a, st);
+    return launch_resident<T, MIXED, false>(ctx, a, st);
 }
 
 bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double* d_K,
