@@ -178,3 +178,27 @@ class FMGSampler:
         qf, qc = self.solve(l, self.points(l, first, n, r))
         y = qf if l == 0 else qf - qc
         return y, qf, qc
+
+
+class SurrogateLevels:
+    """The control-variate level below the coarsest grid (north of the
+    paper's Eq. 2): extended level 0 samples S(xi) on its own stream, extended
+    level 1 samples Q_0(xi) - S(xi) on level 0's stream, extended level l+1 is
+    level l of `sampler`.  E[S] + E[Q_0 - S] + sum_{l>=1} E[Y_l] = E[Q_L] for
+    any S.  predict(xi [n][M]) -> S [n]; surrogate_stream is the Philox level
+    id of extended level 0."""
+
+    def __init__(self, sampler, predict, surrogate_stream=100):
+        self.s, self.predict, self.stream = sampler, predict, surrogate_stream
+
+    def __call__(self, l, first, n, r=None):
+        if l == 0:
+            M = self.s.B[0].shape[1]
+            xi = _lib.mc_normals(self.s.seed, self.stream, first, n, M)
+            y = self.predict(xi)
+            return y, y, np.zeros_like(y)
+        if l == 1:
+            xi = self.s.points(0, first, n, r)
+            qf, _ = self.s.solve(0, xi)
+            return qf - self.predict(xi), qf, self.predict(xi)
+        return self.s(l - 1, first, n, r)

@@ -96,3 +96,29 @@ def test_variance_of_corrections_decays_over_levels():
     V = [np.var(s(l, 0, 200)[0], ddof=1) for l in range(4)]
     assert V[1] < V[0] and V[2] < V[1] and V[3] < V[2]
     assert mlmc.fit_rate(V, 1) > 0.5
+
+
+def test_constant_surrogate_reduces_to_plain_mlmc():
+    """S = c: extended level 0 averages c, extended level 1 averages Q_0 - c,
+    so their sum is the plain level-0 mean sample for sample."""
+    levels = [8, 16]
+    basis = kl.KLBasis(16, 12, 1.0, 0.3, q=16)
+    s = mlmc.FMGSampler(levels, basis, seed=13)
+    sur = mlmc.SurrogateLevels(s, lambda xi: np.full(len(xi), 0.75))
+    y0 = sur(0, 0, 50)[0]
+    y1 = sur(1, 0, 200)[0]
+    plain = s(0, 0, 200)[0]
+    assert np.all(y0 == 0.75)
+    np.testing.assert_allclose(np.mean(y0) + np.mean(y1), np.mean(plain), rtol=1e-14)
+
+
+def test_bad_surrogate_keeps_the_estimator_unbiased():
+    """A surrogate unrelated to Q still gives E[Q_L] within the estimator's RMSE."""
+    levels = [8, 16, 32]
+    basis = _layered_setup(levels)
+    s = mlmc.FMGSampler(levels, basis, seed=17)
+    sur = mlmc.SurrogateLevels(s, lambda xi: 1.0 + 0.5 * np.tanh(xi[:, 0] * xi[:, 1]))
+    cost = np.concatenate([[1.0], mlmc.cost_model(np.array(levels) ** 2)])
+    res = mlmc.mlmc(sur, 3, 5e-3, 100, cost)
+    exact = _layered_expectation(basis, levels[-1])
+    assert abs(res["estimate"] - exact) < 3 * np.sqrt(res["var_estimator"])
