@@ -247,9 +247,11 @@ typedef struct {
 
 /* Draw samples first .. first+n-1 of level `level` (MC if shift < 0, else
  * QMC shift `shift`), synthesise their fields, run the FMG solve and add Y,
- * Y^2, Q^f, Q^c to *d_sums (device).  d_qf / d_qc (nullable, device [n])
- * receive the per-sample QoIs.  Processes the samples in batches of at most
- * the context's max_batch. */
+ * Y^2, Q^f, Q^c to *d_sums (device).  With the surrogate enabled
+ * (surrogate_enable) level -1 is the surrogate level (Y = S(xi), no solve, on
+ * a point stream of its own) and level 0 gives Y = Q_0 - S(xi) with S in the
+ * Q^c sums.  d_qf / d_qc (nullable, device [n]) receive the per-sample QoIs.
+ * Processes the samples in batches of at most the context's max_batch. */
 fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t first, uint32_t n,
                             int32_t shift, fm_level_sums* d_sums, double* d_qf, double* d_qc,
                             void* stream);
@@ -259,6 +261,8 @@ typedef struct {
     int32_t qmc;          /* 0: MLMC (Algorithm 1/3), 1: MLQMC (Algorithm 2) */
     int64_t n_pilot;      /* initial samples per level (per shift for QMC) */
     int32_t max_rounds;
+    int32_t surrogate;    /* 1: add the surrogate control-variate level below level 0 */
+    double surrogate_cost; /* cost of an S-level sample relative to a level-0 sample */
 } fm_estimate_opts;
 
 typedef struct {
@@ -271,6 +275,8 @@ typedef struct {
     double bias;                     /* |mean(Y_L)| / (2^alpha - 1) */
     int32_t rounds;
     double seconds;                  /* wall time of the call */
+    double mean_s, var_s;            /* surrogate level: mean(S), V[S] (or its level-estimate variance) */
+    int64_t N_s;                     /* surrogate-level samples */
 } fm_result;
 
 /* The host controller (Algorithm 3 with the MC rule N_l = (2/eps^2)
@@ -283,6 +289,58 @@ fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* ou
  * asynchronous calls on ctx: FM_ETIMEOUT if a bounded wait inside a kernel
  * ran out (its output is then invalid), FM_ECUDA for a CUDA error. */
 fm_status fm_sync(fm_ctx* ctx);
+
+/* ---------------------------------------------------------------- surrogate */
+
+/* Control-variate level below the coarsest grid (the project's addition to
+ * the telescoping sum of Eq. 2): E[Q_L] = E[S] + E[Q_0 - S] + sum_{l>=1}
+ * E[Y_l], unbiased for any S.  S(xi) = mu + sd f(xi), f an MLP M -> 256 ->
+ * 256 -> 256 -> 1 with GELU(z) = z (1 + erf(z/sqrt 2))/2; hidden layers run
+ * on tcgen05 tensor cores with BF16 operands (weights, input, activations,
+ * back-propagated pre-activation gradients) and FP32 accumulation; FP32
+ * master parameters and Adam.  Flat FP32 parameter layout: W1 [256][M], b1
+ * [256], W2 [256][256], b2, W3 [256][256], b3, w4 [256], b4 [1]. */
+typedef struct {
+    int32_t n_train;      /* training pairs (xi, Q_0) drawn from level 0 (>= 256) */
+    int32_t epochs;
+    double lr;            /* Adam step, cosine-decayed to 0 over the run */
+    uint64_t seed;        /* parameter initialisation and shuffling */
+} fm_train_opts;
+
+typedef struct {
+    double loss_first, loss_last;   /* mini-batch MSE of the standardised target */
+    double mu, sd;                  /* target standardisation */
+    double corr;                    /* correlation of S with Q_0 on the training set */
+    double var_q, var_residual;     /* V[Q_0] and V[Q_0 - S] on the training set */
+    int32_t steps;
+    double seconds;
+} fm_train_report;
+
+/* Turn the surrogate level of mlmc_sample_level on (1) or off (0). */
+fm_status surrogate_enable(fm_ctx* ctx, int32_t on);
+
+/* Number of FP32 parameters of the network for the context's M. */
+int64_t surrogate_param_count(const fm_ctx* ctx);
+
+/* Copy the FP32 parameters to (set = 0) or from (set = 1) host memory. */
+fm_status surrogate_params(fm_ctx* ctx, float* host_params, int32_t set);
+
+/* Set the target standardisation (S = mu + sd f). */
+fm_status surrogate_set_scale(fm_ctx* ctx, double mu, double sd);
+
+/* One forward and backward pass of the MSE loss on a batch of 256 rows:
+ * d_xi [256][M] FP64 inputs, d_target [256] FP32 standardised targets;
+ * host_grads (nullable) receives the gradient in the parameter layout,
+ * host_loss (nullable) the mean squared error.  Synchronous. */
+fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const float* d_target, float* host_grads,
+                              double* host_loss);
+
+/* Train from scratch on n_train level-0 samples of the method (points on a
+ * stream of their own, the context's field and solver).  Synchronous. */
+fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* report);
+
+/* d_s[s] = S(d_xi[s]) for n rows of FP64 KL coefficients [n][M]. */
+fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream);
 
 /* ---------------------------------------------------------------- profiling */
 

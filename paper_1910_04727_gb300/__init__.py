@@ -196,13 +196,53 @@ class Context:
                 launches=s.launches, ms=s.ms, bytes=s.bytes, flops=s.flops)
         return out
 
-    def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100):
+    # ----------------------------------------------------------- surrogate
+    def surrogate_param_count(self):
+        return int(self._L.surrogate_param_count(self._h))
+
+    def surrogate_get_params(self):
+        p = np.zeros(self.surrogate_param_count(), np.float32)
+        self._check(self._L.surrogate_params(self._h, p.ctypes.data_as(C.c_void_p), 0))
+        return p
+
+    def surrogate_set_params(self, params, mu=0.0, sd=1.0):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.surrogate_param_count()
+        self._check(self._L.surrogate_params(self._h, p.ctypes.data_as(C.c_void_p), 1))
+        self._check(self._L.surrogate_set_scale(self._h, mu, sd))
+
+    def surrogate_loss_grad(self, xi, target):
+        """xi: CUDA float64 [256][M]; target: CUDA float32 [256]. Returns (loss, grads)."""
+        g = np.zeros(self.surrogate_param_count(), np.float32)
+        loss = C.c_double()
+        self._check(self._L.surrogate_loss_grad(self._h, _ptr(xi), _ptr(target),
+                                                g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return loss.value, g
+
+    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7):
+        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed)
+        rep = _lib.FmTrainReport()
+        self._check(self._L.surrogate_train(self._h, C.byref(opts), C.byref(rep)))
+        return {f: getattr(rep, f) for f, _ in _lib.FmTrainReport._fields_}
+
+    def surrogate_eval(self, xi):
+        s = torch.empty(xi.shape[0], dtype=torch.float64, device="cuda")
+        self._check(self._L.surrogate_eval(self._h, xi.shape[0], _ptr(xi), _ptr(s), _stream()))
+        return s
+
+    def surrogate_enable(self, on=True):
+        self._check(self._L.surrogate_enable(self._h, int(bool(on))))
+
+    def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100, surrogate=False,
+                      surrogate_cost=0.01):
         torch.cuda.synchronize()
-        opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds)
+        opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds, int(bool(surrogate)),
+                                   surrogate_cost)
         res = _lib.FmResult()
         self._check(self._L.mlmc_estimate(self._h, C.byref(opts), C.byref(res)))
         L = len(self.levels)
         return dict(estimate=res.estimate, var_estimator=res.var_estimator,
                     means=np.array(res.mean[:L]), V=np.array(res.var[:L]),
                     N=np.array(res.N[:L]), alpha=res.alpha, beta=res.beta, bias=res.bias,
-                    rounds=res.rounds, seconds=res.seconds)
+                    rounds=res.rounds, seconds=res.seconds, mean_s=res.mean_s, var_s=res.var_s,
+                    N_s=res.N_s)

@@ -22,7 +22,9 @@ STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "F
 EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_points",
            "sobol_direction_numbers", "kl_basis_set", "kl_basis_build", "kl_basis_get", "kl_field_batch",
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
-           "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static"]
+           "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static",
+           "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
+           "surrogate_train", "surrogate_eval", "surrogate_enable"]
 
 
 class FmConfig(C.Structure):
@@ -49,7 +51,7 @@ class FmLevelSums(C.Structure):
 
 class FmEstimateOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("qmc", C.c_int32), ("n_pilot", C.c_int64),
-                ("max_rounds", C.c_int32)]
+                ("max_rounds", C.c_int32), ("surrogate", C.c_int32), ("surrogate_cost", C.c_double)]
 
 
 class FmKernelStat(C.Structure):
@@ -57,11 +59,22 @@ class FmKernelStat(C.Structure):
                 ("bytes", C.c_double), ("flops", C.c_double)]
 
 
+class FmTrainOpts(C.Structure):
+    _fields_ = [("n_train", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64)]
+
+
+class FmTrainReport(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("mu", C.c_double),
+                ("sd", C.c_double), ("corr", C.c_double), ("var_q", C.c_double),
+                ("var_residual", C.c_double), ("steps", C.c_int32), ("seconds", C.c_double)]
+
+
 class FmResult(C.Structure):
     _fields_ = [("estimate", C.c_double), ("var_estimator", C.c_double),
                 ("mean", C.c_double * FM_MAX_LEVELS), ("var", C.c_double * FM_MAX_LEVELS),
                 ("N", C.c_int64 * FM_MAX_LEVELS), ("alpha", C.c_double), ("beta", C.c_double),
-                ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double)]
+                ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double),
+                ("mean_s", C.c_double), ("var_s", C.c_double), ("N_s", C.c_int64)]
 
 
 _lib = None
@@ -96,6 +109,13 @@ def load(path=None):
         "fm_kernel_family_name": (C.c_char_p, [I32]),
         "fm_sync": (I32, [P]),
         "fmg_solve_batch_static": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P]),
+        "surrogate_param_count": (I64, [P]),
+        "surrogate_params": (I32, [P, P, I32]),
+        "surrogate_set_scale": (I32, [P, D, D]),
+        "surrogate_loss_grad": (I32, [P, P, P, P, P]),
+        "surrogate_train": (I32, [P, C.POINTER(FmTrainOpts), C.POINTER(FmTrainReport)]),
+        "surrogate_eval": (I32, [P, U32, P, P, P]),
+        "surrogate_enable": (I32, [P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -50,7 +50,7 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
         return FM_EINVAL;
     }
     const size_t vbytes = ctx->h_sobol_V.size() * sizeof(uint32_t);
-    const size_t sums = (size_t)cfg->n_levels * (cfg->n_shifts > 0 ? cfg->n_shifts : 1);
+    const size_t sums = (size_t)(cfg->n_levels + 1) * (cfg->n_shifts > 0 ? cfg->n_shifts : 1);
     if (cudaMalloc((void**)&ctx->d_sobol_V, vbytes) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_sums, sums * sizeof(fm_level_sums)) != cudaSuccess) {
         fm_destroy(ctx);
@@ -77,10 +77,17 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     cudaFree(ctx->d_sums);
     cudaFree(ctx->d_partials);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    mlp_free(ctx);
     for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->tc.basis[l]);
     cudaFree(ctx->tc.xi);
     cudaFree(ctx->tc.err);
     delete ctx;
+}
+
+extern "C" fm_status surrogate_enable(fm_ctx* ctx, int32_t on) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_enable: null context");
+    ctx->surrogate_on = on ? 1 : 0;
+    return FM_OK;
 }
 
 extern "C" fm_status fm_sync(fm_ctx* ctx) {
@@ -93,6 +100,10 @@ extern "C" fm_status fm_sync(fm_ctx* ctx) {
             set_error(ctx, "a bounded device-side wait of the tensor-core field synthesis ran out");
             return FM_ETIMEOUT;
         }
+    }
+    if (surrogate_err_flag(ctx)) {
+        set_error(ctx, "a bounded device-side wait of the surrogate network ran out");
+        return FM_ETIMEOUT;
     }
     return FM_OK;
 }

@@ -89,7 +89,7 @@ void set_error(const fm_ctx* ctx, const std::string& msg);
 enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
-    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamilyCount
+    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamilyCount
 };
 
 struct ProfRecord {
@@ -151,6 +151,8 @@ struct fm_ctx {
     size_t partial_capacity = 0;
     fm::Profiler prof;
     fm::TcState tc;
+    void* mlp = nullptr;             // surrogate network state (mlp.cu)
+    int surrogate_on = 0;            // level -1 = S(xi), level 0 = Q_0 - S(xi)
 };
 
 namespace fm {
@@ -205,6 +207,13 @@ fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, do
 
 // KL arithmetic of the context: 1 FP64, 2 BF16, 3 BF16 split (bf16x3).
 int kl_mode_of(const fm_ctx* ctx);
+
+// Surrogate network (mlp.cu).
+constexpr uint32_t kSurrogateLevelStream = 12;   // Philox level id of the S-level samples
+constexpr uint32_t kSurrogateTrainStream = 13;   // Philox level id of the training samples
+fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st);
+int surrogate_err_flag(const fm_ctx* ctx);
+void mlp_free(fm_ctx* ctx);
 
 // Level sums of a batch (mlmc.cu).
 fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc,

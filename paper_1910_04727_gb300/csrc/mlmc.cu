@@ -134,32 +134,43 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
                                        int32_t shift, fm_level_sums* d_sums, double* d_qf, double* d_qc,
                                        void* stream) {
     FM_CHECK_ARG(ctx, ctx != nullptr, "mlmc_sample_level: null context");
-    FM_CHECK_ARG(ctx, level >= 0 && level < ctx->cfg.n_levels, "mlmc_sample_level: bad level");
+    FM_CHECK_ARG(ctx, (level >= 0 || (level == -1 && ctx->surrogate_on)) && level < ctx->cfg.n_levels,
+                 "mlmc_sample_level: bad level (-1, the surrogate level, needs surrogate_enable)");
     FM_CHECK_ARG(ctx, ctx->basis_ready, "mlmc_sample_level: no KL basis installed");
     FM_CHECK_ARG(ctx, shift < ctx->cfg.n_shifts, "mlmc_sample_level: shift out of range");
     FM_CHECK_ARG(ctx, d_sums != nullptr || d_qf != nullptr, "mlmc_sample_level: no output");
     if (n == 0) return FM_OK;
     cudaStream_t st = as_stream(stream);
-    const int N = grid_of_level(ctx, level), M = ctx->cfg.M;
+    const bool s_level = (level == -1);
+    const bool with_s = ctx->surrogate_on && level <= 0;   // S(xi) needed: level -1, or Y_0 = Q_0 - S
+    const int N = grid_of_level(ctx, s_level ? 0 : level), M = ctx->cfg.M;
+    const uint32_t stream_level = s_level ? kSurrogateLevelStream : (uint32_t)level;
     const fm_solve_params prm = solve_params(ctx);
-    const int64_t lim = std::min<int64_t>(batch_limit(ctx, N), (int64_t)65535 * 64);
+    const int64_t lim = s_level ? (int64_t)1 << 20 : std::min<int64_t>(batch_limit(ctx, N), (int64_t)65535 * 64);
     const size_t cap = (size_t)std::min<int64_t>(lim, n);
     FM_TRY(ensure(ctx, &ctx->d_xi, &ctx->xi_capacity, cap * M));
-    FM_TRY(ensure(ctx, &ctx->d_K, &ctx->K_capacity, cap * (size_t)N * N));
+    if (!s_level) FM_TRY(ensure(ctx, &ctx->d_K, &ctx->K_capacity, cap * (size_t)N * N));
     FM_TRY(ensure(ctx, &ctx->d_q, &ctx->q_capacity, 2 * cap));
     for (uint64_t off = 0; off < n; off += cap) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(cap, n - off);
         if (shift < 0) {
-            FM_TRY(mc_points(ctx, (uint32_t)level, first + off, cnt, (uint32_t)M, ctx->d_xi, stream));
+            FM_TRY(mc_points(ctx, stream_level, first + off, cnt, (uint32_t)M, ctx->d_xi, stream));
         } else {
-            FM_TRY(sobol_points(ctx, (uint32_t)level, (uint32_t)M, first + off, cnt, (uint32_t)shift, 1,
-                                nullptr, ctx->d_xi, stream));
+            FM_TRY(sobol_points(ctx, stream_level, (uint32_t)M, first + off, cnt, (uint32_t)shift, 1, nullptr,
+                                ctx->d_xi, stream));
         }
-        FM_TRY(kl_field_batch(ctx, level, cnt, ctx->d_xi, ctx->d_K, stream));
         double* qf = ctx->d_q;
         double* qc = ctx->d_q + cap;
-        FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, nullptr, st));
-        if (d_sums) FM_TRY(level_sums_add(ctx, cnt, qf, qc, level > 0, d_sums, st));
+        if (s_level) {
+            // the surrogate level: Y = S(xi)
+            FM_TRY(surrogate_eval_impl(ctx, cnt, ctx->d_xi, qf, st));
+        } else {
+            FM_TRY(kl_field_batch(ctx, level, cnt, ctx->d_xi, ctx->d_K, stream));
+            FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, nullptr, st));
+            // level 0 with the surrogate: Y = Q_0 - S(xi), S in the Q^c slot
+            if (with_s) FM_TRY(surrogate_eval_impl(ctx, cnt, ctx->d_xi, qc, st));
+        }
+        if (d_sums) FM_TRY(level_sums_add(ctx, cnt, qf, qc, (level > 0 || (with_s && !s_level)) ? 1 : 0, d_sums, st));
         if (d_qf) FM_CUDA_TRY(ctx, cudaMemcpyAsync(d_qf + off, qf, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (d_qc) FM_CUDA_TRY(ctx, cudaMemcpyAsync(d_qc + off, qc, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
@@ -173,23 +184,37 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
     FM_CHECK_ARG(ctx, opts->n_pilot >= 2, "mlmc_estimate: n_pilot must be >= 2");
     FM_CHECK_ARG(ctx, !opts->qmc || ctx->cfg.n_shifts >= 2, "mlmc_estimate: QMC needs n_shifts >= 2");
     const auto t0 = std::chrono::steady_clock::now();
-    const int L = ctx->cfg.n_levels - 1;
+    FM_CHECK_ARG(ctx, !opts->surrogate || (ctx->mlp && opts->surrogate_cost > 0),
+                 "mlmc_estimate: the surrogate level needs a trained network and surrogate_cost > 0");
+    // Extended levels e = 0 .. L_e: with the surrogate, e = 0 is the S level
+    // and e = l + 1 MLMC level l; without it e = l.
+    const int off = opts->surrogate ? 1 : 0;
+    const int Lr = ctx->cfg.n_levels - 1;
+    const int L = Lr + off;
     const int R = opts->qmc ? ctx->cfg.n_shifts : 1;
     const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 100;
     const size_t cells = (size_t)(L + 1) * R;
     std::vector<fm_level_sums> h(cells);
     FM_CUDA_TRY(ctx, cudaMemset(ctx->d_sums, 0, cells * sizeof(fm_level_sums)));
-    double C[FM_MAX_LEVELS];
-    for (int l = 0; l <= L; ++l) {
-        const double n = grid_of_level(ctx, l);
-        C[l] = n * n * 4.0 / 3.0;
+    double C[FM_MAX_LEVELS + 1];
+    for (int e = 0; e <= L; ++e) {
+        const double n = grid_of_level(ctx, std::max(0, e - off));
+        C[e] = n * n * 4.0 / 3.0;
     }
+    if (off) C[0] *= opts->surrogate_cost;   // S-level cost relative to a level-0 sample
     std::memset(out, 0, sizeof(*out));
-    int64_t N[FM_MAX_LEVELS] = {};
-    int64_t dN[FM_MAX_LEVELS];
+    int64_t N[FM_MAX_LEVELS + 1] = {};
+    int64_t dN[FM_MAX_LEVELS + 1];
     for (int l = 0; l <= L; ++l) dN[l] = opts->n_pilot;
-    double mean[FM_MAX_LEVELS] = {}, var[FM_MAX_LEVELS] = {};
+    double mean[FM_MAX_LEVELS + 1] = {}, var[FM_MAX_LEVELS + 1] = {};
     int rounds = 0;
+    const int saved_on = ctx->surrogate_on;
+    ctx->surrogate_on = opts->surrogate ? 1 : 0;
+    struct Restore {
+        fm_ctx* c;
+        int v;
+        ~Restore() { c->surrogate_on = v; }
+    } restore{ctx, saved_on};
 
     auto refresh = [&]() -> fm_status {
         FM_TRY(fm_sync(ctx));
@@ -221,7 +246,7 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
 
     auto run = [&](int l, int64_t first, int64_t cnt) -> fm_status {
         for (int r = 0; r < R; ++r)
-            FM_TRY(mlmc_sample_level(ctx, l, (uint64_t)first, (uint32_t)cnt, opts->qmc ? r : -1,
+            FM_TRY(mlmc_sample_level(ctx, l - off, (uint64_t)first, (uint32_t)cnt, opts->qmc ? r : -1,
                                      ctx->d_sums + (size_t)l * R + r, nullptr, nullptr, nullptr));
         return FM_OK;
     };
@@ -283,17 +308,22 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
         out->var_estimator = v;
     }
     double est = 0.0;
-    for (int l = 0; l <= L; ++l) {
-        est += mean[l];
-        out->mean[l] = mean[l];
-        out->var[l] = var[l];
-        out->N[l] = N[l];
+    for (int e = 0; e <= L; ++e) est += mean[e];
+    for (int l = 0; l <= Lr; ++l) {
+        out->mean[l] = mean[l + off];
+        out->var[l] = var[l + off];
+        out->N[l] = N[l + off];
+    }
+    if (off) {
+        out->mean_s = mean[0];
+        out->var_s = var[0];
+        out->N_s = N[0];
     }
     out->estimate = est;
-    out->alpha = fit_rate(mean, L);
-    out->beta = fit_rate(var, L);
+    out->alpha = fit_rate(out->mean, Lr);
+    out->beta = fit_rate(out->var, Lr);
     out->bias = (std::isfinite(out->alpha) && out->alpha > 0)
-                    ? std::fabs(mean[L]) / (std::pow(2.0, out->alpha) - 1.0) : NAN;
+                    ? std::fabs(out->mean[Lr]) / (std::pow(2.0, out->alpha) - 1.0) : NAN;
     out->rounds = rounds;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return FM_OK;

@@ -1,0 +1,687 @@
+// Surrogate control-variate level: an MLP S(xi) = mu + sd * f(xi), f a
+// 4-layer perceptron M -> 256 -> 256 -> 256 -> 1 with GELU, trained by MSE
+// and Adam on outflux samples the method itself produces, and used as one
+// more estimator level below the coarsest grid:
+//   E[Q_L] = E[S] + E[Q_0 - S] + sum_{l>=1} E[Q_l - Q_(l-1)]
+// (unbiased for any S; a good S lowers the variance of Q_0 - S).
+//
+// Every hidden-layer contraction runs on the tcgen05 tensor cores: BF16
+// operands staged by TMA (128-byte swizzle), FP32 accumulation in TMEM, and
+// fused epilogues: forward bias + GELU writing the next layer's BF16 operand
+// both row-major (next forward GEMM) and transposed (weight-gradient GEMM);
+// backward GELU' writing the BF16 pre-activation gradient both ways; weight
+// gradients in FP32.  The output layer (256 -> 1), bias gradients and Adam
+// are small FP32 kernels.  Operands are BF16 exactly where the FP64 oracle
+// rounds: weights, input, hidden activations, pre-activation gradients.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+#include <random>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace fm {
+
+constexpr int kH = 256;         // hidden width
+constexpr int kGm = 128;        // GEMM tile rows (MMA M)
+constexpr int kGk = 64;         // K per stage
+constexpr int kGStages = 2;
+constexpr int kTrainBatch = 256;
+constexpr int kEvalChunk = 1 << 16;
+
+enum EpiKind { kEpiFwdGelu = 0, kEpiBwdGelu = 1, kEpiF32 = 2 };
+
+struct EpiArgs {
+    int M, N;                       // valid rows / columns of D
+    const float* bias;              // forward: [N]
+    float* Z;                       // forward: pre-activation out; backward: pre-activation in
+    int ldz;
+    __nv_bfloat16* H;               // BF16 out, row-major [M][ldh]
+    int ldh;
+    __nv_bfloat16* HT;              // BF16 out, transposed [N][ldt] (nullable)
+    int ldt;
+    float* F;                       // FP32 out [M][ldf]
+    int ldf;
+};
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// D[m][n] = sum_k A[m][k] B[n][k]: A [M][K] and B [N][K] BF16 K-major, one
+// 128 x BN tile per CTA, then the EPI epilogue on D.
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int kblocks,
+                   EpiArgs e, int* __restrict__ err) {
+    constexpr uint32_t kA = kGm * kGk * 2, kB = BN * kGk * 2;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    uint8_t* base = smem_raw + ((1024 - (raw & 1023)) & 1023);
+    uint8_t* sA = base;
+    uint8_t* sB = base + kGStages * kA;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kGStages * kB);
+    uint64_t* empty = full + kGStages;
+    uint64_t* done = empty + kGStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kGm, n0 = blockIdx.y * BN;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kGStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        tc::prefetch_tensormap(&mapA);
+        tc::prefetch_tensormap(&mapB);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, BN);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int st = kb % kGStages, round = kb / kGStages;
+            if (round > 0 && !tc::mbar_wait(&empty[st], (round - 1) & 1, err)) break;
+            tc::mbar_arrive_expect_tx(&full[st], kA + kB);
+            tc::tma_load_2d(sA + st * kA, &mapA, &full[st], kb * kGk, m0);
+            tc::tma_load_2d(sB + st * kB, &mapB, &full[st], kb * kGk, n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kGm, BN);
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int st = kb % kGStages, round = kb / kGStages;
+            if (!tc::mbar_wait(&full[st], round & 1, err)) break;
+            tc::fence_after_sync();
+            const uint32_t a = tc::smem_u32(sA + st * kA), b = tc::smem_u32(sB + st * kB);
+#pragma unroll
+            for (int j = 0; j < kGk / 16; ++j)
+                tc::mma_bf16(tmem, tc::sdesc_kmajor_sw128(a + 32 * j), tc::sdesc_kmajor_sw128(b + 32 * j), idesc,
+                             (kb | j) != 0);
+            tc::mma_commit(&empty[st]);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait(done, 0, err);
+    __syncwarp();
+    tc::fence_after_sync();
+    if (ok) {
+        const int r = m0 + warp * 32 + lane;
+        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int chunk = 0; chunk < BN / 32; ++chunk) {
+            uint32_t v[32];
+            tc::tmem_ld_32x32b_x32(row + chunk * 32, v);
+            if (r >= e.M) continue;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int c = n0 + chunk * 32 + i;
+                if (c >= e.N) continue;
+                const float acc = __uint_as_float(v[i]);
+                if (EPI == kEpiFwdGelu) {
+                    const float z = acc + e.bias[c];
+                    if (e.Z) e.Z[(size_t)r * e.ldz + c] = z;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
+                    e.H[(size_t)r * e.ldh + c] = h;
+                    if (e.HT) e.HT[(size_t)c * e.ldt + r] = h;
+                } else if (EPI == kEpiBwdGelu) {
+                    const __nv_bfloat16 d = __float2bfloat16_rn(acc * gelu_grad_f(e.Z[(size_t)r * e.ldz + c]));
+                    e.H[(size_t)r * e.ldh + c] = d;
+                    if (e.HT) e.HT[(size_t)c * e.ldt + r] = d;
+                } else {
+                    e.F[(size_t)r * e.ldf + c] = acc;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, BN);
+}
+
+template <int BN>
+constexpr size_t gemm_smem() {
+    return 1024 + kGStages * ((size_t)kGm * kGk * 2 + (size_t)BN * kGk * 2) + 256;
+}
+
+// ------------------------------------------------------------------ small kernels
+// x rows idx[b] of xi (FP64 [*][M]) -> BF16 X [B][D] (zero padded) and XT [D][B].
+__global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, const int32_t* __restrict__ idx,
+                           __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ XT) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * D) return;
+    const int b = t / D, k = t % D;
+    const size_t row = idx ? (size_t)idx[b] : (size_t)b;
+    const __nv_bfloat16 v = __float2bfloat16_rn((float)(k < M ? xi[row * M + k] : 0.0));
+    X[(size_t)b * D + k] = v;
+    if (XT) XT[(size_t)k * B + b] = v;
+}
+
+// out[b] = H3[b] . w4 + b4 (FP32); training: dout[b] = 2 (out[b] - t[b]) / B.
+__global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __nv_bfloat16* __restrict__ w4,
+                          const float* __restrict__ b4, const float* __restrict__ t, float* __restrict__ out,
+                          float* __restrict__ dout, float* __restrict__ sq) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float acc = 0.0f;
+    for (int j = lane; j < kH; j += 32)
+        acc += __bfloat162float(H3[(size_t)b * kH + j]) * __bfloat162float(w4[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        const float o = acc + b4[0];
+        out[b] = o;
+        if (t) {
+            const float d = o - t[b];
+            dout[b] = 2.0f * d / (float)B;
+            sq[b] = d * d;
+        }
+    }
+}
+
+// Output layer backward: dZ3 = bf16((dout w4) * gelu'(Z3)) row-major and transposed.
+__global__ void k_mlp_out_back(int B, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ w4,
+                               const float* __restrict__ Z3, __nv_bfloat16* __restrict__ dZ,
+                               __nv_bfloat16* __restrict__ dZT) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * kH) return;
+    const int b = t / kH, j = t % kH;
+    const float d = dout[b] * __bfloat162float(w4[j]) * gelu_grad_f(Z3[t]);
+    const __nv_bfloat16 v = __float2bfloat16_rn(d);
+    dZ[t] = v;
+    dZT[(size_t)j * B + b] = v;
+}
+
+// gW4[j] = sum_b dout[b] H3[b][j], gb4 = sum_b dout[b] (one thread per output, fixed order).
+__global__ void k_mlp_out_grad(int B, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ H3,
+                               float* __restrict__ gw4, float* __restrict__ gb4) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > kH) return;
+    float acc = 0.0f;
+    for (int b = 0; b < B; ++b) acc += dout[b] * (j < kH ? __bfloat162float(H3[(size_t)b * kH + j]) : 1.0f);
+    if (j < kH) gw4[j] = acc;
+    else gb4[0] = acc;
+}
+
+// gb[j] = sum_b dZT[j][b] (the BF16 gradients the GEMMs use).
+__global__ void k_bias_grad(int N, int B, const __nv_bfloat16* __restrict__ dZT, float* __restrict__ gb) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    float acc = 0.0f;
+    for (int b = 0; b < B; ++b) acc += __bfloat162float(dZT[(size_t)j * B + b]);
+    gb[j] = acc;
+}
+
+// Adam (Kingma & Ba) on FP32 master parameters, then the BF16 operand copies.
+__global__ void k_adam(size_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float gt = g[t];
+    const float mt = b1 * m[t] + (1.0f - b1) * gt;
+    const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
+    m[t] = mt;
+    v[t] = vt;
+    p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+}
+
+// W [rows][cols] FP32 -> BF16 [rows][ld] (zero padded) and, if WT, [cols][rows].
+__global__ void k_weight_bf16(int rows, int cols, int ld, const float* __restrict__ W, __nv_bfloat16* __restrict__ Wb,
+                              __nv_bfloat16* __restrict__ WT) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * ld) return;
+    const int r = t / ld, c = t % ld;
+    const __nv_bfloat16 v = __float2bfloat16_rn(c < cols ? W[(size_t)r * cols + c] : 0.0f);
+    Wb[t] = v;
+    if (WT && c < cols) WT[(size_t)c * rows + r] = v;
+}
+
+__global__ void k_gather_targets(int B, const float* __restrict__ src, const int32_t* __restrict__ idx,
+                                 float* __restrict__ t) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) t[b] = src[idx[b]];
+}
+
+__global__ void k_surrogate_value(int n, const float* __restrict__ out, double mu, double sd, double* __restrict__ s) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) s[t] = mu + sd * (double)out[t];
+}
+
+// ------------------------------------------------------------------ host state
+static unsigned nb(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+struct MlpState {
+    bool ready = false;
+    int M = 0, D = 0;                  // KL modes, padded input width
+    size_t np = 0;                     // FP32 parameters
+    size_t off[8] = {};                // W1 b1 W2 b2 W3 b3 w4 b4
+    float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2T = nullptr, *W3T = nullptr, *w4b = nullptr;
+    // training batch
+    __nv_bfloat16 *X = nullptr, *XT = nullptr, *H[3] = {}, *HT[3] = {}, *dZ[3] = {}, *dZT[3] = {};
+    float *Z[3] = {}, *t = nullptr, *out = nullptr, *dout = nullptr, *sq = nullptr;
+    int32_t* idx = nullptr;
+    CUtensorMap mX, mW1, mW2, mW3, mH1, mH2, mW2T, mW3T, mdZ2, mdZ3, mdZ1T_A, mdZ2T_A, mdZ3T_A, mXT_B, mH1T_B, mH2T_B;
+    // inference
+    __nv_bfloat16 *eX = nullptr, *eH[3] = {};
+    float* eout = nullptr;
+    CUtensorMap meX, meH1, meH2;
+    double mu = 0.0, sd = 1.0;
+    int adam_t = 0;
+    int* err = nullptr;
+};
+
+static MlpState* state(fm_ctx* ctx) { return reinterpret_cast<MlpState*>(ctx->mlp); }
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn_mlp() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// BF16 [rows][K] K-major, box (64 x box_rows), 128-byte swizzle.
+static bool map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows) {
+    auto fn = encode_fn_mlp();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {K, rows};
+    cuuint64_t strides[1] = {K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kGk, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int EPI>
+static void gemm(fm_ctx* ctx, const CUtensorMap& A, const CUtensorMap& B, int M, int N, int K, const EpiArgs& e,
+                 cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_bf16_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemm_smem<BN>());
+        attr = true;
+    }
+    dim3 grid((M + kGm - 1) / kGm, (N + BN - 1) / BN);
+    FM_TIMED(ctx, kFamMlp, st, 2.0 * ((double)M * K + (double)N * K) + 4.0 * (double)M * N,
+             2.0 * (double)M * N * K,
+             k_gemm_bf16_tc<BN, EPI><<<grid, 128, gemm_smem<BN>(), st>>>(A, B, K / kGk, e, state(ctx)->err));
+}
+
+static fm_status mlp_alloc(fm_ctx* ctx) {
+    if (ctx->mlp) return FM_OK;
+    MlpState* S = new MlpState();
+    ctx->mlp = S;
+    // inputs padded to a multiple of 128 so the weight-gradient GEMM's N tile fits
+    const int M = ctx->cfg.M, D = (M + 127) / 128 * 128, B = kTrainBatch;
+    S->M = M;
+    S->D = D;
+    size_t o = 0;
+    const size_t sizes[8] = {(size_t)kH * M, kH, (size_t)kH * kH, kH, (size_t)kH * kH, kH, kH, 1};
+    for (int i = 0; i < 8; ++i) {
+        S->off[i] = o;
+        o += sizes[i];
+    }
+    S->np = o;
+    bool ok = true;
+    auto al = [&](void** p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+        if (ok) cudaMemset(*p, 0, bytes);
+    };
+    al((void**)&S->P, o * 4);
+    al((void**)&S->G, o * 4);
+    al((void**)&S->Am, o * 4);
+    al((void**)&S->Av, o * 4);
+    al((void**)&S->W1b, (size_t)kH * D * 2);
+    al((void**)&S->W2b, (size_t)kH * kH * 2);
+    al((void**)&S->W3b, (size_t)kH * kH * 2);
+    al((void**)&S->W2T, (size_t)kH * kH * 2);
+    al((void**)&S->W3T, (size_t)kH * kH * 2);
+    al((void**)&S->w4b, (size_t)kH * 2);
+    al((void**)&S->X, (size_t)B * D * 2);
+    al((void**)&S->XT, (size_t)D * B * 2);
+    for (int l = 0; l < 3; ++l) {
+        al((void**)&S->H[l], (size_t)B * kH * 2);
+        al((void**)&S->HT[l], (size_t)kH * B * 2);
+        al((void**)&S->dZ[l], (size_t)B * kH * 2);
+        al((void**)&S->dZT[l], (size_t)kH * B * 2);
+        al((void**)&S->Z[l], (size_t)B * kH * 4);
+        al((void**)&S->eH[l], (size_t)kEvalChunk * kH * 2);
+    }
+    al((void**)&S->t, B * 4);
+    al((void**)&S->out, B * 4);
+    al((void**)&S->dout, B * 4);
+    al((void**)&S->sq, B * 4);
+    al((void**)&S->idx, B * 4);
+    al((void**)&S->eX, (size_t)kEvalChunk * D * 2);
+    al((void**)&S->eout, (size_t)kEvalChunk * 4);
+    al((void**)&S->err, 4);
+    if (!ok) {
+        set_error(ctx, "surrogate: device allocation failed");
+        return FM_ENOMEM;
+    }
+    // A operands (rows = M tile of 128) and B operands (rows = N tile)
+    ok = map_bf16(&S->mX, S->X, B, D, kGm) && map_bf16(&S->mW1, S->W1b, kH, D, 256) &&
+         map_bf16(&S->mH1, S->H[0], B, kH, kGm) && map_bf16(&S->mW2, S->W2b, kH, kH, 256) &&
+         map_bf16(&S->mH2, S->H[1], B, kH, kGm) && map_bf16(&S->mW3, S->W3b, kH, kH, 256) &&
+         map_bf16(&S->mW2T, S->W2T, kH, kH, 256) && map_bf16(&S->mW3T, S->W3T, kH, kH, 256) &&
+         map_bf16(&S->mdZ3, S->dZ[2], B, kH, kGm) && map_bf16(&S->mdZ2, S->dZ[1], B, kH, kGm) &&
+         map_bf16(&S->mdZ3T_A, S->dZT[2], kH, B, kGm) && map_bf16(&S->mdZ2T_A, S->dZT[1], kH, B, kGm) &&
+         map_bf16(&S->mdZ1T_A, S->dZT[0], kH, B, kGm) && map_bf16(&S->mXT_B, S->XT, D, B, D >= 256 ? 256 : 128) &&
+         map_bf16(&S->mH1T_B, S->HT[0], kH, B, 256) && map_bf16(&S->mH2T_B, S->HT[1], kH, B, 256) &&
+         map_bf16(&S->meX, S->eX, kEvalChunk, D, kGm) && map_bf16(&S->meH1, S->eH[0], kEvalChunk, kH, kGm) &&
+         map_bf16(&S->meH2, S->eH[1], kEvalChunk, kH, kGm);
+    if (!ok) {
+        set_error(ctx, "surrogate: cuTensorMapEncodeTiled failed");
+        return FM_ECUDA;
+    }
+    return FM_OK;
+}
+
+// BF16 operand copies of the FP32 master parameters.
+static void refresh_bf16(fm_ctx* ctx, cudaStream_t st) {
+    MlpState* S = state(ctx);
+    const int M = S->M, D = S->D;
+    k_weight_bf16<<<nb((size_t)kH * D), 256, 0, st>>>(kH, M, D, S->P + S->off[0], S->W1b, nullptr);
+    k_weight_bf16<<<nb((size_t)kH * kH), 256, 0, st>>>(kH, kH, kH, S->P + S->off[2], S->W2b, S->W2T);
+    k_weight_bf16<<<nb((size_t)kH * kH), 256, 0, st>>>(kH, kH, kH, S->P + S->off[4], S->W3b, S->W3T);
+    k_weight_bf16<<<nb(kH), 256, 0, st>>>(1, kH, kH, S->P + S->off[6], S->w4b, nullptr);
+}
+
+// Forward + backward of one batch of B = 256 rows already in S->X / S->XT / S->t.
+static void train_step_grads(fm_ctx* ctx, cudaStream_t st) {
+    MlpState* S = state(ctx);
+    const int B = kTrainBatch, D = S->D;
+    EpiArgs e{};
+    // forward
+    e = EpiArgs{B, kH, S->P + S->off[1], S->Z[0], kH, S->H[0], kH, S->HT[0], B, nullptr, 0};
+    gemm<256, kEpiFwdGelu>(ctx, S->mX, S->mW1, B, kH, D, e, st);
+    e = EpiArgs{B, kH, S->P + S->off[3], S->Z[1], kH, S->H[1], kH, S->HT[1], B, nullptr, 0};
+    gemm<256, kEpiFwdGelu>(ctx, S->mH1, S->mW2, B, kH, kH, e, st);
+    e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], B, nullptr, 0};
+    gemm<256, kEpiFwdGelu>(ctx, S->mH2, S->mW3, B, kH, kH, e, st);
+    k_mlp_out<<<nb((size_t)B * 32), 256, 0, st>>>(B, S->H[2], S->w4b, S->P + S->off[7], S->t, S->out, S->dout, S->sq);
+    // backward
+    k_mlp_out_grad<<<nb(kH + 1), 256, 0, st>>>(B, S->dout, S->H[2], S->G + S->off[6], S->G + S->off[7]);
+    k_mlp_out_back<<<nb((size_t)B * kH), 256, 0, st>>>(B, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
+    // layer 3: dW3 = dZ3^T H2, db3, dZ2 = (dZ3 W3) * gelu'(Z2)
+    e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[4], kH};
+    gemm<256, kEpiF32>(ctx, S->mdZ3T_A, S->mH2T_B, kH, kH, B, e, st);
+    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[2], S->G + S->off[5]);
+    e = EpiArgs{B, kH, nullptr, S->Z[1], kH, S->dZ[1], kH, S->dZT[1], B, nullptr, 0};
+    gemm<256, kEpiBwdGelu>(ctx, S->mdZ3, S->mW3T, B, kH, kH, e, st);
+    // layer 2
+    e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[2], kH};
+    gemm<256, kEpiF32>(ctx, S->mdZ2T_A, S->mH1T_B, kH, kH, B, e, st);
+    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[1], S->G + S->off[3]);
+    e = EpiArgs{B, kH, nullptr, S->Z[0], kH, S->dZ[0], kH, S->dZT[0], B, nullptr, 0};
+    gemm<256, kEpiBwdGelu>(ctx, S->mdZ2, S->mW2T, B, kH, kH, e, st);
+    // layer 1: dW1 = dZ1^T X (N = D input columns; the FP32 gradient keeps the M real ones)
+    e = EpiArgs{kH, S->M, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[0], S->M};
+    if (D >= 256) gemm<256, kEpiF32>(ctx, S->mdZ1T_A, S->mXT_B, kH, D, B, e, st);
+    else gemm<128, kEpiF32>(ctx, S->mdZ1T_A, S->mXT_B, kH, D, B, e, st);
+    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[0], S->G + S->off[1]);
+}
+
+// Forward of n rows of xi (FP64 [n][M]) into S->eout, chunked.
+static void eval_forward(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st) {
+    MlpState* S = state(ctx);
+    const int D = S->D;
+    for (uint32_t o = 0; o < n; o += kEvalChunk) {
+        const int cnt = (int)std::min<uint32_t>(kEvalChunk, n - o);
+        k_gather_x<<<nb((size_t)cnt * D), 256, 0, st>>>(cnt, S->M, D, d_xi + (size_t)o * S->M, nullptr, S->eX, nullptr);
+        EpiArgs e{cnt, kH, S->P + S->off[1], nullptr, 0, S->eH[0], kH, nullptr, 0, nullptr, 0};
+        gemm<256, kEpiFwdGelu>(ctx, S->meX, S->mW1, cnt, kH, D, e, st);
+        e = EpiArgs{cnt, kH, S->P + S->off[3], nullptr, 0, S->eH[1], kH, nullptr, 0, nullptr, 0};
+        gemm<256, kEpiFwdGelu>(ctx, S->meH1, S->mW2, cnt, kH, kH, e, st);
+        e = EpiArgs{cnt, kH, S->P + S->off[5], nullptr, 0, S->eH[2], kH, nullptr, 0, nullptr, 0};
+        gemm<256, kEpiFwdGelu>(ctx, S->meH2, S->mW3, cnt, kH, kH, e, st);
+        k_mlp_out<<<nb((size_t)cnt * 32), 256, 0, st>>>(cnt, S->eH[2], S->w4b, S->P + S->off[7], nullptr, S->eout,
+                                                        nullptr, nullptr);
+        k_surrogate_value<<<nb(cnt), 256, 0, st>>>(cnt, S->eout, S->mu, S->sd, d_s + o);
+    }
+}
+
+fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st) {
+    FM_CHECK_ARG(ctx, ctx->mlp && state(ctx)->ready, "surrogate: no trained or installed network");
+    if (n == 0) return FM_OK;
+    eval_forward(ctx, n, d_xi, d_s, st);
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
+}
+
+int surrogate_err_flag(const fm_ctx* ctx) {
+    if (!ctx->mlp) return 0;
+    int e = 0;
+    cudaMemcpy(&e, reinterpret_cast<MlpState*>(ctx->mlp)->err, sizeof(int), cudaMemcpyDeviceToHost);
+    return e;
+}
+
+void mlp_free(fm_ctx* ctx) {
+    MlpState* S = state(ctx);
+    if (!S) return;
+    void* ptrs[] = {S->P, S->G, S->Am, S->Av, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b, S->X, S->XT,
+                    S->t, S->out, S->dout, S->sq, S->idx, S->eX, S->eout, S->err};
+    for (void* p : ptrs) cudaFree(p);
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(S->H[l]); cudaFree(S->HT[l]); cudaFree(S->dZ[l]); cudaFree(S->dZT[l]); cudaFree(S->Z[l]);
+        cudaFree(S->eH[l]);
+    }
+    delete S;
+    ctx->mlp = nullptr;
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" fm_status surrogate_params(fm_ctx* ctx, float* host_params, int32_t set) {
+    FM_CHECK_ARG(ctx, ctx != nullptr && host_params != nullptr, "surrogate_params: null argument");
+    FM_TRY(mlp_alloc(ctx));
+    MlpState* S = state(ctx);
+    if (set) {
+        FM_CUDA_TRY(ctx, cudaMemcpy(S->P, host_params, S->np * 4, cudaMemcpyHostToDevice));
+        refresh_bf16(ctx, nullptr);
+        FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+        S->ready = true;
+    } else {
+        FM_CUDA_TRY(ctx, cudaMemcpy(host_params, S->P, S->np * 4, cudaMemcpyDeviceToHost));
+    }
+    return FM_OK;
+}
+
+extern "C" int64_t surrogate_param_count(const fm_ctx* ctx) {
+    if (!ctx) return -1;
+    const int64_t M = ctx->cfg.M;
+    return kH * M + kH + 2 * ((int64_t)kH * kH + kH) + kH + 1;
+}
+
+extern "C" fm_status surrogate_set_scale(fm_ctx* ctx, double mu, double sd) {
+    FM_CHECK_ARG(ctx, ctx != nullptr && sd > 0, "surrogate_set_scale: bad argument");
+    FM_TRY(mlp_alloc(ctx));
+    state(ctx)->mu = mu;
+    state(ctx)->sd = sd;
+    return FM_OK;
+}
+
+extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const float* d_target, float* host_grads,
+                                         double* host_loss) {
+    FM_CHECK_ARG(ctx, ctx != nullptr && d_xi && d_target, "surrogate_loss_grad: null argument");
+    FM_TRY(mlp_alloc(ctx));
+    MlpState* S = state(ctx);
+    FM_CUDA_TRY(ctx, cudaMemset(S->err, 0, 4));
+    k_gather_x<<<nb((size_t)kTrainBatch * S->D), 256>>>(kTrainBatch, S->M, S->D, d_xi, nullptr, S->X, S->XT);
+    FM_CUDA_TRY(ctx, cudaMemcpy(S->t, d_target, kTrainBatch * 4, cudaMemcpyDeviceToDevice));
+    train_step_grads(ctx, nullptr);
+    FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    if (surrogate_err_flag(ctx)) {
+        set_error(ctx, "surrogate_loss_grad: a bounded tensor-core wait ran out");
+        return FM_ETIMEOUT;
+    }
+    if (host_grads) FM_CUDA_TRY(ctx, cudaMemcpy(host_grads, S->G, S->np * 4, cudaMemcpyDeviceToHost));
+    if (host_loss) {
+        std::vector<float> sq(kTrainBatch);
+        FM_CUDA_TRY(ctx, cudaMemcpy(sq.data(), S->sq, kTrainBatch * 4, cudaMemcpyDeviceToHost));
+        double l = 0.0;
+        for (float v : sq) l += v;
+        *host_loss = l / kTrainBatch;
+    }
+    return FM_OK;
+}
+
+extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* rep) {
+    FM_CHECK_ARG(ctx, ctx != nullptr && opts != nullptr, "surrogate_train: null argument");
+    FM_CHECK_ARG(ctx, ctx->basis_ready, "surrogate_train: no KL basis installed");
+    FM_CHECK_ARG(ctx, opts->n_train >= kTrainBatch && opts->epochs >= 1 && opts->lr > 0,
+                 "surrogate_train: need n_train >= 256, epochs >= 1, lr > 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    FM_TRY(mlp_alloc(ctx));
+    MlpState* S = state(ctx);
+    const int n = opts->n_train, M = ctx->cfg.M;
+    // training pairs (xi, Q_0) from the method: level-0 FMG solves on a stream of their own
+    double *xi = nullptr, *q = nullptr, *K = nullptr;
+    const int N0 = grid_of_level(ctx, 0);
+    FM_CUDA_TRY(ctx, cudaMalloc((void**)&xi, (size_t)n * M * 8));
+    FM_CUDA_TRY(ctx, cudaMalloc((void**)&q, (size_t)n * 8));
+    fm_status stt = FM_OK;
+    {
+        const uint32_t chunk = 65536;
+        if (cudaMalloc((void**)&K, (size_t)chunk * N0 * N0 * 8) != cudaSuccess) stt = FM_ENOMEM;
+        fm_solve_params prm{};
+        prm.pW = ctx->cfg.pW; prm.pE = ctx->cfg.pE; prm.n_coarsest = ctx->cfg.n_coarsest;
+        prm.nu0 = ctx->cfg.nu0; prm.nu1 = ctx->cfg.nu1; prm.nu2 = ctx->cfg.nu2;
+        prm.precision = ctx->cfg.precision; prm.converged = ctx->cfg.converged; prm.tol = ctx->cfg.tol;
+        prm.qtol = ctx->cfg.qtol; prm.max_cycles = ctx->cfg.max_cycles;
+        for (uint32_t o = 0; stt == FM_OK && o < (uint32_t)n; o += chunk) {
+            const uint32_t c = std::min<uint32_t>(chunk, n - o);
+            stt = mc_points(ctx, kSurrogateTrainStream, o, c, M, xi + (size_t)o * M, nullptr);
+            if (stt == FM_OK) stt = kl_field_batch(ctx, 0, c, xi + (size_t)o * M, K, nullptr);
+            if (stt == FM_OK) stt = fmg_solve_impl(ctx, N0, c, K, prm, q + o, nullptr, nullptr, nullptr, nullptr);
+        }
+    }
+    std::vector<double> hq(n);
+    if (stt == FM_OK && cudaMemcpy(hq.data(), q, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) stt = FM_ECUDA;
+    if (stt != FM_OK) {
+        cudaFree(xi); cudaFree(q); cudaFree(K);
+        return stt;
+    }
+    double mu = 0.0, var = 0.0;
+    for (double v : hq) mu += v;
+    mu /= n;
+    for (double v : hq) var += (v - mu) * (v - mu);
+    const double sd = std::sqrt(var / (n - 1));
+    S->mu = mu;
+    S->sd = sd > 0 ? sd : 1.0;
+    std::vector<float> ht(n);
+    for (int i = 0; i < n; ++i) ht[i] = (float)((hq[i] - mu) / S->sd);
+    float* tt = nullptr;
+    FM_CUDA_TRY(ctx, cudaMalloc((void**)&tt, (size_t)n * 4));
+    cudaMemcpy(tt, ht.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+    // initial parameters U(-1/sqrt(fan_in), 1/sqrt(fan_in)), Adam state zero
+    std::mt19937_64 gen(opts->seed);
+    std::uniform_real_distribution<double> uni(0.0, 1.0);
+    std::vector<float> hp(S->np);
+    const int fan[8] = {M, M, kH, kH, kH, kH, kH, kH};
+    for (int i = 0; i < 8; ++i) {
+        const size_t end = (i == 7) ? S->np : S->off[i + 1];
+        const double a = 1.0 / std::sqrt((double)fan[i]);
+        for (size_t k = S->off[i]; k < end; ++k) hp[k] = (float)((2.0 * uni(gen) - 1.0) * a);
+    }
+    cudaMemcpy(S->P, hp.data(), S->np * 4, cudaMemcpyHostToDevice);
+    cudaMemset(S->Am, 0, S->np * 4);
+    cudaMemset(S->Av, 0, S->np * 4);
+    cudaMemset(S->err, 0, 4);
+    S->adam_t = 0;
+    refresh_bf16(ctx, nullptr);
+    // epochs of shuffled mini-batches, cosine-decayed learning rate
+    const int steps_per_epoch = n / kTrainBatch;
+    const int total = steps_per_epoch * opts->epochs;
+    std::vector<int32_t> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    double first_loss = NAN, last_loss = NAN;
+    int step = 0;
+    for (int ep = 0; ep < opts->epochs; ++ep) {
+        std::shuffle(perm.begin(), perm.end(), gen);
+        int32_t* dperm = nullptr;
+        cudaMalloc((void**)&dperm, (size_t)n * 4);
+        cudaMemcpy(dperm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+        for (int sb = 0; sb < steps_per_epoch; ++sb, ++step) {
+            const int32_t* bidx = dperm + (size_t)sb * kTrainBatch;
+            k_gather_x<<<nb((size_t)kTrainBatch * S->D), 256>>>(kTrainBatch, M, S->D, xi, bidx, S->X, S->XT);
+            k_gather_targets<<<1, 256>>>(kTrainBatch, tt, bidx, S->t);
+            train_step_grads(ctx, nullptr);
+            const double lr = opts->lr * 0.5 * (1.0 + std::cos(M_PI * step / (double)total));
+            ++S->adam_t;
+            const float c1 = 1.0f - std::pow(0.9f, (float)S->adam_t), c2 = 1.0f - std::pow(0.999f, (float)S->adam_t);
+            k_adam<<<nb(S->np), 256>>>(S->np, S->P, S->Am, S->Av, S->G, (float)lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+            refresh_bf16(ctx, nullptr);
+            if (step == 0 || step == total - 1) {
+                std::vector<float> sq(kTrainBatch);
+                cudaMemcpy(sq.data(), S->sq, kTrainBatch * 4, cudaMemcpyDeviceToHost);
+                double l = 0.0;
+                for (float v : sq) l += v;
+                (step == 0 ? first_loss : last_loss) = l / kTrainBatch;
+            }
+        }
+        cudaFree(dperm);
+    }
+    cudaFree(tt);
+    cudaFree(K);
+    cudaFree(q);
+    FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    if (surrogate_err_flag(ctx)) {
+        cudaFree(xi);
+        set_error(ctx, "surrogate_train: a bounded tensor-core wait ran out");
+        return FM_ETIMEOUT;
+    }
+    S->ready = true;
+    // fit on the training set: correlation of S with Q_0
+    double* sv = nullptr;
+    cudaMalloc((void**)&sv, (size_t)n * 8);
+    eval_forward(ctx, n, xi, sv, nullptr);
+    std::vector<double> hs(n);
+    cudaMemcpy(hs.data(), sv, (size_t)n * 8, cudaMemcpyDeviceToHost);
+    cudaFree(sv);
+    cudaFree(xi);
+    double ms = 0.0, cov = 0.0, vs = 0.0, vr = 0.0;
+    for (int i = 0; i < n; ++i) ms += hs[i];
+    ms /= n;
+    for (int i = 0; i < n; ++i) {
+        cov += (hs[i] - ms) * (hq[i] - mu);
+        vs += (hs[i] - ms) * (hs[i] - ms);
+        vr += (hq[i] - hs[i]) * (hq[i] - hs[i]);
+    }
+    if (rep) {
+        rep->loss_first = first_loss;
+        rep->loss_last = last_loss;
+        rep->mu = mu;
+        rep->sd = S->sd;
+        rep->corr = cov / std::sqrt(vs * var + 1e-300);
+        rep->var_q = var / (n - 1);
+        rep->var_residual = vr / (n - 1);
+        rep->steps = total;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return FM_OK;
+}
+
+extern "C" fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_eval: null context");
+    FM_CHECK_ARG(ctx, n == 0 || (d_xi && d_s), "surrogate_eval: null pointer");
+    return surrogate_eval_impl(ctx, n, d_xi, d_s, as_stream(stream));
+}
