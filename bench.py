@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle's bounded timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64_converged", "fp64_fmg2"])
+    ap.add_argument("--form", default="mixed_surrogate",
+                    choices=["mixed_surrogate", "mixed", "fp64_converged", "fp64_fmg2"])
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     return ap.parse_args()
@@ -144,20 +145,66 @@ def oracle_level_seconds(wl, budget_s, converged):
     return np.array(per), cores, counts
 
 
+def oracle_surrogate_seconds(M, budget_s=4.0):
+    """Seconds of the oracle network (FP64, numpy) per S evaluation and per
+    training step (batch 256: loss, gradients, Adam), from a bounded sample."""
+    from oracle import mlp as omlp
+    r = W.rng(tag=900)
+    params = omlp.init_params(M, lambda n: r.uniform(size=n))
+    X = r.standard_normal((8192, M))
+    t0 = time.perf_counter()
+    omlp.forward(params, X, rounding=True)
+    per_eval = (time.perf_counter() - t0) / len(X)
+    opt = omlp.Adam(params, lr=1e-3)
+    t = r.standard_normal(256)
+    k, t0 = 0, time.perf_counter()
+    while k < 4 or (time.perf_counter() - t0 < budget_s / 2 and k < 64):
+        _, g = omlp.mse_loss_and_grad(params, X[:256], t, rounding=True)
+        params = opt.step(params, g)
+        k += 1
+    per_step = (time.perf_counter() - t0) / k
+    return per_eval, per_step, k
+
+
 # ------------------------------------------------------------------ native
 def flush_l2(buf):
     buf.fill_(1.0)
 
 
 FORMS = {
+    # the mixed form plus the surrogate control-variate level below 16x16; the
+    # network is trained inside every timed step on level-0 samples the
+    # solver produces (training data, training and estimate all timed)
+    "mixed_surrogate": dict(precision=1, converged=True, surrogate=True),
     # FP32 smoothing/transfers/coarsest solve inside FP64 iterative refinement
     # of the stages giving Q^c and Q^f, to ||r|| <= 1e-10 ||b||
-    "mixed": dict(precision=1, converged=True),
+    "mixed": dict(precision=1, converged=True, surrogate=False),
     # the same converged solves, every step in FP64
-    "fp64_converged": dict(precision=0, converged=True),
+    "fp64_converged": dict(precision=0, converged=True, surrogate=False),
     # the paper's fixed schedule: 2 V(2,2) cycles per FMG stage, FP64
-    "fp64_fmg2": dict(precision=0, converged=False),
+    "fp64_fmg2": dict(precision=0, converged=False, surrogate=False),
 }
+
+# surrogate training: 20480 (xi, Q_0) pairs, batch 1024, 40 epochs, Adam 6e-3 cosine
+SURROGATE_TRAIN = dict(n_train=20480, epochs=40, lr=6e-3, seed=7, batch=1024)
+
+
+def surrogate_cost(torch, ctx):
+    """Device seconds of one S-level sample over one level-0 sample."""
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+    sums = ctx.new_sums()
+    ns, n0 = 1 << 20, 1 << 16
+    t_s = timed(lambda: ctx.surrogate_eval_mc(12, 0, ns)) / ns
+    t_0 = timed(lambda: ctx.mlmc_sample_level(0, 0, n0, sums=sums[0])) / n0
+    return t_s / t_0
 
 
 def make_ctx(fm, wl, rank, form):
@@ -169,9 +216,21 @@ def make_ctx(fm, wl, rank, form):
 
 
 def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=False, clocks=None,
-                   dist=None):
+                   dist=None, form="mixed"):
+    sur = FORMS[form]["surrogate"]
+    cost = None
+    if sur:
+        ctx.surrogate_train(**SURROGATE_TRAIN)
+        cost = surrogate_cost(torch, ctx)
+
     def estimate():
-        return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+        if not sur:
+            return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+        rep = ctx.surrogate_train(**SURROGATE_TRAIN)
+        r = ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, surrogate=True, surrogate_cost=cost)
+        r["train"] = rep
+        r["surrogate_cost"] = cost
+        return r
 
     for _ in range(warmup):
         estimate()
@@ -224,7 +283,7 @@ def run_native(args, wl, eps):
     clocks = ClockSampler(local)
     times, results, prof, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
                                                profile=True, clocks=clocks,
-                                               dist=dist if world > 1 else None)
+                                               dist=dist if world > 1 else None, form=args.form)
     t_total = float(np.sum(times))
     if world > 1:
         t = torch.tensor([t_total], device="cuda")
@@ -239,10 +298,13 @@ def run_native(args, wl, eps):
             continue
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
-        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush)
+        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
+                                      form=form)
         others[form] = {"value": float(np.mean(ts)), "unit": "s",
                         "estimate": float(np.mean([r["estimate"] for r in rs])),
-                        "N_per_level": [int(x) for x in rs[-1]["N"]]}
+                        "var_estimator": float(np.mean([r["var_estimator"] for r in rs])),
+                        "N_per_level": [int(x) for x in rs[-1]["N"]],
+                        "V_per_level": [float(x) for x in rs[-1]["V"]]}
         c2.close()
 
     # end to end through the public API from pinned host memory: basis upload,
@@ -251,12 +313,18 @@ def run_native(args, wl, eps):
     ctx.kl_basis_get(B_host)
     ctx2 = make_ctx(fm, wl, rank, args.form)
     e2e_times, rounds = [], []
+    sur = FORMS[args.form]["surrogate"]
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush_l2(flush)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2.kl_basis_set_host_ptr(B_host.data_ptr())
-        r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+        if sur:
+            ctx2.surrogate_train(**SURROGATE_TRAIN)
+            r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, surrogate=True,
+                                   surrogate_cost=results[-1]["surrogate_cost"])
+        else:
+            r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
         e2e_times.append(time.perf_counter() - t0)
         rounds.append(r["rounds"])
     ctx2.close()
@@ -270,7 +338,7 @@ def run_native(args, wl, eps):
     ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "traffic": None, "peak_source": src}
-    if fam in ("kl_gemm_exp", "fmg_resident"):
+    if fam in ("kl_gemm_exp", "fmg_resident", "mlp_gemm"):
         roof["bound"] = "alu"
         roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is ALU/latency bound"
     roof["launches"] = st["launches"]
@@ -292,7 +360,7 @@ def run_native(args, wl, eps):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64" if FORMS[args.form]["precision"] == 1 else "f64",
+        "dtype": ("f32+f64" if FORMS[args.form]["precision"] == 1 else "f64") + ("+bf16" if sur else ""),
         "data": "synthetic (seeded Philox KL coefficients, KL basis built on the GPU)",
         "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
                    "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
@@ -303,6 +371,8 @@ def run_native(args, wl, eps):
         "estimate": float(np.mean(ests)),
         "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in results]))),
         "N_per_level": [int(x) for x in results[-1]["N"]],
+        "samples_per_s_per_level": [float(n / t) if t > 0 else None for n, t in
+                                    zip(results[-1]["N"], results[-1]["level_seconds"])],
         "other_forms": others,
         "roofline": roof,
         "kernel_families": families,
@@ -311,16 +381,39 @@ def run_native(args, wl, eps):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clk,
     }
+    if sur:
+        r = results[-1]
+        sr = {"train": {k: (float(v) if isinstance(v, float) else v) for k, v in r["train"].items()},
+              "surrogate_cost": r["surrogate_cost"], "N_s": int(r["N_s"]), "mean_s": r["mean_s"],
+              "var_s": r["var_s"], "var_q0_minus_s": float(r["V"][0]),
+              "seconds_s_level": r["seconds_s"]}
+        plain = others.get("mixed")
+        if plain:
+            sr["var_q0"] = plain["V_per_level"][0]
+            sr["variance_reduction_level0"] = plain["V_per_level"][0] / max(float(r["V"][0]), 1e-300)
+            sr["plain_estimate"] = plain["estimate"]
+            sr["plain_N_per_level"] = plain["N_per_level"]
+            sr["difference_in_sigmas"] = abs(out["estimate"] - plain["estimate"]) / np.sqrt(
+                np.mean([x["var_estimator"] for x in results]) + plain["var_estimator"])
+        out["surrogate"] = sr
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         conv = FORMS[args.form]["converged"]
         per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds, conv)
         N = results[-1]["N"]
         t_cpu = float(np.sum(per * N))
+        sample = ("oracle FMG-MLMC samples per level %s (%s) timed on %d threads; seconds per sample x "
+                  "the GPU run's N_l (extrapolated)" % (counts, "FP64 V-cycles to 1e-10" if conv
+                                                        else "2 V(2,2) per stage", cores))
+        if sur:
+            r = results[-1]
+            pe, ps, ks = oracle_surrogate_seconds(wl.M)
+            steps = int(r["train"]["steps"])
+            t_cpu += per[0] * SURROGATE_TRAIN["n_train"] + ps * steps + pe * (r["N_s"] + r["N"][0])
+            sample += ("; surrogate: %d training pairs at the level-0 rate, %d timed oracle training steps "
+                       "extrapolated to %d, 8192 timed oracle evaluations extrapolated to N_S + N_0"
+                       % (SURROGATE_TRAIN["n_train"], ks, steps))
         out["cpu_baseline"] = {"value": t_cpu, "unit": "s", "cores": cores, "kind": "oracle",
-                               "sample": "oracle FMG-MLMC samples per level %s (%s) timed on %d "
-                                         "threads; seconds per sample x the GPU run's N_l "
-                                         "(extrapolated)" % (counts, "FP64 V-cycles to 1e-10" if conv
-                                                             else "2 V(2,2) per stage", cores)}
+                               "sample": sample}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -362,7 +455,8 @@ def run_reference(args, wl, eps):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "eps": eps,
-                      "sampler": "mc", "form": args.form, "implementation": "FP64 CPU oracle"},
+                      "sampler": "mc", "form": args.form,
+                      "implementation": "FP64 CPU oracle, plain FMG-MLMC (no surrogate level)"},
            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                             "sample": "per step: a bounded batch per level timed on %d threads, "
                                       "extrapolated to the optimal N_l of eps" % cores},

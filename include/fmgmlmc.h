@@ -277,6 +277,8 @@ typedef struct {
     double seconds;                  /* wall time of the call */
     double mean_s, var_s;            /* surrogate level: mean(S), V[S] (or its level-estimate variance) */
     int64_t N_s;                     /* surrogate-level samples */
+    double level_seconds[FM_MAX_LEVELS]; /* device time spent sampling each level (CUDA events) */
+    double seconds_s;                /* device time spent on the surrogate level */
 } fm_result;
 
 /* The host controller (Algorithm 3 with the MC rule N_l = (2/eps^2)
@@ -305,6 +307,7 @@ typedef struct {
     int32_t epochs;
     double lr;            /* Adam step, cosine-decayed to 0 over the run */
     uint64_t seed;        /* parameter initialisation and shuffling */
+    int32_t batch;        /* mini-batch rows: a multiple of 128, at most 1024 (0: 256) */
 } fm_train_opts;
 
 typedef struct {
@@ -341,6 +344,16 @@ fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_repor
 
 /* d_s[s] = S(d_xi[s]) for n rows of FP64 KL coefficients [n][M]. */
 fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream);
+
+/* S for the MC samples first .. first+n-1 of Philox stream `stream_level`
+ * (the `level` argument of mc_points; the surrogate level draws from stream
+ * 12), evaluated from the samples' Philox words: u from the top 23 bits of
+ * each word, FP32 inverse normal, BF16 network input.  This is the map the
+ * estimator applies on both levels where S enters in MC mode, so S is the
+ * same function of the sample there.  d_s: device [n] FP64.  Asynchronous on
+ * `stream`; FM_EINVAL without an installed network. */
+fm_status surrogate_eval_mc(fm_ctx* ctx, uint32_t stream_level, uint64_t first, uint32_t n, double* d_s,
+                            void* stream);
 
 /* ---------------------------------------------------------------- profiling */
 

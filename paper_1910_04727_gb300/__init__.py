@@ -219,8 +219,8 @@ class Context:
                                                 g.ctypes.data_as(C.c_void_p), C.byref(loss)))
         return loss.value, g
 
-    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7):
-        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed)
+    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7, batch=256):
+        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed, batch)
         rep = _lib.FmTrainReport()
         self._check(self._L.surrogate_train(self._h, C.byref(opts), C.byref(rep)))
         return {f: getattr(rep, f) for f, _ in _lib.FmTrainReport._fields_}
@@ -228,6 +228,12 @@ class Context:
     def surrogate_eval(self, xi):
         s = torch.empty(xi.shape[0], dtype=torch.float64, device="cuda")
         self._check(self._L.surrogate_eval(self._h, xi.shape[0], _ptr(xi), _ptr(s), _stream()))
+        return s
+
+    def surrogate_eval_mc(self, stream_level, first, n):
+        """S for MC samples first..first+n-1 of a Philox stream, from the Philox words."""
+        s = torch.empty(n, dtype=torch.float64, device="cuda")
+        self._check(self._L.surrogate_eval_mc(self._h, stream_level, first, n, _ptr(s), _stream()))
         return s
 
     def surrogate_enable(self, on=True):
@@ -245,4 +251,5 @@ class Context:
                     means=np.array(res.mean[:L]), V=np.array(res.var[:L]),
                     N=np.array(res.N[:L]), alpha=res.alpha, beta=res.beta, bias=res.bias,
                     rounds=res.rounds, seconds=res.seconds, mean_s=res.mean_s, var_s=res.var_s,
-                    N_s=res.N_s)
+                    N_s=res.N_s, level_seconds=np.array(res.level_seconds[:L]),
+                    seconds_s=res.seconds_s)

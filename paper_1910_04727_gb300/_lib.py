@@ -24,7 +24,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
            "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static",
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
-           "surrogate_train", "surrogate_eval", "surrogate_enable"]
+           "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc"]
 
 
 class FmConfig(C.Structure):
@@ -60,7 +60,8 @@ class FmKernelStat(C.Structure):
 
 
 class FmTrainOpts(C.Structure):
-    _fields_ = [("n_train", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64)]
+    _fields_ = [("n_train", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
+                ("batch", C.c_int32)]
 
 
 class FmTrainReport(C.Structure):
@@ -74,7 +75,8 @@ class FmResult(C.Structure):
                 ("mean", C.c_double * FM_MAX_LEVELS), ("var", C.c_double * FM_MAX_LEVELS),
                 ("N", C.c_int64 * FM_MAX_LEVELS), ("alpha", C.c_double), ("beta", C.c_double),
                 ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double),
-                ("mean_s", C.c_double), ("var_s", C.c_double), ("N_s", C.c_int64)]
+                ("mean_s", C.c_double), ("var_s", C.c_double), ("N_s", C.c_int64),
+                ("level_seconds", C.c_double * FM_MAX_LEVELS), ("seconds_s", C.c_double)]
 
 
 _lib = None
@@ -116,6 +118,7 @@ def load(path=None):
         "surrogate_train": (I32, [P, C.POINTER(FmTrainOpts), C.POINTER(FmTrainReport)]),
         "surrogate_eval": (I32, [P, U32, P, P, P]),
         "surrogate_enable": (I32, [P, I32]),
+        "surrogate_eval_mc": (I32, [P, U32, U64, U32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

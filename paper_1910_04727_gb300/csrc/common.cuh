@@ -212,6 +212,10 @@ int kl_mode_of(const fm_ctx* ctx);
 constexpr uint32_t kSurrogateLevelStream = 12;   // Philox level id of the S-level samples
 constexpr uint32_t kSurrogateTrainStream = 13;   // Philox level id of the training samples
 fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st);
+// S for MC samples first .. first+n-1 of Philox stream `level`, from the
+// Philox words directly (FP32 inverse normal, BF16 input).
+fm_status surrogate_eval_mc_impl(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, double* d_s,
+                                 cudaStream_t st);
 int surrogate_err_flag(const fm_ctx* ctx);
 void mlp_free(fm_ctx* ctx);
 

@@ -146,29 +146,36 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
     const int N = grid_of_level(ctx, s_level ? 0 : level), M = ctx->cfg.M;
     const uint32_t stream_level = s_level ? kSurrogateLevelStream : (uint32_t)level;
     const fm_solve_params prm = solve_params(ctx);
-    const int64_t lim = s_level ? (int64_t)1 << 20 : std::min<int64_t>(batch_limit(ctx, N), (int64_t)65535 * 64);
+    // MC surrogate samples need no FP64 points: S is evaluated from the Philox words
+    const bool s_mc = s_level && shift < 0;
+    const int64_t lim = s_level ? (int64_t)1 << 22 : std::min<int64_t>(batch_limit(ctx, N), (int64_t)65535 * 64);
     const size_t cap = (size_t)std::min<int64_t>(lim, n);
-    FM_TRY(ensure(ctx, &ctx->d_xi, &ctx->xi_capacity, cap * M));
+    if (!s_mc) FM_TRY(ensure(ctx, &ctx->d_xi, &ctx->xi_capacity, cap * M));
     if (!s_level) FM_TRY(ensure(ctx, &ctx->d_K, &ctx->K_capacity, cap * (size_t)N * N));
     FM_TRY(ensure(ctx, &ctx->d_q, &ctx->q_capacity, 2 * cap));
     for (uint64_t off = 0; off < n; off += cap) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(cap, n - off);
-        if (shift < 0) {
-            FM_TRY(mc_points(ctx, stream_level, first + off, cnt, (uint32_t)M, ctx->d_xi, stream));
-        } else {
+        if (shift >= 0) {
             FM_TRY(sobol_points(ctx, stream_level, (uint32_t)M, first + off, cnt, (uint32_t)shift, 1, nullptr,
                                 ctx->d_xi, stream));
+        } else if (!s_mc) {
+            FM_TRY(mc_points(ctx, stream_level, first + off, cnt, (uint32_t)M, ctx->d_xi, stream));
         }
         double* qf = ctx->d_q;
         double* qc = ctx->d_q + cap;
+        // S(omega): from the Philox words of the sample for MC, from its QMC point otherwise
+        auto eval_s = [&](double* out) -> fm_status {
+            return shift < 0 ? surrogate_eval_mc_impl(ctx, stream_level, first + off, cnt, out, st)
+                             : surrogate_eval_impl(ctx, cnt, ctx->d_xi, out, st);
+        };
         if (s_level) {
-            // the surrogate level: Y = S(xi)
-            FM_TRY(surrogate_eval_impl(ctx, cnt, ctx->d_xi, qf, st));
+            // the surrogate level: Y = S
+            FM_TRY(eval_s(qf));
         } else {
             FM_TRY(kl_field_batch(ctx, level, cnt, ctx->d_xi, ctx->d_K, stream));
             FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, nullptr, st));
-            // level 0 with the surrogate: Y = Q_0 - S(xi), S in the Q^c slot
-            if (with_s) FM_TRY(surrogate_eval_impl(ctx, cnt, ctx->d_xi, qc, st));
+            // level 0 with the surrogate: Y = Q_0 - S, S in the Q^c slot
+            if (with_s) FM_TRY(eval_s(qc));
         }
         if (d_sums) FM_TRY(level_sums_add(ctx, cnt, qf, qc, (level > 0 || (with_s && !s_level)) ? 1 : 0, d_sums, st));
         if (d_qf) FM_CUDA_TRY(ctx, cudaMemcpyAsync(d_qf + off, qf, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -216,14 +223,47 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
         ~Restore() { c->surrogate_on = v; }
     } restore{ctx, saved_on};
 
+    // device time per extended level: an event pair around each level's
+    // sampling, read back at the next synchronisation
+    struct LevelTimer {
+        std::vector<cudaEvent_t> ev;
+        std::vector<int> lev;
+        size_t used = 0;
+        ~LevelTimer() {
+            for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        }
+    } lt;
+    double lsec[FM_MAX_LEVELS + 1] = {};
+    auto event = [&]() -> cudaEvent_t {
+        if (lt.used == lt.ev.size()) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            lt.ev.push_back(e);
+        }
+        return lt.ev[lt.used++];
+    };
+    auto collect = [&]() {
+        for (size_t i = 0; i + 1 < lt.used; i += 2) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, lt.ev[i], lt.ev[i + 1]) == cudaSuccess) lsec[lt.lev[i / 2]] += ms * 1e-3;
+        }
+        lt.used = 0;
+        lt.lev.clear();
+    };
+
     auto refresh = [&]() -> fm_status {
         FM_TRY(fm_sync(ctx));
+        collect();
         FM_CUDA_TRY(ctx, cudaMemcpy(h.data(), ctx->d_sums, cells * sizeof(fm_level_sums), cudaMemcpyDeviceToHost));
         for (int l = 0; l <= L; ++l) {
             if (!opts->qmc) {
                 const fm_level_sums& s = h[l];
                 const double n = s.count;
                 const double sy = fold(s.sum_y), sy2 = fold(s.sum_y2);
+                if (!std::isfinite(sy) || !std::isfinite(sy2)) {
+                    set_error(ctx, "mlmc_estimate: non-finite samples on level " + std::to_string(l));
+                    return FM_ENOTCONV;
+                }
                 mean[l] = sy / n;
                 var[l] = n > 1 ? std::max(0.0, (sy2 - sy * sy / n) / (n - 1)) : 0.0;
             } else {
@@ -232,6 +272,10 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
                 for (int r = 0; r < R; ++r) {
                     const fm_level_sums& s = h[(size_t)l * R + r];
                     m[r] = fold(s.sum_y) / s.count;
+                    if (!std::isfinite(m[r])) {
+                        set_error(ctx, "mlmc_estimate: non-finite samples on level " + std::to_string(l));
+                        return FM_ENOTCONV;
+                    }
                     mm += m[r];
                 }
                 mm /= R;
@@ -245,9 +289,13 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
     };
 
     auto run = [&](int l, int64_t first, int64_t cnt) -> fm_status {
+        cudaEvent_t e0 = event(), e1 = event();
+        lt.lev.push_back(l);
+        cudaEventRecord(e0, nullptr);
         for (int r = 0; r < R; ++r)
             FM_TRY(mlmc_sample_level(ctx, l - off, (uint64_t)first, (uint32_t)cnt, opts->qmc ? r : -1,
                                      ctx->d_sums + (size_t)l * R + r, nullptr, nullptr, nullptr));
+        cudaEventRecord(e1, nullptr);
         return FM_OK;
     };
 
@@ -314,6 +362,8 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
         out->var[l] = var[l + off];
         out->N[l] = N[l + off];
     }
+    for (int l = 0; l <= Lr; ++l) out->level_seconds[l] = lsec[l + off];
+    out->seconds_s = off ? lsec[0] : 0.0;
     if (off) {
         out->mean_s = mean[0];
         out->var_s = var[0];

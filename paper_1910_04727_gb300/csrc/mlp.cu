@@ -13,6 +13,10 @@
 // gradients in FP32.  The output layer (256 -> 1), bias gradients and Adam
 // are small FP32 kernels.  Operands are BF16 exactly where the FP64 oracle
 // rounds: weights, input, hidden activations, pre-activation gradients.
+//
+// Training runs as one CUDA graph per step (batch gather, forward, backward,
+// Adam with the BF16 refresh, step counter) replayed for the whole run; the
+// step number lives on the device, so every replay is the same graph.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -27,11 +31,14 @@
 
 namespace fm {
 
-constexpr int kH = 256;         // hidden width
-constexpr int kGm = 128;        // GEMM tile rows (MMA M)
-constexpr int kGk = 64;         // K per stage
+constexpr int kH = 256;          // hidden width
+constexpr int kGm = 128;         // GEMM tile rows (MMA M)
+constexpr int kGk = 64;          // K per stage
 constexpr int kGStages = 2;
-constexpr int kTrainBatch = 256;
+constexpr int kMaxBatch = 1024;  // training mini-batch capacity (leading dimension of transposed operands)
+constexpr int kLossBatch = 256;  // rows of surrogate_loss_grad
+constexpr int kTrainBN = 64;     // N tile of the training GEMMs (more CTAs on small problems)
+constexpr int kEvalBN = 256;     // N tile of the inference GEMMs
 constexpr int kEvalChunk = 1 << 16;
 
 enum EpiKind { kEpiFwdGelu = 0, kEpiBwdGelu = 1, kEpiF32 = 2 };
@@ -54,8 +61,51 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
+// n consecutive FP32 / BF16 values of one row: 16-byte stores when the row
+// chunk is whole and aligned, element stores otherwise.
+__device__ __forceinline__ void store_row_f32(float* p, const float (&a)[32], int n) {
+    if (n == 32 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            reinterpret_cast<float4*>(p)[i] = make_float4(a[4 * i], a[4 * i + 1], a[4 * i + 2], a[4 * i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < n) p[i] = a[i];
+    }
+}
+
+__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* p, const __nv_bfloat16 (&h)[32], int n) {
+    if (n == 32 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(p)[i] = reinterpret_cast<const uint4*>(h)[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < n) p[i] = h[i];
+    }
+}
+
+__device__ __forceinline__ void load_row_f32(const float* p, float (&a)[32], int n) {
+    if (n == 32 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(p)[i];
+            a[4 * i] = v.x;
+            a[4 * i + 1] = v.y;
+            a[4 * i + 2] = v.z;
+            a[4 * i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) a[i] = i < n ? p[i] : 0.0f;
+    }
+}
+
 // D[m][n] = sum_k A[m][k] B[n][k]: A [M][K] and B [N][K] BF16 K-major, one
-// 128 x BN tile per CTA, then the EPI epilogue on D.
+// 128 x BN tile per CTA, then the EPI epilogue on D.  Warp 0 lane 0 issues
+// the TMA loads, warp 1 lane 0 the MMAs; all four warps drain TMEM (warp w
+// owns rows 32w .. 32w+31 of the tile, one row per thread).
 template <int BN, int EPI>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_bf16_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int kblocks,
@@ -121,25 +171,34 @@ __global__ void __launch_bounds__(128, 1)
         for (int chunk = 0; chunk < BN / 32; ++chunk) {
             uint32_t v[32];
             tc::tmem_ld_32x32b_x32(row + chunk * 32, v);
-            if (r >= e.M) continue;
+            const int c0 = n0 + chunk * 32;
+            if (r >= e.M || c0 >= e.N) continue;
+            const int n = min(32, e.N - c0);
+            float a[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int c = n0 + chunk * 32 + i;
-                if (c >= e.N) continue;
-                const float acc = __uint_as_float(v[i]);
-                if (EPI == kEpiFwdGelu) {
-                    const float z = acc + e.bias[c];
-                    if (e.Z) e.Z[(size_t)r * e.ldz + c] = z;
-                    const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
-                    e.H[(size_t)r * e.ldh + c] = h;
-                    if (e.HT) e.HT[(size_t)c * e.ldt + r] = h;
-                } else if (EPI == kEpiBwdGelu) {
-                    const __nv_bfloat16 d = __float2bfloat16_rn(acc * gelu_grad_f(e.Z[(size_t)r * e.ldz + c]));
-                    e.H[(size_t)r * e.ldh + c] = d;
-                    if (e.HT) e.HT[(size_t)c * e.ldt + r] = d;
-                } else {
-                    e.F[(size_t)r * e.ldf + c] = acc;
-                }
+            for (int i = 0; i < 32; ++i) a[i] = __uint_as_float(v[i]);
+            if (EPI == kEpiF32) {
+                store_row_f32(e.F + (size_t)r * e.ldf + c0, a, n);
+                continue;
+            }
+            __nv_bfloat16 h[32];
+            if (EPI == kEpiFwdGelu) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) a[i] += (i < n) ? __ldg(e.bias + c0 + i) : 0.0f;
+                if (e.Z) store_row_f32(e.Z + (size_t)r * e.ldz + c0, a, n);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) h[i] = __float2bfloat16_rn(gelu_f(a[i]));
+            } else {
+                float z[32];
+                load_row_f32(e.Z + (size_t)r * e.ldz + c0, z, n);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) h[i] = __float2bfloat16_rn(a[i] * gelu_grad_f(z[i]));
+            }
+            store_row_bf16(e.H + (size_t)r * e.ldh + c0, h, n);
+            if (e.HT) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (i < n) e.HT[(size_t)(c0 + i) * e.ldt + r] = h[i];
             }
         }
     }
@@ -154,19 +213,19 @@ constexpr size_t gemm_smem() {
 }
 
 // ------------------------------------------------------------------ small kernels
-// x rows idx[b] of xi (FP64 [*][M]) -> BF16 X [B][D] (zero padded) and XT [D][B].
-__global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, const int32_t* __restrict__ idx,
-                           __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ XT) {
+// Rows of xi (FP64 [B][M]) -> BF16 X [B][D] (zero padded) and, if XT, XT [D][ldt].
+__global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, __nv_bfloat16* __restrict__ X,
+                           __nv_bfloat16* __restrict__ XT, int ldt) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B * D) return;
     const int b = t / D, k = t % D;
-    const size_t row = idx ? (size_t)idx[b] : (size_t)b;
-    const __nv_bfloat16 v = __float2bfloat16_rn((float)(k < M ? xi[row * M + k] : 0.0));
+    const __nv_bfloat16 v = __float2bfloat16_rn((float)(k < M ? xi[(size_t)b * M + k] : 0.0));
     X[(size_t)b * D + k] = v;
-    if (XT) XT[(size_t)k * B + b] = v;
+    if (XT) XT[(size_t)k * ldt + b] = v;
 }
 
-// out[b] = H3[b] . w4 + b4 (FP32); training: dout[b] = 2 (out[b] - t[b]) / B.
+// out[b] = H3[b] . w4 + b4 (FP32), one warp per row; training: dout[b] =
+// 2 (out[b] - t[b]) / B and the squared error.
 __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __nv_bfloat16* __restrict__ w4,
                           const float* __restrict__ b4, const float* __restrict__ t, float* __restrict__ out,
                           float* __restrict__ dout, float* __restrict__ sq) {
@@ -188,8 +247,8 @@ __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __n
     }
 }
 
-// Output layer backward: dZ3 = bf16((dout w4) * gelu'(Z3)) row-major and transposed.
-__global__ void k_mlp_out_back(int B, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ w4,
+// Output layer backward: dZ3 = bf16((dout w4) * gelu'(Z3)), row-major and transposed [kH][ldt].
+__global__ void k_mlp_out_back(int B, int ldt, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ w4,
                                const float* __restrict__ Z3, __nv_bfloat16* __restrict__ dZ,
                                __nv_bfloat16* __restrict__ dZT) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -198,40 +257,27 @@ __global__ void k_mlp_out_back(int B, const float* __restrict__ dout, const __nv
     const float d = dout[b] * __bfloat162float(w4[j]) * gelu_grad_f(Z3[t]);
     const __nv_bfloat16 v = __float2bfloat16_rn(d);
     dZ[t] = v;
-    dZT[(size_t)j * B + b] = v;
+    dZT[(size_t)j * ldt + b] = v;
 }
 
-// gW4[j] = sum_b dout[b] H3[b][j], gb4 = sum_b dout[b] (one thread per output, fixed order).
-__global__ void k_mlp_out_grad(int B, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ H3,
-                               float* __restrict__ gw4, float* __restrict__ gb4) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > kH) return;
+// Row sums of a transposed operand, one warp per row j (lanes over the batch,
+// fixed order): gb[j] = sum_b w[b] T[j][b], with w = 1 when null.  With
+// ones_row, warp N also writes gb[N] = sum_b w[b] (the output bias).
+__global__ void k_row_sums(int N, int B, int ldt, const __nv_bfloat16* __restrict__ T, const float* __restrict__ w,
+                           float* __restrict__ gb, float* __restrict__ ones_row) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (j > N || (j == N && !ones_row)) return;
     float acc = 0.0f;
-    for (int b = 0; b < B; ++b) acc += dout[b] * (j < kH ? __bfloat162float(H3[(size_t)b * kH + j]) : 1.0f);
-    if (j < kH) gw4[j] = acc;
-    else gb4[0] = acc;
-}
-
-// gb[j] = sum_b dZT[j][b] (the BF16 gradients the GEMMs use).
-__global__ void k_bias_grad(int N, int B, const __nv_bfloat16* __restrict__ dZT, float* __restrict__ gb) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    float acc = 0.0f;
-    for (int b = 0; b < B; ++b) acc += __bfloat162float(dZT[(size_t)j * B + b]);
-    gb[j] = acc;
-}
-
-// Adam (Kingma & Ba) on FP32 master parameters, then the BF16 operand copies.
-__global__ void k_adam(size_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2) {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const float gt = g[t];
-    const float mt = b1 * m[t] + (1.0f - b1) * gt;
-    const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
-    m[t] = mt;
-    v[t] = vt;
-    p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+    for (int b = lane; b < B; b += 32) {
+        const float x = (j < N) ? __bfloat162float(T[(size_t)j * ldt + b]) : 1.0f;
+        acc += w ? w[b] * x : x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        if (j < N) gb[j] = acc;
+        else ones_row[0] = acc;
+    }
 }
 
 // W [rows][cols] FP32 -> BF16 [rows][ld] (zero padded) and, if WT, [cols][rows].
@@ -245,15 +291,102 @@ __global__ void k_weight_bf16(int rows, int cols, int ld, const float* __restric
     if (WT && c < cols) WT[(size_t)c * rows + r] = v;
 }
 
-__global__ void k_gather_targets(int B, const float* __restrict__ src, const int32_t* __restrict__ idx,
-                                 float* __restrict__ t) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) t[b] = src[idx[b]];
-}
-
 __global__ void k_surrogate_value(int n, const float* __restrict__ out, double mu, double sd, double* __restrict__ s) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) s[t] = mu + sd * (double)out[t];
+}
+
+// Mini-batch `*step` of a training run: rows perm[(step / spe) * n + (step %
+// spe) * B + b] of xi (FP64 [n][M]) and of the standardised targets tt, as
+// the BF16 operands X [B][D] (zero padded) and XT [D][ldt] and the FP32 t [B].
+__global__ void k_train_batch(int B, int M, int D, int ldt, int n, int spe, const int* __restrict__ step,
+                              const int32_t* __restrict__ perm, const double* __restrict__ xi,
+                              const float* __restrict__ tt, __nv_bfloat16* __restrict__ X,
+                              __nv_bfloat16* __restrict__ XT, float* __restrict__ t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * D) return;
+    const int b = i / D, k = i % D;
+    const int s = *step;
+    const size_t row = (size_t)perm[(size_t)(s / spe) * n + (size_t)(s % spe) * B + b];
+    const __nv_bfloat16 v = __float2bfloat16_rn((float)(k < M ? xi[row * M + k] : 0.0));
+    X[(size_t)b * D + k] = v;
+    XT[(size_t)k * ldt + b] = v;
+    if (k == 0) t[b] = tt[row];
+}
+
+// One Adam step (Kingma & Ba) at step number *step of `total`, learning rate
+// lr0 (1 + cos(pi step / total)) / 2, followed by the BF16 operand copies of
+// the updated weights (row-major and, for W2 / W3, transposed).
+struct AdamArgs {
+    size_t np;
+    float *P, *m, *v;
+    const float* g;
+    const int* step;
+    int total;
+    float lr0, b1, b2, eps;
+    size_t off[8];
+    int M, D;
+    __nv_bfloat16 *W1b, *W2b, *W3b, *W2T, *W3T, *w4b;
+};
+
+__global__ void k_adam_step(AdamArgs a) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.np) return;
+    const int s = *a.step;
+    const float k = (float)(s + 1);
+    const float lr = a.lr0 * 0.5f * (1.0f + cospif((float)s / (float)a.total));
+    const float c1 = 1.0f - powf(a.b1, k), c2 = 1.0f - powf(a.b2, k);
+    const float gt = a.g[t];
+    const float mt = a.b1 * a.m[t] + (1.0f - a.b1) * gt;
+    const float vt = a.b2 * a.v[t] + (1.0f - a.b2) * gt * gt;
+    a.m[t] = mt;
+    a.v[t] = vt;
+    const float p = a.P[t] - lr * (mt / c1) / (sqrtf(vt / c2) + a.eps);
+    a.P[t] = p;
+    const __nv_bfloat16 h = __float2bfloat16_rn(p);
+    if (t < a.off[1]) {
+        a.W1b[(t / a.M) * a.D + t % a.M] = h;
+    } else if (t >= a.off[2] && t < a.off[3]) {
+        const size_t u = t - a.off[2];
+        a.W2b[u] = h;
+        a.W2T[(u % kH) * kH + u / kH] = h;
+    } else if (t >= a.off[4] && t < a.off[5]) {
+        const size_t u = t - a.off[4];
+        a.W3b[u] = h;
+        a.W3T[(u % kH) * kH + u / kH] = h;
+    } else if (t >= a.off[6] && t < a.off[7]) {
+        a.w4b[t - a.off[6]] = h;
+    }
+}
+
+__global__ void k_tick(int* step) { *step += 1; }
+
+// X[b][k] = bf16(Phi^-1(u)) for the MC sample first + b of Philox stream
+// `level` (the words of the FP64 points: u from the top 23 bits of word k,
+// Phi^-1 in FP32), zero for k >= M.  The surrogate sees its input in BF16,
+// so this FP32 map from the same Philox words is its input on both estimator
+// levels that use it.
+__global__ void k_surrogate_x_mc(uint64_t seed, uint32_t level, uint64_t first, int n, int M, int D,
+                                 __nv_bfloat16* __restrict__ X) {
+    const int blocks = D / 4;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)n * blocks) return;
+    const int s = (int)(t / blocks), b = (int)(t % blocks);
+    __align__(8) __nv_bfloat16 h[4];
+    if (4 * b < M) {
+        u64x4 c = {{(uint64_t)b, first + s, 0, 0}};
+        const u64x4 w = philox4x64(c, seed, (kPurposeMC << 32) | level);
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) {
+            // 23 bits keep (k + 1/2) exact in FP32, so 0 < u < 1 strictly
+            const float u = ((float)(w.v[lane] >> 41) + 0.5f) * 0x1p-23f;
+            h[lane] = __float2bfloat16_rn(4 * b + lane < M ? normcdfinvf(u) : 0.0f);
+        }
+    } else {
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) h[lane] = __float2bfloat16_rn(0.0f);
+    }
+    *reinterpret_cast<uint2*>(X + (size_t)s * D + 4 * b) = *reinterpret_cast<const uint2*>(h);
 }
 
 // ------------------------------------------------------------------ host state
@@ -266,18 +399,20 @@ struct MlpState {
     size_t off[8] = {};                // W1 b1 W2 b2 W3 b3 w4 b4
     float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
     __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2T = nullptr, *W3T = nullptr, *w4b = nullptr;
-    // training batch
+    // training batch (capacity kMaxBatch rows; transposed operands [*][kMaxBatch])
     __nv_bfloat16 *X = nullptr, *XT = nullptr, *H[3] = {}, *HT[3] = {}, *dZ[3] = {}, *dZT[3] = {};
     float *Z[3] = {}, *t = nullptr, *out = nullptr, *dout = nullptr, *sq = nullptr;
-    int32_t* idx = nullptr;
-    CUtensorMap mX, mW1, mW2, mW3, mH1, mH2, mW2T, mW3T, mdZ2, mdZ3, mdZ1T_A, mdZ2T_A, mdZ3T_A, mXT_B, mH1T_B, mH2T_B;
+    // training maps: A operands (box 128 rows), B operands (box kTrainBN rows)
+    CUtensorMap mX, mH1, mH2, mdZ2, mdZ3, mdZ1T, mdZ2T, mdZ3T;
+    CUtensorMap tW1, tW2, tW3, tW2T, tW3T, tXT, tH1T, tH2T;
     // inference
     __nv_bfloat16 *eX = nullptr, *eH[3] = {};
     float* eout = nullptr;
-    CUtensorMap meX, meH1, meH2;
+    CUtensorMap meX, meH1, meH2, eW1, eW2, eW3;
     double mu = 0.0, sd = 1.0;
-    int adam_t = 0;
     int* err = nullptr;
+    int* step = nullptr;               // device step counter of a training run
+    cudaStream_t st = nullptr;         // training stream (graph capture)
 };
 
 static MlpState* state(fm_ctx* ctx) { return reinterpret_cast<MlpState*>(ctx->mlp); }
@@ -309,14 +444,15 @@ static bool map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t 
 }
 
 template <int BN, int EPI>
+static bool gemm_attr() {
+    return cudaFuncSetAttribute(k_gemm_bf16_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_smem<BN>()) == cudaSuccess;
+}
+
+// D = A B^T over K (a multiple of 64): M x N outputs in 128 x BN tiles.
+template <int BN, int EPI>
 static void gemm(fm_ctx* ctx, const CUtensorMap& A, const CUtensorMap& B, int M, int N, int K, const EpiArgs& e,
                  cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_bf16_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gemm_smem<BN>());
-        attr = true;
-    }
     dim3 grid((M + kGm - 1) / kGm, (N + BN - 1) / BN);
     FM_TIMED(ctx, kFamMlp, st, 2.0 * ((double)M * K + (double)N * K) + 4.0 * (double)M * N,
              2.0 * (double)M * N * K,
@@ -327,8 +463,8 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
     if (ctx->mlp) return FM_OK;
     MlpState* S = new MlpState();
     ctx->mlp = S;
-    // inputs padded to a multiple of 128 so the weight-gradient GEMM's N tile fits
-    const int M = ctx->cfg.M, D = (M + 127) / 128 * 128, B = kTrainBatch;
+    // inputs padded to a multiple of 128 (whole K blocks and N tiles)
+    const int M = ctx->cfg.M, D = (M + 127) / 128 * 128, L = kMaxBatch;
     S->M = M;
     S->D = D;
     size_t o = 0;
@@ -353,39 +489,46 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
     al((void**)&S->W2T, (size_t)kH * kH * 2);
     al((void**)&S->W3T, (size_t)kH * kH * 2);
     al((void**)&S->w4b, (size_t)kH * 2);
-    al((void**)&S->X, (size_t)B * D * 2);
-    al((void**)&S->XT, (size_t)D * B * 2);
+    al((void**)&S->X, (size_t)L * D * 2);
+    al((void**)&S->XT, (size_t)D * L * 2);
     for (int l = 0; l < 3; ++l) {
-        al((void**)&S->H[l], (size_t)B * kH * 2);
-        al((void**)&S->HT[l], (size_t)kH * B * 2);
-        al((void**)&S->dZ[l], (size_t)B * kH * 2);
-        al((void**)&S->dZT[l], (size_t)kH * B * 2);
-        al((void**)&S->Z[l], (size_t)B * kH * 4);
+        al((void**)&S->H[l], (size_t)L * kH * 2);
+        al((void**)&S->HT[l], (size_t)kH * L * 2);
+        al((void**)&S->dZ[l], (size_t)L * kH * 2);
+        al((void**)&S->dZT[l], (size_t)kH * L * 2);
+        al((void**)&S->Z[l], (size_t)L * kH * 4);
         al((void**)&S->eH[l], (size_t)kEvalChunk * kH * 2);
     }
-    al((void**)&S->t, B * 4);
-    al((void**)&S->out, B * 4);
-    al((void**)&S->dout, B * 4);
-    al((void**)&S->sq, B * 4);
-    al((void**)&S->idx, B * 4);
+    al((void**)&S->t, L * 4);
+    al((void**)&S->out, L * 4);
+    al((void**)&S->dout, L * 4);
+    al((void**)&S->sq, L * 4);
     al((void**)&S->eX, (size_t)kEvalChunk * D * 2);
     al((void**)&S->eout, (size_t)kEvalChunk * 4);
     al((void**)&S->err, 4);
+    al((void**)&S->step, 4);
+    if (ok && cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) ok = false;
     if (!ok) {
         set_error(ctx, "surrogate: device allocation failed");
         return FM_ENOMEM;
     }
-    // A operands (rows = M tile of 128) and B operands (rows = N tile)
-    ok = map_bf16(&S->mX, S->X, B, D, kGm) && map_bf16(&S->mW1, S->W1b, kH, D, 256) &&
-         map_bf16(&S->mH1, S->H[0], B, kH, kGm) && map_bf16(&S->mW2, S->W2b, kH, kH, 256) &&
-         map_bf16(&S->mH2, S->H[1], B, kH, kGm) && map_bf16(&S->mW3, S->W3b, kH, kH, 256) &&
-         map_bf16(&S->mW2T, S->W2T, kH, kH, 256) && map_bf16(&S->mW3T, S->W3T, kH, kH, 256) &&
-         map_bf16(&S->mdZ3, S->dZ[2], B, kH, kGm) && map_bf16(&S->mdZ2, S->dZ[1], B, kH, kGm) &&
-         map_bf16(&S->mdZ3T_A, S->dZT[2], kH, B, kGm) && map_bf16(&S->mdZ2T_A, S->dZT[1], kH, B, kGm) &&
-         map_bf16(&S->mdZ1T_A, S->dZT[0], kH, B, kGm) && map_bf16(&S->mXT_B, S->XT, D, B, D >= 256 ? 256 : 128) &&
-         map_bf16(&S->mH1T_B, S->HT[0], kH, B, 256) && map_bf16(&S->mH2T_B, S->HT[1], kH, B, 256) &&
+    if (!(gemm_attr<kTrainBN, kEpiFwdGelu>() && gemm_attr<kTrainBN, kEpiBwdGelu>() &&
+          gemm_attr<kTrainBN, kEpiF32>() && gemm_attr<kEvalBN, kEpiFwdGelu>())) {
+        set_error(ctx, "surrogate: cannot raise the GEMM kernels' shared-memory limit");
+        return FM_ECUDA;
+    }
+    const uint32_t bn = kTrainBN;
+    ok = map_bf16(&S->mX, S->X, L, D, kGm) && map_bf16(&S->mH1, S->H[0], L, kH, kGm) &&
+         map_bf16(&S->mH2, S->H[1], L, kH, kGm) && map_bf16(&S->mdZ2, S->dZ[1], L, kH, kGm) &&
+         map_bf16(&S->mdZ3, S->dZ[2], L, kH, kGm) && map_bf16(&S->mdZ1T, S->dZT[0], kH, L, kGm) &&
+         map_bf16(&S->mdZ2T, S->dZT[1], kH, L, kGm) && map_bf16(&S->mdZ3T, S->dZT[2], kH, L, kGm) &&
+         map_bf16(&S->tW1, S->W1b, kH, D, bn) && map_bf16(&S->tW2, S->W2b, kH, kH, bn) &&
+         map_bf16(&S->tW3, S->W3b, kH, kH, bn) && map_bf16(&S->tW2T, S->W2T, kH, kH, bn) &&
+         map_bf16(&S->tW3T, S->W3T, kH, kH, bn) && map_bf16(&S->tXT, S->XT, D, L, bn) &&
+         map_bf16(&S->tH1T, S->HT[0], kH, L, bn) && map_bf16(&S->tH2T, S->HT[1], kH, L, bn) &&
          map_bf16(&S->meX, S->eX, kEvalChunk, D, kGm) && map_bf16(&S->meH1, S->eH[0], kEvalChunk, kH, kGm) &&
-         map_bf16(&S->meH2, S->eH[1], kEvalChunk, kH, kGm);
+         map_bf16(&S->meH2, S->eH[1], kEvalChunk, kH, kGm) && map_bf16(&S->eW1, S->W1b, kH, D, kEvalBN) &&
+         map_bf16(&S->eW2, S->W2b, kH, kH, kEvalBN) && map_bf16(&S->eW3, S->W3b, kH, kH, kEvalBN);
     if (!ok) {
         set_error(ctx, "surrogate: cuTensorMapEncodeTiled failed");
         return FM_ECUDA;
@@ -403,58 +546,85 @@ static void refresh_bf16(fm_ctx* ctx, cudaStream_t st) {
     k_weight_bf16<<<nb(kH), 256, 0, st>>>(1, kH, kH, S->P + S->off[6], S->w4b, nullptr);
 }
 
-// Forward + backward of one batch of B = 256 rows already in S->X / S->XT / S->t.
-static void train_step_grads(fm_ctx* ctx, cudaStream_t st) {
+// Forward + backward of one batch of B rows (a multiple of 128, <= kMaxBatch)
+// already in S->X / S->XT / S->t; gradients into S->G.
+static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st) {
     MlpState* S = state(ctx);
-    const int B = kTrainBatch, D = S->D;
+    const int D = S->D, L = kMaxBatch;
+    constexpr int BN = kTrainBN;
     EpiArgs e{};
-    // forward
-    e = EpiArgs{B, kH, S->P + S->off[1], S->Z[0], kH, S->H[0], kH, S->HT[0], B, nullptr, 0};
-    gemm<256, kEpiFwdGelu>(ctx, S->mX, S->mW1, B, kH, D, e, st);
-    e = EpiArgs{B, kH, S->P + S->off[3], S->Z[1], kH, S->H[1], kH, S->HT[1], B, nullptr, 0};
-    gemm<256, kEpiFwdGelu>(ctx, S->mH1, S->mW2, B, kH, kH, e, st);
-    e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], B, nullptr, 0};
-    gemm<256, kEpiFwdGelu>(ctx, S->mH2, S->mW3, B, kH, kH, e, st);
+    // forward: Z_l = H_(l-1) W_l^T + b_l, H_l = bf16(gelu(Z_l))
+    e = EpiArgs{B, kH, S->P + S->off[1], S->Z[0], kH, S->H[0], kH, S->HT[0], L, nullptr, 0};
+    gemm<BN, kEpiFwdGelu>(ctx, S->mX, S->tW1, B, kH, D, e, st);
+    e = EpiArgs{B, kH, S->P + S->off[3], S->Z[1], kH, S->H[1], kH, S->HT[1], L, nullptr, 0};
+    gemm<BN, kEpiFwdGelu>(ctx, S->mH1, S->tW2, B, kH, kH, e, st);
+    e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], L, nullptr, 0};
+    gemm<BN, kEpiFwdGelu>(ctx, S->mH2, S->tW3, B, kH, kH, e, st);
     k_mlp_out<<<nb((size_t)B * 32), 256, 0, st>>>(B, S->H[2], S->w4b, S->P + S->off[7], S->t, S->out, S->dout, S->sq);
-    // backward
-    k_mlp_out_grad<<<nb(kH + 1), 256, 0, st>>>(B, S->dout, S->H[2], S->G + S->off[6], S->G + S->off[7]);
-    k_mlp_out_back<<<nb((size_t)B * kH), 256, 0, st>>>(B, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
-    // layer 3: dW3 = dZ3^T H2, db3, dZ2 = (dZ3 W3) * gelu'(Z2)
+    // output layer: gw4 = dout^T H3, gb4 = sum dout, dZ3 = bf16(dout w4 gelu'(Z3))
+    k_row_sums<<<nb((size_t)(kH + 1) * 32), 256, 0, st>>>(kH, B, L, S->HT[2], S->dout, S->G + S->off[6],
+                                                          S->G + S->off[7]);
+    k_mlp_out_back<<<nb((size_t)B * kH), 256, 0, st>>>(B, L, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
+    // layer 3: dW3 = dZ3^T H2, db3, dZ2 = bf16((dZ3 W3) gelu'(Z2))
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[4], kH};
-    gemm<256, kEpiF32>(ctx, S->mdZ3T_A, S->mH2T_B, kH, kH, B, e, st);
-    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[2], S->G + S->off[5]);
-    e = EpiArgs{B, kH, nullptr, S->Z[1], kH, S->dZ[1], kH, S->dZT[1], B, nullptr, 0};
-    gemm<256, kEpiBwdGelu>(ctx, S->mdZ3, S->mW3T, B, kH, kH, e, st);
+    gemm<BN, kEpiF32>(ctx, S->mdZ3T, S->tH2T, kH, kH, B, e, st);
+    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[2], nullptr, S->G + S->off[5], nullptr);
+    e = EpiArgs{B, kH, nullptr, S->Z[1], kH, S->dZ[1], kH, S->dZT[1], L, nullptr, 0};
+    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ3, S->tW3T, B, kH, kH, e, st);
     // layer 2
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[2], kH};
-    gemm<256, kEpiF32>(ctx, S->mdZ2T_A, S->mH1T_B, kH, kH, B, e, st);
-    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[1], S->G + S->off[3]);
-    e = EpiArgs{B, kH, nullptr, S->Z[0], kH, S->dZ[0], kH, S->dZT[0], B, nullptr, 0};
-    gemm<256, kEpiBwdGelu>(ctx, S->mdZ2, S->mW2T, B, kH, kH, e, st);
+    gemm<BN, kEpiF32>(ctx, S->mdZ2T, S->tH1T, kH, kH, B, e, st);
+    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[1], nullptr, S->G + S->off[3], nullptr);
+    e = EpiArgs{B, kH, nullptr, S->Z[0], kH, S->dZ[0], kH, S->dZT[0], L, nullptr, 0};
+    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ2, S->tW2T, B, kH, kH, e, st);
     // layer 1: dW1 = dZ1^T X (N = D input columns; the FP32 gradient keeps the M real ones)
     e = EpiArgs{kH, S->M, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[0], S->M};
-    if (D >= 256) gemm<256, kEpiF32>(ctx, S->mdZ1T_A, S->mXT_B, kH, D, B, e, st);
-    else gemm<128, kEpiF32>(ctx, S->mdZ1T_A, S->mXT_B, kH, D, B, e, st);
-    k_bias_grad<<<nb(kH), 256, 0, st>>>(kH, B, S->dZT[0], S->G + S->off[1]);
+    gemm<BN, kEpiF32>(ctx, S->mdZ1T, S->tXT, kH, D, B, e, st);
+    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[0], nullptr, S->G + S->off[1], nullptr);
 }
 
-// Forward of n rows of xi (FP64 [n][M]) into S->eout, chunked.
-static void eval_forward(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st) {
+// Forward of n rows, chunked: fill(o, cnt, st) writes rows o .. o+cnt-1 of
+// the input as BF16 into S->eX; S = mu + sd f lands in d_s.
+template <class Fill>
+static void eval_chunks(fm_ctx* ctx, uint32_t n, Fill fill, double* d_s, cudaStream_t st) {
     MlpState* S = state(ctx);
-    const int D = S->D;
     for (uint32_t o = 0; o < n; o += kEvalChunk) {
         const int cnt = (int)std::min<uint32_t>(kEvalChunk, n - o);
-        k_gather_x<<<nb((size_t)cnt * D), 256, 0, st>>>(cnt, S->M, D, d_xi + (size_t)o * S->M, nullptr, S->eX, nullptr);
+        fill(o, cnt, st);
         EpiArgs e{cnt, kH, S->P + S->off[1], nullptr, 0, S->eH[0], kH, nullptr, 0, nullptr, 0};
-        gemm<256, kEpiFwdGelu>(ctx, S->meX, S->mW1, cnt, kH, D, e, st);
+        gemm<kEvalBN, kEpiFwdGelu>(ctx, S->meX, S->eW1, cnt, kH, S->D, e, st);
         e = EpiArgs{cnt, kH, S->P + S->off[3], nullptr, 0, S->eH[1], kH, nullptr, 0, nullptr, 0};
-        gemm<256, kEpiFwdGelu>(ctx, S->meH1, S->mW2, cnt, kH, kH, e, st);
+        gemm<kEvalBN, kEpiFwdGelu>(ctx, S->meH1, S->eW2, cnt, kH, kH, e, st);
         e = EpiArgs{cnt, kH, S->P + S->off[5], nullptr, 0, S->eH[2], kH, nullptr, 0, nullptr, 0};
-        gemm<256, kEpiFwdGelu>(ctx, S->meH2, S->mW3, cnt, kH, kH, e, st);
+        gemm<kEvalBN, kEpiFwdGelu>(ctx, S->meH2, S->eW3, cnt, kH, kH, e, st);
         k_mlp_out<<<nb((size_t)cnt * 32), 256, 0, st>>>(cnt, S->eH[2], S->w4b, S->P + S->off[7], nullptr, S->eout,
                                                         nullptr, nullptr);
         k_surrogate_value<<<nb(cnt), 256, 0, st>>>(cnt, S->eout, S->mu, S->sd, d_s + o);
     }
+}
+
+// S(xi) for n rows of xi (FP64 [n][M]).
+static void eval_forward(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st) {
+    MlpState* S = state(ctx);
+    eval_chunks(ctx, n, [&](uint32_t o, int cnt, cudaStream_t s2) {
+        k_gather_x<<<nb((size_t)cnt * S->D), 256, 0, s2>>>(cnt, S->M, S->D, d_xi + (size_t)o * S->M, S->eX, nullptr,
+                                                           0);
+    }, d_s, st);
+}
+
+fm_status surrogate_eval_mc_impl(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, double* d_s,
+                                 cudaStream_t st) {
+    FM_CHECK_ARG(ctx, ctx->mlp && state(ctx)->ready, "surrogate: no trained or installed network");
+    if (n == 0) return FM_OK;
+    MlpState* S = state(ctx);
+    const uint64_t seed = ctx->cfg.seed;
+    eval_chunks(ctx, n, [&](uint32_t o, int cnt, cudaStream_t s2) {
+        FM_TIMED(ctx, kFamPoints, s2, (double)cnt * S->D * 2, 0.0,
+                 k_surrogate_x_mc<<<nb((size_t)cnt * (S->D / 4)), 256, 0, s2>>>(seed, level, first + o, cnt, S->M,
+                                                                                 S->D, S->eX));
+    }, d_s, st);
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
 }
 
 fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, cudaStream_t st) {
@@ -476,7 +646,8 @@ void mlp_free(fm_ctx* ctx) {
     MlpState* S = state(ctx);
     if (!S) return;
     void* ptrs[] = {S->P, S->G, S->Am, S->Av, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b, S->X, S->XT,
-                    S->t, S->out, S->dout, S->sq, S->idx, S->eX, S->eout, S->err};
+                    S->t, S->out, S->dout, S->sq, S->eX, S->eout, S->err, S->step};
+    if (S->st) cudaStreamDestroy(S->st);
     for (void* p : ptrs) cudaFree(p);
     for (int l = 0; l < 3; ++l) {
         cudaFree(S->H[l]); cudaFree(S->HT[l]); cudaFree(S->dZ[l]); cudaFree(S->dZT[l]); cudaFree(S->Z[l]);
@@ -525,9 +696,9 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
     FM_TRY(mlp_alloc(ctx));
     MlpState* S = state(ctx);
     FM_CUDA_TRY(ctx, cudaMemset(S->err, 0, 4));
-    k_gather_x<<<nb((size_t)kTrainBatch * S->D), 256>>>(kTrainBatch, S->M, S->D, d_xi, nullptr, S->X, S->XT);
-    FM_CUDA_TRY(ctx, cudaMemcpy(S->t, d_target, kTrainBatch * 4, cudaMemcpyDeviceToDevice));
-    train_step_grads(ctx, nullptr);
+    k_gather_x<<<nb((size_t)kLossBatch * S->D), 256>>>(kLossBatch, S->M, S->D, d_xi, S->X, S->XT, kMaxBatch);
+    FM_CUDA_TRY(ctx, cudaMemcpy(S->t, d_target, kLossBatch * 4, cudaMemcpyDeviceToDevice));
+    train_step_grads(ctx, kLossBatch, nullptr);
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     if (surrogate_err_flag(ctx)) {
         set_error(ctx, "surrogate_loss_grad: a bounded tensor-core wait ran out");
@@ -535,11 +706,11 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
     }
     if (host_grads) FM_CUDA_TRY(ctx, cudaMemcpy(host_grads, S->G, S->np * 4, cudaMemcpyDeviceToHost));
     if (host_loss) {
-        std::vector<float> sq(kTrainBatch);
-        FM_CUDA_TRY(ctx, cudaMemcpy(sq.data(), S->sq, kTrainBatch * 4, cudaMemcpyDeviceToHost));
+        std::vector<float> sq(kLossBatch);
+        FM_CUDA_TRY(ctx, cudaMemcpy(sq.data(), S->sq, kLossBatch * 4, cudaMemcpyDeviceToHost));
         double l = 0.0;
         for (float v : sq) l += v;
-        *host_loss = l / kTrainBatch;
+        *host_loss = l / kLossBatch;
     }
     return FM_OK;
 }
@@ -547,8 +718,11 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
 extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* rep) {
     FM_CHECK_ARG(ctx, ctx != nullptr && opts != nullptr, "surrogate_train: null argument");
     FM_CHECK_ARG(ctx, ctx->basis_ready, "surrogate_train: no KL basis installed");
-    FM_CHECK_ARG(ctx, opts->n_train >= kTrainBatch && opts->epochs >= 1 && opts->lr > 0,
-                 "surrogate_train: need n_train >= 256, epochs >= 1, lr > 0");
+    const int batch = opts->batch > 0 ? opts->batch : 256;
+    FM_CHECK_ARG(ctx, batch % 128 == 0 && batch <= kMaxBatch,
+                 "surrogate_train: batch must be a multiple of 128 and at most 1024");
+    FM_CHECK_ARG(ctx, opts->n_train >= batch && opts->epochs >= 1 && opts->lr > 0,
+                 "surrogate_train: need n_train >= batch, epochs >= 1, lr > 0");
     const auto t0 = std::chrono::steady_clock::now();
     FM_TRY(mlp_alloc(ctx));
     MlpState* S = state(ctx);
@@ -602,47 +776,76 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         const double a = 1.0 / std::sqrt((double)fan[i]);
         for (size_t k = S->off[i]; k < end; ++k) hp[k] = (float)((2.0 * uni(gen) - 1.0) * a);
     }
-    cudaMemcpy(S->P, hp.data(), S->np * 4, cudaMemcpyHostToDevice);
-    cudaMemset(S->Am, 0, S->np * 4);
-    cudaMemset(S->Av, 0, S->np * 4);
-    cudaMemset(S->err, 0, 4);
-    S->adam_t = 0;
-    refresh_bf16(ctx, nullptr);
-    // epochs of shuffled mini-batches, cosine-decayed learning rate
-    const int steps_per_epoch = n / kTrainBatch;
-    const int total = steps_per_epoch * opts->epochs;
-    std::vector<int32_t> perm(n);
-    std::iota(perm.begin(), perm.end(), 0);
-    double first_loss = NAN, last_loss = NAN;
-    int step = 0;
+    // one shuffled permutation per epoch, all uploaded before the run
+    const int spe = n / batch;
+    const int total = spe * opts->epochs;
+    std::vector<int32_t> perm((size_t)n * opts->epochs);
     for (int ep = 0; ep < opts->epochs; ++ep) {
-        std::shuffle(perm.begin(), perm.end(), gen);
-        int32_t* dperm = nullptr;
-        cudaMalloc((void**)&dperm, (size_t)n * 4);
-        cudaMemcpy(dperm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
-        for (int sb = 0; sb < steps_per_epoch; ++sb, ++step) {
-            const int32_t* bidx = dperm + (size_t)sb * kTrainBatch;
-            k_gather_x<<<nb((size_t)kTrainBatch * S->D), 256>>>(kTrainBatch, M, S->D, xi, bidx, S->X, S->XT);
-            k_gather_targets<<<1, 256>>>(kTrainBatch, tt, bidx, S->t);
-            train_step_grads(ctx, nullptr);
-            const double lr = opts->lr * 0.5 * (1.0 + std::cos(M_PI * step / (double)total));
-            ++S->adam_t;
-            const float c1 = 1.0f - std::pow(0.9f, (float)S->adam_t), c2 = 1.0f - std::pow(0.999f, (float)S->adam_t);
-            k_adam<<<nb(S->np), 256>>>(S->np, S->P, S->Am, S->Av, S->G, (float)lr, 0.9f, 0.999f, 1e-8f, c1, c2);
-            refresh_bf16(ctx, nullptr);
-            if (step == 0 || step == total - 1) {
-                std::vector<float> sq(kTrainBatch);
-                cudaMemcpy(sq.data(), S->sq, kTrainBatch * 4, cudaMemcpyDeviceToHost);
-                double l = 0.0;
-                for (float v : sq) l += v;
-                (step == 0 ? first_loss : last_loss) = l / kTrainBatch;
-            }
-        }
-        cudaFree(dperm);
+        int32_t* pe = perm.data() + (size_t)ep * n;
+        std::iota(pe, pe + n, 0);
+        std::shuffle(pe, pe + n, gen);
     }
+    int32_t* dperm = nullptr;
+    cudaStream_t ts = S->st;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double first_loss = NAN, last_loss = NAN;
+    auto batch_loss = [&]() -> double {
+        std::vector<float> sq(batch);
+        cudaMemcpy(sq.data(), S->sq, batch * 4, cudaMemcpyDeviceToHost);
+        double l = 0.0;
+        for (float v : sq) l += v;
+        return l / batch;
+    };
+    auto run = [&]() -> fm_status {
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&dperm, perm.size() * 4));
+        FM_CUDA_TRY(ctx, cudaMemcpy(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
+        FM_CUDA_TRY(ctx, cudaMemcpy(S->P, hp.data(), S->np * 4, cudaMemcpyHostToDevice));
+        FM_CUDA_TRY(ctx, cudaMemset(S->Am, 0, S->np * 4));
+        FM_CUDA_TRY(ctx, cudaMemset(S->Av, 0, S->np * 4));
+        FM_CUDA_TRY(ctx, cudaMemset(S->err, 0, 4));
+        FM_CUDA_TRY(ctx, cudaMemset(S->step, 0, 4));
+        refresh_bf16(ctx, nullptr);
+        FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
+        // one training step as a CUDA graph: batch gather, forward, backward,
+        // Adam + BF16 refresh, step counter; replayed `total` times
+        AdamArgs aa{S->np, S->P, S->Am, S->Av, S->G, S->step, total, (float)opts->lr, 0.9f, 0.999f, 1e-8f,
+                    {}, M, S->D, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b};
+        for (int i = 0; i < 8; ++i) aa.off[i] = S->off[i];
+        const bool prof_on = ctx->prof.active;
+        ctx->prof.active = false;    // no event records inside the captured graph
+        FM_CUDA_TRY(ctx, cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal));
+        k_train_batch<<<nb((size_t)batch * S->D), 256, 0, ts>>>(batch, M, S->D, kMaxBatch, n, spe, S->step, dperm,
+                                                                 xi, tt, S->X, S->XT, S->t);
+        train_step_grads(ctx, batch, ts);
+        k_adam_step<<<nb(S->np), 256, 0, ts>>>(aa);
+        k_tick<<<1, 1, 0, ts>>>(S->step);
+        const cudaError_t ce = cudaStreamEndCapture(ts, &graph);
+        ctx->prof.active = prof_on;
+        FM_CUDA_TRY(ctx, ce);
+        FM_CUDA_TRY(ctx, cudaGraphInstantiate(&exec, graph, 0));
+        const int pidx = prof_start(ctx, kFamMlp, ts);
+        FM_CUDA_TRY(ctx, cudaGraphLaunch(exec, ts));
+        FM_CUDA_TRY(ctx, cudaStreamSynchronize(ts));
+        first_loss = batch_loss();
+        for (int k = 1; k < total; ++k) FM_CUDA_TRY(ctx, cudaGraphLaunch(exec, ts));
+        const double D = S->D;
+        prof_stop(ctx, pidx, ts, 0.0, (double)total * 2.0 * batch * (2.0 * D * kH + 6.0 * kH * kH));
+        FM_CUDA_TRY(ctx, cudaStreamSynchronize(ts));
+        last_loss = batch_loss();
+        return FM_OK;
+    };
+    stt = run();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(dperm);
     cudaFree(tt);
     cudaFree(K);
     cudaFree(q);
+    if (stt != FM_OK) {
+        cudaFree(xi);
+        return stt;
+    }
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     if (surrogate_err_flag(ctx)) {
         cudaFree(xi);
@@ -684,4 +887,11 @@ extern "C" fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi,
     FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_eval: null context");
     FM_CHECK_ARG(ctx, n == 0 || (d_xi && d_s), "surrogate_eval: null pointer");
     return surrogate_eval_impl(ctx, n, d_xi, d_s, as_stream(stream));
+}
+
+extern "C" fm_status surrogate_eval_mc(fm_ctx* ctx, uint32_t stream_level, uint64_t first, uint32_t n, double* d_s,
+                                       void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_eval_mc: null context");
+    FM_CHECK_ARG(ctx, n == 0 || d_s, "surrogate_eval_mc: null pointer");
+    return surrogate_eval_mc_impl(ctx, stream_level, first, n, d_s, as_stream(stream));
 }

@@ -120,3 +120,21 @@ def test_estimate_with_surrogate_agrees_with_plain_mlmc(ctx):
     # the surrogate moves level-0 work onto cheap S samples
     assert sur["N"][0] < plain["N"][0]
     assert sur["N_s"] > sur["N"][0]
+
+
+def test_philox_word_inputs_match_fp64_points(ctx):
+    """The estimator evaluates S from the samples' Philox words (FP32 inverse
+    normal, BF16 input); on the FP64 points of the same samples S differs only
+    where the two inputs round to different BF16 values."""
+    p = _random_params(3)
+    ctx.surrogate_set_params(p, mu=0.5, sd=1.0)
+    n = 20000
+    a = ctx.surrogate_eval_mc(0, 1234, n).cpu().numpy()
+    xi = ctx.mc_points(0, 1234, n)
+    b = ctx.surrogate_eval(xi).cpu().numpy()
+    d = np.abs(a - b)
+    assert np.mean(d > 1e-6) < 0.05
+    assert d.max() < 0.1
+    # and the oracle network on the same FP64 points
+    ref, _ = omlp.forward(_to_oracle(p), xi.cpu().numpy(), rounding=True)
+    assert np.median(np.abs(a - (0.5 + ref))) < 1e-5
