@@ -27,7 +27,8 @@ constexpr int kBlock = 256;
 
 inline unsigned blocks_for(size_t threads) { return (unsigned)((threads + kBlock - 1) / kBlock); }
 
-__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+template <typename C>
+__device__ __forceinline__ C harmonic(C a, C b) { return C(2) * a * b / (a + b); }
 
 // Sample of a flat thread index and whether it still iterates.
 __device__ __forceinline__ bool inactive(const int32_t* active, size_t s) { return active && !active[s]; }
@@ -44,7 +45,10 @@ __global__ void k_inject(int nc, size_t S, const double* __restrict__ Kf, double
 }
 
 // Correction-grid coefficients: K_c[J][I] = geometric mean of the four
-// children K_f[2J+dj][2I+di] on the injected grid one level finer.
+// children K_f[2J+dj][2I+di] on the injected grid one level finer, computed
+// in C (FP32 for the FP32 correction operators of the mixed form: they steer
+// the iteration only, the refined stage operators stay FP64).
+template <typename C>
 __global__ void k_child_geomean(int nc, size_t S, const double* __restrict__ Kf, double* __restrict__ Kc) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)nc * nc;
@@ -53,12 +57,13 @@ __global__ void k_child_geomean(int nc, size_t S, const double* __restrict__ Kf,
     const int c = (int)(t % cells);
     const int I = c % nc, J = c / nc, nf = 2 * nc;
     const double* k = Kf + s * (size_t)nf * nf + (size_t)(2 * J) * nf + 2 * I;
-    Kc[t] = exp(0.25 * (log(k[0]) + log(k[1]) + log(k[nf]) + log(k[nf + 1])));
+    Kc[t] = (double)exp(C(0.25) * (log((C)k[0]) + log((C)k[1]) + log((C)k[nf]) + log((C)k[nf + 1])));
 }
 
 // Face transmissibilities: harmonic mean inside, 2K on the Dirichlet edges,
-// none on the no-flow edges; optional FP64 copies for refined grids.
-template <typename T>
+// none on the no-flow edges, in arithmetic C; optional FP64 copies for
+// refined grids (which take C = double).
+template <typename T, typename C>
 __global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T* __restrict__ Te,
                                T* __restrict__ Tn, T* __restrict__ D, double* __restrict__ Te64,
                                double* __restrict__ Tn64, double* __restrict__ D64) {
@@ -67,19 +72,19 @@ __global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T*
     if (t >= S * cells) return;
     const int c = (int)(t % cells);
     const int i = c % n, j = c / n;
-    const double k = K[t];
-    const double tw = (i > 0) ? harmonic(K[t - 1], k) : 2.0 * k;
-    const double te = (i < n - 1) ? harmonic(k, K[t + 1]) : 2.0 * k;
-    const double ts = (j > 0) ? harmonic(K[t - n], k) : 0.0;
-    const double tn = (j < n - 1) ? harmonic(k, K[t + n]) : 0.0;
-    const double d = tw + te + ts + tn;
+    const C k = (C)K[t];
+    const C tw = (i > 0) ? harmonic<C>((C)K[t - 1], k) : C(2) * k;
+    const C te = (i < n - 1) ? harmonic<C>(k, (C)K[t + 1]) : C(2) * k;
+    const C ts = (j > 0) ? harmonic<C>((C)K[t - n], k) : C(0);
+    const C tn = (j < n - 1) ? harmonic<C>(k, (C)K[t + n]) : C(0);
+    const C d = tw + te + ts + tn;
     Te[t] = (T)te;
     Tn[t] = (T)tn;
     D[t] = (T)d;
     if (Te64) {
-        Te64[t] = te;
-        Tn64[t] = tn;
-        D64[t] = d;
+        Te64[t] = (double)te;
+        Tn64[t] = (double)tn;
+        D64[t] = (double)d;
     }
 }
 
@@ -117,6 +122,72 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b
     if (j > 0) acc += Tn[c - n] * p[c - n];
     if (j < n - 1) acc += Tn[c] * p[c + n];
     p[c] = acc / D[c];
+}
+
+// nsweeps red-black sweeps (colour 0 then 1) on tiles of TI x TI cells of
+// one sample, staged in shared memory with a halo of hh = 2 nsweeps cells:
+// each half-sweep leaves one more ring at the halo's edge stale, so after
+// 2 nsweeps half-sweeps exactly the interior is current.  Every cell update
+// is the colour kernel's, in the same order, so the result is bit-identical
+// to 2 nsweeps k_rbgs_color launches while p, b and the coefficients cross
+// HBM once.  Grid: S * tiles^2 CTAs, tile index fastest.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int hh, int nsweeps,
+                                                   const T* __restrict__ b, const T* __restrict__ Te,
+                                                   const T* __restrict__ Tn, const T* __restrict__ D,
+                                                   T* __restrict__ p, const int32_t* __restrict__ active) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    const int tiles = (n + TI - 1) / TI;
+    const size_t s = blockIdx.x / ((unsigned)tiles * tiles);
+    if (s >= S || inactive(active, s)) return;
+    const int tid = (int)(blockIdx.x % ((unsigned)tiles * tiles));
+    const int ti = tid % tiles, tj = tid / tiles;
+    const int xa = max(ti * TI - hh, 0), ya = max(tj * TI - hh, 0);
+    const int xb = min(ti * TI + TI + hh, n), yb = min(tj * TI + TI + hh, n);
+    const int RW = xb - xa, RH = yb - ya, R = RW * RH;
+    T* sp = reinterpret_cast<T*>(tile_smem);
+    T* sb = sp + R;
+    T* se = sb + R;
+    T* sn = se + R;
+    T* sd = sn + R;
+    const size_t base = s * (size_t)n * n;
+    for (int e = threadIdx.x; e < R; e += blockDim.x) {
+        const int r = e / RW, q = e % RW;
+        const size_t g = base + (size_t)(ya + r) * n + xa + q;
+        sp[e] = p[g];
+        sb[e] = b[g];
+        se[e] = Te[g];
+        sn[e] = Tn[g];
+        sd[e] = D[g];
+    }
+    __syncthreads();
+    const int W2 = (RW + 1) / 2;
+    for (int hs = 0; hs < 2 * nsweeps; ++hs) {
+        const int color = hs & 1;
+        for (int h = threadIdx.x; h < RH * W2; h += blockDim.x) {
+            const int r = h / W2;
+            const int q = 2 * (h % W2) + ((color + xa + ya + r) & 1);
+            if (q >= RW) continue;
+            const int i = xa + q, j = ya + r;
+            // a cell whose in-domain neighbour lies outside the region is not updated
+            if ((i > 0 && q == 0) || (i < n - 1 && q == RW - 1) || (j > 0 && r == 0) || (j < n - 1 && r == RH - 1))
+                continue;
+            const int e = r * RW + q;
+            T acc = sb[e];
+            if (i > 0) acc += se[e - 1] * sp[e - 1];
+            if (i < n - 1) acc += se[e] * sp[e + 1];
+            if (j > 0) acc += sn[e - RW] * sp[e - RW];
+            if (j < n - 1) acc += sn[e] * sp[e + RW];
+            sp[e] = acc / sd[e];
+        }
+        __syncthreads();
+    }
+    const int x0 = ti * TI, y0 = tj * TI;
+    const int IW = min(TI, n - x0), IH = min(TI, n - y0);
+    for (int e = threadIdx.x; e < IW * IH; e += blockDim.x) {
+        const int r = e / IW, q = e % IW;
+        p[base + (size_t)(y0 + r) * n + x0 + q] = sp[(y0 - ya + r) * RW + (x0 - xa + q)];
+    }
 }
 
 template <typename T>
@@ -479,6 +550,41 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
     return FM_OK;
 }
 
+// nsweeps red-black sweeps on one grid of every (active) sample: one tile
+// launch (p, b and the coefficients cross HBM once), or, where the staged
+// tile would not fit in shared memory, one launch per colour and sweep.
+template <typename T>
+static void smooth(fm_ctx* ctx, int n, size_t S, int nsweeps, const T* b, const T* Te, const T* Tn, const T* D,
+                   T* p, const int32_t* active, cudaStream_t st) {
+    if (nsweeps <= 0) return;
+    constexpr int kTile = 32;
+    constexpr size_t kMaxSmem = 200 * 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rbgs_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        attr_set = true;
+    }
+    const size_t cells = S * (size_t)n * n;
+    const int TI = n <= kTile ? n : kTile;
+    const int hh = n <= kTile ? 0 : 2 * nsweeps;
+    const int RW = std::min(TI + 2 * hh, n);
+    const size_t smem = 5 * (size_t)RW * RW * sizeof(T);
+    // FP64 updates are bound by the FP64 divide, which the halo's redundant
+    // updates would add to: FP64 keeps one launch per colour
+    if (sizeof(T) == 4 && smem <= kMaxSmem) {
+        const int tiles = (n + TI - 1) / TI;
+        FM_TIMED(ctx, kFamSmoother, st, 6.0 * sizeof(T) * cells, 10.0 * nsweeps * cells,
+                 k_rbgs_tile<T><<<(unsigned)(S * tiles * tiles), 256, smem, st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D,
+                                                                                    p, active));
+        return;
+    }
+    const size_t half = cells / 2;
+    for (int it = 0; it < nsweeps; ++it)
+        for (int color = 0; color < 2; ++color)
+            FM_TIMED(ctx, kFamSmoother, st, 3.0 * sizeof(T) * cells, 5.0 * cells,
+                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, b, Te, Tn, D, p, active));
+}
+
 // One V(nu1, nu2) cycle on grid k; grid `top` carries the stage operator
 // (injected K), the grids below it the correction operators (child means).
 template <typename T>
@@ -501,15 +607,7 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     }
     const int n = g.n;
     const size_t cells = S * (size_t)n * n;
-    const size_t half = cells / 2;
-    // algorithmic bytes of one colour: half of a single-pass sweep that reads
-    // p, b, Te, Tn, D and writes p (6 words per cell)
-    const double sweep_half_bytes = 3.0 * ts * cells, sweep_half_flops = 5.0 * cells;
-    for (int it = 0; it < prm.nu1; ++it)
-        for (int color = 0; color < 2; ++color)
-            FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, Te, Tn, D, g.p,
-                                                                          active));
+    smooth<T>(ctx, n, S, prm.nu1, g.b, Te, Tn, D, g.p, active, st);
     const GridBufs<T>& c = H.g[k - 1];
     FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
              k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
@@ -517,11 +615,7 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     vcycle(H, k - 1, top, prm, active, st);
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
              k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, g.p, active));
-    for (int it = 0; it < prm.nu2; ++it)
-        for (int color = 0; color < 2; ++color)
-            FM_TIMED(ctx, kFamSmoother, st, sweep_half_bytes, sweep_half_flops,
-                     k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, g.b, Te, Tn, D, g.p,
-                                                                          active));
+    smooth<T>(ctx, n, S, prm.nu2, g.b, Te, Tn, D, g.p, active, st);
 }
 
 template <typename P>
@@ -580,17 +674,23 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
     for (int k = 0; k <= H.m; ++k) {
         const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
-        FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts + (g.Te64 ? 24.0 : 0.0)) * cells, 16.0 * cells,
-                 k_coefficients<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D, g.Te64,
-                                                                         g.Tn64, g.D64));
+        // FP64 arithmetic for FP64 grids and for the refined grids' FP64 copies
+        if (sizeof(T) == 8 || g.Te64)
+            FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts + (g.Te64 ? 24.0 : 0.0)) * cells, 16.0 * cells,
+                     k_coefficients<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D,
+                                                                                     g.Te64, g.Tn64, g.D64));
+        else
+            FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts) * cells, 16.0 * cells,
+                     k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D,
+                                                                               nullptr, nullptr, nullptr));
     }
     for (int k = 0; k < H.m; ++k) {
         const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
         FM_TIMED(ctx, kFamCoefficients, st, (32.0 + 8.0 + 3.0 * ts) * cells, 40.0 * cells,
-                 k_child_geomean<<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, H.g[k + 1].K, g.Kc);
-                 k_coefficients<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.Kc, g.TeC, g.TnC, g.DC,
-                                                                         nullptr, nullptr, nullptr));
+                 k_child_geomean<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, H.g[k + 1].K, g.Kc);
+                 k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.Kc, g.TeC, g.TnC, g.DC,
+                                                                            nullptr, nullptr, nullptr));
     }
     if (H.m >= 1) {
         const int m = H.n0 * H.n0;

@@ -824,7 +824,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         ctx->prof.active = prof_on;
         FM_CUDA_TRY(ctx, ce);
         FM_CUDA_TRY(ctx, cudaGraphInstantiate(&exec, graph, 0));
-        const int pidx = prof_start(ctx, kFamMlp, ts);
+        const int pidx = prof_start(ctx, kFamMlpTrain, ts);
         FM_CUDA_TRY(ctx, cudaGraphLaunch(exec, ts));
         FM_CUDA_TRY(ctx, cudaStreamSynchronize(ts));
         first_loss = batch_loss();
