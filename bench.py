@@ -43,6 +43,7 @@ def parse():
                     choices=["mixed_surrogate", "mixed", "fp64_converged", "fp64_fmg2"])
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-qmc-leg", action="store_true", help="skip timing the randomized-QMC estimator")
     return ap.parse_args()
 
 
@@ -215,19 +216,26 @@ def make_ctx(fm, wl, rank, form):
                       converged=f["converged"], tol=1e-10, qtol=1e-9, max_cycles=200)
 
 
+# randomized QMC (Algorithm 2): 32 points per shift and level to start, 16 digital shifts
+QMC_PILOT = 32
+
+
 def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=False, clocks=None,
-                   dist=None, form="mixed"):
+                   dist=None, form="mixed", qmc=None):
     sur = FORMS[form]["surrogate"]
     cost = None
     if sur:
         ctx.surrogate_train(**SURROGATE_TRAIN)
         cost = surrogate_cost(torch, ctx)
 
+    qmc = args.qmc if qmc is None else qmc
+    n_pilot = wl.n_pilot if not qmc else QMC_PILOT
+
     def estimate():
         if not sur:
-            return ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+            return ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot)
         rep = ctx.surrogate_train(**SURROGATE_TRAIN)
-        r = ctx.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, surrogate=True, surrogate_cost=cost)
+        r = ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, surrogate=True, surrogate_cost=cost)
         r["train"] = rep
         r["surrogate_cost"] = cost
         return r
@@ -307,6 +315,23 @@ def run_native(args, wl, eps):
                         "V_per_level": [float(x) for x in rs[-1]["V"]]}
         c2.close()
 
+    # the randomized-QMC estimator (16 shifted Sobol' point sets, doubling rule)
+    # in the chosen form and in the plain FP64 form, timed the same way
+    qmc_forms = {}
+    for form in ([] if (args.qmc or args.no_qmc_leg) else [args.form, "fp64_converged"]):
+        c2 = make_ctx(fm, wl, rank, form)
+        c2.kl_basis_set(B_dev)
+        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
+                                      form=form, qmc=True)
+        qmc_forms[form] = {"value": float(np.mean(ts)), "unit": "s",
+                           "estimate": float(np.mean([r["estimate"] for r in rs])),
+                           "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in rs]))),
+                           "N_per_level_per_shift": [int(x) for x in rs[-1]["N"]],
+                           "shifts": wl.n_shifts, "rounds": int(rs[-1]["rounds"])}
+        if FORMS[form]["surrogate"]:
+            qmc_forms[form]["N_s_per_shift"] = int(rs[-1]["N_s"])
+        c2.close()
+
     # end to end through the public API from pinned host memory: basis upload,
     # estimate, result read-back
     B_host = torch.empty((n_ref * n_ref, wl.M), dtype=torch.float64).pin_memory()
@@ -375,6 +400,7 @@ def run_native(args, wl, eps):
         "samples_per_s_per_level": [float(n / t) if t > 0 else None for n, t in
                                     zip(results[-1]["N"], results[-1]["level_seconds"])],
         "other_forms": others,
+        "qmc": qmc_forms,
         "roofline": roof,
         "kernel_families": families,
         "gpu_launches": total_launches,

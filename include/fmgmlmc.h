@@ -287,6 +287,61 @@ typedef struct {
  * C_l = (4/3) (n_level0 << l)^2.  Uses the default stream, synchronous. */
 fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out);
 
+/* ---------------------------------------------------------------- controller over ranks */
+
+/* Callbacks of the sample-size controller.  `ext_level` counts the levels
+ * the controller sees (with the surrogate, 0 is the surrogate level and
+ * l + 1 MLMC level l).  enqueue: add samples first .. first+n-1 of
+ * ext_level (QMC shift `shift`, or -1 for MC) to this rank's running sums,
+ * asynchronously if it likes.  read: finish the queued work and copy this
+ * rank's running sums, [n_ext][R] cells (R = 1 for MC), to `local`.
+ * allgather: place every rank's `local` (bytes_per_rank each) into `all`,
+ * rank r at offset r * bytes_per_rank, on every rank.  Each returns FM_OK or
+ * an error status, which ends the estimate with that status. */
+typedef fm_status (*fm_enqueue_fn)(void* user, int32_t ext_level, uint64_t first, uint64_t n, int32_t shift);
+typedef fm_status (*fm_read_fn)(void* user, fm_level_sums* local);
+typedef fm_status (*fm_allgather_fn)(void* user, const fm_level_sums* local, fm_level_sums* all,
+                                     size_t bytes_per_rank);
+
+typedef struct {
+    int32_t n_ext;         /* levels seen by the controller, 1 .. FM_MAX_LEVELS + 1 */
+    const double* cost;    /* [n_ext] cost of one sample of each level (> 0) */
+    double eps;            /* target RMSE */
+    int32_t qmc;           /* 0: MC rule (Algorithm 3); 1: QMC doubling rule (Algorithm 2) */
+    int32_t n_shifts;      /* R for QMC (2 .. 64) */
+    int64_t n_pilot;       /* initial samples per level (per shift for QMC), >= 2 */
+    int32_t max_rounds;    /* controller rounds (<= 0: 100) */
+    int32_t rank, world;   /* this rank and the number of ranks (world 1: no allgather) */
+} fm_core_opts;
+
+typedef struct {
+    double estimate, var_estimator;
+    double mean[FM_MAX_LEVELS + 1], var[FM_MAX_LEVELS + 1];
+    int64_t N[FM_MAX_LEVELS + 1];    /* samples per level over all ranks (per shift for QMC) */
+    int32_t rounds;
+} fm_core_result;
+
+/* Rank `rank`'s contiguous share of samples first .. first+n-1 among `world`
+ * ranks: floor(n / world) each, the remainder one apiece to the lowest
+ * ranks.  Host only. */
+void fm_shard_range(uint64_t first, uint64_t n, int32_t rank, int32_t world, uint64_t* my_first, uint64_t* my_n);
+
+/* The controller of mlmc_estimate over callbacks (Algorithms 1-3 at a fixed
+ * finest level; sample sizes as in mlmc_estimate).  Every request is split
+ * by fm_shard_range; the ranks' sums are folded in rank order (Neumaier), so
+ * all ranks compute the same schedule and the same estimate.  Host only: it
+ * makes no CUDA call.  On an error status `err` (nullable, errlen bytes)
+ * holds a message. */
+fm_status mlmc_estimate_core(const fm_core_opts* opts, fm_enqueue_fn enqueue, fm_read_fn read,
+                             fm_allgather_fn allgather, void* user, fm_core_result* out, char* err, size_t errlen);
+
+/* mlmc_estimate with the samples of every request shared among `world`
+ * ranks (one context per rank, each on its own GPU): rank r solves its
+ * contiguous share, and `allgather` (with `user`) exchanges the level sums
+ * once per controller round.  world = 1 is mlmc_estimate.  Synchronous. */
+fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* opts, int32_t rank, int32_t world,
+                                fm_allgather_fn allgather, void* user, fm_result* out);
+
 /* Synchronise the device and report device-side failures of earlier
  * asynchronous calls on ctx: FM_ETIMEOUT if a bounded wait inside a kernel
  * ran out (its output is then invalid), FM_ECUDA for a CUDA error. */

@@ -12,7 +12,8 @@ import torch
 from . import _lib
 from ._lib import FM_PREC_FP64, FM_PREC_MIXED, STATUS_NAMES
 
-__all__ = ["Context", "FmError", "FM_PREC_FP64", "FM_PREC_MIXED", "load_library"]
+__all__ = ["Context", "FmError", "FM_PREC_FP64", "FM_PREC_MIXED", "load_library", "shard_range",
+           "estimate_core", "allgather_over"]
 
 
 class FmError(RuntimeError):
@@ -37,6 +38,79 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def shard_range(first, n, rank, world):
+    """(first, count) of rank `rank`'s contiguous share of samples first .. first+n-1."""
+    L = _lib.load()
+    a, b = C.c_uint64(), C.c_uint64()
+    L.fm_shard_range(first, n, rank, world, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def allgather_over(group=None):
+    """gather(local_bytes) -> bytes of every rank's buffer in rank order, over a
+    torch.distributed group (gloo on the host, nccl through the GPU)."""
+    import torch.distributed as dist
+
+    def gather(data):
+        world = dist.get_world_size(group)
+        dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        t = torch.frombuffer(bytearray(data), dtype=torch.uint8).to(dev)
+        parts = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(parts, t, group=group)
+        return b"".join(p.cpu().numpy().tobytes() for p in parts)
+    return gather
+
+
+def _allgather_cb(gather):
+    if gather is None:
+        return _lib.ALLGATHER_FN()
+
+    def cb(user, local, all_, nbytes):
+        try:
+            res = gather(C.string_at(local, nbytes))
+            C.memmove(all_, res, len(res))
+            return 0
+        except Exception:
+            return _lib.FM_EINVAL
+    return _lib.ALLGATHER_FN(cb)
+
+
+def estimate_core(cost, eps, enqueue, read, gather=None, qmc=False, n_shifts=0, n_pilot=1000,
+                  max_rounds=100, rank=0, world=1):
+    """mlmc_estimate_core over Python callables: enqueue(ext_level, first, n, shift) queues
+    samples on this rank; read() returns this rank's running sums as a sequence of
+    FmLevelSums ([n_ext][R]); gather(bytes) -> bytes of all ranks (None for one rank)."""
+    L = _lib.load()
+    n_ext = len(cost)
+    costs = (C.c_double * n_ext)(*[float(c) for c in cost])
+    opts = _lib.FmCoreOpts(n_ext, costs, eps, int(bool(qmc)), n_shifts, n_pilot, max_rounds, rank, world)
+
+    def enq(user, e, first, n, shift):
+        try:
+            enqueue(int(e), int(first), int(n), int(shift))
+            return 0
+        except Exception:
+            return _lib.FM_EINVAL
+
+    def rd(user, local):
+        try:
+            sums = read()
+            for i, v in enumerate(sums):
+                local[i] = v
+            return 0
+        except Exception:
+            return _lib.FM_EINVAL
+
+    cb_e, cb_r, cb_g = _lib.ENQUEUE_FN(enq), _lib.READ_FN(rd), _allgather_cb(gather)
+    res = _lib.FmCoreResult()
+    err = C.create_string_buffer(512)
+    st = L.mlmc_estimate_core(C.byref(opts), cb_e, cb_r, cb_g, None, C.byref(res), err, 512)
+    if st != 0:
+        raise FmError(st, err.value.decode())
+    return dict(estimate=res.estimate, var_estimator=res.var_estimator, means=np.array(res.mean[:n_ext]),
+                V=np.array(res.var[:n_ext]), N=np.array(res.N[:n_ext]), rounds=res.rounds)
 
 
 class Context:
@@ -240,12 +314,25 @@ class Context:
         self._check(self._L.surrogate_enable(self._h, int(bool(on))))
 
     def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100, surrogate=False,
-                      surrogate_cost=0.01):
+                      surrogate_cost=0.01, group=None, shard=None):
+        """With a torch.distributed `group` of several ranks (one context per rank, all
+        with the same seed), or shard = (rank, world, gather) with gather(bytes) ->
+        bytes of all ranks, every request is shared among the ranks and the level
+        sums are exchanged once per round; all ranks return the same estimate."""
         torch.cuda.synchronize()
         opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds, int(bool(surrogate)),
                                    surrogate_cost)
         res = _lib.FmResult()
-        self._check(self._L.mlmc_estimate(self._h, C.byref(opts), C.byref(res)))
+        if group is not None:
+            import torch.distributed as dist
+            shard = (dist.get_rank(group), dist.get_world_size(group), allgather_over(group))
+        if shard is None:
+            self._check(self._L.mlmc_estimate(self._h, C.byref(opts), C.byref(res)))
+        else:
+            rank, world, gather = shard
+            cb = _allgather_cb(gather)
+            self._check(self._L.mlmc_estimate_sharded(self._h, C.byref(opts), rank, world, cb, None,
+                                                      C.byref(res)))
         L = len(self.levels)
         return dict(estimate=res.estimate, var_estimator=res.var_estimator,
                     means=np.array(res.mean[:L]), V=np.array(res.var[:L]),

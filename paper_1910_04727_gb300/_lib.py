@@ -24,7 +24,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
            "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static",
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
-           "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc"]
+           "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
+           "mlmc_estimate_core", "mlmc_estimate_sharded"]
 
 
 class FmConfig(C.Structure):
@@ -79,6 +80,22 @@ class FmResult(C.Structure):
                 ("level_seconds", C.c_double * FM_MAX_LEVELS), ("seconds_s", C.c_double)]
 
 
+class FmCoreOpts(C.Structure):
+    _fields_ = [("n_ext", C.c_int32), ("cost", C.POINTER(C.c_double)), ("eps", C.c_double),
+                ("qmc", C.c_int32), ("n_shifts", C.c_int32), ("n_pilot", C.c_int64),
+                ("max_rounds", C.c_int32), ("rank", C.c_int32), ("world", C.c_int32)]
+
+
+class FmCoreResult(C.Structure):
+    _fields_ = [("estimate", C.c_double), ("var_estimator", C.c_double),
+                ("mean", C.c_double * (FM_MAX_LEVELS + 1)), ("var", C.c_double * (FM_MAX_LEVELS + 1)),
+                ("N", C.c_int64 * (FM_MAX_LEVELS + 1)), ("rounds", C.c_int32)]
+
+
+ENQUEUE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32)
+READ_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(FmLevelSums))
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(FmLevelSums), C.POINTER(FmLevelSums), C.c_size_t)
+
 _lib = None
 
 
@@ -119,6 +136,11 @@ def load(path=None):
         "surrogate_eval": (I32, [P, U32, P, P, P]),
         "surrogate_enable": (I32, [P, I32]),
         "surrogate_eval_mc": (I32, [P, U32, U64, U32, P, P]),
+        "fm_shard_range": (None, [U64, U64, I32, I32, C.POINTER(U64), C.POINTER(U64)]),
+        "mlmc_estimate_core": (I32, [C.POINTER(FmCoreOpts), ENQUEUE_FN, READ_FN, ALLGATHER_FN, P,
+                                     C.POINTER(FmCoreResult), C.c_char_p, C.c_size_t]),
+        "mlmc_estimate_sharded": (I32, [P, C.POINTER(FmEstimateOpts), I32, I32, ALLGATHER_FN, P,
+                                        C.POINTER(FmResult)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

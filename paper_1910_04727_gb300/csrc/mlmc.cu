@@ -15,7 +15,6 @@
 namespace fm {
 
 constexpr int kSumBlock = 256;
-constexpr double kMaxSamplesPerLevel = 1e9;   // guard against a runaway sample-size rule
 constexpr int kSumItems = 2048;   // samples per block
 
 struct Pair {
@@ -184,24 +183,84 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
     return FM_OK;
 }
 
-extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out) {
+namespace {
+
+// GPU side of the controller: samples go to mlmc_sample_level with the
+// running sums of (level, shift) cell e * R + r in ctx->d_sums; an event pair
+// around each request gives the device time per level.
+struct GpuSampler {
+    fm_ctx* ctx;
+    int off, R;
+    size_t cells;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> lev;
+    size_t used = 0;
+    double lsec[FM_MAX_LEVELS + 1] = {};
+    ~GpuSampler() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    cudaEvent_t event() {
+        if (used == ev.size()) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+    void collect() {
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) lsec[lev[i / 2]] += ms * 1e-3;
+        }
+        used = 0;
+        lev.clear();
+    }
+};
+
+fm_status gpu_enqueue(void* user, int32_t e, uint64_t first, uint64_t n, int32_t shift) {
+    GpuSampler* g = static_cast<GpuSampler*>(user);
+    cudaEvent_t e0 = g->event(), e1 = g->event();
+    g->lev.push_back(e);
+    cudaEventRecord(e0, nullptr);
+    fm_level_sums* cell = g->ctx->d_sums + (size_t)e * g->R + (shift < 0 ? 0 : shift);
+    for (uint64_t done = 0; done < n;) {
+        const uint32_t cnt = (uint32_t)std::min<uint64_t>(n - done, (uint64_t)1 << 30);
+        FM_TRY(mlmc_sample_level(g->ctx, e - g->off, first + done, cnt, shift, cell, nullptr, nullptr, nullptr));
+        done += cnt;
+    }
+    cudaEventRecord(e1, nullptr);
+    return FM_OK;
+}
+
+fm_status gpu_read(void* user, fm_level_sums* local) {
+    GpuSampler* g = static_cast<GpuSampler*>(user);
+    FM_TRY(fm_sync(g->ctx));
+    g->collect();
+    FM_CUDA_TRY(g->ctx, cudaMemcpy(local, g->ctx->d_sums, g->cells * sizeof(fm_level_sums), cudaMemcpyDeviceToHost));
+    return FM_OK;
+}
+
+}  // namespace
+
+extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* opts, int32_t rank, int32_t world,
+                                           fm_allgather_fn allgather, void* user, fm_result* out) {
     FM_CHECK_ARG(ctx, ctx != nullptr, "mlmc_estimate: null context");
     FM_CHECK_ARG(ctx, opts && out, "mlmc_estimate: null argument");
     FM_CHECK_ARG(ctx, opts->eps > 0, "mlmc_estimate: eps must be positive");
     FM_CHECK_ARG(ctx, opts->n_pilot >= 2, "mlmc_estimate: n_pilot must be >= 2");
     FM_CHECK_ARG(ctx, !opts->qmc || ctx->cfg.n_shifts >= 2, "mlmc_estimate: QMC needs n_shifts >= 2");
-    const auto t0 = std::chrono::steady_clock::now();
+    FM_CHECK_ARG(ctx, world >= 1 && rank >= 0 && rank < world && (world == 1 || allgather),
+                 "mlmc_estimate: bad rank / world, or no allgather for several ranks");
     FM_CHECK_ARG(ctx, !opts->surrogate || (ctx->mlp && opts->surrogate_cost > 0),
                  "mlmc_estimate: the surrogate level needs a trained network and surrogate_cost > 0");
-    // Extended levels e = 0 .. L_e: with the surrogate, e = 0 is the S level
+    const auto t0 = std::chrono::steady_clock::now();
+    // Extended levels e = 0 .. L: with the surrogate, e = 0 is the S level
     // and e = l + 1 MLMC level l; without it e = l.
     const int off = opts->surrogate ? 1 : 0;
     const int Lr = ctx->cfg.n_levels - 1;
     const int L = Lr + off;
     const int R = opts->qmc ? ctx->cfg.n_shifts : 1;
-    const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 100;
     const size_t cells = (size_t)(L + 1) * R;
-    std::vector<fm_level_sums> h(cells);
     FM_CUDA_TRY(ctx, cudaMemset(ctx->d_sums, 0, cells * sizeof(fm_level_sums)));
     double C[FM_MAX_LEVELS + 1];
     for (int e = 0; e <= L; ++e) {
@@ -210,11 +269,6 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
     }
     if (off) C[0] *= opts->surrogate_cost;   // S-level cost relative to a level-0 sample
     std::memset(out, 0, sizeof(*out));
-    int64_t N[FM_MAX_LEVELS + 1] = {};
-    int64_t dN[FM_MAX_LEVELS + 1];
-    for (int l = 0; l <= L; ++l) dN[l] = opts->n_pilot;
-    double mean[FM_MAX_LEVELS + 1] = {}, var[FM_MAX_LEVELS + 1] = {};
-    int rounds = 0;
     const int saved_on = ctx->surrogate_on;
     ctx->surrogate_on = opts->surrogate ? 1 : 0;
     struct Restore {
@@ -223,158 +277,51 @@ extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm
         ~Restore() { c->surrogate_on = v; }
     } restore{ctx, saved_on};
 
-    // device time per extended level: an event pair around each level's
-    // sampling, read back at the next synchronisation
-    struct LevelTimer {
-        std::vector<cudaEvent_t> ev;
-        std::vector<int> lev;
-        size_t used = 0;
-        ~LevelTimer() {
-            for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        }
-    } lt;
-    double lsec[FM_MAX_LEVELS + 1] = {};
-    auto event = [&]() -> cudaEvent_t {
-        if (lt.used == lt.ev.size()) {
-            cudaEvent_t e = nullptr;
-            cudaEventCreate(&e);
-            lt.ev.push_back(e);
-        }
-        return lt.ev[lt.used++];
-    };
-    auto collect = [&]() {
-        for (size_t i = 0; i + 1 < lt.used; i += 2) {
-            float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, lt.ev[i], lt.ev[i + 1]) == cudaSuccess) lsec[lt.lev[i / 2]] += ms * 1e-3;
-        }
-        lt.used = 0;
-        lt.lev.clear();
-    };
-
-    auto refresh = [&]() -> fm_status {
-        FM_TRY(fm_sync(ctx));
-        collect();
-        FM_CUDA_TRY(ctx, cudaMemcpy(h.data(), ctx->d_sums, cells * sizeof(fm_level_sums), cudaMemcpyDeviceToHost));
-        for (int l = 0; l <= L; ++l) {
-            if (!opts->qmc) {
-                const fm_level_sums& s = h[l];
-                const double n = s.count;
-                const double sy = fold(s.sum_y), sy2 = fold(s.sum_y2);
-                if (!std::isfinite(sy) || !std::isfinite(sy2)) {
-                    set_error(ctx, "mlmc_estimate: non-finite samples on level " + std::to_string(l));
-                    return FM_ENOTCONV;
-                }
-                mean[l] = sy / n;
-                var[l] = n > 1 ? std::max(0.0, (sy2 - sy * sy / n) / (n - 1)) : 0.0;
-            } else {
-                double m[64];
-                double mm = 0.0;
-                for (int r = 0; r < R; ++r) {
-                    const fm_level_sums& s = h[(size_t)l * R + r];
-                    m[r] = fold(s.sum_y) / s.count;
-                    if (!std::isfinite(m[r])) {
-                        set_error(ctx, "mlmc_estimate: non-finite samples on level " + std::to_string(l));
-                        return FM_ENOTCONV;
-                    }
-                    mm += m[r];
-                }
-                mm /= R;
-                double v = 0.0;
-                for (int r = 0; r < R; ++r) v += (m[r] - mm) * (m[r] - mm);
-                mean[l] = mm;
-                var[l] = v / ((double)R * (R - 1));
-            }
-        }
-        return FM_OK;
-    };
-
-    auto run = [&](int l, int64_t first, int64_t cnt) -> fm_status {
-        cudaEvent_t e0 = event(), e1 = event();
-        lt.lev.push_back(l);
-        cudaEventRecord(e0, nullptr);
-        for (int r = 0; r < R; ++r)
-            FM_TRY(mlmc_sample_level(ctx, l - off, (uint64_t)first, (uint32_t)cnt, opts->qmc ? r : -1,
-                                     ctx->d_sums + (size_t)l * R + r, nullptr, nullptr, nullptr));
-        cudaEventRecord(e1, nullptr);
-        return FM_OK;
-    };
-
-    if (!opts->qmc) {
-        // Algorithm 1 / 3 at fixed L: evaluate dN, update V_l and the optimal N_l, repeat.
-        while (rounds < max_rounds) {
-            bool any = false;
-            for (int l = 0; l <= L; ++l)
-                if (dN[l] > 0) {
-                    FM_TRY(run(l, N[l], dN[l]));
-                    N[l] += dN[l];
-                    any = true;
-                }
-            if (!any) break;
-            ++rounds;
-            FM_TRY(refresh());
-            double tot = 0.0;
-            for (int l = 0; l <= L; ++l) tot += std::sqrt(var[l] * C[l]);
-            for (int l = 0; l <= L; ++l) {
-                const double opt = std::ceil(2.0 / (opts->eps * opts->eps) * std::sqrt(var[l] / C[l]) * tot);
-                if (!std::isfinite(opt) || opt > kMaxSamplesPerLevel) {
-                    set_error(ctx, "mlmc_estimate: level " + std::to_string(l) + " would need " +
-                                       std::to_string(opt) + " samples (variance " + std::to_string(var[l]) +
-                                       "); beyond the per-level cap");
-                    return FM_ENOTCONV;
-                }
-                dN[l] = std::max<int64_t>(0, (int64_t)opt - N[l]);
-            }
-        }
-        double v = 0.0;
-        for (int l = 0; l <= L; ++l) v += var[l] / (double)N[l];
-        out->var_estimator = v;
-    } else {
-        // Algorithm 2 at fixed L: pilot, then double N_l at argmax V[Y_l]/(N_l C_l).
-        for (int l = 0; l <= L; ++l) {
-            FM_TRY(run(l, 0, opts->n_pilot));
-            N[l] = opts->n_pilot;
-        }
-        FM_TRY(refresh());
-        while (rounds < max_rounds) {
-            double tot = 0.0;
-            for (int l = 0; l <= L; ++l) tot += var[l];
-            if (tot <= opts->eps * opts->eps / 2) break;
-            int best = 0;
-            double bv = -1.0;
-            for (int l = 0; l <= L; ++l) {
-                const double v = var[l] / ((double)N[l] * C[l]);
-                if (v > bv) { bv = v; best = l; }
-            }
-            FM_CHECK_ARG(ctx, N[best] <= ((int64_t)1 << 31), "mlmc_estimate: QMC point budget exhausted");
-            FM_TRY(run(best, N[best], N[best]));
-            N[best] *= 2;
-            ++rounds;
-            FM_TRY(refresh());
-        }
-        double v = 0.0;
-        for (int l = 0; l <= L; ++l) v += var[l];
-        out->var_estimator = v;
+    GpuSampler g;
+    g.ctx = ctx;
+    g.off = off;
+    g.R = R;
+    g.cells = cells;
+    fm_core_opts co{};
+    co.n_ext = L + 1;
+    co.cost = C;
+    co.eps = opts->eps;
+    co.qmc = opts->qmc;
+    co.n_shifts = R;
+    co.n_pilot = opts->n_pilot;
+    co.max_rounds = opts->max_rounds;
+    co.rank = rank;
+    co.world = world;
+    fm_core_result cr{};
+    char msg[512] = {0};
+    const fm_status st = mlmc_estimate_core(&co, gpu_enqueue, gpu_read, allgather, &g, &cr, msg, sizeof(msg));
+    if (st != FM_OK) {
+        if (msg[0]) set_error(ctx, msg);
+        return st;
     }
-    double est = 0.0;
-    for (int e = 0; e <= L; ++e) est += mean[e];
+    out->estimate = cr.estimate;
+    out->var_estimator = cr.var_estimator;
     for (int l = 0; l <= Lr; ++l) {
-        out->mean[l] = mean[l + off];
-        out->var[l] = var[l + off];
-        out->N[l] = N[l + off];
+        out->mean[l] = cr.mean[l + off];
+        out->var[l] = cr.var[l + off];
+        out->N[l] = cr.N[l + off];
+        out->level_seconds[l] = g.lsec[l + off];
     }
-    for (int l = 0; l <= Lr; ++l) out->level_seconds[l] = lsec[l + off];
-    out->seconds_s = off ? lsec[0] : 0.0;
     if (off) {
-        out->mean_s = mean[0];
-        out->var_s = var[0];
-        out->N_s = N[0];
+        out->mean_s = cr.mean[0];
+        out->var_s = cr.var[0];
+        out->N_s = cr.N[0];
+        out->seconds_s = g.lsec[0];
     }
-    out->estimate = est;
     out->alpha = fit_rate(out->mean, Lr);
     out->beta = fit_rate(out->var, Lr);
     out->bias = (std::isfinite(out->alpha) && out->alpha > 0)
                     ? std::fabs(out->mean[Lr]) / (std::pow(2.0, out->alpha) - 1.0) : NAN;
-    out->rounds = rounds;
+    out->rounds = cr.rounds;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return FM_OK;
+}
+
+extern "C" fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out) {
+    return mlmc_estimate_sharded(ctx, opts, 0, 1, nullptr, nullptr, out);
 }
