@@ -231,6 +231,57 @@ fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double*
 fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                                  const fm_solve_params* prm, double* d_qf, double* d_qc, void* stream);
 
+/* ---------------------------------------------------------------- uneven batches */
+
+/* One group of an uneven batch: `count` samples of one grid size. */
+typedef struct {
+    int32_t n_fine;        /* finest grid n_coarsest * 2^m */
+    uint32_t count;        /* samples */
+    const double* d_K;     /* device [count][n_fine][n_fine] coefficients */
+    double* d_qf;          /* device [count] outflux of the finest grid */
+    double* d_qc;          /* device [count] outflux of grid n_fine / 2 (nullable) */
+    int32_t* d_status;     /* device [count] per-sample FM_OK / FM_ENOTCONV (nullable) */
+} fm_batch_group;
+
+/* FMG solves of groups with different grid sizes as one CUDA graph: one
+ * branch per group, the resident kernel for grids up to 64 x 64 and the
+ * level-wise schedule above, the refined stages of the converged mode
+ * looping on the device (conditional graph nodes), so the graph runs without
+ * the host.  Each sample's results are those fmg_solve_batch gives it.  The
+ * executable graph stays in ctx and is updated in place when the next call
+ * has the same shape.  prm->kernel: FM_KERNEL_AUTO or FM_KERNEL_LEVELWISE
+ * (every group level-wise).  Asynchronous on `stream`; one call at a time
+ * per ctx.  Scratch is allocated before the capture (FM_ENOMEM). */
+fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_batch_group* groups,
+                           const fm_solve_params* prm, void* stream);
+
+/* Graph bookkeeping of fmg_solve_uneven: instantiations, in-place updates and
+ * launches so far (host only). */
+fm_status fmg_uneven_stats(const fm_ctx* ctx, int64_t* instantiations, int64_t* updates, int64_t* launches);
+
+/* ---------------------------------------------------------------- autotuning */
+
+/* One tuned grid: the smoother launch shape chosen for it. */
+typedef struct {
+    int32_t n;            /* grid n x n */
+    int32_t tile;         /* tile interior staged in shared memory (0: one launch per colour and sweep) */
+    int32_t threads;      /* threads per CTA of the tile launch */
+    double ms_best;       /* one smoothing call (nsweeps sweeps) with the chosen shape, milliseconds */
+    double ms_default;    /* the same with the built-in default shape */
+    int64_t samples;      /* samples of the timing batch (about 64 Mi cells) */
+} fm_tune_entry;
+
+/* Times the red-black smoother's launch shapes (one launch per colour, or
+ * tiles of 8, 16, 32, 64 cells staged in shared memory with a 2 nsweeps halo,
+ * at 128 or 256 threads) for the grids n_min, 2 n_min, ..., <= n_max on a
+ * synthetic batch of about 64 Mi cells per grid, and keeps the fastest in
+ * ctx for that precision (FM_PREC_FP64: the FP64 grids; FM_PREC_MIXED: the
+ * FP32 ones).  Every later solve on ctx uses the choice; the sweeps' results
+ * are the same whichever shape runs.  Synchronous; entries (nullable) gets up
+ * to max_entries rows. */
+fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps, int32_t n_min, int32_t n_max,
+                      fm_tune_entry* entries, int32_t max_entries, int32_t* n_entries);
+
 /* ---------------------------------------------------------------- MLMC */
 
 /* Running sums of one (level, shift) cell: Neumaier-compensated FP64 pairs

@@ -233,6 +233,38 @@ class Context:
                                             _ptr(p), _ptr(st), _stream()))
         return (qf, qc, p, st) if want_status else (qf, qc, p)
 
+    def solve_uneven(self, Ks, want_qc=True, want_status=False, **params):
+        """One CUDA graph over groups of different grid sizes: Ks is a list of CUDA
+        float64 tensors [count][n][n].  Returns [(qf, qc, status)] per group."""
+        prm = self.solve_params(**params)
+        groups = (_lib.FmBatchGroup * len(Ks))()
+        outs = []
+        for g, K in enumerate(Ks):
+            S, n = K.shape[0], K.shape[1]
+            qf = torch.empty(S, dtype=torch.float64, device="cuda")
+            qc = torch.empty(S, dtype=torch.float64, device="cuda") if want_qc else None
+            st = torch.zeros(S, dtype=torch.int32, device="cuda") if want_status else None
+            groups[g] = _lib.FmBatchGroup(n, S, K.data_ptr(), qf.data_ptr(), qc.data_ptr() if want_qc else None,
+                                          st.data_ptr() if want_status else None)
+            outs.append((qf, qc, st))
+        self._check(self._L.fmg_solve_uneven(self._h, len(Ks), groups, C.byref(prm), _stream()))
+        return outs
+
+    def uneven_stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.fmg_uneven_stats(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return dict(instantiations=a.value, updates=b.value, launches=c.value)
+
+    def autotune(self, precision=None, nsweeps=None, n_min=8, n_max=None):
+        """Times the smoother launch shapes per grid and keeps the fastest (fm_autotune)."""
+        precision = self.cfg.precision if precision is None else precision
+        nsweeps = self.cfg.nu1 if nsweeps is None else nsweeps
+        n_max = n_max or self.levels[-1]
+        out = (_lib.FmTuneEntry * 16)()
+        cnt = C.c_int32()
+        self._check(self._L.fm_autotune(self._h, precision, nsweeps, n_min, n_max, out, 16, C.byref(cnt)))
+        return [{f: getattr(e, f) for f, _ in _lib.FmTuneEntry._fields_} for e in out[:cnt.value]]
+
     # ----------------------------------------------------------- MLMC
     @staticmethod
     def new_sums(count=1):

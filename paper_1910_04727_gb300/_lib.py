@@ -25,7 +25,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static",
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
-           "mlmc_estimate_core", "mlmc_estimate_sharded"]
+           "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
+           "fmg_uneven_stats"]
 
 
 class FmConfig(C.Structure):
@@ -92,6 +93,16 @@ class FmCoreResult(C.Structure):
                 ("N", C.c_int64 * (FM_MAX_LEVELS + 1)), ("rounds", C.c_int32)]
 
 
+class FmTuneEntry(C.Structure):
+    _fields_ = [("n", C.c_int32), ("tile", C.c_int32), ("threads", C.c_int32), ("ms_best", C.c_double),
+                ("ms_default", C.c_double), ("samples", C.c_int64)]
+
+
+class FmBatchGroup(C.Structure):
+    _fields_ = [("n_fine", C.c_int32), ("count", C.c_uint32), ("d_K", C.c_void_p), ("d_qf", C.c_void_p),
+                ("d_qc", C.c_void_p), ("d_status", C.c_void_p)]
+
+
 ENQUEUE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32)
 READ_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(FmLevelSums))
 ALLGATHER_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(FmLevelSums), C.POINTER(FmLevelSums), C.c_size_t)
@@ -136,6 +147,9 @@ def load(path=None):
         "surrogate_eval": (I32, [P, U32, P, P, P]),
         "surrogate_enable": (I32, [P, I32]),
         "surrogate_eval_mc": (I32, [P, U32, U64, U32, P, P]),
+        "fm_autotune": (I32, [P, I32, I32, I32, I32, P, I32, C.POINTER(I32)]),
+        "fmg_solve_uneven": (I32, [P, I32, P, C.POINTER(FmSolveParams), P]),
+        "fmg_uneven_stats": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         "fm_shard_range": (None, [U64, U64, I32, I32, C.POINTER(U64), C.POINTER(U64)]),
         "mlmc_estimate_core": (I32, [C.POINTER(FmCoreOpts), ENQUEUE_FN, READ_FN, ALLGATHER_FN, P,
                                      C.POINTER(FmCoreResult), C.c_char_p, C.c_size_t]),

@@ -62,6 +62,13 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
         set_error(nullptr, "fm_create: copy of the direction numbers failed");
         return FM_ECUDA;
     }
+    if (cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        fm_destroy(ctx);
+        set_error(nullptr, "fm_create: stream creation failed");
+        return FM_ECUDA;
+    }
+    fmg_init_attributes();
+    resident_init_attributes();
     *out = ctx;
     return FM_OK;
 }
@@ -78,6 +85,8 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     cudaFree(ctx->d_partials);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     mlp_free(ctx);
+    uneven_free(ctx);
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
     for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->tc.basis[l]);
     cudaFree(ctx->tc.xi);
     cudaFree(ctx->tc.err);

@@ -89,7 +89,7 @@ void set_error(const fm_ctx* ctx, const std::string& msg);
 enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
-    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamilyCount
+    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamilyCount
 };
 
 struct ProfRecord {
@@ -112,6 +112,13 @@ struct Arena {
     char* base = nullptr;
     size_t capacity = 0;
     size_t used = 0;
+};
+
+// Smoother launch shape per (precision, grid): chosen by fm_autotune.
+struct TuneTable {
+    int32_t n[2][16] = {};        // grid the entry was tuned for (0: none)
+    int32_t tile[2][16] = {};     // tile interior (0: one launch per colour)
+    int32_t threads[2][16] = {};
 };
 
 // Tensor-core KL synthesis state (kl_tc.cu).
@@ -153,6 +160,9 @@ struct fm_ctx {
     fm::TcState tc;
     void* mlp = nullptr;             // surrogate network state (mlp.cu)
     int surrogate_on = 0;            // level -1 = S(xi), level 0 = Q_0 - S(xi)
+    cudaStream_t body_stream = nullptr;  // captures the bodies of device-side refinement loops
+    fm::TuneTable tune;              // smoother launch shapes (fm_autotune)
+    void* uneven = nullptr;          // uneven-batch executor state (uneven.cu)
 };
 
 namespace fm {
@@ -192,6 +202,15 @@ void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops
 int64_t batch_limit(const fm_ctx* ctx, int n);
 
 // FMG solve into caller-provided outputs (used by mlmc_sample_level too).
+// The same with the level-wise scratch taken from `ar` (grown when short,
+// which must not happen during stream capture: see fmg_levelwise_scratch).
+fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const double* d_K,
+                         const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
+                         int32_t* d_status, cudaStream_t st);
+size_t fmg_levelwise_scratch(const fm_ctx* ctx, int n_fine, uint32_t S, const fm_solve_params& prm);
+void fmg_init_attributes();
+void resident_init_attributes();
+void uneven_free(fm_ctx* ctx);
 fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
                          const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
                          int32_t* d_status, cudaStream_t stream);

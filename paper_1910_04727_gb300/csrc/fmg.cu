@@ -130,12 +130,16 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b
 // 2 nsweeps half-sweeps exactly the interior is current.  Every cell update
 // is the colour kernel's, in the same order, so the result is bit-identical
 // to 2 nsweeps k_rbgs_color launches while p, b and the coefficients cross
-// HBM once.  Grid: S * tiles^2 CTAs, tile index fastest.
+// HBM once.  The iterate is read from p_in and written to p_out (another
+// buffer): a tile's halo is its neighbours' interior, which must still hold
+// the values from before the call whatever order the CTAs run in.  Grid:
+// S * tiles^2 CTAs, tile index fastest; inactive samples are not written.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int hh, int nsweeps,
                                                    const T* __restrict__ b, const T* __restrict__ Te,
                                                    const T* __restrict__ Tn, const T* __restrict__ D,
-                                                   T* __restrict__ p, const int32_t* __restrict__ active) {
+                                                   const T* __restrict__ p_in, T* __restrict__ p_out,
+                                                   const int32_t* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
     const int tiles = (n + TI - 1) / TI;
     const size_t s = blockIdx.x / ((unsigned)tiles * tiles);
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
     for (int e = threadIdx.x; e < R; e += blockDim.x) {
         const int r = e / RW, q = e % RW;
         const size_t g = base + (size_t)(ya + r) * n + xa + q;
-        sp[e] = p[g];
+        sp[e] = p_in[g];
         sb[e] = b[g];
         se[e] = Te[g];
         sn[e] = Tn[g];
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
     const int IW = min(TI, n - x0), IH = min(TI, n - y0);
     for (int e = threadIdx.x; e < IW * IH; e += blockDim.x) {
         const int r = e / IW, q = e % IW;
-        p[base + (size_t)(y0 + r) * n + x0 + q] = sp[(y0 - ya + r) * RW + (x0 - xa + q)];
+        p_out[base + (size_t)(y0 + r) * n + x0 + q] = sp[(y0 - ya + r) * RW + (x0 - xa + q)];
     }
 }
 
@@ -446,6 +450,7 @@ struct GridBufs {
     int n;
     const double* K;
     T *Te, *Tn, *D, *p, *b;
+    T* p2;                             // second iterate buffer of the tile smoother
     double* Kc;                        // correction-grid coefficients (k < m)
     T *TeC, *TnC, *DC;                 // their faces and diagonal
     double *p64, *Te64, *Tn64, *D64;   // refined grids of the mixed form only
@@ -462,6 +467,7 @@ struct Hierarchy {
     T* AinvC;          // coarsest correction operator (child means)
     int32_t* active;   // per-sample iterate flags of converged stages
     int32_t* left;     // count of samples still iterating
+    int32_t* iter;     // residual tests done in the current refined stage (graph loops)
     double* qprev;     // outflux of the previous iteration per sample
 };
 
@@ -471,12 +477,12 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
     while ((n0 << m) < n_fine) ++m;
     for (int k = 0; k <= m; ++k) {
         const size_t c = (size_t)(n0 << k) * (n0 << k);
-        total += c * (8 + 5 * tsize) + 5 * 256;
+        total += c * (8 + 6 * tsize) + 6 * 256;
         if (k < m) total += c * (8 + 3 * tsize) + 4 * 256;
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
     total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
-    if (converged) total += 4 * 2 + 8 + 3 * 256;
+    if (converged) total += 4 * 3 + 8 + 4 * 256;
     return total * S + 4096;
 }
 
@@ -490,21 +496,23 @@ int64_t batch_limit(const fm_ctx* ctx, int n) {
     return std::max<int64_t>(lim, 1);
 }
 
+// Scratch of a level-wise batch of S samples: grows `ar` when it is too small
+// (never while a stream is being captured: callers size it first).
 template <typename T>
-static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t S, const double* d_K,
+static fm_status carve(fm_ctx* ctx, Arena& ar, Hierarchy<T>& H, int n_fine, int n0, size_t S, const double* d_K,
                        bool mixed, bool converged) {
     const size_t need = hierarchy_bytes(n_fine, n0, S, sizeof(T), mixed, converged);
-    if (ctx->arena.capacity < need) {
-        if (ctx->arena.base) cudaFree(ctx->arena.base);
-        ctx->arena.base = nullptr;
-        ctx->arena.capacity = 0;
-        if (cudaMalloc((void**)&ctx->arena.base, need) != cudaSuccess) {
+    if (ar.capacity < need) {
+        if (ar.base) cudaFree(ar.base);
+        ar.base = nullptr;
+        ar.capacity = 0;
+        if (cudaMalloc((void**)&ar.base, need) != cudaSuccess) {
             set_error(ctx, "fmg scratch allocation of " + std::to_string(need) + " bytes failed");
             return FM_ENOMEM;
         }
-        ctx->arena.capacity = need;
+        ar.capacity = need;
     }
-    char* cur = ctx->arena.base;
+    char* cur = ar.base;
     auto take = [&](size_t bytes) {
         char* p = cur;
         cur += ((bytes + 255) / 256) * 256;
@@ -526,6 +534,7 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
         g.D = (T*)take(cnt * sizeof(T));
         g.p = (T*)take(cnt * sizeof(T));
         g.b = (T*)take(cnt * sizeof(T));
+        g.p2 = (T*)take(cnt * sizeof(T));
         g.Kc = nullptr;
         g.TeC = g.TnC = g.DC = nullptr;
         if (k < H.m) {
@@ -546,43 +555,77 @@ static fm_status carve(fm_ctx* ctx, Hierarchy<T>& H, int n_fine, int n0, size_t 
     H.AinvC = (T*)take(S * (size_t)n0 * n0 * n0 * n0 * sizeof(T));
     H.active = converged ? (int32_t*)take(S * 4) : nullptr;
     H.left = converged ? (int32_t*)take(4) : nullptr;
+    H.iter = converged ? (int32_t*)take(4) : nullptr;
     H.qprev = converged ? (double*)take(S * 8) : nullptr;
     return FM_OK;
+}
+
+constexpr size_t kMaxSmem = 200 * 1024;   // dynamic shared memory of the tile smoother
+
+// Kernel attributes, set once per process before any launch or capture.
+void fmg_init_attributes() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_rbgs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        cudaFuncSetAttribute(k_rbgs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    });
 }
 
 // nsweeps red-black sweeps on one grid of every (active) sample: one tile
 // launch (p, b and the coefficients cross HBM once), or, where the staged
 // tile would not fit in shared memory, one launch per colour and sweep.
-template <typename T>
-static void smooth(fm_ctx* ctx, int n, size_t S, int nsweeps, const T* b, const T* Te, const T* Tn, const T* D,
-                   T* p, const int32_t* active, cudaStream_t st) {
-    if (nsweeps <= 0) return;
-    constexpr int kTile = 32;
-    constexpr size_t kMaxSmem = 200 * 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_rbgs_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-        attr_set = true;
-    }
-    const size_t cells = S * (size_t)n * n;
-    const int TI = n <= kTile ? n : kTile;
-    const int hh = n <= kTile ? 0 : 2 * nsweeps;
+static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
+    const int TI = std::min(tile, n);
+    const int hh = TI >= n ? 0 : 2 * nsweeps;
     const int RW = std::min(TI + 2 * hh, n);
-    const size_t smem = 5 * (size_t)RW * RW * sizeof(T);
-    // FP64 updates are bound by the FP64 divide, which the halo's redundant
-    // updates would add to: FP64 keeps one launch per colour
-    if (sizeof(T) == 4 && smem <= kMaxSmem) {
+    return 5 * (size_t)RW * RW * tsize;
+}
+
+// Launch shape `tile` (tile interior staged in shared memory, p_in -> p_out;
+// 0: one launch per colour and sweep, in place on p_in) with `threads` per
+// CTA.  Returns the buffer that holds the result.
+template <typename T>
+static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int nsweeps, const T* b, const T* Te,
+                      const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st) {
+    if (nsweeps <= 0) return p_in;
+    const size_t cells = S * (size_t)n * n;
+    if (tile > 0) {
+        const int TI = std::min(tile, n);
+        const int hh = TI >= n ? 0 : 2 * nsweeps;
         const int tiles = (n + TI - 1) / TI;
         FM_TIMED(ctx, kFamSmoother, st, 6.0 * sizeof(T) * cells, 10.0 * nsweeps * cells,
-                 k_rbgs_tile<T><<<(unsigned)(S * tiles * tiles), 256, smem, st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D,
-                                                                                    p, active));
-        return;
+                 k_rbgs_tile<T><<<(unsigned)(S * tiles * tiles), threads, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
+                                  st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+        return p_out;
     }
+    T* p = p_in;
     const size_t half = cells / 2;
     for (int it = 0; it < nsweeps; ++it)
         for (int color = 0; color < 2; ++color)
             FM_TIMED(ctx, kFamSmoother, st, 3.0 * sizeof(T) * cells, 5.0 * cells,
                      k_rbgs_color<T><<<blocks_for(half), kBlock, 0, st>>>(n, S, color, b, Te, Tn, D, p, active));
+    return p;
+}
+
+static int tune_slot(int n) { return std::min(15, 31 - __builtin_clz((unsigned)n)); }
+
+// Smoother launch shape of grid n: FP32 tiles of 32 x 32 by default; FP64,
+// bound by its divide (which the halo's redundant updates add to), one
+// launch per colour; an fm_autotune entry for this grid and precision
+// replaces the default.  Tiles need both smoothing phases of the V-cycle
+// (so the iterate goes p -> p2 -> p) and their staged region in shared memory.
+template <typename T>
+static void smooth_shape(const fm_ctx* ctx, int n, const fm_solve_params& prm, int* tile, int* threads) {
+    const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
+    *tile = sizeof(T) == 4 ? 32 : 0;
+    *threads = 256;
+    if (ctx->tune.n[pi][slot] == n) {
+        *tile = ctx->tune.tile[pi][slot];
+        *threads = ctx->tune.threads[pi][slot];
+    }
+    if (*tile > 0 && (prm.nu1 < 1 || prm.nu2 < 1 ||
+                      tile_smem_bytes(*tile, n, std::max(prm.nu1, prm.nu2), sizeof(T)) > kMaxSmem))
+        *tile = 0;
 }
 
 // One V(nu1, nu2) cycle on grid k; grid `top` carries the stage operator
@@ -607,15 +650,18 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     }
     const int n = g.n;
     const size_t cells = S * (size_t)n * n;
-    smooth<T>(ctx, n, S, prm.nu1, g.b, Te, Tn, D, g.p, active, st);
+    int tile, threads;
+    smooth_shape<T>(ctx, n, prm, &tile, &threads);
+    // pre-smoothing p -> p2 (tiles) or in place; post-smoothing back into p
+    T* cur = smooth_with<T>(ctx, tile, threads, n, S, prm.nu1, g.b, Te, Tn, D, g.p, g.p2, active, st);
     const GridBufs<T>& c = H.g[k - 1];
     FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
              k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
-                 c.n, S, g.b, Te, Tn, D, g.p, c.b, c.p, active));
+                 c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
     vcycle(H, k - 1, top, prm, active, st);
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
-             k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, g.p, active));
-    smooth<T>(ctx, n, S, prm.nu2, g.b, Te, Tn, D, g.p, active, st);
+             k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, cur, active));
+    smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st);
 }
 
 template <typename P>
@@ -625,11 +671,74 @@ static void outflux(fm_ctx* ctx, int n, size_t S, const double* K, const P* p, d
              k_outflux<P><<<blocks_for(S * 32), kBlock, 0, st>>>(n, S, K, p, pE, q));
 }
 
+// Loop control of a refined stage inside a CUDA graph: after residual test
+// number *it, another pass runs while a sample is still active and fewer than
+// max_cycles tests have been made; the bound ends every loop.
+__global__ void k_refine_cond(const int32_t* __restrict__ left, int32_t* __restrict__ it, int max_cycles,
+                              cudaGraphConditionalHandle h) {
+    const int i = *it;
+    *it = i + 1;
+    cudaGraphSetConditional(h, (*left > 0 && i < max_cycles) ? 1u : 0u);
+}
+
+// The refined stage as a device-side loop of the graph being captured on
+// st: a residual test, then a conditional WHILE node whose body is nu0
+// V-cycles (masked to the active samples), the FP64 update of the mixed form
+// and the next test.  No host synchronisation; the same tests and updates in
+// the same order as the host loop of refine_stage.
+template <typename T>
+static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve_params& prm, bool mixed,
+                                    int32_t* status, cudaStream_t st) {
+    fm_ctx* ctx = H.ctx;
+    const GridBufs<T>& g = H.g[k];
+    const size_t S = H.S, cells = (size_t)g.n * g.n;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    FM_CUDA_TRY(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    FM_CUDA_TRY(ctx, cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+    auto test = [&](cudaStream_t s) {
+        cudaMemsetAsync(H.left, 0, sizeof(int32_t), s);
+        k_stage_check<T><<<(unsigned)S, kBlock, 0, s>>>(g.n, S, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64,
+                                                        g.Te64, g.Tn64, g.D64, g.b, g.p, prm.tol, prm.qtol, H.qprev,
+                                                        H.active, H.left);
+        k_refine_cond<<<1, 1, 0, s>>>(H.left, H.iter, prm.max_cycles, h);
+    };
+    FM_CUDA_TRY(ctx, cudaMemsetAsync(H.active, 0xff, S * sizeof(int32_t), st));   // all active (-1)
+    FM_CUDA_TRY(ctx, cudaMemsetAsync(H.qprev, 0xff, S * sizeof(double), st));     // NaN
+    FM_CUDA_TRY(ctx, cudaMemsetAsync(H.iter, 0, sizeof(int32_t), st));
+    test(st);
+    FM_CUDA_TRY(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    FM_CUDA_TRY(ctx, cudaGraphAddNode(&node, graph, deps, nullptr, nd, &np));
+    FM_CUDA_TRY(ctx, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t bs = ctx->body_stream;
+    FM_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed));
+    for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, bs);
+    if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active);
+    test(bs);
+    cudaGraph_t body = nullptr;
+    FM_CUDA_TRY(ctx, cudaStreamEndCapture(bs, &body));
+    if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
+    return FM_OK;
+}
+
 // Cycles of one refined stage until every sample passes its residual test.
 template <typename T>
 static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_params& prm, bool mixed,
                               int32_t* status, cudaStream_t st) {
     fm_ctx* ctx = H.ctx;
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    FM_CUDA_TRY(ctx, cudaStreamIsCapturing(st, &capturing));
+    if (capturing == cudaStreamCaptureStatusActive) return refine_stage_graph(H, k, prm, mixed, status, st);
     const GridBufs<T>& g = H.g[k];
     const size_t S = H.S, cells = (size_t)g.n * g.n;
     FM_CUDA_TRY(ctx, cudaMemsetAsync(H.active, 0xff, S * sizeof(int32_t), st));   // all active (-1)
@@ -751,7 +860,7 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
 }
 
 template <typename T>
-static fm_status levelwise(fm_ctx* ctx, int n_fine, int n0, uint32_t S, const double* d_K,
+static fm_status levelwise(fm_ctx* ctx, Arena& ar, int n_fine, int n0, uint32_t S, const double* d_K,
                            const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
                            int32_t* d_status, cudaStream_t st) {
     const bool mixed = prm.precision == FM_PREC_MIXED;
@@ -760,7 +869,7 @@ static fm_status levelwise(fm_ctx* ctx, int n_fine, int n0, uint32_t S, const do
         const size_t cnt = (size_t)std::min<uint64_t>((uint64_t)lim, S - first);
         const size_t off = first * (size_t)n_fine * n_fine;
         Hierarchy<T> H;
-        FM_TRY(carve(ctx, H, n_fine, n0, cnt, d_K + off, mixed, prm.converged != 0));
+        FM_TRY(carve(ctx, ar, H, n_fine, n0, cnt, d_K + off, mixed, prm.converged != 0));
         FM_TRY(fmg_batch(H, prm, d_qf + first, d_qc ? d_qc + first : nullptr, d_p ? d_p + off : nullptr,
                          d_status ? d_status + first : nullptr, st));
         FM_CUDA_TRY(ctx, cudaGetLastError());
@@ -768,7 +877,20 @@ static fm_status levelwise(fm_ctx* ctx, int n_fine, int n0, uint32_t S, const do
     return FM_OK;
 }
 
+// Scratch bytes a level-wise solve of S samples of grid n_fine takes (one batch).
+size_t fmg_levelwise_scratch(const fm_ctx* ctx, int n_fine, uint32_t S, const fm_solve_params& prm) {
+    const bool mixed = prm.precision == FM_PREC_MIXED;
+    const size_t cnt = (size_t)std::min<int64_t>(batch_limit(ctx, n_fine), S);
+    return hierarchy_bytes(n_fine, prm.n_coarsest, cnt, mixed ? 4 : 8, mixed, prm.converged != 0);
+}
+
 fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
+                         const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
+                         int32_t* d_status, cudaStream_t st) {
+    return fmg_solve_with(ctx, ctx->arena, n_fine, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
+}
+
+fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const double* d_K,
                          const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
                          int32_t* d_status, cudaStream_t st) {
     const int n0 = prm.n_coarsest;
@@ -799,8 +921,8 @@ fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
                      "(n_fine <= 64)");
     }
     if (prm.precision == FM_PREC_MIXED)
-        return levelwise<float>(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
-    return levelwise<double>(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
+        return levelwise<float>(ctx, ar, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
+    return levelwise<double>(ctx, ar, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -862,6 +984,7 @@ static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine
         g.D = (double*)take(cnt * 8);
         g.p = (double*)take(cnt * 8);
         g.b = (double*)take(cnt * 8);
+        g.p2 = (double*)take(cnt * 8);
         g.Kc = nullptr;
         g.TeC = g.TnC = g.DC = nullptr;
         if (k < H.m) {
@@ -876,12 +999,119 @@ static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine
     H.AinvC = (double*)take(S * (size_t)n0 * n0 * n0 * n0 * 8);
     H.active = nullptr;
     H.left = nullptr;
+    H.iter = nullptr;
     H.qprev = nullptr;
+}
+
+// ------------------------------------------------------------------ autotuning
+// Synthetic smoothing problem for timing: faces in (0.5, 1.5), a diagonal
+// that dominates them, rhs and iterate in (-1, 1) (a hash of the index).
+template <typename T>
+__global__ void k_tune_fill(size_t count, T* __restrict__ b, T* __restrict__ Te, T* __restrict__ Tn,
+                            T* __restrict__ D, T* __restrict__ p) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    uint64_t h = t * 0x9E3779B97F4A7C15ULL;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ULL;
+    h ^= h >> 29;
+    const double u0 = (double)(h & 0xFFFFF) / 1048576.0, u1 = (double)((h >> 20) & 0xFFFFF) / 1048576.0;
+    const double u2 = (double)((h >> 40) & 0xFFFFF) / 1048576.0;
+    Te[t] = (T)(0.5 + u0);
+    Tn[t] = (T)(0.5 + u1);
+    D[t] = (T)(4.5 + u2);
+    b[t] = (T)(2.0 * u2 - 1.0);
+    p[t] = (T)(2.0 * u0 - 1.0);
+}
+
+template <typename T>
+static fm_status autotune_grid(fm_ctx* ctx, int n, int nsweeps, fm_tune_entry* e) {
+    // about 64 Mi cells per call (well beyond L2), at least one sample
+    const size_t S = std::max<size_t>(1, ((size_t)64 << 20) / ((size_t)n * n));
+    const size_t cells = S * (size_t)n * n;
+    T* buf = nullptr;
+    FM_CUDA_TRY(ctx, cudaMalloc((void**)&buf, 6 * cells * sizeof(T)));
+    T *b = buf, *Te = b + cells, *Tn = Te + cells, *D = Tn + cells, *p = D + cells, *p2 = p + cells;
+    k_tune_fill<T><<<blocks_for(cells), kBlock>>>(cells, b, Te, Tn, D, p);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = ctx->prof.active;
+    ctx->prof.active = false;
+    auto time_shape = [&](int tile, int threads) -> double {
+        if (tile > 0 && tile_smem_bytes(tile, n, nsweeps, sizeof(T)) > kMaxSmem) return 1e30;
+        smooth_with<T>(ctx, tile, threads, n, S, nsweeps, b, Te, Tn, D, p, p2, nullptr, nullptr);   // warm-up
+        cudaEventRecord(e0);
+        for (int r = 0; r < 4; ++r)   // p -> p2 -> p for tiles
+            smooth_with<T>(ctx, tile, threads, n, S, nsweeps, b, Te, Tn, D, r & 1 ? p2 : p, r & 1 ? p : p2, nullptr,
+                           nullptr);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 4.0;
+    };
+    const int def_tile = sizeof(T) == 4 ? 32 : 0;
+    double best = 1e30;
+    int bt = def_tile, bth = 256;
+    e->ms_default = time_shape(def_tile, 256);
+    const int tiles[] = {0, 8, 16, 32, 64};
+    const int thr[] = {128, 256};
+    for (int tile : tiles) {
+        if (tile > 0 && tile > n && tile != 8) continue;   // one whole-grid candidate is enough
+        for (int th : thr) {
+            if (tile == 0 && th != 256) continue;             // colour launches have a fixed shape
+            const double ms = time_shape(tile, th);
+            if (ms < best) {
+                best = ms;
+                bt = tile;
+                bth = th;
+            }
+        }
+    }
+    if (e->ms_default <= best) {   // the default, timed first, stays unless beaten
+        best = e->ms_default;
+        bt = def_tile;
+        bth = 256;
+    }
+    ctx->prof.active = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
+    ctx->tune.n[pi][slot] = n;
+    ctx->tune.tile[pi][slot] = bt;
+    ctx->tune.threads[pi][slot] = bth;
+    e->n = n;
+    e->tile = bt;
+    e->threads = bth;
+    e->ms_best = best;
+    e->samples = (int64_t)S;
+    return FM_OK;
 }
 
 }  // namespace fm
 
 using namespace fm;
+
+extern "C" fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps, int32_t n_min, int32_t n_max,
+                                 fm_tune_entry* entries, int32_t max_entries, int32_t* n_entries) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_autotune: null context");
+    FM_CHECK_ARG(ctx, precision == FM_PREC_FP64 || precision == FM_PREC_MIXED, "fm_autotune: unknown precision");
+    FM_CHECK_ARG(ctx, nsweeps >= 1 && nsweeps <= 8, "fm_autotune: nsweeps must be 1..8");
+    FM_CHECK_ARG(ctx, n_min >= 2 && n_max >= n_min && n_max <= 8192, "fm_autotune: bad grid range");
+    int count = 0;
+    for (int n = n_min; n <= n_max; n *= 2) {
+        fm_tune_entry e{};
+        if (precision == FM_PREC_MIXED) FM_TRY(autotune_grid<float>(ctx, n, nsweeps, &e));
+        else FM_TRY(autotune_grid<double>(ctx, n, nsweeps, &e));
+        if (entries && count < max_entries) entries[count] = e;
+        ++count;
+    }
+    if (n_entries) *n_entries = std::min(count, max_entries);
+    return FM_OK;
+}
 
 extern "C" fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                                             const fm_solve_params* prm, double* d_qf, double* d_qc,

@@ -20,6 +20,7 @@
 // for the correction, which is added to the FP64 iterate.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -596,12 +597,6 @@ static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st)
     const int groups = WARP ? 4 : 1;
     const size_t smem = groups * (resident_slot_bytes<T>() + resident_smem_bytes(a.n_fine, a.n0, MIXED));
     if (smem > kResidentSmemMax) return false;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_fmg_resident<T, MIXED, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kResidentSmemMax);
-        attr_done = true;
-    }
     const int threads = WARP ? 32 * groups : (a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fmg_resident<T, MIXED, WARP>, threads, smem);
@@ -619,6 +614,17 @@ template <typename T, bool MIXED>
 static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st) {
     if (a.n_fine <= 16) return launch_resident<T, MIXED, true>(ctx, a, st);
     return launch_resident<T, MIXED, false>(ctx, a, st);
+}
+
+void resident_init_attributes() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const int m = (int)kResidentSmemMax;
+        cudaFuncSetAttribute(k_fmg_resident<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        cudaFuncSetAttribute(k_fmg_resident<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        cudaFuncSetAttribute(k_fmg_resident<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        cudaFuncSetAttribute(k_fmg_resident<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    });
 }
 
 bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double* d_K,

@@ -1,0 +1,184 @@
+// Uneven batches: groups of samples with different grid sizes solved in one
+// CUDA graph.
+//
+// Every group gets a branch of its own (fork and join events around it):
+// groups whose hierarchy fits in shared memory run the resident kernel (a
+// persistent grid, one sample per CTA or warp), the others the level-wise
+// schedule with its scratch in an arena of the group's own.  The converged
+// stages of the level-wise schedule loop on the device (a conditional WHILE
+// node per refined stage), so nothing in the graph waits for the host.
+// Branches run concurrently: one group's latency-bound coarse grids and
+// residual tests overlap another group's bandwidth-bound fine grids, and
+// the graph removes the gaps between the thousands of small launches.
+//
+// The executable graph is kept in the context: a later call with the same
+// shape (groups, grids, schedule) only updates the kernel parameters
+// (cudaGraphExecUpdate), otherwise it is instantiated anew.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fm {
+
+struct UnevenState {
+    std::vector<Arena> arenas;        // level-wise scratch, one per group
+    std::vector<cudaStream_t> side;   // one branch stream per group
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;       // capture origin
+    cudaGraphExec_t exec = nullptr;
+    int64_t instantiations = 0, updates = 0, launches = 0;
+};
+
+static UnevenState* uneven_state(fm_ctx* ctx) { return static_cast<UnevenState*>(ctx->uneven); }
+
+void uneven_free(fm_ctx* ctx) {
+    UnevenState* U = uneven_state(ctx);
+    if (!U) return;
+    for (Arena& a : U->arenas) cudaFree(a.base);
+    for (cudaStream_t s : U->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : U->join) cudaEventDestroy(e);
+    if (U->fork) cudaEventDestroy(U->fork);
+    if (U->cap) cudaStreamDestroy(U->cap);
+    if (U->exec) cudaGraphExecDestroy(U->exec);
+    delete U;
+    ctx->uneven = nullptr;
+}
+
+static fm_status uneven_prepare(fm_ctx* ctx, int groups) {
+    if (!ctx->uneven) ctx->uneven = new UnevenState();
+    UnevenState* U = uneven_state(ctx);
+    if (!U->cap) {
+        FM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&U->cap, cudaStreamNonBlocking));
+        FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&U->fork, cudaEventDisableTiming));
+    }
+    while ((int)U->side.size() < groups) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        FM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        U->side.push_back(s);
+        U->join.push_back(e);
+        U->arenas.emplace_back();
+    }
+    return FM_OK;
+}
+
+// A hierarchy fits the resident kernel (its shared-memory limit) for n <= 64.
+static bool resident_grid(int n, const fm_solve_params& prm) {
+    return prm.kernel != FM_KERNEL_LEVELWISE && n <= 64;
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_batch_group* groups,
+                                      const fm_solve_params* prm, void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fmg_solve_uneven: null context");
+    FM_CHECK_ARG(ctx, prm != nullptr && groups != nullptr, "fmg_solve_uneven: null argument");
+    FM_CHECK_ARG(ctx, n_groups >= 1 && n_groups <= 64, "fmg_solve_uneven: 1 .. 64 groups");
+    FM_CHECK_ARG(ctx, prm->kernel != FM_KERNEL_RESIDENT, "fmg_solve_uneven: the schedule is chosen per group");
+    const int n0 = prm->n_coarsest;
+    for (int g = 0; g < n_groups; ++g) {
+        const fm_batch_group& G = groups[g];
+        int m = 0;
+        while (m < 16 && (n0 << m) < G.n_fine) ++m;
+        FM_CHECK_ARG(ctx, n0 >= 2 && n0 <= 4 && G.n_fine >= n0 && (n0 << m) == G.n_fine && G.n_fine <= 8192,
+                     "fmg_solve_uneven: group " + std::to_string(g) + ": n_fine must be n_coarsest * 2^m");
+        FM_CHECK_ARG(ctx, G.count == 0 || (G.d_K && G.d_qf),
+                     "fmg_solve_uneven: group " + std::to_string(g) + ": null input or output");
+    }
+    FM_TRY(uneven_prepare(ctx, n_groups));
+    UnevenState* U = uneven_state(ctx);
+    // level-wise scratch is sized before the capture (no allocation inside it)
+    for (int g = 0; g < n_groups; ++g) {
+        const fm_batch_group& G = groups[g];
+        if (G.count == 0 || resident_grid(G.n_fine, *prm)) continue;
+        const size_t need = fmg_levelwise_scratch(ctx, G.n_fine, G.count, *prm);
+        Arena& a = U->arenas[g];
+        if (a.capacity < need) {
+            if (a.base) cudaFree(a.base);
+            a.base = nullptr;
+            a.capacity = 0;
+            if (cudaMalloc((void**)&a.base, need) != cudaSuccess) {
+                set_error(ctx, "fmg_solve_uneven: scratch allocation of " + std::to_string(need) + " bytes failed");
+                return FM_ENOMEM;
+            }
+            a.capacity = need;
+        }
+    }
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    // capture: fork, one branch per group, join
+    const bool prof = ctx->prof.active;
+    ctx->prof.active = false;
+    fm_status st = FM_OK;
+    cudaGraph_t graph = nullptr;
+    FM_CUDA_TRY(ctx, cudaStreamBeginCapture(U->cap, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(U->fork, U->cap);
+    for (int g = 0; g < n_groups && st == FM_OK; ++g) {
+        const fm_batch_group& G = groups[g];
+        if (G.count == 0) continue;
+        cudaStreamWaitEvent(U->side[g], U->fork, 0);
+        fm_solve_params p = *prm;
+        p.kernel = resident_grid(G.n_fine, *prm) ? FM_KERNEL_AUTO : FM_KERNEL_LEVELWISE;
+        st = fmg_solve_with(ctx, U->arenas[g], G.n_fine, G.count, G.d_K, p, G.d_qf, G.d_qc, nullptr, G.d_status,
+                            U->side[g]);
+        cudaEventRecord(U->join[g], U->side[g]);
+        cudaStreamWaitEvent(U->cap, U->join[g], 0);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(U->cap, &graph);
+    ctx->prof.active = prof;
+    if (st != FM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error(ctx, std::string("fmg_solve_uneven: graph capture failed: ") + cudaGetErrorString(ce));
+        cudaGetLastError();
+        return FM_ECUDA;
+    }
+    // same shape as the kept graph: update its parameters; otherwise instantiate
+    bool updated = false;
+    if (U->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(U->exec, graph, &info) == cudaSuccess) {
+            updated = true;
+            ++U->updates;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(U->exec);
+            U->exec = nullptr;
+        }
+    }
+    if (!updated) {
+        const cudaError_t ie = cudaGraphInstantiate(&U->exec, graph, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            U->exec = nullptr;
+            set_error(ctx, std::string("fmg_solve_uneven: graph instantiation failed: ") + cudaGetErrorString(ie));
+            return FM_ECUDA;
+        }
+        ++U->instantiations;
+    }
+    cudaGraphDestroy(graph);
+    cudaStream_t s = as_stream(stream);
+    double cells = 0.0;
+    for (int g = 0; g < n_groups; ++g) cells += (double)groups[g].count * groups[g].n_fine * groups[g].n_fine;
+    FM_TIMED(ctx, kFamUnevenGraph, s, 8.0 * cells, 0.0, cudaGraphLaunch(U->exec, s));
+    ++U->launches;
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
+}
+
+extern "C" fm_status fmg_uneven_stats(const fm_ctx* ctx, int64_t* instantiations, int64_t* updates,
+                                      int64_t* launches) {
+    if (!ctx) return FM_EINVAL;
+    const UnevenState* U = static_cast<const UnevenState*>(ctx->uneven);
+    if (instantiations) *instantiations = U ? U->instantiations : 0;
+    if (updates) *updates = U ? U->updates : 0;
+    if (launches) *launches = U ? U->launches : 0;
+    return FM_OK;
+}
