@@ -40,7 +40,10 @@ def parse():
                     help="budget of the oracle's bounded timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="mixed_surrogate",
-                    choices=["mixed_surrogate", "mixed", "fp64_converged", "fp64_fmg2"])
+                    choices=["mixed_surrogate", "mixed_surrogate_batched", "mixed", "fp64_converged",
+                             "fp64_fmg2"])
+    ap.add_argument("--no-uneven-leg", action="store_true",
+                    help="skip the uneven-batch leg (4096 samples over 64x64 .. 1024x1024)")
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-qmc-leg", action="store_true", help="skip timing the randomized-QMC estimator")
@@ -117,7 +120,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ oracle
 def oracle_params(converged):
     from oracle import lib as olib
-    return olib.params(converged=converged, tol=1e-10, max_cycles=200)
+    return olib.params(converged=converged, tol=SOLVE_TOL, max_cycles=300)
 
 
 def oracle_level_seconds(wl, budget_s, converged):
@@ -172,13 +175,20 @@ def flush_l2(buf):
     buf.fill_(1.0)
 
 
+# refined stages stop at ||b - A p|| <= 1e-12 ||b|| or an outflux change of at
+# most 1e-10 |Q| between tests: per-sample outflux within 1e-8 of the fully
+# converged FP64 solution on every grid up to 1024 x 1024
+SOLVE_TOL, SOLVE_QTOL = 1e-12, 1e-10
+
 FORMS = {
     # the mixed form plus the surrogate control-variate level below 16x16; the
     # network is trained inside every timed step on level-0 samples the
     # solver produces (training data, training and estimate all timed)
     "mixed_surrogate": dict(precision=1, converged=True, surrogate=True),
+    # the same, each round's solves of all levels as one uneven batch (one CUDA graph)
+    "mixed_surrogate_batched": dict(precision=1, converged=True, surrogate=True, batched=True),
     # FP32 smoothing/transfers/coarsest solve inside FP64 iterative refinement
-    # of the stages giving Q^c and Q^f, to ||r|| <= 1e-10 ||b||
+    # of the stages giving Q^c and Q^f (stopping rule above)
     "mixed": dict(precision=1, converged=True, surrogate=False),
     # the same converged solves, every step in FP64
     "fp64_converged": dict(precision=0, converged=True, surrogate=False),
@@ -213,7 +223,7 @@ def make_ctx(fm, wl, rank, form):
     return fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
                       pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
                       n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank, precision=f["precision"],
-                      converged=f["converged"], tol=1e-10, qtol=1e-9, max_cycles=200)
+                      converged=f["converged"], tol=SOLVE_TOL, qtol=SOLVE_QTOL, max_cycles=200)
 
 
 # randomized QMC (Algorithm 2): 32 points per shift and level to start, 16 digital shifts
@@ -231,11 +241,14 @@ def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=Fals
     qmc = args.qmc if qmc is None else qmc
     n_pilot = wl.n_pilot if not qmc else QMC_PILOT
 
+    batched = FORMS[form].get("batched", False)
+
     def estimate():
         if not sur:
-            return ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot)
+            return ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, batched=batched)
         rep = ctx.surrogate_train(**SURROGATE_TRAIN)
-        r = ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, surrogate=True, surrogate_cost=cost)
+        r = ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, surrogate=True, surrogate_cost=cost,
+                              batched=batched)
         r["train"] = rep
         r["surrogate_cost"] = cost
         return r
@@ -264,6 +277,58 @@ def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=Fals
     prof = ctx.profile_end() if profile else None
     clk = clocks.stop() if clocks else None
     return times, results, prof, clk
+
+
+UNEVEN_COUNTS = [3075, 769, 192, 48, 12]   # 4096 samples, N_l ~ 4^-l (optimal ratio for beta ~ 2)
+
+
+def uneven_leg(torch, fm, flush):
+    """4096 samples over 64x64 .. 1024x1024 (256 KL modes, tensor-core BF16x3
+    fields): the FP32-smoothing / FP64-refinement solves level after level
+    (one fmg_solve_batch per grid) against one uneven batch (one CUDA graph),
+    both after autotuning the smoother launch shapes."""
+    wl = W.WORKLOADS["batched4096"]
+    c = fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW, pE=wl.pE,
+                   n_shifts=wl.n_shifts, seed=wl.seed, precision=1, converged=True, tol=SOLVE_TOL,
+                   qtol=SOLVE_QTOL, max_cycles=200)
+    t0 = time.perf_counter()
+    c.kl_basis_build(q=wl.kl_q)
+    basis_s = time.perf_counter() - t0
+    Ks = []
+    for l, cnt in enumerate(UNEVEN_COUNTS):
+        xi = c.mc_points(l, 0, cnt)
+        Ks.append(c.kl_field_batch(l, xi))
+    tune = c.autotune(n_min=8, n_max=wl.levels[-1])
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return float(np.median(ts)), out
+
+    t_seq, seq = timed(lambda: [c.fmg_solve_batch(K) for K in Ks])
+    t_unv, unv = timed(lambda: c.solve_uneven(Ks))
+    same = all(torch.equal(a[0], b[0]) for a, b in zip(seq, unv))
+    n_total = sum(UNEVEN_COUNTS)
+    out = {"workload": wl.name, "levels": wl.levels, "counts": UNEVEN_COUNTS, "kl_modes": wl.M,
+           "kl": "tcgen05 BF16x3 (field error <= 5e-5)", "form": "FP32 smoothing, FP64 refinement (tol %g, "
+           "outflux change %g)" % (SOLVE_TOL, SOLVE_QTOL), "seconds_per_level_calls": t_seq, "seconds_uneven_graph": t_unv,
+           "samples_per_s_per_level_calls": n_total / t_seq, "samples_per_s_uneven_graph": n_total / t_unv,
+           "speedup": t_seq / t_unv, "identical_results": bool(same), "graph": c.uneven_stats(),
+           "kl_basis_build_s": basis_s,
+           "autotune": [{k: e[k] for k in ("n", "tile", "threads", "ms_best", "ms_default")} for e in tune]}
+    c.close()
+    return out
 
 
 def run_native(args, wl, eps):
@@ -314,6 +379,8 @@ def run_native(args, wl, eps):
                         "N_per_level": [int(x) for x in rs[-1]["N"]],
                         "V_per_level": [float(x) for x in rs[-1]["V"]]}
         c2.close()
+
+    uneven = None if args.no_uneven_leg else uneven_leg(torch, fm, flush)
 
     # the randomized-QMC estimator (16 shifted Sobol' point sets, doubling rule)
     # in the chosen form and in the plain FP64 form, timed the same way
@@ -391,7 +458,7 @@ def run_native(args, wl, eps):
         "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
                    "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
                    "fmg": "4x4 exact, nu0=%d V(%d,%d) RB-GS" % (wl.nu0, wl.nu1, wl.nu2),
-                   "form": args.form, "tol": 1e-10, "qtol": 1e-9, "l2": "flushed between steps (512 MiB write)",
+                   "form": args.form, "tol": SOLVE_TOL, "qtol": SOLVE_QTOL, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "captured_variance": captured},
         "estimate": float(np.mean(ests)),
@@ -401,6 +468,7 @@ def run_native(args, wl, eps):
                                     zip(results[-1]["N"], results[-1]["level_seconds"])],
         "other_forms": others,
         "qmc": qmc_forms,
+        "uneven_batch": uneven,
         "roofline": roof,
         "kernel_families": families,
         "gpu_launches": total_launches,
@@ -429,7 +497,7 @@ def run_native(args, wl, eps):
         N = results[-1]["N"]
         t_cpu = float(np.sum(per * N))
         sample = ("oracle FMG-MLMC samples per level %s (%s) timed on %d threads; seconds per sample x "
-                  "the GPU run's N_l (extrapolated)" % (counts, "FP64 V-cycles to 1e-10" if conv
+                  "the GPU run's N_l (extrapolated)" % (counts, "FP64 V-cycles to %g" % SOLVE_TOL if conv
                                                         else "2 V(2,2) per stage", cores))
         if sur:
             r = results[-1]

@@ -314,6 +314,7 @@ typedef struct {
     int32_t max_rounds;
     int32_t surrogate;    /* 1: add the surrogate control-variate level below level 0 */
     double surrogate_cost; /* cost of an S-level sample relative to a level-0 sample */
+    int32_t batched;      /* 1: each round's solves of all levels as one uneven batch (fmg_solve_uneven) */
 } fm_estimate_opts;
 
 typedef struct {
@@ -330,6 +331,7 @@ typedef struct {
     int64_t N_s;                     /* surrogate-level samples */
     double level_seconds[FM_MAX_LEVELS]; /* device time spent sampling each level (CUDA events) */
     double seconds_s;                /* device time spent on the surrogate level */
+    double batched_seconds;          /* batched mode: device time of the rounds' uneven batches */
 } fm_result;
 
 /* The host controller (Algorithm 3 with the MC rule N_l = (2/eps^2)

@@ -346,14 +346,14 @@ class Context:
         self._check(self._L.surrogate_enable(self._h, int(bool(on))))
 
     def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100, surrogate=False,
-                      surrogate_cost=0.01, group=None, shard=None):
+                      surrogate_cost=0.01, group=None, shard=None, batched=False):
         """With a torch.distributed `group` of several ranks (one context per rank, all
         with the same seed), or shard = (rank, world, gather) with gather(bytes) ->
         bytes of all ranks, every request is shared among the ranks and the level
         sums are exchanged once per round; all ranks return the same estimate."""
         torch.cuda.synchronize()
         opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds, int(bool(surrogate)),
-                                   surrogate_cost)
+                                   surrogate_cost, int(bool(batched)))
         res = _lib.FmResult()
         if group is not None:
             import torch.distributed as dist
@@ -371,4 +371,4 @@ class Context:
                     N=np.array(res.N[:L]), alpha=res.alpha, beta=res.beta, bias=res.bias,
                     rounds=res.rounds, seconds=res.seconds, mean_s=res.mean_s, var_s=res.var_s,
                     N_s=res.N_s, level_seconds=np.array(res.level_seconds[:L]),
-                    seconds_s=res.seconds_s)
+                    seconds_s=res.seconds_s, batched_seconds=res.batched_seconds)

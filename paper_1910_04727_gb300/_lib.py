@@ -53,7 +53,8 @@ class FmLevelSums(C.Structure):
 
 class FmEstimateOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("qmc", C.c_int32), ("n_pilot", C.c_int64),
-                ("max_rounds", C.c_int32), ("surrogate", C.c_int32), ("surrogate_cost", C.c_double)]
+                ("max_rounds", C.c_int32), ("surrogate", C.c_int32), ("surrogate_cost", C.c_double),
+                ("batched", C.c_int32)]
 
 
 class FmKernelStat(C.Structure):
@@ -78,7 +79,8 @@ class FmResult(C.Structure):
                 ("N", C.c_int64 * FM_MAX_LEVELS), ("alpha", C.c_double), ("beta", C.c_double),
                 ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double),
                 ("mean_s", C.c_double), ("var_s", C.c_double), ("N_s", C.c_int64),
-                ("level_seconds", C.c_double * FM_MAX_LEVELS), ("seconds_s", C.c_double)]
+                ("level_seconds", C.c_double * FM_MAX_LEVELS), ("seconds_s", C.c_double),
+                ("batched_seconds", C.c_double)]
 
 
 class FmCoreOpts(C.Structure):

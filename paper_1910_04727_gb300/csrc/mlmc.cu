@@ -185,19 +185,46 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
 
 namespace {
 
+struct Request {
+    int e;               // extended level
+    uint64_t first, n;
+    int shift;
+};
+
+// Per-level buffers of a batched round (kept across rounds).
+struct LevelBuf {
+    double *xi = nullptr, *K = nullptr, *q = nullptr;
+    size_t cap = 0;
+};
+
 // GPU side of the controller: samples go to mlmc_sample_level with the
 // running sums of (level, shift) cell e * R + r in ctx->d_sums; an event pair
-// around each request gives the device time per level.
+// around each request gives the device time per level.  Batched: a round's
+// requests are kept until the controller reads the sums, then every level's
+// points and fields are made, all levels are solved as one uneven batch
+// (fmg_solve_uneven), and the sums are added request by request.
 struct GpuSampler {
     fm_ctx* ctx;
     int off, R;
     size_t cells;
+    bool batched = false;
+    std::vector<Request> pending;
+    LevelBuf lb[FM_MAX_LEVELS];
+    double round_sec = 0.0;
+    cudaEvent_t b0 = nullptr, b1 = nullptr;
     std::vector<cudaEvent_t> ev;
     std::vector<int> lev;
     size_t used = 0;
     double lsec[FM_MAX_LEVELS + 1] = {};
     ~GpuSampler() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (LevelBuf& b : lb) {
+            cudaFree(b.xi);
+            cudaFree(b.K);
+            cudaFree(b.q);
+        }
+        if (b0) cudaEventDestroy(b0);
+        if (b1) cudaEventDestroy(b1);
     }
     cudaEvent_t event() {
         if (used == ev.size()) {
@@ -219,6 +246,10 @@ struct GpuSampler {
 
 fm_status gpu_enqueue(void* user, int32_t e, uint64_t first, uint64_t n, int32_t shift) {
     GpuSampler* g = static_cast<GpuSampler*>(user);
+    if (g->batched && e - g->off >= 0) {
+        g->pending.push_back(Request{e, first, n, shift});
+        return FM_OK;
+    }
     cudaEvent_t e0 = g->event(), e1 = g->event();
     g->lev.push_back(e);
     cudaEventRecord(e0, nullptr);
@@ -232,9 +263,94 @@ fm_status gpu_enqueue(void* user, int32_t e, uint64_t first, uint64_t n, int32_t
     return FM_OK;
 }
 
+// The pending requests of a round as one uneven batch (see GpuSampler).
+fm_status flush_batched(GpuSampler* g) {
+    fm_ctx* ctx = g->ctx;
+    if (g->pending.empty()) return FM_OK;
+    const int L = ctx->cfg.n_levels, M = ctx->cfg.M;
+    const fm_solve_params prm = solve_params(ctx);
+    std::vector<uint64_t> total(L, 0);
+    for (const Request& r : g->pending) total[r.e - g->off] += r.n;
+    if (!g->b0) {
+        cudaEventCreate(&g->b0);
+        cudaEventCreate(&g->b1);
+    }
+    cudaEventRecord(g->b0, nullptr);
+    // points and fields, level by level, requests packed in order
+    std::vector<fm_batch_group> groups;
+    std::vector<int> group_level;
+    for (int l = 0; l < L; ++l) {
+        if (!total[l]) continue;
+        const int N = grid_of_level(ctx, l);
+        LevelBuf& b = g->lb[l];
+        if (b.cap < total[l]) {
+            cudaFree(b.xi);
+            cudaFree(b.K);
+            cudaFree(b.q);
+            b.xi = b.K = b.q = nullptr;
+            b.cap = 0;
+            if (cudaMalloc((void**)&b.xi, total[l] * M * sizeof(double)) != cudaSuccess ||
+                cudaMalloc((void**)&b.K, total[l] * (size_t)N * N * sizeof(double)) != cudaSuccess ||
+                cudaMalloc((void**)&b.q, 2 * total[l] * sizeof(double)) != cudaSuccess) {
+                set_error(ctx, "mlmc_estimate: allocation of a batched round failed");
+                return FM_ENOMEM;
+            }
+            b.cap = total[l];
+        }
+        uint64_t o = 0;
+        for (const Request& r : g->pending) {
+            if (r.e - g->off != l) continue;
+            for (uint64_t d = 0; d < r.n;) {
+                const uint32_t cnt = (uint32_t)std::min<uint64_t>(r.n - d, (uint64_t)1 << 30);
+                double* xi = b.xi + (o + d) * M;
+                if (r.shift < 0) FM_TRY(mc_points(ctx, (uint32_t)l, r.first + d, cnt, (uint32_t)M, xi, nullptr));
+                else FM_TRY(sobol_points(ctx, (uint32_t)l, (uint32_t)M, r.first + d, cnt, (uint32_t)r.shift, 1,
+                                         nullptr, xi, nullptr));
+                d += cnt;
+            }
+            o += r.n;
+        }
+        for (uint64_t d = 0; d < total[l];) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(total[l] - d, (uint64_t)1 << 20);
+            FM_TRY(kl_field_batch(ctx, l, cnt, b.xi + d * M, b.K + d * (size_t)N * N, nullptr));
+            d += cnt;
+        }
+        groups.push_back(fm_batch_group{N, (uint32_t)total[l], b.K, b.q, b.q + total[l], nullptr});
+        group_level.push_back(l);
+    }
+    FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
+    // level-0 surrogate values, then the sums of every request
+    for (int l = 0; l < L; ++l) {
+        if (!total[l]) continue;
+        LevelBuf& b = g->lb[l];
+        uint64_t o = 0;
+        for (const Request& r : g->pending) {
+            if (r.e - g->off != l) continue;
+            double* qf = b.q + o;
+            double* qc = b.q + total[l] + o;
+            const bool with_s = ctx->surrogate_on && l == 0;
+            if (with_s) {
+                if (r.shift < 0) FM_TRY(surrogate_eval_mc_impl(ctx, 0, r.first, (uint32_t)r.n, qc, nullptr));
+                else FM_TRY(surrogate_eval_impl(ctx, (uint32_t)r.n, b.xi + o * M, qc, nullptr));
+            }
+            fm_level_sums* cell = ctx->d_sums + (size_t)r.e * g->R + (r.shift < 0 ? 0 : r.shift);
+            FM_TRY(level_sums_add(ctx, (uint32_t)r.n, qf, qc, (l > 0 || with_s) ? 1 : 0, cell, nullptr));
+            o += r.n;
+        }
+    }
+    cudaEventRecord(g->b1, nullptr);
+    g->pending.clear();
+    return FM_OK;
+}
+
 fm_status gpu_read(void* user, fm_level_sums* local) {
     GpuSampler* g = static_cast<GpuSampler*>(user);
+    FM_TRY(flush_batched(g));
     FM_TRY(fm_sync(g->ctx));
+    if (g->batched && g->b0) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g->b0, g->b1) == cudaSuccess) g->round_sec += ms * 1e-3;
+    }
     g->collect();
     FM_CUDA_TRY(g->ctx, cudaMemcpy(local, g->ctx->d_sums, g->cells * sizeof(fm_level_sums), cudaMemcpyDeviceToHost));
     return FM_OK;
@@ -282,6 +398,7 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
     g.off = off;
     g.R = R;
     g.cells = cells;
+    g.batched = opts->batched != 0;
     fm_core_opts co{};
     co.n_ext = L + 1;
     co.cost = C;
@@ -307,6 +424,7 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
         out->N[l] = cr.N[l + off];
         out->level_seconds[l] = g.lsec[l + off];
     }
+    out->batched_seconds = g.round_sec;
     if (off) {
         out->mean_s = cr.mean[0];
         out->var_s = cr.var[0];

@@ -128,3 +128,58 @@ def test_tile_smoother_is_deterministic_across_runs(ctx):
     a = ctx.fmg_solve_batch(K, **kw)
     b = ctx.fmg_solve_batch(K, **kw)
     assert _same(a[0], b[0]) and _same(a[1], b[1])
+
+
+@pytest.mark.parametrize("qmc", [False, True])
+def test_batched_estimate_matches_per_level_estimate(qmc):
+    """Each round's solves of all levels as one uneven batch: the same
+    samples, the same per-sample results, so the same schedule and estimate."""
+    import paper_1910_04727_gb300 as fm
+    basis = okl.KLBasis(128, 32, 1.0, 0.3, q=32)
+    c = fm.Context(4, 16, 32, sigma2=1.0, lam=0.3, seed=41, precision=1, converged=1, tol=1e-10,
+                   qtol=1e-9, max_cycles=200, n_shifts=8)
+    c.kl_basis_set(basis.B_ref)
+    kw = dict(qmc=qmc, n_pilot=64 if not qmc else 16)
+    a = c.mlmc_estimate(3e-3, **kw)
+    b = c.mlmc_estimate(3e-3, batched=True, **kw)
+    assert list(a["N"]) == list(b["N"]) and a["rounds"] == b["rounds"]
+    assert abs(a["estimate"] - b["estimate"]) <= 1e-14 * abs(a["estimate"])
+    assert b["batched_seconds"] > 0
+
+
+def test_batched_estimate_with_surrogate_level():
+    import paper_1910_04727_gb300 as fm
+    basis = okl.KLBasis(64, 128, 1.0, 0.3, q=32)
+    c = fm.Context(3, 16, 128, sigma2=1.0, lam=0.3, seed=43, precision=1, converged=1, tol=1e-10,
+                   qtol=1e-9, max_cycles=200)
+    c.kl_basis_set(basis.B_ref)
+    c.surrogate_train(n_train=4096, epochs=20, lr=3e-3, seed=3, batch=512)
+    kw = dict(n_pilot=128, surrogate=True, surrogate_cost=0.02)
+    a = c.mlmc_estimate(4e-3, **kw)
+    b = c.mlmc_estimate(4e-3, batched=True, **kw)
+    assert list(a["N"]) == list(b["N"]) and a["N_s"] == b["N_s"]
+    assert abs(a["estimate"] - b["estimate"]) <= 1e-14 * abs(a["estimate"])
+
+
+def test_full_size_uneven_batch_sampled_against_oracle():
+    """The benchmark's uneven batch at its grids (64 x 64 .. 1024 x 1024) and
+    solver settings (FP32 smoothing, FP64 refinement to 1e-12 or an outflux
+    change of 1e-10), fewer samples: per-group results bit for bit, and the
+    first sample of every grid against the converged FP64 oracle (the mixed
+    bar, 1e-8)."""
+    import paper_1910_04727_gb300 as fm
+    c = fm.Context(5, 64, 16, sigma2=1.0, lam=0.3, seed=47, precision=1, converged=1, tol=1e-12, qtol=1e-10,
+                   max_cycles=200)
+    counts = [5, 4, 3, 2, 1]
+    Kn = [W.smooth_lognormal_field(64 << l, S=cnt, tag=1000 + l) for l, cnt in enumerate(counts)]
+    Ks = [torch.tensor(K, device="cuda") for K in Kn]
+    outs = c.solve_uneven(Ks)
+    for K, (qf, qc, _) in zip(Ks, outs):
+        rf, rc, _ = c.fmg_solve_batch(K)
+        assert _same(qf, rf) and _same(qc, rc)
+    errs = []
+    for K, (qf, qc, _) in zip(Kn, outs):
+        of, oc, _, _ = OL.fmg_solve_batch(K[:1], OL.params(converged=True, tol=1e-14, max_cycles=400))
+        errs.append((K.shape[-1], _rel(qf.cpu().numpy()[:1], of), _rel(qc.cpu().numpy()[:1], oc)))
+    print("outflux error against the converged oracle:", errs)
+    assert all(ef < 1e-8 and ec < 1e-8 for _, ef, ec in errs)
