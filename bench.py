@@ -352,6 +352,8 @@ def run_native(args, wl, eps):
     ctx = make_ctx(fm, wl, rank, args.form)
     theta, captured = ctx.kl_basis_build(q=wl.kl_q)
     B_dev = ctx.kl_basis_get()
+    # smoother launch shapes per grid, timed once before any measurement
+    tune = ctx.autotune(n_min=8, n_max=wl.levels[-1])
 
     clocks = ClockSampler(local)
     times, results, prof, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
@@ -371,6 +373,7 @@ def run_native(args, wl, eps):
             continue
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
+        c2.autotune(n_min=8, n_max=wl.levels[-1])
         ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
                                       form=form)
         others[form] = {"value": float(np.mean(ts)), "unit": "s",
@@ -388,6 +391,7 @@ def run_native(args, wl, eps):
     for form in ([] if (args.qmc or args.no_qmc_leg) else [args.form, "fp64_converged"]):
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
+        c2.autotune(n_min=8, n_max=wl.levels[-1])
         ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
                                       form=form, qmc=True)
         qmc_forms[form] = {"value": float(np.mean(ts)), "unit": "s",
@@ -404,6 +408,7 @@ def run_native(args, wl, eps):
     B_host = torch.empty((n_ref * n_ref, wl.M), dtype=torch.float64).pin_memory()
     ctx.kl_basis_get(B_host)
     ctx2 = make_ctx(fm, wl, rank, args.form)
+    ctx2.autotune(n_min=8, n_max=wl.levels[-1])
     e2e_times, rounds = [], []
     sur = FORMS[args.form]["surrogate"]
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
@@ -471,6 +476,7 @@ def run_native(args, wl, eps):
         "uneven_batch": uneven,
         "roofline": roof,
         "kernel_families": families,
+        "smoother_shapes": [{k: e[k] for k in ("n", "tile", "threads", "ms_best", "ms_default")} for e in tune],
         "gpu_launches": total_launches,
         "e2e": {"value": float(np.mean(e2e_times)) if e2e_times else None, "unit": "s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -265,14 +265,16 @@ fm_status fmg_uneven_stats(const fm_ctx* ctx, int64_t* instantiations, int64_t* 
 typedef struct {
     int32_t n;            /* grid n x n */
     int32_t tile;         /* tile interior staged in shared memory (0: one launch per colour and sweep) */
-    int32_t threads;      /* threads per CTA of the tile launch */
+    int32_t threads;      /* 0: register-blocked tile kernel (only p in shared memory); else threads
+                             per CTA of the tile kernel that stages every operand in shared memory */
     double ms_best;       /* one smoothing call (nsweeps sweeps) with the chosen shape, milliseconds */
     double ms_default;    /* the same with the built-in default shape */
     int64_t samples;      /* samples of the timing batch (about 64 Mi cells) */
 } fm_tune_entry;
 
 /* Times the red-black smoother's launch shapes (one launch per colour, or
- * tiles of 8, 16, 32, 64 cells staged in shared memory with a 2 nsweeps halo,
+ * tiles of 8, 16, 32, 64 cells with a 2 nsweeps halo, either register-blocked
+ * with only the iterate in shared memory or with every operand staged there
  * at 128 or 256 threads) for the grids n_min, 2 n_min, ..., <= n_max on a
  * synthetic batch of about 64 Mi cells per grid, and keeps the fastest in
  * ctx for that precision (FM_PREC_FP64: the FP64 grids; FM_PREC_MIXED: the

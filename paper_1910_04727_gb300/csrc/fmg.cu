@@ -121,7 +121,7 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b
     if (i < n - 1) acc += Te[c] * p[c + 1];
     if (j > 0) acc += Tn[c - n] * p[c - n];
     if (j < n - 1) acc += Tn[c] * p[c + n];
-    p[c] = acc / D[c];
+    p[c] = acc * (T(1) / D[c]);
 }
 
 // nsweeps red-black sweeps (colour 0 then 1) on tiles of TI x TI cells of
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
             if (i < n - 1) acc += se[e] * sp[e + 1];
             if (j > 0) acc += sn[e - RW] * sp[e - RW];
             if (j < n - 1) acc += sn[e] * sp[e + RW];
-            sp[e] = acc / sd[e];
+            sp[e] = acc * (T(1) / sd[e]);
         }
         __syncthreads();
     }
@@ -191,6 +191,105 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
     for (int e = threadIdx.x; e < IW * IH; e += blockDim.x) {
         const int r = e / IW, q = e % IW;
         p_out[base + (size_t)(y0 + r) * n + x0 + q] = sp[(y0 - ya + r) * RW + (x0 - xa + q)];
+    }
+}
+
+// The tile smoother with every operand but the iterate in registers.  Thread
+// (c, g) owns the column pair 2c, 2c+1 and rows g RPT .. g RPT + RPT - 1 of an
+// R x R region (tile interior plus halo, clipped at the domain edge) for all
+// sweeps: in every row one of its two cells has the colour being updated, so
+// every lane updates RPT cells per half-sweep with no divergence.  b, 1/D and
+// the four faces of its cells are loaded once (a face that does not exist is
+// zero, and the zero-padded shared array keeps every neighbour read in
+// bounds); only p goes through shared memory, and neighbours inside the
+// thread's own cells come from registers.  Same halo argument, same update
+// order and reciprocal as the colour kernel: bit-identical sweeps (a missing
+// face adds an exact zero).
+template <typename T, int R, int RPT>
+__global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, size_t S, int TI, int hh, int nsweeps,
+                                                                      const T* __restrict__ b,
+                                                                      const T* __restrict__ Te,
+                                                                      const T* __restrict__ Tn,
+                                                                      const T* __restrict__ D,
+                                                                      const T* __restrict__ p_in, T* __restrict__ p_out,
+                                                                      const int32_t* __restrict__ active) {
+    static_assert(R % 2 == 0 && R % RPT == 0, "region must split into column pairs and row strips");
+    constexpr int C = R / 2, P = R + 2;   // column pairs; padded row pitch
+    __shared__ T sp[P * P];
+    const int tiles = (n + TI - 1) / TI;
+    const size_t s = blockIdx.x / ((unsigned)tiles * tiles);
+    if (s >= S || inactive(active, s)) return;
+    const int tid = (int)(blockIdx.x % ((unsigned)tiles * tiles));
+    const int ti = tid % tiles, tj = tid / tiles;
+    const int xa = max(ti * TI - hh, 0), ya = max(tj * TI - hh, 0);
+    const int RW = min(ti * TI + TI + hh, n) - xa, RH = min(tj * TI + TI + hh, n) - ya;
+    const int c = threadIdx.x % C, y0 = (threadIdx.x / C) * RPT;
+    const size_t base = s * (size_t)n * n;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) sp[e] = T(0);
+    __syncthreads();
+    T rb[RPT][2], rr[RPT][2], re[RPT][2], rw[RPT][2], rn[RPT][2], rs[RPT][2], rp[RPT][2];
+    bool up[RPT][2];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int x = 2 * c + j, y = y0 + k, gx = xa + x, gy = ya + y;
+            rb[k][j] = rr[k][j] = re[k][j] = rw[k][j] = rn[k][j] = rs[k][j] = rp[k][j] = T(0);
+            up[k][j] = false;
+            if (x < RW && y < RH) {
+                const size_t g = base + (size_t)gy * n + gx;
+                rp[k][j] = p_in[g];
+                rb[k][j] = b[g];
+                rr[k][j] = T(1) / D[g];
+                if (gx < n - 1) re[k][j] = Te[g];
+                if (gy < n - 1) rn[k][j] = Tn[g];
+                if (gx > 0) rw[k][j] = Te[g - 1];
+                if (gy > 0) rs[k][j] = Tn[g - n];
+                // a cell whose in-domain neighbour lies outside the region is not updated
+                up[k][j] = !((gx > 0 && x == 0) || (gx < n - 1 && x == RW - 1) || (gy > 0 && y == 0) ||
+                             (gy < n - 1 && y == RH - 1));
+                sp[(y + 1) * P + x + 1] = rp[k][j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int hs = 0; hs < 2 * nsweeps; ++hs) {
+        const int color = hs & 1;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int y = y0 + k;
+            // the cell of this colour in row y: column 2c + j (selects, so the
+            // register arrays are never indexed at run time)
+            const bool j = ((color + xa + ya + y) & 1) != 0;
+            const int x = 2 * c + (j ? 1 : 0);
+            const T* row = sp + (y + 1) * P + x + 1;
+            const T p0 = rp[k][0], p1 = rp[k][1];
+            const T pw = j ? p0 : row[-1];
+            const T pe = j ? row[1] : p1;
+            const T ps = k > 0 ? (j ? rp[k - 1][1] : rp[k - 1][0]) : row[-P];
+            const T pn = k < RPT - 1 ? (j ? rp[k + 1][1] : rp[k + 1][0]) : row[P];
+            T acc = j ? rb[k][1] : rb[k][0];
+            acc += (j ? rw[k][1] : rw[k][0]) * pw;
+            acc += (j ? re[k][1] : re[k][0]) * pe;
+            acc += (j ? rs[k][1] : rs[k][0]) * ps;
+            acc += (j ? rn[k][1] : rn[k][0]) * pn;
+            const bool u = j ? up[k][1] : up[k][0];
+            const T v = u ? acc * (j ? rr[k][1] : rr[k][0]) : (j ? p1 : p0);
+            if (j) rp[k][1] = v;
+            else rp[k][0] = v;
+            if (x < RW && y < RH) sp[(y + 1) * P + x + 1] = v;
+        }
+        __syncthreads();
+    }
+    const int x0 = ti * TI, y0i = tj * TI;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int x = 2 * c + j, y = y0 + k, gx = xa + x, gy = ya + y;
+            if (x < RW && y < RH && gx >= x0 && gx < min(x0 + TI, n) && gy >= y0i && gy < min(y0i + TI, n))
+                p_out[base + (size_t)gy * n + gx] = rp[k][j];
+        }
     }
 }
 
@@ -593,8 +692,38 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
         const int TI = std::min(tile, n);
         const int hh = TI >= n ? 0 : 2 * nsweeps;
         const int tiles = (n + TI - 1) / TI;
-        FM_TIMED(ctx, kFamSmoother, st, 6.0 * sizeof(T) * cells, 10.0 * nsweeps * cells,
-                 k_rbgs_tile<T><<<(unsigned)(S * tiles * tiles), threads, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
+        const unsigned grid = (unsigned)(S * tiles * tiles);
+        const double bytes = 6.0 * sizeof(T) * cells, flops = 10.0 * nsweeps * cells;
+        // register-blocked regions (threads == 0): whole grids of 8, 16, 32
+        // (and, FP32, 64) cells, or 32 (and, FP32, 64) interiors with a halo of
+        // up to 4 (nsweeps <= 2); FP64 copies of the large regions would spill
+        constexpr bool f32 = sizeof(T) == 4;
+        if (threads == 0 && hh == 0 && (n == 8 || n == 16 || n == 32 || (f32 && n == 64))) {
+            if (n == 8)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 8, 1><<<grid, 4 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            else if (n == 16)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 16, 2><<<grid, 8 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            else if (n == 32)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 32, 4><<<grid, 16 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            else if constexpr (f32)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 64, 8><<<grid, 32 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            return p_out;
+        }
+        if (threads == 0 && hh > 0 && hh <= 4 && (TI == 32 || (f32 && TI == 64))) {
+            if (TI == 32)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 40, 5><<<grid, 20 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            else if constexpr (f32)
+                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 72, 9><<<grid, 36 * 8, 0, st>>>(
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+            return p_out;
+        }
+        FM_TIMED(ctx, kFamSmoother, st, bytes, flops,
+                 k_rbgs_tile<T><<<grid, threads > 0 ? threads : 256, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
                                   st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
         return p_out;
     }
@@ -609,16 +738,26 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
 
 static int tune_slot(int n) { return std::min(15, 31 - __builtin_clz((unsigned)n)); }
 
-// Smoother launch shape of grid n: FP32 tiles of 32 x 32 by default; FP64,
-// bound by its divide (which the halo's redundant updates add to), one
-// launch per colour; an fm_autotune entry for this grid and precision
-// replaces the default.  Tiles need both smoothing phases of the V-cycle
-// (so the iterate goes p -> p2 -> p) and their staged region in shared memory.
+// Smoother launch shape of grid n.  Untuned defaults (measured on GB300 for
+// two sweeps): register-blocked regions for small grids (FP32 up to 16, FP64
+// up to 32), FP32 tiles of 32 x 32 staged in shared memory at 256 threads up
+// to 128, and above that one bandwidth-bound launch per colour (FP64 too,
+// whose tiles are bound by the FP64 divide); an fm_autotune entry for this
+// grid and precision replaces the default.  Tiles need both smoothing phases
+// of the V-cycle (so the iterate goes p -> p2 -> p) and their staged region
+// in shared memory.
 template <typename T>
 static void smooth_shape(const fm_ctx* ctx, int n, const fm_solve_params& prm, int* tile, int* threads) {
     const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
-    *tile = sizeof(T) == 4 ? 32 : 0;
-    *threads = 256;
+    const bool f32 = sizeof(T) == 4;
+    *tile = 0;
+    *threads = 0;
+    if (n <= (f32 ? 16 : 32)) {
+        *tile = 32;   // one register-blocked region per sample
+    } else if (f32 && n <= 128) {
+        *tile = 32;
+        *threads = 256;
+    }
     if (ctx->tune.n[pi][slot] == n) {
         *tile = ctx->tune.tile[pi][slot];
         *threads = ctx->tune.threads[pi][slot];
@@ -1051,16 +1190,21 @@ static fm_status autotune_grid(fm_ctx* ctx, int n, int nsweeps, fm_tune_entry* e
         cudaEventElapsedTime(&ms, e0, e1);
         return ms / 4.0;
     };
-    const int def_tile = sizeof(T) == 4 ? 32 : 0;
+    fm_solve_params dp{};
+    dp.nu1 = dp.nu2 = nsweeps;
+    int def_tile = 0, def_threads = 0;
+    const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
+    ctx->tune.n[pi][slot] = 0;   // the untuned default
+    smooth_shape<T>(ctx, n, dp, &def_tile, &def_threads);
     double best = 1e30;
-    int bt = def_tile, bth = 256;
-    e->ms_default = time_shape(def_tile, 256);
+    int bt = def_tile, bth = def_threads;
+    e->ms_default = time_shape(def_tile, def_threads);
     const int tiles[] = {0, 8, 16, 32, 64};
-    const int thr[] = {128, 256};
+    const int thr[] = {0, 128, 256};   // 0: register-blocked regions (fixed thread count)
     for (int tile : tiles) {
         if (tile > 0 && tile > n && tile != 8) continue;   // one whole-grid candidate is enough
         for (int th : thr) {
-            if (tile == 0 && th != 256) continue;             // colour launches have a fixed shape
+            if (tile == 0 && th != 0) continue;               // colour launches have a fixed shape
             const double ms = time_shape(tile, th);
             if (ms < best) {
                 best = ms;
@@ -1072,14 +1216,13 @@ static fm_status autotune_grid(fm_ctx* ctx, int n, int nsweeps, fm_tune_entry* e
     if (e->ms_default <= best) {   // the default, timed first, stays unless beaten
         best = e->ms_default;
         bt = def_tile;
-        bth = 256;
+        bth = def_threads;
     }
     ctx->prof.active = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);
     FM_CUDA_TRY(ctx, cudaGetLastError());
-    const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
     ctx->tune.n[pi][slot] = n;
     ctx->tune.tile[pi][slot] = bt;
     ctx->tune.threads[pi][slot] = bth;
