@@ -196,8 +196,8 @@ FORMS = {
     "fp64_fmg2": dict(precision=0, converged=False, surrogate=False),
 }
 
-# surrogate training: 20480 (xi, Q_0) pairs, batch 1024, 40 epochs, Adam 6e-3 cosine
-SURROGATE_TRAIN = dict(n_train=20480, epochs=40, lr=6e-3, seed=7, batch=1024)
+# surrogate training: 20480 (xi, Q_0) pairs, batch 1024, 24 epochs, Adam 4e-3 cosine
+SURROGATE_TRAIN = dict(n_train=20480, epochs=24, lr=4e-3, seed=7, batch=1024)
 
 
 def surrogate_cost(torch, ctx):
@@ -225,6 +225,9 @@ def make_ctx(fm, wl, rank, form):
                       n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank, precision=f["precision"],
                       converged=f["converged"], tol=SOLVE_TOL, qtol=SOLVE_QTOL, max_cycles=200)
 
+
+# DRAM read + write of one FP32 colour launch per cell, measured by ncu
+COLOUR_DRAM_BYTES_PER_CELL_F32 = (1.341171e9 + 0.251231e9) / (64 << 20)
 
 # randomized QMC (Algorithm 2): 32 points per shift and level to start, 16 digital shifts
 QMC_PILOT = 32
@@ -436,6 +439,12 @@ def run_native(args, wl, eps):
     ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "traffic": None, "peak_source": src}
+    if fam == "rbgs_smoother" and FORMS[args.form]["precision"] == 1:
+        # DRAM bytes of one FP32 colour launch per cell (ncu, 64 Mi cells:
+        # profiles/rbgs_smoother_shapes_synthetic_256.md) over its 12
+        # algorithmic bytes, scaled to the average timed launch
+        roof["traffic"] = st["bytes"] / st["launches"] * COLOUR_DRAM_BYTES_PER_CELL_F32 / 12.0
+        roof["traffic_source"] = "ncu dram bytes per cell (64 Mi-cell capture) x cells per launch"
     if fam in ("kl_gemm_exp", "fmg_resident", "mlp_gemm"):
         roof["bound"] = "alu"
         roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is ALU/latency bound"

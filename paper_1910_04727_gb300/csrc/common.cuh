@@ -89,7 +89,7 @@ void set_error(const fm_ctx* ctx, const std::string& msg);
 enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
-    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamilyCount
+    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamSmootherTile, kFamilyCount
 };
 
 struct ProfRecord {

@@ -700,29 +700,29 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
         constexpr bool f32 = sizeof(T) == 4;
         if (threads == 0 && hh == 0 && (n == 8 || n == 16 || n == 32 || (f32 && n == 64))) {
             if (n == 8)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 8, 1><<<grid, 4 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 8, 1><<<grid, 4 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             else if (n == 16)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 16, 2><<<grid, 8 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 16, 2><<<grid, 8 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             else if (n == 32)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 32, 4><<<grid, 16 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 32, 4><<<grid, 16 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             else if constexpr (f32)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 64, 8><<<grid, 32 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 64, 8><<<grid, 32 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             return p_out;
         }
         if (threads == 0 && hh > 0 && hh <= 4 && (TI == 32 || (f32 && TI == 64))) {
             if (TI == 32)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 40, 5><<<grid, 20 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 40, 5><<<grid, 20 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             else if constexpr (f32)
-                FM_TIMED(ctx, kFamSmoother, st, bytes, flops, k_rbgs_tile_reg<T, 72, 9><<<grid, 36 * 8, 0, st>>>(
+                FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 72, 9><<<grid, 36 * 8, 0, st>>>(
                     n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
             return p_out;
         }
-        FM_TIMED(ctx, kFamSmoother, st, bytes, flops,
+        FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops,
                  k_rbgs_tile<T><<<grid, threads > 0 ? threads : 256, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
                                   st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
         return p_out;
