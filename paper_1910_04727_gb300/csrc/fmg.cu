@@ -337,6 +337,18 @@ __device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U g
     return uc[(size_t)J * nc + I];
 }
 
+// (P u_c) at fine cell (i, j): bilinear cell-centred (9, 3, 3, 1) / 16 with
+// the ghosts above.  One expression for every kernel that prolongs.
+template <typename U>
+__device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, U gW, U gE) {
+    const int I = i >> 1, J = j >> 1;
+    const int Ix = (i & 1) ? I + 1 : I - 1;
+    const int Jy = (j & 1) ? J + 1 : J - 1;
+    return (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
+            U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
+           U(16);
+}
+
 // p_f += P e_c (add = 1, boundary values 0) or p_f = P u_c (add = 0, FMG start).
 template <typename U>
 __global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE, int add, U* __restrict__ pf,
@@ -349,14 +361,39 @@ __global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE
     if (inactive(active, s)) return;
     const int c = (int)(t % cells);
     const int i = c % nf, j = c / nf;
-    const U* u = uc + s * (size_t)nc * nc;
-    const int I = i >> 1, J = j >> 1;
-    const int Ix = (i & 1) ? I + 1 : I - 1;
-    const int Jy = (j & 1) ? J + 1 : J - 1;
-    const U v = (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
-                 U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
-                U(16);
+    const U v = prolong_at(nc, uc + s * (size_t)nc * nc, i, j, gW, gE);
     pf[t] = add ? pf[t] + v : v;
+}
+
+// The first colour (0) of post-smoothing fused with the coarse-grid
+// correction p += P e: a red cell's update reads only its black neighbours,
+// so they are read as p + (P e) on the fly and the red cell's own correction
+// is never needed (its value is replaced); the next colour launch then
+// replaces every black cell from the updated red ones.  Each corrected value
+// is k_prolong's and each update k_rbgs_color's, so the sweep is
+// bit-identical to a prolongation pass followed by the colour launches.
+template <typename T>
+__global__ void k_rbgs_color0_prolong(int n, size_t S, const T* __restrict__ b, const T* __restrict__ Te,
+                                      const T* __restrict__ Tn, const T* __restrict__ D, T* __restrict__ p,
+                                      const T* __restrict__ ec, const int32_t* __restrict__ active) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t half = (size_t)n * n / 2;
+    if (t >= S * half) return;
+    const size_t s = t / half;
+    if (inactive(active, s)) return;
+    const int h = (int)(t % half);
+    const int j = h / (n / 2);
+    const int i = 2 * (h % (n / 2)) + (j & 1);
+    const size_t base = s * (size_t)n * n;
+    const size_t c = base + (size_t)j * n + i;
+    const int nc = n / 2;
+    const T* e = ec + s * (size_t)nc * nc;
+    T acc = b[c];
+    if (i > 0) acc += Te[c - 1] * (p[c - 1] + prolong_at(nc, e, i - 1, j, T(0), T(0)));
+    if (i < n - 1) acc += Te[c] * (p[c + 1] + prolong_at(nc, e, i + 1, j, T(0), T(0)));
+    if (j > 0) acc += Tn[c - n] * (p[c - n] + prolong_at(nc, e, i, j - 1, T(0), T(0)));
+    if (j < n - 1) acc += Tn[c] * (p[c + n] + prolong_at(nc, e, i, j + 1, T(0), T(0)));
+    p[c] = acc * (T(1) / D[c]);
 }
 
 // Inverse of the dense operator of the coarsest grid (m = n0^2 <= 16
@@ -455,25 +492,30 @@ __global__ void k_fill(size_t count, double v, double* __restrict__ x) {
 }
 
 // ------------------------------------------------------------------ refinement kernels
-// Per-sample convergence test of the stage problem, one CTA per sample:
-// active[s] = ||b - A p||_2 > tol ||b||_2 (FP64 sums), counted in *left.
-// Mixed form (p64 != null): the residual is formed in FP64 from the FP64
-// grid and written, rounded, into the FP32 rhs bT, with the FP32 correction
-// pT zeroed; FP64 form: the residual of the T grid itself.
+// Per-sample convergence test of the stage problem, split over `chunks`
+// CTAs per sample (grid S * chunks, chunk index fastest): each CTA forms the
+// residual of its slice of cells and writes its partial sums of ||r||^2,
+// ||b||^2 and the outflux to partial[(s * chunks + ch) * 3 + 0..2]; the
+// mixed form (p64 != null) forms the residual in FP64 from the FP64 grid and
+// writes it, rounded, into the FP32 rhs bT with the FP32 correction pT
+// zeroed.  k_stage_decide then folds the partials in chunk order.  b / bT
+// and p / pT are the same arrays, hence no __restrict__ on them.
 template <typename T>
-__global__ void k_stage_check(int n, size_t S, const double* __restrict__ K, double pW, double pE,
-                              const T* __restrict__ b, const T* __restrict__ Te, const T* __restrict__ Tn,
-                              const T* __restrict__ D, const T* __restrict__ p, const double* __restrict__ p64,
-                              const double* __restrict__ Te64, const double* __restrict__ Tn64,
-                              const double* __restrict__ D64, T* __restrict__ bT, T* __restrict__ pT,
-                              double tol, double qtol, double* __restrict__ qprev,
-                              int32_t* __restrict__ active, int32_t* __restrict__ left) {
+__global__ void k_stage_partials(int n, size_t S, int chunks, const double* __restrict__ K, double pW, double pE,
+                                 const T* b, const T* __restrict__ Te, const T* __restrict__ Tn,
+                                 const T* __restrict__ D, const T* p, const double* __restrict__ p64,
+                                 const double* __restrict__ Te64, const double* __restrict__ Tn64,
+                                 const double* __restrict__ D64, T* bT, T* pT, const int32_t* __restrict__ active,
+                                 double* __restrict__ partial) {
     __shared__ double red[3][32];
-    const size_t s = blockIdx.x;
+    const size_t s = blockIdx.x / chunks;
+    const int ch = (int)(blockIdx.x % chunks);
     if (s >= S || inactive(active, s)) return;
     const size_t base = s * (size_t)n * n;
+    const int cells = n * n, per = (cells + chunks - 1) / chunks;
+    const int c0 = ch * per, c1 = min(cells, c0 + per);
     double rr = 0.0, bb = 0.0, qq = 0.0;
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int i = c % n, j = c / n;
         const size_t g = base + c;
         if (i == n - 1) qq += 2.0 * K[g] * ((p64 ? p64[g] : (double)p[g]) - pE);
@@ -515,14 +557,33 @@ __global__ void k_stage_check(int n, size_t S, const double* __restrict__ K, dou
             b2 += red[1][w];
             q += red[2][w];
         }
-        // residual test, or an iteration that moved the outflux by <= qtol |Q|
-        const bool done = a <= tol * tol * b2 || (qtol > 0 && fabs(q - qprev[s]) <= qtol * fabs(q));
-        qprev[s] = q;
-        active[s] = done ? 0 : 1;
-        if (!done) atomicAdd(left, 1);
+        double* out = partial + ((size_t)s * chunks + ch) * 3;
+        out[0] = a;
+        out[1] = b2;
+        out[2] = q;
     }
 }
 
+// The test itself, one thread per sample: active[s] = ||b - A p|| > tol ||b||
+// and the last pass moved the outflux by more than qtol |Q|; counted in *left.
+__global__ void k_stage_decide(size_t S, int chunks, const double* __restrict__ partial, double tol, double qtol,
+                               double* __restrict__ qprev, int32_t* __restrict__ active, int32_t* __restrict__ left) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || inactive(active, s)) return;
+    double a = 0.0, b2 = 0.0, q = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) {
+        const double* v = partial + ((size_t)s * chunks + ch) * 3;
+        a += v[0];
+        b2 += v[1];
+        q += v[2];
+    }
+    const bool done = a <= tol * tol * b2 || (qtol > 0 && fabs(q - qprev[s]) <= qtol * fabs(q));
+    qprev[s] = q;
+    active[s] = done ? 0 : 1;
+    if (!done) atomicAdd(left, 1);
+}
+
+// Mixed form: the FP64 refinement update p64 += e (the FP32 correction).
 template <typename T>
 __global__ void k_ir_update(size_t cells, size_t S, const T* __restrict__ e, double* __restrict__ p64,
                             const int32_t* __restrict__ active) {
@@ -568,7 +629,11 @@ struct Hierarchy {
     int32_t* left;     // count of samples still iterating
     int32_t* iter;     // residual tests done in the current refined stage (graph loops)
     double* qprev;     // outflux of the previous iteration per sample
+    double* partial;   // per-(sample, chunk) partial sums of the residual tests
 };
+
+// CTAs per sample of a residual test on grid n (about 8192 cells each).
+inline int check_chunks(int n) { return std::max(1, std::min(128, n * n / 8192)); }
 
 static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool mixed, bool converged) {
     size_t total = 0;
@@ -581,7 +646,7 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
     total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
-    if (converged) total += 4 * 3 + 8 + 4 * 256;
+    if (converged) total += 4 * 3 + 8 + (size_t)check_chunks(n_fine) * 24 + 5 * 256;
     return total * S + 4096;
 }
 
@@ -656,6 +721,7 @@ static fm_status carve(fm_ctx* ctx, Arena& ar, Hierarchy<T>& H, int n_fine, int 
     H.left = converged ? (int32_t*)take(4) : nullptr;
     H.iter = converged ? (int32_t*)take(4) : nullptr;
     H.qprev = converged ? (double*)take(S * 8) : nullptr;
+    H.partial = converged ? (double*)take(S * (size_t)check_chunks(n_fine) * 24) : nullptr;
     return FM_OK;
 }
 
@@ -798,6 +864,16 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
              k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
                  c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
     vcycle(H, k - 1, top, prm, active, st);
+    if (tile == 0 && prm.nu2 >= 1) {
+        // colour launches: the correction rides in the first post-smoothing colour
+        FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells + ts * S * c.n * c.n, 5.0 * cells,
+                 k_rbgs_color0_prolong<T><<<blocks_for(cells / 2), kBlock, 0, st>>>(n, S, g.b, Te, Tn, D, cur, c.p,
+                                                                                    active));
+        FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells, 5.0 * cells,
+                 k_rbgs_color<T><<<blocks_for(cells / 2), kBlock, 0, st>>>(n, S, 1, g.b, Te, Tn, D, cur, active));
+        smooth_with<T>(ctx, 0, 0, n, S, prm.nu2 - 1, g.b, Te, Tn, D, cur, g.p, active, st);
+        return;
+    }
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
              k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, cur, active));
     smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st);
@@ -808,6 +884,21 @@ static void outflux(fm_ctx* ctx, int n, size_t S, const double* K, const P* p, d
                     cudaStream_t st) {
     FM_TIMED(ctx, kFamOutflux, st, 16.0 * S * n, 3.0 * S * n,
              k_outflux<P><<<blocks_for(S * 32), kBlock, 0, st>>>(n, S, K, p, pE, q));
+}
+
+// One residual test of the refined stage on grid k (partials, then the decision).
+template <typename T>
+static void stage_test(const Hierarchy<T>& H, int k, const fm_solve_params& prm, bool mixed, cudaStream_t st) {
+    fm_ctx* ctx = H.ctx;
+    const GridBufs<T>& g = H.g[k];
+    const size_t S = H.S, cells = (size_t)g.n * g.n;
+    const int chunks = check_chunks(g.n);
+    FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * S * cells, 12.0 * S * cells,
+             k_stage_partials<T><<<(unsigned)(S * chunks), kBlock, 0, st>>>(
+                 g.n, S, chunks, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64, g.b,
+                 g.p, H.active, H.partial);
+             k_stage_decide<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, prm.tol, prm.qtol, H.qprev,
+                                                              H.active, H.left));
 }
 
 // Loop control of a refined stage inside a CUDA graph: after residual test
@@ -840,9 +931,7 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     FM_CUDA_TRY(ctx, cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
     auto test = [&](cudaStream_t s) {
         cudaMemsetAsync(H.left, 0, sizeof(int32_t), s);
-        k_stage_check<T><<<(unsigned)S, kBlock, 0, s>>>(g.n, S, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64,
-                                                        g.Te64, g.Tn64, g.D64, g.b, g.p, prm.tol, prm.qtol, H.qprev,
-                                                        H.active, H.left);
+        stage_test(H, k, prm, mixed, s);
         k_refine_cond<<<1, 1, 0, s>>>(H.left, H.iter, prm.max_cycles, h);
     };
     FM_CUDA_TRY(ctx, cudaMemsetAsync(H.active, 0xff, S * sizeof(int32_t), st));   // all active (-1)
@@ -885,10 +974,7 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
     int32_t left = 0;
     for (int it = 0;; ++it) {
         FM_CUDA_TRY(ctx, cudaMemsetAsync(H.left, 0, sizeof(int32_t), st));
-        FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * S * cells, 12.0 * S * cells,
-                 k_stage_check<T><<<(unsigned)S, kBlock, 0, st>>>(
-                     g.n, S, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64,
-                     g.b, g.p, prm.tol, prm.qtol, H.qprev, H.active, H.left));
+        stage_test(H, k, prm, mixed, st);
         FM_CUDA_TRY(ctx, cudaMemcpyAsync(&left, H.left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
         if (left == 0) break;
@@ -1140,6 +1226,7 @@ static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine
     H.left = nullptr;
     H.iter = nullptr;
     H.qprev = nullptr;
+    H.partial = nullptr;
 }
 
 // ------------------------------------------------------------------ autotuning
