@@ -445,9 +445,22 @@ def run_native(args, wl, eps):
         # algorithmic bytes, scaled to the average timed launch
         roof["traffic"] = st["bytes"] / st["launches"] * COLOUR_DRAM_BYTES_PER_CELL_F32 / 12.0
         roof["traffic_source"] = "ncu dram bytes per cell (64 Mi-cell capture) x cells per launch"
-    if fam in ("kl_gemm_exp", "fmg_resident", "mlp_gemm"):
+    if fam == "fmg_resident":
+        # the whole FMG of a sample in shared memory: bound by the SM's
+        # arithmetic issue and latency, not HBM.  Flops are counted by the
+        # kernel (V-cycles and residual tests of every sample); the peak is
+        # GB300's FP32 FMA rate, 152 SMs x 128 lanes x 2 flops at the
+        # sampled SM clock.
+        clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_tf = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        ach_tf = st["flops"] / (st["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": fam, "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach_tf / peak_tf, "traffic": None,
+                "peak_source": "FP32 FMA lanes x clock (152 SMs x 128 x 2 flops x %.0f MHz)" % clk_mhz,
+                "note": "latency-bound: small grids in shared memory, a barrier per half-sweep"}
+    elif fam in ("kl_gemm_exp", "mlp_gemm"):
         roof["bound"] = "alu"
-        roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is ALU/latency bound"
+        roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is latency bound"
     roof["launches"] = st["launches"]
     roof["avg_launch_ms"] = per_launch_ms
     families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),

@@ -84,6 +84,7 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     cudaFree(ctx->d_sums);
     cudaFree(ctx->d_partials);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    cudaFree(ctx->prof.counters);
     mlp_free(ctx);
     uneven_free(ctx);
     if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);

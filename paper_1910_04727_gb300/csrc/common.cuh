@@ -96,6 +96,7 @@ struct ProfRecord {
     int family;
     cudaEvent_t start, stop;
     double bytes = 0.0, flops = 0.0;
+    int counter = -1;   // device flop counter the kernel adds to (-1: none)
 };
 
 struct Profiler {
@@ -104,6 +105,8 @@ struct Profiler {
     std::vector<ProfRecord> records;
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
+    double* counters = nullptr;   // device flop counters of kernels that count their own work
+    int counters_used = 0;
 };
 
 // ------------------------------------------------------------------ arena
@@ -190,6 +193,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Event-pair timing around one launch of `family` (no-op unless profiling).
 int prof_start(fm_ctx* ctx, int family, cudaStream_t st);
 void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops);
+// A zeroed device double for record idx that the launched kernel adds its
+// flops to (read at fm_profile_end); null when not profiling.
+double* prof_counter(fm_ctx* ctx, int idx);
 
 #define FM_TIMED(ctx, family, st, bytes, flops, ...)          \
     do {                                                       \

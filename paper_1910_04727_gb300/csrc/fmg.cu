@@ -124,6 +124,28 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b
     p[c] = acc * (T(1) / D[c]);
 }
 
+// Coarse value with ghosts: mirror across the no-flow edges, 2g - u across
+// the Dirichlet edges (g = 0 for an error).
+template <typename U>
+__device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U gW, U gE) {
+    J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
+    if (I < 0) return U(2) * gW - uc[(size_t)J * nc];
+    if (I > nc - 1) return U(2) * gE - uc[(size_t)J * nc + nc - 1];
+    return uc[(size_t)J * nc + I];
+}
+
+// (P u_c) at fine cell (i, j): bilinear cell-centred (9, 3, 3, 1) / 16 with
+// the ghosts above.  One expression for every kernel that prolongs.
+template <typename U>
+__device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, U gW, U gE) {
+    const int I = i >> 1, J = j >> 1;
+    const int Ix = (i & 1) ? I + 1 : I - 1;
+    const int Jy = (j & 1) ? J + 1 : J - 1;
+    return (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
+            U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
+           U(16);
+}
+
 // nsweeps red-black sweeps (colour 0 then 1) on tiles of TI x TI cells of
 // one sample, staged in shared memory with a halo of hh = 2 nsweeps cells:
 // each half-sweep leaves one more ring at the halo's edge stale, so after
@@ -139,7 +161,7 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
                                                    const T* __restrict__ b, const T* __restrict__ Te,
                                                    const T* __restrict__ Tn, const T* __restrict__ D,
                                                    const T* __restrict__ p_in, T* __restrict__ p_out,
-                                                   const int32_t* __restrict__ active) {
+                                                   const int32_t* __restrict__ active, const T* __restrict__ ec) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
     const int tiles = (n + TI - 1) / TI;
     const size_t s = blockIdx.x / ((unsigned)tiles * tiles);
@@ -158,7 +180,9 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
     for (int e = threadIdx.x; e < R; e += blockDim.x) {
         const int r = e / RW, q = e % RW;
         const size_t g = base + (size_t)(ya + r) * n + xa + q;
-        sp[e] = p_in[g];
+        // with ec: the coarse-grid correction p + (P e) as k_prolong forms it
+        sp[e] = ec ? p_in[g] + prolong_at(n / 2, ec + s * (size_t)(n / 2) * (n / 2), xa + q, ya + r, T(0), T(0))
+                   : p_in[g];
         sb[e] = b[g];
         se[e] = Te[g];
         sn[e] = Tn[g];
@@ -212,7 +236,8 @@ __global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, si
                                                                       const T* __restrict__ Tn,
                                                                       const T* __restrict__ D,
                                                                       const T* __restrict__ p_in, T* __restrict__ p_out,
-                                                                      const int32_t* __restrict__ active) {
+                                                                      const int32_t* __restrict__ active,
+                                                                      const T* __restrict__ ec) {
     static_assert(R % 2 == 0 && R % RPT == 0, "region must split into column pairs and row strips");
     constexpr int C = R / 2, P = R + 2;   // column pairs; padded row pitch
     __shared__ T sp[P * P];
@@ -238,7 +263,9 @@ __global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, si
             up[k][j] = false;
             if (x < RW && y < RH) {
                 const size_t g = base + (size_t)gy * n + gx;
-                rp[k][j] = p_in[g];
+                // with ec: the coarse-grid correction p + (P e) as k_prolong forms it
+                rp[k][j] = ec ? p_in[g] + prolong_at(n / 2, ec + s * (size_t)(n / 2) * (n / 2), gx, gy, T(0), T(0))
+                              : p_in[g];
                 rb[k][j] = b[g];
                 rr[k][j] = T(1) / D[g];
                 if (gx < n - 1) re[k][j] = Te[g];
@@ -325,28 +352,6 @@ __global__ void k_residual_restrict(int nc, size_t S, const T* __restrict__ bf, 
     const T r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bf, Te, Tn, D, pf);
     bc[t] = r00 + r10 + r01 + r11;
     pc[t] = T(0);
-}
-
-// Coarse value with ghosts: mirror across the no-flow edges, 2g - u across
-// the Dirichlet edges (g = 0 for an error).
-template <typename U>
-__device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U gW, U gE) {
-    J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
-    if (I < 0) return U(2) * gW - uc[(size_t)J * nc];
-    if (I > nc - 1) return U(2) * gE - uc[(size_t)J * nc + nc - 1];
-    return uc[(size_t)J * nc + I];
-}
-
-// (P u_c) at fine cell (i, j): bilinear cell-centred (9, 3, 3, 1) / 16 with
-// the ghosts above.  One expression for every kernel that prolongs.
-template <typename U>
-__device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, U gW, U gE) {
-    const int I = i >> 1, J = j >> 1;
-    const int Ix = (i & 1) ? I + 1 : I - 1;
-    const int Jy = (j & 1) ? J + 1 : J - 1;
-    return (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
-            U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
-           U(16);
 }
 
 // p_f += P e_c (add = 1, boundary values 0) or p_f = P u_c (add = 0, FMG start).
@@ -748,10 +753,13 @@ static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
 
 // Launch shape `tile` (tile interior staged in shared memory, p_in -> p_out;
 // 0: one launch per colour and sweep, in place on p_in) with `threads` per
-// CTA.  Returns the buffer that holds the result.
+// CTA.  Returns the buffer that holds the result.  With ec (tile shapes
+// only), the iterate is p_in + P ec, the coarse-grid correction added as
+// the tiles load.
 template <typename T>
 static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int nsweeps, const T* b, const T* Te,
-                      const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st) {
+                      const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st,
+                      const T* ec = nullptr) {
     if (nsweeps <= 0) return p_in;
     const size_t cells = S * (size_t)n * n;
     if (tile > 0) {
@@ -767,30 +775,30 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
         if (threads == 0 && hh == 0 && (n == 8 || n == 16 || n == 32 || (f32 && n == 64))) {
             if (n == 8)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 8, 1><<<grid, 4 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             else if (n == 16)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 16, 2><<<grid, 8 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             else if (n == 32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 32, 4><<<grid, 16 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             else if constexpr (f32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 64, 8><<<grid, 32 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             return p_out;
         }
         if (threads == 0 && hh > 0 && hh <= 4 && (TI == 32 || (f32 && TI == 64))) {
             if (TI == 32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 40, 5><<<grid, 20 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             else if constexpr (f32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 72, 9><<<grid, 36 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
             return p_out;
         }
         FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops,
                  k_rbgs_tile<T><<<grid, threads > 0 ? threads : 256, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
-                                  st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active));
+                                  st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
         return p_out;
     }
     T* p = p_in;
@@ -872,6 +880,11 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
         FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells, 5.0 * cells,
                  k_rbgs_color<T><<<blocks_for(cells / 2), kBlock, 0, st>>>(n, S, 1, g.b, Te, Tn, D, cur, active));
         smooth_with<T>(ctx, 0, 0, n, S, prm.nu2 - 1, g.b, Te, Tn, D, cur, g.p, active, st);
+        return;
+    }
+    if (tile > 0 && prm.nu2 >= 1) {
+        // tiles: the correction is added as they load the iterate
+        smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, c.p);
         return;
     }
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,

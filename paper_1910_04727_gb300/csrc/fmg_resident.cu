@@ -458,7 +458,20 @@ struct ResidentArgs {
     double tol, qtol;
     double *qf, *qc, *p_out;
     int32_t* status;
+    double* flops;   // nullable: the launch adds its solver flops here (profiling)
 };
+
+// Solver flops of one V(nu1, nu2) cycle from grid k down: per grid j >= 1,
+// nu1 + nu2 sweeps of 10 flops a cell, residual + restriction 10, correction
+// 8; the coarsest solve a dense 16 x 16 product.
+__device__ __forceinline__ double vcycle_flops(int n0, int k, int nu1, int nu2) {
+    double f = 2.0 * (n0 * n0) * (n0 * n0);
+    for (int j = 1; j <= k; ++j) {
+        const double c = (double)(n0 << j) * (n0 << j);
+        f += c * (10.0 * (nu1 + nu2) + 18.0);
+    }
+    return f;
+}
 
 // Shared memory of one CTA: a layout table per group, then each group's data.
 template <typename T>
@@ -491,6 +504,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
         R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
         bool ok = true;
         double q_coarse = NAN, q_fine = NAN;
+        double work = 0.0;   // solver flops of this sample (V-cycles and residual tests)
 
         for (int k = 0; k <= m; ++k) {
             const RGrid<T>& g = L.g[k];
@@ -510,8 +524,10 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             if (g.b) R::resident_stage_rhs(g, tpW, tpE);
             if (k == 0) R::resident_coarse_solve(g, L.ainv, tpW, tpE);
             if (!refined) {
-                if (k > 0)
+                if (k > 0) {
                     for (int it = 0; it < a.nu0; ++it) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
+                }
             } else if (!MIXED) {
                 // FP64: V-cycles on the stage problem until the residual or
                 // outflux-change test passes
@@ -519,6 +535,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 for (int it = 0;; ++it) {
                     double rr, bb;
                     R::stage_norms(g, tpW, tpE, L.red, rr, bb);
+                    work += 14.0 * g.n * g.n;
                     const double q = R::stage_outflux(g.te, g.p, g.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
@@ -528,6 +545,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                         break;
                     }
                     for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
                 }
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
@@ -540,6 +558,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 for (int it = 0;; ++it) {
                     double rr, bb;
                     R::ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
+                    work += 14.0 * h.n * h.n;
                     const double q = R::stage_outflux(h.te, h.p, h.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
@@ -550,6 +569,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                     }
                     // nu0 FP32 V-cycles on the correction equation per FP64 residual
                     for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
+                    work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2) + (double)h.n * h.n;
                     for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] += (double)g.p[c];
                     R::sync();
                 }
@@ -569,6 +589,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             }
         }
         if (R::rank() == 0) {
+            if (a.flops) atomicAdd(a.flops, work);
             a.qf[s] = q_fine;
             if (a.qc) a.qc[s] = q_coarse;
             if (a.status) a.status[s] = ok ? FM_OK : FM_ENOTCONV;
@@ -605,8 +626,11 @@ static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st)
     const size_t need = (a.S + groups - 1) / groups;
     const size_t grid = std::min<size_t>(need, (size_t)std::max(per_sm, 1) * sms);
     const double cells = (double)a.S * a.n_fine * a.n_fine;
-    FM_TIMED(ctx, kFamResidentFmg, st, 8.0 * cells + 16.0 * a.S, 0.0,
-             k_fmg_resident<T, MIXED, WARP><<<(unsigned)grid, threads, smem, st>>>(a));
+    const int pi = prof_start(ctx, kFamResidentFmg, st);
+    ResidentArgs b = a;
+    b.flops = prof_counter(ctx, pi);
+    k_fmg_resident<T, MIXED, WARP><<<(unsigned)grid, threads, smem, st>>>(b);
+    prof_stop(ctx, pi, st, 8.0 * cells + 16.0 * a.S, 0.0);
     return true;
 }
 
@@ -648,6 +672,7 @@ bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double
     a.qc = qc;
     a.p_out = p_out;
     a.status = status;
+    a.flops = nullptr;
     if (prm.precision == FM_PREC_MIXED) return launch_resident<float, true>(ctx, a, st);
     return launch_resident<double, false>(ctx, a, st);
 }

@@ -1,5 +1,6 @@
 // Event-pair timing of kernel families for roofline reports.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -28,6 +29,22 @@ int prof_start(fm_ctx* ctx, int family, cudaStream_t st) {
     return (int)P.records.size() - 1;
 }
 
+constexpr int kMaxCounters = 1 << 14;
+
+double* prof_counter(fm_ctx* ctx, int idx) {
+    Profiler& P = ctx->prof;
+    if (idx < 0 || P.counters_used >= kMaxCounters) return nullptr;
+    if (!P.counters) {
+        if (cudaMalloc((void**)&P.counters, kMaxCounters * sizeof(double)) != cudaSuccess) {
+            P.counters = nullptr;
+            return nullptr;
+        }
+        cudaMemset(P.counters, 0, kMaxCounters * sizeof(double));
+    }
+    P.records[idx].counter = P.counters_used;
+    return P.counters + P.counters_used++;
+}
+
 void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops) {
     if (idx < 0) return;
     ProfRecord& r = ctx->prof.records[idx];
@@ -46,6 +63,8 @@ extern "C" fm_status fm_profile_begin(fm_ctx* ctx, uint32_t family_mask) {
     ctx->prof.mask = family_mask;
     ctx->prof.records.clear();
     ctx->prof.pool_used = 0;
+    if (ctx->prof.counters) cudaMemset(ctx->prof.counters, 0, kMaxCounters * sizeof(double));
+    ctx->prof.counters_used = 0;
     return FM_OK;
 }
 
@@ -56,6 +75,10 @@ extern "C" fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t 
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     fm_kernel_stat acc[kFamilyCount];
     for (int f = 0; f < kFamilyCount; ++f) acc[f] = fm_kernel_stat{f, 0, 0.0, 0.0, 0.0};
+    std::vector<double> counted(ctx->prof.counters_used);
+    if (!counted.empty())
+        FM_CUDA_TRY(ctx, cudaMemcpy(counted.data(), ctx->prof.counters, counted.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost));
     for (const ProfRecord& r : ctx->prof.records) {
         float ms = 0.0f;
         FM_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, r.start, r.stop));
@@ -63,7 +86,7 @@ extern "C" fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t 
         a.launches += 1;
         a.ms += ms;
         a.bytes += r.bytes;
-        a.flops += r.flops;
+        a.flops += r.flops + (r.counter >= 0 ? counted[r.counter] : 0.0);
     }
     int out = 0;
     for (int f = 0; f < kFamilyCount; ++f)
