@@ -10,7 +10,8 @@
 //   te   east-face transmissibility (2K on the east edge)
 //   tn   north-face transmissibility (0 on the north edge)
 //   tw   west-edge transmissibility 2K of each row (n values)
-//   dinv reciprocal diagonal (FP64 form only; FP32 divides on the fly)
+//   dinv reciprocal diagonal (FP64 form, and the mixed form up to 16 x 16;
+//        otherwise the FP32 smoother divides by D formed from the faces)
 //   b    right-hand side.  In the FP64 form the finest grid has none: it only
 //        ever solves its stage problem, whose right-hand side (the Dirichlet
 //        data) is formed on the fly from tw, te, p_W and p_E.
@@ -70,7 +71,10 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         g.te = (T*)take(c * sizeof(T));
         g.tn = (T*)take(c * sizeof(T));
         g.tw = (T*)take(n * sizeof(T));
-        g.dinv = mixed ? nullptr : (T*)take(c * sizeof(T));
+        // the mixed form keeps 1/D only for hierarchies up to 16 x 16 (one
+        // sample per warp), where it costs no occupancy; larger ones form D
+        // from the faces and divide
+        g.dinv = (mixed && n_fine > 16) ? nullptr : (T*)take(c * sizeof(T));
         g.b = (mixed || k < L.m) ? (T*)take(c * sizeof(T)) : nullptr;
     }
     for (int q = 0; q < 2; ++q) {
@@ -122,13 +126,15 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
         const int i = c % n, j = c / n;
         if (h || sizeof(T) == 8) {
             const double k = K(i, j);
-            const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
             const double te = (i < n - 1) ? harm(k, K(i + 1, j)) : 2.0 * k;
-            const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
             const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : 0.0;
             g.te[c] = (T)te;
             g.tn[c] = (T)tn;
-            if (g.dinv) g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
+            if (g.dinv) {   // the FP64 form's diagonal (the mixed form forms it on the fly)
+                const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
+                const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
+                g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
+            }
             if (i == 0) g.tw[j] = (T)(2.0 * k);
             if (h) {
                 h->te[c] = te;
