@@ -146,3 +146,42 @@ def test_two_gloo_ranks_reproduce_one_rank(single):
     for e, n_total in enumerate(N):
         ids = sorted(i for rank in (0, 1) for f, n in res[rank][4][e] for i in range(f, f + n))
         assert ids == list(range(n_total))
+
+
+class HostQMCSampler(HostSampler):
+    """Level sums per (level, shift) of the oracle's randomized-QMC sampler."""
+
+    def __init__(self, n_ext, R):
+        from paper_1910_04727_gb300 import _lib
+        from oracle import lib as OL
+        self.s = mlmc.FMGSampler(LEVELS, _basis(), seed=29, qmc_dirnums=OL.sobol_direction_numbers(16),
+                                 n_shifts=R)
+        self.R = R
+        self.sums = (_lib.FmLevelSums * (n_ext * R))()
+        self.drawn = [[] for _ in range(n_ext)]
+
+    def enqueue(self, e, first, n, shift):
+        y, qf, qc = self.s(e, first, n, shift)
+        cell = self.sums[e * self.R + shift]
+        for v, f, c in zip(y, qf, qc):
+            _neumaier(cell.sum_y, float(v))
+            _neumaier(cell.sum_y2, float(v) * float(v))
+            _neumaier(cell.sum_qf, float(f))
+            _neumaier(cell.sum_qc, float(c) if e > 0 else 0.0)
+        cell.count += n
+
+
+def test_core_follows_the_oracle_mlqmc_doubling_rule():
+    """QMC (Algorithm 2): R shifted Sobol' point sets per level, the doubling
+    rule on the level maximising V[Y^_l] / (N_l C_l); the native controller
+    and the oracle reach the same N_l and estimate."""
+    import paper_1910_04727_gb300 as fm
+    R, eps = 4, 2e-3
+    h = HostQMCSampler(len(LEVELS), R)
+    r = fm.estimate_core(_cost(), eps, h.enqueue, h.read, qmc=True, n_shifts=R, n_pilot=8)
+    from oracle import lib as OL
+    ref_s = mlmc.FMGSampler(LEVELS, _basis(), seed=29, qmc_dirnums=OL.sobol_direction_numbers(16), n_shifts=R)
+    ref = mlmc.mlqmc(ref_s, len(LEVELS) - 1, eps, 8, R, _cost())
+    assert list(r["N"]) == list(ref["N"]) and r["rounds"] == ref["rounds"]
+    assert math.isclose(r["estimate"], ref["estimate"], rel_tol=1e-12)
+    assert r["var_estimator"] <= eps ** 2 / 2
