@@ -61,6 +61,14 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
+// Programmatic dependent launch: wait until the preceding kernel of the
+// stream has completed (and its writes are visible), then let the next one be
+// scheduled.  No-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // n consecutive FP32 / BF16 values of one row: 16-byte stores when the row
 // chunk is whole and aligned, element stores otherwise.
 __device__ __forceinline__ void store_row_f32(float* p, const float (&a)[32], int n) {
@@ -137,6 +145,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    // the setup above overlaps the previous kernel; its outputs are read below
+    pdl_wait_then_release();
     if (warp == 0 && lane == 0) {
         for (int kb = 0; kb < kblocks; ++kb) {
             const int st = kb % kGStages, round = kb / kGStages;
@@ -228,7 +238,8 @@ __global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, _
 // 2 (out[b] - t[b]) / B and the squared error.
 __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __nv_bfloat16* __restrict__ w4,
                           const float* __restrict__ b4, const float* __restrict__ t, float* __restrict__ out,
-                          float* __restrict__ dout, float* __restrict__ sq) {
+                          float* __restrict__ dout, float* __restrict__ sq) {    pdl_wait_then_release();
+
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (b >= B) return;
     float acc = 0.0f;
@@ -250,7 +261,8 @@ __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __n
 // Output layer backward: dZ3 = bf16((dout w4) * gelu'(Z3)), row-major and transposed [kH][ldt].
 __global__ void k_mlp_out_back(int B, int ldt, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ w4,
                                const float* __restrict__ Z3, __nv_bfloat16* __restrict__ dZ,
-                               __nv_bfloat16* __restrict__ dZT) {
+                               __nv_bfloat16* __restrict__ dZT) {    pdl_wait_then_release();
+
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B * kH) return;
     const int b = t / kH, j = t % kH;
@@ -264,7 +276,8 @@ __global__ void k_mlp_out_back(int B, int ldt, const float* __restrict__ dout, c
 // fixed order): gb[j] = sum_b w[b] T[j][b], with w = 1 when null.  With
 // ones_row, warp N also writes gb[N] = sum_b w[b] (the output bias).
 __global__ void k_row_sums(int N, int B, int ldt, const __nv_bfloat16* __restrict__ T, const float* __restrict__ w,
-                           float* __restrict__ gb, float* __restrict__ ones_row) {
+                           float* __restrict__ gb, float* __restrict__ ones_row) {    pdl_wait_then_release();
+
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (j > N || (j == N && !ones_row)) return;
     float acc = 0.0f;
@@ -302,7 +315,8 @@ __global__ void k_surrogate_value(int n, const float* __restrict__ out, double m
 __global__ void k_train_batch(int B, int M, int D, int ldt, int n, int spe, const int* __restrict__ step,
                               const int32_t* __restrict__ perm, const double* __restrict__ xi,
                               const float* __restrict__ tt, __nv_bfloat16* __restrict__ X,
-                              __nv_bfloat16* __restrict__ XT, float* __restrict__ t) {
+                              __nv_bfloat16* __restrict__ XT, float* __restrict__ t) {    pdl_wait_then_release();
+
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * D) return;
     const int b = i / D, k = i % D;
@@ -329,7 +343,8 @@ struct AdamArgs {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W2T, *W3T, *w4b;
 };
 
-__global__ void k_adam_step(AdamArgs a) {
+__global__ void k_adam_step(AdamArgs a) {    pdl_wait_then_release();
+
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.np) return;
     const int s = *a.step;
@@ -359,7 +374,10 @@ __global__ void k_adam_step(AdamArgs a) {
     }
 }
 
-__global__ void k_tick(int* step) { *step += 1; }
+__global__ void k_tick(int* step) {
+    pdl_wait_then_release();
+    *step += 1;
+}
 
 // X[b][k] = bf16(Phi^-1(u)) for the MC sample first + b of Philox stream
 // `level` (the words of the FP64 points: u from the top 23 bits of word k,
@@ -443,6 +461,28 @@ static bool map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Launch, with programmatic stream serialisation when pdl (the training
+// graph: each kernel's launch and prologue overlap the previous kernel).
+template <typename... KArgs, typename... Args>
+static void launch(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args... args) {
+    if (!pdl) {
+        k<<<grid, block, smem, st>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int BN, int EPI>
 static bool gemm_attr() {
     return cudaFuncSetAttribute(k_gemm_bf16_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -452,11 +492,12 @@ static bool gemm_attr() {
 // D = A B^T over K (a multiple of 64): M x N outputs in 128 x BN tiles.
 template <int BN, int EPI>
 static void gemm(fm_ctx* ctx, const CUtensorMap& A, const CUtensorMap& B, int M, int N, int K, const EpiArgs& e,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool pdl = false) {
     dim3 grid((M + kGm - 1) / kGm, (N + BN - 1) / BN);
     FM_TIMED(ctx, kFamMlp, st, 2.0 * ((double)M * K + (double)N * K) + 4.0 * (double)M * N,
              2.0 * (double)M * N * K,
-             k_gemm_bf16_tc<BN, EPI><<<grid, 128, gemm_smem<BN>(), st>>>(A, B, K / kGk, e, state(ctx)->err));
+             launch(pdl, k_gemm_bf16_tc<BN, EPI>, grid, dim3(128), gemm_smem<BN>(), st, A, B, K / kGk, e,
+                    state(ctx)->err));
 }
 
 static fm_status mlp_alloc(fm_ctx* ctx) {
@@ -548,39 +589,39 @@ static void refresh_bf16(fm_ctx* ctx, cudaStream_t st) {
 
 // Forward + backward of one batch of B rows (a multiple of 128, <= kMaxBatch)
 // already in S->X / S->XT / S->t; gradients into S->G.
-static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st) {
+static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = false) {
     MlpState* S = state(ctx);
     const int D = S->D, L = kMaxBatch;
     constexpr int BN = kTrainBN;
     EpiArgs e{};
     // forward: Z_l = H_(l-1) W_l^T + b_l, H_l = bf16(gelu(Z_l))
     e = EpiArgs{B, kH, S->P + S->off[1], S->Z[0], kH, S->H[0], kH, S->HT[0], L, nullptr, 0};
-    gemm<BN, kEpiFwdGelu>(ctx, S->mX, S->tW1, B, kH, D, e, st);
+    gemm<BN, kEpiFwdGelu>(ctx, S->mX, S->tW1, B, kH, D, e, st, pdl);
     e = EpiArgs{B, kH, S->P + S->off[3], S->Z[1], kH, S->H[1], kH, S->HT[1], L, nullptr, 0};
-    gemm<BN, kEpiFwdGelu>(ctx, S->mH1, S->tW2, B, kH, kH, e, st);
+    gemm<BN, kEpiFwdGelu>(ctx, S->mH1, S->tW2, B, kH, kH, e, st, pdl);
     e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], L, nullptr, 0};
-    gemm<BN, kEpiFwdGelu>(ctx, S->mH2, S->tW3, B, kH, kH, e, st);
-    k_mlp_out<<<nb((size_t)B * 32), 256, 0, st>>>(B, S->H[2], S->w4b, S->P + S->off[7], S->t, S->out, S->dout, S->sq);
+    gemm<BN, kEpiFwdGelu>(ctx, S->mH2, S->tW3, B, kH, kH, e, st, pdl);
+    launch(pdl, k_mlp_out, dim3(nb((size_t)B * 32)), dim3(256), 0, st, B, S->H[2], S->w4b, S->P + S->off[7], S->t, S->out, S->dout, S->sq);
     // output layer: gw4 = dout^T H3, gb4 = sum dout, dZ3 = bf16(dout w4 gelu'(Z3))
-    k_row_sums<<<nb((size_t)(kH + 1) * 32), 256, 0, st>>>(kH, B, L, S->HT[2], S->dout, S->G + S->off[6],
+    launch(pdl, k_row_sums, dim3(nb((size_t)(kH + 1) * 32)), dim3(256), 0, st, kH, B, L, S->HT[2], S->dout, S->G + S->off[6],
                                                           S->G + S->off[7]);
-    k_mlp_out_back<<<nb((size_t)B * kH), 256, 0, st>>>(B, L, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
+    launch(pdl, k_mlp_out_back, dim3(nb((size_t)B * kH)), dim3(256), 0, st, B, L, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
     // layer 3: dW3 = dZ3^T H2, db3, dZ2 = bf16((dZ3 W3) gelu'(Z2))
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[4], kH};
-    gemm<BN, kEpiF32>(ctx, S->mdZ3T, S->tH2T, kH, kH, B, e, st);
-    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[2], nullptr, S->G + S->off[5], nullptr);
+    gemm<BN, kEpiF32>(ctx, S->mdZ3T, S->tH2T, kH, kH, B, e, st, pdl);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[2], nullptr, S->G + S->off[5], nullptr);
     e = EpiArgs{B, kH, nullptr, S->Z[1], kH, S->dZ[1], kH, S->dZT[1], L, nullptr, 0};
-    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ3, S->tW3T, B, kH, kH, e, st);
+    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ3, S->tW3T, B, kH, kH, e, st, pdl);
     // layer 2
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[2], kH};
-    gemm<BN, kEpiF32>(ctx, S->mdZ2T, S->tH1T, kH, kH, B, e, st);
-    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[1], nullptr, S->G + S->off[3], nullptr);
+    gemm<BN, kEpiF32>(ctx, S->mdZ2T, S->tH1T, kH, kH, B, e, st, pdl);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[1], nullptr, S->G + S->off[3], nullptr);
     e = EpiArgs{B, kH, nullptr, S->Z[0], kH, S->dZ[0], kH, S->dZT[0], L, nullptr, 0};
-    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ2, S->tW2T, B, kH, kH, e, st);
+    gemm<BN, kEpiBwdGelu>(ctx, S->mdZ2, S->tW2T, B, kH, kH, e, st, pdl);
     // layer 1: dW1 = dZ1^T X (N = D input columns; the FP32 gradient keeps the M real ones)
     e = EpiArgs{kH, S->M, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[0], S->M};
-    gemm<BN, kEpiF32>(ctx, S->mdZ1T, S->tXT, kH, D, B, e, st);
-    k_row_sums<<<nb((size_t)kH * 32), 256, 0, st>>>(kH, B, L, S->dZT[0], nullptr, S->G + S->off[1], nullptr);
+    gemm<BN, kEpiF32>(ctx, S->mdZ1T, S->tXT, kH, D, B, e, st, pdl);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[0], nullptr, S->G + S->off[1], nullptr);
 }
 
 // Forward of n rows, chunked: fill(o, cnt, st) writes rows o .. o+cnt-1 of
@@ -815,11 +856,13 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         const bool prof_on = ctx->prof.active;
         ctx->prof.active = false;    // no event records inside the captured graph
         FM_CUDA_TRY(ctx, cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal));
-        k_train_batch<<<nb((size_t)batch * S->D), 256, 0, ts>>>(batch, M, S->D, kMaxBatch, n, spe, S->step, dperm,
-                                                                 xi, tt, S->X, S->XT, S->t);
-        train_step_grads(ctx, batch, ts);
-        k_adam_step<<<nb(S->np), 256, 0, ts>>>(aa);
-        k_tick<<<1, 1, 0, ts>>>(S->step);
+        // programmatic dependent launches: every kernel's launch and setup
+        // overlap its predecessor (kernels wait for it before touching data)
+        launch(true, k_train_batch, dim3(nb((size_t)batch * S->D)), dim3(256), 0, ts, batch, M, S->D, kMaxBatch, n,
+               spe, (const int*)S->step, (const int32_t*)dperm, (const double*)xi, (const float*)tt, S->X, S->XT, S->t);
+        train_step_grads(ctx, batch, ts, true);
+        launch(true, k_adam_step, dim3(nb(S->np)), dim3(256), 0, ts, aa);
+        launch(true, k_tick, dim3(1), dim3(1), 0, ts, S->step);
         const cudaError_t ce = cudaStreamEndCapture(ts, &graph);
         ctx->prof.active = prof_on;
         FM_CUDA_TRY(ctx, ce);
