@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--form", default="mixed_surrogate",
                     choices=["mixed_surrogate", "mixed_surrogate_batched", "mixed", "fp64_converged",
                              "fp64_fmg2"])
+    ap.add_argument("--no-standard-leg", action="store_true",
+                    help="skip the FMG-MLMC vs standard-MLMC cost comparison")
     ap.add_argument("--no-uneven-leg", action="store_true",
                     help="skip the uneven-batch leg (4096 samples over 64x64 .. 1024x1024)")
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
@@ -344,6 +346,57 @@ def uneven_leg(torch, fm, flush):
     return out
 
 
+def standard_mlmc_leg(torch, ctx, wl, N, flush, samples=1000):
+    """The paper's cost claim (Sec. 1): FMG-MLMC takes Q^c_l from the FMG
+    hierarchy of the level-l solve, where standard MLMC solves the coarse
+    problem of the same sample again.  With nested field points that coarse
+    problem is the level-(l-1) field of the same xi, so its solve is timed
+    here on the same samples, and its outflux checked against the by-product.
+    The saving is the coarse solves' share of standard MLMC's cost at the
+    estimate's N_l (level 0 has no coarse solve in either)."""
+    out = {"levels": [], "samples": samples}
+    t_f, t_c, q_diff, k_diff = [], [], [], [0.0]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    for l in range(len(wl.levels)):
+        xi = ctx.mc_points(l, 0, samples)
+        Kf = ctx.kl_field_batch(l, xi)
+        tf, (qf, qc, _) = timed(lambda: ctx.fmg_solve_batch(Kf))
+        t_f.append(tf / samples)
+        if l == 0:
+            t_c.append(0.0)
+            q_diff.append(0.0)
+            continue
+        Kc = ctx.kl_field_batch(l - 1, xi)
+        inj = Kf[:, ::2, ::2]
+        k_diff.append(float(((Kc - inj).abs() / inj.abs()).max()))
+        tc, (qc_std, _, _) = timed(lambda: ctx.fmg_solve_batch(Kc))
+        t_c.append(tc / samples)
+        q_diff.append(float(((qc_std - qc).abs() / qc.abs()).max()))
+    N = np.asarray(N, float)
+    fmg_cost = float(np.sum(N * np.array(t_f)))
+    std_cost = fmg_cost + float(np.sum(N * np.array(t_c)))
+    out["levels"] = [{"n": n, "fine_us_per_sample": 1e6 * a, "coarse_us_per_sample": 1e6 * c,
+                      "max_rel_diff_field": k, "max_rel_diff_qc": d}
+                     for n, a, c, k, d in zip(wl.levels, t_f, t_c, k_diff, q_diff)]
+    out["saving_of_fmg_mlmc"] = 1.0 - fmg_cost / std_cost
+    out["note"] = ("solver time weighted by the chosen form's N_l; the standard path's coarse field (the "
+                   "level-(l-1) field of the same xi) against the injected fine field, and its separately "
+                   "converged outflux against the FMG by-product")
+    return out
+
+
 def run_native(args, wl, eps):
     import torch
     import torch.distributed as dist
@@ -397,6 +450,7 @@ def run_native(args, wl, eps):
         c2.close()
 
     uneven = None if args.no_uneven_leg else uneven_leg(torch, fm, flush)
+    standard = None if args.no_standard_leg else standard_mlmc_leg(torch, ctx, wl, results[-1]["N"], flush)
 
     # the randomized-QMC estimator (16 shifted Sobol' point sets, doubling rule)
     # in the chosen form and in the plain FP64 form, timed the same way
@@ -504,6 +558,7 @@ def run_native(args, wl, eps):
         "other_forms": others,
         "qmc": qmc_forms,
         "uneven_batch": uneven,
+        "fmg_vs_standard_mlmc": standard,
         "roofline": roof,
         "kernel_families": families,
         "gpu_launches": total_launches,
