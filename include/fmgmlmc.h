@@ -317,6 +317,10 @@ typedef struct {
     int32_t surrogate;    /* 1: add the surrogate control-variate level below level 0 */
     double surrogate_cost; /* cost of an S-level sample relative to a level-0 sample */
     int32_t batched;      /* 1: each round's solves of all levels as one uneven batch (fmg_solve_uneven) */
+    int32_t adapt_L;      /* 1: grow the finest level from L_start (bias test of Algorithms 1-3) up to
+                             n_levels - 1; 0: use every level of the context */
+    int32_t L_start;      /* adapt_L: the first finest level, 1 .. n_levels - 1 (the paper starts at 2) */
+    double alpha;         /* weak rate of the bias test; <= 0: fitted on the level means, floored at 1/2 */
 } fm_estimate_opts;
 
 typedef struct {
@@ -325,8 +329,8 @@ typedef struct {
     double mean[FM_MAX_LEVELS];      /* mean(Y_l) */
     double var[FM_MAX_LEVELS];       /* MC: V_l; QMC: variance of the level estimate */
     int64_t N[FM_MAX_LEVELS];        /* samples per level (per shift for QMC) */
-    double alpha, beta;              /* fitted rates of |E Y_l| and V_l, l >= 1 */
-    double bias;                     /* |mean(Y_L)| / (2^alpha - 1) */
+    double alpha, beta;              /* fitted rates of |E Y_l| and V_l, l = 1 .. L */
+    double bias;                     /* |mean(Y_L)| / (2^alpha_used - 1) (Algorithm 1) */
     int32_t rounds;
     double seconds;                  /* wall time of the call */
     double mean_s, var_s;            /* surrogate level: mean(S), V[S] (or its level-estimate variance) */
@@ -334,12 +338,17 @@ typedef struct {
     double level_seconds[FM_MAX_LEVELS]; /* device time spent sampling each level (CUDA events) */
     double seconds_s;                /* device time spent on the surrogate level */
     double batched_seconds;          /* batched mode: device time of the rounds' uneven batches */
+    int32_t L;                       /* finest level used (n_levels - 1 unless adapt_L stopped earlier) */
+    int32_t bias_ok;                 /* bias < eps / sqrt(2) */
+    double alpha_used;               /* opts alpha if > 0, else max(alpha, 1/2) (1/2 if not fitted) */
 } fm_result;
 
 /* The host controller (Algorithm 3 with the MC rule N_l = (2/eps^2)
  * sqrt(V_l/C_l) sum_k sqrt(V_k C_k), or Algorithm 2's doubling rule for
- * QMC), at the fixed finest level n_levels - 1, with the cost model
- * C_l = (4/3) (n_level0 << l)^2.  Uses the default stream, synchronous. */
+ * QMC), at the fixed finest level n_levels - 1 or, with adapt_L, growing
+ * the finest level until the bias test passes (mlmc_estimate_core), with
+ * the cost model C_l = (4/3) (n_level0 << l)^2.  Uses the default stream,
+ * synchronous. */
 fm_status mlmc_estimate(fm_ctx* ctx, const fm_estimate_opts* opts, fm_result* out);
 
 /* ---------------------------------------------------------------- controller over ranks */
@@ -367,6 +376,11 @@ typedef struct {
     int64_t n_pilot;       /* initial samples per level (per shift for QMC), >= 2 */
     int32_t max_rounds;    /* controller rounds (<= 0: 100) */
     int32_t rank, world;   /* this rank and the number of ranks (world 1: no allgather) */
+    int32_t level0;        /* extended index of MLMC level 0 (1 with a surrogate level below it, else 0) */
+    int32_t adapt;         /* 1: grow the finest level (the bias test of Algorithms 1-3) up to n_ext - 1 */
+    int32_t n_ext_start;   /* adapt: extended levels in use at the start, level0 + 2 .. n_ext */
+    double alpha;          /* weak rate of the bias test; <= 0: the fitted rate of |mean(Y_l)|, l >= 1,
+                              floored at 1/2 */
 } fm_core_opts;
 
 typedef struct {
@@ -374,6 +388,10 @@ typedef struct {
     double mean[FM_MAX_LEVELS + 1], var[FM_MAX_LEVELS + 1];
     int64_t N[FM_MAX_LEVELS + 1];    /* samples per level over all ranks (per shift for QMC) */
     int32_t rounds;
+    int32_t n_ext_used;              /* extended levels in use at the end (n_ext unless adapt) */
+    int32_t bias_ok;                 /* bias < eps / sqrt(2) */
+    double bias, alpha_used;         /* Richardson estimate |mean(Y_L)| / (2^alpha - 1) and its alpha
+                                        (NaN when no level >= 1 is in use) */
 } fm_core_result;
 
 /* Rank `rank`'s contiguous share of samples first .. first+n-1 among `world`
@@ -381,8 +399,14 @@ typedef struct {
  * ranks.  Host only. */
 void fm_shard_range(uint64_t first, uint64_t n, int32_t rank, int32_t world, uint64_t* my_first, uint64_t* my_n);
 
-/* The controller of mlmc_estimate over callbacks (Algorithms 1-3 at a fixed
- * finest level; sample sizes as in mlmc_estimate).  Every request is split
+/* The controller of mlmc_estimate over callbacks (Algorithms 1-3; sample
+ * sizes as in mlmc_estimate).  With adapt the finest level grows: starting
+ * from n_ext_start levels, once the sample sizes are met (MC: no level needs
+ * extra samples; QMC: sum of the level-estimate variances <= eps^2/2) the
+ * run stops if the Richardson bias estimate is below eps/sqrt(2) or every
+ * level is in use, else the next level gets n_pilot samples (per shift) and
+ * the rounds go on.  Without adapt all n_ext levels are used from the start
+ * and the bias estimate is only reported.  Every request is split
  * by fm_shard_range; the ranks' sums are folded in rank order (Neumaier), so
  * all ranks compute the same schedule and the same estimate.  Host only: it
  * makes no CUDA call.  On an error status `err` (nullable, errlen bytes)

@@ -10,6 +10,12 @@ TEST INFRASTRUCTURE ONLY (see the oracle package docstring).
     2.3 states the problem, not the answer): by Lagrange multipliers
     N_l = (2/eps^2) sqrt(V_l/C_l) sum_k sqrt(V_k C_k), rounded up;
   * Richardson bias estimate |E[Y_L]| / (2^alpha - 1) (Algorithm 1);
+  * growth of the finest level (Algorithms 1-3): start at L = L_start; once
+    the sample sizes are met (MC: no level needs extra samples; QMC:
+    sum_l V[Y^_l] <= eps^2/2), stop if the bias estimate is below
+    eps/sqrt(2), else add level L + 1 with a pilot set.  alpha is the
+    caller's weak rate, or the fitted slope of -log2|Y^_l| over l = 1..L
+    floored at 1/2 (a noisy two-point fit must not drive 2^alpha - 1 to 0);
   * MLQMC (Algorithm 2): R independently shifted point sets per level; the
     level estimate is the mean over shifts and its variance the sample
     variance of the R shift means divided by R; while sum_l V[Y^_l] > eps^2/2
@@ -202,3 +208,108 @@ class SurrogateLevels:
             qf, _ = self.s.solve(0, xi)
             return qf - self.predict(xi), qf, self.predict(xi)
         return self.s(l - 1, first, n, r)
+
+
+ALPHA_MIN = 0.5
+
+
+def richardson_bias(level_means, alpha=None):
+    """Algorithm 1's weak-error estimate |E[Q_L - Q]| ~ |E[Y_L]| / (2^alpha - 1).
+    level_means: the means of Y_1 .. Y_L.  Returns (bias, alpha used)."""
+    if alpha is None or not alpha > 0:
+        a = fit_rate(np.concatenate([[np.nan], level_means]), 1)
+        alpha = max(a, ALPHA_MIN) if np.isfinite(a) else ALPHA_MIN
+    return abs(level_means[-1]) / (2.0 ** alpha - 1.0), float(alpha)
+
+
+def mlmc_adaptive(sampler, L_start, L_max, eps, n_pilot, cost, alpha=None, below=0, max_rounds=200):
+    """Algorithm 1 (Algorithm 3 with an FMG sampler) with the finest level
+    grown from L_start up to at most L_max.  Extended levels e = 0 ..
+    below + L: `below` levels sit under MLMC level 0 (1 with the surrogate
+    level), cost[e] is the cost of one sample of extended level e.  Each
+    round evaluates the extra samples dN_e, then updates V_e and the optimal
+    N_e; when no level needs more, the bias test decides between stopping
+    and adding a level with n_pilot samples."""
+    n_all = below + L_max + 1
+    acc = LevelAccumulator(n_all)
+    L = L_start
+    dN = np.zeros(n_all, np.int64)
+    dN[:below + L + 1] = n_pilot
+    rounds = 0
+    while rounds < max_rounds:
+        E = below + L + 1
+        for e in range(E):
+            if dN[e] > 0:
+                y, qf, qc = sampler(e, acc.N(e), int(dN[e]))
+                acc.add(e, y, qf, qc)
+        rounds += 1
+        V = np.array([acc.var(e) for e in range(E)])
+        Nopt = optimal_samples(V, cost[:E], eps)
+        dN[:E] = np.maximum(0, Nopt - np.array([acc.N(e) for e in range(E)]))
+        if np.any(dN[:E] > 0):
+            continue
+        bias, _ = richardson_bias(np.array([acc.mean(e) for e in range(below + 1, E)]), alpha)
+        if bias < eps / math.sqrt(2.0) or L == L_max:
+            break
+        L += 1
+        dN[below + L] = n_pilot
+    E = below + L + 1
+    means = np.array([acc.mean(e) for e in range(E)])
+    V = np.array([acc.var(e) for e in range(E)])
+    N = np.array([acc.N(e) for e in range(E)])
+    bias, a_used = richardson_bias(means[below + 1:], alpha)
+    return dict(estimate=math.fsum(means), means=means, V=V, N=N, var_estimator=float(np.sum(V / N)),
+                L=L, bias=bias, alpha_used=a_used, bias_ok=bool(bias < eps / math.sqrt(2.0)), rounds=rounds,
+                cost=float(np.sum(N * cost[:E])))
+
+
+def mlqmc_adaptive(sampler, L_start, L_max, eps, n_pilot, R, cost, alpha=None, below=0, max_rounds=400):
+    """Algorithm 2 with the finest level grown from L_start up to at most
+    L_max: while sum_e V[Y^_e] > eps^2/2 double N_e on the level maximising
+    V[Y^_e] / (N_e C_e); otherwise stop if the bias estimate is below
+    eps/sqrt(2), else add a level with n_pilot points per shift.  Each
+    doubling and each added level counts as a round."""
+    n_all = below + L_max + 1
+    Ys = [[[] for _ in range(R)] for _ in range(n_all)]
+    N = np.zeros(n_all, np.int64)
+
+    def draw(e, first, n):
+        for r in range(R):
+            Ys[e][r].extend(np.asarray(sampler(e, first, n, r)[0]).tolist())
+
+    def level_stats(e):
+        m = np.array([math.fsum(Ys[e][r]) / len(Ys[e][r]) for r in range(R)])
+        mean = math.fsum(m) / R
+        return mean, math.fsum((m - mean) ** 2) / (R * (R - 1))
+
+    L = L_start
+    for e in range(below + L + 1):
+        draw(e, 0, n_pilot)
+        N[e] = n_pilot
+    rounds = 0
+    while rounds < max_rounds:
+        E = below + L + 1
+        stats = [level_stats(e) for e in range(E)]
+        Vhat = np.array([s[1] for s in stats])
+        if Vhat.sum() > eps ** 2 / 2:
+            e = int(np.argmax(Vhat / (N[:E] * cost[:E])))
+            draw(e, int(N[e]), int(N[e]))
+            N[e] *= 2
+            rounds += 1
+            continue
+        bias, _ = richardson_bias(np.array([s[0] for s in stats[below + 1:]]), alpha)
+        if bias < eps / math.sqrt(2.0) or L == L_max:
+            break
+        L += 1
+        draw(below + L, 0, n_pilot)
+        N[below + L] = n_pilot
+        rounds += 1
+    E = below + L + 1
+    stats = [level_stats(e) for e in range(E)]
+    means = np.array([s[0] for s in stats])
+    Vhat = np.array([s[1] for s in stats])
+    bias, a_used = richardson_bias(means[below + 1:], alpha)
+    return dict(estimate=math.fsum(means), means=means, Vhat=Vhat, N=N[:E].copy(),
+                var_estimator=float(Vhat.sum()), L=L, bias=bias, alpha_used=a_used,
+                bias_ok=bool(bias < eps / math.sqrt(2.0)),
+                rounds=rounds, cost=float(np.sum(N[:E] * R * cost[:E])))

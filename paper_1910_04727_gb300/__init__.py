@@ -78,14 +78,16 @@ def _allgather_cb(gather):
 
 
 def estimate_core(cost, eps, enqueue, read, gather=None, qmc=False, n_shifts=0, n_pilot=1000,
-                  max_rounds=100, rank=0, world=1):
+                  max_rounds=100, rank=0, world=1, level0=0, adapt_from=None, alpha=0.0):
     """mlmc_estimate_core over Python callables: enqueue(ext_level, first, n, shift) queues
     samples on this rank; read() returns this rank's running sums as a sequence of
-    FmLevelSums ([n_ext][R]); gather(bytes) -> bytes of all ranks (None for one rank)."""
+    FmLevelSums ([n_ext][R]); gather(bytes) -> bytes of all ranks (None for one rank).
+    adapt_from = n: start with n extended levels and grow by the bias test."""
     L = _lib.load()
     n_ext = len(cost)
     costs = (C.c_double * n_ext)(*[float(c) for c in cost])
-    opts = _lib.FmCoreOpts(n_ext, costs, eps, int(bool(qmc)), n_shifts, n_pilot, max_rounds, rank, world)
+    opts = _lib.FmCoreOpts(n_ext, costs, eps, int(bool(qmc)), n_shifts, n_pilot, max_rounds, rank, world,
+                           level0, int(adapt_from is not None), adapt_from or 0, alpha)
 
     def enq(user, e, first, n, shift):
         try:
@@ -109,8 +111,10 @@ def estimate_core(cost, eps, enqueue, read, gather=None, qmc=False, n_shifts=0, 
     st = L.mlmc_estimate_core(C.byref(opts), cb_e, cb_r, cb_g, None, C.byref(res), err, 512)
     if st != 0:
         raise FmError(st, err.value.decode())
-    return dict(estimate=res.estimate, var_estimator=res.var_estimator, means=np.array(res.mean[:n_ext]),
-                V=np.array(res.var[:n_ext]), N=np.array(res.N[:n_ext]), rounds=res.rounds)
+    E = res.n_ext_used
+    return dict(estimate=res.estimate, var_estimator=res.var_estimator, means=np.array(res.mean[:E]),
+                V=np.array(res.var[:E]), N=np.array(res.N[:E]), rounds=res.rounds, n_ext_used=E,
+                bias=res.bias, alpha_used=res.alpha_used, bias_ok=bool(res.bias_ok))
 
 
 class Context:
@@ -346,14 +350,17 @@ class Context:
         self._check(self._L.surrogate_enable(self._h, int(bool(on))))
 
     def mlmc_estimate(self, eps, qmc=False, n_pilot=1000, max_rounds=100, surrogate=False,
-                      surrogate_cost=0.01, group=None, shard=None, batched=False):
+                      surrogate_cost=0.01, group=None, shard=None, batched=False, L_start=None, alpha=0.0):
         """With a torch.distributed `group` of several ranks (one context per rank, all
         with the same seed), or shard = (rank, world, gather) with gather(bytes) ->
         bytes of all ranks, every request is shared among the ranks and the level
-        sums are exchanged once per round; all ranks return the same estimate."""
+        sums are exchanged once per round; all ranks return the same estimate.
+        L_start: grow the finest level from L_start by the bias test (alpha > 0 fixes
+        the weak rate, else it is fitted)."""
         torch.cuda.synchronize()
         opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds, int(bool(surrogate)),
-                                   surrogate_cost, int(bool(batched)))
+                                   surrogate_cost, int(bool(batched)), int(L_start is not None),
+                                   L_start or 0, alpha)
         res = _lib.FmResult()
         if group is not None:
             import torch.distributed as dist
@@ -365,8 +372,9 @@ class Context:
             cb = _allgather_cb(gather)
             self._check(self._L.mlmc_estimate_sharded(self._h, C.byref(opts), rank, world, cb, None,
                                                       C.byref(res)))
-        L = len(self.levels)
-        return dict(estimate=res.estimate, var_estimator=res.var_estimator,
+        L = res.L + 1
+        return dict(estimate=res.estimate, var_estimator=res.var_estimator, L=res.L, bias_ok=bool(res.bias_ok),
+                    alpha_used=res.alpha_used,
                     means=np.array(res.mean[:L]), V=np.array(res.var[:L]),
                     N=np.array(res.N[:L]), alpha=res.alpha, beta=res.beta, bias=res.bias,
                     rounds=res.rounds, seconds=res.seconds, mean_s=res.mean_s, var_s=res.var_s,

@@ -54,7 +54,7 @@ class FmLevelSums(C.Structure):
 class FmEstimateOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("qmc", C.c_int32), ("n_pilot", C.c_int64),
                 ("max_rounds", C.c_int32), ("surrogate", C.c_int32), ("surrogate_cost", C.c_double),
-                ("batched", C.c_int32)]
+                ("batched", C.c_int32), ("adapt_L", C.c_int32), ("L_start", C.c_int32), ("alpha", C.c_double)]
 
 
 class FmKernelStat(C.Structure):
@@ -80,19 +80,22 @@ class FmResult(C.Structure):
                 ("bias", C.c_double), ("rounds", C.c_int32), ("seconds", C.c_double),
                 ("mean_s", C.c_double), ("var_s", C.c_double), ("N_s", C.c_int64),
                 ("level_seconds", C.c_double * FM_MAX_LEVELS), ("seconds_s", C.c_double),
-                ("batched_seconds", C.c_double)]
+                ("batched_seconds", C.c_double), ("L", C.c_int32), ("bias_ok", C.c_int32),
+                ("alpha_used", C.c_double)]
 
 
 class FmCoreOpts(C.Structure):
     _fields_ = [("n_ext", C.c_int32), ("cost", C.POINTER(C.c_double)), ("eps", C.c_double),
                 ("qmc", C.c_int32), ("n_shifts", C.c_int32), ("n_pilot", C.c_int64),
-                ("max_rounds", C.c_int32), ("rank", C.c_int32), ("world", C.c_int32)]
+                ("max_rounds", C.c_int32), ("rank", C.c_int32), ("world", C.c_int32),
+                ("level0", C.c_int32), ("adapt", C.c_int32), ("n_ext_start", C.c_int32), ("alpha", C.c_double)]
 
 
 class FmCoreResult(C.Structure):
     _fields_ = [("estimate", C.c_double), ("var_estimator", C.c_double),
                 ("mean", C.c_double * (FM_MAX_LEVELS + 1)), ("var", C.c_double * (FM_MAX_LEVELS + 1)),
-                ("N", C.c_int64 * (FM_MAX_LEVELS + 1)), ("rounds", C.c_int32)]
+                ("N", C.c_int64 * (FM_MAX_LEVELS + 1)), ("rounds", C.c_int32), ("n_ext_used", C.c_int32),
+                ("bias_ok", C.c_int32), ("bias", C.c_double), ("alpha_used", C.c_double)]
 
 
 class FmTuneEntry(C.Structure):

@@ -1,5 +1,6 @@
 // The MLMC / MLQMC sample-size controller as a host routine over callbacks
-// (Sec. 2.3, Sec. 2.4, Algorithms 1-3 at a fixed finest level).
+// (Sec. 2.3, Sec. 2.4, Algorithms 1-3: the finest level fixed, or grown
+// until the Richardson bias estimate passes).
 //
 // The controller owns no device state: the caller's `enqueue` adds samples
 // of one (extended) level to its running sums, `read` returns them, and,
@@ -78,25 +79,32 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
         set_err(err, errlen, "mlmc_estimate_core: null argument");
         return FM_EINVAL;
     }
-    const int E = o->n_ext;
+    const int Emax = o->n_ext;
     const int R = o->qmc ? o->n_shifts : 1;
     const int world = o->world > 0 ? o->world : 1;
-    if (E < 1 || E > FM_MAX_LEVELS + 1 || !o->cost || !(o->eps > 0) || o->n_pilot < 2 ||
-        (o->qmc && (R < 2 || R > 64)) || o->rank < 0 || o->rank >= world || (world > 1 && !allgather)) {
+    const int lv0 = o->level0;
+    if (Emax < 1 || Emax > FM_MAX_LEVELS + 1 || !o->cost || !(o->eps > 0) || o->n_pilot < 2 ||
+        (o->qmc && (R < 2 || R > 64)) || o->rank < 0 || o->rank >= world || (world > 1 && !allgather) ||
+        lv0 < 0 || lv0 >= Emax) {
         set_err(err, errlen, "mlmc_estimate_core: bad options (levels, cost, eps, n_pilot >= 2, shifts, rank)");
         return FM_EINVAL;
     }
-    for (int e = 0; e < E; ++e)
+    if (o->adapt && (o->n_ext_start < lv0 + 2 || o->n_ext_start > Emax)) {
+        set_err(err, errlen, "mlmc_estimate_core: adapt needs level0 + 2 <= n_ext_start <= n_ext");
+        return FM_EINVAL;
+    }
+    for (int e = 0; e < Emax; ++e)
         if (!(o->cost[e] > 0)) {
             set_err(err, errlen, "mlmc_estimate_core: costs must be positive");
             return FM_EINVAL;
         }
     const int max_rounds = o->max_rounds > 0 ? o->max_rounds : 100;
-    const size_t cells = (size_t)E * R;
+    const size_t cells = (size_t)Emax * R;
     std::vector<fm_level_sums> local(cells), all(cells * world), tot(cells);
     std::memset(out, 0, sizeof(*out));
     int64_t N[FM_MAX_LEVELS + 1] = {};
     double mean[FM_MAX_LEVELS + 1] = {}, var[FM_MAX_LEVELS + 1] = {};
+    int E = o->adapt ? o->n_ext_start : Emax;   // extended levels in use
 
     // this rank's share of samples first .. first+n-1 of extended level e, every shift
     auto draw = [&](int e, int64_t first, int64_t n) -> fm_status {
@@ -109,7 +117,7 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
         }
         return FM_OK;
     };
-    // every rank's sums, folded in rank order, then the level statistics
+    // every rank's sums, folded in rank order, then the statistics of the levels in use
     auto refresh = [&]() -> fm_status {
         fm_status st = read(user, local.data());
         if (st != FM_OK) return st;
@@ -152,12 +160,44 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
         }
         return FM_OK;
     };
+    // Richardson estimate of the weak error (Algorithm 1): |mean(Y_L)| /
+    // (2^alpha - 1), alpha the caller's or the least-squares slope of
+    // -log2|mean(Y_l)| over l = 1 .. L, floored at 1/2 so that a noisy fit of
+    // a few levels cannot drive the denominator to 0.
+    auto bias_estimate = [&](double* alpha_used) -> double {
+        const int L = E - 1 - lv0;
+        if (L < 1) {
+            *alpha_used = NAN;
+            return NAN;
+        }
+        double a = o->alpha;
+        if (!(a > 0)) {
+            double sx = 0, sy = 0, sxx = 0, sxy = 0;
+            bool ok = L >= 2;
+            for (int l = 1; l <= L && ok; ++l) {
+                const double v = std::fabs(mean[lv0 + l]);
+                if (!(v > 0)) ok = false;
+                const double y = std::log2(v);
+                sx += l;
+                sy += y;
+                sxx += (double)l * l;
+                sxy += l * y;
+            }
+            const double n = L;
+            const double fit = ok ? -(n * sxy - sx * sy) / (n * sxx - sx * sx) : NAN;
+            a = std::isfinite(fit) ? std::max(fit, 0.5) : 0.5;
+        }
+        *alpha_used = a;
+        return std::fabs(mean[E - 1]) / (std::pow(2.0, a) - 1.0);
+    };
+    const double bias_bar = o->eps / std::sqrt(2.0);
 
     int rounds = 0;
     if (!o->qmc) {
-        // Algorithm 1 / 3 at fixed L: evaluate dN, update V_l and the optimal
-        // N_l = ceil((2/eps^2) sqrt(V_l/C_l) sum_k sqrt(V_k C_k)), repeat.
-        int64_t dN[FM_MAX_LEVELS + 1];
+        // Algorithms 1 / 3: evaluate dN, update V_l and the optimal
+        // N_l = ceil((2/eps^2) sqrt(V_l/C_l) sum_k sqrt(V_k C_k)), repeat; when
+        // no level needs more samples, the bias test (adapt) adds a level.
+        int64_t dN[FM_MAX_LEVELS + 1] = {};
         for (int e = 0; e < E; ++e) dN[e] = o->n_pilot;
         while (rounds < max_rounds) {
             bool any = false;
@@ -174,6 +214,7 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
             if (st != FM_OK) return st;
             double tot_vc = 0.0;
             for (int e = 0; e < E; ++e) tot_vc += std::sqrt(var[e] * o->cost[e]);
+            bool more = false;
             for (int e = 0; e < E; ++e) {
                 const double opt = std::ceil(2.0 / (o->eps * o->eps) * std::sqrt(var[e] / o->cost[e]) * tot_vc);
                 if (!std::isfinite(opt) || opt > kMaxSamplesPerLevel) {
@@ -183,13 +224,20 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
                     return FM_ENOTCONV;
                 }
                 dN[e] = std::max<int64_t>(0, (int64_t)opt - N[e]);
+                more = more || dN[e] > 0;
             }
+            if (more || !o->adapt) continue;
+            double a;
+            if (bias_estimate(&a) < bias_bar || E == Emax) break;
+            dN[E] = o->n_pilot;
+            ++E;
         }
         double v = 0.0;
         for (int e = 0; e < E; ++e) v += var[e] / (double)N[e];
         out->var_estimator = v;
     } else {
-        // Algorithm 2 at fixed L: pilot, then double N_l at argmax V[Y_l]/(N_l C_l)
+        // Algorithm 2: pilot, then double N_l at argmax V[Y_l]/(N_l C_l) while
+        // the variance is too large; then the bias test (adapt) adds a level.
         for (int e = 0; e < E; ++e) {
             const fm_status st = draw(e, 0, o->n_pilot);
             if (st != FM_OK) return st;
@@ -200,23 +248,31 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
         while (rounds < max_rounds) {
             double tot_v = 0.0;
             for (int e = 0; e < E; ++e) tot_v += var[e];
-            if (tot_v <= o->eps * o->eps / 2) break;
-            int best = 0;
-            double bv = -1.0;
-            for (int e = 0; e < E; ++e) {
-                const double v = var[e] / ((double)N[e] * o->cost[e]);
-                if (v > bv) {
-                    bv = v;
-                    best = e;
+            if (tot_v <= o->eps * o->eps / 2) {
+                double a;
+                if (!o->adapt || bias_estimate(&a) < bias_bar || E == Emax) break;
+                st = draw(E, 0, o->n_pilot);
+                if (st != FM_OK) return st;
+                N[E] = o->n_pilot;
+                ++E;
+            } else {
+                int best = 0;
+                double bv = -1.0;
+                for (int e = 0; e < E; ++e) {
+                    const double v = var[e] / ((double)N[e] * o->cost[e]);
+                    if (v > bv) {
+                        bv = v;
+                        best = e;
+                    }
                 }
+                if (N[best] > ((int64_t)1 << 31)) {
+                    set_err(err, errlen, "mlmc_estimate: QMC point budget exhausted");
+                    return FM_ENOTCONV;
+                }
+                st = draw(best, N[best], N[best]);
+                if (st != FM_OK) return st;
+                N[best] *= 2;
             }
-            if (N[best] > ((int64_t)1 << 31)) {
-                set_err(err, errlen, "mlmc_estimate: QMC point budget exhausted");
-                return FM_ENOTCONV;
-            }
-            st = draw(best, N[best], N[best]);
-            if (st != FM_OK) return st;
-            N[best] *= 2;
             ++rounds;
             st = refresh();
             if (st != FM_OK) return st;
@@ -234,5 +290,8 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
     }
     out->estimate = est;
     out->rounds = rounds;
+    out->n_ext_used = E;
+    out->bias = bias_estimate(&out->alpha_used);
+    out->bias_ok = out->bias < bias_bar ? 1 : 0;
     return FM_OK;
 }

@@ -369,6 +369,8 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
                  "mlmc_estimate: bad rank / world, or no allgather for several ranks");
     FM_CHECK_ARG(ctx, !opts->surrogate || (ctx->mlp && opts->surrogate_cost > 0),
                  "mlmc_estimate: the surrogate level needs a trained network and surrogate_cost > 0");
+    FM_CHECK_ARG(ctx, !opts->adapt_L || (opts->L_start >= 1 && opts->L_start < ctx->cfg.n_levels),
+                 "mlmc_estimate: adapt_L needs 1 <= L_start < n_levels");
     const auto t0 = std::chrono::steady_clock::now();
     // Extended levels e = 0 .. L: with the surrogate, e = 0 is the S level
     // and e = l + 1 MLMC level l; without it e = l.
@@ -409,6 +411,10 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
     co.max_rounds = opts->max_rounds;
     co.rank = rank;
     co.world = world;
+    co.level0 = off;
+    co.adapt = opts->adapt_L ? 1 : 0;
+    co.n_ext_start = opts->adapt_L ? opts->L_start + 1 + off : L + 1;
+    co.alpha = opts->alpha;
     fm_core_result cr{};
     char msg[512] = {0};
     const fm_status st = mlmc_estimate_core(&co, gpu_enqueue, gpu_read, allgather, &g, &cr, msg, sizeof(msg));
@@ -416,9 +422,11 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
         if (msg[0]) set_error(ctx, msg);
         return st;
     }
+    // the finest level the controller ended on
+    const int Lu = cr.n_ext_used - 1 - off;
     out->estimate = cr.estimate;
     out->var_estimator = cr.var_estimator;
-    for (int l = 0; l <= Lr; ++l) {
+    for (int l = 0; l <= Lu; ++l) {
         out->mean[l] = cr.mean[l + off];
         out->var[l] = cr.var[l + off];
         out->N[l] = cr.N[l + off];
@@ -431,10 +439,12 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
         out->N_s = cr.N[0];
         out->seconds_s = g.lsec[0];
     }
-    out->alpha = fit_rate(out->mean, Lr);
-    out->beta = fit_rate(out->var, Lr);
-    out->bias = (std::isfinite(out->alpha) && out->alpha > 0)
-                    ? std::fabs(out->mean[Lr]) / (std::pow(2.0, out->alpha) - 1.0) : NAN;
+    out->alpha = fit_rate(out->mean, Lu);
+    out->beta = fit_rate(out->var, Lu);
+    out->bias = cr.bias;
+    out->alpha_used = cr.alpha_used;
+    out->bias_ok = cr.bias_ok;
+    out->L = Lu;
     out->rounds = cr.rounds;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return FM_OK;
