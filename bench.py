@@ -235,6 +235,11 @@ def make_ctx(fm, wl, rank, form):
 
 # DRAM read + write of one FP32 colour launch per cell, measured by ncu
 COLOUR_DRAM_BYTES_PER_CELL_F32 = (1.341171e9 + 0.251231e9) / (64 << 20)
+# DRAM read + write of one FP32 strip call (two sweeps) per cell, measured by
+# ncu on 64 Mi cells of 256 x 256 (profiles/rbgs_strip_synthetic_256.md),
+# against its 24 algorithmic bytes per cell
+STRIP_DRAM_BYTES_PER_CELL_F32 = 1.72e9 / (64 << 20)
+STRIP_ALG_BYTES_PER_CELL_F32 = 24.0
 
 # randomized QMC (Algorithm 2): 32 points per shift and level to start, 16 digital shifts
 QMC_PILOT = 32
@@ -525,6 +530,20 @@ def run_native(args, wl, eps):
         roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is latency bound"
     roof["launches"] = st["launches"]
     roof["avg_launch_ms"] = per_launch_ms
+    # the HBM-bound kernels of the level-wise solves, beside the dominant one:
+    # achieved = algorithmic bytes / event time over the timed steps
+    hbm_kernels = {}
+    for k in ("rbgs_strip", "residual_restrict", "rbgs_smoother"):
+        if k not in prof or prof[k]["ms"] <= 0:
+            continue
+        v = prof[k]
+        a = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        e = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s", "frac": round(a / hbm, 4),
+             "launches": v["launches"], "avg_launch_ms": round(v["ms"] / v["launches"], 4), "traffic": None}
+        if k == "rbgs_strip" and FORMS[args.form]["precision"] == 1:
+            e["traffic"] = v["bytes"] / v["launches"] * STRIP_DRAM_BYTES_PER_CELL_F32 / STRIP_ALG_BYTES_PER_CELL_F32
+            e["traffic_source"] = "ncu dram bytes per cell (64 Mi-cell capture of the plain strip) x cells per launch"
+        hbm_kernels[k] = e
     families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                     "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
                     "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3)} for k, v in prof.items()}
@@ -560,6 +579,7 @@ def run_native(args, wl, eps):
         "uneven_batch": uneven,
         "fmg_vs_standard_mlmc": standard,
         "roofline": roof,
+        "hbm_kernels": hbm_kernels,
         "kernel_families": families,
         "gpu_launches": total_launches,
         "e2e": {"value": float(np.mean(e2e_times)) if e2e_times else None, "unit": "s",

@@ -264,7 +264,8 @@ fm_status fmg_uneven_stats(const fm_ctx* ctx, int64_t* instantiations, int64_t* 
 /* One tuned grid: the smoother launch shape chosen for it. */
 typedef struct {
     int32_t n;            /* grid n x n */
-    int32_t tile;         /* tile interior staged in shared memory (0: one launch per colour and sweep) */
+    int32_t tile;         /* tile interior staged in shared memory (0: one launch per colour and sweep;
+                             -1: column strips) */
     int32_t threads;      /* 0: register-blocked tile kernel (only p in shared memory); else threads
                              per CTA of the tile kernel that stages every operand in shared memory */
     double ms_best;       /* one smoothing call (nsweeps sweeps) with the chosen shape, milliseconds */
@@ -272,8 +273,8 @@ typedef struct {
     int64_t samples;      /* samples of the timing batch (about 64 Mi cells) */
 } fm_tune_entry;
 
-/* Times the red-black smoother's launch shapes (one launch per colour, or
- * tiles of 8, 16, 32, 64 cells with a 2 nsweeps halo, either register-blocked
+/* Times the red-black smoother's launch shapes (one launch per colour,
+ * column strips, or tiles of 8, 16, 32, 64 cells with a 2 nsweeps halo, either register-blocked
  * with only the iterate in shared memory or with every operand staged there
  * at 128 or 256 threads) for the grids n_min, 2 n_min, ..., <= n_max on a
  * synthetic batch of about 64 Mi cells per grid, and keeps the fastest in
@@ -283,6 +284,16 @@ typedef struct {
  * to max_entries rows. */
 fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps, int32_t n_min, int32_t n_max,
                       fm_tune_entry* entries, int32_t max_entries, int32_t* n_entries);
+
+/* Sets the smoother launch shape of grid n (a power of two) for one
+ * precision, as fm_autotune would set it: tile = 0 one launch per colour
+ * and sweep; -1 column strips (one warp per 64-column strip marching up the
+ * rows, 1 or 2 sweeps); 8, 16, 32 or 64 tiles with threads = 0
+ * (register-blocked) or 128 / 256 (staged in shared memory); tile = -2
+ * removes the entry so the built-in default applies.  A shape that cannot
+ * run a solve's sweeps (sweep counts, shared memory) falls back to colour
+ * launches; every shape gives the same results.  FM_EINVAL otherwise. */
+fm_status fm_set_smoother_shape(fm_ctx* ctx, int32_t precision, int32_t n, int32_t tile, int32_t threads);
 
 /* ---------------------------------------------------------------- MLMC */
 

@@ -269,6 +269,13 @@ class Context:
         self._check(self._L.fm_autotune(self._h, precision, nsweeps, n_min, n_max, out, 16, C.byref(cnt)))
         return [{f: getattr(e, f) for f, _ in _lib.FmTuneEntry._fields_} for e in out[:cnt.value]]
 
+    def set_smoother_shape(self, n, tile, threads=0, precision=None):
+        """Smoother launch shape of grid n (fm_set_smoother_shape): tile 0 colour launches,
+        -1 column strips, 8..64 tiles (threads 0 register-blocked, 128 / 256 staged),
+        -2 back to the built-in default."""
+        precision = self.cfg.precision if precision is None else precision
+        self._check(self._L.fm_set_smoother_shape(self._h, precision, n, tile, threads))
+
     # ----------------------------------------------------------- MLMC
     @staticmethod
     def new_sums(count=1):

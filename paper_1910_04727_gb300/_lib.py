@@ -26,7 +26,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
-           "fmg_uneven_stats"]
+           "fmg_uneven_stats", "fm_set_smoother_shape"]
 
 
 class FmConfig(C.Structure):
@@ -155,6 +155,7 @@ def load(path=None):
         "fm_autotune": (I32, [P, I32, I32, I32, I32, P, I32, C.POINTER(I32)]),
         "fmg_solve_uneven": (I32, [P, I32, P, C.POINTER(FmSolveParams), P]),
         "fmg_uneven_stats": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+        "fm_set_smoother_shape": (I32, [P, I32, I32, I32, I32]),
         "fm_shard_range": (None, [U64, U64, I32, I32, C.POINTER(U64), C.POINTER(U64)]),
         "mlmc_estimate_core": (I32, [C.POINTER(FmCoreOpts), ENQUEUE_FN, READ_FN, ALLGATHER_FN, P,
                                      C.POINTER(FmCoreResult), C.c_char_p, C.c_size_t]),

@@ -89,7 +89,8 @@ void set_error(const fm_ctx* ctx, const std::string& msg);
 enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
-    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamSmootherTile, kFamilyCount
+    kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamSmootherTile,
+    kFamSmootherStrip, kFamilyCount
 };
 
 struct ProfRecord {
@@ -120,7 +121,7 @@ struct Arena {
 // Smoother launch shape per (precision, grid): chosen by fm_autotune.
 struct TuneTable {
     int32_t n[2][16] = {};        // grid the entry was tuned for (0: none)
-    int32_t tile[2][16] = {};     // tile interior (0: one launch per colour)
+    int32_t tile[2][16] = {};     // tile interior (0: one launch per colour, -1: column strips)
     int32_t threads[2][16] = {};
 };
 

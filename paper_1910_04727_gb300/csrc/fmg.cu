@@ -136,14 +136,19 @@ __device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U g
 
 // (P u_c) at fine cell (i, j): bilinear cell-centred (9, 3, 3, 1) / 16 with
 // the ghosts above.  One expression for every kernel that prolongs.
+// The weights on the four coarse values: own cell (I, J), its x neighbour
+// Ix, its y neighbour Jy, and the diagonal one.
+template <typename U>
+__device__ __forceinline__ U prolong_vals(U own, U nx, U ny, U nxy) {
+    return (U(9) * own + U(3) * nx + U(3) * ny + U(1) * nxy) / U(16);
+}
 template <typename U>
 __device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, U gW, U gE) {
     const int I = i >> 1, J = j >> 1;
     const int Ix = (i & 1) ? I + 1 : I - 1;
     const int Jy = (j & 1) ? J + 1 : J - 1;
-    return (U(9) * coarse_ghost(nc, u, I, J, gW, gE) + U(3) * coarse_ghost(nc, u, Ix, J, gW, gE) +
-            U(3) * coarse_ghost(nc, u, I, Jy, gW, gE) + U(1) * coarse_ghost(nc, u, Ix, Jy, gW, gE)) /
-           U(16);
+    return prolong_vals(coarse_ghost(nc, u, I, J, gW, gE), coarse_ghost(nc, u, Ix, J, gW, gE),
+                        coarse_ghost(nc, u, I, Jy, gW, gE), coarse_ghost(nc, u, Ix, Jy, gW, gE));
 }
 
 // nsweeps red-black sweeps (colour 0 then 1) on tiles of TI x TI cells of
@@ -320,14 +325,302 @@ __global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, si
     }
 }
 
+// Asynchronous global -> shared copies of B = 4, 8 or 16 bytes (cp.async, both
+// addresses B-aligned), commit groups, and the wait until at most N groups
+// of this thread are still in flight.
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    static_assert(B == 4 || B == 8 || B == 16, "cp.async of 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem), "n"(B)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A product the compiler may not fuse into a neighbouring add.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Column-strip wavefront smoother: nsweeps red-black sweeps (HS = 2 nsweeps
+// half-sweeps) by one warp over a window of 64 columns of one sample,
+// marching up the rows.  Lane l owns columns 2l, 2l+1 of the window, so in
+// every row it holds one cell of each colour; W / E neighbours in other
+// lanes come by warp shuffles, N / S neighbours from the rows the lane keeps
+// in registers.  At step y the warp takes in row y and runs half-sweep k on
+// row y - k for k = 1 .. HS: row y - k + 1 has just had half-sweep k - 1 and
+// row y - k - 1 had it one step earlier, so every update sees the values the
+// sweep order prescribes, and row y - HS is final and is written out.  The
+// HS + 2 rows in flight stay in registers (a ring whose slots are fixed by
+// the unrolled step index); two rows are loaded ahead.  A cell with an
+// in-domain neighbour outside the window (first or last column, first or
+// last row of a segment) is not updated, so after HS half-sweeps the window
+// minus HS columns and rows on each side is exact.  Every update is the
+// colour kernel's in the same order with the reciprocal of D, so the sweeps
+// are bit-identical to the other shapes (a missing face adds an exact zero).
+// Operands cross HBM once per call, as float2 / double2 rows of 64 columns.
+// p_in -> p_out as for the tiles; with ec the iterate is p_in + P ec: the
+// coarse row a fine row needs comes through the same ring (each lane's
+// coarse column, plus the columns left and right of the window), and the
+// three coarse rows in use stay in registers, so the correction adds no
+// dependent loads.
+//
+// With FUSE (pre-smoothing of a V-cycle) the warp also forms the residual
+// b - A p of each final row once the row above it is final, and the
+// restriction to the coarse grid: the lane's column pair is one coarse
+// column, so it sums its four fine residuals over two rows in
+// k_residual_restrict's order and writes b_c (and p_c = 0).  The residual
+// needs exact neighbours, so the strip and segment halos grow by two.
+// Strips overlap by 2 XH columns and row segments by 2 VH rows; one unit
+// (sample, row segment, strip) per warp, strip index fastest.
+constexpr int kStripWarps = 4;
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+// Rows in flight per warp of the strip shapes (shared-memory ring of 40 KB per CTA).
+template <typename T>
+__host__ __device__ constexpr int strip_depth() { return sizeof(T) == 4 ? 8 : 4; }
+
+// Window offset (columns left of the output columns) and halo rows of the strip shapes.
+__host__ __device__ constexpr int strip_xh(int HS, bool fuse) { return fuse ? HS + 2 : HS; }
+__host__ __device__ constexpr int strip_ow(int HS, bool fuse) { return 64 - 2 * strip_xh(HS, fuse); }
+
+template <typename T, int HS, bool FUSE>
+__global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rbgs_strip(int n, size_t S, int strips, int seg, int segs,
+                                                                 const T* __restrict__ b, const T* __restrict__ Te,
+                                                                 const T* __restrict__ Tn, const T* __restrict__ D,
+                                                                 const T* __restrict__ p_in, T* __restrict__ p_out,
+                                                                 const int32_t* __restrict__ active,
+                                                                 const T* __restrict__ ec, T* __restrict__ bc,
+                                                                 T* __restrict__ pc, const int32_t* __restrict__ order) {
+    using V2 = typename Pair<T>::type;
+    constexpr int R = HS + 2;                       // rows in registers: y - HS - 1 .. y
+    constexpr int XH = strip_xh(HS, FUSE), VH = XH;  // halo columns and rows (even)
+    constexpr int OW = strip_ow(HS, FUSE);          // output columns of a strip
+    constexpr int DEPTH = strip_depth<T>();         // rows in flight in the shared-memory ring
+    static_assert(HS % 2 == 0 && XH % 2 == 0, "even half-sweep count and halos");
+    // Each lane copies its own float2 / double2 of the five operands of a row
+    // into its own slot of the warp's ring (cp.async, one commit group per
+    // row) and reads back only what it copied, so no lane waits for another.
+    __shared__ V2 ring[kStripWarps][DEPTH][5][32];
+    __shared__ T cring[kStripWarps][DEPTH][34];   // with ec: [0] left of lane 0, [1 + l] lane l, [33] right of lane 31
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const size_t unit = (size_t)blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+    if (unit >= S * (size_t)segs * strips) return;   // S: the samples enumerated (listed by order, if given)
+    const int sx = (int)(unit % strips);
+    const size_t rest = unit / strips;
+    const int sy = (int)(rest % segs);
+    const size_t s = order ? (size_t)order[rest / segs] : rest / segs;
+    if (inactive(active, s)) return;
+    const int ox = sx * OW, oy = sy * seg, oye = min(oy + seg, n);
+    const int gx = ox - XH + 2 * lane;   // even, so (n even) both cells are in the domain or neither
+    const bool in_x = gx >= 0 && gx < n;
+    const int ys = max(oy - VH, 0), ye = min(oye + VH, n);   // rows taken in; ys even
+    const bool updL = in_x && !(gx > 0 && lane == 0);
+    const bool updR = in_x && !(gx + 1 < n - 1 && lane == 31);
+    const bool out_x = in_x && gx >= ox && gx < ox + OW;
+    const size_t base = s * (size_t)n * n;
+    const T* ecs = ec ? ec + s * (size_t)(n / 2) * (n / 2) : nullptr;
+    const V2 zero2{T(0), T(0)}, one2{T(1), T(1)};
+
+    V2(*my)[5][32] = ring[threadIdx.x >> 5];
+    T(*myc)[34] = cring[threadIdx.x >> 5];
+    const int nc = n / 2, I = gx >> 1;   // the lane's coarse column
+    // row y into ring slot (y - ys) % DEPTH, with ec also coarse row
+    // min((y + 1) / 2, nc - 1), the highest one fine row y needs; every step
+    // commits one group
+    auto fetch = [&](int y) {
+        if (y < ye) {
+            const int slot = (y - ys) % DEPTH;
+            if (in_x) {
+                const size_t g = base + (size_t)y * n + gx;
+                V2* v = &my[slot][0][lane];
+                constexpr int B = (int)sizeof(V2);
+                cp_async<B>(v + 0 * 32, p_in + g);
+                cp_async<B>(v + 1 * 32, b + g);
+                cp_async<B>(v + 2 * 32, D + g);
+                cp_async<B>(v + 3 * 32, Te + g);
+                cp_async<B>(v + 4 * 32, Tn + g);
+            }
+            if (ecs) {
+                const T* crow = ecs + (size_t)min((y + 1) >> 1, nc - 1) * nc;
+                if (in_x) cp_async<(int)sizeof(T)>(&myc[slot][1 + lane], crow + I);
+                if (lane == 0 && I - 1 >= 0 && I - 1 < nc) cp_async<(int)sizeof(T)>(&myc[slot][0], crow + I - 1);
+                if (lane == 31 && I + 1 >= 0 && I + 1 < nc) cp_async<(int)sizeof(T)>(&myc[slot][33], crow + I + 1);
+            }
+        }
+        cp_async_commit();
+    };
+    // with ec: coarse values (own column, left and right neighbours with the
+    // Dirichlet ghosts of coarse_ghost) of the coarse rows taken in at the
+    // last three steps
+    T cs0[3] = {T(0), T(0), T(0)}, cs1[3] = {T(0), T(0), T(0)}, cs2[3] = {T(0), T(0), T(0)};
+    auto coarse3 = [&](T own, T left, T right, T (&dst)[3]) {
+        dst[0] = own;
+        dst[1] = I == 0 ? T(2) * T(0) - own : left;
+        dst[2] = I == nc - 1 ? T(2) * T(0) - own : right;
+    };
+    if (ecs && in_x && ys > 0) {   // coarse row ys / 2 - 1, the lower y neighbour of fine row ys
+        const T* crow = ecs + (size_t)(ys / 2 - 1) * nc;
+        coarse3(crow[I], I > 0 ? crow[I - 1] : T(0), I + 1 < nc ? crow[I + 1] : T(0), cs1);
+    }
+    T p[R][2], bb[R][2], rr[R][2], ee[R][2], nf[R][2], wl[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        p[c][0] = p[c][1] = bb[c][0] = bb[c][1] = ee[c][0] = ee[c][1] = nf[c][0] = nf[c][1] = wl[c] = T(0);
+        rr[c][0] = rr[c][1] = T(0);
+    }
+    // FUSE: the row leaving the ring (p and north faces) and the partial coarse sum
+    T pq[2] = {T(0), T(0)}, nq[2] = {T(0), T(0)}, rsum = T(0);
+    for (int q = 0; q < DEPTH; ++q) fetch(ys + q);
+    const int steps = ye - ys + HS + (FUSE ? 1 : 0);
+    for (int y0 = ys; y0 < ys + steps; y0 += R) {
+#pragma unroll
+        for (int J = 0; J < R; ++J) {
+            const int y = y0 + J;
+            if (FUSE) {   // keep row y - R (the S neighbour of the residual row y - HS - 1)
+                pq[0] = p[J][0];
+                pq[1] = p[J][1];
+                nq[0] = nf[J][0];
+                nq[1] = nf[J][1];
+            }
+            {   // take in row y (register slot J), then start the copy of row y + DEPTH
+                cp_async_wait<DEPTH - 1>();   // this lane's copies of row y have landed
+                V2 fp = zero2, fb = zero2, fd = one2, fe = zero2, fn = zero2;
+                if (in_x && y < ye) {
+                    const V2* slot = &my[(y - ys) % DEPTH][0][lane];
+                    fp = slot[0 * 32];
+                    fb = slot[1 * 32];
+                    fd = slot[2 * 32];
+                    fe = slot[3 * 32];
+                    fn = slot[4 * 32];
+                }
+                T a0 = fp.x, a1 = fp.y;
+                if (ecs) {   // the coarse-grid correction p + (P e) as k_prolong forms it
+                    __syncwarp();   // the neighbouring lanes' coarse copies have landed too
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        cs2[q] = cs1[q];
+                        cs1[q] = cs0[q];
+                    }
+                    if (in_x && y < ye) {
+                        const T* cv = myc[(y - ys) % DEPTH];
+                        coarse3(cv[1 + lane], cv[lane], cv[2 + lane], cs0);
+                        // fine row y: coarse row y / 2 and its y neighbour (one row down for
+                        // even y, clamped at 0; one up for odd y, clamped at nc - 1); the
+                        // step index J has the parity of y
+                        const T* uJ = (J & 1) ? cs1 : cs0;
+                        const T* uJy = (J & 1) ? cs0 : (y == 0 ? cs0 : cs2);
+                        a0 = a0 + prolong_vals(uJ[0], uJ[1], uJy[0], uJy[1]);
+                        a1 = a1 + prolong_vals(uJ[0], uJ[2], uJy[0], uJy[2]);
+                    }
+                }
+                p[J][0] = a0;
+                p[J][1] = a1;
+                bb[J][0] = fb.x;
+                bb[J][1] = fb.y;
+                rr[J][0] = T(1) / fd.x;
+                rr[J][1] = T(1) / fd.y;
+                ee[J][0] = fe.x;
+                ee[J][1] = gx + 1 < n - 1 ? fe.y : T(0);
+                nf[J][0] = y < n - 1 ? fn.x : T(0);
+                nf[J][1] = y < n - 1 ? fn.y : T(0);
+                wl[J] = __shfl_up_sync(kAll, ee[J][1], 1);   // W face of the left cell
+                if (ecs) __syncwarp();   // every lane has read the coarse slot before it is refilled
+                fetch(y + DEPTH);
+            }
+#pragma unroll
+            for (int k = 1; k <= HS; ++k) {
+                // half-sweep k (colour (k - 1) & 1) on row r: the left cell
+                // (even column) has that colour iff y is odd
+                const int r = y - k;
+                const int c = (J - k + 4 * R) % R, lo = (J - k - 1 + 4 * R) % R, hi = (J - k + 1 + 4 * R) % R;
+                const bool row_ok = r >= ys && r < ye && (r > ys || ys == 0) && (r < ye - 1 || ye == n);
+                if (J & 1) {
+                    const T pw = __shfl_up_sync(kAll, p[c][1], 1);
+                    T acc = bb[c][0];
+                    acc += wl[c] * pw;
+                    acc += ee[c][0] * p[c][1];
+                    acc += nf[lo][0] * p[lo][0];
+                    acc += nf[c][0] * p[hi][0];
+                    const T v = acc * rr[c][0];
+                    p[c][0] = (row_ok && updL) ? v : p[c][0];
+                } else {
+                    const T pe = __shfl_down_sync(kAll, p[c][0], 1);
+                    T acc = bb[c][1];
+                    acc += ee[c][0] * p[c][0];
+                    acc += ee[c][1] * pe;
+                    acc += nf[lo][1] * p[lo][1];
+                    acc += nf[c][1] * p[hi][1];
+                    const T v = acc * rr[c][1];
+                    p[c][1] = (row_ok && updR) ? v : p[c][1];
+                }
+            }
+            {
+                const int r = y - HS;
+                if (out_x && r >= oy && r < oye) {
+                    const int c = (J - HS + 4 * R) % R;
+                    *reinterpret_cast<V2*>(p_out + base + (size_t)r * n + gx) = V2{p[c][0], p[c][1]};
+                }
+            }
+            if (FUSE) {
+                // residual of row q = y - HS - 1 (rows q - 1, q + 1 final), as residual_at forms it
+                const int q = y - HS - 1;
+                const int c = (J - HS - 1 + 4 * R) % R, hi = (J - HS + 4 * R) % R;
+                const T pw = __shfl_up_sync(kAll, p[c][1], 1);
+                const T pe = __shfl_down_sync(kAll, p[c][0], 1);
+                if (out_x && q >= oy && q < oye) {
+                    const V2 dq = *reinterpret_cast<const V2*>(D + base + (size_t)q * n + gx);
+                    T v0 = mul_rn(dq.x, p[c][0]);
+                    v0 = fma(-wl[c], pw, v0);
+                    v0 = fma(-ee[c][0], p[c][1], v0);
+                    v0 = fma(-nq[0], pq[0], v0);
+                    v0 = fma(-nf[c][0], p[hi][0], v0);
+                    const T r0 = bb[c][0] - v0;
+                    T v1 = mul_rn(dq.y, p[c][1]);
+                    v1 = fma(-ee[c][0], p[c][0], v1);
+                    v1 = fma(-ee[c][1], pe, v1);
+                    v1 = fma(-nq[1], pq[1], v1);
+                    v1 = fma(-nf[c][1], p[hi][1], v1);
+                    const T r1 = bb[c][1] - v1;
+                    if ((J & 1) == 0) {   // q odd: the coarse cell's upper row
+                        const size_t cc = s * (size_t)(n / 2) * (n / 2) + (size_t)(q / 2) * (n / 2) + gx / 2;
+                        bc[cc] = rsum + r0 + r1;
+                        pc[cc] = T(0);
+                    } else {
+                        rsum = r0 + r1;
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// r = b - A p at cell c: D p rounded, then one fused multiply-add per face
+// (W, E, S, N), spelled out so that every kernel forming a residual rounds
+// the same way whatever the compiler would contract.
 template <typename T>
 __device__ __forceinline__ T residual_at(int n, size_t c, int i, int j, const T* b, const T* Te, const T* Tn,
                                          const T* D, const T* p) {
-    T v = D[c] * p[c];
-    if (i > 0) v -= Te[c - 1] * p[c - 1];
-    if (i < n - 1) v -= Te[c] * p[c + 1];
-    if (j > 0) v -= Tn[c - n] * p[c - n];
-    if (j < n - 1) v -= Tn[c] * p[c + n];
+    T v = mul_rn(D[c], p[c]);
+    if (i > 0) v = fma(-Te[c - 1], p[c - 1], v);
+    if (i < n - 1) v = fma(-Te[c], p[c + 1], v);
+    if (j > 0) v = fma(-Tn[c - n], p[c - n], v);
+    if (j < n - 1) v = fma(-Tn[c], p[c + n], v);
     return b[c] - v;
 }
 
@@ -511,11 +804,13 @@ __global__ void k_stage_partials(int n, size_t S, int chunks, const double* __re
                                  const T* __restrict__ D, const T* p, const double* __restrict__ p64,
                                  const double* __restrict__ Te64, const double* __restrict__ Tn64,
                                  const double* __restrict__ D64, T* bT, T* pT, const int32_t* __restrict__ active,
-                                 double* __restrict__ partial) {
+                                 double* __restrict__ partial, const int32_t* __restrict__ order) {
     __shared__ double red[3][32];
-    const size_t s = blockIdx.x / chunks;
+    // S: the samples enumerated (listed by order, if given)
+    if (blockIdx.x / chunks >= S) return;
+    const size_t s = order ? (size_t)order[blockIdx.x / chunks] : blockIdx.x / chunks;
     const int ch = (int)(blockIdx.x % chunks);
-    if (s >= S || inactive(active, s)) return;
+    if (inactive(active, s)) return;
     const size_t base = s * (size_t)n * n;
     const int cells = n * n, per = (cells + chunks - 1) / chunks;
     const int c0 = ch * per, c1 = min(cells, c0 + per);
@@ -572,7 +867,8 @@ __global__ void k_stage_partials(int n, size_t S, int chunks, const double* __re
 // The test itself, one thread per sample: active[s] = ||b - A p|| > tol ||b||
 // and the last pass moved the outflux by more than qtol |Q|; counted in *left.
 __global__ void k_stage_decide(size_t S, int chunks, const double* __restrict__ partial, double tol, double qtol,
-                               double* __restrict__ qprev, int32_t* __restrict__ active, int32_t* __restrict__ left) {
+                               double* __restrict__ qprev, int32_t* __restrict__ active, int32_t* __restrict__ left,
+                               int32_t* __restrict__ order) {
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S || inactive(active, s)) return;
     double a = 0.0, b2 = 0.0, q = 0.0;
@@ -585,17 +881,22 @@ __global__ void k_stage_decide(size_t S, int chunks, const double* __restrict__ 
     const bool done = a <= tol * tol * b2 || (qtol > 0 && fabs(q - qprev[s]) <= qtol * fabs(q));
     qprev[s] = q;
     active[s] = done ? 0 : 1;
-    if (!done) atomicAdd(left, 1);
+    if (!done) {   // count it and list it (in no particular order) for launches over the active samples
+        const int i = atomicAdd(left, 1);
+        if (order) order[i] = (int32_t)s;
+    }
 }
 
 // Mixed form: the FP64 refinement update p64 += e (the FP32 correction).
 template <typename T>
 __global__ void k_ir_update(size_t cells, size_t S, const T* __restrict__ e, double* __restrict__ p64,
-                            const int32_t* __restrict__ active) {
+                            const int32_t* __restrict__ active, const int32_t* __restrict__ order) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= S * cells) return;
-    if (inactive(active, t / cells)) return;
-    p64[t] += (double)e[t];
+    if (t >= S * cells) return;   // S: the samples enumerated (listed by order, if given)
+    const size_t s = order ? (size_t)order[t / cells] : t / cells;
+    if (inactive(active, s)) return;
+    const size_t g = s * cells + t % cells;
+    p64[g] += (double)e[g];
 }
 
 template <typename T>
@@ -635,6 +936,14 @@ struct Hierarchy {
     int32_t* iter;     // residual tests done in the current refined stage (graph loops)
     double* qprev;     // outflux of the previous iteration per sample
     double* partial;   // per-(sample, chunk) partial sums of the residual tests
+    int32_t* order;    // the samples still iterating, as listed by the last residual test
+    // Host-side count of the samples still iterating in a refined stage (the
+    // host loop reads it after every test; S otherwise): the strip smoother
+    // sizes its row segments for it, so that a launch with few active samples
+    // does not march long columns.
+    mutable size_t busy = 0;
+    // launches may enumerate only the listed samples
+    bool listed() const { return order && busy > 0 && busy < S; }
 };
 
 // CTAs per sample of a residual test on grid n (about 8192 cells each).
@@ -651,7 +960,7 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
     total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
-    if (converged) total += 4 * 3 + 8 + (size_t)check_chunks(n_fine) * 24 + 5 * 256;
+    if (converged) total += 4 * 4 + 8 + (size_t)check_chunks(n_fine) * 24 + 6 * 256;
     return total * S + 4096;
 }
 
@@ -727,23 +1036,96 @@ static fm_status carve(fm_ctx* ctx, Arena& ar, Hierarchy<T>& H, int n_fine, int 
     H.iter = converged ? (int32_t*)take(4) : nullptr;
     H.qprev = converged ? (double*)take(S * 8) : nullptr;
     H.partial = converged ? (double*)take(S * (size_t)check_chunks(n_fine) * 24) : nullptr;
+    H.order = converged ? (int32_t*)take(S * 4) : nullptr;
     return FM_OK;
 }
 
 constexpr size_t kMaxSmem = 200 * 1024;   // dynamic shared memory of the tile smoother
 
-// Kernel attributes, set once per process before any launch or capture.
+// Resident warps of the strip smoother on the whole GPU, [FP64, FP32][1 or 2 sweeps][fused residual].
+static int g_strip_warps[2][2][2] = {};
+
+template <typename T, int HS, bool FUSE>
+static void strip_occupancy(int sms) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_rbgs_strip<T, HS, FUSE>, 32 * kStripWarps, 0) !=
+        cudaSuccess)
+        blocks = 1;
+    g_strip_warps[sizeof(T) == 4 ? 1 : 0][HS / 2 - 1][FUSE ? 1 : 0] =
+        std::max(1, blocks) * kStripWarps * std::max(1, sms);
+}
+
+// Kernel attributes and occupancies, set once per process before any launch
+// or capture.
 void fmg_init_attributes() {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_rbgs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         cudaFuncSetAttribute(k_rbgs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        strip_occupancy<float, 2, false>(sms);
+        strip_occupancy<float, 4, false>(sms);
+        strip_occupancy<double, 2, false>(sms);
+        strip_occupancy<double, 4, false>(sms);
+        strip_occupancy<float, 2, true>(sms);
+        strip_occupancy<float, 4, true>(sms);
+        strip_occupancy<double, 2, true>(sms);
+        strip_occupancy<double, 4, true>(sms);
+        cudaGetLastError();
     });
 }
 
-// nsweeps red-black sweeps on one grid of every (active) sample: one tile
-// launch (p, b and the coefficients cross HBM once), or, where the staged
-// tile would not fit in shared memory, one launch per colour and sweep.
+// Rows per segment of the strip smoother: the power-of-two fraction of n (at
+// least 16 rows) that minimises the waves of units over the resident warps
+// times the steps of one unit (segment plus 2 VH halo rows plus the steps
+// that drain the wavefront).
+static int strip_segment(int n, size_t S, int strips, int HS, int VH, int resident) {
+    int best = n;
+    double best_cost = 1e300;
+    for (int seg = n; seg >= 16; seg /= 2) {
+        const size_t units = S * (size_t)strips * ((n + seg - 1) / seg);
+        const double waves = std::ceil((double)units / std::max(1, resident));
+        const double cost = waves * (std::min(seg + (seg < n ? 2 * VH : 0), n) + HS + 1);
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = seg;
+        }
+    }
+    return best;
+}
+
+// One strip-smoother launch (bc, pc: with the fused residual and restriction
+// to the coarse grid).  nsweeps is 1 or 2 and n even (smooth_shape).
+template <typename T, int HS, bool FUSE>
+static void strip_launch(fm_ctx* ctx, int n, size_t S, const T* b, const T* Te, const T* Tn, const T* D,
+                         const T* p_in, T* p_out, const int32_t* active, const T* ec, T* bc, T* pc,
+                         cudaStream_t st, size_t busy, const int32_t* order) {
+    constexpr int OW = strip_ow(HS, FUSE), VH = strip_xh(HS, FUSE);
+    const int strips = (n + OW - 1) / OW;
+    // with the host's count of active samples and their list, enumerate only those
+    const bool listed = order && busy > 0 && busy < S;
+    const size_t sb = listed ? busy : S;
+    const int seg = strip_segment(n, sb, strips, HS, VH, g_strip_warps[sizeof(T) == 4 ? 1 : 0][HS / 2 - 1][FUSE]);
+    const int segs = (n + seg - 1) / seg;
+    const size_t units = sb * (size_t)strips * segs, cells = sb * (size_t)n * n;
+    const unsigned grid = (unsigned)((units + kStripWarps - 1) / kStripWarps);
+    const double bytes = (6.0 + (FUSE ? 0.5 : 0.0)) * sizeof(T) * cells;
+    const double flops = 5.0 * HS * cells + (FUSE ? 12.0 * cells : 0.0);
+    FM_TIMED(ctx, kFamSmootherStrip, st, bytes, flops,
+             k_rbgs_strip<T, HS, FUSE><<<grid, 32 * kStripWarps, 0, st>>>(n, sb, strips, seg, segs, b, Te, Tn, D,
+                                                                         p_in, p_out, active, ec, bc, pc,
+                                                                         listed ? order : nullptr));
+}
+
+// Launch shape code of the column-strip smoother (tile codes are > 0, colour
+// launches 0).  It runs 1 or 2 sweeps on even grids of at least 16 cells.
+constexpr int kShapeStrip = -1;
+static bool strip_fits(int n, int nu1, int nu2) {
+    return n >= 16 && n % 2 == 0 && nu1 >= 1 && nu1 <= 2 && nu2 >= 1 && nu2 <= 2;
+}
+
 static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
     const int TI = std::min(tile, n);
     const int hh = TI >= n ? 0 : 2 * nsweeps;
@@ -759,9 +1141,18 @@ static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
 template <typename T>
 static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int nsweeps, const T* b, const T* Te,
                       const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st,
-                      const T* ec = nullptr) {
+                      const T* ec = nullptr, size_t busy = 0, const int32_t* order = nullptr) {
     if (nsweeps <= 0) return p_in;
     const size_t cells = S * (size_t)n * n;
+    if (tile == kShapeStrip) {
+        if (nsweeps == 2)
+            strip_launch<T, 4, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
+                                      order);
+        else
+            strip_launch<T, 2, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
+                                      order);
+        return p_out;
+    }
     if (tile > 0) {
         const int TI = std::min(tile, n);
         const int hh = TI >= n ? 0 : 2 * nsweeps;
@@ -812,26 +1203,22 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
 
 static int tune_slot(int n) { return std::min(15, 31 - __builtin_clz((unsigned)n)); }
 
-// Smoother launch shape of grid n.  Untuned defaults (measured on GB300 for
-// two sweeps): register-blocked regions for small grids (FP32 up to 16, FP64
-// up to 32), FP32 tiles of 32 x 32 staged in shared memory at 256 threads up
-// to 128, and above that one bandwidth-bound launch per colour (FP64 too,
-// whose tiles are bound by the FP64 divide); an fm_autotune entry for this
-// grid and precision replaces the default.  Tiles need both smoothing phases
-// of the V-cycle (so the iterate goes p -> p2 -> p) and their staged region
-// in shared memory.
+// Smoother launch shape of grid n.  Untuned defaults (fm_autotune's choices
+// on GB300 for two sweeps): register-blocked regions up to 32 x 32, then FP32
+// column strips; FP64 keeps one launch per colour up to 512 (its strips and
+// tiles are bound by the FP64 divide) and strips above.  An fm_autotune or
+// fm_set_smoother_shape entry for this grid and precision replaces the
+// default.  Tiles and strips need both smoothing phases of the V-cycle (so
+// the iterate goes p -> p2 -> p); tiles need their staged region in shared
+// memory, strips 1 or 2 sweeps.
 template <typename T>
 static void smooth_shape(const fm_ctx* ctx, int n, const fm_solve_params& prm, int* tile, int* threads) {
     const int pi = sizeof(T) == 4 ? 1 : 0, slot = tune_slot(n);
     const bool f32 = sizeof(T) == 4;
     *tile = 0;
     *threads = 0;
-    if (n <= (f32 ? 16 : 32)) {
-        *tile = 32;   // one register-blocked region per sample
-    } else if (f32 && n <= 128) {
-        *tile = 32;
-        *threads = 256;
-    }
+    if (n <= 32) *tile = 32;   // one register-blocked region per sample
+    else if (f32 || n > 512) *tile = kShapeStrip;
     if (ctx->tune.n[pi][slot] == n) {
         *tile = ctx->tune.tile[pi][slot];
         *threads = ctx->tune.threads[pi][slot];
@@ -839,6 +1226,7 @@ static void smooth_shape(const fm_ctx* ctx, int n, const fm_solve_params& prm, i
     if (*tile > 0 && (prm.nu1 < 1 || prm.nu2 < 1 ||
                       tile_smem_bytes(*tile, n, std::max(prm.nu1, prm.nu2), sizeof(T)) > kMaxSmem))
         *tile = 0;
+    if (*tile == kShapeStrip && !strip_fits(n, prm.nu1, prm.nu2)) *tile = 0;
 }
 
 // One V(nu1, nu2) cycle on grid k; grid `top` carries the stage operator
@@ -865,12 +1253,25 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     const size_t cells = S * (size_t)n * n;
     int tile, threads;
     smooth_shape<T>(ctx, n, prm, &tile, &threads);
-    // pre-smoothing p -> p2 (tiles) or in place; post-smoothing back into p
-    T* cur = smooth_with<T>(ctx, tile, threads, n, S, prm.nu1, g.b, Te, Tn, D, g.p, g.p2, active, st);
+    // pre-smoothing p -> p2 (tiles, strips) or in place; post-smoothing back into p
     const GridBufs<T>& c = H.g[k - 1];
-    FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
-             k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
-                 c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
+    T* cur;
+    if (tile == kShapeStrip) {
+        // strips form the residual and its restriction in the same pass
+        if (prm.nu1 == 2)
+            strip_launch<T, 4, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
+                                     H.order);
+        else
+            strip_launch<T, 2, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
+                                     H.order);
+        cur = g.p2;
+    } else {
+        cur = smooth_with<T>(ctx, tile, threads, n, S, prm.nu1, g.b, Te, Tn, D, g.p, g.p2, active, st, nullptr,
+                             H.busy, H.order);
+        FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
+                 k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
+                     c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
+    }
     vcycle(H, k - 1, top, prm, active, st);
     if (tile == 0 && prm.nu2 >= 1) {
         // colour launches: the correction rides in the first post-smoothing colour
@@ -882,14 +1283,16 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
         smooth_with<T>(ctx, 0, 0, n, S, prm.nu2 - 1, g.b, Te, Tn, D, cur, g.p, active, st);
         return;
     }
-    if (tile > 0 && prm.nu2 >= 1) {
-        // tiles: the correction is added as they load the iterate
-        smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, c.p);
+    if (tile != 0 && prm.nu2 >= 1) {
+        // tiles and strips: the correction is added as they load the iterate
+        smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, c.p, H.busy,
+                       H.order);
         return;
     }
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
              k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, cur, active));
-    smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st);
+    smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
+                   H.order);
 }
 
 template <typename P>
@@ -906,12 +1309,13 @@ static void stage_test(const Hierarchy<T>& H, int k, const fm_solve_params& prm,
     const GridBufs<T>& g = H.g[k];
     const size_t S = H.S, cells = (size_t)g.n * g.n;
     const int chunks = check_chunks(g.n);
-    FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * S * cells, 12.0 * S * cells,
-             k_stage_partials<T><<<(unsigned)(S * chunks), kBlock, 0, st>>>(
-                 g.n, S, chunks, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64, g.b,
-                 g.p, H.active, H.partial);
+    const size_t ns = H.listed() ? H.busy : S;
+    FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * ns * cells, 12.0 * ns * cells,
+             k_stage_partials<T><<<(unsigned)(ns * chunks), kBlock, 0, st>>>(
+                 g.n, ns, chunks, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64, g.b,
+                 g.p, H.active, H.partial, H.listed() ? H.order : nullptr);
              k_stage_decide<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, prm.tol, prm.qtol, H.qprev,
-                                                              H.active, H.left));
+                                                              H.active, H.left, H.order));
 }
 
 // Loop control of a refined stage inside a CUDA graph: after residual test
@@ -964,7 +1368,7 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     FM_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
     for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, bs);
-    if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active);
+    if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active, nullptr);
     test(bs);
     cudaGraph_t body = nullptr;
     FM_CUDA_TRY(ctx, cudaStreamEndCapture(bs, &body));
@@ -990,6 +1394,7 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
         stage_test(H, k, prm, mixed, st);
         FM_CUDA_TRY(ctx, cudaMemcpyAsync(&left, H.left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        H.busy = left > 0 ? (size_t)left : S;
         if (left == 0) break;
         if (it >= prm.max_cycles) {
             if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
@@ -997,8 +1402,10 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
         }
         for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, st);
         if (mixed)
-            k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, st>>>(cells, S, g.p, g.p64, H.active);
+            k_ir_update<T><<<blocks_for((H.listed() ? H.busy : S) * cells), kBlock, 0, st>>>(
+                cells, H.listed() ? H.busy : S, g.p, g.p64, H.active, H.listed() ? H.order : nullptr);
     }
+    H.busy = 0;   // later stages run every sample
     return FM_OK;
 }
 
@@ -1240,6 +1647,7 @@ static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine
     H.iter = nullptr;
     H.qprev = nullptr;
     H.partial = nullptr;
+    H.order = nullptr;
 }
 
 // ------------------------------------------------------------------ autotuning
@@ -1299,12 +1707,13 @@ static fm_status autotune_grid(fm_ctx* ctx, int n, int nsweeps, fm_tune_entry* e
     double best = 1e30;
     int bt = def_tile, bth = def_threads;
     e->ms_default = time_shape(def_tile, def_threads);
-    const int tiles[] = {0, 8, 16, 32, 64};
+    const int tiles[] = {0, kShapeStrip, 8, 16, 32, 64};
     const int thr[] = {0, 128, 256};   // 0: register-blocked regions (fixed thread count)
     for (int tile : tiles) {
         if (tile > 0 && tile > n && tile != 8) continue;   // one whole-grid candidate is enough
+        if (tile == kShapeStrip && !strip_fits(n, nsweeps, nsweeps)) continue;
         for (int th : thr) {
-            if (tile == 0 && th != 0) continue;               // colour launches have a fixed shape
+            if (tile <= 0 && th != 0) continue;               // colour launches and strips have a fixed shape
             const double ms = time_shape(tile, th);
             if (ms < best) {
                 best = ms;
@@ -1353,6 +1762,28 @@ extern "C" fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps
         ++count;
     }
     if (n_entries) *n_entries = std::min(count, max_entries);
+    return FM_OK;
+}
+
+extern "C" fm_status fm_set_smoother_shape(fm_ctx* ctx, int32_t precision, int32_t n, int32_t tile,
+                                          int32_t threads) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_set_smoother_shape: null context");
+    FM_CHECK_ARG(ctx, precision == FM_PREC_FP64 || precision == FM_PREC_MIXED,
+                 "fm_set_smoother_shape: unknown precision");
+    FM_CHECK_ARG(ctx, n >= 2 && n <= 8192 && (n & (n - 1)) == 0, "fm_set_smoother_shape: n must be a power of two");
+    const bool tile_ok = tile == 8 || tile == 16 || tile == 32 || tile == 64;
+    FM_CHECK_ARG(ctx, tile == -2 || tile == 0 || tile == kShapeStrip || tile_ok,
+                 "fm_set_smoother_shape: tile must be -2, -1, 0, 8, 16, 32 or 64");
+    FM_CHECK_ARG(ctx, (tile_ok && (threads == 0 || threads == 128 || threads == 256)) || (!tile_ok && threads == 0),
+                 "fm_set_smoother_shape: threads must be 0 (or 128, 256 for tiles)");
+    const int pi = precision == FM_PREC_MIXED ? 1 : 0, slot = tune_slot(n);
+    if (tile == -2) {
+        if (ctx->tune.n[pi][slot] == n) ctx->tune.n[pi][slot] = 0;
+        return FM_OK;
+    }
+    ctx->tune.n[pi][slot] = n;
+    ctx->tune.tile[pi][slot] = tile;
+    ctx->tune.threads[pi][slot] = threads;
     return FM_OK;
 }
 
