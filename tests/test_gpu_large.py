@@ -1,0 +1,61 @@
+"""The finest grid of the large high-contrast case on the GPU (2048 x 2048
+cells, log-permeability variance 2 in short-wavelength modes, contrast
+about 150 to 1000), against converged FP64 oracle outfluxes stored in
+tests/golden/large_2048.json (written by tests/golden/make_large_2048.py,
+which calls only the oracle).  The 1024-mode KL synthesis of that case is
+covered at smaller grids by the tensor-core field tests.
+
+On the field of contrast about 1000 the V-cycles diverge, in the oracle
+(FP64, its stored outflux is about -1e126) as on the GPU: the child-mean
+correction operators stop contracting at this contrast and wavelength.  A
+stored value counts as converged when it lies between the harmonic and the
+arithmetic mean of K (the Wiener bounds of the effective permeability).
+Where the oracle converged, converged FP64 must meet the FP64 bar and the
+mixed form the mixed bar; where it diverged, the GPU's device loop must stop
+at its bound and report FM_ENOTCONV (4) in both precisions, so the estimator
+refuses the sample instead of using it.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_2048.json")))
+
+
+def _fields():
+    f = GOLD["field"]
+    return W.smooth_lognormal_field(f["n"], S=f["S"], sigma=f["sigma"], modes=f["modes"], tag=f["tag"],
+                                    kmax=f["kmax"])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_2048_high_contrast_against_oracle(precision):
+    import paper_1910_04727_gb300 as fm
+    K = _fields()
+    of, oc = np.array(GOLD["qf"]), np.array(GOLD["qc"])
+    # FP64: the residual test alone (1e-13); mixed: the benchmark's rule (1e-12 or an outflux change
+    # of 1e-10), which stops slowly contracting fields about 1e-9 from the converged value
+    rule = dict(tol=1e-13, qtol=0.0, max_cycles=400) if precision == 0 else dict(tol=1e-12, qtol=1e-10,
+                                                                                 max_cycles=200)
+    c = fm.Context(6, 64, 16, precision=precision, converged=1, **rule)
+    qf, qc, _, st = c.fmg_solve_batch(torch.tensor(K, device="cuda"), want_status=True)
+    st = st.cpu().numpy()
+    ef = np.abs(qf.cpu().numpy() - of) / np.abs(of)
+    ec = np.abs(qc.cpu().numpy() - oc) / np.abs(oc)
+    print("2048^2, contrast", [round(x) for x in GOLD["contrast"]], "precision", precision,
+          "Q^f error", ef, "Q^c error", ec, "status", st)
+    hm = 1.0 / np.mean(1.0 / K, axis=(1, 2))
+    am = np.mean(K, axis=(1, 2))
+    ok = np.isfinite(of) & (of >= hm) & (of <= am)
+    assert ok.sum() == 2 and not ok[2]   # the oracle converged on the first two fields only
+    bar = 1e-10 if precision == 0 else 1e-8
+    assert np.all(st[ok] == 0) or precision == 0   # FP64 may end at its bound inside the bar
+    assert np.all(ef[ok] < bar) and np.all(ec[ok] < bar)
+    assert np.all(st[~ok] == 4)   # reported, not returned as a result

@@ -71,14 +71,15 @@ def lognormal_field(n, S=1, sigma=1.0, seed=DEFAULT_SEED, tag=1):
     return np.exp(g)
 
 
-def smooth_lognormal_field(n, S=1, sigma=1.0, modes=6, seed=DEFAULT_SEED, tag=2):
-    """exp of a few random Fourier modes [S][n][n]: a smooth field for solver tests."""
+def smooth_lognormal_field(n, S=1, sigma=1.0, modes=6, seed=DEFAULT_SEED, tag=2, kmax=4):
+    """exp of a few random Fourier modes [S][n][n] (wave numbers below kmax):
+    a smooth field for solver tests."""
     r = rng(seed, tag)
     x = (np.arange(n) + 0.5) / n
     X, Y = np.meshgrid(x, x, indexing="xy")
     g = np.zeros((S, n, n))
     for _ in range(modes):
-        kx, ky = r.integers(0, 4, size=2)
+        kx, ky = r.integers(0, kmax, size=2)
         a = r.standard_normal(S)[:, None, None] * sigma / np.sqrt(modes)
         ph = r.uniform(0, 2 * np.pi, size=S)[:, None, None]
         g += a * np.cos(np.pi * (kx * X + ky * Y)[None] + ph)
