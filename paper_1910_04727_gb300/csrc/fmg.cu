@@ -354,14 +354,16 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // row y - k for k = 1 .. HS: row y - k + 1 has just had half-sweep k - 1 and
 // row y - k - 1 had it one step earlier, so every update sees the values the
 // sweep order prescribes, and row y - HS is final and is written out.  The
-// HS + 2 rows in flight stay in registers (a ring whose slots are fixed by
-// the unrolled step index); two rows are loaded ahead.  A cell with an
+// HS + 2 rows being swept stay in registers (a ring whose slots are fixed by
+// the unrolled step index); the rows ahead of them arrive through a
+// per-warp shared-memory ring filled by cp.async (strip_depth rows deep:
+// each lane copies and later reads back only its own pairs).  A cell with an
 // in-domain neighbour outside the window (first or last column, first or
 // last row of a segment) is not updated, so after HS half-sweeps the window
 // minus HS columns and rows on each side is exact.  Every update is the
 // colour kernel's in the same order with the reciprocal of D, so the sweeps
 // are bit-identical to the other shapes (a missing face adds an exact zero).
-// Operands cross HBM once per call, as float2 / double2 rows of 64 columns.
+// Operands cross HBM once per call, as float2 / double2 pairs per lane.
 // p_in -> p_out as for the tiles; with ec the iterate is p_in + P ec: the
 // coarse row a fine row needs comes through the same ring (each lane's
 // coarse column, plus the columns left and right of the window), and the
