@@ -294,6 +294,9 @@ typedef struct {
                         operators: 0 the injected field itself, 1 the geometric
                         mean of the four children of the injected field one
                         grid finer */
+    int energy_step; /* 1: scale each prolongated correction d by the step
+                        (r, d) / (d, A d) that minimises the energy error
+                        along d (r the residual it corrects) */
 } or_params;
 
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
@@ -494,6 +497,8 @@ typedef struct {
     double* x[32];   /* iterate per grid */
     double* b[32];   /* rhs per grid */
     double* r[32];   /* residual work per grid */
+    double* d[32];   /* prolongated correction and A d (energy step), 2 cells per cell */
+    int energy_step;
 } hierarchy;
 
 static int grid_n(const hierarchy* H, int k) { return H->n0 << k; }
@@ -508,9 +513,11 @@ static void geometric_children(int nc, const double* Kf, double* Kc)
                                          log(Kf[(2 * J + 1) * nf + 2 * I]) + log(Kf[(2 * J + 1) * nf + 2 * I + 1])));
 }
 
-static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fine, int coarse_op)
+static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fine, int coarse_op,
+                           int energy_step)
 {
     memset(H, 0, sizeof(*H));
+    H->energy_step = energy_step;
     H->n0 = n0;
     int m = 0;
     while ((n0 << m) < n_fine) ++m;
@@ -521,6 +528,7 @@ static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fin
         H->x[k] = (double*)calloc(cells, sizeof(double));
         H->b[k] = (double*)calloc(cells, sizeof(double));
         H->r[k] = (double*)calloc(cells, sizeof(double));
+        if (energy_step) H->d[k] = (double*)calloc(2 * cells, sizeof(double));
     }
     memcpy(H->K[m], K_fine, sizeof(double) * (size_t)n_fine * n_fine);
     for (int k = m; k >= 1; --k) or_inject(grid_n(H, k - 1), H->K[k], H->K[k - 1]);
@@ -537,7 +545,7 @@ static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fin
 static void hierarchy_free(hierarchy* H)
 {
     for (int k = 0; k <= H->m; ++k) {
-        free(H->K[k]); free(H->x[k]); free(H->b[k]); free(H->r[k]); free(H->Kavg[k]);
+        free(H->K[k]); free(H->x[k]); free(H->b[k]); free(H->r[k]); free(H->Kavg[k]); free(H->d[k]);
     }
 }
 
@@ -556,7 +564,25 @@ static void vcycle(hierarchy* H, int k, int top, int nu1, int nu2)
     or_restrict_sum(n / 2, H->r[k], H->b[k - 1]);
     memset(H->x[k - 1], 0, sizeof(double) * (size_t)(n / 2) * (n / 2));
     vcycle(H, k - 1, top, nu1, nu2);
-    or_prolong_add(n / 2, H->x[k - 1], H->x[k]);
+    if (!H->energy_step) {
+        or_prolong_add(n / 2, H->x[k - 1], H->x[k]);
+    } else {
+        /* d = P e_c; x += alpha d with alpha = (r, d) / (d, A d), the exact
+           line minimum of the energy error (A symmetric positive definite) */
+        size_t cells = (size_t)n * n;
+        double* d = H->d[k];
+        double* Ad = d + cells;
+        memset(d, 0, sizeof(double) * cells);
+        or_prolong_add(n / 2, H->x[k - 1], d);
+        or_apply_A(n, K, d, Ad);
+        double rd = 0.0, dAd = 0.0;
+        for (size_t c = 0; c < cells; ++c) {
+            rd += H->r[k][c] * d[c];
+            dAd += d[c] * Ad[c];
+        }
+        double alpha = dAd > 0.0 ? rd / dAd : 0.0;
+        for (size_t c = 0; c < cells; ++c) H->x[k][c] += alpha * d[c];
+    }
     for (int s = 0; s < nu2; ++s) or_rbgs_sweep(n, K, H->b[k], H->x[k]);
 }
 
@@ -596,7 +622,7 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
                  double* p_out, double* qf, double* qc)
 {
     hierarchy H;
-    hierarchy_init(&H, n_fine, n0, K_fine, P->coarse_op);
+    hierarchy_init(&H, n_fine, n0, K_fine, P->coarse_op, P->energy_step);
     int cycles = 0;
     *qc = NAN;
     or_stage_rhs(n0, H.K[0], P->pW, P->pE, H.b[0]);
@@ -618,10 +644,10 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
 /* V-cycles on a given problem A x = b from the given x (for convergence-factor
  * checks).  res_hist[c] = ||b - A x|| after cycle c (c = 0 before any). */
 void or_vcycle_solve(int n, int n0, const double* K, const double* b, double* x,
-                     int nu1, int nu2, int ncycles, int coarse_op, double* res_hist)
+                     int nu1, int nu2, int ncycles, int coarse_op, int energy_step, double* res_hist)
 {
     hierarchy H;
-    hierarchy_init(&H, n, n0, K, coarse_op);
+    hierarchy_init(&H, n, n0, K, coarse_op, energy_step);
     memcpy(H.b[H.m], b, sizeof(double) * (size_t)n * n);
     memcpy(H.x[H.m], x, sizeof(double) * (size_t)n * n);
     for (int c = 0; c <= ncycles; ++c) {

@@ -15,12 +15,14 @@ class Params(C.Structure):
     """Solver parameters (mirrors ``or_params`` in fmg_oracle.c)."""
     _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("nu0", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("converged", C.c_int),
-                ("tol", C.c_double), ("max_cycles", C.c_int), ("coarse_op", C.c_int)]
+                ("tol", C.c_double), ("max_cycles", C.c_int), ("coarse_op", C.c_int),
+                ("energy_step", C.c_int)]
 
 
 def params(pW=1.0, pE=0.0, nu0=2, nu1=2, nu2=2, converged=False, tol=1e-12,
-           max_cycles=100, coarse_op=1):
-    return Params(pW, pE, nu0, nu1, nu2, int(bool(converged)), tol, max_cycles, coarse_op)
+           max_cycles=100, coarse_op=1, energy_step=False):
+    return Params(pW, pE, nu0, nu1, nu2, int(bool(converged)), tol, max_cycles, coarse_op,
+                  int(bool(energy_step)))
 
 
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -63,7 +65,7 @@ def lib():
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.or_fmg_solve.restype = C.c_int
         L.or_vcycle_solve.argtypes = [C.c_int, C.c_int, _D, _D, _D, C.c_int, C.c_int,
-                                      C.c_int, C.c_int, _D]
+                                      C.c_int, C.c_int, C.c_int, _D]
         L.or_fmg_solve_batch.argtypes = [C.c_int, C.c_int, C.c_int, _D, C.POINTER(Params),
                                          C.c_void_p, _D, _D, C.c_int]
         L.or_fmg_solve_batch.restype = C.c_int
@@ -216,11 +218,12 @@ def fmg_solve(K, prm=None, n0=4, want_p=False):
     return qf.value, qc.value, p, cyc
 
 
-def vcycle_solve(K, b, x0, nu1=2, nu2=2, ncycles=10, n0=4, coarse_op=1):
+def vcycle_solve(K, b, x0, nu1=2, nu2=2, ncycles=10, n0=4, coarse_op=1, energy_step=False):
     """V-cycles on A x = b; returns (x, residual norms before/after each cycle)."""
     x = _c(x0).copy()
     hist = np.zeros(ncycles + 1)
-    lib().or_vcycle_solve(K.shape[0], n0, _c(K), _c(b), x, nu1, nu2, ncycles, coarse_op, hist)
+    lib().or_vcycle_solve(K.shape[0], n0, _c(K), _c(b), x, nu1, nu2, ncycles, coarse_op,
+                          int(bool(energy_step)), hist)
     return x, hist
 
 
