@@ -118,6 +118,10 @@ typedef struct {
     double qtol;          /* also stop once a cycle changes the outflux by <= qtol |Q| */
     int32_t max_cycles;   /* cap per converged stage; a sample that reaches it gets
                              status FM_ENOTCONV */
+    int32_t energy_step;  /* 1 (converged mode, level-wise schedule): add each V-cycle's
+                             coarse-grid correction d = P e_c as alpha d, alpha = (r, d) /
+                             (d, A d) per sample, the energy minimum along d, so no cycle
+                             raises the energy error (robust at high contrast) */
 } fm_solve_params;
 
 /* ---------------------------------------------------------------- context */

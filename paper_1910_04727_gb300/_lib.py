@@ -43,7 +43,8 @@ class FmSolveParams(C.Structure):
     _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("n_coarsest", C.c_int32),
                 ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("converged", C.c_int32),
-                ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32)]
+                ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
+                ("energy_step", C.c_int32)]
 
 
 class FmLevelSums(C.Structure):

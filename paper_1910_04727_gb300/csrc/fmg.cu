@@ -665,6 +665,93 @@ __global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE
     pf[t] = add ? pf[t] + v : v;
 }
 
+// Energy-optimal step of a coarse-grid correction: the correction d = P e_c
+// is added as alpha d with alpha = (r, d) / (d, A d), r = b - A x the
+// residual it answers, the exact line minimum of the energy error for the
+// symmetric positive definite A (so a cycle never raises the energy error,
+// whatever the correction operators).  Per (sample, chunk) of grid n: the
+// partial sums of (r, d) and (d, A d) in FP64, with d formed on the fly by
+// the prolongation (A d takes it at the four neighbours too); entries 0 and
+// 1 of the sample's 3-double slots in partial.
+template <typename T>
+__global__ void k_energy_partials(int n, size_t S, int chunks, const T* __restrict__ b, const T* __restrict__ Te,
+                                  const T* __restrict__ Tn, const T* __restrict__ D, const T* __restrict__ x,
+                                  const T* __restrict__ ec, const int32_t* __restrict__ active,
+                                  const int32_t* __restrict__ order, double* __restrict__ partial) {
+    __shared__ double red[2][32];
+    if (blockIdx.x / chunks >= S) return;   // S: the samples enumerated (listed by order, if given)
+    const size_t s = order ? (size_t)order[blockIdx.x / chunks] : blockIdx.x / chunks;
+    const int ch = (int)(blockIdx.x % chunks);
+    if (inactive(active, s)) return;
+    const int nc = n / 2;
+    const size_t base = s * (size_t)n * n;
+    const T* e = ec + s * (size_t)nc * nc;
+    const int cells = n * n, per = (cells + chunks - 1) / chunks;
+    const int c0 = ch * per, c1 = min(cells, c0 + per);
+    double rd = 0.0, dad = 0.0;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const int i = c % n, j = c / n;
+        const size_t g = base + c;
+        const T r = residual_at(n, g, i, j, b, Te, Tn, D, x);
+        const T d = prolong_at(nc, e, i, j, T(0), T(0));
+        T ad = mul_rn(D[g], d);
+        if (i > 0) ad = fma(-Te[g - 1], prolong_at(nc, e, i - 1, j, T(0), T(0)), ad);
+        if (i < n - 1) ad = fma(-Te[g], prolong_at(nc, e, i + 1, j, T(0), T(0)), ad);
+        if (j > 0) ad = fma(-Tn[g - n], prolong_at(nc, e, i, j - 1, T(0), T(0)), ad);
+        if (j < n - 1) ad = fma(-Tn[g], prolong_at(nc, e, i, j + 1, T(0), T(0)), ad);
+        rd += (double)r * (double)d;
+        dad += (double)d * (double)ad;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rd += __shfl_down_sync(0xffffffffu, rd, off);
+        dad += __shfl_down_sync(0xffffffffu, dad, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = rd;
+        red[1][threadIdx.x >> 5] = dad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, q = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            q += red[1][w];
+        }
+        double* out = partial + ((size_t)s * chunks + ch) * 3;
+        out[0] = a;
+        out[1] = q;
+    }
+}
+
+// alpha[s] = (r, d) / (d, A d) from the chunks' partial sums (0 when d = 0).
+__global__ void k_energy_alpha(size_t S, int chunks, const double* __restrict__ partial, double* __restrict__ alpha,
+                               const int32_t* __restrict__ active) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || inactive(active, s)) return;
+    double rd = 0.0, dad = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) {
+        rd += partial[((size_t)s * chunks + ch) * 3];
+        dad += partial[((size_t)s * chunks + ch) * 3 + 1];
+    }
+    alpha[s] = dad > 0.0 ? rd / dad : 0.0;
+}
+
+// p_f += alpha[s] P e_c, the stepped correction (in FP64, rounded once to T).
+template <typename T>
+__global__ void k_prolong_step(int nc, size_t S, const T* __restrict__ uc, const double* __restrict__ alpha,
+                               T* __restrict__ pf, const int32_t* __restrict__ active) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nf = 2 * nc;
+    const size_t cells = (size_t)nf * nf;
+    if (t >= S * cells) return;
+    const size_t s = t / cells;
+    if (inactive(active, s)) return;
+    const int c = (int)(t % cells);
+    const T v = prolong_at(nc, uc + s * (size_t)nc * nc, c % nf, c / nf, T(0), T(0));
+    pf[t] = (T)((double)pf[t] + alpha[s] * (double)v);
+}
+
 // The first colour (0) of post-smoothing fused with the coarse-grid
 // correction p += P e: a red cell's update reads only its black neighbours,
 // so they are read as p + (P e) on the fly and the red cell's own correction
@@ -939,6 +1026,7 @@ struct Hierarchy {
     double* qprev;     // outflux of the previous iteration per sample
     double* partial;   // per-(sample, chunk) partial sums of the residual tests
     int32_t* order;    // the samples still iterating, as listed by the last residual test
+    double* alpha;     // per-sample step of the energy-optimal coarse-grid correction
     // Host-side count of the samples still iterating in a refined stage (the
     // host loop reads it after every test; S otherwise): the strip smoother
     // sizes its row segments for it, so that a launch with few active samples
@@ -962,7 +1050,7 @@ static size_t hierarchy_bytes(int n_fine, int n0, size_t S, size_t tsize, bool m
         if (mixed && k >= m - 1) total += c * 32 + 4 * 256;
     }
     total += 2 * ((size_t)n0 * n0 * n0 * n0 * tsize + 256);
-    if (converged) total += 4 * 4 + 8 + (size_t)check_chunks(n_fine) * 24 + 6 * 256;
+    if (converged) total += 4 * 4 + 16 + (size_t)check_chunks(n_fine) * 24 + 7 * 256;
     return total * S + 4096;
 }
 
@@ -1039,6 +1127,7 @@ static fm_status carve(fm_ctx* ctx, Arena& ar, Hierarchy<T>& H, int n_fine, int 
     H.qprev = converged ? (double*)take(S * 8) : nullptr;
     H.partial = converged ? (double*)take(S * (size_t)check_chunks(n_fine) * 24) : nullptr;
     H.order = converged ? (int32_t*)take(S * 4) : nullptr;
+    H.alpha = converged ? (double*)take(S * 8) : nullptr;
     return FM_OK;
 }
 
@@ -1275,6 +1364,20 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
                      c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
     }
     vcycle(H, k - 1, top, prm, active, st);
+    if (prm.energy_step) {
+        // the stepped correction (converged mode: partials and alpha in the hierarchy)
+        const int chunks = check_chunks(n);
+        const bool listed = H.listed();
+        const size_t ns = listed ? H.busy : S;
+        FM_TIMED(ctx, kFamProlong, st, (5.0 * ts + 1.25 * ts) * ns * n * n + 2.0 * ts * cells, 40.0 * ns * n * n,
+                 k_energy_partials<T><<<(unsigned)(ns * chunks), kBlock, 0, st>>>(
+                     n, ns, chunks, g.b, Te, Tn, D, cur, c.p, active, listed ? H.order : nullptr, H.partial);
+                 k_energy_alpha<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, H.alpha, active);
+                 k_prolong_step<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, H.alpha, cur, active));
+        smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
+                       H.order);
+        return;
+    }
     if (tile == 0 && prm.nu2 >= 1) {
         // colour launches: the correction rides in the first post-smoothing colour
         FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells + ts * S * c.n * c.n, 5.0 * cells,
@@ -1557,8 +1660,11 @@ fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const d
     FM_CHECK_ARG(ctx, S == 0 || (d_K && d_qf), "fmg_solve_batch: null input or output");
     FM_CHECK_ARG(ctx, prm.kernel >= FM_KERNEL_AUTO && prm.kernel <= FM_KERNEL_RESIDENT,
                  "fmg_solve_batch: unknown kernel schedule");
+    FM_CHECK_ARG(ctx, !prm.energy_step || (prm.converged && prm.kernel != FM_KERNEL_RESIDENT),
+                 "fmg_solve_batch: the energy-optimal correction step runs in converged mode on the level-wise "
+                 "schedule");
     if (S == 0) return FM_OK;
-    if (prm.kernel != FM_KERNEL_LEVELWISE) {
+    if (prm.kernel != FM_KERNEL_LEVELWISE && !prm.energy_step) {
         if (fmg_resident_launch(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st)) {
             FM_CUDA_TRY(ctx, cudaGetLastError());
             return FM_OK;
@@ -1650,6 +1756,7 @@ static void carve_into(fm_ctx* ctx, Hierarchy<double>& H, char* base, int n_fine
     H.qprev = nullptr;
     H.partial = nullptr;
     H.order = nullptr;
+    H.alpha = nullptr;
 }
 
 // ------------------------------------------------------------------ autotuning

@@ -65,9 +65,10 @@ static fm_status uneven_prepare(fm_ctx* ctx, int groups) {
     return FM_OK;
 }
 
-// A hierarchy fits the resident kernel (its shared-memory limit) for n <= 64.
+// A hierarchy fits the resident kernel (its shared-memory limit) for n <= 64;
+// the energy-optimal correction step runs on the level-wise schedule only.
 static bool resident_grid(int n, const fm_solve_params& prm) {
-    return prm.kernel != FM_KERNEL_LEVELWISE && n <= 64;
+    return prm.kernel != FM_KERNEL_LEVELWISE && !prm.energy_step && n <= 64;
 }
 
 }  // namespace fm

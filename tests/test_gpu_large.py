@@ -59,3 +59,59 @@ def test_2048_high_contrast_against_oracle(precision):
     assert np.all(st[ok] == 0) or precision == 0   # FP64 may end at its bound inside the bar
     assert np.all(ef[ok] < bar) and np.all(ec[ok] < bar)
     assert np.all(st[~ok] == 4)   # reported, not returned as a result
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_2048_energy_step_solves_every_field(precision):
+    """With the energy-optimal correction step every field converges, the
+    contrast-1000 one included, to the outfluxes of the stepped oracle."""
+    import paper_1910_04727_gb300 as fm
+    K = _fields()
+    of, oc = np.array(GOLD["qf_energy_step"]), np.array(GOLD["qc_energy_step"])
+    rule = dict(tol=1e-13, qtol=0.0, max_cycles=400) if precision == 0 else dict(tol=1e-12, qtol=1e-10,
+                                                                                 max_cycles=200)
+    c = fm.Context(6, 64, 16, precision=precision, converged=1, **rule)
+    qf, qc, _, st = c.fmg_solve_batch(torch.tensor(K, device="cuda"), want_status=True, energy_step=1)
+    st = st.cpu().numpy()
+    ef = np.abs(qf.cpu().numpy() - of) / np.abs(of)
+    ec = np.abs(qc.cpu().numpy() - oc) / np.abs(oc)
+    print("2048^2 with the energy step, precision", precision, "Q^f error", ef, "Q^c error", ec, "status", st)
+    if precision == 0:
+        # a relative residual of 1e-13 leaves an outflux error of about n tol (2e-10 at
+        # n = 2048: b lives on the boundary column); measured 1.6e-10 at most
+        assert np.all(st == 0)
+        bar = 2 * 2048 * 1e-13
+        assert np.all(ef < bar) and np.all(ec < bar)
+    else:
+        assert np.all((st == 0) | (st == 4))
+        assert np.all(ef < 1e-8) and np.all(ec < 1e-8)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_energy_step_matches_oracle_at_128(precision):
+    """High-contrast 128 x 128 fields (one on which the plain cycle diverges):
+    the stepped GPU solve against the stepped oracle, every sample."""
+    import paper_1910_04727_gb300 as fm
+    from oracle import lib as OL
+    K = W.smooth_lognormal_field(128, S=6, sigma=np.sqrt(2.0), modes=24, tag=3100, kmax=12)
+    ref_f, ref_c, _, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-14, max_cycles=400,
+                                                         energy_step=True))
+    c = fm.Context(6, 4, 16, precision=precision, converged=1, tol=1e-13 if precision == 0 else 1e-12,
+                   qtol=0.0 if precision == 0 else 1e-10, max_cycles=400)
+    qf, qc, _, st = c.fmg_solve_batch(torch.tensor(K, device="cuda"), want_status=True, energy_step=1)
+    ef = np.abs(qf.cpu().numpy() - ref_f) / np.abs(ref_f)
+    ec = np.abs(qc.cpu().numpy() - ref_c) / np.abs(ref_c)
+    print("128^2 with the energy step, precision", precision, "errors", ef.max(), ec.max(), "status", st.cpu().numpy())
+    bar = 1e-10 if precision == 0 else 1e-8
+    assert np.all(st.cpu().numpy() == 0)
+    assert ef.max() < bar and ec.max() < bar
+
+
+def test_energy_step_arguments_are_checked():
+    import paper_1910_04727_gb300 as fm
+    K = torch.tensor(W.smooth_lognormal_field(32, S=2, tag=3500), device="cuda")
+    c = fm.Context(3, 8, 16, converged=1, tol=1e-12, max_cycles=100)
+    with pytest.raises(fm.FmError):
+        c.fmg_solve_batch(K, energy_step=1, kernel=2)        # the resident schedule
+    with pytest.raises(fm.FmError):
+        c.fmg_solve_batch(K, energy_step=1, converged=0)     # a fixed schedule
