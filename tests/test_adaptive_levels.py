@@ -285,3 +285,15 @@ def test_two_gloo_ranks_grow_like_one_rank():
     E, N, rounds, est = res[0]
     assert E == one["n_ext_used"] and N == list(one["N"]) and rounds == one["rounds"]
     assert math.isclose(est, one["estimate"], rel_tol=1e-13)
+
+
+def test_adaptive_options_are_checked():
+    import paper_1910_04727_gb300 as fm
+    m = Model(1.0, 4, below=1, s0=0.05, seed=15)
+    cost = _cost(6, 1)
+    for kw in (dict(level0=1, adapt_from=2),        # fewer than MLMC levels 0 and 1
+               dict(level0=0, adapt_from=7),        # more than n_ext
+               dict(level0=6, adapt_from=6)):       # level 0 outside the extended levels
+        h = Sums(m, len(cost))
+        with pytest.raises(fm.FmError):
+            fm.estimate_core(cost, 1e-2, h.enqueue, h.read, n_pilot=32, **kw)
