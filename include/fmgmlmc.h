@@ -147,6 +147,14 @@ const char* fm_last_error(const fm_ctx* ctx);
 fm_status mc_points(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, uint32_t dim,
                     double* d_xi, void* stream);
 
+/* The raw 64-bit Philox4x64-10 words behind mc_points (Sec. 2.3):
+ * d_words[s*dim + k] = word k of the stream keyed (seed, 1<<32 | level) at
+ * counter (k/4, first + s, 0, 0), lane k%4, written by the same kernel that
+ * mc_points runs, so the normals are Phi^{-1}(((w >> 11) + 1/2) 2^-53) of
+ * exactly these words.  n samples; dim <= 4096; d_words device [n][dim]. */
+fm_status mc_words(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, uint32_t dim,
+                   uint64_t* d_words, void* stream);
+
 /* Randomized Sobol' points (Sec. 2.4 / 3.1): point index first + s (Gray-code
  * order, x = XOR of the direction numbers selected by the bits of
  * (n XOR n>>1)), XOR a digital shift per (level, shift r, dimension) drawn
@@ -204,8 +212,10 @@ fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d
  * NaN if n_fine == n_coarsest); d_p (nullable) the finest solution
  * [n][n_fine][n_fine]; d_status (nullable) per-sample FM_OK / FM_ENOTCONV.
  * n_fine must be n_coarsest times a power of two.  Scratch is owned by the
- * context.  FM_PREC_MIXED and converged mode run on the resident schedule
- * (n_fine <= 64). */
+ * context.  prm->kernel picks the schedule: the resident one (the whole
+ * hierarchy of a sample in shared memory, n_fine <= 64) or the level-wise
+ * one (any n_fine up to 8192); both run FP64 and mixed, fixed and converged
+ * (the energy step: level-wise only). */
 fm_status fmg_solve_batch(fm_ctx* ctx, int32_t n_fine, uint32_t n, const double* d_K,
                           const fm_solve_params* prm, double* d_qf, double* d_qc,
                           double* d_p, int32_t* d_status, void* stream);
@@ -312,6 +322,22 @@ typedef struct {
     double count;
     double pad[7];
 } fm_level_sums;
+
+/* Statistics of one fm_level_sums cell (host memory; no CUDA call). */
+typedef struct {
+    double count;         /* samples */
+    double mean;          /* sum Y / count */
+    double var;           /* Bessel-corrected sample variance of Y (0 for count < 2) */
+    double sum_qf, sum_qc;
+} fm_level_stat;
+
+/* Mean and variance of the samples behind one cell (Sec. 2.2: the sample
+ * mean of Y_l and the estimate V_l of its variance).  The compensated sums
+ * of Y and of the exact Y^2 are read as double-double numbers and
+ * S2 - S1^2 / n is formed in double-double arithmetic, so the variance keeps
+ * its accuracy when |mean| is much larger than the standard deviation.
+ * FM_EINVAL for a null pointer. */
+fm_status fm_level_stats(const fm_level_sums* sums, fm_level_stat* out);
 
 /* Draw samples first .. first+n-1 of level `level` (MC if shift < 0, else
  * QMC shift `shift`), synthesise their fields, run the FMG solve and add Y,

@@ -139,6 +139,16 @@ void or_mc_normals(uint64_t seed, uint32_t level, uint64_t first, uint32_t n,
         }
 }
 
+/* The 64-bit words behind or_mc_normals: w[s*dim + k] = word k of the
+ * stream (seed, MC<<32 | level) at sample index first + s. */
+void or_mc_words(uint64_t seed, uint32_t level, uint64_t first, uint32_t n, uint32_t dim, uint64_t* w)
+{
+    uint64_t key1 = ((uint64_t)OR_PURPOSE_MC << 32) | level;
+    for (uint32_t s = 0; s < n; ++s)
+        for (uint32_t k = 0; k < dim; ++k)
+            w[(size_t)s * dim + k] = or_philox_word(seed, key1, first + s, k);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sobol' points (Sec. 2.4, Sobol' sequence; Bratley & Fox, ACM TOMS 1988).  */
 /* ------------------------------------------------------------------------ */
@@ -504,7 +514,7 @@ typedef struct {
 static int grid_n(const hierarchy* H, int k) { return H->n0 << k; }
 
 /* K_c[J][I] = (K_f[2J][2I] K_f[2J][2I+1] K_f[2J+1][2I] K_f[2J+1][2I+1])^(1/4) */
-static void geometric_children(int nc, const double* Kf, double* Kc)
+void or_geometric_children(int nc, const double* Kf, double* Kc)
 {
     int nf = 2 * nc;
     for (int J = 0; J < nc; ++J)
@@ -536,7 +546,7 @@ static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fin
         H->Kop[k] = H->K[k];
         if (coarse_op == 1 && k < m) {
             H->Kavg[k] = (double*)malloc(sizeof(double) * (size_t)grid_n(H, k) * grid_n(H, k));
-            geometric_children(grid_n(H, k), H->K[k + 1], H->Kavg[k]);
+            or_geometric_children(grid_n(H, k), H->K[k + 1], H->Kavg[k]);
             H->Kop[k] = H->Kavg[k];
         }
     }

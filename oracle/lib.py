@@ -42,6 +42,7 @@ def lib():
         L.or_norminv.restype = C.c_double
         L.or_mc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32,
                                     C.c_uint32, _D]
+        L.or_mc_words.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, _U64]
         L.or_gf2_is_primitive.argtypes = [C.c_uint64, C.c_int]
         L.or_primitive_polys.argtypes = [C.c_int, _U64, _I32]
         L.or_sobol_direction_numbers.argtypes = [C.c_uint32, _U32]
@@ -56,6 +57,7 @@ def lib():
         L.or_prolong_add.argtypes = [C.c_int, _D, _D]
         L.or_fmg_interpolate.argtypes = [C.c_int, _D, C.c_double, C.c_double, _D]
         L.or_inject.argtypes = [C.c_int, _D, _D]
+        L.or_geometric_children.argtypes = [C.c_int, _D, _D]
         L.or_exact_solve.argtypes = [C.c_int, _D, _D, _D]
         L.or_outflux.argtypes = [C.c_int, _D, _D, C.c_double]
         L.or_outflux.restype = C.c_double
@@ -97,6 +99,13 @@ def mc_normals(seed, level, first, n, dim):
     xi = np.zeros((n, dim))
     lib().or_mc_normals(seed, level, first, n, dim, xi)
     return xi
+
+
+def mc_words(seed, level, first, n, dim):
+    """The 64-bit Philox words behind mc_normals, [n][dim] uint64."""
+    w = np.zeros((n, dim), np.uint64)
+    lib().or_mc_words(seed, level, first, n, dim, w)
+    return w
 
 
 def primitive_polys(count):
@@ -188,6 +197,15 @@ def inject(Kf):
     nc = Kf.shape[0] // 2
     Kc = np.zeros((nc, nc))
     lib().or_inject(nc, _c(Kf), Kc)
+    return Kc
+
+
+def geometric_children(Kf):
+    """Coefficients of a correction grid: the geometric mean of each coarse
+    cell's four children on the finer grid Kf."""
+    nc = Kf.shape[0] // 2
+    Kc = np.zeros((nc, nc))
+    lib().or_geometric_children(nc, _c(Kf), Kc)
     return Kc
 
 

@@ -159,6 +159,13 @@ class Context:
         self._check(self._L.mc_points(self._h, level, first, n, dim, _ptr(out), _stream()))
         return out
 
+    def mc_words(self, level, first, n, dim=None):
+        """The raw 64-bit Philox words behind mc_points, [n][dim] (int64 bit patterns)."""
+        dim = dim or self.M
+        out = torch.empty((n, dim), dtype=torch.int64, device="cuda")
+        self._check(self._L.mc_words(self._h, level, first, n, dim, _ptr(out), _stream()))
+        return out
+
     def sobol_points(self, level, first, n, first_shift=0, n_shifts=1, dim=None, want_x=True,
                      want_xi=True):
         dim = dim or self.M
@@ -290,13 +297,15 @@ class Context:
 
     @staticmethod
     def read_sums(sums):
-        """(mean, var, count, sum_qf, sum_qc) of one fm_level_sums row."""
-        s = sums.detach().cpu().numpy()
-        n = s[8]
-        sy, sy2 = s[0] + s[1], s[2] + s[3]
-        mean = sy / n
-        var = (sy2 - sy * sy / n) / (n - 1) if n > 1 else 0.0
-        return mean, var, n, s[4] + s[5], s[6] + s[7]
+        """(mean, var, count, sum_qf, sum_qc) of one fm_level_sums row (fm_level_stats)."""
+        L = _lib.load()
+        raw = np.ascontiguousarray(sums.detach().cpu().numpy(), dtype=np.float64)
+        cell = _lib.FmLevelSums.from_buffer_copy(raw.tobytes())
+        st = _lib.FmLevelStat()
+        rc = L.fm_level_stats(C.byref(cell), C.byref(st))
+        if rc != 0:
+            raise FmError(rc, "fm_level_stats")
+        return st.mean, st.var, st.count, st.sum_qf, st.sum_qc
 
     # ----------------------------------------------------------- profiling
     def profile_begin(self, mask=0xFFFFFFFF):

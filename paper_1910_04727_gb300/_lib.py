@@ -26,7 +26,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
-           "fmg_uneven_stats", "fm_set_smoother_shape"]
+           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats"]
 
 
 class FmConfig(C.Structure):
@@ -50,6 +50,11 @@ class FmSolveParams(C.Structure):
 class FmLevelSums(C.Structure):
     _fields_ = [("sum_y", C.c_double * 2), ("sum_y2", C.c_double * 2), ("sum_qf", C.c_double * 2),
                 ("sum_qc", C.c_double * 2), ("count", C.c_double), ("pad", C.c_double * 7)]
+
+
+class FmLevelStat(C.Structure):
+    _fields_ = [("count", C.c_double), ("mean", C.c_double), ("var", C.c_double), ("sum_qf", C.c_double),
+                ("sum_qc", C.c_double)]
 
 
 class FmEstimateOpts(C.Structure):
@@ -131,6 +136,8 @@ def load(path=None):
         "fm_destroy": (None, [P]),
         "fm_last_error": (C.c_char_p, [P]),
         "mc_points": (I32, [P, U32, U64, U32, U32, P, P]),
+        "mc_words": (I32, [P, U32, U64, U32, U32, P, P]),
+        "fm_level_stats": (I32, [P, C.POINTER(FmLevelStat)]),
         "sobol_points": (I32, [P, U32, U32, U64, U32, U32, U32, P, P, P]),
         "sobol_direction_numbers": (I32, [P, P]),
         "kl_basis_set": (I32, [P, P, I32]),

@@ -50,11 +50,69 @@ void fold_ranks(const fm_level_sums* all, int world, size_t cells, fm_level_sums
     }
 }
 
+// Double-double helpers (Dekker 1971; Knuth's two-sum): a value is the
+// unevaluated sum hi + lo.
+struct DD {
+    double hi, lo;
+};
+
+DD two_sum(double a, double b) {
+    const double s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+DD dd_add(DD a, DD b) {
+    const DD s = two_sum(a.hi, b.hi);
+    return two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+
+DD dd_mul(DD a, DD b) {
+    const double p = a.hi * b.hi;
+    const double e = std::fma(a.hi, b.hi, -p);
+    return two_sum(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+
+DD dd_div(DD a, double d) {
+    const double q = a.hi / d;
+    // remainder a - q d, formed exactly to first order
+    const DD qd = dd_mul({q, 0.0}, {d, 0.0});
+    const DD r = dd_add(a, {-qd.hi, -qd.lo});
+    return two_sum(q, (r.hi + r.lo) / d);
+}
+
+// Mean and Bessel-corrected variance of one level-sum cell.  The sums are
+// Neumaier pairs (sum, compensation) of Y and Y^2 (Y^2 accumulated with its
+// exact rounding error), read as double-double numbers; S2 - S1^2 / n is
+// formed in double-double, so the cancellation when |mean| >> sd costs
+// nothing until sd / |mean| nears 1e-16.
+void level_mean_var(const fm_level_sums& s, double* mean, double* var) {
+    const double n = s.count;
+    const DD s1 = two_sum(s.sum_y[0], s.sum_y[1]);
+    const DD s2 = two_sum(s.sum_y2[0], s.sum_y2[1]);
+    *mean = n > 0 ? (s1.hi + s1.lo) / n : NAN;
+    if (!(n > 1)) {
+        *var = 0.0;
+        return;
+    }
+    const DD sq = dd_div(dd_mul(s1, s1), n);
+    const DD d = dd_add(s2, {-sq.hi, -sq.lo});
+    *var = std::max(0.0, (d.hi + d.lo) / (n - 1));
+}
+
 void set_err(char* err, size_t len, const std::string& msg) {
     if (err && len) std::snprintf(err, len, "%s", msg.c_str());
 }
 
 }  // namespace
+
+extern "C" fm_status fm_level_stats(const fm_level_sums* sums, fm_level_stat* out) {
+    if (!sums || !out) return FM_EINVAL;
+    out->count = sums->count;
+    level_mean_var(*sums, &out->mean, &out->var);
+    out->sum_qf = sums->sum_qf[0] + sums->sum_qf[1];
+    out->sum_qc = sums->sum_qc[0] + sums->sum_qc[1];
+    return FM_OK;
+}
 
 extern "C" void fm_shard_range(uint64_t first, uint64_t n, int32_t rank, int32_t world, uint64_t* my_first,
                                uint64_t* my_n) {
@@ -137,8 +195,8 @@ extern "C" fm_status mlmc_estimate_core(const fm_core_opts* o, fm_enqueue_fn enq
                     set_err(err, errlen, "mlmc_estimate: non-finite samples on level " + std::to_string(e));
                     return FM_ENOTCONV;
                 }
-                mean[e] = sy / n;
-                var[e] = n > 1 ? std::max(0.0, (sy2 - sy * sy / n) / (n - 1)) : 0.0;
+                (void)n;
+                level_mean_var(s, &mean[e], &var[e]);
             } else {
                 double m[64];
                 double mm = 0.0;

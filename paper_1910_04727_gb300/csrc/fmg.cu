@@ -1911,6 +1911,9 @@ extern "C" fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_
                  "fmg_solve_batch_static: need nu0 >= 1 and nu1 + nu2 >= 1");
     FM_CHECK_ARG(ctx, prm->precision == FM_PREC_FP64 && !prm->converged,
                  "fmg_solve_batch_static: only the FP64 fixed-cycle schedule (converged = 0)");
+    // the energy step keeps per-sample dot products and step lengths that the
+    // static hierarchy has no room for
+    FM_CHECK_ARG(ctx, !prm->energy_step, "fmg_solve_batch_static: the energy-optimal step is not available here");
     FM_CHECK_ARG(ctx, n == 0 || (d_K && d_qf), "fmg_solve_batch_static: null input or output");
     if (n == 0) return FM_OK;
     const size_t need = hierarchy_bytes(n_fine, n0, n, 8, false, false);
@@ -1923,7 +1926,12 @@ extern "C" fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_
     if (!base) return st;
     Hierarchy<double> H;
     carve_into(ctx, H, base, n_fine, n0, n, d_K);
-    FM_TRY(fmg_batch(H, *prm, d_qf, d_qc, nullptr, nullptr, as_stream(stream)));
+    // per-launch profiling creates events and counters: off for this call
+    const bool prof = ctx->prof.active;
+    ctx->prof.active = false;
+    const fm_status rs = fmg_batch(H, *prm, d_qf, d_qc, nullptr, nullptr, as_stream(stream));
+    ctx->prof.active = prof;
+    FM_TRY(rs);
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
 }

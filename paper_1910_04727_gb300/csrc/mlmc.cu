@@ -41,7 +41,12 @@ __global__ void __launch_bounds__(kSumBlock) k_level_partials(size_t S, const do
         const double c = coarse ? qc[i] : 0.0;
         const double y = f - c;
         neumaier_add(acc[0], acc[1], y);
-        neumaier_add(acc[2], acc[3], y * y);
+        // y^2 with its rounding error (exact product): the pair then holds
+        // the sum of the exact squares, which the variance needs when
+        // |mean| >> sd
+        const double y2 = y * y;
+        neumaier_add(acc[2], acc[3], y2);
+        acc[3] += fma(y, y, -y2);
         neumaier_add(acc[4], acc[5], f);
         neumaier_add(acc[6], acc[7], coarse ? c : 0.0);
     }

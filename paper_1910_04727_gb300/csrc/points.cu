@@ -9,8 +9,10 @@
 
 namespace fm {
 
+// xi (nullable): the normals; words (nullable): the raw 64-bit Philox words
+// they come from, in the same [sample][dim] layout.
 __global__ void k_mc_points(uint64_t seed, uint32_t level, uint64_t first, uint32_t n,
-                            uint32_t dim, double* __restrict__ xi) {
+                            uint32_t dim, double* __restrict__ xi, uint64_t* __restrict__ words) {
     const uint32_t blocks = (dim + 3) / 4;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (uint64_t)n * blocks) return;
@@ -22,8 +24,11 @@ __global__ void k_mc_points(uint64_t seed, uint32_t level, uint64_t first, uint3
     for (int lane = 0; lane < 4; ++lane) {
         uint32_t k = 4 * b + lane;
         if (k < dim) {
-            double u = ((double)(w.v[lane] >> 11) + 0.5) * 0x1p-53;
-            xi[(size_t)s * dim + k] = normcdfinv(u);
+            if (words) words[(size_t)s * dim + k] = w.v[lane];
+            if (xi) {
+                const double u = ((double)(w.v[lane] >> 11) + 0.5) * 0x1p-53;
+                xi[(size_t)s * dim + k] = normcdfinv(u);
+            }
         }
     }
 }
@@ -141,7 +146,22 @@ extern "C" fm_status mc_points(fm_ctx* ctx, uint32_t level, uint64_t first, uint
     const int bs = 256;
     FM_TIMED(ctx, kFamPoints, as_stream(stream), 8.0 * n * dim, 0.0,
              k_mc_points<<<(unsigned)((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
-                 ctx->cfg.seed, level, first, n, dim, d_xi));
+                 ctx->cfg.seed, level, first, n, dim, d_xi, nullptr));
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
+}
+
+extern "C" fm_status mc_words(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, uint32_t dim,
+                              uint64_t* d_words, void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "mc_words: null context");
+    FM_CHECK_ARG(ctx, dim >= 1 && dim <= 4096, "mc_words: dim must be in [1, 4096]");
+    FM_CHECK_ARG(ctx, n == 0 || d_words != nullptr, "mc_words: null output");
+    if (n == 0) return FM_OK;
+    const uint64_t threads = (uint64_t)n * ((dim + 3) / 4);
+    const int bs = 256;
+    FM_TIMED(ctx, kFamPoints, as_stream(stream), 8.0 * n * dim, 0.0,
+             k_mc_points<<<(unsigned)((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+                 ctx->cfg.seed, level, first, n, dim, nullptr, d_words));
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
 }

@@ -55,3 +55,35 @@ def test_create_rejects_bad_config_without_touching_the_gpu(lib_path):
     cfg = _lib.FmConfig(2, 12, 4, 8, 1.0, 0.3, 1.0, 0.0, 2, 2, 2, 0, 0, 1, 0)    # 12 != 4*2^m
     assert L.fm_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.FM_EINVAL
     assert not h.value
+
+
+def _dd(x):
+    """(hi, lo) doubles with hi + lo = the rational x to about 2^-106 relative."""
+    hi = float(x)
+    return hi, float(x - __import__("fractions").Fraction(hi))
+
+
+@pytest.mark.parametrize("mean,sd", [(1.0, 0.5), (1e4, 1e-3), (-3e6, 0.5), (0.0, 1e-9)])
+def test_level_stats_from_exact_sums(lib_path, mean, sd):
+    """fm_level_stats (host only) on level sums holding the exact sums of Y
+    and Y^2 as (sum, compensation) pairs: mean and Bessel-corrected variance
+    agree with exact rational arithmetic, even with mean^2 / var near 1e14,
+    where S2 - S1^2/n in plain doubles keeps about two digits."""
+    from fractions import Fraction
+    import numpy as np
+    from paper_1910_04727_gb300 import _lib
+    L = _lib.load(lib_path)
+    y = mean + sd * np.random.default_rng(3).standard_normal(1000)
+    s1 = sum(Fraction(v) for v in y)
+    s2 = sum(Fraction(v) * Fraction(v) for v in y)
+    n = len(y)
+    cell = _lib.FmLevelSums()
+    cell.sum_y[0], cell.sum_y[1] = _dd(s1)
+    cell.sum_y2[0], cell.sum_y2[1] = _dd(s2)
+    cell.count = n
+    st = _lib.FmLevelStat()
+    assert L.fm_level_stats(ctypes.byref(cell), ctypes.byref(st)) == 0
+    want_var = (s2 - s1 * s1 / n) / (n - 1)
+    assert abs(st.mean - float(s1 / n)) <= 1e-15 * abs(float(s1 / n)) + 1e-300
+    assert abs(Fraction(st.var) - want_var) <= Fraction(1, 10 ** 12) * want_var
+    assert L.fm_level_stats(None, ctypes.byref(st)) == _lib.FM_EINVAL

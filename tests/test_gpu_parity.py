@@ -50,6 +50,50 @@ def test_mc_points_match_oracle(small):
         np.testing.assert_allclose(xi, ref, rtol=1e-13, atol=1e-15)
 
 
+def test_mc_philox_words_bit_exact(small):
+    """The raw 64-bit words of the MC streams equal the oracle's Philox4x64-10
+    words bit for bit: over a million counters at level 0, on other levels,
+    and on sample indices near 2^40 (the counter's second word)."""
+    ctx, _ = small
+    for level, first, n, dim in [(0, 0, 16384, 64), (3, 12345, 999, 37), (11, 2 ** 40 - 5, 1000, 24),
+                                 (12, 2 ** 40 + 3, 257, 128)]:
+        w = ctx.mc_words(level, first, n, dim).cpu().numpy().view(np.uint64)
+        np.testing.assert_array_equal(w, OL.mc_words(77, level, first, n, dim))
+
+
+def test_mc_points_are_the_inverse_normal_of_their_words(small):
+    """u = ((w >> 11) + 1/2) 2^-53 of the very words the kernel drew: the
+    normals are the oracle's inverse normal of those u to a few ulp."""
+    ctx, _ = small
+    w = ctx.mc_words(2, 777, 4096, 24).cpu().numpy().view(np.uint64)
+    xi = ctx.mc_points(2, 777, 4096, 24).cpu().numpy()
+    u = ((w >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    ref = OL.norminv(u)
+    np.testing.assert_allclose(xi, ref, rtol=1e-13, atol=1e-15)
+
+
+def test_level_stats_keep_the_variance_when_the_mean_dominates(fm):
+    """sigma^2 = 1e-12: Q is 1 + O(1e-6), so mean^2 / var is about 1e12 and
+    S2 - S1^2/n cancels 12 digits.  The library's level statistics (exact
+    squares in the sums, double-double fold) match a two-pass fsum variance
+    of the per-sample outputs; the naive double formula misses by ~1e-4."""
+    import math
+    basis = okl.KLBasis(16, 8, 1e-12, 0.3, q=16)
+    ctx = fm.Context(1, 16, 8, sigma2=1e-12, lam=0.3, seed=5)
+    ctx.kl_basis_set(basis.B_ref)
+    sums = ctx.new_sums()
+    qf, _ = ctx.mlmc_sample_level(0, 0, 50000, -1, sums=sums[0], want_q=True)
+    torch.cuda.synchronize()
+    q = qf.cpu().numpy()
+    mean, var, n, _, _ = ctx.read_sums(sums[0])
+    m = math.fsum(q) / len(q)
+    v = math.fsum((x - m) ** 2 for x in q) / (len(q) - 1)
+    assert n == 50000
+    assert abs(mean - m) <= 1e-15 * abs(m)
+    assert v > 0 and abs(var - v) <= 1e-9 * v, (var, v)
+    ctx.close()
+
+
 def test_sobol_direction_numbers_bit_exact(small):
     ctx, _ = small
     np.testing.assert_array_equal(ctx.sobol_direction_numbers(), OL.sobol_direction_numbers(24))

@@ -138,3 +138,36 @@ def test_philox_word_inputs_match_fp64_points(ctx):
     # and the oracle network on the same FP64 points
     ref, _ = omlp.forward(_to_oracle(p), xi.cpu().numpy(), rounding=True)
     assert np.median(np.abs(a - (0.5 + ref))) < 1e-5
+
+
+def test_surrogate_level_is_unbiased_over_many_seeds():
+    """E[S] + E[Q_0 - S] = E[Q_0] holds only if the S level and level 0 apply
+    the same map from a sample to S.  For 24 seeds (each its own Philox
+    streams and its own trained network) the control-variate estimate of
+    E[Q_0] is compared with a plain level-0 mean on disjoint samples of the
+    same seed: the z-scores must average to 0 within 3/sqrt(24) and none
+    may exceed 4."""
+    import paper_1910_04727_gb300 as fm
+    basis = okl.KLBasis(32, M, 1.0, 0.3, q=32)
+    z = []
+    for seed in range(24):
+        c = fm.Context(2, 16, M, sigma2=1.0, lam=0.3, seed=1000 + seed)
+        c.kl_basis_set(basis.B_ref)
+        c.surrogate_train(n_train=4096, epochs=8, lr=3e-3, seed=seed, batch=256)
+        c.surrogate_enable(True)
+        s_sums, r_sums, p_sums = c.new_sums(), c.new_sums(), c.new_sums()
+        c.mlmc_sample_level(-1, 0, 1 << 18, -1, sums=s_sums[0])
+        c.mlmc_sample_level(0, 0, 16384, -1, sums=r_sums[0])
+        c.surrogate_enable(False)
+        # plain level-0 samples with ids disjoint from the ones above
+        c.mlmc_sample_level(0, 1 << 30, 16384, -1, sums=p_sums[0])
+        torch.cuda.synchronize()
+        ms, vs, ns = c.read_sums(s_sums[0])[:3]
+        mr, vr, nr = c.read_sums(r_sums[0])[:3]
+        mp, vp, npl = c.read_sums(p_sums[0])[:3]
+        z.append(((ms + mr) - mp) / np.sqrt(vs / ns + vr / nr + vp / npl))
+        c.close()
+    z = np.array(z)
+    print("z-scores:", np.round(z, 2))
+    assert abs(z.mean()) < 3.0 / np.sqrt(len(z))
+    assert np.max(np.abs(z)) < 4.0

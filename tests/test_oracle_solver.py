@@ -178,6 +178,27 @@ def test_correction_operators_from_child_means_keep_the_cycle_contracting():
     assert max(rho[1]) < 0.6          # child means: all contract
 
 
+@pytest.mark.parametrize("nc", [2, 4, 16])
+def test_child_geometric_mean_of_a_log_affine_field_is_its_value_at_the_parent_centre(nc):
+    """K = exp(a + b x + c y) at the cell centres of grid 2 nc.  The four
+    children of a coarse cell are placed symmetrically about its centre, so
+    their geometric mean is exp(a + b X + c Y) at the coarse centre (X, Y),
+    whatever a, b, c.  An arithmetic mean, a wrong set of children, or
+    swapped row / column indices all miss this value."""
+    nf = 2 * nc
+    a, b, c = 0.3, 2.1, -1.4
+    x = (np.arange(nf) + 0.5) / nf
+    Kf = np.exp(a + b * x[None, :] + c * x[:, None])      # [j][i], x fastest
+    X = (np.arange(nc) + 0.5) / nc
+    want = np.exp(a + b * X[None, :] + c * X[:, None])
+    got = L.geometric_children(Kf)
+    np.testing.assert_allclose(got, want, rtol=2e-15, atol=0)
+    # the children are the 2x2 block of the parent: a field constant on
+    # each block (and different between blocks) passes through unchanged
+    r = np.random.default_rng(5).uniform(0.5, 2.0, (nc, nc))
+    np.testing.assert_allclose(L.geometric_children(np.kron(r, np.ones((2, 2)))), r, rtol=2e-15)
+
+
 def test_fmg_two_vcycles_is_close_to_converged_for_smooth_fields():
     K = W.smooth_lognormal_field(64, S=1, sigma=1.0, tag=20)[0]
     q2 = L.fmg_solve(K)[0]

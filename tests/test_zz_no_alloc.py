@@ -55,3 +55,40 @@ def test_static_scratch_solve_rejects_batches_beyond_its_array():
     st = L.fmg_solve_batch_static(ctx._h, 256, 64, _ptr(K), C.byref(prm), _ptr(qf), None, None)
     assert st == _lib.FM_EINVAL
     assert b"static scratch" in L.fm_last_error(ctx._h)
+
+
+def test_static_scratch_solve_refuses_the_energy_step():
+    # the energy-optimal step keeps per-sample dot products that the static
+    # layout has no room for: the call must refuse it before any launch
+    import paper_1910_04727_gb300 as fm
+    from paper_1910_04727_gb300 import _lib
+    L = _lib.load()
+    ctx = fm.Context(2, 32, 8, seed=3)
+    K = torch.ones((4, 32, 32), dtype=torch.float64, device="cuda")
+    qf = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    prm = ctx.solve_params(energy_step=1)
+    st = L.fmg_solve_batch_static(ctx._h, 32, 4, _ptr(K), C.byref(prm), _ptr(qf), None, None)
+    assert st == _lib.FM_EINVAL
+    assert b"energy" in L.fm_last_error(ctx._h)
+    torch.cuda.synchronize()
+    assert torch.isnan(qf).all()
+
+
+def test_static_scratch_solve_leaves_an_open_profile_alone():
+    # with a profile open the call still allocates nothing: it times nothing
+    import paper_1910_04727_gb300 as fm
+    from paper_1910_04727_gb300 import _lib
+    L = _lib.load()
+    ctx = fm.Context(2, 32, 8, seed=3)
+    K = torch.tensor(W.smooth_lognormal_field(32, S=5, tag=202), device="cuda")
+    ref_qf, _, _ = ctx.fmg_solve_batch(K, kernel=LEVELWISE)
+    qf = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.profile_begin()
+    prm = ctx.solve_params()
+    st = L.fmg_solve_batch_static(ctx._h, 32, 5, _ptr(K), C.byref(prm), _ptr(qf), None,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, L.fm_last_error(ctx._h)
+    prof = ctx.profile_end()
+    assert sum(v["launches"] for v in prof.values()) == 0
+    a, b = qf.cpu().numpy(), ref_qf.cpu().numpy()
+    assert np.max(np.abs(a - b) / np.abs(b)) < 1e-10
