@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-qmc-leg", action="store_true", help="skip timing the randomized-QMC estimator")
+    ap.add_argument("--detail-out", default=None,
+                    help="write the full record (every leg, every kernel family) to this JSON file")
+    ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
+                    help="run one small isolated kernel case (for a profiler) instead of the benchmark")
     return ap.parse_args()
 
 
@@ -151,6 +155,28 @@ def oracle_level_seconds(wl, budget_s, converged):
     return np.array(per), cores, counts
 
 
+def oracle_level_seconds_1core(wl, budget_s, converged):
+    """Seconds per sample of the oracle on one host core, per level, from a
+    bounded sample (about budget_s seconds in total)."""
+    from oracle import kl as okl
+    from oracle import mlmc as omlmc
+    basis = okl.KLBasis(wl.n_ref, wl.M, wl.sigma2, wl.lam, q=32 if wl.M <= 128 else 0)
+    s = omlmc.FMGSampler(wl.levels, basis, seed=wl.seed, prm=oracle_params(converged), nthreads=1)
+    per, counts = [], []
+    share = budget_s / len(wl.levels)
+    for l in range(len(wl.levels)):
+        k = 2
+        t0 = time.perf_counter()
+        s(l, 0, k)
+        dt = time.perf_counter() - t0
+        k2 = int(min(256, max(2, k * share / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        s(l, k, k2)
+        per.append((time.perf_counter() - t0) / k2)
+        counts.append(k2)
+    return np.array(per), counts
+
+
 def oracle_surrogate_seconds(M, budget_s=4.0):
     """Seconds of the oracle network (FP64, numpy) per S evaluation and per
     training step (batch 256: loss, gradients, Adam), from a bounded sample."""
@@ -233,13 +259,17 @@ def make_ctx(fm, wl, rank, form):
                       converged=f["converged"], tol=SOLVE_TOL, qtol=SOLVE_QTOL, max_cycles=200)
 
 
-# DRAM read + write of one FP32 colour launch per cell, measured by ncu
-COLOUR_DRAM_BYTES_PER_CELL_F32 = (1.341171e9 + 0.251231e9) / (64 << 20)
-# DRAM read + write of one FP32 strip call (two sweeps) per cell, measured by
-# ncu on 64 Mi cells of 256 x 256 (profiles/rbgs_strip_synthetic_256.md),
-# against its 24 algorithmic bytes per cell
+# DRAM read + write of one FP32 strip call (two red-black sweeps) per cell:
+# ncu's dram__bytes_read.sum + dram__bytes_write.sum of one k_rbgs_strip
+# launch over 64 Mi cells (1024 samples of 256 x 256, synthetic operands)
+# was 1.72 GB, i.e. 25.6 B per cell against the kernel's 24 algorithmic
+# bytes per cell (read p, b, D, Te, Tn once, write p once)
 STRIP_DRAM_BYTES_PER_CELL_F32 = 1.72e9 / (64 << 20)
 STRIP_ALG_BYTES_PER_CELL_F32 = 24.0
+
+# FP64 rate of GB300 (nominal, TFLOP/s): the denominator of the FP64 part of
+# the resident kernel's ALU view
+FP64_PEAK_TFLOPS = 1.25
 
 # randomized QMC (Algorithm 2): 32 points per shift and level to start, 16 digital shifts
 QMC_PILOT = 32
@@ -297,6 +327,29 @@ def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=Fals
     prof = ctx.profile_end() if profile else None
     clk = clocks.stop() if clocks else None
     return times, results, prof, clk
+
+
+def _case_resident(torch, fm, level, S):
+    """S level-`level` samples of the five-level workload in the mixed
+    converged form, solved three times on the resident schedule."""
+    wl = W.WORKLOADS["fmg_mlmc5"]
+    ctx = make_ctx(fm, wl, 0, "mixed")
+    ctx.kl_basis_build(q=wl.kl_q)
+    K = ctx.kl_field_batch(level, ctx.mc_points(level, 0, S))
+    for _ in range(3):
+        qf, qc, _ = ctx.fmg_solve_batch(K, kernel=2)
+    torch.cuda.synchronize()
+    ctx.sync()
+    print("kernel case: %d samples of %dx%d, mean Q^f %.6f" % (S, K.shape[-1], K.shape[-1], float(qf.mean())))
+    ctx.close()
+
+
+# one small isolated launch pattern per case, for a profiler (-k/-c select it)
+KERNEL_CASES = {
+    "fmg_resident_mixed16": lambda torch, fm: _case_resident(torch, fm, 0, 65536),
+    "fmg_resident_mixed32": lambda torch, fm: _case_resident(torch, fm, 1, 16384),
+    "fmg_resident_mixed64": lambda torch, fm: _case_resident(torch, fm, 2, 4096),
+}
 
 
 UNEVEN_COUNTS = [3075, 769, 192, 48, 12]   # 4096 samples, N_l ~ 4^-l (optimal ratio for beta ~ 2)
@@ -428,15 +481,21 @@ def run_native(args, wl, eps):
     # table keeps the schedule the same under a profiler
 
     clocks = ClockSampler(local)
-    times, results, prof, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
-                                               profile=True, clocks=clocks,
-                                               dist=dist if world > 1 else None, form=args.form)
+    times, results, _, clk = time_estimates(torch, ctx, eps, args, wl, args.steps, args.warmup, flush,
+                                            profile=False, clocks=clocks,
+                                            dist=dist if world > 1 else None, form=args.form)
     t_total = float(np.sum(times))
     if world > 1:
         t = torch.tensor([t_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_total = float(t.item())
         dist.barrier()
+
+    # kernel families of the same schedule: one more step with a CUDA event
+    # pair around every launch (kept out of the timed steps above)
+    _, prof_results, prof, _ = time_estimates(torch, ctx, eps, args, wl, 1, 0, flush, profile=True,
+                                              form=args.form)
+    same_schedule = [int(x) for x in prof_results[-1]["N"]] == [int(x) for x in results[-1]["N"]]
 
     # the other forms of the same estimate, timed the same way
     others = {}
@@ -445,7 +504,7 @@ def run_native(args, wl, eps):
             continue
         c2 = make_ctx(fm, wl, rank, form)
         c2.kl_basis_set(B_dev)
-        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 2)), 1, flush,
+        ts, rs, _, _ = time_estimates(torch, c2, eps, args, wl, max(1, min(args.steps, 3)), 1, flush,
                                       form=form)
         others[form] = {"value": float(np.mean(ts)), "unit": "s",
                         "estimate": float(np.mean([r["estimate"] for r in rs])),
@@ -499,93 +558,91 @@ def run_native(args, wl, eps):
     d2h = int(np.mean(rounds) if rounds else 0) * len(wl.levels) * (wl.n_shifts if args.qmc else 1) * 128
 
     hbm, bf16, src = peaks()
-    # dominant kernel family by event-timed device time
+    clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak_fp32_tf = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    # dominant kernel family by event-timed device time in the profiled step
     # (the training graph is a whole replay loop, not one kernel)
     fam, st = max(((k, v) for k, v in prof.items() if k != "mlp_train_graph"), key=lambda kv: kv[1]["ms"])
-    per_launch_ms = st["ms"] / st["launches"]
     ach = st["bytes"] / (st["ms"] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None, "peak_source": src}
-    if fam == "rbgs_smoother" and FORMS[args.form]["precision"] == 1:
-        # DRAM bytes of one FP32 colour launch per cell (ncu, 64 Mi cells:
-        # profiles/rbgs_smoother_shapes_synthetic_256.md) over its 12
-        # algorithmic bytes, scaled to the average timed launch
-        roof["traffic"] = st["bytes"] / st["launches"] * COLOUR_DRAM_BYTES_PER_CELL_F32 / 12.0
-        roof["traffic_source"] = "ncu dram bytes per cell (64 Mi-cell capture) x cells per launch"
+    roof = {"bound": "hbm", "kernel": fam, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": None,
+            "peak_source": src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "launches": st["launches"], "avg_launch_ms": round(st["ms"] / st["launches"], 4)}
     if fam == "fmg_resident":
-        # the whole FMG of a sample in shared memory: bound by the SM's
-        # arithmetic issue and latency, not HBM.  Flops are counted by the
-        # kernel (V-cycles and residual tests of every sample); the peak is
-        # GB300's FP32 FMA rate, 152 SMs x 128 lanes x 2 flops at the
-        # sampled SM clock.
-        clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak_tf = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-        ach_tf = st["flops"] / (st["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": fam, "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach_tf / peak_tf, "traffic": None,
-                "peak_source": "FP32 FMA lanes x clock (152 SMs x 128 x 2 flops x %.0f MHz)" % clk_mhz,
-                "note": "latency-bound: small grids in shared memory, a barrier per half-sweep"}
-    elif fam in ("kl_gemm_exp", "mlp_gemm"):
-        roof["bound"] = "alu"
-        roof["note"] = "achieved = algorithmic HBM bytes / time; the kernel is latency bound"
-    roof["launches"] = st["launches"]
-    roof["avg_launch_ms"] = per_launch_ms
+        # the whole FMG of a sample in shared memory.  achieved = the byte
+        # model of the level-wise kernels (16 B a cell per FP32 sweep, 13 B
+        # residual + restriction, 9 B correction, 20 B per FP64 residual test;
+        # 310 B per finest cell for a fixed FMG with nu0 = 2) for the cycles
+        # the kernel ran, over its event time.  Its own DRAM traffic is only K
+        # in and the QoIs out.  The ALU view beside it: FP32 flops against
+        # the FP32 FMA lanes, FP64 flops against GB300's FP64 rate.
+        f64 = st.get("flops_fp64", 0.0)
+        f32 = st["flops"] - f64
+        sec = st["ms"] / 1e3
+        roof["bytes_model"] = "streaming byte model of the level-wise kernels (310 B per finest cell for FMG nu0=2)"
+        roof["alu"] = {"fp32_tflops": round(f32 / sec / 1e12, 3), "fp32_peak": round(peak_fp32_tf, 1),
+                       "fp64_tflops": round(f64 / sec / 1e12, 4), "fp64_peak": FP64_PEAK_TFLOPS,
+                       "fp64_frac": round(f64 / sec / 1e12 / FP64_PEAK_TFLOPS, 4)}
     # the HBM-bound kernels of the level-wise solves, beside the dominant one:
-    # achieved = algorithmic bytes / event time over the timed steps
+    # achieved = algorithmic bytes / event time over the profiled step
     hbm_kernels = {}
-    for k in ("rbgs_strip", "residual_restrict", "rbgs_smoother"):
+    for k in ("rbgs_strip", "residual_restrict", "rbgs_smoother", "rbgs_tile"):
         if k not in prof or prof[k]["ms"] <= 0:
             continue
         v = prof[k]
         a = v["bytes"] / (v["ms"] / 1e3) / 1e9
-        e = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s", "frac": round(a / hbm, 4),
-             "launches": v["launches"], "avg_launch_ms": round(v["ms"] / v["launches"], 4), "traffic": None}
+        e = {"achieved": round(a, 1), "frac": round(a / hbm, 4), "launches": v["launches"],
+             "avg_launch_ms": round(v["ms"] / v["launches"], 4)}
         if k == "rbgs_strip" and FORMS[args.form]["precision"] == 1:
-            e["traffic"] = v["bytes"] / v["launches"] * STRIP_DRAM_BYTES_PER_CELL_F32 / STRIP_ALG_BYTES_PER_CELL_F32
-            e["traffic_source"] = "ncu dram bytes per cell (64 Mi-cell capture of the plain strip) x cells per launch"
+            e["traffic"] = round(v["bytes"] / v["launches"] * STRIP_DRAM_BYTES_PER_CELL_F32
+                                 / STRIP_ALG_BYTES_PER_CELL_F32, 1)
         hbm_kernels[k] = e
     families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                     "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
                     "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3)} for k, v in prof.items()}
-    total_launches = int(sum(v["launches"] for v in prof.values()))
+    launches_per_step = int(sum(v["launches"] for v in prof.values()))
 
     ests = [r["estimate"] for r in results]
+    value = t_total / args.steps
+    fp64_fmg2 = others.get("fp64_fmg2", {}).get("value")
+    fp64_conv = others.get("fp64_converged", {}).get("value")
     out = {
         "metric": METRIC,
-        "value": t_total / args.steps,
+        "value": value,
         "unit": "s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_total / args.steps,
+        "ms_per_step": 1e3 * value,
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": ("f32+f64" if FORMS[args.form]["precision"] == 1 else "f64") + ("+bf16" if sur else ""),
         "data": "synthetic (seeded Philox KL coefficients, KL basis built on the GPU)",
+        "plain_fp64_fmg2_s": fp64_fmg2,
+        "plain_fp64_converged_s": fp64_conv,
+        "speedup_vs_fp64_fmg2": (fp64_fmg2 / value) if fp64_fmg2 else None,
+        "speedup_vs_fp64_converged": (fp64_conv / value) if fp64_conv else None,
         "config": {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2,
                    "lambda": wl.lam, "eps": eps, "sampler": "qmc" if args.qmc else "mc",
-                   "fmg": "4x4 exact, nu0=%d V(%d,%d) RB-GS" % (wl.nu0, wl.nu1, wl.nu2),
-                   "form": args.form, "tol": SOLVE_TOL, "qtol": SOLVE_QTOL, "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "captured_variance": captured},
+                   "form": args.form, "tol": SOLVE_TOL, "qtol": SOLVE_QTOL,
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "smoother_hbm": hbm_kernels,
+        "e2e": {"value": float(np.mean(e2e_times)) if e2e_times else None, "unit": "s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
         "estimate": float(np.mean(ests)),
         "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in results]))),
         "N_per_level": [int(x) for x in results[-1]["N"]],
-        "samples_per_s_per_level": [float(n / t) if t > 0 else None for n, t in
+        "samples_per_s_per_level": [round(float(n / t), 1) if t > 0 else None for n, t in
                                     zip(results[-1]["N"], results[-1]["level_seconds"])],
-        "other_forms": others,
-        "qmc": qmc_forms,
-        "uneven_batch": uneven,
-        "fmg_vs_standard_mlmc": standard,
-        "roofline": roof,
-        "hbm_kernels": hbm_kernels,
-        "kernel_families": families,
-        "gpu_launches": total_launches,
-        "e2e": {"value": float(np.mean(e2e_times)) if e2e_times else None, "unit": "s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "clocks": clk,
     }
+    detail = {"other_forms": others, "qmc": qmc_forms, "uneven_batch": uneven, "fmg_vs_standard_mlmc": standard,
+              "kernel_families": families, "profiled_step_same_schedule": same_schedule,
+              "captured_variance": captured, "step_seconds": times}
     if sur:
         r = results[-1]
         sr = {"train": {k: (float(v) if isinstance(v, float) else v) for k, v in r["train"].items()},
@@ -598,28 +655,43 @@ def run_native(args, wl, eps):
             sr["var_q0"] = plain["V_per_level"][0]
             sr["variance_reduction_level0"] = plain["V_per_level"][0] / max(float(r["V"][0]), 1e-300)
             sr["plain_estimate"] = plain["estimate"]
-            sr["plain_N_per_level"] = plain["N_per_level"]
             sr["difference_in_sigmas"] = abs(out["estimate"] - plain["estimate"]) / np.sqrt(
                 np.mean([x["var_estimator"] for x in results]) + plain["var_estimator"])
-        out["surrogate"] = sr
+        detail["surrogate"] = sr
+        out["surrogate"] = {"N_s": sr["N_s"], "variance_reduction_level0": sr.get("variance_reduction_level0"),
+                            "difference_in_sigmas": sr.get("difference_in_sigmas"),
+                            "train_corr": sr["train"].get("corr")}
+    if uneven:
+        out["uneven_batch"] = {"samples": sum(UNEVEN_COUNTS), "seconds_uneven_graph": uneven["seconds_uneven_graph"],
+                               "seconds_per_level_calls": uneven["seconds_per_level_calls"],
+                               "identical_results": uneven["identical_results"]}
+    if standard:
+        out["fmg_vs_standard_mlmc_saving"] = standard["saving_of_fmg_mlmc"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         conv = FORMS[args.form]["converged"]
         per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds, conv)
+        per1, counts1 = oracle_level_seconds_1core(wl, args.cpu_seconds / 2, conv)
         N = results[-1]["N"]
         t_cpu = float(np.sum(per * N))
-        sample = ("oracle FMG-MLMC samples per level %s (%s) timed on %d threads; seconds per sample x "
-                  "the GPU run's N_l (extrapolated)" % (counts, "FP64 V-cycles to %g" % SOLVE_TOL if conv
-                                                        else "2 V(2,2) per stage", cores))
+        t_cpu1 = float(np.sum(per1 * N))
+        sample = ("oracle FMG-MLMC samples per level %s (%s) timed on %d threads, %s on 1 thread; seconds "
+                  "per sample x the GPU run's N_l (extrapolated)" % (
+                      counts, "FP64 V-cycles to %g" % SOLVE_TOL if conv else "2 V(2,2) per stage", cores, counts1))
         if sur:
             r = results[-1]
             pe, ps, ks = oracle_surrogate_seconds(wl.M)
             steps = int(r["train"]["steps"])
-            t_cpu += per[0] * SURROGATE_TRAIN["n_train"] + ps * steps + pe * (r["N_s"] + r["N"][0])
+            extra = pe * (r["N_s"] + r["N"][0]) + ps * steps
+            t_cpu += per[0] * SURROGATE_TRAIN["n_train"] + extra
+            t_cpu1 += per1[0] * SURROGATE_TRAIN["n_train"] + extra
             sample += ("; surrogate: %d training pairs at the level-0 rate, %d timed oracle training steps "
                        "extrapolated to %d, 8192 timed oracle evaluations extrapolated to N_S + N_0"
                        % (SURROGATE_TRAIN["n_train"], ks, steps))
         out["cpu_baseline"] = {"value": t_cpu, "unit": "s", "cores": cores, "kind": "oracle",
-                               "sample": sample}
+                               "value_1core": t_cpu1, "sample": sample}
+    if args.detail_out and rank == 0:
+        with open(args.detail_out, "w") as f:
+            json.dump(dict(out, **detail), f, indent=1)
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -672,6 +744,12 @@ def run_reference(args, wl, eps):
 
 def main():
     args = parse()
+    if args.kernel_case:
+        import torch
+        import paper_1910_04727_gb300 as fm
+        torch.cuda.set_device(0)
+        KERNEL_CASES[args.kernel_case](torch, fm)
+        return
     wl = W.WORKLOADS[args.workload]
     eps = args.eps if args.eps is not None else wl.eps
     if args.impl == "reference":

@@ -464,8 +464,19 @@ fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* opts, int32
 
 /* Synchronise the device and report device-side failures of earlier
  * asynchronous calls on ctx: FM_ETIMEOUT if a bounded wait inside a kernel
- * ran out (its output is then invalid), FM_ECUDA for a CUDA error. */
+ * ran out (its output is then invalid; the flag is cleared once reported),
+ * FM_ECUDA for a CUDA error.  Every wait of the tensor-core kernels on an
+ * mbarrier (TMA tiles, MMA completion) gives up after 50 ms of wall time;
+ * the kernel then waits, again bounded, for the copies it issued, frees its
+ * tensor memory and returns. */
 fm_status fm_sync(fm_ctx* ctx);
+
+/* Check of the failure path above, not part of the method: one CTA waits,
+ * with the same bounded wait, on an mbarrier that nothing arrives on, for
+ * budget_ns (0 .. 1e9) of wall time.  The wait runs out, the kernel sets the
+ * context's device flag and returns, and the next fm_sync reports
+ * FM_ETIMEOUT; the context stays usable.  Asynchronous on `stream`. */
+fm_status fm_wait_check(fm_ctx* ctx, int64_t budget_ns, void* stream);
 
 /* ---------------------------------------------------------------- surrogate */
 
@@ -543,8 +554,11 @@ typedef struct {
     int32_t family;       /* family index */
     int64_t launches;
     double ms;            /* sum of event-timed launch durations */
-    double bytes;         /* sum of algorithmic bytes */
+    double bytes;         /* sum of algorithmic bytes (the resident FMG: the byte model of the
+                             V-cycles and residual tests it ran, as if each grid operation
+                             streamed its operands through HBM) */
     double flops;         /* sum of algorithmic flops */
+    double flops_fp64;    /* the part of flops done in FP64 (kernels that count their own work) */
 } fm_kernel_stat;
 
 /* Close the profile: synchronises the device, returns one entry per family

@@ -319,7 +319,7 @@ class Context:
         out = {}
         for s in stats[:n.value]:
             out[self._L.fm_kernel_family_name(s.family).decode()] = dict(
-                launches=s.launches, ms=s.ms, bytes=s.bytes, flops=s.flops)
+                launches=s.launches, ms=s.ms, bytes=s.bytes, flops=s.flops, flops_fp64=s.flops_fp64)
         return out
 
     # ----------------------------------------------------------- surrogate

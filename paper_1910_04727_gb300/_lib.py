@@ -26,7 +26,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
-           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats"]
+           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check"]
 
 
 class FmConfig(C.Structure):
@@ -65,7 +65,7 @@ class FmEstimateOpts(C.Structure):
 
 class FmKernelStat(C.Structure):
     _fields_ = [("family", C.c_int32), ("launches", C.c_int64), ("ms", C.c_double),
-                ("bytes", C.c_double), ("flops", C.c_double)]
+                ("bytes", C.c_double), ("flops", C.c_double), ("flops_fp64", C.c_double)]
 
 
 class FmTrainOpts(C.Structure):
@@ -151,6 +151,7 @@ def load(path=None):
         "fm_profile_end": (I32, [P, P, I32, C.POINTER(I32)]),
         "fm_kernel_family_name": (C.c_char_p, [I32]),
         "fm_sync": (I32, [P]),
+        "fm_wait_check": (I32, [P, I64, P]),
         "fmg_solve_batch_static": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P]),
         "surrogate_param_count": (I64, [P]),
         "surrogate_params": (I32, [P, P, I32]),

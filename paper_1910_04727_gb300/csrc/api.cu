@@ -107,7 +107,9 @@ extern "C" fm_status fm_sync(fm_ctx* ctx) {
         int e = 0;
         FM_CUDA_TRY(ctx, cudaMemcpy(&e, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
-            set_error(ctx, "a bounded device-side wait of the tensor-core field synthesis ran out");
+            // reported once: the flag is cleared for the calls that follow
+            FM_CUDA_TRY(ctx, cudaMemset(ctx->tc.err, 0, sizeof(int)));
+            set_error(ctx, "a bounded device-side wait of the tensor-core kernels ran out");
             return FM_ETIMEOUT;
         }
     }

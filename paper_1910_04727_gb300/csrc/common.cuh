@@ -194,8 +194,11 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Event-pair timing around one launch of `family` (no-op unless profiling).
 int prof_start(fm_ctx* ctx, int family, cudaStream_t st);
 void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops);
-// A zeroed device double for record idx that the launched kernel adds its
-// flops to (read at fm_profile_end); null when not profiling.
+// Zeroed device doubles for record idx that the launched kernel adds its own
+// counts to (read at fm_profile_end): [0] flops, [1] the FP64 part of them,
+// [2] algorithmic bytes of the work it ran (0: keep the launch's figure).
+// Null when not profiling.
+constexpr int kCountersPerRecord = 3;
 double* prof_counter(fm_ctx* ctx, int idx);
 
 #define FM_TIMED(ctx, family, st, bytes, flops, ...)          \

@@ -464,7 +464,7 @@ struct ResidentArgs {
     double tol, qtol;
     double *qf, *qc, *p_out;
     int32_t* status;
-    double* flops;   // nullable: the launch adds its solver flops here (profiling)
+    double* flops;   // nullable (profiling): [0] solver flops, [1] their FP64 part, [2] model bytes
 };
 
 // Solver flops of one V(nu1, nu2) cycle from grid k down: per grid j >= 1,
@@ -477,6 +477,20 @@ __device__ __forceinline__ double vcycle_flops(int n0, int k, int nu1, int nu2) 
         f += c * (10.0 * (nu1 + nu2) + 18.0);
     }
     return f;
+}
+
+// Algorithmic bytes of the same cycle in the streaming byte model of the
+// level-wise kernels (each sweep reads p, K, b and writes p: 16 B per cell in
+// FP32; residual + restriction 13 B and prolongation + correction 9 B per
+// fine cell; twice that in FP64), the yardstick the resident kernel's
+// effective bandwidth is quoted against.
+__device__ __forceinline__ double vcycle_bytes(int n0, int k, int nu1, int nu2, int ts) {
+    double b = 0.0;
+    for (int j = 1; j <= k; ++j) {
+        const double c = (double)(n0 << j) * (n0 << j);
+        b += c * (16.0 * (nu1 + nu2) + 22.0) * (ts / 4.0);
+    }
+    return b;
 }
 
 // Shared memory of one CTA: a layout table per group, then each group's data.
@@ -511,6 +525,9 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
         bool ok = true;
         double q_coarse = NAN, q_fine = NAN;
         double work = 0.0;   // solver flops of this sample (V-cycles and residual tests)
+        double work64 = 0.0; // the FP64 part of them
+        double model = 0.0;  // their algorithmic bytes (byte model of the level-wise kernels)
+        constexpr int ts = (int)sizeof(T);
 
         for (int k = 0; k <= m; ++k) {
             const RGrid<T>& g = L.g[k];
@@ -533,6 +550,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 if (k > 0) {
                     for (int it = 0; it < a.nu0; ++it) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
+                    model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                 }
             } else if (!MIXED) {
                 // FP64: V-cycles on the stage problem until the residual or
@@ -542,6 +560,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                     double rr, bb;
                     R::stage_norms(g, tpW, tpE, L.red, rr, bb);
                     work += 14.0 * g.n * g.n;
+                    model += 20.0 * g.n * g.n;
                     const double q = R::stage_outflux(g.te, g.p, g.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
@@ -552,6 +571,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                     }
                     for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
+                    model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                 }
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
@@ -565,6 +585,8 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                     double rr, bb;
                     R::ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
                     work += 14.0 * h.n * h.n;
+                    work64 += 14.0 * h.n * h.n;
+                    model += 20.0 * h.n * h.n;
                     const double q = R::stage_outflux(h.te, h.p, h.n, a.pE, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
@@ -576,6 +598,8 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                     // nu0 FP32 V-cycles on the correction equation per FP64 residual
                     for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2) + (double)h.n * h.n;
+                    work64 += (double)h.n * h.n;
+                    model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                     for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] += (double)g.p[c];
                     R::sync();
                 }
@@ -595,7 +619,11 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             }
         }
         if (R::rank() == 0) {
-            if (a.flops) atomicAdd(a.flops, work);
+            if (a.flops) {
+                atomicAdd(a.flops, work);
+                atomicAdd(a.flops + 1, MIXED ? work64 : work);
+                atomicAdd(a.flops + 2, model);
+            }
             a.qf[s] = q_fine;
             if (a.qc) a.qc[s] = q_coarse;
             if (a.status) a.status[s] = ok ? FM_OK : FM_ENOTCONV;

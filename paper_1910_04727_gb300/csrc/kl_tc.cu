@@ -64,13 +64,16 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0 && lane == 0) {
         // producer: K blocks through a kTcStages-deep ring
+        int issued = 0;
         for (int kb = 0; kb < kblocks; ++kb) {
             const int st = kb % kTcStages, round = kb / kTcStages;
             if (round > 0 && !tc::mbar_wait(&empty[st], (round - 1) & 1, err)) break;
             tc::mbar_arrive_expect_tx(&full[st], kTcABytes + kTcBBytes);
             tc::tma_load_2d(sA + st * kTcABytes, &mapA, &full[st], kb * kTcK, c0);
             tc::tma_load_2d(sB + st * kTcBBytes, &mapB, &full[st], kb * kTcK, s0);
+            ++issued;
         }
+        tc::drain_loads(full, kTcStages, issued, err);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: four K=16 steps per stage, accumulate after the first
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
@@ -110,6 +113,17 @@ __global__ void __launch_bounds__(128, 1)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTcN);
+}
+
+// One CTA waits, with the bounded wait of the kernels above, on an mbarrier
+// that no thread ever arrives on: the wait runs out after budget_ns, sets
+// *err and the kernel returns.
+__global__ void k_wait_check(uint64_t budget_ns, int* __restrict__ err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+    tc::mbar_wait(&bar, 0, err, budget_ns);
 }
 
 // x [n][M] FP64 -> [n][Kp] BF16 in the split layout (hi, lo, hi) or plain (hi).
@@ -220,14 +234,17 @@ fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, do
         }
         ctx->tc.mapB_rows = n;
     }
-    if (!ctx->tc.err) FM_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->tc.err, sizeof(int)));
+    if (!ctx->tc.err) {
+        // the flag stays set until fm_sync reports it
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->tc.err, sizeof(int)));
+        FM_CUDA_TRY(ctx, cudaMemset(ctx->tc.err, 0, sizeof(int)));
+    }
     static bool attr = false;
     if (!attr) {
         FM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_kl_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kTcSmem));
         attr = true;
     }
-    FM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->tc.err, 0, sizeof(int), st));
     k_xi_to_bf16<<<nblk((size_t)n * Mpad), 256, 0, st>>>(n, M, Mpad, ctx->tc.split, d_xi,
                                                         (__nv_bfloat16*)ctx->tc.xi);
     // the coefficient map covers the buffer's capacity; rows >= n are never stored
@@ -243,3 +260,16 @@ fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, do
 }
 
 }  // namespace fm
+
+extern "C" fm_status fm_wait_check(fm_ctx* ctx, int64_t budget_ns, void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_wait_check: null context");
+    FM_CHECK_ARG(ctx, budget_ns >= 0 && budget_ns <= 1000000000LL, "fm_wait_check: budget must be 0 .. 1e9 ns");
+    if (!ctx->tc.err) {
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->tc.err, sizeof(int)));
+        FM_CUDA_TRY(ctx, cudaMemset(ctx->tc.err, 0, sizeof(int)));
+    }
+    cudaStream_t st = fm::as_stream(stream);
+    fm::k_wait_check<<<1, 32, 0, st>>>((uint64_t)budget_ns, ctx->tc.err);
+    FM_CUDA_TRY(ctx, cudaGetLastError());
+    return FM_OK;
+}

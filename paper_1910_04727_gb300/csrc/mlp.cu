@@ -148,13 +148,16 @@ __global__ void __launch_bounds__(128, 1)
     // the setup above overlaps the previous kernel; its outputs are read below
     pdl_wait_then_release();
     if (warp == 0 && lane == 0) {
+        int issued = 0;
         for (int kb = 0; kb < kblocks; ++kb) {
             const int st = kb % kGStages, round = kb / kGStages;
             if (round > 0 && !tc::mbar_wait(&empty[st], (round - 1) & 1, err)) break;
             tc::mbar_arrive_expect_tx(&full[st], kA + kB);
             tc::tma_load_2d(sA + st * kA, &mapA, &full[st], kb * kGk, m0);
             tc::tma_load_2d(sB + st * kB, &mapB, &full[st], kb * kGk, n0);
+            ++issued;
         }
+        tc::drain_loads(full, kGStages, issued, err);
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kGm, BN);
         for (int kb = 0; kb < kblocks; ++kb) {

@@ -33,7 +33,7 @@ constexpr int kMaxCounters = 1 << 14;
 
 double* prof_counter(fm_ctx* ctx, int idx) {
     Profiler& P = ctx->prof;
-    if (idx < 0 || P.counters_used >= kMaxCounters) return nullptr;
+    if (idx < 0 || P.counters_used + kCountersPerRecord > kMaxCounters) return nullptr;
     if (!P.counters) {
         if (cudaMalloc((void**)&P.counters, kMaxCounters * sizeof(double)) != cudaSuccess) {
             P.counters = nullptr;
@@ -42,7 +42,9 @@ double* prof_counter(fm_ctx* ctx, int idx) {
         cudaMemset(P.counters, 0, kMaxCounters * sizeof(double));
     }
     P.records[idx].counter = P.counters_used;
-    return P.counters + P.counters_used++;
+    double* c = P.counters + P.counters_used;
+    P.counters_used += kCountersPerRecord;
+    return c;
 }
 
 void prof_stop(fm_ctx* ctx, int idx, cudaStream_t st, double bytes, double flops) {
@@ -74,7 +76,7 @@ extern "C" fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t 
     ctx->prof.active = false;
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
     fm_kernel_stat acc[kFamilyCount];
-    for (int f = 0; f < kFamilyCount; ++f) acc[f] = fm_kernel_stat{f, 0, 0.0, 0.0, 0.0};
+    for (int f = 0; f < kFamilyCount; ++f) acc[f] = fm_kernel_stat{f, 0, 0.0, 0.0, 0.0, 0.0};
     std::vector<double> counted(ctx->prof.counters_used);
     if (!counted.empty())
         FM_CUDA_TRY(ctx, cudaMemcpy(counted.data(), ctx->prof.counters, counted.size() * sizeof(double),
@@ -85,8 +87,16 @@ extern "C" fm_status fm_profile_end(fm_ctx* ctx, fm_kernel_stat* stats, int32_t 
         fm_kernel_stat& a = acc[r.family];
         a.launches += 1;
         a.ms += ms;
-        a.bytes += r.bytes;
-        a.flops += r.flops + (r.counter >= 0 ? counted[r.counter] : 0.0);
+        if (r.counter >= 0) {
+            // counted by the kernel: [flops, of which FP64, model bytes]
+            const double* c = &counted[r.counter];
+            a.flops += r.flops + c[0];
+            a.flops_fp64 += c[1];
+            a.bytes += c[2] > 0.0 ? c[2] : r.bytes;
+        } else {
+            a.flops += r.flops;
+            a.bytes += r.bytes;
+        }
     }
     int out = 0;
     for (int f = 0; f < kFamilyCount; ++f)

@@ -11,7 +11,16 @@
 namespace fm {
 namespace tc {
 
-constexpr long long kSpinLimit = 1LL << 28;   // ~ seconds of polling
+// Wall-clock budget of one bounded wait (%globaltimer nanoseconds).  A TMA
+// tile or an MMA group lands in microseconds; a wait still open after this
+// long sets the error flag and gives up.
+constexpr uint64_t kWaitBudgetNs = 50ull * 1000 * 1000;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -45,12 +54,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-    for (long long i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+// Wait for the phase with the given parity to complete, for at most
+// budget_ns of wall time; on running out set *err and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          uint64_t budget_ns = kWaitBudgetNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 >= budget_ns) break;
+    }
     atomicExch(err, 1);
     return false;
+}
+
+// Producer side of a `stages`-deep ring whose loads complete on full[]: wait
+// (bounded) until the last load issued into every stage has landed, so no
+// copy is still writing shared memory when the CTA leaves, also after a wait
+// that ran out.  `issued` = loads issued, stage kb % stages for load kb.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int stages, int issued, int* err) {
+    for (int st = 0; st < stages && st < issued; ++st) {
+        const int last = st + stages * ((issued - 1 - st) / stages);
+        mbar_wait(&full[st], (uint32_t)((last / stages) & 1), err);
+    }
 }
 
 // 2-D tiled TMA load into shared memory, completion counted on `bar`.
