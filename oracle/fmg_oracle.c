@@ -19,9 +19,11 @@
  *     GF(2), direction-number recurrence), Gray-code index, digital shift
  *     (the randomized QMC of Sec. 2.4).
  *   - Cell-centred finite volumes for -div(k grad u) = 0 (Eq. 1) on the
- *     unit square, Case II of Table 1: Dirichlet u=pW on the west edge,
- *     u=pE on the east edge, zero flux on north and south; QoI = outflux
- *     through the east edge.
+ *     unit square, both cases of Table 1.  Case II: Dirichlet u=pW on the
+ *     west edge, u=pE on the east edge, zero flux on north and south; QoI =
+ *     outflux through the east edge.  Case I: Dirichlet data on all four
+ *     edges (pW, pE, pS, pN); QoI = u(0.5, 0.5), the mean of the four cells
+ *     that meet at the centre.
  *   - Red-black Gauss-Seidel V(nu1,nu2) cycles, full multigrid over the
  *     same grid hierarchy as the MLMC levels (Sec. 2.5), coefficient
  *     coarsening by injection k^c_{I,J} = k^f_{2I-1,2J-1} (Sec. 2.5, written
@@ -286,10 +288,12 @@ void or_sobol_points(const uint32_t* V, uint32_t dim, uint64_t first, uint32_t n
 }
 
 /* ------------------------------------------------------------------------ */
-/* Finite volumes, Eq. 1 / Table 1 Case II.                                  */
+/* Finite volumes, Eq. 1 / Table 1.                                          */
 /* Interior face: harmonic mean 2 k_a k_b / (k_a + k_b) (unit face over unit */
-/* centre distance on square cells).  West/east boundary face: the centre is */
-/* h/2 from the face, T = 2 k.  North/south: no flow, T = 0.                  */
+/* centre distance on square cells).  Dirichlet boundary face: the centre is */
+/* h/2 from the face, T = 2 k.  West/east faces are Dirichlet in both cases; */
+/* north/south are no-flow (T = 0) in Case II and Dirichlet in Case I (the   */
+/* flag `ns` below).                                                         */
 /* Cell equation: sum_faces T (u_c - u_other) = 0, u_other = boundary value   */
 /* on a Dirichlet face.                                                      */
 /* ------------------------------------------------------------------------ */
@@ -307,27 +311,48 @@ typedef struct {
     int energy_step; /* 1: scale each prolongated correction d by the step
                         (r, d) / (d, A d) that minimises the energy error
                         along d (r the residual it corrects) */
+    int bc_case;     /* Table 1: 2 (default) Case II, 1 Case I */
+    double pS, pN;   /* Case I: Dirichlet values on the south and north edges */
 } or_params;
+
+/* Boundary data of one problem: g[0..3] = west, east, south, north values,
+ * ns = 1 when the north and south edges are Dirichlet (Case I). */
+typedef struct {
+    double g[4];
+    int ns;
+} or_bc;
+
+static or_bc bc_of(const or_params* P)
+{
+    or_bc b;
+    b.g[0] = P->pW;
+    b.g[1] = P->pE;
+    b.ns = (P->bc_case == 1);
+    b.g[2] = b.ns ? P->pS : 0.0;
+    b.g[3] = b.ns ? P->pN : 0.0;
+    return b;
+}
 
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
-static void cell_faces(int n, const double* K, int i, int j,
+static void cell_faces(int n, const double* K, int ns, int i, int j,
                        double* tw, double* te, double* ts, double* tn)
 {
     double k = K[j * n + i];
+    double tb = ns ? 2.0 * k : 0.0; /* north / south boundary face */
     *tw = (i > 0) ? harmonic(K[j * n + i - 1], k) : 2.0 * k;
     *te = (i < n - 1) ? harmonic(k, K[j * n + i + 1]) : 2.0 * k;
-    *ts = (j > 0) ? harmonic(K[(j - 1) * n + i], k) : 0.0;
-    *tn = (j < n - 1) ? harmonic(k, K[(j + 1) * n + i]) : 0.0;
+    *ts = (j > 0) ? harmonic(K[(j - 1) * n + i], k) : tb;
+    *tn = (j < n - 1) ? harmonic(k, K[(j + 1) * n + i]) : tb;
 }
 
 /* y = A x (boundary values enter the rhs, not A). */
-void or_apply_A(int n, const double* K, const double* x, double* y)
+void or_apply_A_bc(int n, const double* K, int ns, const double* x, double* y)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
             double tw, te, ts, tn;
-            cell_faces(n, K, i, j, &tw, &te, &ts, &tn);
+            cell_faces(n, K, ns, i, j, &tw, &te, &ts, &tn);
             double v = (tw + te + ts + tn) * x[j * n + i];
             if (i > 0) v -= tw * x[j * n + i - 1];
             if (i < n - 1) v -= te * x[j * n + i + 1];
@@ -337,27 +362,39 @@ void or_apply_A(int n, const double* K, const double* x, double* y)
         }
 }
 
-/* rhs of the stage problem: the Dirichlet data moved to the right side. */
-void or_stage_rhs(int n, const double* K, double pW, double pE, double* b)
+void or_apply_A(int n, const double* K, const double* x, double* y) { or_apply_A_bc(n, K, 0, x, y); }
+
+/* rhs of the stage problem: the Dirichlet data moved to the right side,
+ * T g on every Dirichlet boundary face. */
+void or_stage_rhs_bc(int n, const double* K, const double* g, int ns, double* b)
 {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
+            double k = K[j * n + i];
             double v = 0.0;
-            if (i == 0) v += 2.0 * K[j * n + i] * pW;
-            if (i == n - 1) v += 2.0 * K[j * n + i] * pE;
+            if (i == 0) v += 2.0 * k * g[0];
+            if (i == n - 1) v += 2.0 * k * g[1];
+            if (ns && j == 0) v += 2.0 * k * g[2];
+            if (ns && j == n - 1) v += 2.0 * k * g[3];
             b[j * n + i] = v;
         }
 }
 
+void or_stage_rhs(int n, const double* K, double pW, double pE, double* b)
+{
+    double g[4] = {pW, pE, 0.0, 0.0};
+    or_stage_rhs_bc(n, K, g, 0, b);
+}
+
 /* One red-black Gauss-Seidel sweep: red cells ((i+j) even) then black. */
-void or_rbgs_sweep(int n, const double* K, const double* b, double* x)
+void or_rbgs_sweep_bc(int n, const double* K, int ns, const double* b, double* x)
 {
     for (int color = 0; color < 2; ++color)
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 if (((i + j) & 1) != color) continue;
                 double tw, te, ts, tn;
-                cell_faces(n, K, i, j, &tw, &te, &ts, &tn);
+                cell_faces(n, K, ns, i, j, &tw, &te, &ts, &tn);
                 double s = b[j * n + i];
                 if (i > 0) s += tw * x[j * n + i - 1];
                 if (i < n - 1) s += te * x[j * n + i + 1];
@@ -367,11 +404,18 @@ void or_rbgs_sweep(int n, const double* K, const double* b, double* x)
             }
 }
 
+void or_rbgs_sweep(int n, const double* K, const double* b, double* x) { or_rbgs_sweep_bc(n, K, 0, b, x); }
+
 /* r = b - A x */
+void or_residual_bc(int n, const double* K, int ns, const double* b, const double* x, double* r)
+{
+    or_apply_A_bc(n, K, ns, x, r);
+    for (int c = 0; c < n * n; ++c) r[c] = b[c] - r[c];
+}
+
 void or_residual(int n, const double* K, const double* b, const double* x, double* r)
 {
-    or_apply_A(n, K, x, r);
-    for (int c = 0; c < n * n; ++c) r[c] = b[c] - r[c];
+    or_residual_bc(n, K, 0, b, x, r);
 }
 
 /* Coarse rhs = sum of the four fine residuals of each coarse cell. */
@@ -384,43 +428,58 @@ void or_restrict_sum(int nc, const double* rf, double* bc)
                              rf[(2 * J + 1) * nf + 2 * I] + rf[(2 * J + 1) * nf + 2 * I + 1];
 }
 
-/* Coarse value with ghost cells: north/south (no flow) mirror the edge
- * cell; west/east (Dirichlet gW/gE on the face) extrapolate 2 g - u. */
-static double coarse_value(int nc, const double* uc, int I, int J, double gW, double gE)
+/* Coarse value with ghost cells.  A Dirichlet face with value g on it
+ * extrapolates 2 g - u from the edge cell (west / east always, north /
+ * south in Case I); a no-flow face mirrors the edge cell (north / south in
+ * Case II).  A ghost in a corner takes the x rule on the y ghost. */
+static double coarse_value(int nc, const double* uc, int I, int J, const double* g, int ns)
 {
-    if (J < 0) J = 0;
-    if (J > nc - 1) J = nc - 1;
-    if (I < 0) return 2.0 * gW - uc[J * nc + 0];
-    if (I > nc - 1) return 2.0 * gE - uc[J * nc + nc - 1];
+    if (J < 0 || J > nc - 1) {
+        int Je = J < 0 ? 0 : nc - 1;
+        double ge = J < 0 ? g[2] : g[3];
+        double edge = coarse_value(nc, uc, I, Je, g, ns);
+        return ns ? 2.0 * ge - edge : edge;
+    }
+    if (I < 0) return 2.0 * g[0] - uc[J * nc + 0];
+    if (I > nc - 1) return 2.0 * g[1] - uc[J * nc + nc - 1];
     return uc[J * nc + I];
 }
 
 /* Bilinear cell-centred interpolation: 9/16 parent, 3/16 each of the two
  * nearest coarse neighbours in x and y, 1/16 the diagonal one.             */
-static double bilinear(int nc, const double* uc, int i, int j, double gW, double gE)
+static double bilinear(int nc, const double* uc, int i, int j, const double* g, int ns)
 {
     int I = i / 2, J = j / 2;
     int Ix = (i & 1) ? I + 1 : I - 1;
     int Jy = (j & 1) ? J + 1 : J - 1;
-    return (9.0 * coarse_value(nc, uc, I, J, gW, gE) + 3.0 * coarse_value(nc, uc, Ix, J, gW, gE) +
-            3.0 * coarse_value(nc, uc, I, Jy, gW, gE) + 1.0 * coarse_value(nc, uc, Ix, Jy, gW, gE)) /
+    return (9.0 * coarse_value(nc, uc, I, J, g, ns) + 3.0 * coarse_value(nc, uc, Ix, J, g, ns) +
+            3.0 * coarse_value(nc, uc, I, Jy, g, ns) + 1.0 * coarse_value(nc, uc, Ix, Jy, g, ns)) /
            16.0;
 }
 
 /* x_f += P e_c (the error vanishes on the Dirichlet faces). */
-void or_prolong_add(int nc, const double* ec, double* xf)
+void or_prolong_add_bc(int nc, const double* ec, int ns, double* xf)
 {
+    static const double zero[4] = {0.0, 0.0, 0.0, 0.0};
     int nf = 2 * nc;
     for (int j = 0; j < nf; ++j)
-        for (int i = 0; i < nf; ++i) xf[j * nf + i] += bilinear(nc, ec, i, j, 0.0, 0.0);
+        for (int i = 0; i < nf; ++i) xf[j * nf + i] += bilinear(nc, ec, i, j, zero, ns);
 }
 
+void or_prolong_add(int nc, const double* ec, double* xf) { or_prolong_add_bc(nc, ec, 0, xf); }
+
 /* FMG start of a stage: x_f = P u_c with the Dirichlet data as ghosts. */
-void or_fmg_interpolate(int nc, const double* uc, double pW, double pE, double* xf)
+void or_fmg_interpolate_bc(int nc, const double* uc, const double* g, int ns, double* xf)
 {
     int nf = 2 * nc;
     for (int j = 0; j < nf; ++j)
-        for (int i = 0; i < nf; ++i) xf[j * nf + i] = bilinear(nc, uc, i, j, pW, pE);
+        for (int i = 0; i < nf; ++i) xf[j * nf + i] = bilinear(nc, uc, i, j, g, ns);
+}
+
+void or_fmg_interpolate(int nc, const double* uc, double pW, double pE, double* xf)
+{
+    double g[4] = {pW, pE, 0.0, 0.0};
+    or_fmg_interpolate_bc(nc, uc, g, 0, xf);
 }
 
 /* Coefficient coarsening by injection: K_c[J][I] = K_f[2J][2I]. */
@@ -433,7 +492,7 @@ void or_inject(int nc, const double* Kf, double* Kc)
 
 /* Exact solve on a small grid: assemble the dense SPD matrix and factor it
  * by Cholesky, A = L L^T, then two triangular solves. */
-void or_exact_solve(int n, const double* K, const double* b, double* x)
+void or_exact_solve_bc(int n, const double* K, int ns, const double* b, double* x)
 {
     int m = n * n;
     double* A = (double*)calloc((size_t)m * m, sizeof(double));
@@ -441,7 +500,7 @@ void or_exact_solve(int n, const double* K, const double* b, double* x)
     double* col = (double*)calloc((size_t)m, sizeof(double));
     for (int c = 0; c < m; ++c) { /* column c of A is A e_c */
         e[c] = 1.0;
-        or_apply_A(n, K, e, col);
+        or_apply_A_bc(n, K, ns, e, col);
         for (int r = 0; r < m; ++r) A[r * m + c] = col[r];
         e[c] = 0.0;
     }
@@ -469,6 +528,17 @@ void or_exact_solve(int n, const double* K, const double* b, double* x)
     free(A);
     free(e);
     free(col);
+}
+
+void or_exact_solve(int n, const double* K, const double* b, double* x) { or_exact_solve_bc(n, K, 0, b, x); }
+
+/* QoI of Case I: u(0.5, 0.5).  For even n the centre is the corner shared by
+ * cells (n/2-1 .. n/2, n/2-1 .. n/2); bilinear interpolation from their
+ * centres gives the mean of the four. */
+double or_centre_value(int n, const double* x)
+{
+    int h = n / 2;
+    return 0.25 * (x[(h - 1) * n + h - 1] + x[(h - 1) * n + h] + x[h * n + h - 1] + x[h * n + h]);
 }
 
 /* QoI of Case II: outflux through the east edge,
@@ -509,6 +579,7 @@ typedef struct {
     double* r[32];   /* residual work per grid */
     double* d[32];   /* prolongated correction and A d (energy step), 2 cells per cell */
     int energy_step;
+    int ns;          /* north / south edges Dirichlet (Case I) */
 } hierarchy;
 
 static int grid_n(const hierarchy* H, int k) { return H->n0 << k; }
@@ -524,10 +595,11 @@ void or_geometric_children(int nc, const double* Kf, double* Kc)
 }
 
 static void hierarchy_init(hierarchy* H, int n_fine, int n0, const double* K_fine, int coarse_op,
-                           int energy_step)
+                           int energy_step, int ns)
 {
     memset(H, 0, sizeof(*H));
     H->energy_step = energy_step;
+    H->ns = ns;
     H->n0 = n0;
     int m = 0;
     while ((n0 << m) < n_fine) ++m;
@@ -566,16 +638,16 @@ static void vcycle(hierarchy* H, int k, int top, int nu1, int nu2)
     int n = grid_n(H, k);
     const double* K = (k == top) ? H->K[k] : H->Kop[k];
     if (k == 0) {
-        or_exact_solve(n, K, H->b[0], H->x[0]);
+        or_exact_solve_bc(n, K, H->ns, H->b[0], H->x[0]);
         return;
     }
-    for (int s = 0; s < nu1; ++s) or_rbgs_sweep(n, K, H->b[k], H->x[k]);
-    or_residual(n, K, H->b[k], H->x[k], H->r[k]);
+    for (int s = 0; s < nu1; ++s) or_rbgs_sweep_bc(n, K, H->ns, H->b[k], H->x[k]);
+    or_residual_bc(n, K, H->ns, H->b[k], H->x[k], H->r[k]);
     or_restrict_sum(n / 2, H->r[k], H->b[k - 1]);
     memset(H->x[k - 1], 0, sizeof(double) * (size_t)(n / 2) * (n / 2));
     vcycle(H, k - 1, top, nu1, nu2);
     if (!H->energy_step) {
-        or_prolong_add(n / 2, H->x[k - 1], H->x[k]);
+        or_prolong_add_bc(n / 2, H->x[k - 1], H->ns, H->x[k]);
     } else {
         /* d = P e_c; x += alpha d with alpha = (r, d) / (d, A d), the exact
            line minimum of the energy error (A symmetric positive definite) */
@@ -583,8 +655,8 @@ static void vcycle(hierarchy* H, int k, int top, int nu1, int nu2)
         double* d = H->d[k];
         double* Ad = d + cells;
         memset(d, 0, sizeof(double) * cells);
-        or_prolong_add(n / 2, H->x[k - 1], d);
-        or_apply_A(n, K, d, Ad);
+        or_prolong_add_bc(n / 2, H->x[k - 1], H->ns, d);
+        or_apply_A_bc(n, K, H->ns, d, Ad);
         double rd = 0.0, dAd = 0.0;
         for (size_t c = 0; c < cells; ++c) {
             rd += H->r[k][c] * d[c];
@@ -593,14 +665,14 @@ static void vcycle(hierarchy* H, int k, int top, int nu1, int nu2)
         double alpha = dAd > 0.0 ? rd / dAd : 0.0;
         for (size_t c = 0; c < cells; ++c) H->x[k][c] += alpha * d[c];
     }
-    for (int s = 0; s < nu2; ++s) or_rbgs_sweep(n, K, H->b[k], H->x[k]);
+    for (int s = 0; s < nu2; ++s) or_rbgs_sweep_bc(n, K, H->ns, H->b[k], H->x[k]);
 }
 
 /* Relative residual ||b - A x|| / ||b|| on grid k. */
 static double rel_residual(hierarchy* H, int k)
 {
     int n = grid_n(H, k);
-    or_residual(n, H->K[k], H->b[k], H->x[k], H->r[k]);
+    or_residual_bc(n, H->K[k], H->ns, H->b[k], H->x[k], H->r[k]);
     double nb = or_norm2(n * n, H->b[k]);
     return or_norm2(n * n, H->r[k]) / (nb > 0 ? nb : 1.0);
 }
@@ -622,6 +694,12 @@ static int stage_cycles(hierarchy* H, int k, const or_params* P)
     return it;
 }
 
+/* QoI of a stage solution: Case II the east outflux, Case I u(0.5, 0.5). */
+static double stage_qoi(const or_bc* bc, int n, const double* K, const double* x)
+{
+    return bc->ns ? or_centre_value(n, x) : or_outflux(n, K, x, bc->g[1]);
+}
+
 /* Full multigrid for one sample: exact solve on the coarsest grid, then for
  * each finer grid interpolate the previous stage's solution and run the
  * stage's V-cycles.  Q^c is the outflux of the stage one below the finest
@@ -632,20 +710,21 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
                  double* p_out, double* qf, double* qc)
 {
     hierarchy H;
-    hierarchy_init(&H, n_fine, n0, K_fine, P->coarse_op, P->energy_step);
+    or_bc bc = bc_of(P);
+    hierarchy_init(&H, n_fine, n0, K_fine, P->coarse_op, P->energy_step, bc.ns);
     int cycles = 0;
     *qc = NAN;
-    or_stage_rhs(n0, H.K[0], P->pW, P->pE, H.b[0]);
-    or_exact_solve(n0, H.K[0], H.b[0], H.x[0]);
-    if (H.m == 1) *qc = or_outflux(n0, H.K[0], H.x[0], P->pE);
+    or_stage_rhs_bc(n0, H.K[0], bc.g, bc.ns, H.b[0]);
+    or_exact_solve_bc(n0, H.K[0], bc.ns, H.b[0], H.x[0]);
+    if (H.m == 1) *qc = stage_qoi(&bc, n0, H.K[0], H.x[0]);
     for (int k = 1; k <= H.m; ++k) {
         int n = grid_n(&H, k);
-        or_fmg_interpolate(n / 2, H.x[k - 1], P->pW, P->pE, H.x[k]);
-        or_stage_rhs(n, H.K[k], P->pW, P->pE, H.b[k]);
+        or_fmg_interpolate_bc(n / 2, H.x[k - 1], bc.g, bc.ns, H.x[k]);
+        or_stage_rhs_bc(n, H.K[k], bc.g, bc.ns, H.b[k]);
         cycles += stage_cycles(&H, k, P);
-        if (k == H.m - 1) *qc = or_outflux(n, H.K[k], H.x[k], P->pE);
+        if (k == H.m - 1) *qc = stage_qoi(&bc, n, H.K[k], H.x[k]);
     }
-    *qf = or_outflux(n_fine, H.K[H.m], H.x[H.m], P->pE);
+    *qf = stage_qoi(&bc, n_fine, H.K[H.m], H.x[H.m]);
     if (p_out) memcpy(p_out, H.x[H.m], sizeof(double) * (size_t)n_fine * n_fine);
     hierarchy_free(&H);
     return cycles;
@@ -654,16 +733,16 @@ int or_fmg_solve(int n_fine, int n0, const double* K_fine, const or_params* P,
 /* V-cycles on a given problem A x = b from the given x (for convergence-factor
  * checks).  res_hist[c] = ||b - A x|| after cycle c (c = 0 before any). */
 void or_vcycle_solve(int n, int n0, const double* K, const double* b, double* x,
-                     int nu1, int nu2, int ncycles, int coarse_op, int energy_step, double* res_hist)
+                     int nu1, int nu2, int ncycles, int coarse_op, int energy_step, int ns, double* res_hist)
 {
     hierarchy H;
-    hierarchy_init(&H, n, n0, K, coarse_op, energy_step);
+    hierarchy_init(&H, n, n0, K, coarse_op, energy_step, ns);
     memcpy(H.b[H.m], b, sizeof(double) * (size_t)n * n);
     memcpy(H.x[H.m], x, sizeof(double) * (size_t)n * n);
     for (int c = 0; c <= ncycles; ++c) {
         if (c > 0) vcycle(&H, H.m, H.m, nu1, nu2);
         if (res_hist) {
-            or_residual(n, H.K[H.m], H.b[H.m], H.x[H.m], H.r[H.m]);
+            or_residual_bc(n, H.K[H.m], ns, H.b[H.m], H.x[H.m], H.r[H.m]);
             res_hist[c] = or_norm2(n * n, H.r[H.m]);
         }
     }

@@ -16,13 +16,24 @@ class Params(C.Structure):
     _fields_ = [("pW", C.c_double), ("pE", C.c_double), ("nu0", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("converged", C.c_int),
                 ("tol", C.c_double), ("max_cycles", C.c_int), ("coarse_op", C.c_int),
-                ("energy_step", C.c_int)]
+                ("energy_step", C.c_int), ("bc_case", C.c_int), ("pS", C.c_double), ("pN", C.c_double)]
 
 
 def params(pW=1.0, pE=0.0, nu0=2, nu1=2, nu2=2, converged=False, tol=1e-12,
-           max_cycles=100, coarse_op=1, energy_step=False):
+           max_cycles=100, coarse_op=1, energy_step=False, bc_case=2, pS=0.0, pN=0.0):
+    """bc_case 2: Table 1 Case II (no flow north / south, outflux QoI);
+    1: Case I (Dirichlet pS / pN on the south / north edges, QoI u(0.5, 0.5))."""
     return Params(pW, pE, nu0, nu1, nu2, int(bool(converged)), tol, max_cycles, coarse_op,
-                  int(bool(energy_step)))
+                  int(bool(energy_step)), bc_case, pS, pN)
+
+
+def case1_params(**kw):
+    """Table 1 Case I: u = 100 / 0 / 10 / 50 on the west / east / south / north edges."""
+    kw.setdefault("pW", 100.0)
+    kw.setdefault("pE", 0.0)
+    kw.setdefault("pS", 10.0)
+    kw.setdefault("pN", 50.0)
+    return params(bc_case=1, **kw)
 
 
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -67,7 +78,14 @@ def lib():
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.or_fmg_solve.restype = C.c_int
         L.or_vcycle_solve.argtypes = [C.c_int, C.c_int, _D, _D, _D, C.c_int, C.c_int,
-                                      C.c_int, C.c_int, C.c_int, _D]
+                                      C.c_int, C.c_int, C.c_int, C.c_int, _D]
+        L.or_apply_A_bc.argtypes = [C.c_int, _D, C.c_int, _D, _D]
+        L.or_stage_rhs_bc.argtypes = [C.c_int, _D, _D, C.c_int, _D]
+        L.or_prolong_add_bc.argtypes = [C.c_int, _D, C.c_int, _D]
+        L.or_fmg_interpolate_bc.argtypes = [C.c_int, _D, _D, C.c_int, _D]
+        L.or_exact_solve_bc.argtypes = [C.c_int, _D, C.c_int, _D, _D]
+        L.or_centre_value.argtypes = [C.c_int, _D]
+        L.or_centre_value.restype = C.c_double
         L.or_fmg_solve_batch.argtypes = [C.c_int, C.c_int, C.c_int, _D, C.POINTER(Params),
                                          C.c_void_p, _D, _D, C.c_int]
         L.or_fmg_solve_batch.restype = C.c_int
@@ -236,13 +254,51 @@ def fmg_solve(K, prm=None, n0=4, want_p=False):
     return qf.value, qc.value, p, cyc
 
 
-def vcycle_solve(K, b, x0, nu1=2, nu2=2, ncycles=10, n0=4, coarse_op=1, energy_step=False):
-    """V-cycles on A x = b; returns (x, residual norms before/after each cycle)."""
+def vcycle_solve(K, b, x0, nu1=2, nu2=2, ncycles=10, n0=4, coarse_op=1, energy_step=False, ns=0):
+    """V-cycles on A x = b (ns = 1: Dirichlet north / south edges, Case I);
+    returns (x, residual norms before/after each cycle)."""
     x = _c(x0).copy()
     hist = np.zeros(ncycles + 1)
     lib().or_vcycle_solve(K.shape[0], n0, _c(K), _c(b), x, nu1, nu2, ncycles, coarse_op,
-                          int(bool(energy_step)), hist)
+                          int(bool(energy_step)), int(ns), hist)
     return x, hist
+
+
+# ----------------------------------------------------------------- Case I (all-Dirichlet)
+def apply_A_bc(K, x, ns):
+    y = np.zeros_like(_c(x))
+    lib().or_apply_A_bc(K.shape[0], _c(K), int(ns), _c(x), y)
+    return y
+
+
+def stage_rhs_bc(K, g, ns):
+    """g = (west, east, south, north) boundary values."""
+    b = np.zeros_like(_c(K))
+    lib().or_stage_rhs_bc(K.shape[0], _c(K), _c(g), int(ns), b)
+    return b
+
+
+def prolong_add_bc(ec, xf, ns):
+    xf = _c(xf).copy()
+    lib().or_prolong_add_bc(ec.shape[0], _c(ec), int(ns), xf)
+    return xf
+
+
+def fmg_interpolate_bc(uc, g, ns):
+    nc = uc.shape[0]
+    xf = np.zeros((2 * nc, 2 * nc))
+    lib().or_fmg_interpolate_bc(nc, _c(uc), _c(g), int(ns), xf)
+    return xf
+
+
+def exact_solve_bc(K, b, ns):
+    x = np.zeros_like(_c(b))
+    lib().or_exact_solve_bc(K.shape[0], _c(K), int(ns), _c(b), x)
+    return x
+
+
+def centre_value(x):
+    return lib().or_centre_value(x.shape[0], _c(x))
 
 
 def fmg_solve_batch(K, prm=None, n0=4, want_p=False, nthreads=0):
