@@ -5,9 +5,10 @@
  * Method: Liu, Li, Sun & Yu, "A full multigrid multilevel (quasi-) Monte
  * Carlo method for the single-phase subsurface flow with random
  * coefficients", arXiv 1910.04727.  The model problem is Eq. 1 on the unit
- * square with the boundary data and QoI of Table 1, Case II (Dirichlet p_W /
- * p_E on the west / east edges, no flow north and south, QoI = outflux
- * through the east edge); the permeability is k = exp(g), g a Gaussian field
+ * square with the boundary data and QoI of Table 1: Case II (the default:
+ * Dirichlet p_W / p_E on the west / east edges, no flow north and south,
+ * QoI = outflux through the east edge) or Case I (Dirichlet data on all
+ * four edges, QoI = u(0.5, 0.5)); the permeability is k = exp(g), g a Gaussian field
  * with the exponential Matern covariance of Sec. 3.1, represented by its
  * truncated KL expansion.  The MLMC levels (Sec. 2.2, Algorithm 1) share
  * their grid hierarchy with the full multigrid solver (Sec. 2.5): one FMG
@@ -93,7 +94,20 @@ typedef struct {
     int32_t n_shifts;     /* QMC digital shifts R */
     uint64_t seed;        /* key of the Philox streams (MC points, QMC shifts) */
     int64_t max_batch;    /* most samples per device batch (0: library's choice) */
+    int32_t bc_case;      /* Table 1: FM_CASE_II (0 is read as Case II) or FM_CASE_I */
+    double pS, pN;        /* Case I: Dirichlet data on the south / north edges */
 } fm_config;
+
+/* Boundary conditions and QoI (Table 1).
+ * FM_CASE_II: p = pW on the west edge, pE on the east edge, no flow through
+ *             the north and south edges; QoI = the outflux through the east
+ *             edge, sum_j 2 K_(n-1,j) (p_(n-1,j) - pE).
+ * FM_CASE_I:  Dirichlet data pW, pE, pS, pN on the west, east, south and
+ *             north edges; QoI = u(0.5, 0.5).  The centre is the corner of
+ *             the four middle cells of every grid, and the bilinear
+ *             interpolation of their centre values there is their mean. */
+#define FM_CASE_I 1
+#define FM_CASE_II 2
 
 /* Kernel schedule of a batched FMG solve (same arithmetic, same result up
  * to rounding order). */
@@ -122,6 +136,8 @@ typedef struct {
                              coarse-grid correction d = P e_c as alpha d, alpha = (r, d) /
                              (d, A d) per sample, the energy minimum along d, so no cycle
                              raises the energy error (robust at high contrast) */
+    int32_t bc_case;      /* FM_CASE_II (0 is read as Case II) or FM_CASE_I */
+    double pS, pN;        /* Case I: Dirichlet data on the south / north edges */
 } fm_solve_params;
 
 /* ---------------------------------------------------------------- context */
@@ -202,13 +218,14 @@ fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d
 /* ---------------------------------------------------------------- solver */
 
 /* Full multigrid (Sec. 2.5) for n independent problems on an n_fine x n_fine
- * grid with coefficients d_K [n][n_fine][n_fine]: coefficients coarsened by
+ * grid with coefficients d_K [n][n_fine][n_fine] (boundary data and QoI of
+ * prm->bc_case, Table 1): coefficients coarsened by
  * injection K^c[I][J] = K^f[2I][2J] down to the coarsest grid, exact solve
  * there, then per finer grid bilinear interpolation of the previous stage's
  * solution and nu0 V(nu1,nu2) cycles (red-black Gauss-Seidel, residual
  * restricted by summing the 2x2 children, bilinear cell-centred
- * prolongation).  Outputs: d_qf[s] outflux of the finest stage; d_qc[s]
- * (nullable) outflux of the stage one grid coarser (the Q^c by-product;
+ * prolongation).  Outputs: d_qf[s] QoI of the finest stage; d_qc[s]
+ * (nullable) QoI of the stage one grid coarser (the Q^c by-product;
  * NaN if n_fine == n_coarsest); d_p (nullable) the finest solution
  * [n][n_fine][n_fine]; d_status (nullable) per-sample FM_OK / FM_ENOTCONV.
  * n_fine must be n_coarsest times a power of two.  Scratch is owned by the

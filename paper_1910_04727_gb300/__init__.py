@@ -123,11 +123,13 @@ class Context:
     def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
                  nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
                  precision=FM_PREC_FP64, converged=False, tol=1e-10, qtol=0.0, max_cycles=100,
-                 kl_mode=0):
+                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0):
+        """bc_case: Table 1's FM_CASE_II (no flow north / south, east outflux) or
+        FM_CASE_I (Dirichlet pW, pE, pS, pN on all four edges, QoI u(0.5, 0.5))."""
         self._L = _lib.load()
         cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
                             precision, int(bool(converged)), tol, qtol, max_cycles, kl_mode, n_shifts,
-                            seed, max_batch)
+                            seed, max_batch, bc_case, pS, pN)
         h = C.c_void_p()
         st = self._L.fm_create(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -227,7 +229,8 @@ class Context:
     def solve_params(self, **over):
         c = self.cfg
         p = _lib.FmSolveParams(c.pW, c.pE, c.n_coarsest, c.nu0, c.nu1, c.nu2, c.precision,
-                               _lib.FM_KERNEL_AUTO, c.converged, c.tol, c.qtol, c.max_cycles)
+                               _lib.FM_KERNEL_AUTO, c.converged, c.tol, c.qtol, c.max_cycles, 0,
+                               c.bc_case, c.pS, c.pN)
         for k, v in over.items():
             setattr(p, k, v)
         return p

@@ -14,6 +14,7 @@ FM_PREC_FP64 = 0
 FM_PREC_MIXED = 1
 FM_KERNEL_AUTO, FM_KERNEL_LEVELWISE, FM_KERNEL_RESIDENT = 0, 1, 2
 FM_KL_AUTO, FM_KL_FP64, FM_KL_BF16, FM_KL_BF16X3 = 0, 1, 2, 3
+FM_CASE_I, FM_CASE_II = 1, 2
 
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENOTCONV",
                 5: "FM_ETIMEOUT", 6: "FM_EUNSUPPORTED"}
@@ -36,7 +37,8 @@ class FmConfig(C.Structure):
                 ("nu2", C.c_int32), ("precision", C.c_int32), ("converged", C.c_int32),
                 ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
                 ("kl_mode", C.c_int32),
-                ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64)]
+                ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64),
+                ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double)]
 
 
 class FmSolveParams(C.Structure):
@@ -44,7 +46,7 @@ class FmSolveParams(C.Structure):
                 ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("converged", C.c_int32),
                 ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
-                ("energy_step", C.c_int32)]
+                ("energy_step", C.c_int32), ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double)]
 
 
 class FmLevelSums(C.Structure):

@@ -37,6 +37,8 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
                  "fm_create: converged mode needs tol > 0 and max_cycles >= 1");
     FM_CHECK_ARG(nullptr, cfg->n_shifts >= 0 && cfg->n_shifts <= 64, "fm_create: n_shifts must be in [0, 64]");
     FM_CHECK_ARG(nullptr, cfg->kl_mode >= FM_KL_AUTO && cfg->kl_mode <= FM_KL_BF16X3, "fm_create: unknown kl_mode");
+    FM_CHECK_ARG(nullptr, cfg->bc_case == 0 || cfg->bc_case == FM_CASE_I || cfg->bc_case == FM_CASE_II,
+                 "fm_create: bc_case must be FM_CASE_I or FM_CASE_II");
     fm_ctx* ctx = new (std::nothrow) fm_ctx();
     if (!ctx) {
         set_error(nullptr, "fm_create: host allocation failed");

@@ -59,6 +59,45 @@ __host__ __device__ inline u64x4 philox4x64(u64x4 c, uint64_t k0, uint64_t k1) {
     return c;
 }
 
+// ------------------------------------------------------------------ boundary data
+// Boundary data of a problem (Table 1): Dirichlet values g[0..3] on the
+// west, east, south and north edges; ns = 1 when the north and south edges
+// are Dirichlet (Case I), 0 when they are no-flow (Case II, where g[2] and
+// g[3] are unused).
+struct Bnd {
+    double g[4];
+    int ns;
+};
+
+// Ghost values of a prolongation: the boundary data of the function being
+// interpolated (zero for an error), in its arithmetic U.
+template <typename U>
+struct Ghost {
+    U w, e, s, n;
+    int ns;
+};
+
+inline Bnd bnd_of(const fm_solve_params& prm) {
+    Bnd b;
+    b.ns = prm.bc_case == FM_CASE_I ? 1 : 0;
+    b.g[0] = prm.pW;
+    b.g[1] = prm.pE;
+    b.g[2] = b.ns ? prm.pS : 0.0;
+    b.g[3] = b.ns ? prm.pN : 0.0;
+    return b;
+}
+
+// The Dirichlet data of cell (i, j) of an n x n grid moved to the right-hand
+// side: 2 k g for every Dirichlet boundary face of the cell (coefficient k).
+__host__ __device__ inline double dirichlet_rhs(const Bnd& b, int n, int i, int j, double k) {
+    double v = 0.0;
+    if (i == 0) v += 2.0 * k * b.g[0];
+    if (i == n - 1) v += 2.0 * k * b.g[1];
+    if (b.ns && j == 0) v += 2.0 * k * b.g[2];
+    if (b.ns && j == n - 1) v += 2.0 * k * b.g[3];
+    return v;
+}
+
 // ------------------------------------------------------------------ errors
 #define FM_CUDA_TRY(ctx, expr)                                                        \
     do {                                                                              \
@@ -207,6 +246,9 @@ double* prof_counter(fm_ctx* ctx, int idx);
         __VA_ARGS__;                                           \
         fm::prof_stop((ctx), pi_, (st), (bytes), (flops));     \
     } while (0)
+
+// The solver parameters of the context's configuration (mlmc.cu).
+fm_solve_params solve_params(const fm_ctx* ctx);
 
 // Samples per device batch for grid n (memory of the FMG hierarchy and field).
 int64_t batch_limit(const fm_ctx* ctx, int n);

@@ -60,11 +60,14 @@ __global__ void k_child_geomean(int nc, size_t S, const double* __restrict__ Kf,
     Kc[t] = (double)exp(C(0.25) * (log((C)k[0]) + log((C)k[1]) + log((C)k[nf]) + log((C)k[nf + 1])));
 }
 
-// Face transmissibilities: harmonic mean inside, 2K on the Dirichlet edges,
-// none on the no-flow edges, in arithmetic C; optional FP64 copies for
-// refined grids (which take C = double).
+// Face transmissibilities: harmonic mean inside, 2K on the Dirichlet edges
+// (west / east; north / south too when ns, Table 1 Case I), none on the
+// no-flow edges, in arithmetic C; optional FP64 copies for refined grids
+// (which take C = double).  Te of the east column and Tn of the north row
+// hold the boundary faces: every kernel couples neighbours only across
+// interior faces, so these enter through D alone.
 template <typename T, typename C>
-__global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T* __restrict__ Te,
+__global__ void k_coefficients(int n, size_t S, int ns, const double* __restrict__ K, T* __restrict__ Te,
                                T* __restrict__ Tn, T* __restrict__ D, double* __restrict__ Te64,
                                double* __restrict__ Tn64, double* __restrict__ D64) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,8 +78,9 @@ __global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T*
     const C k = (C)K[t];
     const C tw = (i > 0) ? harmonic<C>((C)K[t - 1], k) : C(2) * k;
     const C te = (i < n - 1) ? harmonic<C>(k, (C)K[t + 1]) : C(2) * k;
-    const C ts = (j > 0) ? harmonic<C>((C)K[t - n], k) : C(0);
-    const C tn = (j < n - 1) ? harmonic<C>(k, (C)K[t + n]) : C(0);
+    const C tb = ns ? C(2) * k : C(0);   // north / south boundary face
+    const C ts = (j > 0) ? harmonic<C>((C)K[t - n], k) : tb;
+    const C tn = (j < n - 1) ? harmonic<C>(k, (C)K[t + n]) : tb;
     const C d = tw + te + ts + tn;
     Te[t] = (T)te;
     Tn[t] = (T)tn;
@@ -90,16 +94,13 @@ __global__ void k_coefficients(int n, size_t S, const double* __restrict__ K, T*
 
 // Right-hand side of a stage problem: the Dirichlet data moved to the rhs.
 template <typename T>
-__global__ void k_stage_rhs(int n, size_t S, const double* __restrict__ K, double pW, double pE,
-                            T* __restrict__ b) {
+__global__ void k_stage_rhs(int n, size_t S, const double* __restrict__ K, Bnd bd, T* __restrict__ b) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)n * n;
     if (t >= S * cells) return;
-    const int i = (int)(t % cells) % n;
-    double v = 0.0;
-    if (i == 0) v += 2.0 * K[t] * pW;
-    if (i == n - 1) v += 2.0 * K[t] * pE;
-    b[t] = (T)v;
+    const int c = (int)(t % cells);
+    const int i = c % n, j = c / n;
+    b[t] = (T)dirichlet_rhs(bd, n, i, j, K[t]);
 }
 
 // One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == color.
@@ -124,14 +125,26 @@ __global__ void k_rbgs_color(int n, size_t S, int color, const T* __restrict__ b
     p[c] = acc * (T(1) / D[c]);
 }
 
-// Coarse value with ghosts: mirror across the no-flow edges, 2g - u across
-// the Dirichlet edges (g = 0 for an error).
+// Coarse value with ghosts: 2g - u across the Dirichlet edges (g = 0 for an
+// error), the edge value mirrored across the no-flow edges; a corner ghost
+// takes the x rule on the y ghost.
 template <typename U>
-__device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, U gW, U gE) {
-    J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
-    if (I < 0) return U(2) * gW - uc[(size_t)J * nc];
-    if (I > nc - 1) return U(2) * gE - uc[(size_t)J * nc + nc - 1];
+__device__ __forceinline__ U coarse_ghost_x(int nc, const U* uc, int I, int J, const Ghost<U>& g) {
+    if (I < 0) return U(2) * g.w - uc[(size_t)J * nc];
+    if (I > nc - 1) return U(2) * g.e - uc[(size_t)J * nc + nc - 1];
     return uc[(size_t)J * nc + I];
+}
+template <typename U>
+__device__ __forceinline__ U coarse_ghost(int nc, const U* uc, int I, int J, const Ghost<U>& g) {
+    if (J < 0) {
+        const U edge = coarse_ghost_x(nc, uc, I, 0, g);
+        return g.ns ? U(2) * g.s - edge : edge;
+    }
+    if (J > nc - 1) {
+        const U edge = coarse_ghost_x(nc, uc, I, nc - 1, g);
+        return g.ns ? U(2) * g.n - edge : edge;
+    }
+    return coarse_ghost_x(nc, uc, I, J, g);
 }
 
 // (P u_c) at fine cell (i, j): bilinear cell-centred (9, 3, 3, 1) / 16 with
@@ -143,12 +156,18 @@ __device__ __forceinline__ U prolong_vals(U own, U nx, U ny, U nxy) {
     return (U(9) * own + U(3) * nx + U(3) * ny + U(1) * nxy) / U(16);
 }
 template <typename U>
-__device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, U gW, U gE) {
+__device__ __forceinline__ U prolong_at(int nc, const U* u, int i, int j, const Ghost<U>& g) {
     const int I = i >> 1, J = j >> 1;
     const int Ix = (i & 1) ? I + 1 : I - 1;
     const int Jy = (j & 1) ? J + 1 : J - 1;
-    return prolong_vals(coarse_ghost(nc, u, I, J, gW, gE), coarse_ghost(nc, u, Ix, J, gW, gE),
-                        coarse_ghost(nc, u, I, Jy, gW, gE), coarse_ghost(nc, u, Ix, Jy, gW, gE));
+    return prolong_vals(coarse_ghost(nc, u, I, J, g), coarse_ghost(nc, u, Ix, J, g), coarse_ghost(nc, u, I, Jy, g),
+                        coarse_ghost(nc, u, Ix, Jy, g));
+}
+// an error's ghosts: zero boundary data
+template <typename U>
+__device__ __forceinline__ U prolong_err(int nc, const U* u, int i, int j, int ns) {
+    const Ghost<U> g{U(0), U(0), U(0), U(0), ns};
+    return prolong_at(nc, u, i, j, g);
 }
 
 // nsweeps red-black sweeps (colour 0 then 1) on tiles of TI x TI cells of
@@ -166,7 +185,8 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
                                                    const T* __restrict__ b, const T* __restrict__ Te,
                                                    const T* __restrict__ Tn, const T* __restrict__ D,
                                                    const T* __restrict__ p_in, T* __restrict__ p_out,
-                                                   const int32_t* __restrict__ active, const T* __restrict__ ec) {
+                                                   const int32_t* __restrict__ active, const T* __restrict__ ec,
+                                                   int ns) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
     const int tiles = (n + TI - 1) / TI;
     const size_t s = blockIdx.x / ((unsigned)tiles * tiles);
@@ -186,7 +206,7 @@ __global__ void __launch_bounds__(256) k_rbgs_tile(int n, size_t S, int TI, int 
         const int r = e / RW, q = e % RW;
         const size_t g = base + (size_t)(ya + r) * n + xa + q;
         // with ec: the coarse-grid correction p + (P e) as k_prolong forms it
-        sp[e] = ec ? p_in[g] + prolong_at(n / 2, ec + s * (size_t)(n / 2) * (n / 2), xa + q, ya + r, T(0), T(0))
+        sp[e] = ec ? p_in[g] + prolong_err(n / 2, ec + s * (size_t)(n / 2) * (n / 2), xa + q, ya + r, ns)
                    : p_in[g];
         sb[e] = b[g];
         se[e] = Te[g];
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, si
                                                                       const T* __restrict__ D,
                                                                       const T* __restrict__ p_in, T* __restrict__ p_out,
                                                                       const int32_t* __restrict__ active,
-                                                                      const T* __restrict__ ec) {
+                                                                      const T* __restrict__ ec, int ns) {
     static_assert(R % 2 == 0 && R % RPT == 0, "region must split into column pairs and row strips");
     constexpr int C = R / 2, P = R + 2;   // column pairs; padded row pitch
     __shared__ T sp[P * P];
@@ -269,7 +289,7 @@ __global__ void __launch_bounds__((R / 2) * (R / RPT)) k_rbgs_tile_reg(int n, si
             if (x < RW && y < RH) {
                 const size_t g = base + (size_t)gy * n + gx;
                 // with ec: the coarse-grid correction p + (P e) as k_prolong forms it
-                rp[k][j] = ec ? p_in[g] + prolong_at(n / 2, ec + s * (size_t)(n / 2) * (n / 2), gx, gy, T(0), T(0))
+                rp[k][j] = ec ? p_in[g] + prolong_err(n / 2, ec + s * (size_t)(n / 2) * (n / 2), gx, gy, ns)
                               : p_in[g];
                 rb[k][j] = b[g];
                 rr[k][j] = T(1) / D[g];
@@ -406,7 +426,8 @@ __global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rb
                                                                  const T* __restrict__ p_in, T* __restrict__ p_out,
                                                                  const int32_t* __restrict__ active,
                                                                  const T* __restrict__ ec, T* __restrict__ bc,
-                                                                 T* __restrict__ pc, const int32_t* __restrict__ order) {
+                                                                 T* __restrict__ pc, const int32_t* __restrict__ order,
+                                                                 int ns) {
     using V2 = typename Pair<T>::type;
     constexpr int R = HS + 2;                       // rows in registers: y - HS - 1 .. y
     constexpr int XH = strip_xh(HS, FUSE), VH = XH;  // halo columns and rows (even)
@@ -522,12 +543,16 @@ __global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rb
                         const T* cv = myc[(y - ys) % DEPTH];
                         coarse3(cv[1 + lane], cv[lane], cv[2 + lane], cs0);
                         // fine row y: coarse row y / 2 and its y neighbour (one row down for
-                        // even y, clamped at 0; one up for odd y, clamped at nc - 1); the
-                        // step index J has the parity of y
+                        // even y, one up for odd y); the step index J has the parity of y.
+                        // Past the south / north edge the neighbour is the ghost row: the
+                        // edge row itself across a no-flow edge, its negative across a
+                        // Dirichlet one (ns: -own, and -(the x ghosts) in the corners)
                         const T* uJ = (J & 1) ? cs1 : cs0;
-                        const T* uJy = (J & 1) ? cs0 : (y == 0 ? cs0 : cs2);
-                        a0 = a0 + prolong_vals(uJ[0], uJ[1], uJy[0], uJy[1]);
-                        a1 = a1 + prolong_vals(uJ[0], uJ[2], uJy[0], uJy[2]);
+                        const bool edge = (J & 1) ? y == n - 1 : y == 0;
+                        const T* uJy = (J & 1) ? (edge ? cs1 : cs0) : (edge ? cs0 : cs2);
+                        const T sg = (edge && ns) ? T(-1) : T(1);
+                        a0 = a0 + prolong_vals(uJ[0], uJ[1], sg * uJy[0], sg * uJy[1]);
+                        a1 = a1 + prolong_vals(uJ[0], uJ[2], sg * uJy[0], sg * uJy[2]);
                     }
                 }
                 p[J][0] = a0;
@@ -649,9 +674,10 @@ __global__ void k_residual_restrict(int nc, size_t S, const T* __restrict__ bf, 
     pc[t] = T(0);
 }
 
-// p_f += P e_c (add = 1, boundary values 0) or p_f = P u_c (add = 0, FMG start).
+// p_f += P e_c (add = 1, boundary values 0) or p_f = P u_c (add = 0, FMG start,
+// the Dirichlet data as ghost values).
 template <typename U>
-__global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE, int add, U* __restrict__ pf,
+__global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, Ghost<U> gh, int add, U* __restrict__ pf,
                           const int32_t* __restrict__ active) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nf = 2 * nc;
@@ -661,7 +687,7 @@ __global__ void k_prolong(int nc, size_t S, const U* __restrict__ uc, U gW, U gE
     if (inactive(active, s)) return;
     const int c = (int)(t % cells);
     const int i = c % nf, j = c / nf;
-    const U v = prolong_at(nc, uc + s * (size_t)nc * nc, i, j, gW, gE);
+    const U v = prolong_at(nc, uc + s * (size_t)nc * nc, i, j, gh);
     pf[t] = add ? pf[t] + v : v;
 }
 
@@ -677,7 +703,7 @@ template <typename T>
 __global__ void k_energy_partials(int n, size_t S, int chunks, const T* __restrict__ b, const T* __restrict__ Te,
                                   const T* __restrict__ Tn, const T* __restrict__ D, const T* __restrict__ x,
                                   const T* __restrict__ ec, const int32_t* __restrict__ active,
-                                  const int32_t* __restrict__ order, double* __restrict__ partial) {
+                                  const int32_t* __restrict__ order, double* __restrict__ partial, int ns) {
     __shared__ double red[2][32];
     if (blockIdx.x / chunks >= S) return;   // S: the samples enumerated (listed by order, if given)
     const size_t s = order ? (size_t)order[blockIdx.x / chunks] : blockIdx.x / chunks;
@@ -693,12 +719,12 @@ __global__ void k_energy_partials(int n, size_t S, int chunks, const T* __restri
         const int i = c % n, j = c / n;
         const size_t g = base + c;
         const T r = residual_at(n, g, i, j, b, Te, Tn, D, x);
-        const T d = prolong_at(nc, e, i, j, T(0), T(0));
+        const T d = prolong_err(nc, e, i, j, ns);
         T ad = mul_rn(D[g], d);
-        if (i > 0) ad = fma(-Te[g - 1], prolong_at(nc, e, i - 1, j, T(0), T(0)), ad);
-        if (i < n - 1) ad = fma(-Te[g], prolong_at(nc, e, i + 1, j, T(0), T(0)), ad);
-        if (j > 0) ad = fma(-Tn[g - n], prolong_at(nc, e, i, j - 1, T(0), T(0)), ad);
-        if (j < n - 1) ad = fma(-Tn[g], prolong_at(nc, e, i, j + 1, T(0), T(0)), ad);
+        if (i > 0) ad = fma(-Te[g - 1], prolong_err(nc, e, i - 1, j, ns), ad);
+        if (i < n - 1) ad = fma(-Te[g], prolong_err(nc, e, i + 1, j, ns), ad);
+        if (j > 0) ad = fma(-Tn[g - n], prolong_err(nc, e, i, j - 1, ns), ad);
+        if (j < n - 1) ad = fma(-Tn[g], prolong_err(nc, e, i, j + 1, ns), ad);
         rd += (double)r * (double)d;
         dad += (double)d * (double)ad;
     }
@@ -740,7 +766,7 @@ __global__ void k_energy_alpha(size_t S, int chunks, const double* __restrict__ 
 // p_f += alpha[s] P e_c, the stepped correction (in FP64, rounded once to T).
 template <typename T>
 __global__ void k_prolong_step(int nc, size_t S, const T* __restrict__ uc, const double* __restrict__ alpha,
-                               T* __restrict__ pf, const int32_t* __restrict__ active) {
+                               T* __restrict__ pf, const int32_t* __restrict__ active, int ns) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nf = 2 * nc;
     const size_t cells = (size_t)nf * nf;
@@ -748,7 +774,7 @@ __global__ void k_prolong_step(int nc, size_t S, const T* __restrict__ uc, const
     const size_t s = t / cells;
     if (inactive(active, s)) return;
     const int c = (int)(t % cells);
-    const T v = prolong_at(nc, uc + s * (size_t)nc * nc, c % nf, c / nf, T(0), T(0));
+    const T v = prolong_err(nc, uc + s * (size_t)nc * nc, c % nf, c / nf, ns);
     pf[t] = (T)((double)pf[t] + alpha[s] * (double)v);
 }
 
@@ -762,7 +788,7 @@ __global__ void k_prolong_step(int nc, size_t S, const T* __restrict__ uc, const
 template <typename T>
 __global__ void k_rbgs_color0_prolong(int n, size_t S, const T* __restrict__ b, const T* __restrict__ Te,
                                       const T* __restrict__ Tn, const T* __restrict__ D, T* __restrict__ p,
-                                      const T* __restrict__ ec, const int32_t* __restrict__ active) {
+                                      const T* __restrict__ ec, const int32_t* __restrict__ active, int ns) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t half = (size_t)n * n / 2;
     if (t >= S * half) return;
@@ -776,10 +802,10 @@ __global__ void k_rbgs_color0_prolong(int n, size_t S, const T* __restrict__ b, 
     const int nc = n / 2;
     const T* e = ec + s * (size_t)nc * nc;
     T acc = b[c];
-    if (i > 0) acc += Te[c - 1] * (p[c - 1] + prolong_at(nc, e, i - 1, j, T(0), T(0)));
-    if (i < n - 1) acc += Te[c] * (p[c + 1] + prolong_at(nc, e, i + 1, j, T(0), T(0)));
-    if (j > 0) acc += Tn[c - n] * (p[c - n] + prolong_at(nc, e, i, j - 1, T(0), T(0)));
-    if (j < n - 1) acc += Tn[c] * (p[c + n] + prolong_at(nc, e, i, j + 1, T(0), T(0)));
+    if (i > 0) acc += Te[c - 1] * (p[c - 1] + prolong_err(nc, e, i - 1, j, ns));
+    if (i < n - 1) acc += Te[c] * (p[c + 1] + prolong_err(nc, e, i + 1, j, ns));
+    if (j > 0) acc += Tn[c - n] * (p[c - n] + prolong_err(nc, e, i, j - 1, ns));
+    if (j < n - 1) acc += Tn[c] * (p[c + n] + prolong_err(nc, e, i, j + 1, ns));
     p[c] = acc * (T(1) / D[c]);
 }
 
@@ -791,7 +817,7 @@ constexpr int kInvWarps = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kInvWarps) k_coarse_inverse(int n0, size_t S, const double* __restrict__ K,
-                                                                   T* __restrict__ Ainv) {
+                                                                   T* __restrict__ Ainv, int ns) {
     __shared__ double sh[kInvWarps][2][16][16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t s = (size_t)blockIdx.x * kInvWarps + warp;
@@ -808,8 +834,9 @@ __global__ void __launch_bounds__(32 * kInvWarps) k_coarse_inverse(int n0, size_
         const int i = r % n0, j = r / n0;
         const double tw = (i > 0) ? harmonic(k[r - 1], k[r]) : 2.0 * k[r];
         const double te = (i < n0 - 1) ? harmonic(k[r], k[r + 1]) : 2.0 * k[r];
-        const double ts = (j > 0) ? harmonic(k[r - n0], k[r]) : 0.0;
-        const double tn = (j < n0 - 1) ? harmonic(k[r], k[r + n0]) : 0.0;
+        const double tb = ns ? 2.0 * k[r] : 0.0;   // north / south boundary face
+        const double ts = (j > 0) ? harmonic(k[r - n0], k[r]) : tb;
+        const double tn = (j < n0 - 1) ? harmonic(k[r], k[r + n0]) : tb;
         A[r][r] = tw + te + ts + tn;
         if (i > 0) A[r][r - 1] = -tw;
         if (i < n0 - 1) A[r][r + 1] = -te;
@@ -857,17 +884,26 @@ __global__ void k_coarse_solve(int m, size_t S, const T* __restrict__ Ainv, cons
     p[t] = acc;
 }
 
-// Q = sum_j 2 K_(n-1,j) (p_(n-1,j) - pE), one warp per sample, shuffle reduction.
+// The QoI of Table 1, one warp per sample.  Case II: the east outflux
+// Q = sum_j 2 K_(n-1,j) (p_(n-1,j) - pE), shuffle reduction.  Case I:
+// u(0.5, 0.5), the mean of the four cells at the centre.
 template <typename P>
-__global__ void k_outflux(int n, size_t S, const double* __restrict__ K, const P* __restrict__ p, double pE,
+__global__ void k_outflux(int n, size_t S, const double* __restrict__ K, const P* __restrict__ p, Bnd bd,
                           double* __restrict__ q) {
     const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x & 31;
     if (warp >= S) return;
+    if (bd.ns) {
+        if (lane == 0) {
+            const size_t c = warp * (size_t)n * n + (size_t)(n / 2 - 1) * n + n / 2 - 1;
+            q[warp] = 0.25 * (((double)p[c] + (double)p[c + 1]) + ((double)p[c + n] + (double)p[c + n + 1]));
+        }
+        return;
+    }
     const size_t base = warp * (size_t)n * n + (n - 1);
     double acc = 0.0;
     for (int j = lane; j < n; j += 32)
-        acc += 2.0 * K[base + (size_t)j * n] * ((double)p[base + (size_t)j * n] - pE);
+        acc += 2.0 * K[base + (size_t)j * n] * ((double)p[base + (size_t)j * n] - bd.g[1]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) q[warp] = acc;
@@ -888,7 +924,7 @@ __global__ void k_fill(size_t count, double v, double* __restrict__ x) {
 // zeroed.  k_stage_decide then folds the partials in chunk order.  b / bT
 // and p / pT are the same arrays, hence no __restrict__ on them.
 template <typename T>
-__global__ void k_stage_partials(int n, size_t S, int chunks, const double* __restrict__ K, double pW, double pE,
+__global__ void k_stage_partials(int n, size_t S, int chunks, const double* __restrict__ K, Bnd bd,
                                  const T* b, const T* __restrict__ Te, const T* __restrict__ Tn,
                                  const T* __restrict__ D, const T* p, const double* __restrict__ p64,
                                  const double* __restrict__ Te64, const double* __restrict__ Tn64,
@@ -907,10 +943,13 @@ __global__ void k_stage_partials(int n, size_t S, int chunks, const double* __re
     for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const int i = c % n, j = c / n;
         const size_t g = base + c;
-        if (i == n - 1) qq += 2.0 * K[g] * ((p64 ? p64[g] : (double)p[g]) - pE);
-        double f = 0.0;
-        if (i == 0) f += 2.0 * K[g] * pW;
-        if (i == n - 1) f += 2.0 * K[g] * pE;
+        const double pv = p64 ? p64[g] : (double)p[g];
+        if (bd.ns) {   // Case I: u(0.5, 0.5), the four centre cells
+            if ((i == n / 2 - 1 || i == n / 2) && (j == n / 2 - 1 || j == n / 2)) qq += 0.25 * pv;
+        } else if (i == n - 1) {
+            qq += 2.0 * K[g] * (pv - bd.g[1]);
+        }
+        const double f = dirichlet_rhs(bd, n, i, j, K[g]);
         double r;
         if (p64) {
             double v = D64[g] * p64[g];
@@ -1192,7 +1231,7 @@ static int strip_segment(int n, size_t S, int strips, int HS, int VH, int reside
 template <typename T, int HS, bool FUSE>
 static void strip_launch(fm_ctx* ctx, int n, size_t S, const T* b, const T* Te, const T* Tn, const T* D,
                          const T* p_in, T* p_out, const int32_t* active, const T* ec, T* bc, T* pc,
-                         cudaStream_t st, size_t busy, const int32_t* order) {
+                         cudaStream_t st, size_t busy, const int32_t* order, int ns) {
     constexpr int OW = strip_ow(HS, FUSE), VH = strip_xh(HS, FUSE);
     const int strips = (n + OW - 1) / OW;
     // with the host's count of active samples and their list, enumerate only those
@@ -1207,7 +1246,7 @@ static void strip_launch(fm_ctx* ctx, int n, size_t S, const T* b, const T* Te, 
     FM_TIMED(ctx, kFamSmootherStrip, st, bytes, flops,
              k_rbgs_strip<T, HS, FUSE><<<grid, 32 * kStripWarps, 0, st>>>(n, sb, strips, seg, segs, b, Te, Tn, D,
                                                                          p_in, p_out, active, ec, bc, pc,
-                                                                         listed ? order : nullptr));
+                                                                         listed ? order : nullptr, ns));
 }
 
 // Launch shape code of the column-strip smoother (tile codes are > 0, colour
@@ -1232,16 +1271,16 @@ static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
 template <typename T>
 static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int nsweeps, const T* b, const T* Te,
                       const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st,
-                      const T* ec = nullptr, size_t busy = 0, const int32_t* order = nullptr) {
+                      const T* ec = nullptr, size_t busy = 0, const int32_t* order = nullptr, int ns = 0) {
     if (nsweeps <= 0) return p_in;
     const size_t cells = S * (size_t)n * n;
     if (tile == kShapeStrip) {
         if (nsweeps == 2)
             strip_launch<T, 4, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
-                                      order);
+                                      order, ns);
         else
             strip_launch<T, 2, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
-                                      order);
+                                      order, ns);
         return p_out;
     }
     if (tile > 0) {
@@ -1257,30 +1296,30 @@ static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int n
         if (threads == 0 && hh == 0 && (n == 8 || n == 16 || n == 32 || (f32 && n == 64))) {
             if (n == 8)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 8, 1><<<grid, 4 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             else if (n == 16)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 16, 2><<<grid, 8 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             else if (n == 32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 32, 4><<<grid, 16 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             else if constexpr (f32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 64, 8><<<grid, 32 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             return p_out;
         }
         if (threads == 0 && hh > 0 && hh <= 4 && (TI == 32 || (f32 && TI == 64))) {
             if (TI == 32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 40, 5><<<grid, 20 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             else if constexpr (f32)
                 FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops, k_rbgs_tile_reg<T, 72, 9><<<grid, 36 * 8, 0, st>>>(
-                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                    n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
             return p_out;
         }
         FM_TIMED(ctx, kFamSmootherTile, st, bytes, flops,
                  k_rbgs_tile<T><<<grid, threads > 0 ? threads : 256, tile_smem_bytes(tile, n, nsweeps, sizeof(T)),
-                                  st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec));
+                                  st>>>(n, S, TI, hh, nsweeps, b, Te, Tn, D, p_in, p_out, active, ec, ns));
         return p_out;
     }
     T* p = p_in;
@@ -1330,6 +1369,7 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     const GridBufs<T>& g = H.g[k];
     const double ts = sizeof(T);
     const bool stage_op = (k == top);
+    const int ns = prm.bc_case == FM_CASE_I ? 1 : 0;   // Dirichlet north / south edges (Table 1, Case I)
     const T* Te = stage_op ? g.Te : g.TeC;
     const T* Tn = stage_op ? g.Tn : g.TnC;
     const T* D = stage_op ? g.D : g.DC;
@@ -1351,14 +1391,14 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
         // strips form the residual and its restriction in the same pass
         if (prm.nu1 == 2)
             strip_launch<T, 4, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
-                                     H.order);
+                                     H.order, ns);
         else
             strip_launch<T, 2, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
-                                     H.order);
+                                     H.order, ns);
         cur = g.p2;
     } else {
         cur = smooth_with<T>(ctx, tile, threads, n, S, prm.nu1, g.b, Te, Tn, D, g.p, g.p2, active, st, nullptr,
-                             H.busy, H.order);
+                             H.busy, H.order, ns);
         FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
                  k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
                      c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
@@ -1368,21 +1408,21 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
         // the stepped correction (converged mode: partials and alpha in the hierarchy)
         const int chunks = check_chunks(n);
         const bool listed = H.listed();
-        const size_t ns = listed ? H.busy : S;
-        FM_TIMED(ctx, kFamProlong, st, (5.0 * ts + 1.25 * ts) * ns * n * n + 2.0 * ts * cells, 40.0 * ns * n * n,
-                 k_energy_partials<T><<<(unsigned)(ns * chunks), kBlock, 0, st>>>(
-                     n, ns, chunks, g.b, Te, Tn, D, cur, c.p, active, listed ? H.order : nullptr, H.partial);
+        const size_t nl = listed ? H.busy : S;
+        FM_TIMED(ctx, kFamProlong, st, (5.0 * ts + 1.25 * ts) * nl * n * n + 2.0 * ts * cells, 40.0 * nl * n * n,
+                 k_energy_partials<T><<<(unsigned)(nl * chunks), kBlock, 0, st>>>(
+                     n, nl, chunks, g.b, Te, Tn, D, cur, c.p, active, listed ? H.order : nullptr, H.partial, ns);
                  k_energy_alpha<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, H.alpha, active);
-                 k_prolong_step<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, H.alpha, cur, active));
+                 k_prolong_step<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, H.alpha, cur, active, ns));
         smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
-                       H.order);
+                       H.order, ns);
         return;
     }
     if (tile == 0 && prm.nu2 >= 1) {
         // colour launches: the correction rides in the first post-smoothing colour
         FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells + ts * S * c.n * c.n, 5.0 * cells,
                  k_rbgs_color0_prolong<T><<<blocks_for(cells / 2), kBlock, 0, st>>>(n, S, g.b, Te, Tn, D, cur, c.p,
-                                                                                    active));
+                                                                                    active, ns));
         FM_TIMED(ctx, kFamSmoother, st, 3.0 * ts * cells, 5.0 * cells,
                  k_rbgs_color<T><<<blocks_for(cells / 2), kBlock, 0, st>>>(n, S, 1, g.b, Te, Tn, D, cur, active));
         smooth_with<T>(ctx, 0, 0, n, S, prm.nu2 - 1, g.b, Te, Tn, D, cur, g.p, active, st);
@@ -1391,20 +1431,21 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     if (tile != 0 && prm.nu2 >= 1) {
         // tiles and strips: the correction is added as they load the iterate
         smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, c.p, H.busy,
-                       H.order);
+                       H.order, ns);
         return;
     }
+    const Ghost<T> zero{T(0), T(0), T(0), T(0), ns};
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
-             k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, T(0), T(0), 1, cur, active));
+             k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, zero, 1, cur, active));
     smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
-                   H.order);
+                   H.order, ns);
 }
 
 template <typename P>
-static void outflux(fm_ctx* ctx, int n, size_t S, const double* K, const P* p, double pE, double* q,
+static void outflux(fm_ctx* ctx, int n, size_t S, const double* K, const P* p, const Bnd& bd, double* q,
                     cudaStream_t st) {
     FM_TIMED(ctx, kFamOutflux, st, 16.0 * S * n, 3.0 * S * n,
-             k_outflux<P><<<blocks_for(S * 32), kBlock, 0, st>>>(n, S, K, p, pE, q));
+             k_outflux<P><<<blocks_for(S * 32), kBlock, 0, st>>>(n, S, K, p, bd, q));
 }
 
 // One residual test of the refined stage on grid k (partials, then the decision).
@@ -1417,7 +1458,7 @@ static void stage_test(const Hierarchy<T>& H, int k, const fm_solve_params& prm,
     const size_t ns = H.listed() ? H.busy : S;
     FM_TIMED(ctx, kFamResidualRestrict, st, (mixed ? 48.0 : 40.0) * ns * cells, 12.0 * ns * cells,
              k_stage_partials<T><<<(unsigned)(ns * chunks), kBlock, 0, st>>>(
-                 g.n, ns, chunks, g.K, prm.pW, prm.pE, g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64, g.b,
+                 g.n, ns, chunks, g.K, bnd_of(prm), g.b, g.Te, g.Tn, g.D, g.p, g.p64, g.Te64, g.Tn64, g.D64, g.b,
                  g.p, H.active, H.partial, H.listed() ? H.order : nullptr);
              k_stage_decide<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, prm.tol, prm.qtol, H.qprev,
                                                               H.active, H.left, H.order));
@@ -1522,6 +1563,7 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
     const bool mixed = prm.precision == FM_PREC_MIXED;
     const bool conv = prm.converged != 0;
     const double ts = sizeof(T);
+    const Bnd bd = bnd_of(prm);
     if (status) FM_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int32_t) * S, st));
     // coefficient hierarchy: inject, then faces and diagonals on every grid
     for (int k = H.m; k >= 1; --k) {
@@ -1536,11 +1578,11 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
         // FP64 arithmetic for FP64 grids and for the refined grids' FP64 copies
         if (sizeof(T) == 8 || g.Te64)
             FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts + (g.Te64 ? 24.0 : 0.0)) * cells, 16.0 * cells,
-                     k_coefficients<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D,
-                                                                                     g.Te64, g.Tn64, g.D64));
+                     k_coefficients<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn,
+                                                                                     g.D, g.Te64, g.Tn64, g.D64));
         else
             FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts) * cells, 16.0 * cells,
-                     k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, g.Te, g.Tn, g.D,
+                     k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn, g.D,
                                                                                nullptr, nullptr, nullptr));
     }
     for (int k = 0; k < H.m; ++k) {
@@ -1548,19 +1590,20 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
         const size_t cells = S * (size_t)g.n * g.n;
         FM_TIMED(ctx, kFamCoefficients, st, (32.0 + 8.0 + 3.0 * ts) * cells, 40.0 * cells,
                  k_child_geomean<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, H.g[k + 1].K, g.Kc);
-                 k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.Kc, g.TeC, g.TnC, g.DC,
+                 k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.Kc, g.TeC, g.TnC, g.DC,
                                                                             nullptr, nullptr, nullptr));
     }
     if (H.m >= 1) {
         const int m = H.n0 * H.n0;
         FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (8 * m + ts * m * m), 2.0 * S * m * m * m,
                  k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(
-                     H.n0, S, H.g[0].Kc, H.AinvC));
+                     H.n0, S, H.g[0].Kc, H.AinvC, bd.ns));
     }
     {
         const int m = H.n0 * H.n0;
         FM_TIMED(ctx, kFamCoarseInverse, st, (double)S * (8 * m + ts * m * m), 2.0 * S * m * m * m,
-                 k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(H.n0, S, H.g[0].K, H.Ainv));
+                 k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(H.n0, S, H.g[0].K, H.Ainv,
+                                                                                                 bd.ns));
     }
     for (int k = 0; k <= H.m; ++k) {
         const GridBufs<T>& g = H.g[k];
@@ -1570,16 +1613,18 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
             const GridBufs<T>& c = H.g[k - 1];
             if (mixed && refined && k == H.m && H.m >= 1) {
                 FM_TIMED(ctx, kFamFmgInterp, st, 10.0 * cells, 8.0 * cells,
-                         k_prolong<double><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p64, prm.pW, prm.pE, 0,
-                                                                                 g.p64, nullptr));
+                         k_prolong<double><<<blocks_for(cells), kBlock, 0, st>>>(
+                             c.n, S, c.p64, Ghost<double>{bd.g[0], bd.g[1], bd.g[2], bd.g[3], bd.ns}, 0, g.p64,
+                             nullptr));
             } else {
                 FM_TIMED(ctx, kFamFmgInterp, st, 1.25 * ts * cells, 8.0 * cells,
-                         k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, (T)prm.pW, (T)prm.pE, 0,
-                                                                            g.p, nullptr));
+                         k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(
+                             c.n, S, c.p, Ghost<T>{(T)bd.g[0], (T)bd.g[1], (T)bd.g[2], (T)bd.g[3], bd.ns}, 0, g.p,
+                             nullptr));
             }
         }
         FM_TIMED(ctx, kFamStageRhs, st, (8.0 + ts) * cells, 2.0 * cells,
-                 k_stage_rhs<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, prm.pW, prm.pE, g.b));
+                 k_stage_rhs<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, g.K, bd, g.b));
         if (k == 0) vcycle(H, 0, 0, prm, nullptr, st);
         if (!refined) {
             if (k > 0)
@@ -1590,15 +1635,15 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
             FM_TRY(refine_stage(H, k, prm, mixed, status, st));
         }
         if (k == H.m - 1 && qc) {
-            if (mixed && refined) outflux(ctx, g.n, S, g.K, g.p64, prm.pE, qc, st);
-            else outflux(ctx, g.n, S, g.K, g.p, prm.pE, qc, st);
+            if (mixed && refined) outflux(ctx, g.n, S, g.K, g.p64, bd, qc, st);
+            else outflux(ctx, g.n, S, g.K, g.p, bd, qc, st);
         }
     }
     const GridBufs<T>& f = H.g[H.m];
     const bool fine64 = mixed && conv;
     if (H.m == 0 && qc) k_fill<<<blocks_for(S), kBlock, 0, st>>>(S, std::nan(""), qc);
-    if (fine64) outflux(ctx, f.n, S, f.K, f.p64, prm.pE, qf, st);
-    else outflux(ctx, f.n, S, f.K, f.p, prm.pE, qf, st);
+    if (fine64) outflux(ctx, f.n, S, f.K, f.p64, bd, qf, st);
+    else outflux(ctx, f.n, S, f.K, f.p, bd, qf, st);
     if (p_out) {
         const size_t cells = S * (size_t)f.n * f.n;
         if (fine64)
@@ -1660,6 +1705,8 @@ fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const d
     FM_CHECK_ARG(ctx, S == 0 || (d_K && d_qf), "fmg_solve_batch: null input or output");
     FM_CHECK_ARG(ctx, prm.kernel >= FM_KERNEL_AUTO && prm.kernel <= FM_KERNEL_RESIDENT,
                  "fmg_solve_batch: unknown kernel schedule");
+    FM_CHECK_ARG(ctx, prm.bc_case == 0 || prm.bc_case == FM_CASE_I || prm.bc_case == FM_CASE_II,
+                 "fmg_solve_batch: bc_case must be FM_CASE_I or FM_CASE_II");
     FM_CHECK_ARG(ctx, !prm.energy_step || (prm.converged && prm.kernel != FM_KERNEL_RESIDENT),
                  "fmg_solve_batch: the energy-optimal correction step runs in converged mode on the level-wise "
                  "schedule");
@@ -1914,6 +1961,8 @@ extern "C" fm_status fmg_solve_batch_static(fm_ctx* ctx, int32_t n_fine, uint32_
     // the energy step keeps per-sample dot products and step lengths that the
     // static hierarchy has no room for
     FM_CHECK_ARG(ctx, !prm->energy_step, "fmg_solve_batch_static: the energy-optimal step is not available here");
+    FM_CHECK_ARG(ctx, prm->bc_case == 0 || prm->bc_case == FM_CASE_I || prm->bc_case == FM_CASE_II,
+                 "fmg_solve_batch_static: bc_case must be FM_CASE_I or FM_CASE_II");
     FM_CHECK_ARG(ctx, n == 0 || (d_K && d_qf), "fmg_solve_batch_static: null input or output");
     if (n == 0) return FM_OK;
     const size_t need = hierarchy_bytes(n_fine, n0, n, 8, false, false);

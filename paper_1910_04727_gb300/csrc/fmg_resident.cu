@@ -10,6 +10,9 @@
 //   te   east-face transmissibility (2K on the east edge)
 //   tn   north-face transmissibility (0 on the north edge)
 //   tw   west-edge transmissibility 2K of each row (n values)
+//   ts   south-edge transmissibility of each column (n values: 2K in Case I of
+//        Table 1, where the south and north edges are Dirichlet, else 0; tn
+//        of the north row likewise holds the north-edge face)
 //   dinv reciprocal diagonal (FP64 form, and the mixed form up to 16 x 16;
 //        otherwise the FP32 smoother divides by D formed from the faces)
 //   b    right-hand side.  In the FP64 form the finest grid has none: it only
@@ -30,12 +33,12 @@ namespace fm {
 template <typename T>
 struct RGrid {
     int n;
-    T *p, *te, *tn, *dinv, *tw, *b;   // dinv and b may be null
+    T *p, *te, *tn, *dinv, *tw, *ts, *b;   // dinv and b may be null
 };
 
 struct HGrid {
     int n;
-    double *p, *te, *tn, *tw;
+    double *p, *te, *tn, *tw, *ts;
 };
 
 template <typename T>
@@ -71,6 +74,7 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         g.te = (T*)take(c * sizeof(T));
         g.tn = (T*)take(c * sizeof(T));
         g.tw = (T*)take(n * sizeof(T));
+        g.ts = (T*)take(n * sizeof(T));
         // the mixed form keeps 1/D only for hierarchies up to 16 x 16 (one
         // sample per warp), where it costs no occupancy; larger ones form D
         // from the faces and divide
@@ -81,13 +85,14 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         const int k = L.m - 1 + q;
         HGrid& h = L.h[q];
         h.n = (k >= 0) ? (n0 << k) : 0;
-        h.p = h.te = h.tn = h.tw = nullptr;
+        h.p = h.te = h.tn = h.tw = h.ts = nullptr;
         if (!mixed || k < 0) continue;
         const size_t c = (size_t)h.n * h.n;
         h.p = (double*)take(c * 8);
         h.te = (double*)take(c * 8);
         h.tn = (double*)take(c * 8);
         h.tw = (double*)take(h.n * 8);
+        h.ts = (double*)take(h.n * 8);
     }
     L.ainv = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
     L.work = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
@@ -117,7 +122,7 @@ struct Res {
 // Face transmissibilities of grid n, K injected from the fine field at
 // stride s = n_fine / n (read from global memory; L1/L2 serve the reuse).
 static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, const double* __restrict__ Kf,
-                                    int n_fine) {
+                                    int n_fine, int ns) {
     // FP64 faces where an FP64 copy is kept (or T is FP64); otherwise the
     // FP32 correction-solver coefficients are formed in FP32
     const int n = g.n, s = n_fine / n;
@@ -126,31 +131,36 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
         const int i = c % n, j = c / n;
         if (h || sizeof(T) == 8) {
             const double k = K(i, j);
+            const double tb = ns ? 2.0 * k : 0.0;   // south / north edge face
             const double te = (i < n - 1) ? harm(k, K(i + 1, j)) : 2.0 * k;
-            const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : 0.0;
+            const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : tb;
             g.te[c] = (T)te;
             g.tn[c] = (T)tn;
             if (g.dinv) {   // the FP64 form's diagonal (the mixed form forms it on the fly)
                 const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
-                const double ts = (j > 0) ? harm(K(i, j - 1), k) : 0.0;
+                const double ts = (j > 0) ? harm(K(i, j - 1), k) : tb;
                 g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
             }
             if (i == 0) g.tw[j] = (T)(2.0 * k);
+            if (j == 0) g.ts[i] = (T)tb;
             if (h) {
                 h->te[c] = te;
                 h->tn[c] = tn;
                 if (i == 0) h->tw[j] = 2.0 * k;
+                if (j == 0) h->ts[i] = tb;
             }
         } else {
             const T k = (T)K(i, j);
+            const T tb = ns ? T(2) * k : T(0);
             const T tw = (i > 0) ? harm((T)K(i - 1, j), k) : T(2) * k;
             const T te = (i < n - 1) ? harm(k, (T)K(i + 1, j)) : T(2) * k;
-            const T ts = (j > 0) ? harm((T)K(i, j - 1), k) : T(0);
-            const T tn = (j < n - 1) ? harm(k, (T)K(i, j + 1)) : T(0);
+            const T ts = (j > 0) ? harm((T)K(i, j - 1), k) : tb;
+            const T tn = (j < n - 1) ? harm(k, (T)K(i, j + 1)) : tb;
             g.te[c] = te;
             g.tn[c] = tn;
             if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
             if (i == 0) g.tw[j] = T(2) * k;
+            if (j == 0) g.ts[i] = tb;
         }
     }
 }
@@ -159,7 +169,8 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
 // geometric mean of its four children on the injected grid 2n, i.e. of the
 // fine field at stride s/2.  Uses the grid's iterate as scratch, so it runs
 // once the grid's stage solution has been interpolated to the next grid.
-static __device__ void resident_setup_correction(const RGrid<T>& g, const double* __restrict__ Kf, int n_fine) {
+static __device__ void resident_setup_correction(const RGrid<T>& g, const double* __restrict__ Kf, int n_fine,
+                                                 int ns) {
     const int n = g.n, s = n_fine / n, h2 = s / 2;
     for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
@@ -174,31 +185,42 @@ static __device__ void resident_setup_correction(const RGrid<T>& g, const double
     for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         const T k = g.p[c];
+        const T tb = ns ? T(2) * k : T(0);
         const T tw = (i > 0) ? harm(g.p[c - 1], k) : T(2) * k;
         const T te = (i < n - 1) ? harm(k, g.p[c + 1]) : T(2) * k;
-        const T ts = (j > 0) ? harm(g.p[c - n], k) : T(0);
-        const T tn = (j < n - 1) ? harm(k, g.p[c + n]) : T(0);
+        const T ts = (j > 0) ? harm(g.p[c - n], k) : tb;
+        const T tn = (j < n - 1) ? harm(k, g.p[c + n]) : tb;
         g.te[c] = te;
         g.tn[c] = tn;
         if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
         if (i == 0) g.tw[j] = T(2) * k;
+        if (j == 0) g.ts[i] = tb;
     }
     sync();
 }
 
 // ------------------------------------------------------------------ V-cycle pieces
-// Right-hand side of cell (i, j): stored, or the stage problem's Dirichlet data.
-static __device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
-    if (g.b) return g.b[c];
-    T v = T(0);
-    if (i == 0) v += g.tw[j] * pW;
-    if (i == g.n - 1) v += g.te[c] * pE;
+// The stage problem's Dirichlet data of cell (i, j) moved to the rhs (the
+// south / north edge faces are 0 unless those edges are Dirichlet).
+template <typename G, typename U>
+static __device__ __forceinline__ U dirichlet_at(const G& g, int c, int i, int j, const Ghost<U>& d) {
+    U v = U(0);
+    if (i == 0) v += g.tw[j] * d.w;
+    if (i == g.n - 1) v += g.te[c] * d.e;
+    if (d.ns && j == 0) v += g.ts[i] * d.s;
+    if (d.ns && j == g.n - 1) v += g.tn[c] * d.n;
     return v;
+}
+
+// Right-hand side of cell (i, j): stored, or the stage problem's Dirichlet data.
+static __device__ __forceinline__ T rhs_at(const RGrid<T>& g, int c, int i, int j, const Ghost<T>& d) {
+    if (g.b) return g.b[c];
+    return dirichlet_at(g, c, i, j, d);
 }
 
 static __device__ __forceinline__ T diag_at(const RGrid<T>& g, int c, int i, int j) {
     const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
-    const T ts = (j > 0) ? g.tn[c - g.n] : T(0);
+    const T ts = (j > 0) ? g.tn[c - g.n] : g.ts[i];
     return tw + g.te[c] + ts + g.tn[c];
 }
 
@@ -249,24 +271,24 @@ static __device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A)
     }
 }
 
-static __device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, const T* ainv, T pW, T pE) {
+static __device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, const T* ainv, const Ghost<T>& d) {
     const int n = g.n, m = n * n;
     T acc = T(0);
     if (rank() < m)
-        for (int c = 0; c < m; ++c) acc += ainv[rank() * m + c] * rhs_at(g, c, c % n, c / n, pW, pE);
+        for (int c = 0; c < m; ++c) acc += ainv[rank() * m + c] * rhs_at(g, c, c % n, c / n, d);
     sync();
     if (rank() < m) g.p[rank()] = acc;
     sync();
 }
 
-static __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T pE) {
+static __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, const Ghost<T>& d) {
     const int n = g.n, half = n * n / 2, hn = n / 2;
     for (int color = 0; color < 2; ++color) {
         for (int h = rank(); h < half; h += size()) {
             const int j = h / hn;
             const int i = 2 * (h % hn) + ((j + color) & 1);
             const int c = j * n + i;
-            T acc = rhs_at(g, c, i, j, pW, pE);
+            T acc = rhs_at(g, c, i, j, d);
             if (i > 0) acc += g.te[c - 1] * g.p[c - 1];
             if (i < n - 1) acc += g.te[c] * g.p[c + 1];
             if (j > 0) acc += g.tn[c - n] * g.p[c - n];
@@ -277,48 +299,62 @@ static __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, T pW, T 
     }
 }
 
-static __device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, int j, T pW, T pE) {
+static __device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, int i, int j, const Ghost<T>& d) {
     const int n = g.n;
     T v = diag_at(g, c, i, j) * g.p[c];
     if (i > 0) v -= g.te[c - 1] * g.p[c - 1];
     if (i < n - 1) v -= g.te[c] * g.p[c + 1];
     if (j > 0) v -= g.tn[c - n] * g.p[c - n];
     if (j < n - 1) v -= g.tn[c] * g.p[c + n];
-    return rhs_at(g, c, i, j, pW, pE) - v;
+    return rhs_at(g, c, i, j, d) - v;
 }
 
-static __device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, T pW, T pE) {
+static __device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, const Ghost<T>& d) {
     const int nc = cg.n, nf = f.n;
     for (int C = rank(); C < nc * nc; C += size()) {
         const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J, c0 = j0 * nf + i0;
-        const T r00 = resident_residual(f, c0, i0, j0, pW, pE);
-        const T r10 = resident_residual(f, c0 + 1, i0 + 1, j0, pW, pE);
-        const T r01 = resident_residual(f, c0 + nf, i0, j0 + 1, pW, pE);
-        const T r11 = resident_residual(f, c0 + nf + 1, i0 + 1, j0 + 1, pW, pE);
+        const T r00 = resident_residual(f, c0, i0, j0, d);
+        const T r10 = resident_residual(f, c0 + 1, i0 + 1, j0, d);
+        const T r01 = resident_residual(f, c0 + nf, i0, j0 + 1, d);
+        const T r11 = resident_residual(f, c0 + nf + 1, i0 + 1, j0 + 1, d);
         cg.b[C] = r00 + r10 + r01 + r11;
         cg.p[C] = T(0);
     }
     sync();
 }
 
+// Coarse value with ghosts: 2g - u across a Dirichlet edge, the edge value
+// mirrored across a no-flow edge; a corner ghost takes the x rule on the y
+// ghost.
 template <typename U>
-static __device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, U gW, U gE) {
-    J = J < 0 ? 0 : (J > nc - 1 ? nc - 1 : J);
-    if (I < 0) return U(2) * gW - uc[J * nc];
-    if (I > nc - 1) return U(2) * gE - uc[J * nc + nc - 1];
+static __device__ __forceinline__ U ghost_x(const U* uc, int nc, int I, int J, const Ghost<U>& g) {
+    if (I < 0) return U(2) * g.w - uc[J * nc];
+    if (I > nc - 1) return U(2) * g.e - uc[J * nc + nc - 1];
     return uc[J * nc + I];
+}
+template <typename U>
+static __device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, const Ghost<U>& g) {
+    if (J < 0) {
+        const U edge = ghost_x(uc, nc, I, 0, g);
+        return g.ns ? U(2) * g.s - edge : edge;
+    }
+    if (J > nc - 1) {
+        const U edge = ghost_x(uc, nc, I, nc - 1, g);
+        return g.ns ? U(2) * g.n - edge : edge;
+    }
+    return ghost_x(uc, nc, I, J, g);
 }
 
 // out (+)= bilinear interpolation of uc (nc x nc) onto the 2nc x 2nc grid.
 template <typename U>
-static __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, U gW, U gE, bool add) {
+static __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, const Ghost<U>& gd, bool add) {
     const int nf = 2 * nc;
     for (int c = rank(); c < nf * nf; c += size()) {
         const int i = c % nf, j = c / nf, I = i >> 1, J = j >> 1;
         const int Ix = (i & 1) ? I + 1 : I - 1;
         const int Jy = (j & 1) ? J + 1 : J - 1;
-        const U v = (U(9) * ghost(uc, nc, I, J, gW, gE) + U(3) * ghost(uc, nc, Ix, J, gW, gE) +
-                     U(3) * ghost(uc, nc, I, Jy, gW, gE) + U(1) * ghost(uc, nc, Ix, Jy, gW, gE)) /
+        const U v = (U(9) * ghost(uc, nc, I, J, gd) + U(3) * ghost(uc, nc, Ix, J, gd) +
+                     U(3) * ghost(uc, nc, I, Jy, gd) + U(1) * ghost(uc, nc, Ix, Jy, gd)) /
                     U(16);
         out[c] = add ? out[c] + v : v;
     }
@@ -327,16 +363,18 @@ static __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* 
 
 // One V(nu1, nu2) cycle on grid k, iteratively: descend (smooth, restrict
 // the residual), exact coarsest solve, ascend (prolong the correction,
-// smooth).  pW/pE only enter through a grid without a stored rhs.
-static __device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, T pW, T pE) {
+// smooth).  The boundary data d only enter through a grid without a stored
+// rhs; the corrections take zero ghost data on the same edges.
+static __device__ void resident_vcycle(const RLayout<T>& L, int k, int nu1, int nu2, const Ghost<T>& d) {
     for (int l = k; l >= 1; --l) {
-        for (int s = 0; s < nu1; ++s) resident_rbgs(L.g[l], pW, pE);
-        resident_restrict(L.g[l], L.g[l - 1], pW, pE);
+        for (int s = 0; s < nu1; ++s) resident_rbgs(L.g[l], d);
+        resident_restrict(L.g[l], L.g[l - 1], d);
     }
-    resident_coarse_solve(L.g[0], L.ainv, pW, pE);
+    resident_coarse_solve(L.g[0], L.ainv, d);
+    const Ghost<T> zero{T(0), T(0), T(0), T(0), d.ns};
     for (int l = 1; l <= k; ++l) {
-        resident_prolong(L.g[l - 1].p, L.g[l - 1].n, L.g[l].p, T(0), T(0), true);
-        for (int s = 0; s < nu2; ++s) resident_rbgs(L.g[l], pW, pE);
+        resident_prolong(L.g[l - 1].p, L.g[l - 1].n, L.g[l].p, zero, true);
+        for (int s = 0; s < nu2; ++s) resident_rbgs(L.g[l], d);
     }
 }
 
@@ -374,24 +412,21 @@ static __device__ __forceinline__ void block_sum2(double a, double b, double* re
 }
 
 // Stage problem of grid k written into its rhs: the Dirichlet data.
-static __device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, T pW, T pE) {
+static __device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, const Ghost<T>& d) {
     for (int c = rank(); c < g.n * g.n; c += size()) {
         const int i = c % g.n, j = c / g.n;
-        T v = T(0);
-        if (i == 0) v += g.tw[j] * pW;
-        if (i == g.n - 1) v += g.te[c] * pE;
-        g.b[c] = v;
+        g.b[c] = dirichlet_at(g, c, i, j, d);
     }
     sync();
 }
 
 // ||r||^2 and ||rhs||^2 of the stage problem on grid k (V-cycle type).
-static __device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, double& rr, double& bb) {
+static __device__ void stage_norms(const RGrid<T>& g, const Ghost<T>& d, double* red, double& rr, double& bb) {
     double a = 0.0, b = 0.0;
     for (int c = rank(); c < g.n * g.n; c += size()) {
         const int i = c % g.n, j = c / g.n;
-        const double r = (double)resident_residual(g, c, i, j, pW, pE);
-        const double f = (double)rhs_at(g, c, i, j, pW, pE);
+        const double r = (double)resident_residual(g, c, i, j, d);
+        const double f = (double)rhs_at(g, c, i, j, d);
         a += r * r;
         b += f * f;
     }
@@ -400,17 +435,15 @@ static __device__ void stage_norms(const RGrid<T>& g, T pW, T pE, double* red, d
 
 // FP64 residual of the stage problem on h into the FP32 grid's rhs (the
 // correction equation), zero the correction; returns the norms.
-static __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW, double pE, double* red,
+static __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, const Ghost<double>& d, double* red,
                             double& rr, double& bb) {
     const int n = h.n;
     double a = 0.0, b = 0.0;
     for (int c = rank(); c < n * n; c += size()) {
         const int i = c % n, j = c / n;
         const double tw = (i > 0) ? h.te[c - 1] : h.tw[j];
-        const double ts = (j > 0) ? h.tn[c - n] : 0.0;
-        double f = 0.0;
-        if (i == 0) f += h.tw[j] * pW;
-        if (i == n - 1) f += h.te[c] * pE;
+        const double ts = (j > 0) ? h.tn[c - n] : h.ts[i];
+        const double f = dirichlet_at(h, c, i, j, d);
         double v = (tw + h.te[c] + ts + h.tn[c]) * h.p[c];
         if (i > 0) v -= h.te[c - 1] * h.p[c - 1];
         if (i < n - 1) v -= h.te[c] * h.p[c + 1];
@@ -425,9 +458,16 @@ static __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, double pW,
     block_sum2(a, b, red, rr, bb);
 }
 
-// Q = sum_j te(n-1, j) (p(n-1, j) - pE); warp 0 reduces, valid in thread 0.
+// The QoI of Table 1 (valid in thread 0).  Case II: Q = sum_j te(n-1, j)
+// (p(n-1, j) - pE), warp 0 reduces.  Case I (d.ns): u(0.5, 0.5), the mean of
+// the four centre cells.
 template <typename P, typename Q>
-static __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, double pE) {
+static __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int n, const Ghost<double>& d) {
+    const double pE = d.e;
+    if (d.ns) {
+        const int c = (n / 2 - 1) * n + n / 2 - 1;
+        return 0.25 * (((double)p[c] + (double)p[c + 1]) + ((double)p[c + n] + (double)p[c + n + 1]));
+    }
     double acc = 0.0;
     if (rank() < 32) {
         for (int j = rank(); j < n; j += 32) {
@@ -442,8 +482,9 @@ static __device__ __forceinline__ double outflux_of(const P* te, const Q* p, int
 
 // Outflux broadcast to every thread of the CTA.
 template <typename P, typename Q>
-static __device__ __forceinline__ double stage_outflux(const P* te, const Q* p, int n, double pE, double* red) {
-    const double q = outflux_of(te, p, n, pE);
+static __device__ __forceinline__ double stage_outflux(const P* te, const Q* p, int n, const Ghost<double>& d,
+                                                       double* red) {
+    const double q = outflux_of(te, p, n, d);
     if (WARP) return __shfl_sync(0xffffffffu, q, 0);
     if (rank() == 0) red[70] = q;
     sync();
@@ -458,7 +499,7 @@ struct ResidentArgs {
     int n_fine, n0;
     size_t S;
     const double* K;
-    double pW, pE;
+    Ghost<double> bd;   // boundary data (Table 1)
     int nu0, nu1, nu2;
     int converged, max_cycles;
     double tol, qtol;
@@ -511,14 +552,17 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
     if (R::rank() == 0) *slot = resident_layout<T>(data, a.n_fine, a.n0, MIXED);
     R::sync();
     const RLayout<T>& L = *slot;
-    const T tpW = (T)a.pW, tpE = (T)a.pE;
+    // the boundary data in the V-cycle arithmetic, and zero data on the same
+    // edges for the mixed form's correction equation
+    const Ghost<T> td{(T)a.bd.w, (T)a.bd.e, (T)a.bd.s, (T)a.bd.n, a.bd.ns};
+    const Ghost<T> t0{T(0), T(0), T(0), T(0), a.bd.ns};
     const int m = L.m;
     const size_t stride = (size_t)gridDim.x * groups;
     for (size_t s = (size_t)blockIdx.x * groups + grp; s < a.S; s += stride) {
         const double* Kf = a.K + s * (size_t)a.n_fine * a.n_fine;
         for (int k = 0; k <= m; ++k) {
             const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
-            R::resident_setup_grid(L.g[k], h, Kf, a.n_fine);
+            R::resident_setup_grid(L.g[k], h, Kf, a.n_fine, a.bd.ns);
         }
         R::sync();
         R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
@@ -536,19 +580,19 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             if (k > 0) {
                 if (MIXED && refined && k == m && m >= 1) {
                     // FP64 interpolation of the refined stage m-1 solution
-                    R::resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.pW, a.pE, false);
+                    R::resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.bd, false);
                 } else {
-                    R::resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, tpW, tpE, false);
+                    R::resident_prolong(L.g[k - 1].p, L.g[k - 1].n, g.p, td, false);
                 }
                 // grid k-1 now only carries corrections of the V-cycles on grid k
-                R::resident_setup_correction(L.g[k - 1], Kf, a.n_fine);
+                R::resident_setup_correction(L.g[k - 1], Kf, a.n_fine, a.bd.ns);
                 if (k == 1) R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
             }
-            if (g.b) R::resident_stage_rhs(g, tpW, tpE);
-            if (k == 0) R::resident_coarse_solve(g, L.ainv, tpW, tpE);
+            if (g.b) R::resident_stage_rhs(g, td);
+            if (k == 0) R::resident_coarse_solve(g, L.ainv, td);
             if (!refined) {
                 if (k > 0) {
-                    for (int it = 0; it < a.nu0; ++it) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    for (int it = 0; it < a.nu0; ++it) R::resident_vcycle(L, k, a.nu1, a.nu2, td);
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
                     model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                 }
@@ -558,10 +602,10 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
-                    R::stage_norms(g, tpW, tpE, L.red, rr, bb);
+                    R::stage_norms(g, td, L.red, rr, bb);
                     work += 14.0 * g.n * g.n;
                     model += 20.0 * g.n * g.n;
-                    const double q = R::stage_outflux(g.te, g.p, g.n, a.pE, L.red);
+                    const double q = R::stage_outflux(g.te, g.p, g.n, a.bd, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
                     q_prev = q;
@@ -569,7 +613,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, tpW, tpE);
+                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, td);
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
                     model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                 }
@@ -583,11 +627,11 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 double q_prev = NAN;
                 for (int it = 0;; ++it) {
                     double rr, bb;
-                    R::ir_residual(h, g, a.pW, a.pE, L.red, rr, bb);
+                    R::ir_residual(h, g, a.bd, L.red, rr, bb);
                     work += 14.0 * h.n * h.n;
                     work64 += 14.0 * h.n * h.n;
                     model += 20.0 * h.n * h.n;
-                    const double q = R::stage_outflux(h.te, h.p, h.n, a.pE, L.red);
+                    const double q = R::stage_outflux(h.te, h.p, h.n, a.bd, L.red);
                     if (rr <= a.tol * a.tol * bb) break;
                     if (a.qtol > 0 && fabs(q - q_prev) <= a.qtol * fabs(q)) break;
                     q_prev = q;
@@ -596,7 +640,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                         break;
                     }
                     // nu0 FP32 V-cycles on the correction equation per FP64 residual
-                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, T(0), T(0));
+                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, t0);
                     work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2) + (double)h.n * h.n;
                     work64 += (double)h.n * h.n;
                     model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
@@ -609,9 +653,9 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 double q;
                 if (MIXED && refined) {
                     const HGrid& h = L.h[k - (m - 1)];
-                    q = R::outflux_of(h.te, h.p, h.n, a.pE);
+                    q = R::outflux_of(h.te, h.p, h.n, a.bd);
                 } else {
-                    q = R::outflux_of(g.te, g.p, g.n, a.pE);
+                    q = R::outflux_of(g.te, g.p, g.n, a.bd);
                 }
                 if (k == m) q_fine = q;
                 else q_coarse = q;
@@ -693,8 +737,8 @@ bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double
     a.n0 = n0;
     a.S = S;
     a.K = d_K;
-    a.pW = prm.pW;
-    a.pE = prm.pE;
+    const Bnd bd = bnd_of(prm);
+    a.bd = Ghost<double>{bd.g[0], bd.g[1], bd.g[2], bd.g[3], bd.ns};
     a.nu0 = prm.nu0;
     a.nu1 = prm.nu1;
     a.nu2 = prm.nu2;

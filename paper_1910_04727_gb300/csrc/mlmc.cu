@@ -97,7 +97,7 @@ fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const doub
     return FM_OK;
 }
 
-static fm_solve_params solve_params(const fm_ctx* ctx) {
+fm_solve_params solve_params(const fm_ctx* ctx) {
     fm_solve_params p{};
     p.pW = ctx->cfg.pW;
     p.pE = ctx->cfg.pE;
@@ -111,6 +111,9 @@ static fm_solve_params solve_params(const fm_ctx* ctx) {
     p.tol = ctx->cfg.tol;
     p.qtol = ctx->cfg.qtol;
     p.max_cycles = ctx->cfg.max_cycles;
+    p.bc_case = ctx->cfg.bc_case;
+    p.pS = ctx->cfg.pS;
+    p.pN = ctx->cfg.pN;
     return p;
 }
 

@@ -780,11 +780,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     {
         const uint32_t chunk = 65536;
         if (cudaMalloc((void**)&K, (size_t)chunk * N0 * N0 * 8) != cudaSuccess) stt = FM_ENOMEM;
-        fm_solve_params prm{};
-        prm.pW = ctx->cfg.pW; prm.pE = ctx->cfg.pE; prm.n_coarsest = ctx->cfg.n_coarsest;
-        prm.nu0 = ctx->cfg.nu0; prm.nu1 = ctx->cfg.nu1; prm.nu2 = ctx->cfg.nu2;
-        prm.precision = ctx->cfg.precision; prm.converged = ctx->cfg.converged; prm.tol = ctx->cfg.tol;
-        prm.qtol = ctx->cfg.qtol; prm.max_cycles = ctx->cfg.max_cycles;
+        const fm_solve_params prm = solve_params(ctx);
         for (uint32_t o = 0; stt == FM_OK && o < (uint32_t)n; o += chunk) {
             const uint32_t c = std::min<uint32_t>(chunk, n - o);
             stt = mc_points(ctx, kSurrogateTrainStream, o, c, M, xi + (size_t)o * M, nullptr);

@@ -1,0 +1,140 @@
+"""Table 1 Case I on the GPU: Dirichlet data on all four edges (west 100,
+east 0, south 10, north 50) and the point QoI u(0.5, 0.5), against the
+oracle's Case I.  Same bars as Case II: FP64 per-sample QoI within 1e-10
+relative, the mixed form within 1e-8 of the converged oracle, and every
+smoother launch shape bit-identical to every other."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import kl as okl
+from oracle import lib as OL
+
+pytestmark = pytest.mark.gpu
+
+LEVELWISE, RESIDENT = 1, 2
+CASE1 = dict(bc_case=1, pW=100.0, pE=0.0, pS=10.0, pN=50.0)
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+def _ctx(**kw):
+    import paper_1910_04727_gb300 as fm
+    return fm.Context(2, 16, 16, **dict(CASE1, **kw))
+
+
+@pytest.mark.parametrize("n,S,kernel", [(4, 3, LEVELWISE), (8, 9, LEVELWISE), (16, 33, LEVELWISE),
+                                        (32, 17, LEVELWISE), (64, 5, LEVELWISE), (128, 3, LEVELWISE),
+                                        (256, 2, LEVELWISE), (8, 9, RESIDENT), (16, 300, RESIDENT),
+                                        (32, 17, RESIDENT), (64, 5, RESIDENT)])
+def test_fixed_schedule_matches_the_oracle(n, S, kernel):
+    ctx = _ctx()
+    K = W.smooth_lognormal_field(n, S=S, tag=3000 + n)
+    qf, qc, p = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), want_p=True, kernel=kernel)
+    rf, rc, rp, _ = OL.fmg_solve_batch(K, OL.case1_params(), want_p=True)
+    assert _rel(qf.cpu().numpy(), rf) < 1e-10
+    if n > 4:
+        assert _rel(qc.cpu().numpy(), rc) < 1e-10
+    np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=1e-9)
+    ctx.close()
+
+
+@pytest.mark.parametrize("kernel", [LEVELWISE, RESIDENT])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_converged_forms_match_the_converged_oracle(kernel, precision):
+    ctx = _ctx(precision=precision, converged=True, tol=1e-12, qtol=1e-10, max_cycles=200)
+    for n, S in [(16, 64), (64, 9)] + ([(256, 3)] if kernel == LEVELWISE else []):
+        K = W.smooth_lognormal_field(n, S=S, sigma=1.2, tag=3100 + n)
+        qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), kernel=kernel)
+        rf, rc, _, _ = OL.fmg_solve_batch(K, OL.case1_params(converged=True, tol=1e-13, max_cycles=300))
+        bar = 1e-10 if precision == 0 else 1e-8
+        assert _rel(qf.cpu().numpy(), rf) < bar, (n, precision)
+        assert _rel(qc.cpu().numpy(), rc) < bar, (n, precision)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,converged", [(0, 0), (1, 1)])
+def test_every_shape_gives_the_same_solve(precision, converged):
+    ctx = _ctx(precision=precision, converged=converged, tol=1e-12, max_cycles=200)
+    shapes = [(0, 0), (-1, 0), (32, 256), (16, 0), (32, 0)]
+    for n, S in [(16, 5), (64, 7), (256, 3)]:
+        K = torch.tensor(W.smooth_lognormal_field(n, S=S, tag=3200 + n), device="cuda")
+        ref = None
+        for tile, threads in shapes:
+            for m in [4 << k for k in range(8) if (4 << k) <= n]:
+                ctx.set_smoother_shape(m, tile, threads)
+            out = ctx.fmg_solve_batch(K, want_p=True, kernel=LEVELWISE)
+            got = [x.cpu().numpy() for x in out]
+            if ref is None:
+                ref = got
+                continue
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b, equal_nan=True), (n, tile, threads)
+    ctx.close()
+
+
+def test_energy_step_matches_the_stepped_oracle():
+    ctx = _ctx(converged=True, tol=1e-12, max_cycles=200)
+    K = W.smooth_lognormal_field(64, S=4, sigma=1.5, tag=3300)
+    qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), kernel=LEVELWISE, energy_step=1)
+    rf, rc, _, _ = OL.fmg_solve_batch(K, OL.case1_params(converged=True, tol=1e-13, max_cycles=300,
+                                                         energy_step=True))
+    assert _rel(qf.cpu().numpy(), rf) < 1e-10
+    assert _rel(qc.cpu().numpy(), rc) < 1e-10
+    ctx.close()
+
+
+def test_symmetric_field_gives_the_mean_of_the_edge_values():
+    """A field invariant under the square's symmetries: u(0.5, 0.5) is the
+    mean of the four edge values, 40, on every schedule and precision."""
+    n = 64
+    d = np.minimum(np.arange(n), n - 1 - np.arange(n))
+    DX, DY = np.meshgrid(d, d, indexing="xy")
+    K = np.exp(0.8 * np.cos(0.7 * np.minimum(DX, DY)) + 0.5 * np.sin(0.3 * np.maximum(DX, DY)))[None]
+    Kt = torch.tensor(np.repeat(K, 3, axis=0), device="cuda")
+    for precision in (0, 1):
+        ctx = _ctx(precision=precision, converged=True, tol=1e-12, max_cycles=200)
+        for kernel in (LEVELWISE, RESIDENT):
+            qf, _, _ = ctx.fmg_solve_batch(Kt, kernel=kernel)
+            assert np.max(np.abs(qf.cpu().numpy() - 40.0)) < 1e-8 * 40, (precision, kernel)
+        ctx.close()
+
+
+def test_kl_levels_coarse_qoi_is_the_previous_fine_qoi():
+    """Q^c_l(omega) = Q^f_(l-1)(omega) with nested field points, Case I."""
+    import paper_1910_04727_gb300 as fm
+    basis = okl.KLBasis(64, 24, 1.0, 0.3, q=24)
+    ctx = fm.Context(3, 16, 24, seed=17, **CASE1)
+    ctx.kl_basis_set(basis.B_ref)
+    for l in (1, 2):
+        _, qc = ctx.mlmc_sample_level(l, 0, 200, want_q=True)
+        qf, _ = ctx.mlmc_sample_level(l - 1, 0, 200, want_q=True)
+        assert _rel(qc.cpu().numpy(), qf.cpu().numpy()) < 1e-12
+    # and the per-sample QoI of level 1 against the oracle sampler
+    from oracle import mlmc as omlmc
+    qf, qc = ctx.mlmc_sample_level(1, 0, 64, want_q=True)
+    y, rf, rc = omlmc.FMGSampler([16, 32, 64], basis, seed=17, prm=OL.case1_params())(1, 0, 64)
+    assert _rel(qf.cpu().numpy(), rf) < 1e-10
+    assert _rel(qc.cpu().numpy(), rc) < 1e-10
+    ctx.close()
+
+
+def test_uneven_batch_equals_per_group_solves():
+    ctx = _ctx(precision=1, converged=True, tol=1e-12, qtol=1e-10, max_cycles=200)
+    Ks = [torch.tensor(W.smooth_lognormal_field(n, S=S, tag=3400 + n), device="cuda")
+          for n, S in [(16, 40), (64, 9), (128, 3)]]
+    outs = ctx.solve_uneven(Ks)
+    for K, (qf, qc, _) in zip(Ks, outs):
+        a, b, _ = ctx.fmg_solve_batch(K)
+        assert torch.equal(a, qf) and torch.equal(b, qc)
+    ctx.close()
+
+
+def test_case_is_checked():
+    import paper_1910_04727_gb300 as fm
+    with pytest.raises(fm.FmError, match="bc_case"):
+        fm.Context(2, 16, 16, bc_case=3)
