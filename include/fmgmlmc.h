@@ -96,6 +96,8 @@ typedef struct {
     int64_t max_batch;    /* most samples per device batch (0: library's choice) */
     int32_t bc_case;      /* Table 1: FM_CASE_II (0 is read as Case II) or FM_CASE_I */
     double pS, pN;        /* Case I: Dirichlet data on the south / north edges */
+    double nu;            /* Matern smoothness of the field (Sec. 3.1, Table 2): 0.5 (exponential;
+                             0 is read as 0.5), 1, 1.5 or 2.5 */
 } fm_config;
 
 /* Boundary conditions and QoI (Table 1).
@@ -195,14 +197,23 @@ fm_status sobol_direction_numbers(const fm_ctx* ctx, uint32_t* V);
  * level l-1 coincide.  basis_ref is device memory if on_device, else host. */
 fm_status kl_basis_set(fm_ctx* ctx, const double* basis_ref, int32_t on_device);
 
-/* Build the KL basis of the exponential covariance sigma2 exp(-|x-y|/lambda)
- * on the GPU by the Nystrom method: midpoint quadrature on a q x q grid
+/* Build the KL basis of the Matern covariance of Sec. 3.1 (smoothness cfg.nu,
+ * see fm_matern_covariance) on the GPU by the Nystrom method: midpoint quadrature on a q x q grid
  * (q = 0: smallest q >= 32 with q^2 >= 8 M), a dense symmetric eigensolve
  * (cuSOLVER) of the weighted covariance matrix, and Nystrom interpolation
  * of the top M eigenfunctions to the field points.  theta_out (nullable,
  * host) receives the M eigenvalues, captured_out (nullable, host)
  * sum_{k<=M} theta_k / (sigma2 meas(Omega)).  Synchronous. */
 fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, double* captured_out);
+
+/* The Matern covariance of Sec. 3.1 at n distances (host memory, no CUDA
+ * call): C(d) = sigma2 2^(1-nu) / Gamma(nu) (sqrt(2 nu) d / lambda)^nu
+ * K_nu(sqrt(2 nu) d / lambda), C(0) = sigma2, for nu = 0.5 (sigma2
+ * exp(-d/lambda)), 1 (sigma2 x K_1(x), x = sqrt 2 d / lambda, K_1 by its
+ * ascending series for x <= 2 and the trapezoidal rule on its integral
+ * representation above), 1.5 and 2.5 (closed forms).  FM_EINVAL for another
+ * nu, non-positive sigma2 or lambda, or a negative distance. */
+fm_status fm_matern_covariance(double nu, double sigma2, double lambda, const double* d, int64_t n, double* c);
 
 /* Copy the installed basis of the finest grid (the layout kl_basis_set takes)
  * to basis_ref_out: device memory if on_device, else host.  Synchronous. */

@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see the oracle package docstring).
 
-The Gaussian field g has the Matern covariance of Sec. 3.1; for nu = 1/2 it
-is the exponential C(d) = sigma^2 exp(-d / lambda), d the Euclidean distance.
+The Gaussian field g has the Matern covariance of Sec. 3.1,
+C(d) = sigma^2 2^(1-nu) / Gamma(nu) (sqrt(2 nu) d / lambda)^nu K_nu(sqrt(2 nu) d / lambda),
+C(0) = sigma^2, d the Euclidean distance (Table 2 uses nu = 1/2, the
+exponential sigma^2 exp(-d / lambda), and nu = 1).
 Its KL expansion g(x) = sum_k sqrt(theta_k) phi_k(x) xi_k, truncated to M
 terms, is computed by the Nystrom method (the paper cites Ernst et al. for
 the eigenproblem and states no method of its own):
@@ -28,6 +30,7 @@ in law.
 import numpy as np
 import scipy.linalg
 import scipy.optimize
+import scipy.special
 
 
 def quadrature_points(q, dim=2):
@@ -39,9 +42,20 @@ def quadrature_points(q, dim=2):
     return np.stack([X.ravel(), Y.ravel()], axis=1)
 
 
-def covariance(X, Y, sigma2, lam, metric="l2"):
-    """Exponential (Matern nu = 1/2) covariance between point sets X [a][d], Y [b][d].
-    metric 'l1' (separable) exists only to pin the 2-D code against 1-D results."""
+def matern(d, sigma2, lam, nu=0.5):
+    """The Matern covariance of Sec. 3.1 at distances d, written as the paper
+    states it (scipy's modified Bessel function K_nu); C(0) = sigma^2."""
+    d = np.asarray(d, dtype=np.float64)
+    x = np.sqrt(2.0 * nu) * d / lam
+    with np.errstate(invalid="ignore", divide="ignore"):
+        c = sigma2 * 2.0 ** (1.0 - nu) / scipy.special.gamma(nu) * x ** nu * scipy.special.kv(nu, x)
+    return np.where(x == 0.0, sigma2, c)
+
+
+def covariance(X, Y, sigma2, lam, metric="l2", nu=0.5):
+    """Matern covariance (smoothness nu) between point sets X [a][d], Y [b][d].
+    metric 'l1' (separable, nu = 1/2) exists only to pin the 2-D code against
+    1-D results."""
     diff = X[:, None, :] - Y[None, :, :]
     if metric == "l2":
         d = np.sqrt(np.sum(diff * diff, axis=-1))
@@ -49,16 +63,18 @@ def covariance(X, Y, sigma2, lam, metric="l2"):
         d = np.sum(np.abs(diff), axis=-1)
     else:
         raise ValueError(metric)
-    return sigma2 * np.exp(-d / lam)
+    if nu == 0.5:
+        return sigma2 * np.exp(-d / lam)
+    return matern(d, sigma2, lam, nu)
 
 
-def nystrom_eigs(q, M, sigma2, lam, dim=2, metric="l2", all_modes=False):
+def nystrom_eigs(q, M, sigma2, lam, dim=2, metric="l2", all_modes=False, nu=0.5):
     """Top-M eigenpairs of the Nystrom matrix, eigenvalues descending.
     Returns (theta [M], V [q^dim][M] orthonormal columns, points, w, trace)."""
     pts = quadrature_points(q, dim)
     n = pts.shape[0]
     w = 1.0 / n
-    A = w * covariance(pts, pts, sigma2, lam, metric)
+    A = w * covariance(pts, pts, sigma2, lam, metric, nu)
     if all_modes or M >= n:
         theta, V = scipy.linalg.eigh(A)
     else:
@@ -71,12 +87,12 @@ def nystrom_eigs(q, M, sigma2, lam, dim=2, metric="l2", all_modes=False):
     return theta, V, pts, w, float(np.trace(A))
 
 
-def nystrom_basis(points, theta, V, qpts, w, sigma2, lam, metric="l2", chunk=4096):
+def nystrom_basis(points, theta, V, qpts, w, sigma2, lam, metric="l2", chunk=4096, nu=0.5):
     """B[x][k] = sqrt(theta_k) phi_k(x) = (1/sqrt(theta_k)) sum_j sqrt(w) C(x,x_j) v_jk."""
     B = np.empty((points.shape[0], theta.shape[0]))
     scale = np.sqrt(w) / np.sqrt(theta)
     for a in range(0, points.shape[0], chunk):
-        Cx = covariance(points[a:a + chunk], qpts, sigma2, lam, metric)
+        Cx = covariance(points[a:a + chunk], qpts, sigma2, lam, metric, nu)
         B[a:a + chunk] = (Cx @ V) * scale
     return B
 
@@ -100,16 +116,16 @@ def level_rows(n, n_ref):
 class KLBasis:
     """Truncated KL basis on the finest grid's points; coarser grids take rows."""
 
-    def __init__(self, n_ref, M, sigma2, lam, q=None, metric="l2"):
+    def __init__(self, n_ref, M, sigma2, lam, q=None, metric="l2", nu=0.5):
         if q is None:
             q = max(32, int(np.ceil(np.sqrt(8 * M))))
-        self.n_ref, self.M, self.sigma2, self.lam, self.q = n_ref, M, sigma2, lam, q
-        theta, V, qpts, w, trace = nystrom_eigs(q, M, sigma2, lam, 2, metric)
+        self.n_ref, self.M, self.sigma2, self.lam, self.q, self.nu = n_ref, M, sigma2, lam, q, nu
+        theta, V, qpts, w, trace = nystrom_eigs(q, M, sigma2, lam, 2, metric, nu=nu)
         self.theta = theta
         self.trace = trace                           # = sigma^2 meas(Omega)
         self.captured = float(theta.sum() / trace)   # fraction of variability kept
         self.B_ref = nystrom_basis(field_points(n_ref, n_ref), theta, V, qpts, w,
-                                   sigma2, lam, metric)
+                                   sigma2, lam, metric, nu=nu)
 
     def level_basis(self, n):
         """[n*n][M] rows of the basis for the n x n grid."""

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import FM_PREC_FP64, FM_PREC_MIXED, STATUS_NAMES
 
 __all__ = ["Context", "FmError", "FM_PREC_FP64", "FM_PREC_MIXED", "load_library", "shard_range",
-           "estimate_core", "allgather_over"]
+           "estimate_core", "allgather_over", "matern_covariance"]
 
 
 class FmError(RuntimeError):
@@ -38,6 +38,18 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def matern_covariance(d, nu, sigma2=1.0, lam=1.0):
+    """The library's Matern covariance (fm_matern_covariance) at distances d (host)."""
+    L = _lib.load()
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    c = np.empty_like(d)
+    st = L.fm_matern_covariance(nu, sigma2, lam, d.ctypes.data_as(C.c_void_p), d.size,
+                                c.ctypes.data_as(C.c_void_p))
+    if st != 0:
+        raise FmError(st, "fm_matern_covariance")
+    return c
 
 
 def shard_range(first, n, rank, world):
@@ -123,13 +135,14 @@ class Context:
     def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
                  nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
                  precision=FM_PREC_FP64, converged=False, tol=1e-10, qtol=0.0, max_cycles=100,
-                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0):
+                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0, nu=0.5):
         """bc_case: Table 1's FM_CASE_II (no flow north / south, east outflux) or
-        FM_CASE_I (Dirichlet pW, pE, pS, pN on all four edges, QoI u(0.5, 0.5))."""
+        FM_CASE_I (Dirichlet pW, pE, pS, pN on all four edges, QoI u(0.5, 0.5)).
+        nu: Matern smoothness of the field (0.5, 1, 1.5 or 2.5)."""
         self._L = _lib.load()
         cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
                             precision, int(bool(converged)), tol, qtol, max_cycles, kl_mode, n_shifts,
-                            seed, max_batch, bc_case, pS, pN)
+                            seed, max_batch, bc_case, pS, pN, nu)
         h = C.c_void_p()
         st = self._L.fm_create(C.byref(cfg), C.byref(h))
         if st != 0:

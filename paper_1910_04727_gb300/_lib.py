@@ -27,7 +27,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
-           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check"]
+           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance"]
 
 
 class FmConfig(C.Structure):
@@ -38,7 +38,7 @@ class FmConfig(C.Structure):
                 ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
                 ("kl_mode", C.c_int32),
                 ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64),
-                ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double)]
+                ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double), ("nu", C.c_double)]
 
 
 class FmSolveParams(C.Structure):
@@ -154,6 +154,7 @@ def load(path=None):
         "fm_kernel_family_name": (C.c_char_p, [I32]),
         "fm_sync": (I32, [P]),
         "fm_wait_check": (I32, [P, I64, P]),
+        "fm_matern_covariance": (I32, [D, D, D, P, I64, P]),
         "fmg_solve_batch_static": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P]),
         "surrogate_param_count": (I64, [P]),
         "surrogate_params": (I32, [P, P, I32]),

@@ -39,6 +39,8 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
     FM_CHECK_ARG(nullptr, cfg->kl_mode >= FM_KL_AUTO && cfg->kl_mode <= FM_KL_BF16X3, "fm_create: unknown kl_mode");
     FM_CHECK_ARG(nullptr, cfg->bc_case == 0 || cfg->bc_case == FM_CASE_I || cfg->bc_case == FM_CASE_II,
                  "fm_create: bc_case must be FM_CASE_I or FM_CASE_II");
+    FM_CHECK_ARG(nullptr, cfg->nu == 0.0 || cfg->nu == 0.5 || cfg->nu == 1.0 || cfg->nu == 1.5 || cfg->nu == 2.5,
+                 "fm_create: nu must be 0.5, 1, 1.5 or 2.5");
     fm_ctx* ctx = new (std::nothrow) fm_ctx();
     if (!ctx) {
         set_error(nullptr, "fm_create: host allocation failed");

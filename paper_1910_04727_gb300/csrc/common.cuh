@@ -226,6 +226,8 @@ fm_status ensure(fm_ctx* ctx, T** buf, size_t* capacity, size_t count) {
 }
 
 inline int grid_of_level(const fm_ctx* ctx, int level) { return ctx->cfg.n_level0 << level; }
+// Matern smoothness of the configured field (0 is read as 1/2, the exponential covariance).
+inline double matern_nu(const fm_config& cfg) { return cfg.nu > 0.0 ? cfg.nu : 0.5; }
 inline int finest_grid(const fm_ctx* ctx) { return grid_of_level(ctx, ctx->cfg.n_levels - 1); }
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }

@@ -278,6 +278,41 @@ def test_kl_basis_build_matches_oracle_spectrum(fm):
     np.testing.assert_allclose(Bg @ Bg.T, B_or @ B_or.T, atol=1e-10)
 
 
+@pytest.mark.parametrize("nu,lam", [(1.0, 0.5), (1.0, 1.0), (1.5, 0.3), (2.5, 0.3)])
+def test_kl_basis_build_of_smoother_matern_fields_matches_oracle(fm, nu, lam):
+    """Table 2's nu = 1 fields (lambda = 0.5 and 1) and the closed-form
+    smoothness values: spectrum and field covariance of the GPU-built basis
+    against the oracle's (the covariance through scipy's K_nu)."""
+    ctx = fm.Context(2, 16, 32, sigma2=1.0, lam=lam, nu=nu)
+    theta, captured = ctx.kl_basis_build(q=24)
+    th, V, qpts, w, trace = okl.nystrom_eigs(24, 32, 1.0, lam, nu=nu)
+    np.testing.assert_allclose(theta, th, rtol=1e-10)
+    assert abs(captured - th.sum() / trace) < 1e-12
+    B_or = okl.nystrom_basis(okl.field_points(32, 32), th, V, qpts, w, 1.0, lam, nu=nu)
+    xi = torch.eye(32, dtype=torch.float64, device="cuda")
+    Bg = torch.log(ctx.kl_field_batch(1, xi)).reshape(32, -1).T.cpu().numpy()
+    np.testing.assert_allclose(Bg @ Bg.T, B_or @ B_or.T, atol=1e-10)
+    ctx.close()
+
+
+def test_matern_nu1_level_samples_match_oracle(fm):
+    """A two-level run on the nu = 1, lambda = 0.5 field of Table 2 (the
+    oracle's basis installed): per-sample Q^f, Q^c within 1e-10."""
+    basis = okl.KLBasis(32, 24, 1.0, 0.5, q=24, nu=1.0)
+    ctx = fm.Context(2, 16, 24, sigma2=1.0, lam=0.5, nu=1.0, seed=31)
+    ctx.kl_basis_set(basis.B_ref)
+    qf, qc = ctx.mlmc_sample_level(1, 0, 200, want_q=True)
+    y, rf, rc = omlmc.FMGSampler([16, 32], basis, seed=31)(1, 0, 200)
+    assert _rel(qf.cpu().numpy(), rf) < RTOL_Q
+    assert _rel(qc.cpu().numpy(), rc) < RTOL_Q
+    ctx.close()
+
+
+def test_unsupported_smoothness_is_refused(fm):
+    with pytest.raises(fm.FmError, match="nu"):
+        fm.Context(2, 16, 8, nu=0.75)
+
+
 # ------------------------------------------------------------------ full size
 def test_full_size_level_sampled_against_oracle(fm):
     """The 256 x 256 level of the five-level workload (128 modes) in the batch

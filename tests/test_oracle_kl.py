@@ -78,3 +78,61 @@ def test_captured_fraction_of_the_workload_field():
     assert abs(b.trace - 1.0) < 1e-12
     assert 0.8 < b.captured < 1.0
     assert b.B_ref.shape == (32 * 32, 64)
+
+
+# ---------------------------------------------------------------- Matern smoothness (Table 2)
+@pytest.mark.parametrize("lam", [0.1, 0.5, 1.0])
+def test_matern_general_formula_reduces_to_the_closed_forms(lam):
+    """The paper's formula with K_nu: nu = 1/2 is sigma^2 exp(-d/lambda);
+    nu = 3/2 is (1 + x) e^-x with x = sqrt(3) d / lambda; nu = 5/2 is
+    (1 + x + x^2/3) e^-x with x = sqrt(5) d / lambda."""
+    d = np.linspace(0.0, 2.0, 401)
+    np.testing.assert_allclose(kl.matern(d, 1.3, lam, 0.5), 1.3 * np.exp(-d / lam), rtol=1e-13)
+    x = np.sqrt(3.0) * d / lam
+    np.testing.assert_allclose(kl.matern(d, 1.3, lam, 1.5), 1.3 * (1 + x) * np.exp(-x), rtol=1e-12)
+    x = np.sqrt(5.0) * d / lam
+    np.testing.assert_allclose(kl.matern(d, 1.3, lam, 2.5), 1.3 * (1 + x + x * x / 3) * np.exp(-x), rtol=1e-12)
+
+
+@pytest.mark.parametrize("r", [0.03, 0.2, 0.7, 1.4])
+def test_matern_nu1_is_the_hankel_transform_of_its_spectral_density(r):
+    """In two dimensions the Matern covariance with nu = 1 has spectral
+    density proportional to (a^2 + w^2)^-2, a = sqrt(2)/lambda, so
+    C(r) / sigma^2 = 2 a^2 int_0^inf J_0(w r) w / (a^2 + w^2)^2 dw."""
+    import scipy.integrate
+    import scipy.special
+    lam = 0.5
+    a = np.sqrt(2.0) / lam
+    f = lambda w: scipy.special.j0(w * r) * w / (a * a + w * w) ** 2
+    total, cut = 0.0, 0.0
+    step = 2 * np.pi / r
+    while cut < 4000.0:
+        total += scipy.integrate.quad(f, cut, cut + step, limit=200, epsabs=1e-16, epsrel=1e-13)[0]
+        cut += step
+    want = 2 * a * a * total
+    assert abs(kl.matern(r, 1.0, lam, 1.0) - want) < 1e-8
+
+
+def test_matern_nu1_spectrum_satisfies_the_trace_identity():
+    theta, V, pts, w, trace = kl.nystrom_eigs(16, 256, 0.9, 0.5, all_modes=True, nu=1.0)
+    assert abs(theta.sum() - 0.9) < 1e-12 and abs(trace - 0.9) < 1e-12
+    assert np.all(theta > -1e-14)
+    # a smoother field puts more variance in its first modes than nu = 1/2
+    t05, *_ = kl.nystrom_eigs(16, 8, 0.9, 0.5, nu=0.5)
+    assert theta[:8].sum() > t05.sum()
+
+
+def test_library_covariance_matches_the_oracle():
+    """fm_matern_covariance (the library's own x K_1(x): ascending series
+    below 2, trapezoidal rule on its integral above) against the oracle's
+    formula through scipy, for every smoothness the library builds."""
+    import paper_1910_04727_gb300 as fm
+    d = np.concatenate([[0.0, 1e-12, 1e-6], np.linspace(1e-4, 3.0, 3001)])
+    for nu in (0.5, 1.0, 1.5, 2.5):
+        for lam in (0.1, 0.5, 1.0):
+            got = fm.matern_covariance(d, nu, 1.7, lam)
+            want = kl.matern(d, 1.7, lam, nu)
+            big = want > 1e-200
+            np.testing.assert_allclose(got[big], want[big], rtol=5e-14, atol=0)
+    with pytest.raises(fm.FmError):
+        fm.matern_covariance(d, 0.75, 1.0, 1.0)
