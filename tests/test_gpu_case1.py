@@ -46,7 +46,10 @@ def test_fixed_schedule_matches_the_oracle(n, S, kernel):
 @pytest.mark.parametrize("kernel", [LEVELWISE, RESIDENT])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_converged_forms_match_the_converged_oracle(kernel, precision):
-    ctx = _ctx(precision=precision, converged=True, tol=1e-12, qtol=1e-10, max_cycles=200)
+    # FP64: the residual test alone (the outflux-change test stops about n tol
+    # short of the converged value); mixed: the benchmark's stopping rule
+    rule = dict(tol=1e-13, qtol=0.0) if precision == 0 else dict(tol=1e-12, qtol=1e-10)
+    ctx = _ctx(precision=precision, converged=True, max_cycles=300, **rule)
     for n, S in [(16, 64), (64, 9)] + ([(256, 3)] if kernel == LEVELWISE else []):
         K = W.smooth_lognormal_field(n, S=S, sigma=1.2, tag=3100 + n)
         qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), kernel=kernel)
@@ -111,8 +114,10 @@ def test_kl_levels_coarse_qoi_is_the_previous_fine_qoi():
     ctx = fm.Context(3, 16, 24, seed=17, **CASE1)
     ctx.kl_basis_set(basis.B_ref)
     for l in (1, 2):
-        _, qc = ctx.mlmc_sample_level(l, 0, 200, want_q=True)
-        qf, _ = ctx.mlmc_sample_level(l - 1, 0, 200, want_q=True)
+        # the same coefficients xi on level l and on level l - 1
+        xi = ctx.mc_points(l, 0, 200)
+        _, qc, _ = ctx.fmg_solve_batch(ctx.kl_field_batch(l, xi))
+        qf, _, _ = ctx.fmg_solve_batch(ctx.kl_field_batch(l - 1, xi))
         assert _rel(qc.cpu().numpy(), qf.cpu().numpy()) < 1e-12
     # and the per-sample QoI of level 1 against the oracle sampler
     from oracle import mlmc as omlmc
