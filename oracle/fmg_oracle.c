@@ -288,6 +288,161 @@ void or_sobol_points(const uint32_t* V, uint32_t dim, uint64_t first, uint32_t n
 }
 
 /* ------------------------------------------------------------------------ */
+/* Randomized QMC rules (Sec. 2.4: random shift of a lattice rule, scramble   */
+/* of the Sobol' sequence).                                                  */
+/* ------------------------------------------------------------------------ */
+#define OR_PURPOSE_LATTICE_SHIFT 4u
+#define OR_PURPOSE_OWEN 5u
+
+/* omega(x) = B_2(x) = x^2 - x + 1/6, the shift-invariant kernel of the
+ * unanchored Sobolev space of first-order mixed smoothness. */
+static double bernoulli2(double x) { return x * x - x + 1.0 / 6.0; }
+
+/* Rank-1 lattice generating vector for the embedded point sets of 2^m
+ * points, m = m_min .. m_max, component by component: z_1 = 1; component s
+ * is the odd z < 2^(m_max - 1) minimising
+ *   C(z) = sum_m e^2_m(z_1..z_(s-1), z) / e^2_m(z_1..z_(s-1)),
+ * with the shift-averaged squared worst-case error of the 2^m-point lattice
+ * e^2_m = -1 + 2^-m sum_k prod_j (1 + gamma_j omega({k z_j / 2^m})) and
+ * product weights gamma_j = 1 / j^2.  With P_m = sum_k p_k and
+ * E_m(z) = sum_k p_k omega({k z / 2^m}), p_k the product over the chosen
+ * components, e^2_m(z) = -1 + (P_m + gamma_s E_m(z)) / 2^m.  Sums run over
+ * k in increasing order; ties go to the smaller z (z and 2^m - z give the
+ * same lattice).  Plain O(dim 2^(2 m_max)) evaluation. */
+int or_lattice_cbc(uint32_t dim, int m_min, int m_max, uint32_t* z)
+{
+    if (m_min < 1 || m_max < m_min || m_max > 24 || dim < 1) return -1;
+    int nm = m_max - m_min + 1;
+    double** p = (double**)calloc((size_t)nm, sizeof(double*));
+    double* e2 = (double*)calloc((size_t)nm, sizeof(double));
+    double* P = (double*)calloc((size_t)nm, sizeof(double));
+    for (int a = 0; a < nm; ++a) {
+        uint32_t n = 1u << (m_min + a);
+        p[a] = (double*)malloc(sizeof(double) * n);
+        double sum = 0.0;
+        for (uint32_t k = 0; k < n; ++k) {
+            p[a][k] = 1.0 + 1.0 * bernoulli2((double)k / n);   /* z_1 = 1, gamma_1 = 1 */
+            sum += p[a][k];
+        }
+        e2[a] = -1.0 + sum / n;
+    }
+    z[0] = 1;
+    uint32_t half = 1u << (m_max - 1);
+    for (uint32_t s = 1; s < dim; ++s) {
+        double gamma = 1.0 / ((double)(s + 1) * (s + 1));
+        for (int a = 0; a < nm; ++a) {
+            uint32_t n = 1u << (m_min + a);
+            double sum = 0.0;
+            for (uint32_t k = 0; k < n; ++k) sum += p[a][k];
+            P[a] = sum;
+        }
+        uint32_t best = 1;
+        double bestC = INFINITY;
+        for (uint32_t c = 1; c < half; c += 2) {
+            double C = 0.0;
+            for (int a = 0; a < nm; ++a) {
+                uint32_t n = 1u << (m_min + a);
+                double E = 0.0;
+                for (uint32_t k = 0; k < n; ++k)
+                    E += p[a][k] * bernoulli2((double)(((uint64_t)k * c) & (n - 1)) / n);
+                C += (-1.0 + (P[a] + gamma * E) / n) / e2[a];
+            }
+            if (C < bestC) { bestC = C; best = c; }
+        }
+        z[s] = best;
+        for (int a = 0; a < nm; ++a) {
+            uint32_t n = 1u << (m_min + a);
+            double sum = 0.0;
+            for (uint32_t k = 0; k < n; ++k) {
+                p[a][k] *= 1.0 + gamma * bernoulli2((double)(((uint64_t)k * best) & (n - 1)) / n);
+                sum += p[a][k];
+            }
+            e2[a] = -1.0 + sum / n;
+        }
+    }
+    for (int a = 0; a < nm; ++a) free(p[a]);
+    free(p); free(e2); free(P);
+    return 0;
+}
+
+/* Shift-averaged squared worst-case error e^2 of the 2^m-point lattice with
+ * generating vector z (the quantity the construction above works with). */
+double or_lattice_e2(const uint32_t* z, uint32_t dim, int m)
+{
+    uint32_t n = 1u << m;
+    double sum = 0.0;
+    for (uint32_t k = 0; k < n; ++k) {
+        double prod = 1.0;
+        for (uint32_t j = 0; j < dim; ++j)
+            prod *= 1.0 + bernoulli2((double)(((uint64_t)k * z[j]) & (n - 1)) / n) / ((double)(j + 1) * (j + 1));
+        sum += prod;
+    }
+    return -1.0 + sum / n;
+}
+
+/* Points of the randomly shifted lattice sequence, 32-bit fixed point:
+ * point index i is taken in radical-inverse order (its m_max low bits
+ * reversed), so the first 2^m points are the 2^m-point lattice, and
+ * x[r][s][d] = (z_d phi(i) 2^(32 - m_max) + Delta_(r,d)) mod 2^32 with the
+ * shift Delta = the high 32 bits of word d of the Philox stream
+ * (seed, LATTICE_SHIFT << 32 | level) at index r.  u = (x + 1/2) 2^-32. */
+void or_lattice_points(const uint32_t* z, uint32_t dim, int m_max, uint64_t seed, uint32_t level,
+                       uint64_t first, uint32_t n, uint32_t first_shift, uint32_t n_shifts, uint32_t* x)
+{
+    uint64_t key1 = ((uint64_t)OR_PURPOSE_LATTICE_SHIFT << 32) | level;
+    for (uint32_t r = 0; r < n_shifts; ++r)
+        for (uint32_t s = 0; s < n; ++s) {
+            uint64_t i = first + s;
+            uint32_t rev = 0;
+            for (int b = 0; b < m_max; ++b)
+                if ((i >> b) & 1) rev |= 1u << (m_max - 1 - b);
+            for (uint32_t d = 0; d < dim; ++d) {
+                uint32_t delta = (uint32_t)(or_philox_word(seed, key1, first_shift + r, d) >> 32);
+                uint32_t t = (uint32_t)((uint64_t)z[d] * rev) & ((m_max == 32) ? 0xFFFFFFFFu : ((1u << m_max) - 1));
+                x[((size_t)r * n + s) * dim + d] = (t << (32 - m_max)) + delta;
+            }
+        }
+}
+
+/* Nested uniform scrambling (Owen 1995) of a 32-bit coordinate: output bit
+ * b (b = 0 the most significant) is input bit b XOR a random bit that
+ * depends on the scramble r, the dimension d, b and the input's b leading
+ * bits.  The random bit of that tree node is the low bit of word 0 of
+ * Philox4x64-10 with key (seed, OWEN << 32 | level) at counter
+ * (prefix, r << 32 | d, b, 0). */
+uint32_t or_owen_scramble(uint64_t seed, uint32_t level, uint32_t r, uint32_t d, uint32_t x)
+{
+    uint64_t key[2] = {seed, ((uint64_t)OR_PURPOSE_OWEN << 32) | level};
+    uint32_t y = 0;
+    for (int b = 0; b < 32; ++b) {
+        uint64_t prefix = b == 0 ? 0 : (uint64_t)(x >> (32 - b));
+        uint64_t ctr[4] = {prefix, ((uint64_t)r << 32) | d, (uint64_t)b, 0};
+        uint64_t out[4];
+        or_philox4x64_10(ctr, key, out);
+        uint32_t bit = ((x >> (31 - b)) & 1u) ^ (uint32_t)(out[0] & 1u);
+        y |= bit << (31 - b);
+    }
+    return y;
+}
+
+/* Owen-scrambled Sobol' points: the plain Gray-code point (no digital
+ * shift), then the nested scramble of scramble r = first_shift + r'. */
+void or_sobol_owen_points(const uint32_t* V, uint32_t dim, uint64_t seed, uint32_t level, uint64_t first,
+                          uint32_t n, uint32_t first_shift, uint32_t n_shifts, uint32_t* x)
+{
+    for (uint32_t r = 0; r < n_shifts; ++r)
+        for (uint32_t s = 0; s < n; ++s) {
+            uint64_t idx = first + s, gray = idx ^ (idx >> 1);
+            for (uint32_t d = 0; d < dim; ++d) {
+                uint32_t v = 0;
+                for (int b = 0; b < 32; ++b)
+                    if ((gray >> b) & 1) v ^= V[(size_t)d * 32 + b];
+                x[((size_t)r * n + s) * dim + d] = or_owen_scramble(seed, level, first_shift + r, d, v);
+            }
+        }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Finite volumes, Eq. 1 / Table 1.                                          */
 /* Interior face: harmonic mean 2 k_a k_b / (k_a + k_b) (unit face over unit */
 /* centre distance on square cells).  Dirichlet boundary face: the centre is */

@@ -54,6 +54,15 @@ def lib():
         L.or_mc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32,
                                     C.c_uint32, _D]
         L.or_mc_words.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, _U64]
+        L.or_lattice_cbc.argtypes = [C.c_uint32, C.c_int, C.c_int, _U32]
+        L.or_lattice_e2.argtypes = [_U32, C.c_uint32, C.c_int]
+        L.or_lattice_e2.restype = C.c_double
+        L.or_lattice_points.argtypes = [_U32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64,
+                                        C.c_uint32, C.c_uint32, C.c_uint32, _U32]
+        L.or_owen_scramble.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.or_owen_scramble.restype = C.c_uint32
+        L.or_sobol_owen_points.argtypes = [_U32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32,
+                                           C.c_uint32, C.c_uint32, _U32]
         L.or_gf2_is_primitive.argtypes = [C.c_uint64, C.c_int]
         L.or_primitive_polys.argtypes = [C.c_int, _U64, _I32]
         L.or_sobol_direction_numbers.argtypes = [C.c_uint32, _U32]
@@ -124,6 +133,41 @@ def mc_words(seed, level, first, n, dim):
     w = np.zeros((n, dim), np.uint64)
     lib().or_mc_words(seed, level, first, n, dim, w)
     return w
+
+
+def lattice_cbc(dim, m_min, m_max):
+    """Generating vector of the embedded lattice sequence (component by component)."""
+    z = np.zeros(dim, np.uint32)
+    assert lib().or_lattice_cbc(dim, m_min, m_max, z) == 0
+    return z
+
+
+def lattice_e2(z, m):
+    """Shift-averaged squared worst-case error of the 2^m-point lattice."""
+    z = np.ascontiguousarray(z, np.uint32)
+    return lib().or_lattice_e2(z, len(z), m)
+
+
+def lattice_points(z, m_max, seed, level, first, n, first_shift=0, n_shifts=1):
+    """Randomly shifted lattice sequence, uint32 [n_shifts][n][dim]."""
+    z = np.ascontiguousarray(z, np.uint32)
+    x = np.zeros((n_shifts, n, len(z)), np.uint32)
+    lib().or_lattice_points(z, len(z), m_max, seed, level, first, n, first_shift, n_shifts, x)
+    return x
+
+
+def owen_scramble(seed, level, r, d, x):
+    return np.array([lib().or_owen_scramble(seed, level, r, d, int(v)) for v in np.ravel(x)],
+                    np.uint32).reshape(np.shape(x))
+
+
+def sobol_owen_points(V, seed, level, first, n, first_shift=0, n_shifts=1):
+    """Owen-scrambled Sobol' points, uint32 [n_shifts][n][dim]."""
+    V = np.ascontiguousarray(V, np.uint32)
+    dim = V.shape[0]
+    x = np.zeros((n_shifts, n, dim), np.uint32)
+    lib().or_sobol_owen_points(V, dim, seed, level, first, n, first_shift, n_shifts, x)
+    return x
 
 
 def primitive_polys(count):
