@@ -98,7 +98,21 @@ typedef struct {
     double pS, pN;        /* Case I: Dirichlet data on the south / north edges */
     double nu;            /* Matern smoothness of the field (Sec. 3.1, Table 2): 0.5 (exponential;
                              0 is read as 0.5), 1, 1.5 or 2.5 */
+    int32_t qmc_rule;     /* randomized QMC points of the MLQMC estimator (FM_QMC_*) */
+    int32_t lattice_m;    /* FM_QMC_LATTICE: the sequence holds 2^lattice_m points (5 .. 24;
+                             0 is read as 16) */
 } fm_config;
+
+/* Randomized QMC rules (Sec. 2.4).
+ * FM_QMC_SOBOL_SHIFT: Sobol' points, XOR with a random digital shift.
+ * FM_QMC_SOBOL_OWEN:  Sobol' points, nested uniform (Owen) scrambling.
+ * FM_QMC_LATTICE:     rank-1 lattice sequence (generating vector from
+ *                     fm_lattice_cbc for the embedded sets of 2^5 ..
+ *                     2^lattice_m points, built when the context is
+ *                     created), shifted modulo 1 by a random vector. */
+#define FM_QMC_SOBOL_SHIFT 0
+#define FM_QMC_SOBOL_OWEN 1
+#define FM_QMC_LATTICE 2
 
 /* Boundary conditions and QoI (Table 1).
  * FM_CASE_II: p = pW on the west edge, pE on the east edge, no flow through
@@ -186,6 +200,38 @@ fm_status sobol_points(fm_ctx* ctx, uint32_t level, uint32_t dim, uint64_t first
 
 /* Host copy of the Sobol' direction numbers V[d*32 + b] (d < M, b < 32). */
 fm_status sobol_direction_numbers(const fm_ctx* ctx, uint32_t* V);
+
+/* Randomized QMC points of rule `rule` (FM_QMC_*), point indices first ..
+ * first+n-1, randomizations first_shift .. first_shift+n_shifts-1, 32-bit
+ * fixed point x in d_x (nullable) and Phi^{-1}((x + 1/2) 2^-32) in d_xi
+ * (nullable), both [n_shifts][n][dim], dim <= M.
+ *   FM_QMC_SOBOL_SHIFT: as sobol_points.
+ *   FM_QMC_SOBOL_OWEN:  the Gray-code Sobol' point x, then output bit b
+ *       (b = 0 the leading bit) = input bit b XOR the random bit of tree node
+ *       (b, the b leading input bits): the low bit of word 0 of Philox4x64-10
+ *       keyed (seed, 5 << 32 | level) at counter (prefix, r << 32 | d, b, 0).
+ *   FM_QMC_LATTICE:     point index i in radical-inverse order over
+ *       lattice_m bits, x = (z_d phi(i) 2^(32 - lattice_m) + Delta) mod 2^32,
+ *       Delta = high 32 bits of word d of the Philox stream (seed, 4 << 32 |
+ *       level) at index r; first + n <= 2^lattice_m.  Needs a context created
+ *       with qmc_rule = FM_QMC_LATTICE (FM_EINVAL otherwise). */
+fm_status qmc_points(fm_ctx* ctx, int32_t rule, uint32_t level, uint32_t dim, uint64_t first, uint32_t n,
+                     uint32_t first_shift, uint32_t n_shifts, uint32_t* d_x, double* d_xi, void* stream);
+
+/* Generating vector of a rank-1 lattice sequence for the embedded point sets
+ * of 2^m points, m = m_min .. m_max (Sec. 2.4 lattice rules; host only, no
+ * CUDA call).  Component by component: z_1 = 1; component s is the odd
+ * z < 2^(m_max-1) minimising sum_m e^2_m(z_1..z_(s-1), z) / e^2_m(z_1..z_(s-1)),
+ * e^2_m = -1 + 2^-m sum_k prod_j (1 + gamma_j B_2({k z_j / 2^m})) the
+ * shift-averaged squared worst-case error with product weights
+ * gamma_j = 1/j^2 (ties to the smaller z).  Evaluated by the fast
+ * construction of Nuyens and Cools (FFTs over the group of odd residues
+ * mod 2^m), the minimum confirmed on plain sums.  z: host [dim], dim <= 4096,
+ * 1 <= m_min <= m_max <= 24. */
+fm_status fm_lattice_cbc(uint32_t dim, int32_t m_min, int32_t m_max, uint32_t* z);
+
+/* Host copy of the context's lattice generating vector [M] (FM_QMC_LATTICE). */
+fm_status lattice_generating_vector(const fm_ctx* ctx, uint32_t* z);
 
 /* ---------------------------------------------------------------- KL field */
 

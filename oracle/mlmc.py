@@ -153,14 +153,19 @@ class FMGSampler:
     with level_basis(n)); seed: the Philox key for MC points and QMC shifts."""
 
     def __init__(self, levels, basis, seed, prm=None, n0=4, qmc_dirnums=None,
-                 n_shifts=0, nthreads=0):
+                 n_shifts=0, nthreads=0, rule="shift", lattice_z=None, lattice_m=16):
+        """rule (randomized QMC, Sec. 2.4): 'shift' Sobol' + digital shift,
+        'owen' Sobol' + nested uniform scrambling (qmc_dirnums needed for
+        both), 'lattice' the shifted lattice sequence with generating vector
+        lattice_z over 2^lattice_m points."""
         self.levels, self.basis, self.seed = list(levels), basis, seed
         self.prm = prm or _lib.params()
         self.n0 = n0
         self.B = [basis.level_basis(n) for n in self.levels]
         self.V = qmc_dirnums
+        self.rule, self.z, self.mz = rule, lattice_z, lattice_m
         self.shifts = None
-        if qmc_dirnums is not None:
+        if qmc_dirnums is not None and rule == "shift":
             M = self.B[0].shape[1]
             self.shifts = [_lib.sobol_shifts(seed, l, n_shifts, M) for l in range(len(levels))]
         self.nthreads = nthreads
@@ -170,8 +175,14 @@ class FMGSampler:
         M = self.B[l].shape[1]
         if r is None:
             return _lib.mc_normals(self.seed, l, first, n, M)
-        _, xi = _lib.sobol_points(self.V, first, n, self.shifts[l][r:r + 1], want_xi=True)
-        return xi[0]
+        if self.rule == "owen":
+            x = _lib.sobol_owen_points(self.V, self.seed, l, first, n, r, 1)[0]
+        elif self.rule == "lattice":
+            x = _lib.lattice_points(self.z, self.mz, self.seed, l, first, n, r, 1)[0]
+        else:
+            _, xi = _lib.sobol_points(self.V, first, n, self.shifts[l][r:r + 1], want_xi=True)
+            return xi[0]
+        return _lib.norminv((x.astype(np.float64) + 0.5) * 2.0 ** -32)
 
     def solve(self, l, xi):
         n = self.levels[l]

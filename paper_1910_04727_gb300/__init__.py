@@ -52,6 +52,16 @@ def matern_covariance(d, nu, sigma2=1.0, lam=1.0):
     return c
 
 
+def lattice_cbc(dim, m_min, m_max):
+    """Generating vector of the embedded lattice sequence (fm_lattice_cbc, host)."""
+    L = _lib.load()
+    z = np.zeros(dim, np.uint32)
+    st = L.fm_lattice_cbc(dim, m_min, m_max, z.ctypes.data_as(C.c_void_p))
+    if st != 0:
+        raise FmError(st, "fm_lattice_cbc")
+    return z
+
+
 def shard_range(first, n, rank, world):
     """(first, count) of rank `rank`'s contiguous share of samples first .. first+n-1."""
     L = _lib.load()
@@ -135,14 +145,15 @@ class Context:
     def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
                  nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
                  precision=FM_PREC_FP64, converged=False, tol=1e-10, qtol=0.0, max_cycles=100,
-                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0, nu=0.5):
+                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0, nu=0.5, qmc_rule=0, lattice_m=0):
         """bc_case: Table 1's FM_CASE_II (no flow north / south, east outflux) or
         FM_CASE_I (Dirichlet pW, pE, pS, pN on all four edges, QoI u(0.5, 0.5)).
-        nu: Matern smoothness of the field (0.5, 1, 1.5 or 2.5)."""
+        nu: Matern smoothness of the field (0.5, 1, 1.5 or 2.5).
+        qmc_rule: FM_QMC_SOBOL_SHIFT, FM_QMC_SOBOL_OWEN or FM_QMC_LATTICE (2^lattice_m points)."""
         self._L = _lib.load()
         cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
                             precision, int(bool(converged)), tol, qtol, max_cycles, kl_mode, n_shifts,
-                            seed, max_batch, bc_case, pS, pN, nu)
+                            seed, max_batch, bc_case, pS, pN, nu, qmc_rule, lattice_m)
         h = C.c_void_p()
         st = self._L.fm_create(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -189,6 +200,21 @@ class Context:
         self._check(self._L.sobol_points(self._h, level, dim, first, n, first_shift, n_shifts,
                                          _ptr(x), _ptr(xi), _stream()))
         return x, xi
+
+    def qmc_points(self, rule, level, first, n, first_shift=0, n_shifts=1, dim=None, want_x=True,
+                   want_xi=True):
+        """Randomized QMC points of an FM_QMC_* rule: (x uint32 bits as int32, xi) [n_shifts][n][dim]."""
+        dim = dim or self.M
+        x = torch.empty((n_shifts, n, dim), dtype=torch.int32, device="cuda") if want_x else None
+        xi = torch.empty((n_shifts, n, dim), dtype=torch.float64, device="cuda") if want_xi else None
+        self._check(self._L.qmc_points(self._h, rule, level, dim, first, n, first_shift, n_shifts,
+                                       _ptr(x), _ptr(xi), _stream()))
+        return x, xi
+
+    def lattice_generating_vector(self):
+        z = np.zeros(self.M, np.uint32)
+        self._check(self._L.lattice_generating_vector(self._h, z.ctypes.data_as(C.c_void_p)))
+        return z
 
     def sobol_direction_numbers(self):
         V = np.zeros((self.M, 32), np.uint32)

@@ -15,6 +15,7 @@ FM_PREC_MIXED = 1
 FM_KERNEL_AUTO, FM_KERNEL_LEVELWISE, FM_KERNEL_RESIDENT = 0, 1, 2
 FM_KL_AUTO, FM_KL_FP64, FM_KL_BF16, FM_KL_BF16X3 = 0, 1, 2, 3
 FM_CASE_I, FM_CASE_II = 1, 2
+FM_QMC_SOBOL_SHIFT, FM_QMC_SOBOL_OWEN, FM_QMC_LATTICE = 0, 1, 2
 
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENOTCONV",
                 5: "FM_ETIMEOUT", 6: "FM_EUNSUPPORTED"}
@@ -27,7 +28,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
-           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance"]
+           "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance", "qmc_points",
+           "fm_lattice_cbc", "lattice_generating_vector"]
 
 
 class FmConfig(C.Structure):
@@ -38,7 +40,8 @@ class FmConfig(C.Structure):
                 ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
                 ("kl_mode", C.c_int32),
                 ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64),
-                ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double), ("nu", C.c_double)]
+                ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double), ("nu", C.c_double),
+                ("qmc_rule", C.c_int32), ("lattice_m", C.c_int32)]
 
 
 class FmSolveParams(C.Structure):
@@ -155,6 +158,9 @@ def load(path=None):
         "fm_sync": (I32, [P]),
         "fm_wait_check": (I32, [P, I64, P]),
         "fm_matern_covariance": (I32, [D, D, D, P, I64, P]),
+        "qmc_points": (I32, [P, I32, U32, U32, U64, U32, U32, U32, P, P, P]),
+        "fm_lattice_cbc": (I32, [U32, I32, I32, P]),
+        "lattice_generating_vector": (I32, [P, P]),
         "fmg_solve_batch_static": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P]),
         "surrogate_param_count": (I64, [P]),
         "surrogate_params": (I32, [P, P, I32]),

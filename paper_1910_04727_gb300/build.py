@@ -17,8 +17,10 @@ BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfmgmlmc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", _INC, "-I", _SRC]
+# host code without fused multiply-add contraction: the lattice construction
+# takes its decisions on sums that must round the same on every host
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr", "-I", _INC, "-I", _SRC]
 
 
 def _nvcc():

@@ -41,12 +41,17 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
                  "fm_create: bc_case must be FM_CASE_I or FM_CASE_II");
     FM_CHECK_ARG(nullptr, cfg->nu == 0.0 || cfg->nu == 0.5 || cfg->nu == 1.0 || cfg->nu == 1.5 || cfg->nu == 2.5,
                  "fm_create: nu must be 0.5, 1, 1.5 or 2.5");
+    FM_CHECK_ARG(nullptr, cfg->qmc_rule >= FM_QMC_SOBOL_SHIFT && cfg->qmc_rule <= FM_QMC_LATTICE,
+                 "fm_create: unknown qmc_rule");
+    FM_CHECK_ARG(nullptr, cfg->lattice_m == 0 || (cfg->lattice_m >= 5 && cfg->lattice_m <= 24),
+                 "fm_create: lattice_m must be 5 .. 24");
     fm_ctx* ctx = new (std::nothrow) fm_ctx();
     if (!ctx) {
         set_error(nullptr, "fm_create: host allocation failed");
         return FM_ENOMEM;
     }
     ctx->cfg = *cfg;
+    if (ctx->cfg.lattice_m == 0) ctx->cfg.lattice_m = 16;
     cudaGetDevice(&ctx->device);
     if (sobol_direction_numbers_host((uint32_t)cfg->M, ctx->h_sobol_V) != 0) {
         delete ctx;
@@ -66,6 +71,18 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
         set_error(nullptr, "fm_create: copy of the direction numbers failed");
         return FM_ECUDA;
     }
+    if (cfg->qmc_rule == FM_QMC_LATTICE) {
+        const int mm = ctx->cfg.lattice_m;
+        const std::vector<uint32_t>* z = lattice_vector_cached((uint32_t)cfg->M, lattice_m_min(mm), mm);
+        if (!z || cudaMalloc((void**)&ctx->d_lattice_z, z->size() * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMemcpy(ctx->d_lattice_z, z->data(), z->size() * sizeof(uint32_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            fm_destroy(ctx);
+            set_error(nullptr, "fm_create: lattice generating vector unavailable");
+            return FM_ENOMEM;
+        }
+        ctx->h_lattice_z = *z;
+    }
     if (cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
         fm_destroy(ctx);
         set_error(nullptr, "fm_create: stream creation failed");
@@ -81,6 +98,7 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     if (!ctx) return;
     for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->d_basis[l]);
     cudaFree(ctx->d_sobol_V);
+    cudaFree(ctx->d_lattice_z);
     cudaFree(ctx->arena.base);
     cudaFree(ctx->d_xi);
     cudaFree(ctx->d_K);

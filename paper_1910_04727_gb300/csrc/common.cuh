@@ -26,6 +26,8 @@ constexpr uint64_t kPhiloxW1 = 0xBB67AE8584CAA73BULL;
 constexpr uint64_t kPurposeMC = 1;
 constexpr uint64_t kPurposeShift = 2;
 constexpr uint64_t kPurposeSobolDir = 3;
+constexpr uint64_t kPurposeLatticeShift = 4;
+constexpr uint64_t kPurposeOwen = 5;
 constexpr uint64_t kSobolDirSeed = 0x1910047270ULL;
 
 struct u64x4 {
@@ -188,6 +190,9 @@ struct fm_ctx {
     // Sobol' direction numbers [M][32] (device and host copies).
     uint32_t* d_sobol_V = nullptr;
     std::vector<uint32_t> h_sobol_V;
+    // lattice generating vector [M] (device and host copies; FM_QMC_LATTICE)
+    uint32_t* d_lattice_z = nullptr;
+    std::vector<uint32_t> h_lattice_z;
     // scratch
     fm::Arena arena;
     double* d_xi = nullptr;          // points of the current batch
@@ -298,5 +303,11 @@ fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const doub
 
 // Host-side Sobol' direction numbers (points.cu).
 int sobol_direction_numbers_host(uint32_t dim, std::vector<uint32_t>& V);
+
+// Lattice generating vector of the embedded 2^m point sets (lattice.cu).
+int lattice_cbc_host(uint32_t dim, int m_min, int m_max, uint32_t* z);
+const std::vector<uint32_t>* lattice_vector_cached(uint32_t dim, int m_min, int m_max);
+// The smallest embedded size of the lattice sequence: 2^5 points (the QMC pilot).
+inline int lattice_m_min(int m_max) { return m_max < 5 ? m_max : 5; }
 
 }  // namespace fm

@@ -163,8 +163,8 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
     for (uint64_t off = 0; off < n; off += cap) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(cap, n - off);
         if (shift >= 0) {
-            FM_TRY(sobol_points(ctx, stream_level, (uint32_t)M, first + off, cnt, (uint32_t)shift, 1, nullptr,
-                                ctx->d_xi, stream));
+            FM_TRY(qmc_points(ctx, ctx->cfg.qmc_rule, stream_level, (uint32_t)M, first + off, cnt, (uint32_t)shift, 1,
+                              nullptr, ctx->d_xi, stream));
         } else if (!s_mc) {
             FM_TRY(mc_points(ctx, stream_level, first + off, cnt, (uint32_t)M, ctx->d_xi, stream));
         }
@@ -312,8 +312,8 @@ fm_status flush_batched(GpuSampler* g) {
                 const uint32_t cnt = (uint32_t)std::min<uint64_t>(r.n - d, (uint64_t)1 << 30);
                 double* xi = b.xi + (o + d) * M;
                 if (r.shift < 0) FM_TRY(mc_points(ctx, (uint32_t)l, r.first + d, cnt, (uint32_t)M, xi, nullptr));
-                else FM_TRY(sobol_points(ctx, (uint32_t)l, (uint32_t)M, r.first + d, cnt, (uint32_t)r.shift, 1,
-                                         nullptr, xi, nullptr));
+                else FM_TRY(qmc_points(ctx, ctx->cfg.qmc_rule, (uint32_t)l, (uint32_t)M, r.first + d, cnt,
+                                       (uint32_t)r.shift, 1, nullptr, xi, nullptr));
                 d += cnt;
             }
             o += r.n;

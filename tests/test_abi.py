@@ -87,3 +87,18 @@ def test_level_stats_from_exact_sums(lib_path, mean, sd):
     assert abs(st.mean - float(s1 / n)) <= 1e-15 * abs(float(s1 / n)) + 1e-300
     assert abs(Fraction(st.var) - want_var) <= Fraction(1, 10 ** 12) * want_var
     assert L.fm_level_stats(None, ctypes.byref(st)) == _lib.FM_EINVAL
+
+
+@pytest.mark.parametrize("dim,m_min,m_max", [(8, 3, 7), (32, 4, 10), (128, 5, 10), (16, 5, 12)])
+def test_fast_lattice_construction_equals_the_plain_one(lib_path, dim, m_min, m_max):
+    """fm_lattice_cbc (host only: FFTs over the odd residues, the minimum
+    confirmed on plain sums) gives the oracle's plain component-by-component
+    vector bit for bit."""
+    import numpy as np
+    from oracle import lib as OL
+    from paper_1910_04727_gb300 import _lib
+    L = _lib.load(lib_path)
+    z = np.zeros(dim, np.uint32)
+    assert L.fm_lattice_cbc(dim, m_min, m_max, z.ctypes.data_as(ctypes.c_void_p)) == 0
+    np.testing.assert_array_equal(z, OL.lattice_cbc(dim, m_min, m_max))
+    assert L.fm_lattice_cbc(dim, 6, 5, z.ctypes.data_as(ctypes.c_void_p)) == _lib.FM_EINVAL
