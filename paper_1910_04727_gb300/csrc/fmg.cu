@@ -1718,7 +1718,7 @@ fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const d
         }
         FM_CHECK_ARG(ctx, prm.kernel == FM_KERNEL_AUTO,
                      "fmg_solve_batch: the resident schedule needs the hierarchy in shared memory "
-                     "(n_fine <= 64)");
+                     "(n_fine <= 64) and a power-of-two coarsest grid (2 or 4)");
     }
     if (prm.precision == FM_PREC_MIXED)
         return levelwise<float>(ctx, ar, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st);

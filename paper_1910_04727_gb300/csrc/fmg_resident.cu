@@ -30,16 +30,24 @@
 
 namespace fm {
 
+// Grids are n = 2^lg cells a side (the resident schedule takes power-of-two
+// hierarchies), so cell c = j n + i splits by shifts and masks.
 template <typename T>
 struct RGrid {
-    int n;
+    int n, lg;
     T *p, *te, *tn, *dinv, *tw, *ts, *b;   // dinv and b may be null
 };
 
 struct HGrid {
-    int n;
+    int n, lg;
     double *p, *te, *tn, *tw, *ts;
 };
+
+__host__ __device__ inline int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
 
 template <typename T>
 struct RLayout {
@@ -52,9 +60,10 @@ struct RLayout {
     size_t bytes;
 };
 
-// Carve the shared buffer (or count its size when base == nullptr).
+// Carve the shared buffer (or count its size when base == nullptr).  warp:
+// one sample per warp (its reductions are shuffles, no block scratch).
 template <typename T>
-__host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, int n0, bool mixed) {
+__host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, int n0, bool mixed, bool warp) {
     RLayout<T> L;
     L.n0 = n0;
     L.m = 0;
@@ -70,6 +79,7 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         const size_t c = (size_t)n * n;
         RGrid<T>& g = L.g[k];
         g.n = n;
+        g.lg = ilog2(n);
         g.p = (T*)take(c * sizeof(T));
         g.te = (T*)take(c * sizeof(T));
         g.tn = (T*)take(c * sizeof(T));
@@ -85,6 +95,7 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         const int k = L.m - 1 + q;
         HGrid& h = L.h[q];
         h.n = (k >= 0) ? (n0 << k) : 0;
+        h.lg = ilog2(h.n);
         h.p = h.te = h.tn = h.tw = h.ts = nullptr;
         if (!mixed || k < 0) continue;
         const size_t c = (size_t)h.n * h.n;
@@ -95,8 +106,17 @@ __host__ __device__ inline RLayout<T> resident_layout(char* base, int n_fine, in
         h.ts = (double*)take(h.n * 8);
     }
     L.ainv = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
-    L.work = (T*)take((size_t)n0 * n0 * n0 * n0 * sizeof(T));
-    L.red = (double*)take(80 * 8);
+    // Gauss-Jordan scratch of the coarse inverses (formed before the stage
+    // loop and at stage 1): the finest grid's iterate (FP64 copy in the mixed
+    // form), which nothing touches before stage m >= 2
+    const size_t wbytes = (size_t)n0 * n0 * n0 * n0 * sizeof(T);
+    if (L.m >= 2 && mixed && L.h[1].p)
+        L.work = (T*)L.h[1].p;
+    else if (L.m >= 2 && !mixed && (size_t)n_fine * n_fine * sizeof(T) >= wbytes)
+        L.work = L.g[L.m].p;
+    else
+        L.work = (T*)take(wbytes);
+    L.red = warp ? nullptr : (double*)take(80 * 8);
     L.bytes = off;
     return L;
 }
@@ -128,7 +148,7 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
     const int n = g.n, s = n_fine / n;
     auto K = [&](int i, int j) { return __ldg(Kf + (size_t)(s * j) * n_fine + (size_t)s * i); };
     for (int c = rank(); c < n * n; c += size()) {
-        const int i = c % n, j = c / n;
+        const int i = c & (n - 1), j = c >> g.lg;
         if (h || sizeof(T) == 8) {
             const double k = K(i, j);
             const double tb = ns ? 2.0 * k : 0.0;   // south / north edge face
@@ -136,11 +156,6 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
             const double tn = (j < n - 1) ? harm(k, K(i, j + 1)) : tb;
             g.te[c] = (T)te;
             g.tn[c] = (T)tn;
-            if (g.dinv) {   // the FP64 form's diagonal (the mixed form forms it on the fly)
-                const double tw = (i > 0) ? harm(K(i - 1, j), k) : 2.0 * k;
-                const double ts = (j > 0) ? harm(K(i, j - 1), k) : tb;
-                g.dinv[c] = (T)(1.0 / (tw + te + ts + tn));
-            }
             if (i == 0) g.tw[j] = (T)(2.0 * k);
             if (j == 0) g.ts[i] = (T)tb;
             if (h) {
@@ -152,15 +167,33 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
         } else {
             const T k = (T)K(i, j);
             const T tb = ns ? T(2) * k : T(0);
-            const T tw = (i > 0) ? harm((T)K(i - 1, j), k) : T(2) * k;
             const T te = (i < n - 1) ? harm(k, (T)K(i + 1, j)) : T(2) * k;
-            const T ts = (j > 0) ? harm((T)K(i, j - 1), k) : tb;
             const T tn = (j < n - 1) ? harm(k, (T)K(i, j + 1)) : tb;
             g.te[c] = te;
             g.tn[c] = tn;
-            if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
             if (i == 0) g.tw[j] = T(2) * k;
             if (j == 0) g.ts[i] = tb;
+        }
+    }
+}
+
+// Reciprocal diagonal of grid n from its stored faces, once every face of the
+// grid is in place (each face is formed once: the west face of a cell is its
+// west neighbour's east face, the same harmonic mean of the same two values).
+// With an FP64 copy h the sum and reciprocal are taken in FP64.
+static __device__ void resident_setup_diag(const RGrid<T>& g, const HGrid* h) {
+    if (!g.dinv) return;
+    const int n = g.n;
+    for (int c = rank(); c < n * n; c += size()) {
+        const int i = c & (n - 1), j = c >> g.lg;
+        if (h) {
+            const double tw = (i > 0) ? h->te[c - 1] : h->tw[j];
+            const double ts = (j > 0) ? h->tn[c - n] : h->ts[i];
+            g.dinv[c] = (T)(1.0 / (tw + h->te[c] + ts + h->tn[c]));
+        } else {
+            const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
+            const T ts = (j > 0) ? g.tn[c - n] : g.ts[i];
+            g.dinv[c] = T(1) / (tw + g.te[c] + ts + g.tn[c]);
         }
     }
 }
@@ -173,7 +206,7 @@ static __device__ void resident_setup_correction(const RGrid<T>& g, const double
                                                  int ns) {
     const int n = g.n, s = n_fine / n, h2 = s / 2;
     for (int c = rank(); c < n * n; c += size()) {
-        const int i = c % n, j = c / n;
+        const int i = c & (n - 1), j = c >> g.lg;
         const size_t r0 = (size_t)(s * j) * n_fine + (size_t)s * i, r1 = r0 + (size_t)h2 * n_fine;
         const double a = __ldg(Kf + r0), b = __ldg(Kf + r0 + h2), cc = __ldg(Kf + r1), d = __ldg(Kf + r1 + h2);
         if (sizeof(T) == 8)
@@ -183,19 +216,18 @@ static __device__ void resident_setup_correction(const RGrid<T>& g, const double
     }
     sync();
     for (int c = rank(); c < n * n; c += size()) {
-        const int i = c % n, j = c / n;
+        const int i = c & (n - 1), j = c >> g.lg;
         const T k = g.p[c];
         const T tb = ns ? T(2) * k : T(0);
-        const T tw = (i > 0) ? harm(g.p[c - 1], k) : T(2) * k;
         const T te = (i < n - 1) ? harm(k, g.p[c + 1]) : T(2) * k;
-        const T ts = (j > 0) ? harm(g.p[c - n], k) : tb;
         const T tn = (j < n - 1) ? harm(k, g.p[c + n]) : tb;
         g.te[c] = te;
         g.tn[c] = tn;
-        if (g.dinv) g.dinv[c] = T(1) / (tw + te + ts + tn);
         if (i == 0) g.tw[j] = T(2) * k;
         if (j == 0) g.ts[i] = tb;
     }
+    sync();
+    resident_setup_diag(g, nullptr);
     sync();
 }
 
@@ -234,12 +266,13 @@ static __device__ __forceinline__ T divide_by_diag(const RGrid<T>& g, T acc, int
 static __device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A) {
     const int n = g.n, m = n * n;
     for (int e = rank(); e < m * m; e += size()) {
-        const int r = e / m, c = e % m;
+        const int lm = 2 * g.lg;   // m = n^2 = 2^lm
+        const int r = e >> lm, c = e & (m - 1);
         T v = T(0);
         if (r == c) {
-            v = diag_at(g, r, r % n, r / n);
+            v = diag_at(g, r, r & (n - 1), r >> g.lg);
         } else {
-            const int ri = r % n, rj = r / n, ci = c % n, cj = c / n;
+            const int ri = r & (n - 1), rj = r >> g.lg, ci = c & (n - 1), cj = c >> g.lg;
             if (rj == cj && ci == ri + 1) v = -g.te[r];
             if (rj == cj && ci == ri - 1) v = -g.te[c];
             if (ri == ci && cj == rj + 1) v = -g.tn[r];
@@ -258,7 +291,7 @@ static __device__ void resident_coarse_inverse(const RGrid<T>& g, T* ainv, T* A)
         }
         sync();
         for (int e = rank(); e < m * m; e += size()) {
-            const int r = e / m, c = e % m;
+            const int r = e >> (2 * g.lg), c = e & (m - 1);
             if (r == k) continue;
             const T f = A[r * m + k];   // column k is left alone until the next phase
             if (c != k) A[e] -= f * A[k * m + c];
@@ -275,7 +308,7 @@ static __device__ __forceinline__ void resident_coarse_solve(const RGrid<T>& g, 
     const int n = g.n, m = n * n;
     T acc = T(0);
     if (rank() < m)
-        for (int c = 0; c < m; ++c) acc += ainv[rank() * m + c] * rhs_at(g, c, c % n, c / n, d);
+        for (int c = 0; c < m; ++c) acc += ainv[rank() * m + c] * rhs_at(g, c, c & (n - 1), c >> g.lg, d);
     sync();
     if (rank() < m) g.p[rank()] = acc;
     sync();
@@ -285,8 +318,8 @@ static __device__ __forceinline__ void resident_rbgs(const RGrid<T>& g, const Gh
     const int n = g.n, half = n * n / 2, hn = n / 2;
     for (int color = 0; color < 2; ++color) {
         for (int h = rank(); h < half; h += size()) {
-            const int j = h / hn;
-            const int i = 2 * (h % hn) + ((j + color) & 1);
+            const int j = h >> (g.lg - 1);
+            const int i = 2 * (h & (hn - 1)) + ((j + color) & 1);
             const int c = j * n + i;
             T acc = rhs_at(g, c, i, j, d);
             if (i > 0) acc += g.te[c - 1] * g.p[c - 1];
@@ -312,7 +345,7 @@ static __device__ __forceinline__ T resident_residual(const RGrid<T>& g, int c, 
 static __device__ __forceinline__ void resident_restrict(const RGrid<T>& f, const RGrid<T>& cg, const Ghost<T>& d) {
     const int nc = cg.n, nf = f.n;
     for (int C = rank(); C < nc * nc; C += size()) {
-        const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J, c0 = j0 * nf + i0;
+        const int I = C & (nc - 1), J = C >> cg.lg, i0 = 2 * I, j0 = 2 * J, c0 = j0 * nf + i0;
         const T r00 = resident_residual(f, c0, i0, j0, d);
         const T r10 = resident_residual(f, c0 + 1, i0 + 1, j0, d);
         const T r01 = resident_residual(f, c0 + nf, i0, j0 + 1, d);
@@ -348,9 +381,9 @@ static __device__ __forceinline__ U ghost(const U* uc, int nc, int I, int J, con
 // out (+)= bilinear interpolation of uc (nc x nc) onto the 2nc x 2nc grid.
 template <typename U>
 static __device__ __forceinline__ void resident_prolong(const U* uc, int nc, U* out, const Ghost<U>& gd, bool add) {
-    const int nf = 2 * nc;
+    const int nf = 2 * nc, lgf = ilog2(nf);
     for (int c = rank(); c < nf * nf; c += size()) {
-        const int i = c % nf, j = c / nf, I = i >> 1, J = j >> 1;
+        const int i = c & (nf - 1), j = c >> lgf, I = i >> 1, J = j >> 1;
         const int Ix = (i & 1) ? I + 1 : I - 1;
         const int Jy = (j & 1) ? J + 1 : J - 1;
         const U v = (U(9) * ghost(uc, nc, I, J, gd) + U(3) * ghost(uc, nc, Ix, J, gd) +
@@ -414,7 +447,7 @@ static __device__ __forceinline__ void block_sum2(double a, double b, double* re
 // Stage problem of grid k written into its rhs: the Dirichlet data.
 static __device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, const Ghost<T>& d) {
     for (int c = rank(); c < g.n * g.n; c += size()) {
-        const int i = c % g.n, j = c / g.n;
+        const int i = c & (g.n - 1), j = c >> g.lg;
         g.b[c] = dirichlet_at(g, c, i, j, d);
     }
     sync();
@@ -424,7 +457,7 @@ static __device__ __forceinline__ void resident_stage_rhs(const RGrid<T>& g, con
 static __device__ void stage_norms(const RGrid<T>& g, const Ghost<T>& d, double* red, double& rr, double& bb) {
     double a = 0.0, b = 0.0;
     for (int c = rank(); c < g.n * g.n; c += size()) {
-        const int i = c % g.n, j = c / g.n;
+        const int i = c & (g.n - 1), j = c >> g.lg;
         const double r = (double)resident_residual(g, c, i, j, d);
         const double f = (double)rhs_at(g, c, i, j, d);
         a += r * r;
@@ -440,7 +473,7 @@ static __device__ void ir_residual(const HGrid& h, const RGrid<T>& g, const Ghos
     const int n = h.n;
     double a = 0.0, b = 0.0;
     for (int c = rank(); c < n * n; c += size()) {
-        const int i = c % n, j = c / n;
+        const int i = c & (n - 1), j = c >> h.lg;
         const double tw = (i > 0) ? h.te[c - 1] : h.tw[j];
         const double ts = (j > 0) ? h.tn[c - n] : h.ts[i];
         const double f = dirichlet_at(h, c, i, j, d);
@@ -547,9 +580,9 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
     const int groups = WARP ? (int)(blockDim.x >> 5) : 1;
     const int grp = WARP ? (int)(threadIdx.x >> 5) : 0;
     RLayout<T>* slot = reinterpret_cast<RLayout<T>*>(smem + grp * resident_slot_bytes<T>());
-    const size_t data_bytes = resident_layout<T>(nullptr, a.n_fine, a.n0, MIXED).bytes;
+    const size_t data_bytes = resident_layout<T>(nullptr, a.n_fine, a.n0, MIXED, WARP).bytes;
     char* data = smem + groups * resident_slot_bytes<T>() + grp * data_bytes;
-    if (R::rank() == 0) *slot = resident_layout<T>(data, a.n_fine, a.n0, MIXED);
+    if (R::rank() == 0) *slot = resident_layout<T>(data, a.n_fine, a.n0, MIXED, WARP);
     R::sync();
     const RLayout<T>& L = *slot;
     // the boundary data in the V-cycle arithmetic, and zero data on the same
@@ -563,6 +596,11 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
         for (int k = 0; k <= m; ++k) {
             const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
             R::resident_setup_grid(L.g[k], h, Kf, a.n_fine, a.bd.ns);
+        }
+        R::sync();
+        for (int k = 0; k <= m; ++k) {
+            const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
+            R::resident_setup_diag(L.g[k], h);
         }
         R::sync();
         R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
@@ -682,9 +720,9 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
     }
 }
 
-size_t resident_smem_bytes(int n_fine, int n0, bool mixed) {
-    return mixed ? resident_layout<float>(nullptr, n_fine, n0, true).bytes
-                 : resident_layout<double>(nullptr, n_fine, n0, false).bytes;
+size_t resident_smem_bytes(int n_fine, int n0, bool mixed, bool warp) {
+    return mixed ? resident_layout<float>(nullptr, n_fine, n0, true, warp).bytes
+                 : resident_layout<double>(nullptr, n_fine, n0, false, warp).bytes;
 }
 
 constexpr size_t kResidentSmemMax = 227 * 1024;
@@ -694,7 +732,7 @@ constexpr size_t kResidentSmemMax = 227 * 1024;
 template <typename T, bool MIXED, bool WARP>
 static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st) {
     const int groups = WARP ? 4 : 1;
-    const size_t smem = groups * (resident_slot_bytes<T>() + resident_smem_bytes(a.n_fine, a.n0, MIXED));
+    const size_t smem = groups * (resident_slot_bytes<T>() + resident_smem_bytes(a.n_fine, a.n0, MIXED, WARP));
     if (smem > kResidentSmemMax) return false;
     const int threads = WARP ? 32 * groups : (a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128));
     int per_sm = 0;
@@ -732,6 +770,7 @@ void resident_init_attributes() {
 bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double* d_K,
                          const fm_solve_params& prm, double* qf, double* qc, double* p_out,
                          int32_t* status, cudaStream_t st) {
+    if (n0 & (n0 - 1)) return false;   // power-of-two hierarchies only (shift-and-mask indexing)
     ResidentArgs a;
     a.n_fine = n_fine;
     a.n0 = n0;
