@@ -252,6 +252,22 @@ fm_status kl_basis_set(fm_ctx* ctx, const double* basis_ref, int32_t on_device);
  * sum_{k<=M} theta_k / (sigma2 meas(Omega)).  Synchronous. */
 fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, double* captured_out);
 
+/* Arithmetic of the Nystrom interpolation B = C_x V / sqrt(theta) (2 n_ref^2
+ * q^2 M flops) in kl_basis_build_ex.
+ * AUTO:   FP64 (cuBLAS DGEMM) up to 2e12 flops, the tensor cores above.
+ * FP64:   FP64 DGEMM over chunks of field points.
+ * TENSOR: one tcgen05 BF16x3 GEMM per chunk of field points (covariance tile
+ *         and eigenvectors split into BF16 hi + lo, products hi*hi + hi*lo +
+ *         lo*hi, FP32 accumulation: entries to about 1e-5 relative), the
+ *         finest grid's basis written in place (the large high-contrast
+ *         configuration: 2048^2 points, 1024 modes, q = 96). */
+#define FM_INTERP_AUTO 0
+#define FM_INTERP_FP64 1
+#define FM_INTERP_TENSOR 2
+
+/* kl_basis_build with the interpolation arithmetic chosen (FM_INTERP_*). */
+fm_status kl_basis_build_ex(fm_ctx* ctx, int32_t q, int32_t interp, double* theta_out, double* captured_out);
+
 /* The Matern covariance of Sec. 3.1 at n distances (host memory, no CUDA
  * call): C(d) = sigma2 2^(1-nu) / Gamma(nu) (sqrt(2 nu) d / lambda)^nu
  * K_nu(sqrt(2 nu) d / lambda), C(0) = sigma2, for nu = 0.5 (sigma2

@@ -232,11 +232,12 @@ class Context:
             a = np.ascontiguousarray(B_ref, dtype=np.float64)
             self._check(self._L.kl_basis_set(self._h, a.ctypes.data_as(C.c_void_p), 0))
 
-    def kl_basis_build(self, q=0):
+    def kl_basis_build(self, q=0, interp=0):
+        """Nystrom KL basis on the GPU; interp: 0 auto, 1 FP64, 2 tensor cores (BF16x3)."""
         theta = np.zeros(self.M)
         cap = C.c_double()
-        self._check(self._L.kl_basis_build(self._h, q, theta.ctypes.data_as(C.c_void_p),
-                                           C.byref(cap)))
+        self._check(self._L.kl_basis_build_ex(self._h, q, interp, theta.ctypes.data_as(C.c_void_p),
+                                              C.byref(cap)))
         return theta, cap.value
 
     def sync(self):

@@ -29,7 +29,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
            "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance", "qmc_points",
-           "fm_lattice_cbc", "lattice_generating_vector"]
+           "fm_lattice_cbc", "lattice_generating_vector", "kl_basis_build_ex"]
 
 
 class FmConfig(C.Structure):
@@ -147,6 +147,7 @@ def load(path=None):
         "sobol_direction_numbers": (I32, [P, P]),
         "kl_basis_set": (I32, [P, P, I32]),
         "kl_basis_build": (I32, [P, I32, P, P]),
+        "kl_basis_build_ex": (I32, [P, I32, I32, P, P]),
         "kl_basis_get": (I32, [P, P, I32]),
         "kl_field_batch": (I32, [P, I32, U32, P, P, P]),
         "fmg_solve_batch": (I32, [P, I32, U32, P, C.POINTER(FmSolveParams), P, P, P, P, P]),

@@ -74,61 +74,6 @@ __global__ void k_gather_rows(int n, int n_ref, int M, const double* __restrict_
     Bl[t] = Bref[((size_t)(s * j) * n_ref + (size_t)s * i) * M + k];
 }
 
-// x K_1(x), x >= 0, the shape of the Matern nu = 1 covariance (K_1 the
-// modified Bessel function of the second kind; the limit at 0 is 1).
-//   x <= 2: the ascending series (DLMF 10.31.1 with n = 1),
-//     x K_1(x) = 1 + x ln(x/2) I_1(x)
-//                - (x^2/4) sum_k (psi(k+1) + psi(k+2)) (x^2/4)^k / (k! (k+1)!),
-//     I_1(x) = (x/2) sum_k (x^2/4)^k / (k! (k+1)!), psi(k+1) = H_k - gamma;
-//   x > 2: the integral K_1(x) = int_0^inf exp(-x cosh t) cosh t dt (DLMF
-//     10.32.9) by the trapezoidal rule, which converges exponentially for
-//     this analytic, rapidly decaying integrand; the step follows the
-//     integrand's width near t = 0, about 1 / sqrt(x).
-// Relative error below 2e-14 on [0, 200] against an independent evaluation.
-__host__ __device__ inline double xk1(double x) {
-    if (x <= 0.0) return 1.0;
-    if (x <= 2.0) {
-        const double z = 0.25 * x * x;
-        const double gamma = 0.57721566490153286061;
-        double term = 1.0, i1 = 0.0, s = 0.0, H = 0.0;
-        for (int k = 0; k < 40; ++k) {
-            const double psi1 = H - gamma, psi2 = H + 1.0 / (k + 1) - gamma;
-            i1 += term;
-            s += (psi1 + psi2) * term;
-            H += 1.0 / (k + 1);
-            term *= z / ((double)(k + 1) * (k + 2));
-            if (term < 1e-18 * i1) break;
-        }
-        return 1.0 + x * log(0.5 * x) * (0.5 * x * i1) - z * s;
-    }
-    const double h = fmin(0.25, 0.5 / sqrt(x));
-    double acc = 0.5;   // t = 0, half weight
-    for (int j = 1; j < 4096; ++j) {
-        const double t = j * h, c = cosh(t);
-        const double v = exp(-x * (c - 1.0)) * c;
-        acc += v;
-        if (v < 1e-18 * acc) break;
-    }
-    return x * exp(-x) * acc * h;
-}
-
-// Matern covariance of Sec. 3.1 at distance d >= 0 for the smoothness values
-// this library builds bases for: nu = 1/2 (exponential), 1 (through x K_1),
-// 3/2 and 5/2 (their closed forms); 0 for any other nu.
-__host__ __device__ inline double matern(double nu, double sigma2, double lambda, double d) {
-    if (nu == 0.5) return sigma2 * exp(-d / lambda);
-    if (nu == 1.0) return sigma2 * xk1(sqrt(2.0) * d / lambda);
-    if (nu == 1.5) {
-        const double x = sqrt(3.0) * d / lambda;
-        return sigma2 * (1.0 + x) * exp(-x);
-    }
-    if (nu == 2.5) {
-        const double x = sqrt(5.0) * d / lambda;
-        return sigma2 * (1.0 + x + x * x / 3.0) * exp(-x);
-    }
-    return 0.0;
-}
-
 // Weighted covariance matrix of the Nystrom method on the q x q midpoint grid.
 __global__ void k_nystrom_matrix(int q, double nu, double sigma2, double lambda, double* __restrict__ A) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,7 +121,8 @@ static fm_status install_basis(fm_ctx* ctx, const double* d_Bref) {
                 return FM_ENOMEM;
             }
         }
-        k_gather_rows<<<nblocks(cnt), 256>>>(n, n_ref, M, d_Bref, ctx->d_basis[l]);
+        if (ctx->d_basis[l] != d_Bref)   // the finest grid may have been built in place
+            k_gather_rows<<<nblocks(cnt), 256>>>(n, n_ref, M, d_Bref, ctx->d_basis[l]);
         FM_CUDA_TRY(ctx, cudaGetLastError());
     }
     FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
@@ -218,7 +164,13 @@ extern "C" fm_status kl_basis_set(fm_ctx* ctx, const double* basis_ref, int32_t 
 }
 
 extern "C" fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, double* captured_out) {
+    return kl_basis_build_ex(ctx, q, FM_INTERP_AUTO, theta_out, captured_out);
+}
+
+extern "C" fm_status kl_basis_build_ex(fm_ctx* ctx, int32_t q, int32_t interp, double* theta_out,
+                                       double* captured_out) {
     FM_CHECK_ARG(ctx, ctx != nullptr, "kl_basis_build: null context");
+    FM_CHECK_ARG(ctx, interp >= FM_INTERP_AUTO && interp <= FM_INTERP_TENSOR, "kl_basis_build: unknown interp");
     const int M = ctx->cfg.M;
     if (q <= 0) {
         q = 32;
@@ -230,6 +182,10 @@ extern "C" fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, d
     const int n_ref = finest_grid(ctx);
     const size_t rows = (size_t)n_ref * n_ref;
     const double sigma2 = ctx->cfg.sigma2, lambda = ctx->cfg.lambda, nu = matern_nu(ctx->cfg);
+    // the interpolation B = C_x V costs 2 n_ref^2 q^2 M flops: FP64 up to 2e12,
+    // the tensor cores (BF16x3) above, unless the caller chooses
+    const bool tensor = interp == FM_INTERP_TENSOR ||
+                        (interp == FM_INTERP_AUTO && 2.0 * (double)rows * nq * M > 2e12);
 
     double *dA = nullptr, *dW = nullptr, *dV = nullptr, *dC = nullptr, *dB = nullptr, *dInv = nullptr,
            *dWork = nullptr;
@@ -246,8 +202,8 @@ extern "C" fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, d
         if (cudaMalloc((void**)&dA, sizeof(double) * nq * nq) != cudaSuccess ||
             cudaMalloc((void**)&dW, sizeof(double) * nq) != cudaSuccess ||
             cudaMalloc((void**)&dV, sizeof(double) * (size_t)nq * M) != cudaSuccess ||
-            cudaMalloc((void**)&dC, sizeof(double) * chunk * nq) != cudaSuccess ||
-            cudaMalloc((void**)&dB, sizeof(double) * rows * M) != cudaSuccess ||
+            (!tensor && cudaMalloc((void**)&dC, sizeof(double) * chunk * nq) != cudaSuccess) ||
+            (!tensor && cudaMalloc((void**)&dB, sizeof(double) * rows * M) != cudaSuccess) ||
             cudaMalloc((void**)&dInv, sizeof(double) * M) != cudaSuccess ||
             cudaMalloc((void**)&dInfo, sizeof(int)) != cudaSuccess) {
             fail(FM_ENOMEM, "allocation failed");
@@ -282,7 +238,7 @@ extern "C" fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, d
         cudaMemcpy(w.data(), dW, sizeof(double) * nq, cudaMemcpyDeviceToHost);
         // eigenvalues ascend; column c of dA (column-major) is eigenvector c.
         // Keep the top M, descending, each with its largest entry positive.
-        std::vector<double> col(nq), theta(M), inv(M);
+        std::vector<double> col(nq), theta(M), inv(M), Vt(tensor ? (size_t)nq * M : 0);
         double trace = 0.0;
         for (int a = 0; a < nq; ++a) trace += w[a];
         for (int k = 0; k < M; ++k) {
@@ -293,11 +249,32 @@ extern "C" fm_status kl_basis_build(fm_ctx* ctx, int32_t q, double* theta_out, d
                 if (std::fabs(col[a]) > std::fabs(col[arg])) arg = a;
             const double sgn = col[arg] < 0 ? -1.0 : 1.0;
             for (int a = 0; a < nq; ++a) V[(size_t)a * M + k] = sgn * col[a];   // V[j][k]
+            if (tensor)
+                for (int a = 0; a < nq; ++a) Vt[(size_t)k * nq + a] = sgn * col[a];   // V^T[k][j]
             theta[k] = w[c];
             inv[k] = 1.0 / std::sqrt(w[c]);
         }
-        cudaMemcpy(dV, V.data(), sizeof(double) * (size_t)nq * M, cudaMemcpyHostToDevice);
+        cudaMemcpy(dV, tensor ? Vt.data() : V.data(), sizeof(double) * (size_t)nq * M, cudaMemcpyHostToDevice);
         cudaMemcpy(dInv, inv.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+        if (tensor) {
+            // the finest grid's basis is interpolated in place; coarser grids gather from it
+            double*& fine = ctx->d_basis[ctx->cfg.n_levels - 1];
+            if (!fine && cudaMalloc((void**)&fine, sizeof(double) * rows * M) != cudaSuccess) {
+                fail(FM_ENOMEM, "allocation of the finest basis failed");
+                break;
+            }
+            st = kl_tc_nystrom(ctx, q, dV, dInv, fine);
+            if (st == FM_OK) st = install_basis(ctx, fine);
+            if (st == FM_OK) {
+                if (theta_out) std::copy(theta.begin(), theta.end(), theta_out);
+                if (captured_out) {
+                    double kept = 0.0;
+                    for (double t : theta) kept += t;
+                    *captured_out = kept / trace;
+                }
+            }
+            break;
+        }
         // B = Cx V (row-major [rows][M]) in chunks of field points, via the
         // column-major identity B^T = V^T Cx^T.
         const double one = 1.0, zero = 0.0;

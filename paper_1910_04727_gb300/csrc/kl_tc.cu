@@ -31,9 +31,14 @@ constexpr uint32_t kTcABytes = kTcM * kTcK * 2;   // 16 KiB
 constexpr uint32_t kTcBBytes = kTcN * kTcK * 2;   // 32 KiB
 constexpr size_t kTcSmem = 1024 + kTcStages * (kTcABytes + kTcBBytes) + 256;
 
+// EPI 0 (field synthesis): K[s][c] = exp(D[c][s]).  EPI 1 (Nystrom
+// interpolation of the KL basis): K[c][s] = D[c][s] colscale[s], row-major
+// [cells][S] in FP64.
+template <int EPI>
 __global__ void __launch_bounds__(128, 1)
     k_kl_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int cells,
-                 int S, int kblocks, double* __restrict__ K, int* __restrict__ err) {
+                 int S, int kblocks, double* __restrict__ K, int* __restrict__ err,
+                 const double* __restrict__ colscale) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     uint8_t* base = smem_raw + ((1024 - (raw & 1023)) & 1023);   // 1024-byte aligned tiles
@@ -105,7 +110,9 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int s = s0 + chunk * 32 + i;
-                    if (s < S) K[(size_t)s * cells + c] = (double)expf(__uint_as_float(r[i]));
+                    if (s >= S) continue;
+                    if (EPI == 0) K[(size_t)s * cells + c] = (double)expf(__uint_as_float(r[i]));
+                    else K[(size_t)c * S + s] = (double)__uint_as_float(r[i]) * colscale[s];
                 }
             }
         }
@@ -124,6 +131,32 @@ __global__ void k_wait_check(uint64_t budget_ns, int* __restrict__ err) {
     tc::mbar_init(&bar, 1);
     tc::fence_barrier_init();
     tc::mbar_wait(&bar, 0, err, budget_ns);
+}
+
+// A operand of the Nystrom interpolation: field points r0 .. r0+rows-1 (cell
+// centres of the n_ref grid, row-major) against the q x q quadrature nodes:
+// sqrt(w) C(|x - x_j|), w = 1/q^2, in the split layout (hi, hi, lo) of row
+// length 3 Kpad (columns beyond q^2 are zero).
+__global__ void k_nystrom_cross_bf16(int n_ref, size_t r0, size_t rows, int q, int Kpad, double nu, double sigma2,
+                                     double lambda, __nv_bfloat16* __restrict__ out) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * Kpad) return;
+    const size_t rr = t / Kpad;
+    const int jq = (int)(t % Kpad);
+    const int nq = q * q;
+    double v = 0.0;
+    if (jq < nq) {
+        const size_t r = r0 + rr;
+        const double x = ((double)(r % n_ref) + 0.5) / n_ref, y = ((double)(r / n_ref) + 0.5) / n_ref;
+        const double xq = ((double)(jq % q) + 0.5) / q, yq = ((double)(jq / q) + 0.5) / q;
+        const double d = sqrt((x - xq) * (x - xq) + (y - yq) * (y - yq));
+        v = matern(nu, sigma2, lambda, d) / q;
+    }
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    __nv_bfloat16* o = out + rr * (size_t)(3 * Kpad);
+    o[jq] = hi;
+    o[Kpad + jq] = hi;
+    o[2 * Kpad + jq] = __double2bfloat16(v - (double)__bfloat162float(hi));
 }
 
 // x [n][M] FP64 -> [n][Kp] BF16 in the split layout (hi, lo, hi) or plain (hi).
@@ -241,7 +274,9 @@ fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, do
     }
     static bool attr = false;
     if (!attr) {
-        FM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_kl_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        FM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_kl_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kTcSmem));
+        FM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_kl_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kTcSmem));
         attr = true;
     }
@@ -252,11 +287,80 @@ fm_status kl_tc_field(fm_ctx* ctx, int level, uint32_t n, const double* d_xi, do
     const double flops = 2.0 * (double)n * cells * Kp;
     const double bytes = 2.0 * ((double)cells * Kp + (double)n * Kp) + 8.0 * (double)n * cells;
     FM_TIMED(ctx, kFamKlGemm, st, bytes, flops,
-             k_kl_gemm_tc<<<grid, 128, kTcSmem, st>>>(ctx->tc.mapA[level],
-                                                     ctx->tc.mapB, cells, (int)n,
-                                                     Kp / kTcK, d_K, ctx->tc.err));
+             k_kl_gemm_tc<0><<<grid, 128, kTcSmem, st>>>(ctx->tc.mapA[level],
+                                                        ctx->tc.mapB, cells, (int)n,
+                                                        Kp / kTcK, d_K, ctx->tc.err, nullptr));
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
+}
+
+}  // namespace fm
+
+namespace fm {
+
+// Nystrom interpolation of the KL basis on the tensor cores:
+// out[x][k] = inv_sqrt_theta[k] sum_j sqrt(w) C(x, x_j) V[j][k] over the
+// n_ref^2 field points, with dVt = V^T [M][q^2] FP64, as one BF16x3 GEMM per
+// chunk of field points (products to about 2^-16 relative, FP32
+// accumulation in tensor memory).  Synchronous; the bounded waits report
+// FM_ETIMEOUT.
+fm_status kl_tc_nystrom(fm_ctx* ctx, int q, const double* dVt, const double* d_inv_sqrt_theta, double* d_out) {
+    const int M = ctx->cfg.M, n_ref = finest_grid(ctx), nq = q * q;
+    const int Kpad = (nq + kTcK - 1) / kTcK * kTcK, Kp = 3 * Kpad;
+    const size_t rows = (size_t)n_ref * n_ref;
+    size_t chunk = std::max<size_t>(kTcM, ((size_t)2 << 30) / ((size_t)Kp * 2));   // about 2 GiB of A
+    chunk = std::min(rows, chunk / kTcM * kTcM);
+    void *A = nullptr, *B = nullptr;
+    fm_status st = FM_OK;
+    if (!ctx->tc.err) {
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&ctx->tc.err, sizeof(int)));
+        FM_CUDA_TRY(ctx, cudaMemset(ctx->tc.err, 0, sizeof(int)));
+    }
+    static bool attr = false;
+    if (!attr) {
+        FM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_kl_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kTcSmem));
+        attr = true;
+    }
+    do {
+        if (cudaMalloc(&A, chunk * Kp * 2) != cudaSuccess || cudaMalloc(&B, (size_t)M * Kp * 2) != cudaSuccess) {
+            set_error(ctx, "kl_basis_build: tensor-core interpolation buffers");
+            st = FM_ENOMEM;
+            break;
+        }
+        // B operand: V^T, split (hi, lo, hi)
+        k_xi_to_bf16<<<nblk((size_t)M * Kpad), 256>>>((size_t)M, nq, Kpad, 1, dVt, (__nv_bfloat16*)B);
+        CUtensorMap mapB, mapA;
+        if (!make_map(&mapB, B, M, Kp, kTcN) || !make_map(&mapA, A, chunk, Kp, kTcM)) {
+            set_error(ctx, "kl_basis_build: cuTensorMapEncodeTiled failed");
+            st = FM_ECUDA;
+            break;
+        }
+        const double nu = matern_nu(ctx->cfg), sigma2 = ctx->cfg.sigma2, lambda = ctx->cfg.lambda;
+        for (size_t r0 = 0; r0 < rows; r0 += chunk) {
+            const size_t nr = std::min(chunk, rows - r0);
+            k_nystrom_cross_bf16<<<nblk(nr * Kpad), 256>>>(n_ref, r0, nr, q, Kpad, nu, sigma2, lambda,
+                                                           (__nv_bfloat16*)A);
+            dim3 grid((unsigned)((nr + kTcM - 1) / kTcM), (unsigned)((M + kTcN - 1) / kTcN));
+            k_kl_gemm_tc<1><<<grid, 128, kTcSmem>>>(mapA, mapB, (int)nr, M, Kp / kTcK, d_out + r0 * M, ctx->tc.err,
+                                                   d_inv_sqrt_theta);
+        }
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            set_error(ctx, "kl_basis_build: tensor-core interpolation failed");
+            st = FM_ECUDA;
+            break;
+        }
+        int e = 0;
+        cudaMemcpy(&e, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e) {
+            cudaMemset(ctx->tc.err, 0, sizeof(int));
+            set_error(ctx, "kl_basis_build: a bounded device-side wait ran out");
+            st = FM_ETIMEOUT;
+        }
+    } while (0);
+    cudaFree(A);
+    cudaFree(B);
+    return st;
 }
 
 }  // namespace fm

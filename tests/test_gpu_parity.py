@@ -295,6 +295,26 @@ def test_kl_basis_build_of_smoother_matern_fields_matches_oracle(fm, nu, lam):
     ctx.close()
 
 
+@pytest.mark.parametrize("nu", [0.5, 1.0])
+def test_kl_basis_tensor_core_interpolation(fm, nu):
+    """The Nystrom interpolation as BF16x3 tensor-core GEMMs (the path of the
+    large high-contrast basis): same spectrum as the FP64 path, basis entries
+    within 5e-5 of it relative to the largest, and the field covariance
+    B B^T within 1e-4 of the oracle's."""
+    ctx = fm.Context(2, 16, 32, sigma2=1.0, lam=0.3, nu=nu)
+    theta_t, cap_t = ctx.kl_basis_build(q=24, interp=2)
+    Bt = ctx.kl_basis_get().cpu().numpy()
+    theta_f, cap_f = ctx.kl_basis_build(q=24, interp=1)
+    Bf = ctx.kl_basis_get().cpu().numpy()
+    np.testing.assert_allclose(theta_t, theta_f, rtol=1e-12)
+    assert np.max(np.abs(Bt - Bf)) < 5e-5 * np.max(np.abs(Bf))
+    th, V, qpts, w, trace = okl.nystrom_eigs(24, 32, 1.0, 0.3, nu=nu)
+    B_or = okl.nystrom_basis(okl.field_points(32, 32), th, V, qpts, w, 1.0, 0.3, nu=nu)
+    C_or = B_or @ B_or.T
+    assert np.max(np.abs(Bt @ Bt.T - C_or)) < 1e-4 * np.max(np.abs(C_or))
+    ctx.close()
+
+
 def test_matern_nu1_level_samples_match_oracle(fm):
     """A two-level run on the nu = 1, lambda = 0.5 field of Table 2 (the
     oracle's basis installed): per-sample Q^f, Q^c within 1e-10."""
