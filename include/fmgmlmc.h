@@ -101,6 +101,9 @@ typedef struct {
     int32_t qmc_rule;     /* randomized QMC points of the MLQMC estimator (FM_QMC_*) */
     int32_t lattice_m;    /* FM_QMC_LATTICE: the sequence holds 2^lattice_m points (5 .. 24;
                              0 is read as 16) */
+    int32_t ir_cycles;    /* converged stages: V-cycles between residual tests (0: nu0) */
+    int32_t energy_step;  /* 1: the energy-optimal correction step in every solve (see
+                             fm_solve_params; the level-wise schedule) */
 } fm_config;
 
 /* Randomized QMC rules (Sec. 2.4).
@@ -154,6 +157,8 @@ typedef struct {
                              raises the energy error (robust at high contrast) */
     int32_t bc_case;      /* FM_CASE_II (0 is read as Case II) or FM_CASE_I */
     double pS, pN;        /* Case I: Dirichlet data on the south / north edges */
+    int32_t ir_cycles;    /* converged mode: V-cycles between residual tests (in the mixed form:
+                             FP32 V-cycles per FP64 residual); 0: nu0 */
 } fm_solve_params;
 
 /* ---------------------------------------------------------------- context */

@@ -145,15 +145,19 @@ class Context:
     def __init__(self, n_levels, n_level0, M, sigma2=1.0, lam=0.3, pW=1.0, pE=0.0, nu0=2, nu1=2,
                  nu2=2, n_coarsest=4, n_shifts=16, seed=1910047270, max_batch=0,
                  precision=FM_PREC_FP64, converged=False, tol=1e-10, qtol=0.0, max_cycles=100,
-                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0, nu=0.5, qmc_rule=0, lattice_m=0):
+                 kl_mode=0, bc_case=_lib.FM_CASE_II, pS=0.0, pN=0.0, nu=0.5, qmc_rule=0, lattice_m=0,
+                 ir_cycles=0, energy_step=False):
         """bc_case: Table 1's FM_CASE_II (no flow north / south, east outflux) or
         FM_CASE_I (Dirichlet pW, pE, pS, pN on all four edges, QoI u(0.5, 0.5)).
         nu: Matern smoothness of the field (0.5, 1, 1.5 or 2.5).
-        qmc_rule: FM_QMC_SOBOL_SHIFT, FM_QMC_SOBOL_OWEN or FM_QMC_LATTICE (2^lattice_m points)."""
+        qmc_rule: FM_QMC_SOBOL_SHIFT, FM_QMC_SOBOL_OWEN or FM_QMC_LATTICE (2^lattice_m points).
+        ir_cycles: V-cycles between residual tests of converged stages (0: nu0).
+        energy_step: the energy-optimal coarse-grid correction step in every solve."""
         self._L = _lib.load()
         cfg = _lib.FmConfig(n_levels, n_level0, n_coarsest, M, sigma2, lam, pW, pE, nu0, nu1, nu2,
                             precision, int(bool(converged)), tol, qtol, max_cycles, kl_mode, n_shifts,
-                            seed, max_batch, bc_case, pS, pN, nu, qmc_rule, lattice_m)
+                            seed, max_batch, bc_case, pS, pN, nu, qmc_rule, lattice_m, ir_cycles,
+                            int(bool(energy_step)))
         h = C.c_void_p()
         st = self._L.fm_create(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -269,8 +273,8 @@ class Context:
     def solve_params(self, **over):
         c = self.cfg
         p = _lib.FmSolveParams(c.pW, c.pE, c.n_coarsest, c.nu0, c.nu1, c.nu2, c.precision,
-                               _lib.FM_KERNEL_AUTO, c.converged, c.tol, c.qtol, c.max_cycles, 0,
-                               c.bc_case, c.pS, c.pN)
+                               _lib.FM_KERNEL_AUTO, c.converged, c.tol, c.qtol, c.max_cycles, c.energy_step,
+                               c.bc_case, c.pS, c.pN, c.ir_cycles)
         for k, v in over.items():
             setattr(p, k, v)
         return p

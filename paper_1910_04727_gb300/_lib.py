@@ -41,7 +41,8 @@ class FmConfig(C.Structure):
                 ("kl_mode", C.c_int32),
                 ("n_shifts", C.c_int32), ("seed", C.c_uint64), ("max_batch", C.c_int64),
                 ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double), ("nu", C.c_double),
-                ("qmc_rule", C.c_int32), ("lattice_m", C.c_int32)]
+                ("qmc_rule", C.c_int32), ("lattice_m", C.c_int32), ("ir_cycles", C.c_int32),
+                ("energy_step", C.c_int32)]
 
 
 class FmSolveParams(C.Structure):
@@ -49,7 +50,8 @@ class FmSolveParams(C.Structure):
                 ("nu0", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("converged", C.c_int32),
                 ("tol", C.c_double), ("qtol", C.c_double), ("max_cycles", C.c_int32),
-                ("energy_step", C.c_int32), ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double)]
+                ("energy_step", C.c_int32), ("bc_case", C.c_int32), ("pS", C.c_double), ("pN", C.c_double),
+                ("ir_cycles", C.c_int32)]
 
 
 class FmLevelSums(C.Structure):

@@ -45,6 +45,9 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
                  "fm_create: unknown qmc_rule");
     FM_CHECK_ARG(nullptr, cfg->lattice_m == 0 || (cfg->lattice_m >= 5 && cfg->lattice_m <= 24),
                  "fm_create: lattice_m must be 5 .. 24");
+    FM_CHECK_ARG(nullptr, cfg->ir_cycles >= 0 && cfg->ir_cycles <= 64, "fm_create: ir_cycles must be 0 .. 64");
+    FM_CHECK_ARG(nullptr, !cfg->energy_step || cfg->converged,
+                 "fm_create: the energy-optimal step runs in converged mode");
     fm_ctx* ctx = new (std::nothrow) fm_ctx();
     if (!ctx) {
         set_error(nullptr, "fm_create: host allocation failed");

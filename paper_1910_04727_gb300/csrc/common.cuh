@@ -79,6 +79,9 @@ struct Ghost {
     int ns;
 };
 
+// V-cycles between residual tests of a converged stage.
+inline int cycles_per_test(const fm_solve_params& prm) { return prm.ir_cycles > 0 ? prm.ir_cycles : prm.nu0; }
+
 inline Bnd bnd_of(const fm_solve_params& prm) {
     Bnd b;
     b.ns = prm.bc_case == FM_CASE_I ? 1 : 0;

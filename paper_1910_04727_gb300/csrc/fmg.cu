@@ -1513,7 +1513,7 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     cudaStream_t bs = ctx->body_stream;
     FM_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
-    for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, bs);
+    for (int v = 0; v < cycles_per_test(prm); ++v) vcycle(H, k, k, prm, H.active, bs);
     if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active, nullptr);
     test(bs);
     cudaGraph_t body = nullptr;
@@ -1546,7 +1546,7 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
             if (status) k_status<<<blocks_for(S), kBlock, 0, st>>>(S, H.active, status);
             break;
         }
-        for (int v = 0; v < prm.nu0; ++v) vcycle(H, k, k, prm, H.active, st);
+        for (int v = 0; v < cycles_per_test(prm); ++v) vcycle(H, k, k, prm, H.active, st);
         if (mixed)
             k_ir_update<T><<<blocks_for((H.listed() ? H.busy : S) * cells), kBlock, 0, st>>>(
                 cells, H.listed() ? H.busy : S, g.p, g.p64, H.active, H.listed() ? H.order : nullptr);
@@ -1705,6 +1705,7 @@ fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const d
     FM_CHECK_ARG(ctx, S == 0 || (d_K && d_qf), "fmg_solve_batch: null input or output");
     FM_CHECK_ARG(ctx, prm.kernel >= FM_KERNEL_AUTO && prm.kernel <= FM_KERNEL_RESIDENT,
                  "fmg_solve_batch: unknown kernel schedule");
+    FM_CHECK_ARG(ctx, prm.ir_cycles >= 0 && prm.ir_cycles <= 64, "fmg_solve_batch: ir_cycles must be 0 .. 64");
     FM_CHECK_ARG(ctx, prm.bc_case == 0 || prm.bc_case == FM_CASE_I || prm.bc_case == FM_CASE_II,
                  "fmg_solve_batch: bc_case must be FM_CASE_I or FM_CASE_II");
     FM_CHECK_ARG(ctx, !prm.energy_step || (prm.converged && prm.kernel != FM_KERNEL_RESIDENT),

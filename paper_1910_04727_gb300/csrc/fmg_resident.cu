@@ -179,22 +179,17 @@ static __device__ void resident_setup_grid(const RGrid<T>& g, const HGrid* h, co
 
 // Reciprocal diagonal of grid n from its stored faces, once every face of the
 // grid is in place (each face is formed once: the west face of a cell is its
-// west neighbour's east face, the same harmonic mean of the same two values).
-// With an FP64 copy h the sum and reciprocal are taken in FP64.
-static __device__ void resident_setup_diag(const RGrid<T>& g, const HGrid* h) {
+// west neighbour's east face, the same harmonic mean of the same two values),
+// in the arithmetic of the V-cycles that use it (FP32 in the mixed form, also
+// on the refined grids whose FP64 faces serve the residual only).
+static __device__ void resident_setup_diag(const RGrid<T>& g) {
     if (!g.dinv) return;
     const int n = g.n;
     for (int c = rank(); c < n * n; c += size()) {
         const int i = c & (n - 1), j = c >> g.lg;
-        if (h) {
-            const double tw = (i > 0) ? h->te[c - 1] : h->tw[j];
-            const double ts = (j > 0) ? h->tn[c - n] : h->ts[i];
-            g.dinv[c] = (T)(1.0 / (tw + h->te[c] + ts + h->tn[c]));
-        } else {
-            const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
-            const T ts = (j > 0) ? g.tn[c - n] : g.ts[i];
-            g.dinv[c] = T(1) / (tw + g.te[c] + ts + g.tn[c]);
-        }
+        const T tw = (i > 0) ? g.te[c - 1] : g.tw[j];
+        const T ts = (j > 0) ? g.tn[c - n] : g.ts[i];
+        g.dinv[c] = T(1) / (tw + g.te[c] + ts + g.tn[c]);
     }
 }
 
@@ -227,7 +222,7 @@ static __device__ void resident_setup_correction(const RGrid<T>& g, const double
         if (j == 0) g.ts[i] = tb;
     }
     sync();
-    resident_setup_diag(g, nullptr);
+    resident_setup_diag(g);
     sync();
 }
 
@@ -534,6 +529,7 @@ struct ResidentArgs {
     const double* K;
     Ghost<double> bd;   // boundary data (Table 1)
     int nu0, nu1, nu2;
+    int ir;   // V-cycles between residual tests of a converged stage
     int converged, max_cycles;
     double tol, qtol;
     double *qf, *qc, *p_out;
@@ -598,10 +594,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             R::resident_setup_grid(L.g[k], h, Kf, a.n_fine, a.bd.ns);
         }
         R::sync();
-        for (int k = 0; k <= m; ++k) {
-            const HGrid* h = (MIXED && k >= m - 1) ? &L.h[k - (m - 1)] : nullptr;
-            R::resident_setup_diag(L.g[k], h);
-        }
+        for (int k = 0; k <= m; ++k) R::resident_setup_diag(L.g[k]);
         R::sync();
         R::resident_coarse_inverse(L.g[0], L.ainv, L.work);
         bool ok = true;
@@ -651,9 +644,9 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, td);
-                    work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2);
-                    model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
+                    for (int v = 0; v < a.ir; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, td);
+                    work += a.ir * vcycle_flops(a.n0, k, a.nu1, a.nu2);
+                    model += a.ir * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                 }
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
@@ -677,11 +670,11 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                         ok = false;
                         break;
                     }
-                    // nu0 FP32 V-cycles on the correction equation per FP64 residual
-                    for (int v = 0; v < a.nu0; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, t0);
-                    work += a.nu0 * vcycle_flops(a.n0, k, a.nu1, a.nu2) + (double)h.n * h.n;
+                    // ir FP32 V-cycles on the correction equation per FP64 residual
+                    for (int v = 0; v < a.ir; ++v) R::resident_vcycle(L, k, a.nu1, a.nu2, t0);
+                    work += a.ir * vcycle_flops(a.n0, k, a.nu1, a.nu2) + (double)h.n * h.n;
                     work64 += (double)h.n * h.n;
-                    model += a.nu0 * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
+                    model += a.ir * vcycle_bytes(a.n0, k, a.nu1, a.nu2, ts);
                     for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] += (double)g.p[c];
                     R::sync();
                 }
@@ -781,6 +774,7 @@ bool fmg_resident_launch(fm_ctx* ctx, int n_fine, int n0, size_t S, const double
     a.nu0 = prm.nu0;
     a.nu1 = prm.nu1;
     a.nu2 = prm.nu2;
+    a.ir = cycles_per_test(prm);
     a.converged = prm.converged;
     a.max_cycles = prm.max_cycles;
     a.tol = prm.tol;

@@ -112,6 +112,8 @@ fm_solve_params solve_params(const fm_ctx* ctx) {
     p.qtol = ctx->cfg.qtol;
     p.max_cycles = ctx->cfg.max_cycles;
     p.bc_case = ctx->cfg.bc_case;
+    p.ir_cycles = ctx->cfg.ir_cycles;
+    p.energy_step = ctx->cfg.energy_step;
     p.pS = ctx->cfg.pS;
     p.pN = ctx->cfg.pN;
     return p;

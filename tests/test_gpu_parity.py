@@ -156,6 +156,22 @@ def test_fmg_solve_matches_oracle(small, n, S, kernel):
     np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=1e-11)
 
 
+@pytest.mark.parametrize("kernel", [LEVELWISE, RESIDENT])
+@pytest.mark.parametrize("ir", [1, 3, 4])
+def test_cycles_between_residual_tests_keep_the_converged_result(fm, kernel, ir):
+    """ir_cycles FP32 V-cycles per FP64 residual test (instead of nu0 = 2):
+    a different path to the same converged QoIs, within the mixed bar."""
+    ctx = fm.Context(2, 16, 8, precision=1, converged=True, tol=1e-12, qtol=1e-10, max_cycles=200,
+                     ir_cycles=ir)
+    for n, S in [(16, 40), (64, 7)]:
+        K = W.smooth_lognormal_field(n, S=S, tag=880 + n)
+        qf, qc, _ = ctx.fmg_solve_batch(torch.tensor(K, device="cuda"), kernel=kernel)
+        rf, rc, _, _ = OL.fmg_solve_batch(K, OL.params(converged=True, tol=1e-13, max_cycles=300))
+        assert _rel(qf.cpu().numpy(), rf) < 1e-8
+        assert _rel(qc.cpu().numpy(), rc) < 1e-8
+    ctx.close()
+
+
 def test_resident_schedule_rejects_grids_beyond_shared_memory(fm, small):
     ctx, _ = small
     K = torch.ones((2, 128, 128), dtype=torch.float64, device="cuda")

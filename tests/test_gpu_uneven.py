@@ -183,3 +183,23 @@ def test_full_size_uneven_batch_sampled_against_oracle():
         errs.append((K.shape[-1], _rel(qf.cpu().numpy()[:1], of), _rel(qc.cpu().numpy()[:1], oc)))
     print("outflux error against the converged oracle:", errs)
     assert all(ef < 1e-8 and ec < 1e-8 for _, ef, ec in errs)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_energy_step_in_the_graph_equals_per_group_solves(ctx, precision):
+    """The energy-optimal correction step inside the captured graph (device
+    refinement loops, level-wise branches for every group): the same results
+    as per-group fmg_solve_batch calls, bit for bit, and within the bars of
+    the stepped oracle."""
+    Ks = [torch.tensor(W.smooth_lognormal_field(n, S=S, sigma=1.4, tag=950 + n), device="cuda")
+          for n, S in [(32, 11), (64, 6), (128, 3)]]
+    kw = dict(precision=precision, converged=1, tol=1e-12, qtol=0.0, max_cycles=300, energy_step=1)
+    outs = ctx.solve_uneven(Ks, **kw)
+    for K, (qf, qc, _) in zip(Ks, outs):
+        a, b, _ = ctx.fmg_solve_batch(K, **kw)
+        assert _same(a, qf) and _same(b, qc)
+        rf, rc, _, _ = OL.fmg_solve_batch(K.cpu().numpy(), OL.params(converged=True, tol=1e-13, max_cycles=300,
+                                                                     energy_step=True))
+        bar = 1e-10 if precision == 0 else 1e-8
+        assert _rel(qf.cpu().numpy(), rf) < bar
+        assert _rel(qc.cpu().numpy(), rc) < bar
