@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--only-chosen", action="store_true", help="skip timing the other forms")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-qmc-leg", action="store_true", help="skip timing the randomized-QMC estimator")
+    ap.add_argument("--c5-leg", action="store_true",
+                    help="also run the large high-contrast case (6 levels 64x64 .. 2048x2048, 1024 modes, "
+                         "sigma^2 = 2, lambda = 0.1, RMSE 5e-4) in the chosen form and in plain FP64")
+    ap.add_argument("--c5-steps", type=int, default=1, help="timed estimates per form in the large case")
+    ap.add_argument("--ir-cycles", type=int, default=None,
+                    help="FP32 V-cycles per FP64 residual test in the mixed forms (default: MIXED_IR_CYCLES)")
     ap.add_argument("--detail-out", default=None,
                     help="write the full record (every leg, every kernel family) to this JSON file")
     ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
@@ -251,12 +257,18 @@ def surrogate_cost(torch, ctx):
     return t_s / t_0
 
 
+# FP32 V-cycles per FP64 residual test in the mixed forms' refinement loops
+MIXED_IR_CYCLES = 2
+IR_CYCLES = [MIXED_IR_CYCLES]
+
+
 def make_ctx(fm, wl, rank, form):
     f = FORMS[form]
     return fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, pW=wl.pW,
                       pE=wl.pE, nu0=wl.nu0, nu1=wl.nu1, nu2=wl.nu2, n_coarsest=wl.n0,
                       n_shifts=wl.n_shifts, seed=wl.seed + 7919 * rank, precision=f["precision"],
-                      converged=f["converged"], tol=SOLVE_TOL, qtol=SOLVE_QTOL, max_cycles=200)
+                      converged=f["converged"], tol=SOLVE_TOL, qtol=SOLVE_QTOL, max_cycles=200,
+                      ir_cycles=IR_CYCLES[0] if f["precision"] == 1 else 0)
 
 
 # DRAM read + write of one FP32 strip call (two red-black sweeps) per cell:
@@ -404,6 +416,73 @@ def uneven_leg(torch, fm, flush):
     return out
 
 
+def c5_leg(torch, fm, flush, steps):
+    """The large high-contrast case: six levels 64x64 .. 2048x2048, Matern
+    nu = 1/2 with sigma^2 = 2 and lambda = 0.1, 1024 KL modes, RMSE 5e-4.
+    Chosen form: randomized QMC (16 shifted Sobol' point sets), the surrogate
+    level below 64x64, FP32 V-cycles in FP64 refinement, each round's solves
+    as one uneven batch, and the energy-optimal correction step (the plain
+    V-cycle diverges on some fields of this contrast).  Beside it the plain
+    FP64 form: every step in FP64, converged stages, energy step, the same
+    QMC estimator without the surrogate.  The KL basis (Nystrom, q = 96,
+    interpolated on the tensor cores) is built once, outside the timed
+    region, and handed to the second context."""
+    wl = W.WORKLOADS["contrast6"]
+    out = {"workload": wl.name, "levels": wl.levels, "kl_modes": wl.M, "sigma2": wl.sigma2, "lambda": wl.lam,
+           "eps": wl.eps, "sampler": "qmc", "shifts": wl.n_shifts}
+
+    def make(precision):
+        return fm.Context(len(wl.levels), wl.levels[0], wl.M, sigma2=wl.sigma2, lam=wl.lam, n_shifts=wl.n_shifts,
+                          seed=wl.seed, precision=precision, converged=True, tol=SOLVE_TOL, qtol=SOLVE_QTOL,
+                          max_cycles=300, energy_step=True, ir_cycles=IR_CYCLES[0] if precision == 1 else 0)
+
+    c = make(1)
+    t0 = time.perf_counter()
+    theta, captured = c.kl_basis_build(q=96)
+    torch.cuda.synchronize()
+    out["kl_basis_build_s"] = time.perf_counter() - t0
+    out["captured_variance"] = captured
+
+    def run(ctx, sur, batched):
+        ts, rs = [], []
+        for step in range(steps + 1):   # the first is a warm-up
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if sur:
+                rep_ = ctx.surrogate_train(**SURROGATE_TRAIN)
+                r = ctx.mlmc_estimate(wl.eps, qmc=True, n_pilot=QMC_PILOT, surrogate=True,
+                                      surrogate_cost=SURROGATE_COST, batched=batched)
+                r["train_corr"] = rep_["corr"]
+            else:
+                r = ctx.mlmc_estimate(wl.eps, qmc=True, n_pilot=QMC_PILOT, batched=batched)
+            b.record()
+            torch.cuda.synchronize()
+            if step > 0:
+                ts.append(a.elapsed_time(b) / 1e3)
+                rs.append(r)
+        r = rs[-1]
+        return {"value": float(np.mean(ts)), "unit": "s", "estimate": float(r["estimate"]),
+                "rmse_estimate": float(np.sqrt(r["var_estimator"])), "N_per_level_per_shift": [int(x) for x in r["N"]],
+                "rounds": int(r["rounds"]), "N_s_per_shift": int(r.get("N_s", 0)),
+                "train_corr": r.get("train_corr")}
+
+    out["chosen"] = run(c, True, True)
+    B = c.kl_basis_get()
+    c.close()
+    c2 = make(0)
+    c2.kl_basis_set(B)
+    del B
+    torch.cuda.empty_cache()
+    out["plain_fp64"] = run(c2, False, False)
+    c2.close()
+    out["speedup_vs_plain_fp64"] = out["plain_fp64"]["value"] / out["chosen"]["value"]
+    out["difference_in_sigmas"] = abs(out["chosen"]["estimate"] - out["plain_fp64"]["estimate"]) / np.hypot(
+        out["chosen"]["rmse_estimate"], out["plain_fp64"]["rmse_estimate"])
+    return out
+
+
 def standard_mlmc_leg(torch, ctx, wl, N, flush, samples=1000):
     """The paper's cost claim (Sec. 1): FMG-MLMC takes Q^c_l from the FMG
     hierarchy of the level-l solve, where standard MLMC solves the coarse
@@ -514,6 +593,7 @@ def run_native(args, wl, eps):
         c2.close()
 
     uneven = None if args.no_uneven_leg else uneven_leg(torch, fm, flush)
+    c5 = c5_leg(torch, fm, flush, args.c5_steps) if args.c5_leg else None
     standard = None if args.no_standard_leg else standard_mlmc_leg(torch, ctx, wl, results[-1]["N"], flush)
 
     # the randomized-QMC estimator (16 shifted Sobol' point sets, doubling rule)
@@ -641,6 +721,7 @@ def run_native(args, wl, eps):
                                     zip(results[-1]["N"], results[-1]["level_seconds"])],
     }
     detail = {"other_forms": others, "qmc": qmc_forms, "uneven_batch": uneven, "fmg_vs_standard_mlmc": standard,
+              "large_high_contrast": c5,
               "kernel_families": families, "profiled_step_same_schedule": same_schedule,
               "captured_variance": captured, "step_seconds": times}
     if sur:
@@ -667,6 +748,10 @@ def run_native(args, wl, eps):
                                "identical_results": uneven["identical_results"]}
     if standard:
         out["fmg_vs_standard_mlmc_saving"] = standard["saving_of_fmg_mlmc"]
+    if c5:
+        out["large_high_contrast"] = {"chosen_s": c5["chosen"]["value"], "plain_fp64_s": c5["plain_fp64"]["value"],
+                                      "speedup": c5["speedup_vs_plain_fp64"], "eps": c5["eps"],
+                                      "rmse": c5["chosen"]["rmse_estimate"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         conv = FORMS[args.form]["converged"]
         per, cores, counts = oracle_level_seconds(wl, args.cpu_seconds, conv)
@@ -744,6 +829,8 @@ def run_reference(args, wl, eps):
 
 def main():
     args = parse()
+    if args.ir_cycles is not None:
+        IR_CYCLES[0] = args.ir_cycles
     if args.kernel_case:
         import torch
         import paper_1910_04727_gb300 as fm

@@ -204,7 +204,8 @@ struct Request {
 // Per-level buffers of a batched round (kept across rounds).
 struct LevelBuf {
     double *xi = nullptr, *K = nullptr, *q = nullptr;
-    size_t cap = 0;
+    size_t cap = 0;    // samples of xi and q
+    size_t kcap = 0;   // samples of K (one pass)
 };
 
 // GPU side of the controller: samples go to mlmc_sample_level with the
@@ -286,26 +287,31 @@ fm_status flush_batched(GpuSampler* g) {
         cudaEventCreate(&g->b1);
     }
     cudaEventRecord(g->b0, nullptr);
-    // points and fields, level by level, requests packed in order
-    std::vector<fm_batch_group> groups;
-    std::vector<int> group_level;
+    // points of every request, level by level, requests packed in order;
+    // fields and solves in passes of at most batch_limit samples per level,
+    // one uneven batch per pass (every level's next chunk)
+    std::vector<uint64_t> chunk(L, 0);
+    uint64_t passes = 0;
     for (int l = 0; l < L; ++l) {
         if (!total[l]) continue;
         const int N = grid_of_level(ctx, l);
+        chunk[l] = std::min<uint64_t>(total[l], (uint64_t)batch_limit(ctx, N));
+        passes = std::max<uint64_t>(passes, (total[l] + chunk[l] - 1) / chunk[l]);
         LevelBuf& b = g->lb[l];
-        if (b.cap < total[l]) {
+        if (b.cap < total[l] || b.kcap < chunk[l]) {
             cudaFree(b.xi);
             cudaFree(b.K);
             cudaFree(b.q);
             b.xi = b.K = b.q = nullptr;
-            b.cap = 0;
+            b.cap = b.kcap = 0;
             if (cudaMalloc((void**)&b.xi, total[l] * M * sizeof(double)) != cudaSuccess ||
-                cudaMalloc((void**)&b.K, total[l] * (size_t)N * N * sizeof(double)) != cudaSuccess ||
+                cudaMalloc((void**)&b.K, chunk[l] * (size_t)N * N * sizeof(double)) != cudaSuccess ||
                 cudaMalloc((void**)&b.q, 2 * total[l] * sizeof(double)) != cudaSuccess) {
                 set_error(ctx, "mlmc_estimate: allocation of a batched round failed");
                 return FM_ENOMEM;
             }
             b.cap = total[l];
+            b.kcap = chunk[l];
         }
         uint64_t o = 0;
         for (const Request& r : g->pending) {
@@ -320,15 +326,24 @@ fm_status flush_batched(GpuSampler* g) {
             }
             o += r.n;
         }
-        for (uint64_t d = 0; d < total[l];) {
-            const uint32_t cnt = (uint32_t)std::min<uint64_t>(total[l] - d, (uint64_t)1 << 20);
-            FM_TRY(kl_field_batch(ctx, l, cnt, b.xi + d * M, b.K + d * (size_t)N * N, nullptr));
-            d += cnt;
-        }
-        groups.push_back(fm_batch_group{N, (uint32_t)total[l], b.K, b.q, b.q + total[l], nullptr});
-        group_level.push_back(l);
     }
-    FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
+    for (uint64_t pass = 0; pass < passes; ++pass) {
+        std::vector<fm_batch_group> groups;
+        for (int l = 0; l < L; ++l) {
+            const uint64_t d0 = pass * chunk[l];
+            if (!total[l] || d0 >= total[l]) continue;
+            const int N = grid_of_level(ctx, l);
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(chunk[l], total[l] - d0);
+            LevelBuf& b = g->lb[l];
+            for (uint64_t d = 0; d < cnt;) {
+                const uint32_t c = (uint32_t)std::min<uint64_t>(cnt - d, (uint64_t)1 << 20);
+                FM_TRY(kl_field_batch(ctx, l, c, b.xi + (d0 + d) * M, b.K + d * (size_t)N * N, nullptr));
+                d += c;
+            }
+            groups.push_back(fm_batch_group{N, cnt, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+        }
+        FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
+    }
     // level-0 surrogate values, then the sums of every request
     for (int l = 0; l < L; ++l) {
         if (!total[l]) continue;

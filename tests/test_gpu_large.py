@@ -115,3 +115,30 @@ def test_energy_step_arguments_are_checked():
         c.fmg_solve_batch(K, energy_step=1, kernel=2)        # the resident schedule
     with pytest.raises(fm.FmError):
         c.fmg_solve_batch(K, energy_step=1, converged=0)     # a fixed schedule
+
+
+def test_kl_samples_of_the_large_case_against_the_stepped_oracle():
+    """Fields of the large high-contrast configuration itself: the 1024-mode
+    KL basis of sigma^2 = 2, lambda = 0.1 at the 2048 x 2048 points (Nystrom
+    on q = 96, interpolated on the tensor cores), two samples synthesised in
+    FP64 and solved on the GPU with the energy-optimal step, mixed form under
+    the benchmark's stopping rule, against the stepped FP64 oracle on the
+    same coefficient fields (mixed bar, 1e-8)."""
+    import paper_1910_04727_gb300 as fm
+    from oracle import lib as OL
+    wl = W.WORKLOADS["contrast6"]
+    n = wl.levels[-1]
+    c = fm.Context(1, n, wl.M, sigma2=wl.sigma2, lam=wl.lam, seed=wl.seed, precision=1, converged=True,
+                   tol=1e-12, qtol=1e-10, max_cycles=300, energy_step=True, kl_mode=1)
+    theta, captured = c.kl_basis_build(q=96, interp=2)
+    assert abs(theta.sum() / captured - wl.sigma2) < 1e-6 * wl.sigma2   # trace identity of the spectrum
+    xi = c.mc_points(0, 0, 2)
+    K = c.kl_field_batch(0, xi)
+    qf, qc, _, st = c.fmg_solve_batch(K, want_status=True)
+    Kh = K.cpu().numpy()
+    print("contrast", Kh.max(axis=(1, 2)) / Kh.min(axis=(1, 2)))
+    rf, rc, _, _ = OL.fmg_solve_batch(Kh, OL.params(converged=True, tol=1e-13, max_cycles=400, energy_step=True))
+    assert np.all(st.cpu().numpy() == 0)
+    assert np.max(np.abs(qf.cpu().numpy() - rf) / np.abs(rf)) < 1e-8
+    assert np.max(np.abs(qc.cpu().numpy() - rc) / np.abs(rc)) < 1e-8
+    c.close()
