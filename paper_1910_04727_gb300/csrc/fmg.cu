@@ -65,31 +65,49 @@ __global__ void k_child_geomean(int nc, size_t S, const double* __restrict__ Kf,
 // no-flow edges, in arithmetic C; optional FP64 copies for refined grids
 // (which take C = double).  Te of the east column and Tn of the north row
 // hold the boundary faces: every kernel couples neighbours only across
-// interior faces, so these enter through D alone.
+// interior faces, so these enter through D alone.  Each face is formed once
+// (the east and north faces of its cell); k_diagonal then sums them.
 template <typename T, typename C>
-__global__ void k_coefficients(int n, size_t S, int ns, const double* __restrict__ K, T* __restrict__ Te,
-                               T* __restrict__ Tn, T* __restrict__ D, double* __restrict__ Te64,
-                               double* __restrict__ Tn64, double* __restrict__ D64) {
+__global__ void k_faces(int n, size_t S, int ns, const double* __restrict__ K, T* __restrict__ Te,
+                        T* __restrict__ Tn, double* __restrict__ Te64, double* __restrict__ Tn64) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t cells = (size_t)n * n;
     if (t >= S * cells) return;
     const int c = (int)(t % cells);
     const int i = c % n, j = c / n;
     const C k = (C)K[t];
-    const C tw = (i > 0) ? harmonic<C>((C)K[t - 1], k) : C(2) * k;
     const C te = (i < n - 1) ? harmonic<C>(k, (C)K[t + 1]) : C(2) * k;
-    const C tb = ns ? C(2) * k : C(0);   // north / south boundary face
-    const C ts = (j > 0) ? harmonic<C>((C)K[t - n], k) : tb;
-    const C tn = (j < n - 1) ? harmonic<C>(k, (C)K[t + n]) : tb;
-    const C d = tw + te + ts + tn;
+    const C tn = (j < n - 1) ? harmonic<C>(k, (C)K[t + n]) : (ns ? C(2) * k : C(0));
     Te[t] = (T)te;
     Tn[t] = (T)tn;
-    D[t] = (T)d;
     if (Te64) {
         Te64[t] = (double)te;
         Tn64[t] = (double)tn;
-        D64[t] = (double)d;
     }
+}
+
+// D = tw + te + ts + tn from the faces in their arithmetic C (the FP64 copies
+// where they exist): the west face of a cell is its west neighbour's east
+// face, the same harmonic mean of the same two values, so D equals the sum
+// of four freshly formed faces bit for bit.  Boundary faces: 2K west, 2K
+// south when ns, else 0.
+template <typename T, typename C>
+__global__ void k_diagonal(int n, size_t S, int ns, const double* __restrict__ K, const T* __restrict__ Te,
+                           const T* __restrict__ Tn, const double* __restrict__ Te64,
+                           const double* __restrict__ Tn64, T* __restrict__ D, double* __restrict__ D64) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t cells = (size_t)n * n;
+    if (t >= S * cells) return;
+    const int c = (int)(t % cells);
+    const int i = c % n, j = c / n;
+    auto fe = [&](size_t u) { return Te64 ? (C)Te64[u] : (C)Te[u]; };
+    auto fn = [&](size_t u) { return Tn64 ? (C)Tn64[u] : (C)Tn[u]; };
+    const C k = (C)K[t];
+    const C tw = (i > 0) ? fe(t - 1) : C(2) * k;
+    const C ts = (j > 0) ? fn(t - n) : (ns ? C(2) * k : C(0));
+    const C d = tw + fe(t) + ts + fn(t);
+    D[t] = (T)d;
+    if (D64) D64[t] = (double)d;
 }
 
 // Right-hand side of a stage problem: the Dirichlet data moved to the rhs.
@@ -1578,20 +1596,26 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
         // FP64 arithmetic for FP64 grids and for the refined grids' FP64 copies
         if (sizeof(T) == 8 || g.Te64)
             FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts + (g.Te64 ? 24.0 : 0.0)) * cells, 16.0 * cells,
-                     k_coefficients<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn,
-                                                                                     g.D, g.Te64, g.Tn64, g.D64));
+                     k_faces<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn,
+                                                                              g.Te64, g.Tn64);
+                     k_diagonal<T, double><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn,
+                                                                                 g.Te64, g.Tn64, g.D, g.D64));
         else
             FM_TIMED(ctx, kFamCoefficients, st, (8.0 + 3.0 * ts) * cells, 16.0 * cells,
-                     k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn, g.D,
-                                                                               nullptr, nullptr, nullptr));
+                     k_faces<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn, nullptr,
+                                                                         nullptr);
+                     k_diagonal<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.K, g.Te, g.Tn, nullptr,
+                                                                            nullptr, g.D, nullptr));
     }
     for (int k = 0; k < H.m; ++k) {
         const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
         FM_TIMED(ctx, kFamCoefficients, st, (32.0 + 8.0 + 3.0 * ts) * cells, 40.0 * cells,
                  k_child_geomean<T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, H.g[k + 1].K, g.Kc);
-                 k_coefficients<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.Kc, g.TeC, g.TnC, g.DC,
-                                                                            nullptr, nullptr, nullptr));
+                 k_faces<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.Kc, g.TeC, g.TnC, nullptr,
+                                                                     nullptr);
+                 k_diagonal<T, T><<<blocks_for(cells), kBlock, 0, st>>>(g.n, S, bd.ns, g.Kc, g.TeC, g.TnC, nullptr,
+                                                                        nullptr, g.DC, nullptr));
     }
     if (H.m >= 1) {
         const int m = H.n0 * H.n0;

@@ -193,7 +193,10 @@ def test_energy_step_in_the_graph_equals_per_group_solves(ctx, precision):
     the stepped oracle."""
     Ks = [torch.tensor(W.smooth_lognormal_field(n, S=S, sigma=1.4, tag=950 + n), device="cuda")
           for n, S in [(32, 11), (64, 6), (128, 3)]]
-    kw = dict(precision=precision, converged=1, tol=1e-12, qtol=0.0, max_cycles=300, energy_step=1)
+    # FP64: the residual test alone at 1e-13 (the stopping rule of the FP64 bar);
+    # mixed: the benchmark's rule
+    rule = dict(tol=1e-13, qtol=0.0) if precision == 0 else dict(tol=1e-12, qtol=1e-10)
+    kw = dict(precision=precision, converged=1, max_cycles=300, energy_step=1, **rule)
     outs = ctx.solve_uneven(Ks, **kw)
     for K, (qf, qc, _) in zip(Ks, outs):
         a, b, _ = ctx.fmg_solve_batch(K, **kw)
