@@ -53,6 +53,8 @@ def parse():
                     help="also run the large high-contrast case (6 levels 64x64 .. 2048x2048, 1024 modes, "
                          "sigma^2 = 2, lambda = 0.1, RMSE 5e-4) in the chosen form and in plain FP64")
     ap.add_argument("--c5-steps", type=int, default=1, help="timed estimates per form in the large case")
+    ap.add_argument("--train-epochs", type=int, default=None,
+                    help="epochs of the surrogate's training inside each step (default: SURROGATE_TRAIN)")
     ap.add_argument("--ir-cycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 residual test in the mixed forms (default: MIXED_IR_CYCLES)")
     ap.add_argument("--detail-out", default=None,
@@ -833,6 +835,8 @@ def main():
     args = parse()
     if args.ir_cycles is not None:
         IR_CYCLES[0] = args.ir_cycles
+    if args.train_epochs is not None:
+        SURROGATE_TRAIN["epochs"] = args.train_epochs
     if args.kernel_case:
         import torch
         import paper_1910_04727_gb300 as fm

@@ -130,7 +130,9 @@ typedef struct {
 
 /* Kernel schedule of a batched FMG solve (same arithmetic, same result up
  * to rounding order). */
-#define FM_KERNEL_AUTO 0       /* resident where the hierarchy fits, else levelwise */
+#define FM_KERNEL_AUTO 0       /* resident where it is the faster schedule (up to 32 x 32 in the
+                                  mixed form, 64 x 64 in FP64; not with the energy step), else
+                                  levelwise */
 #define FM_KERNEL_LEVELWISE 1  /* one kernel per grid operation over all samples */
 #define FM_KERNEL_RESIDENT 2   /* one CTA per sample, hierarchy in shared memory
                                   (n_fine <= 64 in FP64) */
@@ -353,7 +355,7 @@ typedef struct {
 } fm_batch_group;
 
 /* FMG solves of groups with different grid sizes as one CUDA graph: one
- * branch per group, the resident kernel for grids up to 64 x 64 and the
+ * branch per group, the resident kernel where FM_KERNEL_AUTO takes it and the
  * level-wise schedule above, the refined stages of the converged mode
  * looping on the device (conditional graph nodes), so the graph runs without
  * the host.  Each sample's results are those fmg_solve_batch gives it.  The

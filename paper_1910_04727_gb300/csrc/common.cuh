@@ -79,6 +79,16 @@ struct Ghost {
     int ns;
 };
 
+// The schedule FM_KERNEL_AUTO takes for a grid: the resident kernel where it
+// is the faster one on GB300 (measured per grid: 2x the level-wise schedule at
+// 16 x 16, level at 32 x 32, and 13% behind the column-strip level-wise
+// schedule at 64 x 64 in the mixed form), the level-wise schedule elsewhere
+// and for the energy-optimal step, which the resident kernel lacks.
+inline bool auto_resident(int n_fine, const fm_solve_params& prm) {
+    if (prm.energy_step) return false;
+    return n_fine <= (prm.precision == FM_PREC_MIXED ? 32 : 64);
+}
+
 // V-cycles between residual tests of a converged stage.
 inline int cycles_per_test(const fm_solve_params& prm) { return prm.ir_cycles > 0 ? prm.ir_cycles : prm.nu0; }
 

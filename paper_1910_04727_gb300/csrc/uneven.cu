@@ -65,10 +65,9 @@ static fm_status uneven_prepare(fm_ctx* ctx, int groups) {
     return FM_OK;
 }
 
-// A hierarchy fits the resident kernel (its shared-memory limit) for n <= 64;
-// the energy-optimal correction step runs on the level-wise schedule only.
+// Groups on the resident kernel: where FM_KERNEL_AUTO would take it.
 static bool resident_grid(int n, const fm_solve_params& prm) {
-    return prm.kernel != FM_KERNEL_LEVELWISE && !prm.energy_step && n <= 64;
+    return prm.kernel != FM_KERNEL_LEVELWISE && auto_resident(n, prm);
 }
 
 }  // namespace fm
