@@ -406,6 +406,14 @@ fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps, int32_t n
  * launches; every shape gives the same results.  FM_EINVAL otherwise. */
 fm_status fm_set_smoother_shape(fm_ctx* ctx, int32_t precision, int32_t n, int32_t tile, int32_t threads);
 
+/* Level-wise V-cycles: the part below a correction grid of at most n_max x
+ * n_max cells (a power of two up to 32; default 32) runs as one resident
+ * launch per cycle (every listed sample's tail in shared memory) instead of
+ * several launches per grid; 0 launches grid by grid throughout.  Same
+ * arithmetic in the same order: the results do not change.  The
+ * energy-optimal step always runs grid by grid. */
+fm_status fm_set_vcycle_tail(fm_ctx* ctx, int32_t n_max);
+
 /* ---------------------------------------------------------------- MLMC */
 
 /* Running sums of one (level, shift) cell: Neumaier-compensated FP64 pairs

@@ -323,6 +323,11 @@ class Context:
         self._check(self._L.fm_autotune(self._h, precision, nsweeps, n_min, n_max, out, 16, C.byref(cnt)))
         return [{f: getattr(e, f) for f, _ in _lib.FmTuneEntry._fields_} for e in out[:cnt.value]]
 
+    def set_vcycle_tail(self, n_max):
+        """Level-wise V-cycles run the part below correction grids up to n_max as one resident
+        launch (0: grid by grid); the results are the same either way."""
+        self._check(self._L.fm_set_vcycle_tail(self._h, n_max))
+
     def set_smoother_shape(self, n, tile, threads=0, precision=None):
         """Smoother launch shape of grid n (fm_set_smoother_shape): tile 0 colour launches,
         -1 column strips, 8..64 tiles (threads 0 register-blocked, 128 / 256 staged),

@@ -29,7 +29,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "surrogate_train", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
            "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance", "qmc_points",
-           "fm_lattice_cbc", "lattice_generating_vector", "kl_basis_build_ex"]
+           "fm_lattice_cbc", "lattice_generating_vector", "kl_basis_build_ex",
+           "fm_set_vcycle_tail"]
 
 
 class FmConfig(C.Structure):
@@ -177,6 +178,7 @@ def load(path=None):
         "fmg_solve_uneven": (I32, [P, I32, P, C.POINTER(FmSolveParams), P]),
         "fmg_uneven_stats": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         "fm_set_smoother_shape": (I32, [P, I32, I32, I32, I32]),
+        "fm_set_vcycle_tail": (I32, [P, I32]),
         "fm_shard_range": (None, [U64, U64, I32, I32, C.POINTER(U64), C.POINTER(U64)]),
         "mlmc_estimate_core": (I32, [C.POINTER(FmCoreOpts), ENQUEUE_FN, READ_FN, ALLGATHER_FN, P,
                                      C.POINTER(FmCoreResult), C.c_char_p, C.c_size_t]),

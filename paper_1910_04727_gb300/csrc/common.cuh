@@ -200,7 +200,7 @@ enum Family {
     kFamPoints = 0, kFamKlGemm, kFamInject, kFamCoefficients, kFamStageRhs, kFamSmoother,
     kFamResidualRestrict, kFamProlong, kFamFmgInterp, kFamCoarseInverse, kFamCoarseSolve,
     kFamOutflux, kFamLevelSums, kFamResidentFmg, kFamMlp, kFamMlpTrain, kFamUnevenGraph, kFamSmootherTile,
-    kFamSmootherStrip, kFamilyCount
+    kFamSmootherStrip, kFamVcycleTail, kFamilyCount
 };
 
 struct ProfRecord {
@@ -280,6 +280,8 @@ struct fm_ctx {
     cudaStream_t body_stream = nullptr;  // captures the bodies of device-side refinement loops
     fm::TuneTable tune;              // smoother launch shapes (fm_autotune)
     void* uneven = nullptr;          // uneven-batch executor state (uneven.cu)
+    int tail_max = 32;               // level-wise V-cycles: grids <= tail_max below the top run as one
+                                     // resident tail kernel (0: per-grid launches throughout)
 };
 
 namespace fm {

@@ -1056,6 +1056,132 @@ __global__ void k_status(size_t S, const int32_t* __restrict__ active, int32_t* 
     if (s < S && active[s]) status[s] = FM_ENOTCONV;
 }
 
+// ------------------------------------------------------------------ V-cycle tail
+// The part of a level-wise V-cycle below a correction grid of at most 32 x 32
+// cells, per sample in shared memory: pre-smoothing, residual and restriction
+// down to the coarsest grid, its solve, then prolongation and post-smoothing
+// back up.  One CTA per listed sample replaces the per-grid launches of those
+// grids (several tiny launches per grid and cycle).  Every operation is the
+// level-wise kernels' own, in their order and rounding: sweeps in colour
+// order with the faces W, E, S, N fused into the accumulator and the
+// reciprocal of D, residuals as residual_at forms them, restriction sums in
+// k_residual_restrict's order, the coarse product as k_coarse_solve sums it,
+// corrections as prolong_vals forms them; so the result is the per-grid
+// schedule's bit for bit (up to the sign of a zero).
+constexpr int kTailMaxN = 32;
+constexpr int kTailThreads = 128;
+
+template <typename T>
+struct TailArgs {
+    int kt, n0, nu1, nu2, ns;               // grids 0 .. kt, n_j = n0 << j; ns: Dirichlet north / south
+    size_t S;                               // samples enumerated (the listed ones, with order)
+    const T* Te[8];                         // correction operators of grids 0 .. kt
+    const T* Tn[8];
+    const T* D[8];
+    const T* b;                             // rhs of grid kt [..][n_kt^2]
+    T* p;                                   // out: the correction on grid kt
+    const T* Ainv;                          // coarsest correction operator's inverse [..][m][m]
+    const int32_t* active;
+    const int32_t* order;
+};
+
+template <typename T>
+__host__ __device__ inline size_t tail_smem_bytes(int kt, int n0) {
+    size_t cells = 0;
+    for (int j = 0; j <= kt; ++j) cells += (size_t)(n0 << j) * (n0 << j);
+    return (6 * cells + (size_t)n0 * n0 * n0 * n0) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    const size_t u = blockIdx.x;
+    if (u >= a.S) return;
+    const size_t s = a.order ? (size_t)a.order[u] : u;
+    if (inactive(a.active, s)) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // per grid j: te, tn, d, rd (1 / d), b, p
+    T* sm = reinterpret_cast<T*>(tail_smem);
+    T *te[8], *tn[8], *dd[8], *rd[8], *bb[8], *pp[8];
+    for (int j = 0; j <= a.kt; ++j) {
+        const int c = (a.n0 << j) * (a.n0 << j);
+        te[j] = sm; tn[j] = te[j] + c; dd[j] = tn[j] + c; rd[j] = dd[j] + c; bb[j] = rd[j] + c; pp[j] = bb[j] + c;
+        sm = pp[j] + c;
+    }
+    const int m = a.n0 * a.n0;
+    T* ainv = sm;
+    for (int j = 0; j <= a.kt; ++j) {
+        const int n = a.n0 << j, c = n * n;
+        const T* gte = a.Te[j] + s * (size_t)c;
+        const T* gtn = a.Tn[j] + s * (size_t)c;
+        const T* gd = a.D[j] + s * (size_t)c;
+        for (int e = tid; e < c; e += nt) {
+            te[j][e] = gte[e];
+            tn[j][e] = gtn[e];
+            dd[j][e] = gd[e];
+            rd[j][e] = T(1) / gd[e];
+        }
+    }
+    {
+        const int c = (a.n0 << a.kt) * (a.n0 << a.kt);
+        const T* gb = a.b + s * (size_t)c;
+        for (int e = tid; e < c; e += nt) {
+            bb[a.kt][e] = gb[e];
+            pp[a.kt][e] = T(0);   // the restriction left a zero correction
+        }
+        const T* gA = a.Ainv + s * (size_t)m * m;
+        for (int e = tid; e < m * m; e += nt) ainv[e] = gA[e];
+    }
+    __syncthreads();
+    auto sweeps = [&](int j, int nsw) {
+        const int n = a.n0 << j, hn = n / 2;
+        for (int it = 0; it < nsw; ++it)
+            for (int color = 0; color < 2; ++color) {
+                for (int h = tid; h < n * hn; h += nt) {
+                    const int y = h / hn, x = 2 * (h % hn) + ((y + color) & 1), c = y * n + x;
+                    T acc = bb[j][c];
+                    if (x > 0) acc = fma(te[j][c - 1], pp[j][c - 1], acc);
+                    if (x < n - 1) acc = fma(te[j][c], pp[j][c + 1], acc);
+                    if (y > 0) acc = fma(tn[j][c - n], pp[j][c - n], acc);
+                    if (y < n - 1) acc = fma(tn[j][c], pp[j][c + n], acc);
+                    pp[j][c] = acc * rd[j][c];
+                }
+                __syncthreads();
+            }
+    };
+    for (int j = a.kt; j >= 1; --j) {
+        sweeps(j, a.nu1);
+        const int nf = a.n0 << j, nc = nf / 2;
+        for (int C = tid; C < nc * nc; C += nt) {
+            const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J;
+            const size_t c00 = (size_t)j0 * nf + i0;
+            const T r00 = residual_at(nf, c00, i0, j0, bb[j], te[j], tn[j], dd[j], pp[j]);
+            const T r10 = residual_at(nf, c00 + 1, i0 + 1, j0, bb[j], te[j], tn[j], dd[j], pp[j]);
+            const T r01 = residual_at(nf, c00 + nf, i0, j0 + 1, bb[j], te[j], tn[j], dd[j], pp[j]);
+            const T r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bb[j], te[j], tn[j], dd[j], pp[j]);
+            bb[j - 1][C] = r00 + r10 + r01 + r11;
+            pp[j - 1][C] = T(0);
+        }
+        __syncthreads();
+    }
+    if (tid < m) {
+        T acc = T(0);
+        for (int c = 0; c < m; ++c) acc = fma(ainv[tid * m + c], bb[0][c], acc);
+        pp[0][tid] = acc;
+    }
+    __syncthreads();
+    for (int j = 1; j <= a.kt; ++j) {
+        const int nf = a.n0 << j, nc = nf / 2;
+        for (int c = tid; c < nf * nf; c += nt)
+            pp[j][c] = pp[j][c] + prolong_err(nc, pp[j - 1], c % nf, c / nf, a.ns);
+        __syncthreads();
+        sweeps(j, a.nu2);
+    }
+    const int c = (a.n0 << a.kt) * (a.n0 << a.kt);
+    T* gp = a.p + s * (size_t)c;
+    for (int e = tid; e < c; e += nt) gp[e] = pp[a.kt][e];
+}
+
 // ------------------------------------------------------------------ driver
 template <typename T>
 struct GridBufs {
@@ -1210,6 +1336,10 @@ void fmg_init_attributes() {
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_rbgs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         cudaFuncSetAttribute(k_rbgs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tail_smem_bytes<float>(4, 2) + 1024);
+        cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tail_smem_bytes<double>(4, 2) + 1024);
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1377,6 +1507,39 @@ static void smooth_shape(const fm_ctx* ctx, int n, const fm_solve_params& prm, i
     if (*tile == kShapeStrip && !strip_fits(n, prm.nu1, prm.nu2)) *tile = 0;
 }
 
+// The V-cycle below correction grid kt (<= 32 x 32) as one resident tail
+// launch over the listed samples (k_vcycle_tail).
+template <typename T>
+static void vcycle_tail(const Hierarchy<T>& H, int kt, const fm_solve_params& prm, const int32_t* active,
+                        cudaStream_t st) {
+    fm_ctx* ctx = H.ctx;
+    TailArgs<T> a{};
+    a.kt = kt;
+    a.n0 = H.n0;
+    a.nu1 = prm.nu1;
+    a.nu2 = prm.nu2;
+    a.ns = prm.bc_case == FM_CASE_I ? 1 : 0;
+    const bool listed = H.listed();
+    a.S = listed ? H.busy : H.S;
+    double cells = 0.0;
+    for (int j = 0; j <= kt; ++j) {
+        a.Te[j] = H.g[j].TeC;
+        a.Tn[j] = H.g[j].TnC;
+        a.D[j] = H.g[j].DC;
+        cells += (double)H.g[j].n * H.g[j].n;
+    }
+    a.b = H.g[kt].b;
+    a.p = H.g[kt].p;
+    a.Ainv = H.AinvC;
+    a.active = active;
+    a.order = listed ? H.order : nullptr;
+    const size_t smem = tail_smem_bytes<T>(kt, H.n0);
+    const double top = (double)H.g[kt].n * H.g[kt].n;
+    FM_TIMED(ctx, kFamVcycleTail, st, (3.0 * cells + 2.0 * top) * sizeof(T) * a.S,
+             (10.0 * (prm.nu1 + prm.nu2) + 18.0) * cells * a.S,
+             k_vcycle_tail<T><<<(unsigned)a.S, kTailThreads, smem, st>>>(a));
+}
+
 // One V(nu1, nu2) cycle on grid k; grid `top` carries the stage operator
 // (injected K), the grids below it the correction operators (child means).
 template <typename T>
@@ -1421,7 +1584,12 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
                  k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
                      c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
     }
-    vcycle(H, k - 1, top, prm, active, st);
+    // the V-cycle below: the resident tail for correction grids up to
+    // ctx->tail_max, else grid by grid
+    if (k - 1 >= 1 && c.n <= ctx->tail_max && !prm.energy_step && S > 0)
+        vcycle_tail(H, k - 1, prm, active, st);
+    else
+        vcycle(H, k - 1, top, prm, active, st);
     if (prm.energy_step) {
         // the stepped correction (converged mode: partials and alpha in the hierarchy)
         const int chunks = check_chunks(n);
@@ -1943,6 +2111,14 @@ extern "C" fm_status fm_autotune(fm_ctx* ctx, int32_t precision, int32_t nsweeps
         ++count;
     }
     if (n_entries) *n_entries = std::min(count, max_entries);
+    return FM_OK;
+}
+
+extern "C" fm_status fm_set_vcycle_tail(fm_ctx* ctx, int32_t n_max) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fm_set_vcycle_tail: null context");
+    FM_CHECK_ARG(ctx, n_max == 0 || (n_max >= 2 && n_max <= kTailMaxN && (n_max & (n_max - 1)) == 0),
+                 "fm_set_vcycle_tail: n_max must be 0 or a power of two up to 32");
+    ctx->tail_max = n_max;
     return FM_OK;
 }
 

@@ -10,7 +10,7 @@ static const char* kFamilyNames[kFamilyCount] = {
     "points", "kl_gemm_exp", "inject", "coefficients", "stage_rhs", "rbgs_smoother",
     "residual_restrict", "prolong_correct", "fmg_interpolate", "coarse_inverse",
     "coarse_solve", "outflux", "level_sums", "fmg_resident", "mlp_gemm", "mlp_train_graph",
-    "uneven_graph", "rbgs_tile", "rbgs_strip"};
+    "uneven_graph", "rbgs_tile", "rbgs_strip", "vcycle_tail"};
 
 int prof_start(fm_ctx* ctx, int family, cudaStream_t st) {
     Profiler& P = ctx->prof;

@@ -70,3 +70,25 @@ def test_shape_arguments_are_checked():
     for args in [(24, 0, 0), (64, 48, 0), (64, -1, 128), (64, 0, 256), (64, 32, 64)]:
         with pytest.raises(fm.FmError):
             c.set_smoother_shape(*args)
+
+
+@pytest.mark.parametrize("precision,converged,case", [(0, 0, 2), (0, 1, 2), (1, 1, 2), (1, 1, 1)])
+def test_resident_vcycle_tail_changes_nothing(precision, converged, case):
+    """The V-cycle below 32 x 32 as one resident launch per cycle (the default)
+    against grid-by-grid launches: every result bit for bit, on every shape of
+    the grids above it, in both boundary cases."""
+    import paper_1910_04727_gb300 as fm
+    c = fm.Context(2, 16, 16, precision=precision, converged=converged, tol=1e-12, qtol=1e-10, max_cycles=200,
+                   bc_case=case, pS=0.3, pN=0.7)
+    for n, S in [(64, 7), (128, 3), (256, 2)]:
+        K = torch.tensor(W.smooth_lognormal_field(n, S=S, tag=2300 + n), device="cuda")
+        out = {}
+        for tail in (32, 0, 16):
+            c.set_vcycle_tail(tail)
+            out[tail] = c.fmg_solve_batch(K, want_p=True, kernel=LEVELWISE)
+        for tail in (0, 16):
+            for a, b in zip(out[32], out[tail]):
+                assert _same(a, b), (n, tail)
+    c.set_vcycle_tail(32)
+    with pytest.raises(fm.FmError):
+        c.set_vcycle_tail(24)
