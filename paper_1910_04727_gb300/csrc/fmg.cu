@@ -1092,6 +1092,19 @@ __host__ __device__ inline size_t tail_smem_bytes(int kt, int n0) {
     return (6 * cells + (size_t)n0 * n0 * n0 * n0) * sizeof(T);
 }
 
+// The largest tail footprint over every coarsest size (2, 3, 4) and the
+// deepest correction grid of at most kTailMaxN cells a side above it.
+template <typename T>
+inline size_t tail_smem_max() {
+    size_t m = 0;
+    for (int n0 = 2; n0 <= 4; ++n0) {
+        int kt = 0;
+        while ((n0 << (kt + 1)) <= kTailMaxN) ++kt;
+        m = std::max(m, tail_smem_bytes<T>(kt, n0));
+    }
+    return m;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs<T> a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
@@ -1337,9 +1350,9 @@ void fmg_init_attributes() {
         cudaFuncSetAttribute(k_rbgs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         cudaFuncSetAttribute(k_rbgs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tail_smem_bytes<float>(4, 2) + 1024);
+                             (int)tail_smem_max<float>());
         cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tail_smem_bytes<double>(4, 2) + 1024);
+                             (int)tail_smem_max<double>());
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -2,7 +2,7 @@
 // CUDA graph.
 //
 // Every group gets a branch of its own (fork and join events around it):
-// groups whose hierarchy fits in shared memory run the resident kernel (a
+// groups where FM_KERNEL_AUTO takes the resident kernel run it (a
 // persistent grid, one sample per CTA or warp), the others the level-wise
 // schedule with its scratch in an arena of the group's own.  The converged
 // stages of the level-wise schedule loop on the device (a conditional WHILE

@@ -72,15 +72,17 @@ def test_shape_arguments_are_checked():
             c.set_smoother_shape(*args)
 
 
-@pytest.mark.parametrize("precision,converged,case", [(0, 0, 2), (0, 1, 2), (1, 1, 2), (1, 1, 1)])
-def test_resident_vcycle_tail_changes_nothing(precision, converged, case):
+@pytest.mark.parametrize("precision,converged,case,nc", [(0, 0, 2, 4), (0, 1, 2, 4), (1, 1, 2, 4), (1, 1, 1, 4),
+                                                          (0, 0, 2, 2), (0, 1, 1, 3), (1, 1, 2, 3)])
+def test_resident_vcycle_tail_changes_nothing(precision, converged, case, nc):
     """The V-cycle below 32 x 32 as one resident launch per cycle (the default)
     against grid-by-grid launches: every result bit for bit, on every shape of
-    the grids above it, in both boundary cases."""
+    the grids above it, in both boundary cases, for coarsest grids of 2, 3 and
+    4 cells a side (the tail's deepest and largest footprints)."""
     import paper_1910_04727_gb300 as fm
-    c = fm.Context(2, 16, 16, precision=precision, converged=converged, tol=1e-12, qtol=1e-10, max_cycles=200,
-                   bc_case=case, pS=0.3, pN=0.7)
-    for n, S in [(64, 7), (128, 3), (256, 2)]:
+    c = fm.Context(2, nc * 4, 16, n_coarsest=nc, precision=precision, converged=converged, tol=1e-12, qtol=1e-10,
+                   max_cycles=200, bc_case=case, pS=0.3, pN=0.7)
+    for n, S in [(nc * 16, 7), (nc * 32, 3), (nc * 64, 2)]:
         K = torch.tensor(W.smooth_lognormal_field(n, S=S, tag=2300 + n), device="cuda")
         out = {}
         for tail in (32, 0, 16):
