@@ -79,16 +79,17 @@ struct Ghost {
     int ns;
 };
 
-// The schedule FM_KERNEL_AUTO takes for a grid: the resident kernel up to
-// 16 x 16, where it is the faster one on GB300, the level-wise schedule (with
-// its V-cycle tail below 32 x 32) above and for the energy-optimal step,
-// which the resident kernel lacks.  Measured per grid, samples per second of
-// resident over level-wise: 16 x 16 2.0x (mixed), 1.1x (FP64, two cycles per
-// stage), 1.2x (FP64 converged); 32 x 32 0.97x, 0.84x, 0.93x; 64 x 64 0.82x,
-// 0.89x, 1.04x.
+// The schedule FM_KERNEL_AUTO takes for a grid: the resident kernel where it
+// is the faster one on GB300 (up to 32 x 32 in the mixed form, 16 x 16 in
+// FP64), the level-wise schedule (with its V-cycle tail below 32 x 32) above
+// and for the energy-optimal step, which the resident kernel lacks.
+// Measured per grid, samples per second of resident over level-wise:
+// 16 x 16 2.0x (mixed), 1.1x (FP64, two cycles per stage), 1.2x (FP64
+// converged); 64 x 64 0.82x, 0.89x, 1.04x; 32 x 32 0.93x and 0.84x in FP64,
+// level in the mixed form (0.97x alone, ahead inside the five-level estimate).
 inline bool auto_resident(int n_fine, const fm_solve_params& prm) {
     if (prm.energy_step) return false;
-    return n_fine <= 16;
+    return n_fine <= (prm.precision == FM_PREC_MIXED ? 32 : 16);
 }
 
 // V-cycles between residual tests of a converged stage.

@@ -935,12 +935,19 @@ __global__ void k_fill(size_t count, double v, double* __restrict__ x) {
 // ------------------------------------------------------------------ refinement kernels
 // Per-sample convergence test of the stage problem, split over `chunks`
 // CTAs per sample (grid S * chunks, chunk index fastest): each CTA forms the
-// residual of its slice of cells and writes its partial sums of ||r||^2,
+// residual of its band of rows and writes its partial sums of ||r||^2,
 // ||b||^2 and the outflux to partial[(s * chunks + ch) * 3 + 0..2]; the
 // mixed form (p64 != null) forms the residual in FP64 from the FP64 grid and
 // writes it, rounded, into the FP32 rhs bT with the FP32 correction pT
 // zeroed.  k_stage_decide then folds the partials in chunk order.  b / bT
 // and p / pT are the same arrays, hence no __restrict__ on them.
+// Threads walk rows (a column each, or several rows per pass on grids
+// narrower than the block), so no cell index is divided.  The rhs of a stage
+// problem is zero off the Dirichlet edges: interior cells take r = -A p with
+// no K load, and only edge cells form the Dirichlet term and add to ||b||^2.
+// On GB300 the FP64 pipe (1/58 of the FP32 rate) bounds this kernel, so the
+// interior FP64 work is the residual's product and four FMAs, the square
+// and one rounding.
 template <typename T>
 __global__ void k_stage_partials(int n, size_t S, int chunks, const double* __restrict__ K, Bnd bd,
                                  const T* b, const T* __restrict__ Te, const T* __restrict__ Tn,
@@ -955,34 +962,57 @@ __global__ void k_stage_partials(int n, size_t S, int chunks, const double* __re
     const int ch = (int)(blockIdx.x % chunks);
     if (inactive(active, s)) return;
     const size_t base = s * (size_t)n * n;
-    const int cells = n * n, per = (cells + chunks - 1) / chunks;
-    const int c0 = ch * per, c1 = min(cells, c0 + per);
+    const int rows = (n + chunks - 1) / chunks;
+    const int j0 = ch * rows, j1 = min(n, j0 + rows);
+    // thread -> first column i0 and row offset jo; a pass covers rpi rows
+    const int nt = (int)blockDim.x;
+    const bool wide = n >= nt;
+    const int rpi = wide ? 1 : nt / n;
+    const int i0 = wide ? (int)threadIdx.x : (int)threadIdx.x % n;
+    const int jo = wide ? 0 : (int)threadIdx.x / n;
+    const int istep = wide ? nt : n;
+    const int h0 = n / 2 - 1, h1 = n / 2;   // Case I: the four centre cells
     double rr = 0.0, bb = 0.0, qq = 0.0;
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        const int i = c % n, j = c / n;
-        const size_t g = base + c;
-        const double pv = p64 ? p64[g] : (double)p[g];
-        if (bd.ns) {   // Case I: u(0.5, 0.5), the four centre cells
-            if ((i == n / 2 - 1 || i == n / 2) && (j == n / 2 - 1 || j == n / 2)) qq += 0.25 * pv;
-        } else if (i == n - 1) {
-            qq += 2.0 * K[g] * (pv - bd.g[1]);
+    if (jo < rpi) {
+        for (int j = j0 + jo; j < j1; j += rpi) {
+            const bool row_edge = bd.ns && (j == 0 || j == n - 1);
+            const bool row_centre = bd.ns && (j == h0 || j == h1);
+            for (int i = i0; i < n; i += istep) {
+                const size_t g = base + (size_t)j * n + i;
+                const bool edge = row_edge || i == 0 || i == n - 1;
+                double r, pv;
+                if (p64) {
+                    pv = p64[g];
+                    double v = D64[g] * pv;
+                    if (i > 0) v -= Te64[g - 1] * p64[g - 1];
+                    if (i < n - 1) v -= Te64[g] * p64[g + 1];
+                    if (j > 0) v -= Tn64[g - n] * p64[g - n];
+                    if (j < n - 1) v -= Tn64[g] * p64[g + n];
+                    if (edge) {
+                        const double f = dirichlet_rhs(bd, n, i, j, K[g]);
+                        r = f - v;
+                        bb += f * f;
+                    } else {
+                        r = -v;
+                    }
+                    bT[g] = (T)r;
+                    pT[g] = T(0);
+                } else {
+                    pv = (double)p[g];
+                    r = (double)residual_at(n, g, i, j, b, Te, Tn, D, p);
+                    if (edge) {
+                        const double f = dirichlet_rhs(bd, n, i, j, K[g]);
+                        bb += f * f;
+                    }
+                }
+                rr += r * r;
+                if (bd.ns) {
+                    if (row_centre && (i == h0 || i == h1)) qq += 0.25 * pv;
+                } else if (i == n - 1) {
+                    qq += 2.0 * K[g] * (pv - bd.g[1]);
+                }
+            }
         }
-        const double f = dirichlet_rhs(bd, n, i, j, K[g]);
-        double r;
-        if (p64) {
-            double v = D64[g] * p64[g];
-            if (i > 0) v -= Te64[g - 1] * p64[g - 1];
-            if (i < n - 1) v -= Te64[g] * p64[g + 1];
-            if (j > 0) v -= Tn64[g - n] * p64[g - n];
-            if (j < n - 1) v -= Tn64[g] * p64[g + n];
-            r = f - v;
-            bT[g] = (T)r;
-            pT[g] = T(0);
-        } else {
-            r = (double)residual_at(n, g, i, j, b, Te, Tn, D, p);
-        }
-        rr += r * r;
-        bb += f * f;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
