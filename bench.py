@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle's bounded timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="mixed_surrogate",
+    ap.add_argument("--form", default="mixed_surrogate_batched",
                     choices=["mixed_surrogate", "mixed_surrogate_batched", "mixed", "fp64_converged",
                              "fp64_fmg2"])
     ap.add_argument("--no-standard-leg", action="store_true",
@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--c5-steps", type=int, default=1, help="timed estimates per form in the large case")
     ap.add_argument("--train-epochs", type=int, default=None,
                     help="epochs of the surrogate's training inside each step (default: SURROGATE_TRAIN)")
+    ap.add_argument("--train-batch", type=int, default=None,
+                    help="minibatch of the surrogate's training (default: SURROGATE_TRAIN)")
+    ap.add_argument("--train-lr", type=float, default=None,
+                    help="peak Adam learning rate of the surrogate's training (default: SURROGATE_TRAIN)")
     ap.add_argument("--ir-cycles", type=int, default=None,
                     help="FP32 V-cycles per FP64 residual test in the mixed forms (default: MIXED_IR_CYCLES)")
     ap.add_argument("--detail-out", default=None,
@@ -363,8 +367,24 @@ def _case_resident(torch, fm, level, S):
     ctx.close()
 
 
+def _case_levelwise(torch, fm, level, S):
+    """S level-`level` samples of the five-level workload in the mixed
+    converged form, solved three times on the level-wise schedule."""
+    wl = W.WORKLOADS["fmg_mlmc5"]
+    ctx = make_ctx(fm, wl, 0, "mixed")
+    ctx.kl_basis_build(q=wl.kl_q)
+    K = ctx.kl_field_batch(level, ctx.mc_points(level, 0, S))
+    for _ in range(3):
+        qf, qc, _ = ctx.fmg_solve_batch(K, kernel=1)
+    torch.cuda.synchronize()
+    ctx.sync()
+    print("kernel case: %d samples of %dx%d, mean Q^f %.6f" % (S, K.shape[-1], K.shape[-1], float(qf.mean())))
+    ctx.close()
+
+
 # one small isolated launch pattern per case, for a profiler (-k/-c select it)
 KERNEL_CASES = {
+    "fmg_levelwise_mixed256": lambda torch, fm: _case_levelwise(torch, fm, 4, 300),
     "fmg_resident_mixed16": lambda torch, fm: _case_resident(torch, fm, 0, 65536),
     "fmg_resident_mixed32": lambda torch, fm: _case_resident(torch, fm, 1, 16384),
     "fmg_resident_mixed64": lambda torch, fm: _case_resident(torch, fm, 2, 4096),
@@ -578,9 +598,13 @@ def run_native(args, wl, eps):
         dist.barrier()
 
     # kernel families of the same schedule: one more step with a CUDA event
-    # pair around every launch (kept out of the timed steps above)
+    # pair around every launch (kept out of the timed steps above).  A batched
+    # form's rounds run as one CUDA graph, timed as a whole; its kernels are
+    # profiled in the per-level form of the same samples (the same kernels on
+    # the same samples, one level after another instead of concurrently)
+    prof_form = args.form[:-len("_batched")] if args.form.endswith("_batched") else args.form
     _, prof_results, prof, _ = time_estimates(torch, ctx, eps, args, wl, 1, 0, flush, profile=True,
-                                              form=args.form)
+                                              form=prof_form)
     same_schedule = [int(x) for x in prof_results[-1]["N"]] == [int(x) for x in results[-1]["N"]]
 
     # the other forms of the same estimate, timed the same way
@@ -596,7 +620,8 @@ def run_native(args, wl, eps):
                         "estimate": float(np.mean([r["estimate"] for r in rs])),
                         "var_estimator": float(np.mean([r["var_estimator"] for r in rs])),
                         "N_per_level": [int(x) for x in rs[-1]["N"]],
-                        "V_per_level": [float(x) for x in rs[-1]["V"]]}
+                        "V_per_level": [float(x) for x in rs[-1]["V"]],
+                        "level_seconds": [float(x) for x in rs[-1]["level_seconds"]]}
         c2.close()
 
     uneven = None if args.no_uneven_leg else uneven_leg(torch, fm, flush)
@@ -627,6 +652,7 @@ def run_native(args, wl, eps):
     ctx2 = make_ctx(fm, wl, rank, args.form)
     e2e_times, rounds = [], []
     sur = FORMS[args.form]["surrogate"]
+    batched = FORMS[args.form].get("batched", False)
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush_l2(flush)
         torch.cuda.synchronize()
@@ -635,9 +661,9 @@ def run_native(args, wl, eps):
         if sur:
             ctx2.surrogate_train(**SURROGATE_TRAIN)
             r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, surrogate=True,
-                                   surrogate_cost=results[-1]["surrogate_cost"])
+                                   surrogate_cost=results[-1]["surrogate_cost"], batched=batched)
         else:
-            r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot)
+            r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, batched=batched)
         e2e_times.append(time.perf_counter() - t0)
         rounds.append(r["rounds"])
     ctx2.close()
@@ -691,6 +717,11 @@ def run_native(args, wl, eps):
 
     ests = [r["estimate"] for r in results]
     value = t_total / args.steps
+    # per-level rates: a batched form solves all levels of a round in one
+    # graph, so its rates come from the per-level form of the same samples
+    level_seconds, level_source = results[-1]["level_seconds"], args.form
+    if FORMS[args.form].get("batched") and prof_form in others:
+        level_seconds, level_source = others[prof_form]["level_seconds"], prof_form + " (per-level calls)"
     fp64_fmg2 = others.get("fp64_fmg2", {}).get("value")
     fp64_conv = others.get("fp64_converged", {}).get("value")
     out = {
@@ -725,7 +756,8 @@ def run_native(args, wl, eps):
         "rmse_estimate": float(np.sqrt(np.mean([r["var_estimator"] for r in results]))),
         "N_per_level": [int(x) for x in results[-1]["N"]],
         "samples_per_s_per_level": [round(float(n / t), 1) if t > 0 else None for n, t in
-                                    zip(results[-1]["N"], results[-1]["level_seconds"])],
+                                    zip(results[-1]["N"], level_seconds)],
+        "samples_per_s_source": level_source,
     }
     detail = {"other_forms": others, "qmc": qmc_forms, "uneven_batch": uneven, "fmg_vs_standard_mlmc": standard,
               "large_high_contrast": c5,
@@ -840,6 +872,10 @@ def main():
         IR_CYCLES[0] = args.ir_cycles
     if args.train_epochs is not None:
         SURROGATE_TRAIN["epochs"] = args.train_epochs
+    if args.train_batch is not None:
+        SURROGATE_TRAIN["batch"] = args.train_batch
+    if args.train_lr is not None:
+        SURROGATE_TRAIN["lr"] = args.train_lr
     if args.kernel_case:
         import torch
         import paper_1910_04727_gb300 as fm

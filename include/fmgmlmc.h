@@ -598,7 +598,7 @@ typedef struct {
     int32_t epochs;
     double lr;            /* Adam step, cosine-decayed to 0 over the run */
     uint64_t seed;        /* parameter initialisation and shuffling */
-    int32_t batch;        /* mini-batch rows: a multiple of 128, at most 1024 (0: 256) */
+    int32_t batch;        /* mini-batch rows: a multiple of 128, at most 4096 (0: 256) */
 } fm_train_opts;
 
 typedef struct {

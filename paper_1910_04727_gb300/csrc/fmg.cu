@@ -1143,86 +1143,113 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs<T> a) {
     const size_t s = a.order ? (size_t)a.order[u] : u;
     if (inactive(a.active, s)) return;
     const int tid = threadIdx.x, nt = blockDim.x;
-    // per grid j: te, tn, d, rd (1 / d), b, p
-    T* sm = reinterpret_cast<T*>(tail_smem);
-    T *te[8], *tn[8], *dd[8], *rd[8], *bb[8], *pp[8];
+    // Grid j holds six arrays of n_j^2 = m0 4^j values (te, tn, d, 1/d, b, p)
+    // from 6 m0 (4^j - 1) / 3 values into shared memory; the coarsest
+    // operator's inverse follows the last grid.  Addresses are formed in
+    // registers (no per-grid pointer tables in local memory).
+    T* const sm = reinterpret_cast<T*>(tail_smem);
+    const int m0 = a.n0 * a.n0;
+    auto arr = [&](int j, int q) -> T* { return sm + 2 * m0 * ((1 << (2 * j)) - 1) + q * (m0 << (2 * j)); };
     for (int j = 0; j <= a.kt; ++j) {
-        const int c = (a.n0 << j) * (a.n0 << j);
-        te[j] = sm; tn[j] = te[j] + c; dd[j] = tn[j] + c; rd[j] = dd[j] + c; bb[j] = rd[j] + c; pp[j] = bb[j] + c;
-        sm = pp[j] + c;
-    }
-    const int m = a.n0 * a.n0;
-    T* ainv = sm;
-    for (int j = 0; j <= a.kt; ++j) {
-        const int n = a.n0 << j, c = n * n;
+        const int c = m0 << (2 * j);
         const T* gte = a.Te[j] + s * (size_t)c;
         const T* gtn = a.Tn[j] + s * (size_t)c;
         const T* gd = a.D[j] + s * (size_t)c;
+        T* te = arr(j, 0);
+        T* tn = arr(j, 1);
+        T* dd = arr(j, 2);
+        T* rd = arr(j, 3);
+#pragma unroll 4
         for (int e = tid; e < c; e += nt) {
-            te[j][e] = gte[e];
-            tn[j][e] = gtn[e];
-            dd[j][e] = gd[e];
-            rd[j][e] = T(1) / gd[e];
+            const T d = gd[e];
+            te[e] = gte[e];
+            tn[e] = gtn[e];
+            dd[e] = d;
+            rd[e] = T(1) / d;
         }
     }
+    T* const ainv = arr(a.kt + 1, 0);
     {
-        const int c = (a.n0 << a.kt) * (a.n0 << a.kt);
+        const int c = m0 << (2 * a.kt);
         const T* gb = a.b + s * (size_t)c;
+        T* bt = arr(a.kt, 4);
+        T* pt = arr(a.kt, 5);
+#pragma unroll 4
         for (int e = tid; e < c; e += nt) {
-            bb[a.kt][e] = gb[e];
-            pp[a.kt][e] = T(0);   // the restriction left a zero correction
+            bt[e] = gb[e];
+            pt[e] = T(0);   // the restriction left a zero correction
         }
-        const T* gA = a.Ainv + s * (size_t)m * m;
-        for (int e = tid; e < m * m; e += nt) ainv[e] = gA[e];
+        const T* gA = a.Ainv + s * (size_t)m0 * m0;
+        for (int e = tid; e < m0 * m0; e += nt) ainv[e] = gA[e];
     }
     __syncthreads();
+    // Red-black sweeps on grid j: thread -> column pair xh of rows y0, y0 + ry, ...
     auto sweeps = [&](int j, int nsw) {
-        const int n = a.n0 << j, hn = n / 2;
+        const int n = a.n0 << j, hn = n >> 1, ry = nt / hn;
+        const int xh = tid % hn, y0 = tid / hn;
+        const T* te = arr(j, 0);
+        const T* tn = arr(j, 1);
+        const T* rd = arr(j, 3);
+        const T* bb = arr(j, 4);
+        T* pp = arr(j, 5);
         for (int it = 0; it < nsw; ++it)
             for (int color = 0; color < 2; ++color) {
-                for (int h = tid; h < n * hn; h += nt) {
-                    const int y = h / hn, x = 2 * (h % hn) + ((y + color) & 1), c = y * n + x;
-                    T acc = bb[j][c];
-                    if (x > 0) acc = fma(te[j][c - 1], pp[j][c - 1], acc);
-                    if (x < n - 1) acc = fma(te[j][c], pp[j][c + 1], acc);
-                    if (y > 0) acc = fma(tn[j][c - n], pp[j][c - n], acc);
-                    if (y < n - 1) acc = fma(tn[j][c], pp[j][c + n], acc);
-                    pp[j][c] = acc * rd[j][c];
+                for (int y = y0; y < n && y0 < ry; y += ry) {
+                    const int x = 2 * xh + ((y + color) & 1), c = y * n + x;
+                    T acc = bb[c];
+                    if (x > 0) acc = fma(te[c - 1], pp[c - 1], acc);
+                    if (x < n - 1) acc = fma(te[c], pp[c + 1], acc);
+                    if (y > 0) acc = fma(tn[c - n], pp[c - n], acc);
+                    if (y < n - 1) acc = fma(tn[c], pp[c + n], acc);
+                    pp[c] = acc * rd[c];
                 }
                 __syncthreads();
             }
     };
     for (int j = a.kt; j >= 1; --j) {
         sweeps(j, a.nu1);
-        const int nf = a.n0 << j, nc = nf / 2;
-        for (int C = tid; C < nc * nc; C += nt) {
-            const int I = C % nc, J = C / nc, i0 = 2 * I, j0 = 2 * J;
+        const int nf = a.n0 << j, nc = nf / 2, rc = nt / nc;
+        const int I = tid % nc, J0 = tid / nc;
+        const T* te = arr(j, 0);
+        const T* tn = arr(j, 1);
+        const T* dd = arr(j, 2);
+        const T* bf = arr(j, 4);
+        const T* pf = arr(j, 5);
+        T* bc = arr(j - 1, 4);
+        T* pc = arr(j - 1, 5);
+        for (int J = J0; J < nc && J0 < rc; J += rc) {
+            const int i0 = 2 * I, j0 = 2 * J;
             const size_t c00 = (size_t)j0 * nf + i0;
-            const T r00 = residual_at(nf, c00, i0, j0, bb[j], te[j], tn[j], dd[j], pp[j]);
-            const T r10 = residual_at(nf, c00 + 1, i0 + 1, j0, bb[j], te[j], tn[j], dd[j], pp[j]);
-            const T r01 = residual_at(nf, c00 + nf, i0, j0 + 1, bb[j], te[j], tn[j], dd[j], pp[j]);
-            const T r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bb[j], te[j], tn[j], dd[j], pp[j]);
-            bb[j - 1][C] = r00 + r10 + r01 + r11;
-            pp[j - 1][C] = T(0);
+            const T r00 = residual_at(nf, c00, i0, j0, bf, te, tn, dd, pf);
+            const T r10 = residual_at(nf, c00 + 1, i0 + 1, j0, bf, te, tn, dd, pf);
+            const T r01 = residual_at(nf, c00 + nf, i0, j0 + 1, bf, te, tn, dd, pf);
+            const T r11 = residual_at(nf, c00 + nf + 1, i0 + 1, j0 + 1, bf, te, tn, dd, pf);
+            bc[J * nc + I] = r00 + r10 + r01 + r11;
+            pc[J * nc + I] = T(0);
         }
         __syncthreads();
     }
-    if (tid < m) {
+    if (tid < m0) {
+        const T* b0 = arr(0, 4);
         T acc = T(0);
-        for (int c = 0; c < m; ++c) acc = fma(ainv[tid * m + c], bb[0][c], acc);
-        pp[0][tid] = acc;
+        for (int c = 0; c < m0; ++c) acc = fma(ainv[tid * m0 + c], b0[c], acc);
+        arr(0, 5)[tid] = acc;
     }
     __syncthreads();
     for (int j = 1; j <= a.kt; ++j) {
-        const int nf = a.n0 << j, nc = nf / 2;
-        for (int c = tid; c < nf * nf; c += nt)
-            pp[j][c] = pp[j][c] + prolong_err(nc, pp[j - 1], c % nf, c / nf, a.ns);
+        const int nf = a.n0 << j, nc = nf / 2, rf = nt / nf;
+        const int i = tid % nf, y0 = tid / nf;
+        const T* pc = arr(j - 1, 5);
+        T* pf = arr(j, 5);
+        for (int y = y0; y < nf && y0 < rf; y += rf) pf[y * nf + i] = pf[y * nf + i] + prolong_err(nc, pc, i, y, a.ns);
         __syncthreads();
         sweeps(j, a.nu2);
     }
-    const int c = (a.n0 << a.kt) * (a.n0 << a.kt);
+    const int c = m0 << (2 * a.kt);
+    const T* pt = arr(a.kt, 5);
     T* gp = a.p + s * (size_t)c;
-    for (int e = tid; e < c; e += nt) gp[e] = pp[a.kt][e];
+#pragma unroll 4
+    for (int e = tid; e < c; e += nt) gp[e] = pt[e];
 }
 
 // ------------------------------------------------------------------ driver

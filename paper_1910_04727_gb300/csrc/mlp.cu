@@ -35,7 +35,7 @@ constexpr int kH = 256;          // hidden width
 constexpr int kGm = 128;         // GEMM tile rows (MMA M)
 constexpr int kGk = 64;          // K per stage
 constexpr int kGStages = 2;
-constexpr int kMaxBatch = 1024;  // training mini-batch capacity (leading dimension of transposed operands)
+constexpr int kMaxBatch = 4096;  // training mini-batch capacity (leading dimension of transposed operands)
 constexpr int kLossBatch = 256;  // rows of surrogate_loss_grad
 constexpr int kTrainBN = 64;     // N tile of the training GEMMs (more CTAs on small problems)
 constexpr int kEvalBN = 256;     // N tile of the inference GEMMs
@@ -764,7 +764,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     FM_CHECK_ARG(ctx, ctx->basis_ready, "surrogate_train: no KL basis installed");
     const int batch = opts->batch > 0 ? opts->batch : 256;
     FM_CHECK_ARG(ctx, batch % 128 == 0 && batch <= kMaxBatch,
-                 "surrogate_train: batch must be a multiple of 128 and at most 1024");
+                 "surrogate_train: batch must be a multiple of 128 and at most 4096");
     FM_CHECK_ARG(ctx, opts->n_train >= batch && opts->epochs >= 1 && opts->lr > 0,
                  "surrogate_train: need n_train >= batch, epochs >= 1, lr > 0");
     const auto t0 = std::chrono::steady_clock::now();
