@@ -319,10 +319,13 @@ def time_estimates(torch, ctx, eps, args, wl, steps, warmup, flush, profile=Fals
     def estimate():
         if not sur:
             return ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, batched=batched)
-        rep = ctx.surrogate_train(**SURROGATE_TRAIN)
+        # the training steps run on the network's stream beside the estimate's
+        # first round (its solves need no network); the surrogate level and
+        # level 0 wait for the last step on the device
+        ctx.surrogate_train(**SURROGATE_TRAIN, async_run=True)
         r = ctx.mlmc_estimate(eps, qmc=qmc, n_pilot=n_pilot, surrogate=True, surrogate_cost=cost,
                               batched=batched)
-        r["train"] = rep
+        r["train"] = ctx.surrogate_train_finish()
         r["surrogate_cost"] = cost
         r["surrogate_cost_measured"] = measured
         return r
@@ -479,10 +482,10 @@ def c5_leg(torch, fm, flush, steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             if sur:
-                rep_ = ctx.surrogate_train(**SURROGATE_TRAIN)
+                ctx.surrogate_train(**SURROGATE_TRAIN, async_run=True)
                 r = ctx.mlmc_estimate(wl.eps, qmc=True, n_pilot=QMC_PILOT, surrogate=True,
                                       surrogate_cost=SURROGATE_COST, batched=batched)
-                r["train_corr"] = rep_["corr"]
+                r["train_corr"] = ctx.surrogate_train_finish()["corr"]
             else:
                 r = ctx.mlmc_estimate(wl.eps, qmc=True, n_pilot=QMC_PILOT, batched=batched)
             b.record()
@@ -668,9 +671,10 @@ def run_native(args, wl, eps):
         t0 = time.perf_counter()
         ctx2.kl_basis_set_host_ptr(B_host.data_ptr())
         if sur:
-            ctx2.surrogate_train(**SURROGATE_TRAIN)
+            ctx2.surrogate_train(**SURROGATE_TRAIN, async_run=True)
             r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, surrogate=True,
                                    surrogate_cost=results[-1]["surrogate_cost"], batched=batched)
+            ctx2.surrogate_train_finish()
         else:
             r = ctx2.mlmc_estimate(eps, qmc=args.qmc, n_pilot=wl.n_pilot, batched=batched)
         e2e_times.append(time.perf_counter() - t0)

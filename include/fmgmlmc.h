@@ -599,6 +599,7 @@ typedef struct {
     double lr;            /* Adam step, cosine-decayed to 0 over the run */
     uint64_t seed;        /* parameter initialisation and shuffling */
     int32_t batch;        /* mini-batch rows: a multiple of 128, at most 4096 (0: 256) */
+    int32_t async_run;    /* 1: return once the training steps are launched (see surrogate_train) */
 } fm_train_opts;
 
 typedef struct {
@@ -630,8 +631,23 @@ fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const float* d_ta
                               double* host_loss);
 
 /* Train from scratch on n_train level-0 samples of the method (points on a
- * stream of their own, the context's field and solver).  Synchronous. */
+ * stream of their own, the context's field and solver).  The training pairs
+ * are formed synchronously; the training steps run on the network's own
+ * stream.  async_run = 0: returns when training is done, with the whole
+ * report.  async_run = 1: returns once the steps are launched; the report
+ * then holds mu, sd, var_q and steps (the losses, corr and var_residual are
+ * NaN) and surrogate_train_finish gives the rest.  Meanwhile other work runs
+ * beside the steps (an estimator round solving levels >= 1, say), and every
+ * use of the network (surrogate_eval*, the surrogate level of
+ * mlmc_sample_level and mlmc_estimate, surrogate_params, a new training)
+ * waits for the steps to end: on the device where it is asynchronous, on the
+ * host otherwise.  The network's state is the same either way. */
 fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* report);
+
+/* End of a training run launched with async_run = 1: waits for its steps,
+ * fills the whole report (report nullable) and releases the run's buffers.
+ * FM_EINVAL if no run is in flight. */
+fm_status surrogate_train_finish(fm_ctx* ctx, fm_train_report* report);
 
 /* d_s[s] = S(d_xi[s]) for n rows of FP64 KL coefficients [n][M]. */
 fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream);

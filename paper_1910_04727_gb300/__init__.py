@@ -397,10 +397,17 @@ class Context:
                                                 g.ctypes.data_as(C.c_void_p), C.byref(loss)))
         return loss.value, g
 
-    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7, batch=256):
-        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed, batch)
+    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7, batch=256, async_run=False):
+        """async_run: return once the training steps are launched (the report's
+        losses and fit are NaN until surrogate_train_finish)."""
+        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed, batch, int(bool(async_run)))
         rep = _lib.FmTrainReport()
         self._check(self._L.surrogate_train(self._h, C.byref(opts), C.byref(rep)))
+        return {f: getattr(rep, f) for f, _ in _lib.FmTrainReport._fields_}
+
+    def surrogate_train_finish(self):
+        rep = _lib.FmTrainReport()
+        self._check(self._L.surrogate_train_finish(self._h, C.byref(rep)))
         return {f: getattr(rep, f) for f, _ in _lib.FmTrainReport._fields_}
 
     def surrogate_eval(self, xi):
@@ -424,8 +431,9 @@ class Context:
         bytes of all ranks, every request is shared among the ranks and the level
         sums are exchanged once per round; all ranks return the same estimate.
         L_start: grow the finest level from L_start by the bias test (alpha > 0 fixes
-        the weak rate, else it is fitted)."""
-        torch.cuda.synchronize()
+        the weak rate, else it is fitted).  The library orders the estimate after
+        earlier work of the legacy default stream; a surrogate training launched
+        with async_run keeps running beside it."""
         opts = _lib.FmEstimateOpts(eps, int(bool(qmc)), n_pilot, max_rounds, int(bool(surrogate)),
                                    surrogate_cost, int(bool(batched)), int(L_start is not None),
                                    L_start or 0, alpha)

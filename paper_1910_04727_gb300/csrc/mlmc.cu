@@ -257,7 +257,7 @@ struct GpuSampler {
 
 fm_status gpu_enqueue(void* user, int32_t e, uint64_t first, uint64_t n, int32_t shift) {
     GpuSampler* g = static_cast<GpuSampler*>(user);
-    if (g->batched && e - g->off >= 0) {
+    if (g->batched) {
         g->pending.push_back(Request{e, first, n, shift});
         return FM_OK;
     }
@@ -281,7 +281,8 @@ fm_status flush_batched(GpuSampler* g) {
     const int L = ctx->cfg.n_levels, M = ctx->cfg.M;
     const fm_solve_params prm = solve_params(ctx);
     std::vector<uint64_t> total(L, 0);
-    for (const Request& r : g->pending) total[r.e - g->off] += r.n;
+    for (const Request& r : g->pending)
+        if (r.e - g->off >= 0) total[r.e - g->off] += r.n;
     if (!g->b0) {
         cudaEventCreate(&g->b0);
         cudaEventCreate(&g->b1);
@@ -299,9 +300,9 @@ fm_status flush_batched(GpuSampler* g) {
         passes = std::max<uint64_t>(passes, (total[l] + chunk[l] - 1) / chunk[l]);
         LevelBuf& b = g->lb[l];
         if (b.cap < total[l] || b.kcap < chunk[l]) {
-            cudaFree(b.xi);
-            cudaFree(b.K);
-            cudaFree(b.q);
+            if (b.xi) cudaFree(b.xi);
+            if (b.K) cudaFree(b.K);
+            if (b.q) cudaFree(b.q);
             b.xi = b.K = b.q = nullptr;
             b.cap = b.kcap = 0;
             if (cudaMalloc((void**)&b.xi, total[l] * M * sizeof(double)) != cudaSuccess ||
@@ -344,8 +345,11 @@ fm_status flush_batched(GpuSampler* g) {
         }
         FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
     }
-    // level-0 surrogate values, then the sums of every request
-    for (int l = 0; l < L; ++l) {
+    // the sums of every request: levels >= 1, then level 0 (with the
+    // surrogate, Y_0 = Q_0 - S) and the surrogate level, whose network may
+    // still be training on its own stream (they wait for it on the device)
+    for (int k = 0; k < L; ++k) {
+        const int l = (k + 1) % L;
         if (!total[l]) continue;
         LevelBuf& b = g->lb[l];
         uint64_t o = 0;
@@ -362,6 +366,19 @@ fm_status flush_batched(GpuSampler* g) {
             FM_TRY(level_sums_add(ctx, (uint32_t)r.n, qf, qc, (l > 0 || with_s) ? 1 : 0, cell, nullptr));
             o += r.n;
         }
+    }
+    for (const Request& r : g->pending) {
+        if (r.e - g->off >= 0) continue;
+        cudaEvent_t e0 = g->event(), e1 = g->event();
+        g->lev.push_back(r.e);
+        cudaEventRecord(e0, nullptr);
+        fm_level_sums* cell = ctx->d_sums + (size_t)r.e * g->R + (r.shift < 0 ? 0 : r.shift);
+        for (uint64_t done = 0; done < r.n;) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(r.n - done, (uint64_t)1 << 30);
+            FM_TRY(mlmc_sample_level(ctx, r.e - g->off, r.first + done, cnt, r.shift, cell, nullptr, nullptr, nullptr));
+            done += cnt;
+        }
+        cudaEventRecord(e1, nullptr);
     }
     cudaEventRecord(g->b1, nullptr);
     g->pending.clear();

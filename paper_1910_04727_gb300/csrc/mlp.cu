@@ -434,9 +434,40 @@ struct MlpState {
     int* err = nullptr;
     int* step = nullptr;               // device step counter of a training run
     cudaStream_t st = nullptr;         // training stream (graph capture)
+    // A training run whose steps may still be running on `st` (launched with
+    // fm_train_opts.async_run): every use of the network waits for `trained`
+    // on its stream, host-side uses wait on the host.  The run's buffers and
+    // graph live until surrogate_train_finish (or the next run) releases them.
+    struct Run {
+        bool pending = false;          // steps launched, not yet finished
+        cudaEvent_t trained = nullptr; // recorded after the last step
+        double* xi = nullptr;          // training inputs [n][M] (the fit report evaluates on them)
+        float* tt = nullptr;           // standardised targets
+        int32_t* perm = nullptr;       // shuffles of every epoch
+        float* sq0 = nullptr;          // squared errors of the first step's batch
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<double> hq;        // targets Q_0 on the host
+        int n = 0, batch = 0;
+        fm_train_report rep{};         // fields known at launch
+        std::chrono::steady_clock::time_point t0;
+    } run;
 };
 
 static MlpState* state(fm_ctx* ctx) { return reinterpret_cast<MlpState*>(ctx->mlp); }
+
+// Device-side ordering after a training run still in flight: work on `st`
+// that reads the network waits for its last step (no host wait).
+static void wait_trained(MlpState* S, cudaStream_t st) {
+    if (S && S->run.pending) cudaStreamWaitEvent(st, S->run.trained, 0);
+}
+
+// Host-side: wait until a training run in flight has finished its steps.
+static void settle(MlpState* S) {
+    if (S && S->run.pending) cudaEventSynchronize(S->run.trained);
+}
+
+static fm_status train_finish(fm_ctx* ctx, fm_train_report* rep);
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn_mlp() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -551,7 +582,12 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
     al((void**)&S->eout, (size_t)kEvalChunk * 4);
     al((void**)&S->err, 4);
     al((void**)&S->step, 4);
-    if (ok && cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+    // the training stream at the highest priority: a run beside an estimator
+    // round gets its small, latency-bound steps scheduled ahead of the
+    // round's wide launches instead of queueing behind them
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (ok && cudaStreamCreateWithPriority(&S->st, cudaStreamNonBlocking, hi) != cudaSuccess) ok = false;
     if (!ok) {
         set_error(ctx, "surrogate: device allocation failed");
         return FM_ENOMEM;
@@ -632,6 +668,7 @@ static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = fal
 template <class Fill>
 static void eval_chunks(fm_ctx* ctx, uint32_t n, Fill fill, double* d_s, cudaStream_t st) {
     MlpState* S = state(ctx);
+    wait_trained(S, st);
     for (uint32_t o = 0; o < n; o += kEvalChunk) {
         const int cnt = (int)std::min<uint32_t>(kEvalChunk, n - o);
         fill(o, cnt, st);
@@ -689,6 +726,8 @@ int surrogate_err_flag(const fm_ctx* ctx) {
 void mlp_free(fm_ctx* ctx) {
     MlpState* S = state(ctx);
     if (!S) return;
+    train_finish(ctx, nullptr);
+    if (S->run.trained) cudaEventDestroy(S->run.trained);
     void* ptrs[] = {S->P, S->G, S->Am, S->Av, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b, S->X, S->XT,
                     S->t, S->out, S->dout, S->sq, S->eX, S->eout, S->err, S->step};
     if (S->st) cudaStreamDestroy(S->st);
@@ -709,6 +748,7 @@ extern "C" fm_status surrogate_params(fm_ctx* ctx, float* host_params, int32_t s
     FM_CHECK_ARG(ctx, ctx != nullptr && host_params != nullptr, "surrogate_params: null argument");
     FM_TRY(mlp_alloc(ctx));
     MlpState* S = state(ctx);
+    settle(S);
     if (set) {
         FM_CUDA_TRY(ctx, cudaMemcpy(S->P, host_params, S->np * 4, cudaMemcpyHostToDevice));
         refresh_bf16(ctx, nullptr);
@@ -729,6 +769,7 @@ extern "C" int64_t surrogate_param_count(const fm_ctx* ctx) {
 extern "C" fm_status surrogate_set_scale(fm_ctx* ctx, double mu, double sd) {
     FM_CHECK_ARG(ctx, ctx != nullptr && sd > 0, "surrogate_set_scale: bad argument");
     FM_TRY(mlp_alloc(ctx));
+    settle(state(ctx));
     state(ctx)->mu = mu;
     state(ctx)->sd = sd;
     return FM_OK;
@@ -739,6 +780,7 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
     FM_CHECK_ARG(ctx, ctx != nullptr && d_xi && d_target, "surrogate_loss_grad: null argument");
     FM_TRY(mlp_alloc(ctx));
     MlpState* S = state(ctx);
+    settle(S);
     FM_CUDA_TRY(ctx, cudaMemset(S->err, 0, 4));
     k_gather_x<<<nb((size_t)kLossBatch * S->D), 256>>>(kLossBatch, S->M, S->D, d_xi, S->X, S->XT, kMaxBatch);
     FM_CUDA_TRY(ctx, cudaMemcpy(S->t, d_target, kLossBatch * 4, cudaMemcpyDeviceToDevice));
@@ -759,6 +801,90 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
     return FM_OK;
 }
 
+namespace fm {
+
+// The end of a training run: wait for its steps, read the first and last
+// mini-batch losses, evaluate the fit on the training set, release the run's
+// buffers and graph.  rep (nullable) receives the whole report.
+static fm_status train_finish(fm_ctx* ctx, fm_train_report* rep) {
+    MlpState* S = state(ctx);
+    if (!S || !S->run.pending) return FM_OK;
+    MlpState::Run& R = S->run;
+    fm_status stt = FM_OK;
+    if (cudaEventSynchronize(R.trained) != cudaSuccess) stt = FM_ECUDA;
+    const int n = R.n, batch = R.batch;
+    auto mean_sq = [&](const float* d) {
+        std::vector<float> sq(batch);
+        cudaMemcpy(sq.data(), d, batch * 4, cudaMemcpyDeviceToHost);
+        double l = 0.0;
+        for (float v : sq) l += v;
+        return l / batch;
+    };
+    double first_loss = NAN, last_loss = NAN, corr = NAN, var_res = NAN;
+    if (stt == FM_OK) {
+        first_loss = mean_sq(R.sq0);
+        last_loss = mean_sq(S->sq);
+    }
+    R.pending = false;   // the network is final from here on
+    if (stt == FM_OK && surrogate_err_flag(ctx)) {
+        set_error(ctx, "surrogate_train: a bounded tensor-core wait ran out");
+        stt = FM_ETIMEOUT;
+    }
+    if (stt == FM_OK) {
+        S->ready = true;
+        // fit on the training set: correlation of S with Q_0
+        double* sv = nullptr;
+        if (cudaMalloc((void**)&sv, (size_t)n * 8) != cudaSuccess) {
+            stt = FM_ENOMEM;
+        } else {
+            eval_forward(ctx, n, R.xi, sv, nullptr);
+            std::vector<double> hs(n);
+            cudaMemcpy(hs.data(), sv, (size_t)n * 8, cudaMemcpyDeviceToHost);
+            cudaFree(sv);
+            const std::vector<double>& hq = R.hq;
+            double ms = 0.0, mu = 0.0, cov = 0.0, vs = 0.0, vq = 0.0, vr = 0.0;
+            for (int i = 0; i < n; ++i) {
+                ms += hs[i];
+                mu += hq[i];
+            }
+            ms /= n;
+            mu /= n;
+            for (int i = 0; i < n; ++i) {
+                cov += (hs[i] - ms) * (hq[i] - mu);
+                vs += (hs[i] - ms) * (hs[i] - ms);
+                vq += (hq[i] - mu) * (hq[i] - mu);
+                vr += (hq[i] - hs[i]) * (hq[i] - hs[i]);
+            }
+            corr = cov / std::sqrt(vs * vq + 1e-300);
+            var_res = vr / (n - 1);
+        }
+    }
+    if (rep) {
+        *rep = R.rep;
+        rep->loss_first = first_loss;
+        rep->loss_last = last_loss;
+        rep->corr = corr;
+        rep->var_residual = var_res;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - R.t0).count();
+    }
+    if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.graph) cudaGraphDestroy(R.graph);
+    cudaFree(R.xi);
+    cudaFree(R.tt);
+    cudaFree(R.perm);
+    cudaFree(R.sq0);
+    R.exec = nullptr;
+    R.graph = nullptr;
+    R.xi = nullptr;
+    R.tt = nullptr;
+    R.perm = nullptr;
+    R.sq0 = nullptr;
+    R.hq.clear();
+    return stt;
+}
+
+}  // namespace fm
+
 extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* rep) {
     FM_CHECK_ARG(ctx, ctx != nullptr && opts != nullptr, "surrogate_train: null argument");
     FM_CHECK_ARG(ctx, ctx->basis_ready, "surrogate_train: no KL basis installed");
@@ -769,13 +895,19 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
                  "surrogate_train: need n_train >= batch, epochs >= 1, lr > 0");
     const auto t0 = std::chrono::steady_clock::now();
     FM_TRY(mlp_alloc(ctx));
+    FM_TRY(train_finish(ctx, nullptr));   // a run still in flight ends first
     MlpState* S = state(ctx);
+    MlpState::Run& R = S->run;
     const int n = opts->n_train, M = ctx->cfg.M;
     // training pairs (xi, Q_0) from the method: level-0 FMG solves on a stream of their own
     double *xi = nullptr, *q = nullptr, *K = nullptr;
     const int N0 = grid_of_level(ctx, 0);
     FM_CUDA_TRY(ctx, cudaMalloc((void**)&xi, (size_t)n * M * 8));
-    FM_CUDA_TRY(ctx, cudaMalloc((void**)&q, (size_t)n * 8));
+    if (cudaMalloc((void**)&q, (size_t)n * 8) != cudaSuccess) {
+        cudaFree(xi);
+        set_error(ctx, "surrogate_train: device allocation failed");
+        return FM_ENOMEM;
+    }
     fm_status stt = FM_OK;
     {
         const uint32_t chunk = 65536;
@@ -790,8 +922,10 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     }
     std::vector<double> hq(n);
     if (stt == FM_OK && cudaMemcpy(hq.data(), q, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) stt = FM_ECUDA;
+    cudaFree(K);
+    cudaFree(q);
     if (stt != FM_OK) {
-        cudaFree(xi); cudaFree(q); cudaFree(K);
+        cudaFree(xi);
         return stt;
     }
     double mu = 0.0, var = 0.0;
@@ -803,9 +937,6 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     S->sd = sd > 0 ? sd : 1.0;
     std::vector<float> ht(n);
     for (int i = 0; i < n; ++i) ht[i] = (float)((hq[i] - mu) / S->sd);
-    float* tt = nullptr;
-    FM_CUDA_TRY(ctx, cudaMalloc((void**)&tt, (size_t)n * 4));
-    cudaMemcpy(tt, ht.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
     // initial parameters U(-1/sqrt(fan_in), 1/sqrt(fan_in)), Adam state zero
     std::mt19937_64 gen(opts->seed);
     std::uniform_real_distribution<double> uni(0.0, 1.0);
@@ -825,21 +956,25 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         std::iota(pe, pe + n, 0);
         std::shuffle(pe, pe + n, gen);
     }
-    int32_t* dperm = nullptr;
+    // the run's state: from here on train_finish releases it
+    R.xi = xi;
+    R.hq = std::move(hq);
+    R.n = n;
+    R.batch = batch;
+    R.t0 = t0;
+    R.rep = fm_train_report{};
+    R.rep.mu = mu;
+    R.rep.sd = S->sd;
+    R.rep.var_q = var / (n - 1);
+    R.rep.steps = total;
+    if (!R.trained) FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&R.trained, cudaEventDisableTiming));
     cudaStream_t ts = S->st;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    double first_loss = NAN, last_loss = NAN;
-    auto batch_loss = [&]() -> double {
-        std::vector<float> sq(batch);
-        cudaMemcpy(sq.data(), S->sq, batch * 4, cudaMemcpyDeviceToHost);
-        double l = 0.0;
-        for (float v : sq) l += v;
-        return l / batch;
-    };
-    auto run = [&]() -> fm_status {
-        FM_CUDA_TRY(ctx, cudaMalloc((void**)&dperm, perm.size() * 4));
-        FM_CUDA_TRY(ctx, cudaMemcpy(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
+    auto launch_run = [&]() -> fm_status {
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.tt, (size_t)n * 4));
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.perm, perm.size() * 4));
+        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.sq0, (size_t)batch * 4));
+        FM_CUDA_TRY(ctx, cudaMemcpy(R.tt, ht.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+        FM_CUDA_TRY(ctx, cudaMemcpy(R.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
         FM_CUDA_TRY(ctx, cudaMemcpy(S->P, hp.data(), S->np * 4, cudaMemcpyHostToDevice));
         FM_CUDA_TRY(ctx, cudaMemset(S->Am, 0, S->np * 4));
         FM_CUDA_TRY(ctx, cudaMemset(S->Av, 0, S->np * 4));
@@ -858,71 +993,48 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         // programmatic dependent launches: every kernel's launch and setup
         // overlap its predecessor (kernels wait for it before touching data)
         launch(true, k_train_batch, dim3(nb((size_t)batch * S->D)), dim3(256), 0, ts, batch, M, S->D, kMaxBatch, n,
-               spe, (const int*)S->step, (const int32_t*)dperm, (const double*)xi, (const float*)tt, S->X, S->XT, S->t);
+               spe, (const int*)S->step, (const int32_t*)R.perm, (const double*)R.xi, (const float*)R.tt, S->X,
+               S->XT, S->t);
         train_step_grads(ctx, batch, ts, true);
         launch(true, k_adam_step, dim3(nb(S->np)), dim3(256), 0, ts, aa);
         launch(true, k_tick, dim3(1), dim3(1), 0, ts, S->step);
-        const cudaError_t ce = cudaStreamEndCapture(ts, &graph);
+        const cudaError_t ce = cudaStreamEndCapture(ts, &R.graph);
         ctx->prof.active = prof_on;
         FM_CUDA_TRY(ctx, ce);
-        FM_CUDA_TRY(ctx, cudaGraphInstantiate(&exec, graph, 0));
+        FM_CUDA_TRY(ctx, cudaGraphInstantiate(&R.exec, R.graph, 0));
         const int pidx = prof_start(ctx, kFamMlpTrain, ts);
-        FM_CUDA_TRY(ctx, cudaGraphLaunch(exec, ts));
-        FM_CUDA_TRY(ctx, cudaStreamSynchronize(ts));
-        first_loss = batch_loss();
-        for (int k = 1; k < total; ++k) FM_CUDA_TRY(ctx, cudaGraphLaunch(exec, ts));
+        FM_CUDA_TRY(ctx, cudaGraphLaunch(R.exec, ts));
+        // the first step's batch errors, for the report
+        FM_CUDA_TRY(ctx, cudaMemcpyAsync(R.sq0, S->sq, (size_t)batch * 4, cudaMemcpyDeviceToDevice, ts));
+        for (int k = 1; k < total; ++k) FM_CUDA_TRY(ctx, cudaGraphLaunch(R.exec, ts));
         const double D = S->D;
         prof_stop(ctx, pidx, ts, 0.0, (double)total * 2.0 * batch * (2.0 * D * kH + 6.0 * kH * kH));
-        FM_CUDA_TRY(ctx, cudaStreamSynchronize(ts));
-        last_loss = batch_loss();
+        FM_CUDA_TRY(ctx, cudaEventRecord(R.trained, ts));
         return FM_OK;
     };
-    stt = run();
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaFree(dperm);
-    cudaFree(tt);
-    cudaFree(K);
-    cudaFree(q);
+    R.pending = true;   // train_finish releases whatever launch_run allocated
+    S->ready = true;    // users of the network wait for R.trained
+    stt = launch_run();
     if (stt != FM_OK) {
-        cudaFree(xi);
+        cudaStreamSynchronize(ts);
+        train_finish(ctx, nullptr);
         return stt;
     }
-    FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
-    if (surrogate_err_flag(ctx)) {
-        cudaFree(xi);
-        set_error(ctx, "surrogate_train: a bounded tensor-core wait ran out");
-        return FM_ETIMEOUT;
+    if (opts->async_run) {
+        if (rep) {   // the fields known now; surrogate_train_finish gives the rest
+            *rep = R.rep;
+            rep->loss_first = rep->loss_last = rep->corr = rep->var_residual = NAN;
+            rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        return FM_OK;
     }
-    S->ready = true;
-    // fit on the training set: correlation of S with Q_0
-    double* sv = nullptr;
-    cudaMalloc((void**)&sv, (size_t)n * 8);
-    eval_forward(ctx, n, xi, sv, nullptr);
-    std::vector<double> hs(n);
-    cudaMemcpy(hs.data(), sv, (size_t)n * 8, cudaMemcpyDeviceToHost);
-    cudaFree(sv);
-    cudaFree(xi);
-    double ms = 0.0, cov = 0.0, vs = 0.0, vr = 0.0;
-    for (int i = 0; i < n; ++i) ms += hs[i];
-    ms /= n;
-    for (int i = 0; i < n; ++i) {
-        cov += (hs[i] - ms) * (hq[i] - mu);
-        vs += (hs[i] - ms) * (hs[i] - ms);
-        vr += (hq[i] - hs[i]) * (hq[i] - hs[i]);
-    }
-    if (rep) {
-        rep->loss_first = first_loss;
-        rep->loss_last = last_loss;
-        rep->mu = mu;
-        rep->sd = S->sd;
-        rep->corr = cov / std::sqrt(vs * var + 1e-300);
-        rep->var_q = var / (n - 1);
-        rep->var_residual = vr / (n - 1);
-        rep->steps = total;
-        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
-    return FM_OK;
+    return train_finish(ctx, rep);
+}
+
+extern "C" fm_status surrogate_train_finish(fm_ctx* ctx, fm_train_report* rep) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_train_finish: null context");
+    FM_CHECK_ARG(ctx, ctx->mlp && state(ctx)->run.pending, "surrogate_train_finish: no training run in flight");
+    return train_finish(ctx, rep);
 }
 
 extern "C" fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream) {
