@@ -279,8 +279,8 @@ __global__ void k_mlp_out_back(int B, int ldt, const float* __restrict__ dout, c
 // fixed order): gb[j] = sum_b w[b] T[j][b], with w = 1 when null.  With
 // ones_row, warp N also writes gb[N] = sum_b w[b] (the output bias).
 __global__ void k_row_sums(int N, int B, int ldt, const __nv_bfloat16* __restrict__ T, const float* __restrict__ w,
-                           float* __restrict__ gb, float* __restrict__ ones_row) {    pdl_wait_then_release();
-
+                           float* __restrict__ gb, float* __restrict__ ones_row) {
+    pdl_wait_then_release();
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (j > N || (j == N && !ones_row)) return;
     float acc = 0.0f;
@@ -434,6 +434,10 @@ struct MlpState {
     int* err = nullptr;
     int* step = nullptr;               // device step counter of a training run
     cudaStream_t st = nullptr;         // training stream (graph capture)
+    // the weight- and bias-gradient kernels of a step run on `side`, beside
+    // the back-propagation chain on the step's stream (fork / join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_dz2 = nullptr, ev_dz1 = nullptr, ev_join = nullptr;
     // A training run whose steps may still be running on `st` (launched with
     // fm_train_opts.async_run): every use of the network waits for `trained`
     // on its stream, host-side uses wait on the host.  The run's buffers and
@@ -588,6 +592,9 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (ok && cudaStreamCreateWithPriority(&S->st, cudaStreamNonBlocking, hi) != cudaSuccess) ok = false;
+    if (ok && cudaStreamCreateWithPriority(&S->side, cudaStreamNonBlocking, hi) != cudaSuccess) ok = false;
+    for (cudaEvent_t* e : {&S->ev_fork, &S->ev_dz2, &S->ev_dz1, &S->ev_join})
+        if (ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) ok = false;
     if (!ok) {
         set_error(ctx, "surrogate: device allocation failed");
         return FM_ENOMEM;
@@ -627,11 +634,18 @@ static void refresh_bf16(fm_ctx* ctx, cudaStream_t st) {
 }
 
 // Forward + backward of one batch of B rows (a multiple of 128, <= kMaxBatch)
-// already in S->X / S->XT / S->t; gradients into S->G.
+// already in S->X / S->XT / S->t; gradients into S->G.  The chain that
+// back-propagates (dZ3 -> dZ2 -> dZ1 -> dW1) runs on st; the other weight
+// and bias gradients, which nothing downstream reads but Adam, run beside it
+// on S->side (forked after the output layer, joined at the end), so a
+// training step's critical path is 11 kernels (batch gather, three forward
+// GEMMs, output layer, its gradient, dZ2, dZ1, dW1, Adam, step counter)
+// instead of 17.
 static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = false) {
     MlpState* S = state(ctx);
     const int D = S->D, L = kMaxBatch;
     constexpr int BN = kTrainBN;
+    cudaStream_t sd = S->side;
     EpiArgs e{};
     // forward: Z_l = H_(l-1) W_l^T + b_l, H_l = bf16(gelu(Z_l))
     e = EpiArgs{B, kH, S->P + S->off[1], S->Z[0], kH, S->H[0], kH, S->HT[0], L, nullptr, 0};
@@ -640,27 +654,41 @@ static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = fal
     gemm<BN, kEpiFwdGelu>(ctx, S->mH1, S->tW2, B, kH, kH, e, st, pdl);
     e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], L, nullptr, 0};
     gemm<BN, kEpiFwdGelu>(ctx, S->mH2, S->tW3, B, kH, kH, e, st, pdl);
-    launch(pdl, k_mlp_out, dim3(nb((size_t)B * 32)), dim3(256), 0, st, B, S->H[2], S->w4b, S->P + S->off[7], S->t, S->out, S->dout, S->sq);
-    // output layer: gw4 = dout^T H3, gb4 = sum dout, dZ3 = bf16(dout w4 gelu'(Z3))
-    launch(pdl, k_row_sums, dim3(nb((size_t)(kH + 1) * 32)), dim3(256), 0, st, kH, B, L, S->HT[2], S->dout, S->G + S->off[6],
-                                                          S->G + S->off[7]);
-    launch(pdl, k_mlp_out_back, dim3(nb((size_t)B * kH)), dim3(256), 0, st, B, L, S->dout, S->w4b, S->Z[2], S->dZ[2], S->dZT[2]);
-    // layer 3: dW3 = dZ3^T H2, db3, dZ2 = bf16((dZ3 W3) gelu'(Z2))
+    launch(pdl, k_mlp_out, dim3(nb((size_t)B * 32)), dim3(256), 0, st, B, S->H[2], S->w4b, S->P + S->off[7], S->t,
+           S->out, S->dout, S->sq);
+    // output layer: dZ3 = bf16(dout w4 gelu'(Z3)) on st; gw4 = dout^T H3, gb4 = sum dout beside it
+    launch(pdl, k_mlp_out_back, dim3(nb((size_t)B * kH)), dim3(256), 0, st, B, L, S->dout, S->w4b, S->Z[2], S->dZ[2],
+           S->dZT[2]);
+    cudaEventRecord(S->ev_fork, st);
+    cudaStreamWaitEvent(sd, S->ev_fork, 0);
+    launch(pdl, k_row_sums, dim3(nb((size_t)(kH + 1) * 32)), dim3(256), 0, sd, kH, B, L, S->HT[2], S->dout,
+           S->G + S->off[6], S->G + S->off[7]);
+    // layer 3: dW3 = dZ3^T H2, db3 beside; dZ2 = bf16((dZ3 W3) gelu'(Z2)) on st
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[4], kH};
-    gemm<BN, kEpiF32>(ctx, S->mdZ3T, S->tH2T, kH, kH, B, e, st, pdl);
-    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[2], nullptr, S->G + S->off[5], nullptr);
+    gemm<BN, kEpiF32>(ctx, S->mdZ3T, S->tH2T, kH, kH, B, e, sd, pdl);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, sd, kH, B, L, S->dZT[2], nullptr,
+           S->G + S->off[5], nullptr);
     e = EpiArgs{B, kH, nullptr, S->Z[1], kH, S->dZ[1], kH, S->dZT[1], L, nullptr, 0};
     gemm<BN, kEpiBwdGelu>(ctx, S->mdZ3, S->tW3T, B, kH, kH, e, st, pdl);
-    // layer 2
+    // layer 2: dW2, db2 beside; dZ1 on st
+    cudaEventRecord(S->ev_dz2, st);
+    cudaStreamWaitEvent(sd, S->ev_dz2, 0);
     e = EpiArgs{kH, kH, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[2], kH};
-    gemm<BN, kEpiF32>(ctx, S->mdZ2T, S->tH1T, kH, kH, B, e, st, pdl);
-    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[1], nullptr, S->G + S->off[3], nullptr);
+    gemm<BN, kEpiF32>(ctx, S->mdZ2T, S->tH1T, kH, kH, B, e, sd, pdl);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, sd, kH, B, L, S->dZT[1], nullptr,
+           S->G + S->off[3], nullptr);
     e = EpiArgs{B, kH, nullptr, S->Z[0], kH, S->dZ[0], kH, S->dZT[0], L, nullptr, 0};
     gemm<BN, kEpiBwdGelu>(ctx, S->mdZ2, S->tW2T, B, kH, kH, e, st, pdl);
-    // layer 1: dW1 = dZ1^T X (N = D input columns; the FP32 gradient keeps the M real ones)
+    // layer 1: db1 beside; dW1 = dZ1^T X on st (N = D input columns; the FP32
+    // gradient keeps the M real ones)
+    cudaEventRecord(S->ev_dz1, st);
+    cudaStreamWaitEvent(sd, S->ev_dz1, 0);
+    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, sd, kH, B, L, S->dZT[0], nullptr,
+           S->G + S->off[1], nullptr);
     e = EpiArgs{kH, S->M, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, S->G + S->off[0], S->M};
     gemm<BN, kEpiF32>(ctx, S->mdZ1T, S->tXT, kH, D, B, e, st, pdl);
-    launch(pdl, k_row_sums, dim3(nb((size_t)kH * 32)), dim3(256), 0, st, kH, B, L, S->dZT[0], nullptr, S->G + S->off[1], nullptr);
+    cudaEventRecord(S->ev_join, sd);
+    cudaStreamWaitEvent(st, S->ev_join, 0);
 }
 
 // Forward of n rows, chunked: fill(o, cnt, st) writes rows o .. o+cnt-1 of
@@ -731,6 +759,9 @@ void mlp_free(fm_ctx* ctx) {
     void* ptrs[] = {S->P, S->G, S->Am, S->Av, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b, S->X, S->XT,
                     S->t, S->out, S->dout, S->sq, S->eX, S->eout, S->err, S->step};
     if (S->st) cudaStreamDestroy(S->st);
+    if (S->side) cudaStreamDestroy(S->side);
+    for (cudaEvent_t e : {S->ev_fork, S->ev_dz2, S->ev_dz1, S->ev_join})
+        if (e) cudaEventDestroy(e);
     for (void* p : ptrs) cudaFree(p);
     for (int l = 0; l < 3; ++l) {
         cudaFree(S->H[l]); cudaFree(S->HT[l]); cudaFree(S->dZ[l]); cudaFree(S->dZT[l]); cudaFree(S->Z[l]);
