@@ -241,8 +241,8 @@ __global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, _
 // 2 (out[b] - t[b]) / B and the squared error.
 __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __nv_bfloat16* __restrict__ w4,
                           const float* __restrict__ b4, const float* __restrict__ t, float* __restrict__ out,
-                          float* __restrict__ dout, float* __restrict__ sq) {    pdl_wait_then_release();
-
+                          float* __restrict__ dout, float* __restrict__ sq) {
+    pdl_wait_then_release();
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (b >= B) return;
     float acc = 0.0f;
@@ -261,18 +261,39 @@ __global__ void k_mlp_out(int B, const __nv_bfloat16* __restrict__ H3, const __n
     }
 }
 
-// Output layer backward: dZ3 = bf16((dout w4) * gelu'(Z3)), row-major and transposed [kH][ldt].
-__global__ void k_mlp_out_back(int B, int ldt, const float* __restrict__ dout, const __nv_bfloat16* __restrict__ w4,
-                               const float* __restrict__ Z3, __nv_bfloat16* __restrict__ dZ,
-                               __nv_bfloat16* __restrict__ dZT) {    pdl_wait_then_release();
-
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= B * kH) return;
-    const int b = t / kH, j = t % kH;
-    const float d = dout[b] * __bfloat162float(w4[j]) * gelu_grad_f(Z3[t]);
-    const __nv_bfloat16 v = __float2bfloat16_rn(d);
-    dZ[t] = v;
-    dZT[(size_t)j * ldt + b] = v;
+// Training: the output layer and its gradient in one pass, one warp per row:
+// out, dout and the squared error as k_mlp_out forms them, then the
+// pre-activation gradient dZ3 = bf16((dout w4) * gelu'(Z3)), row-major and
+// transposed [kH][ldt].
+__global__ void k_mlp_out_train(int B, int ldt, const __nv_bfloat16* __restrict__ H3,
+                                const __nv_bfloat16* __restrict__ w4, const float* __restrict__ b4,
+                                const float* __restrict__ t, float* __restrict__ out, float* __restrict__ dout,
+                                float* __restrict__ sq, const float* __restrict__ Z3, __nv_bfloat16* __restrict__ dZ,
+                                __nv_bfloat16* __restrict__ dZT) {
+    pdl_wait_then_release();
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float acc = 0.0f;
+    for (int j = lane; j < kH; j += 32)
+        acc += __bfloat162float(H3[(size_t)b * kH + j]) * __bfloat162float(w4[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    float dv = 0.0f;
+    if (lane == 0) {
+        const float o = acc + b4[0];
+        out[b] = o;
+        const float d = o - t[b];
+        dv = 2.0f * d / (float)B;
+        dout[b] = dv;
+        sq[b] = d * d;
+    }
+    dv = __shfl_sync(0xffffffffu, dv, 0);
+    for (int j = lane; j < kH; j += 32) {
+        const float d = dv * __bfloat162float(w4[j]) * gelu_grad_f(Z3[(size_t)b * kH + j]);
+        const __nv_bfloat16 v = __float2bfloat16_rn(d);
+        dZ[(size_t)b * kH + j] = v;
+        dZT[(size_t)j * ldt + b] = v;
+    }
 }
 
 // Row sums of a transposed operand, one warp per row j (lanes over the batch,
@@ -333,12 +354,14 @@ __global__ void k_train_batch(int B, int M, int D, int ldt, int n, int spe, cons
 
 // One Adam step (Kingma & Ba) at step number *step of `total`, learning rate
 // lr0 (1 + cos(pi step / total)) / 2, followed by the BF16 operand copies of
-// the updated weights (row-major and, for W2 / W3, transposed).
+// the updated weights (row-major and, for W2 / W3, transposed); the step
+// counter then advances (`done` counts finished blocks, zero between steps).
 struct AdamArgs {
     size_t np;
     float *P, *m, *v;
     const float* g;
-    const int* step;
+    int* step;
+    int* done;
     int total;
     float lr0, b1, b2, eps;
     size_t off[8];
@@ -346,11 +369,8 @@ struct AdamArgs {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W2T, *W3T, *w4b;
 };
 
-__global__ void k_adam_step(AdamArgs a) {    pdl_wait_then_release();
-
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.np) return;
-    const int s = *a.step;
+// One parameter's Adam update at step s, and its BF16 operand copies.
+__device__ __forceinline__ void adam_update(const AdamArgs& a, size_t t, int s) {
     const float k = (float)(s + 1);
     const float lr = a.lr0 * 0.5f * (1.0f + cospif((float)s / (float)a.total));
     const float c1 = 1.0f - powf(a.b1, k), c2 = 1.0f - powf(a.b2, k);
@@ -377,9 +397,21 @@ __global__ void k_adam_step(AdamArgs a) {    pdl_wait_then_release();
     }
 }
 
-__global__ void k_tick(int* step) {
+__global__ void k_adam_step(AdamArgs a) {
     pdl_wait_then_release();
-    *step += 1;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = *a.step;
+    if (t < a.np) adam_update(a, t, s);
+    // the last block to finish advances the step counter (every block has
+    // read it by then) and re-arms the block count for the next step
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
+            *a.step = s + 1;
+            *a.done = 0;
+        }
+    }
 }
 
 // X[b][k] = bf16(Phi^-1(u)) for the MC sample first + b of Philox stream
@@ -432,7 +464,7 @@ struct MlpState {
     CUtensorMap meX, meH1, meH2, eW1, eW2, eW3;
     double mu = 0.0, sd = 1.0;
     int* err = nullptr;
-    int* step = nullptr;               // device step counter of a training run
+    int* step = nullptr;               // device step counter of a training run; step[1]: Adam's block count
     cudaStream_t st = nullptr;         // training stream (graph capture)
     // the weight- and bias-gradient kernels of a step run on `side`, beside
     // the back-propagation chain on the step's stream (fork / join events)
@@ -585,7 +617,7 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
     al((void**)&S->eX, (size_t)kEvalChunk * D * 2);
     al((void**)&S->eout, (size_t)kEvalChunk * 4);
     al((void**)&S->err, 4);
-    al((void**)&S->step, 4);
+    al((void**)&S->step, 8);
     // the training stream at the highest priority: a run beside an estimator
     // round gets its small, latency-bound steps scheduled ahead of the
     // round's wide launches instead of queueing behind them
@@ -638,9 +670,9 @@ static void refresh_bf16(fm_ctx* ctx, cudaStream_t st) {
 // back-propagates (dZ3 -> dZ2 -> dZ1 -> dW1) runs on st; the other weight
 // and bias gradients, which nothing downstream reads but Adam, run beside it
 // on S->side (forked after the output layer, joined at the end), so a
-// training step's critical path is 11 kernels (batch gather, three forward
-// GEMMs, output layer, its gradient, dZ2, dZ1, dW1, Adam, step counter)
-// instead of 17.
+// training step's critical path is 9 kernels (batch gather, three forward
+// GEMMs, the output layer with its gradient, dZ2, dZ1, dW1, Adam with the
+// step counter) instead of 17.
 static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = false) {
     MlpState* S = state(ctx);
     const int D = S->D, L = kMaxBatch;
@@ -654,11 +686,9 @@ static void train_step_grads(fm_ctx* ctx, int B, cudaStream_t st, bool pdl = fal
     gemm<BN, kEpiFwdGelu>(ctx, S->mH1, S->tW2, B, kH, kH, e, st, pdl);
     e = EpiArgs{B, kH, S->P + S->off[5], S->Z[2], kH, S->H[2], kH, S->HT[2], L, nullptr, 0};
     gemm<BN, kEpiFwdGelu>(ctx, S->mH2, S->tW3, B, kH, kH, e, st, pdl);
-    launch(pdl, k_mlp_out, dim3(nb((size_t)B * 32)), dim3(256), 0, st, B, S->H[2], S->w4b, S->P + S->off[7], S->t,
-           S->out, S->dout, S->sq);
-    // output layer: dZ3 = bf16(dout w4 gelu'(Z3)) on st; gw4 = dout^T H3, gb4 = sum dout beside it
-    launch(pdl, k_mlp_out_back, dim3(nb((size_t)B * kH)), dim3(256), 0, st, B, L, S->dout, S->w4b, S->Z[2], S->dZ[2],
-           S->dZT[2]);
+    // output layer and dZ3 = bf16(dout w4 gelu'(Z3)) on st; gw4 = dout^T H3, gb4 = sum dout beside it
+    launch(pdl, k_mlp_out_train, dim3(nb((size_t)B * 32)), dim3(256), 0, st, B, L, S->H[2], S->w4b,
+           S->P + S->off[7], S->t, S->out, S->dout, S->sq, S->Z[2], S->dZ[2], S->dZT[2]);
     cudaEventRecord(S->ev_fork, st);
     cudaStreamWaitEvent(sd, S->ev_fork, 0);
     launch(pdl, k_row_sums, dim3(nb((size_t)(kH + 1) * 32)), dim3(256), 0, sd, kH, B, L, S->HT[2], S->dout,
@@ -1010,12 +1040,12 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         FM_CUDA_TRY(ctx, cudaMemset(S->Am, 0, S->np * 4));
         FM_CUDA_TRY(ctx, cudaMemset(S->Av, 0, S->np * 4));
         FM_CUDA_TRY(ctx, cudaMemset(S->err, 0, 4));
-        FM_CUDA_TRY(ctx, cudaMemset(S->step, 0, 4));
+        FM_CUDA_TRY(ctx, cudaMemset(S->step, 0, 8));
         refresh_bf16(ctx, nullptr);
         FM_CUDA_TRY(ctx, cudaDeviceSynchronize());
         // one training step as a CUDA graph: batch gather, forward, backward,
         // Adam + BF16 refresh, step counter; replayed `total` times
-        AdamArgs aa{S->np, S->P, S->Am, S->Av, S->G, S->step, total, (float)opts->lr, 0.9f, 0.999f, 1e-8f,
+        AdamArgs aa{S->np, S->P, S->Am, S->Av, S->G, S->step, S->step + 1, total, (float)opts->lr, 0.9f, 0.999f, 1e-8f,
                     {}, M, S->D, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b};
         for (int i = 0; i < 8; ++i) aa.off[i] = S->off[i];
         const bool prof_on = ctx->prof.active;
@@ -1028,7 +1058,6 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
                S->XT, S->t);
         train_step_grads(ctx, batch, ts, true);
         launch(true, k_adam_step, dim3(nb(S->np)), dim3(256), 0, ts, aa);
-        launch(true, k_tick, dim3(1), dim3(1), 0, ts, S->step);
         const cudaError_t ce = cudaStreamEndCapture(ts, &R.graph);
         ctx->prof.active = prof_on;
         FM_CUDA_TRY(ctx, ce);
