@@ -438,14 +438,15 @@ __host__ __device__ constexpr int strip_xh(int HS, bool fuse) { return fuse ? HS
 __host__ __device__ constexpr int strip_ow(int HS, bool fuse) { return 64 - 2 * strip_xh(HS, fuse); }
 
 template <typename T, int HS, bool FUSE>
-__global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rbgs_strip(int n, size_t S, int strips, int seg, int segs,
+__global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rbgs_strip(int n, size_t S_all, int strips, int seg_all, int segs_all,
                                                                  const T* __restrict__ b, const T* __restrict__ Te,
                                                                  const T* __restrict__ Tn, const T* __restrict__ D,
                                                                  const T* __restrict__ p_in, T* __restrict__ p_out,
                                                                  const int32_t* __restrict__ active,
                                                                  const T* __restrict__ ec, T* __restrict__ bc,
                                                                  T* __restrict__ pc, const int32_t* __restrict__ order,
-                                                                 int ns) {
+                                                                 int ns, const int32_t* __restrict__ dcount,
+                                                                 int resident) {
     using V2 = typename Pair<T>::type;
     constexpr int R = HS + 2;                       // rows in registers: y - HS - 1 .. y
     constexpr int XH = strip_xh(HS, FUSE), VH = XH;  // halo columns and rows (even)
@@ -459,6 +460,21 @@ __global__ void __launch_bounds__(32 * kStripWarps, sizeof(T) == 4 ? 4 : 1) k_rb
     __shared__ T cring[kStripWarps][DEPTH][34];   // with ec: [0] left of lane 0, [1 + l] lane l, [33] right of lane 31
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    // the samples enumerated and their row segments: as launched, or (dcount:
+    // inside a device-side refinement loop) the count of listed samples the
+    // last residual test left, with segments short enough to fill one wave
+    // of warps when those samples are few
+    size_t S = S_all;
+    int seg = seg_all, segs = segs_all;
+    if (dcount) {
+        S = (size_t)*dcount;
+        if (S * strips < (size_t)resident) {
+            int sg = n;
+            while (sg / 2 >= 16 && S * strips * (size_t)((n + sg / 2 - 1) / (sg / 2)) <= (size_t)resident) sg /= 2;
+            seg = sg;
+            segs = (n + sg - 1) / sg;
+        }
+    }
     const size_t unit = (size_t)blockIdx.x * kStripWarps + (threadIdx.x >> 5);
     if (unit >= S * (size_t)segs * strips) return;   // S: the samples enumerated (listed by order, if given)
     const int sx = (int)(unit % strips);
@@ -1285,6 +1301,10 @@ struct Hierarchy {
     // sizes its row segments for it, so that a launch with few active samples
     // does not march long columns.
     mutable size_t busy = 0;
+    // Device-side count of the samples still iterating (the refinement loop
+    // of a graph, where the host cannot read it): the strip smoother then
+    // enumerates the listed samples itself.
+    mutable const int32_t* dcount = nullptr;
     // launches may enumerate only the listed samples
     bool listed() const { return order && busy > 0 && busy < S; }
 };
@@ -1449,22 +1469,29 @@ static int strip_segment(int n, size_t S, int strips, int HS, int VH, int reside
 template <typename T, int HS, bool FUSE>
 static void strip_launch(fm_ctx* ctx, int n, size_t S, const T* b, const T* Te, const T* Tn, const T* D,
                          const T* p_in, T* p_out, const int32_t* active, const T* ec, T* bc, T* pc,
-                         cudaStream_t st, size_t busy, const int32_t* order, int ns) {
+                         cudaStream_t st, size_t busy, const int32_t* order, int ns, const int32_t* dcount) {
     constexpr int OW = strip_ow(HS, FUSE), VH = strip_xh(HS, FUSE);
     const int strips = (n + OW - 1) / OW;
-    // with the host's count of active samples and their list, enumerate only those
-    const bool listed = order && busy > 0 && busy < S;
+    const int resident = g_strip_warps[sizeof(T) == 4 ? 1 : 0][HS / 2 - 1][FUSE];
+    // with the host's count of active samples and their list, enumerate only
+    // those; with a device-side count (dcount, refinement loops inside a
+    // graph) the kernel enumerates the listed samples itself, and the grid
+    // covers the most units it can form (all samples, or one wave)
+    const bool dev = dcount && order;
+    const bool listed = !dev && order && busy > 0 && busy < S;
     const size_t sb = listed ? busy : S;
-    const int seg = strip_segment(n, sb, strips, HS, VH, g_strip_warps[sizeof(T) == 4 ? 1 : 0][HS / 2 - 1][FUSE]);
+    const int seg = strip_segment(n, sb, strips, HS, VH, resident);
     const int segs = (n + seg - 1) / seg;
-    const size_t units = sb * (size_t)strips * segs, cells = sb * (size_t)n * n;
+    size_t units = sb * (size_t)strips * segs;
+    if (dev) units = std::max(units, (size_t)resident);
+    const size_t cells = sb * (size_t)n * n;
     const unsigned grid = (unsigned)((units + kStripWarps - 1) / kStripWarps);
     const double bytes = (6.0 + (FUSE ? 0.5 : 0.0)) * sizeof(T) * cells;
     const double flops = 5.0 * HS * cells + (FUSE ? 12.0 * cells : 0.0);
     FM_TIMED(ctx, kFamSmootherStrip, st, bytes, flops,
-             k_rbgs_strip<T, HS, FUSE><<<grid, 32 * kStripWarps, 0, st>>>(n, sb, strips, seg, segs, b, Te, Tn, D,
-                                                                         p_in, p_out, active, ec, bc, pc,
-                                                                         listed ? order : nullptr, ns));
+             k_rbgs_strip<T, HS, FUSE><<<grid, 32 * kStripWarps, 0, st>>>(
+                 n, sb, strips, seg, segs, b, Te, Tn, D, p_in, p_out, active, ec, bc, pc,
+                 (listed || dev) ? order : nullptr, ns, dev ? dcount : nullptr, resident));
 }
 
 // Launch shape code of the column-strip smoother (tile codes are > 0, colour
@@ -1489,16 +1516,17 @@ static size_t tile_smem_bytes(int tile, int n, int nsweeps, size_t tsize) {
 template <typename T>
 static T* smooth_with(fm_ctx* ctx, int tile, int threads, int n, size_t S, int nsweeps, const T* b, const T* Te,
                       const T* Tn, const T* D, T* p_in, T* p_out, const int32_t* active, cudaStream_t st,
-                      const T* ec = nullptr, size_t busy = 0, const int32_t* order = nullptr, int ns = 0) {
+                      const T* ec = nullptr, size_t busy = 0, const int32_t* order = nullptr, int ns = 0,
+                      const int32_t* dcount = nullptr) {
     if (nsweeps <= 0) return p_in;
     const size_t cells = S * (size_t)n * n;
     if (tile == kShapeStrip) {
         if (nsweeps == 2)
             strip_launch<T, 4, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
-                                      order, ns);
+                                      order, ns, dcount);
         else
             strip_launch<T, 2, false>(ctx, n, S, b, Te, Tn, D, p_in, p_out, active, ec, nullptr, nullptr, st, busy,
-                                      order, ns);
+                                      order, ns, dcount);
         return p_out;
     }
     if (tile > 0) {
@@ -1642,14 +1670,14 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
         // strips form the residual and its restriction in the same pass
         if (prm.nu1 == 2)
             strip_launch<T, 4, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
-                                     H.order, ns);
+                                     H.order, ns, H.dcount);
         else
             strip_launch<T, 2, true>(ctx, n, S, g.b, Te, Tn, D, g.p, g.p2, active, nullptr, c.b, c.p, st, H.busy,
-                                     H.order, ns);
+                                     H.order, ns, H.dcount);
         cur = g.p2;
     } else {
         cur = smooth_with<T>(ctx, tile, threads, n, S, prm.nu1, g.b, Te, Tn, D, g.p, g.p2, active, st, nullptr,
-                             H.busy, H.order, ns);
+                             H.busy, H.order, ns, H.dcount);
         FM_TIMED(ctx, kFamResidualRestrict, st, 5.5 * ts * cells, 10.0 * cells,
                  k_residual_restrict<T><<<blocks_for(S * (size_t)c.n * c.n), kBlock, 0, st>>>(
                      c.n, S, g.b, Te, Tn, D, cur, c.b, c.p, active));
@@ -1671,7 +1699,7 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
                  k_energy_alpha<<<blocks_for(S), kBlock, 0, st>>>(S, chunks, H.partial, H.alpha, active);
                  k_prolong_step<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, H.alpha, cur, active, ns));
         smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
-                       H.order, ns);
+                       H.order, ns, H.dcount);
         return;
     }
     if (tile == 0 && prm.nu2 >= 1) {
@@ -1687,14 +1715,14 @@ static void vcycle(const Hierarchy<T>& H, int k, int top, const fm_solve_params&
     if (tile != 0 && prm.nu2 >= 1) {
         // tiles and strips: the correction is added as they load the iterate
         smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, c.p, H.busy,
-                       H.order, ns);
+                       H.order, ns, H.dcount);
         return;
     }
     const Ghost<T> zero{T(0), T(0), T(0), T(0), ns};
     FM_TIMED(ctx, kFamProlong, st, 2.25 * ts * cells, 8.0 * cells,
              k_prolong<T><<<blocks_for(cells), kBlock, 0, st>>>(c.n, S, c.p, zero, 1, cur, active));
     smooth_with<T>(ctx, tile, threads, n, S, prm.nu2, g.b, Te, Tn, D, cur, g.p, active, st, nullptr, H.busy,
-                   H.order, ns);
+                   H.order, ns, H.dcount);
 }
 
 template <typename P>
@@ -1769,7 +1797,10 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     cudaStream_t bs = ctx->body_stream;
     FM_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
+    // the body's strips enumerate the samples the last test listed
+    H.dcount = H.order ? H.left : nullptr;
     for (int v = 0; v < cycles_per_test(prm); ++v) vcycle(H, k, k, prm, H.active, bs);
+    H.dcount = nullptr;
     if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active, nullptr);
     test(bs);
     cudaGraph_t body = nullptr;
