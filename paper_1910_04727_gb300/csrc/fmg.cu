@@ -1081,14 +1081,20 @@ __global__ void k_stage_decide(size_t S, int chunks, const double* __restrict__ 
 
 // Mixed form: the FP64 refinement update p64 += e (the FP32 correction).
 template <typename T>
+// Grid-stride over the enumerated cells: S samples (listed by order, if
+// given), or with dcount (inside a graph's refinement loop) the count the
+// last residual test left, so a launch sized for every sample does little
+// work once few of them still iterate.
 __global__ void k_ir_update(size_t cells, size_t S, const T* __restrict__ e, double* __restrict__ p64,
-                            const int32_t* __restrict__ active, const int32_t* __restrict__ order) {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= S * cells) return;   // S: the samples enumerated (listed by order, if given)
-    const size_t s = order ? (size_t)order[t / cells] : t / cells;
-    if (inactive(active, s)) return;
-    const size_t g = s * cells + t % cells;
-    p64[g] += (double)e[g];
+                            const int32_t* __restrict__ active, const int32_t* __restrict__ order,
+                            const int32_t* __restrict__ dcount) {
+    const size_t total = (dcount ? (size_t)*dcount : S) * cells;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = order ? (size_t)order[t / cells] : t / cells;
+        if (inactive(active, s)) continue;
+        const size_t g = s * cells + t % cells;
+        p64[g] += (double)e[g];
+    }
 }
 
 template <typename T>
@@ -1748,6 +1754,14 @@ static void stage_test(const Hierarchy<T>& H, int k, const fm_solve_params& prm,
                                                               H.active, H.left, H.order));
 }
 
+// Blocks of a refinement update over `work` cells: enough to fill the GPU a
+// few times over, the grid-stride loop takes the rest.
+static unsigned ir_update_blocks(const fm_ctx* ctx, size_t work) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    return (unsigned)std::max<size_t>(1, std::min<size_t>(blocks_for(work), (size_t)sms * 16));
+}
+
 // Loop control of a refined stage inside a CUDA graph: after residual test
 // number *it, another pass runs while a sample is still active and fewer than
 // max_cycles tests have been made; the bound ends every loop.
@@ -1801,7 +1815,9 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     H.dcount = H.order ? H.left : nullptr;
     for (int v = 0; v < cycles_per_test(prm); ++v) vcycle(H, k, k, prm, H.active, bs);
     H.dcount = nullptr;
-    if (mixed) k_ir_update<T><<<blocks_for(S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active, nullptr);
+    if (mixed)
+        k_ir_update<T><<<ir_update_blocks(ctx, S * cells), kBlock, 0, bs>>>(cells, S, g.p, g.p64, H.active,
+                                                                              H.order, H.order ? H.left : nullptr);
     test(bs);
     cudaGraph_t body = nullptr;
     FM_CUDA_TRY(ctx, cudaStreamEndCapture(bs, &body));
@@ -1835,8 +1851,8 @@ static fm_status refine_stage(const Hierarchy<T>& H, int k, const fm_solve_param
         }
         for (int v = 0; v < cycles_per_test(prm); ++v) vcycle(H, k, k, prm, H.active, st);
         if (mixed)
-            k_ir_update<T><<<blocks_for((H.listed() ? H.busy : S) * cells), kBlock, 0, st>>>(
-                cells, H.listed() ? H.busy : S, g.p, g.p64, H.active, H.listed() ? H.order : nullptr);
+            k_ir_update<T><<<ir_update_blocks(ctx, (H.listed() ? H.busy : S) * cells), kBlock, 0, st>>>(
+                cells, H.listed() ? H.busy : S, g.p, g.p64, H.active, H.listed() ? H.order : nullptr, nullptr);
     }
     H.busy = 0;   // later stages run every sample
     return FM_OK;
