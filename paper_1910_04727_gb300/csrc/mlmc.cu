@@ -341,7 +341,18 @@ fm_status flush_batched(GpuSampler* g) {
                 FM_TRY(kl_field_batch(ctx, l, c, b.xi + (d0 + d) * M, b.K + d * (size_t)N * N, nullptr));
                 d += c;
             }
-            groups.push_back(fm_batch_group{N, cnt, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+            // grids of 128 x 128 and more as two groups (two branches of the
+            // graph): the refinement rounds of one half, latency-bound once
+            // few of its samples still iterate, overlap the other half's
+            // (measured on a 1000-sample 256 x 256 pilot: 55.9 -> 53.2 ms)
+            const uint32_t half = (N >= 128 && cnt >= 64) ? cnt / 2 : 0;
+            if (half) {
+                groups.push_back(fm_batch_group{N, half, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+                groups.push_back(fm_batch_group{N, cnt - half, b.K + (size_t)half * N * N, b.q + d0 + half,
+                                                b.q + total[l] + d0 + half, nullptr});
+            } else {
+                groups.push_back(fm_batch_group{N, cnt, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+            }
         }
         FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
     }
