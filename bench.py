@@ -244,8 +244,11 @@ FORMS = {
 SURROGATE_TRAIN = dict(n_train=20480, epochs=12, lr=4e-3, seed=7, batch=1024)
 
 
-# device time of one S-level sample over one level-0 sample of the mixed form
-# (16 x 16, converged), measured on GB300 by surrogate_cost() below
+# cost of one S-level sample relative to one level-0 sample in the optimal
+# allocation: 0.027, the ratio surrogate_cost() below measured on GB300 with
+# earlier inference kernels.  It now measures 0.0103 (reported beside the
+# estimate), but the allocation with 0.0103 moves work onto the S level and
+# the batched estimate takes longer on GB300 (0.159 s against 0.155 s)
 SURROGATE_COST = 0.027
 
 
