@@ -649,6 +649,13 @@ fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_repor
  * FM_EINVAL if no run is in flight. */
 fm_status surrogate_train_finish(fm_ctx* ctx, fm_train_report* report);
 
+/* Schedule of surrogate_eval_mc (and of the surrogate level in MC mode):
+ * on = 1 (the default), for M <= 256 the whole network runs in one kernel per
+ * 128 rows (inputs formed in shared memory, the hidden layers back to back on
+ * the tensor cores, activations never leaving the SM); on = 0, layer by layer
+ * through device memory.  Both give the same S bit for bit. */
+fm_status surrogate_set_fused(fm_ctx* ctx, int32_t on);
+
 /* d_s[s] = S(d_xi[s]) for n rows of FP64 KL coefficients [n][M]. */
 fm_status surrogate_eval(fm_ctx* ctx, uint32_t n, const double* d_xi, double* d_s, void* stream);
 

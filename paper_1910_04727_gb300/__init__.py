@@ -421,6 +421,9 @@ class Context:
         self._check(self._L.surrogate_eval_mc(self._h, stream_level, first, n, _ptr(s), _stream()))
         return s
 
+    def surrogate_set_fused(self, on=True):
+        self._check(self._L.surrogate_set_fused(self._h, int(bool(on))))
+
     def surrogate_enable(self, on=True):
         self._check(self._L.surrogate_enable(self._h, int(bool(on))))
 

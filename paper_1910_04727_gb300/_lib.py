@@ -26,7 +26,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_last_error", "mc_points", "sobol_point
            "fmg_solve_batch", "mlmc_sample_level", "mlmc_estimate", "fm_profile_begin",
            "fm_profile_end", "fm_kernel_family_name", "fm_sync", "fmg_solve_batch_static",
            "surrogate_param_count", "surrogate_params", "surrogate_set_scale", "surrogate_loss_grad",
-           "surrogate_train", "surrogate_train_finish", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
+           "surrogate_train", "surrogate_train_finish", "surrogate_set_fused", "surrogate_eval", "surrogate_enable", "surrogate_eval_mc", "fm_shard_range",
            "mlmc_estimate_core", "mlmc_estimate_sharded", "fm_autotune", "fmg_solve_uneven",
            "fmg_uneven_stats", "fm_set_smoother_shape", "mc_words", "fm_level_stats", "fm_wait_check", "fm_matern_covariance", "qmc_points",
            "fm_lattice_cbc", "lattice_generating_vector", "kl_basis_build_ex",
@@ -172,6 +172,7 @@ def load(path=None):
         "surrogate_loss_grad": (I32, [P, P, P, P, P]),
         "surrogate_train": (I32, [P, C.POINTER(FmTrainOpts), C.POINTER(FmTrainReport)]),
         "surrogate_train_finish": (I32, [P, C.POINTER(FmTrainReport)]),
+        "surrogate_set_fused": (I32, [P, I32]),
         "surrogate_eval": (I32, [P, U32, P, P, P]),
         "surrogate_enable": (I32, [P, I32]),
         "surrogate_eval_mc": (I32, [P, U32, U64, U32, P, P]),

@@ -283,6 +283,7 @@ struct fm_ctx {
     cudaStream_t body_stream = nullptr;  // captures the bodies of device-side refinement loops
     fm::TuneTable tune;              // smoother launch shapes (fm_autotune)
     void* uneven = nullptr;          // uneven-batch executor state (uneven.cu)
+    int fused_infer = 1;             // MC surrogate evaluation in one fused kernel (inputs up to 256 wide)
     int tail_max = 32;               // level-wise V-cycles: grids <= tail_max below the top run as one
                                      // resident tail kernel (0: per-grid launches throughout)
 };

@@ -225,6 +225,195 @@ constexpr size_t gemm_smem() {
     return 1024 + kGStages * ((size_t)kGm * kGk * 2 + (size_t)BN * kGk * 2) + 256;
 }
 
+// ------------------------------------------------------------------ fused MC inference
+// S for MC samples in one kernel, one 128-row tile per CTA (eight warps):
+// the tile's BF16 inputs are formed from the samples' Philox words straight
+// into shared memory (k_surrogate_x_mc's map), the three hidden layers run
+// back to back on the tensor cores with the activations kept in shared
+// memory between them (TMEM accumulator, bias + GELU + BF16 epilogue written
+// as the next layer's A operand), and the output layer and S = mu + sd f
+// close the tile.  Every value is formed as the layer-by-layer path forms it
+// (same MMA sequence, same epilogue, k_mlp_out's summation order), so S is
+// bit-identical to it; what goes away is the activations' round trips
+// through HBM and five launches per 65536 rows.  Inputs up to 256 wide.
+constexpr int kFusedRows = 128;
+constexpr int kFusedThreads = 256;
+constexpr uint32_t kFusedKBlock = kFusedRows * kGk * 2;   // 16 KB: 128 rows x 64 columns BF16
+constexpr uint32_t kFusedWStage = kH * kGk * 2;           // 32 KB: 256 rows x 64 columns BF16
+constexpr int kFusedH3Stride = kH * 2 + 16;               // bytes per row of the staged last layer
+
+__host__ __device__ constexpr size_t fused_smem_bytes() {
+    return 1024 + 4 * (size_t)kFusedKBlock + 2 * (size_t)kFusedWStage + 128;
+}
+
+// Byte offset of element (r, k) of a 128 x 256 BF16 A operand stored as four
+// K-blocks of 64 columns, each 128 rows of 128 bytes with the 128-byte
+// swizzle (16-byte chunk c of row r at chunk c ^ (r mod 8)), the layout TMA
+// writes for the tensor-core descriptors.
+__device__ __forceinline__ uint32_t fused_a_offset(int r, int k) {
+    const int kb = k >> 6, kk = k & 63;
+    return (uint32_t)kb * kFusedKBlock + (uint32_t)r * 128u + (uint32_t)((((kk >> 3) ^ (r & 7)) << 4) | ((kk & 7) << 1));
+}
+
+struct FusedArgs {
+    uint64_t seed, first;
+    uint32_t level;
+    int n, M, D;
+    const float *b1, *b2, *b3, *b4;
+    const __nv_bfloat16* w4;
+    double mu, sd;
+    double* s;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_mlp_infer_mc(const __grid_constant__ CUtensorMap mapW1, const __grid_constant__ CUtensorMap mapW2,
+                   const __grid_constant__ CUtensorMap mapW3, FusedArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    uint8_t* base = smem_raw + ((1024 - (raw & 1023)) & 1023);
+    uint8_t* sAct = base;                                   // the layer's A operand (4 K-blocks)
+    uint8_t* sW = base + 4 * kFusedKBlock;                  // weight K-blocks, two stages
+    uint64_t* full = reinterpret_cast<uint64_t*>(sW + 2 * kFusedWStage);
+    uint64_t* empty = full + 2;
+    uint64_t* done = empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * kFusedRows;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        tc::prefetch_tensormap(&mapW1);
+        tc::prefetch_tensormap(&mapW2);
+        tc::prefetch_tensormap(&mapW3);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, kH);
+    // the tile's inputs: 4 columns per Philox call, as k_surrogate_x_mc forms them
+    {
+        const int groups = a.D / 4;
+        for (int t = threadIdx.x; t < kFusedRows * groups; t += kFusedThreads) {
+            const int r = t / groups, g = t % groups;
+            __align__(8) __nv_bfloat16 h[4];
+            if (r0 + r < a.n && 4 * g < a.M) {
+                u64x4 c = {{(uint64_t)g, a.first + (uint64_t)(r0 + r), 0, 0}};
+                const u64x4 w = philox4x64(c, a.seed, (kPurposeMC << 32) | a.level);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float u = ((float)(w.v[q] >> 41) + 0.5f) * 0x1p-23f;
+                    h[q] = __float2bfloat16_rn(4 * g + q < a.M ? normcdfinvf(u) : 0.0f);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = __float2bfloat16_rn(0.0f);
+            }
+            *reinterpret_cast<uint2*>(sAct + fused_a_offset(r, 4 * g)) = *reinterpret_cast<const uint2*>(h);
+        }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    // weight K-blocks in one sequence over the three layers (W1: D / 64, W2
+    // and W3: 4 each), through a two-stage ring: block q in stage q % 2
+    const int kb1 = a.D / kGk;
+    const int lstart[4] = {0, kb1, kb1 + 4, kb1 + 8};
+    const CUtensorMap* maps[3] = {&mapW1, &mapW2, &mapW3};
+    const float* biases[3] = {a.b1, a.b2, a.b3};
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kFusedRows, kH);
+    int issued = 0;   // producer (warp 0 lane 0): weight blocks issued so far
+    bool ok = true;
+    const int qd = warp & 3, ch = warp >> 2;   // TMEM lane quadrant, column half of the epilogue
+    const int r = 32 * qd + lane;               // the tile row this thread drains
+    for (int L = 0; L < 3 && ok; ++L) {
+        if (warp == 0 && lane == 0) {
+            // this layer's blocks and up to two of the next one (their stages
+            // free up as this layer's MMAs complete, without the epilogue)
+            const int upto = L < 2 ? min(lstart[L + 1] + 2, lstart[L + 2]) : lstart[3];
+            while (issued < upto) {
+                const int q = issued, st = q & 1, lq = q < lstart[1] ? 0 : (q < lstart[2] ? 1 : 2);
+                if (q >= 2 && !tc::mbar_wait(&empty[st], ((q >> 1) - 1) & 1, a.err)) break;
+                tc::mbar_arrive_expect_tx(&full[st], kFusedWStage);
+                tc::tma_load_2d(sW + st * kFusedWStage, maps[lq], &full[st], (q - lstart[lq]) * kGk, 0);
+                ++issued;
+            }
+        } else if (warp == 1 && lane == 0) {
+            for (int q = lstart[L]; q < lstart[L + 1]; ++q) {
+                const int st = q & 1, kb = q - lstart[L];
+                if (!tc::mbar_wait(&full[st], (q >> 1) & 1, a.err)) break;
+                tc::fence_after_sync();
+                const uint32_t aa = tc::smem_u32(sAct + kb * kFusedKBlock), bb = tc::smem_u32(sW + st * kFusedWStage);
+#pragma unroll
+                for (int j = 0; j < kGk / 16; ++j)
+                    tc::mma_bf16(tmem, tc::sdesc_kmajor_sw128(aa + 32 * j), tc::sdesc_kmajor_sw128(bb + 32 * j), idesc,
+                                 (kb | j) != 0);
+                tc::mma_commit(&empty[st]);
+            }
+            tc::mma_commit(done);
+        }
+        __syncwarp();
+        // every thread goes on alike: a wait that ran out anywhere ends the
+        // layers for the whole CTA (the error flag is already set)
+        ok = __syncthreads_and(tc::mbar_wait(done, L & 1, a.err)) != 0;
+        tc::fence_after_sync();
+        if (ok) {
+            // bias + GELU + BF16, as the layer-by-layer epilogue forms it: the
+            // next layer's A operand in place, the last layer's rows plainly
+            const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                const int c0 = ch * 128 + c * 32;
+                uint32_t v[32];
+                tc::tmem_ld_32x32b_x32(trow + c0, v);
+                float x[32];
+                __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    x[i] = __uint_as_float(v[i]) + __ldg(biases[L] + c0 + i);
+                    h[i] = __float2bfloat16_rn(gelu_f(x[i]));
+                }
+                if (L < 2) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        *reinterpret_cast<uint4*>(sAct + fused_a_offset(r, c0 + 8 * m)) =
+                            reinterpret_cast<const uint4*>(h)[m];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        *reinterpret_cast<uint4*>(base + (size_t)r * kFusedH3Stride + (c0 + 8 * m) * 2) =
+                            reinterpret_cast<const uint4*>(h)[m];
+                }
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (warp == 0 && lane == 0) tc::drain_loads(full, 2, issued, a.err);
+    if (ok) {
+        // output layer, one warp per row in k_mlp_out's order, then S = mu + sd f
+        for (int rr = warp; rr < kFusedRows; rr += kFusedThreads / 32) {
+            const __nv_bfloat16* h3 = reinterpret_cast<const __nv_bfloat16*>(base + (size_t)rr * kFusedH3Stride);
+            float acc = 0.0f;
+            for (int j = lane; j < kH; j += 32) acc += __bfloat162float(h3[j]) * __bfloat162float(a.w4[j]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0 && r0 + rr < a.n) {
+                const float o = acc + a.b4[0];
+                a.s[r0 + rr] = a.mu + a.sd * (double)o;
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kH);
+}
+
 // ------------------------------------------------------------------ small kernels
 // Rows of xi (FP64 [B][M]) -> BF16 X [B][D] (zero padded) and, if XT, XT [D][ldt].
 __global__ void k_gather_x(int B, int M, int D, const double* __restrict__ xi, __nv_bfloat16* __restrict__ X,
@@ -632,7 +821,9 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
         return FM_ENOMEM;
     }
     if (!(gemm_attr<kTrainBN, kEpiFwdGelu>() && gemm_attr<kTrainBN, kEpiBwdGelu>() &&
-          gemm_attr<kTrainBN, kEpiF32>() && gemm_attr<kEvalBN, kEpiFwdGelu>())) {
+          gemm_attr<kTrainBN, kEpiF32>() && gemm_attr<kEvalBN, kEpiFwdGelu>() &&
+          cudaFuncSetAttribute(k_mlp_infer_mc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fused_smem_bytes()) == cudaSuccess)) {
         set_error(ctx, "surrogate: cannot raise the GEMM kernels' shared-memory limit");
         return FM_ECUDA;
     }
@@ -757,6 +948,18 @@ fm_status surrogate_eval_mc_impl(fm_ctx* ctx, uint32_t level, uint64_t first, ui
     if (n == 0) return FM_OK;
     MlpState* S = state(ctx);
     const uint64_t seed = ctx->cfg.seed;
+    if (S->D <= kH && ctx->fused_infer) {
+        // inputs up to 256 wide: the whole network in one kernel per 128 rows
+        wait_trained(S, st);
+        FusedArgs fa{seed, first, level, (int)n, S->M, S->D, S->P + S->off[1], S->P + S->off[3], S->P + S->off[5],
+                     S->P + S->off[7], S->w4b, S->mu, S->sd, d_s, S->err};
+        const double flops = 2.0 * n * ((double)S->D * kH + 2.0 * kH * kH + kH);
+        FM_TIMED(ctx, kFamMlp, st, 8.0 * n, flops,
+                 k_mlp_infer_mc<<<(unsigned)((n + kFusedRows - 1) / kFusedRows), kFusedThreads, fused_smem_bytes(),
+                                  st>>>(S->eW1, S->eW2, S->eW3, fa));
+        FM_CUDA_TRY(ctx, cudaGetLastError());
+        return FM_OK;
+    }
     eval_chunks(ctx, n, [&](uint32_t o, int cnt, cudaStream_t s2) {
         FM_TIMED(ctx, kFamPoints, s2, (double)cnt * S->D * 2, 0.0,
                  k_surrogate_x_mc<<<nb((size_t)cnt * (S->D / 4)), 256, 0, s2>>>(seed, level, first + o, cnt, S->M,
@@ -1089,6 +1292,12 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         return FM_OK;
     }
     return train_finish(ctx, rep);
+}
+
+extern "C" fm_status surrogate_set_fused(fm_ctx* ctx, int32_t on) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "surrogate_set_fused: null context");
+    ctx->fused_infer = on ? 1 : 0;
+    return FM_OK;
 }
 
 extern "C" fm_status surrogate_train_finish(fm_ctx* ctx, fm_train_report* rep) {
