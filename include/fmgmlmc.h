@@ -359,8 +359,9 @@ typedef struct {
  * level-wise schedule above, the refined stages of the converged mode
  * looping on the device (conditional graph nodes), so the graph runs without
  * the host.  Each sample's results are those fmg_solve_batch gives it.  The
- * executable graph stays in ctx and is updated in place when the next call
- * has the same shape.  prm->kernel: FM_KERNEL_AUTO or FM_KERNEL_LEVELWISE
+ * executable graphs stay in ctx, one per shape (up to 8, the least recently
+ * used replaced), and a call with a kept shape updates that graph in place.
+ * prm->kernel: FM_KERNEL_AUTO or FM_KERNEL_LEVELWISE
  * (every group level-wise).  Asynchronous on `stream`; one call at a time
  * per ctx.  Scratch is allocated before the capture (FM_ENOMEM). */
 fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_batch_group* groups,
@@ -644,9 +645,9 @@ fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const float* d_ta
  * host otherwise.  The network's state is the same either way. */
 fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_train_report* report);
 
-/* End of a training run launched with async_run = 1: waits for its steps,
- * fills the whole report (report nullable) and releases the run's buffers.
- * FM_EINVAL if no run is in flight. */
+/* End of a training run launched with async_run = 1: waits for its steps
+ * and fills the whole report (report nullable).  FM_EINVAL if no run is in
+ * flight. */
 fm_status surrogate_train_finish(fm_ctx* ctx, fm_train_report* report);
 
 /* Schedule of surrogate_eval_mc (and of the surrogate level in MC mode):

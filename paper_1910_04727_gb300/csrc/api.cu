@@ -112,6 +112,7 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     cudaFree(ctx->prof.counters);
     mlp_free(ctx);
     uneven_free(ctx);
+    batched_free(ctx);
     if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
     for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->tc.basis[l]);
     cudaFree(ctx->tc.xi);

@@ -283,6 +283,7 @@ struct fm_ctx {
     cudaStream_t body_stream = nullptr;  // captures the bodies of device-side refinement loops
     fm::TuneTable tune;              // smoother launch shapes (fm_autotune)
     void* uneven = nullptr;          // uneven-batch executor state (uneven.cu)
+    void* batched = nullptr;         // buffers of batched estimator rounds, kept across estimates (mlmc.cu)
     int fused_infer = 1;             // MC surrogate evaluation in one fused kernel (inputs up to 256 wide)
     int tail_max = 32;               // level-wise V-cycles: grids <= tail_max below the top run as one
                                      // resident tail kernel (0: per-grid launches throughout)
@@ -345,6 +346,7 @@ size_t fmg_levelwise_scratch(const fm_ctx* ctx, int n_fine, uint32_t S, const fm
 void fmg_init_attributes();
 void resident_init_attributes();
 void uneven_free(fm_ctx* ctx);
+void batched_free(fm_ctx* ctx);
 fm_status fmg_solve_impl(fm_ctx* ctx, int n_fine, uint32_t S, const double* d_K,
                          const fm_solve_params& prm, double* d_qf, double* d_qc, double* d_p,
                          int32_t* d_status, cudaStream_t stream);

@@ -201,12 +201,21 @@ struct Request {
     int shift;
 };
 
-// Per-level buffers of a batched round (kept across rounds).
+// Per-level buffers of a batched round, kept in the context across rounds
+// and estimates (grown when short), so a timed estimate allocates nothing.
 struct LevelBuf {
     double *xi = nullptr, *K = nullptr, *q = nullptr;
     size_t cap = 0;    // samples of xi and q
     size_t kcap = 0;   // samples of K (one pass)
 };
+struct BatchedBufs {
+    LevelBuf lb[FM_MAX_LEVELS];
+};
+
+LevelBuf* batched_bufs(fm_ctx* ctx) {
+    if (!ctx->batched) ctx->batched = new BatchedBufs();
+    return static_cast<BatchedBufs*>(ctx->batched)->lb;
+}
 
 // GPU side of the controller: samples go to mlmc_sample_level with the
 // running sums of (level, shift) cell e * R + r in ctx->d_sums; an event pair
@@ -220,7 +229,7 @@ struct GpuSampler {
     size_t cells;
     bool batched = false;
     std::vector<Request> pending;
-    LevelBuf lb[FM_MAX_LEVELS];
+    LevelBuf* lb = nullptr;   // the context's (batched_bufs)
     double round_sec = 0.0;
     cudaEvent_t b0 = nullptr, b1 = nullptr;
     std::vector<cudaEvent_t> ev;
@@ -229,11 +238,6 @@ struct GpuSampler {
     double lsec[FM_MAX_LEVELS + 1] = {};
     ~GpuSampler() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        for (LevelBuf& b : lb) {
-            cudaFree(b.xi);
-            cudaFree(b.K);
-            cudaFree(b.q);
-        }
         if (b0) cudaEventDestroy(b0);
         if (b1) cudaEventDestroy(b1);
     }
@@ -411,6 +415,21 @@ fm_status gpu_read(void* user, fm_level_sums* local) {
 
 }  // namespace
 
+namespace fm {
+
+void batched_free(fm_ctx* ctx) {
+    if (!ctx->batched) return;
+    for (LevelBuf& b : static_cast<BatchedBufs*>(ctx->batched)->lb) {
+        cudaFree(b.xi);
+        cudaFree(b.K);
+        cudaFree(b.q);
+    }
+    delete static_cast<BatchedBufs*>(ctx->batched);
+    ctx->batched = nullptr;
+}
+
+}  // namespace fm
+
 extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* opts, int32_t rank, int32_t world,
                                            fm_allgather_fn allgather, void* user, fm_result* out) {
     FM_CHECK_ARG(ctx, ctx != nullptr, "mlmc_estimate: null context");
@@ -454,6 +473,7 @@ extern "C" fm_status mlmc_estimate_sharded(fm_ctx* ctx, const fm_estimate_opts* 
     g.R = R;
     g.cells = cells;
     g.batched = opts->batched != 0;
+    g.lb = batched_bufs(ctx);
     fm_core_opts co{};
     co.n_ext = L + 1;
     co.cost = C;

@@ -236,10 +236,13 @@ constexpr size_t gemm_smem() {
 // (same MMA sequence, same epilogue, k_mlp_out's summation order), so S is
 // bit-identical to it; what goes away is the activations' round trips
 // through HBM and five launches per 65536 rows.  Inputs up to 256 wide.
+// Weights stream in blocks of 64 inputs x 128 outputs (16 KB, two MMAs of
+// N = 128 per 64-input block), so a CTA takes 97 KB of shared memory and two
+// CTAs share an SM: one's epilogue runs beside the other's loads and MMAs.
 constexpr int kFusedRows = 128;
 constexpr int kFusedThreads = 256;
 constexpr uint32_t kFusedKBlock = kFusedRows * kGk * 2;   // 16 KB: 128 rows x 64 columns BF16
-constexpr uint32_t kFusedWStage = kH * kGk * 2;           // 32 KB: 256 rows x 64 columns BF16
+constexpr uint32_t kFusedWStage = (kH / 2) * kGk * 2;     // 16 KB: half the rows (128 outputs) x 64 columns BF16
 constexpr int kFusedH3Stride = kH * 2 + 16;               // bytes per row of the staged last layer
 
 __host__ __device__ constexpr size_t fused_smem_bytes() {
@@ -266,7 +269,7 @@ struct FusedArgs {
     int* err;
 };
 
-__global__ void __launch_bounds__(kFusedThreads, 1)
+__global__ void __launch_bounds__(kFusedThreads, 2)
     k_mlp_infer_mc(const __grid_constant__ CUtensorMap mapW1, const __grid_constant__ CUtensorMap mapW2,
                    const __grid_constant__ CUtensorMap mapW3, FusedArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -318,13 +321,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    // weight K-blocks in one sequence over the three layers (W1: D / 64, W2
-    // and W3: 4 each), through a two-stage ring: block q in stage q % 2
-    const int kb1 = a.D / kGk;
-    const int lstart[4] = {0, kb1, kb1 + 4, kb1 + 8};
+    // weight blocks (64 inputs x 128 outputs) in one sequence over the three
+    // layers (W1: 2 D / 64, W2 and W3: 8 each; output half fastest), through
+    // a two-stage ring: block q in stage q % 2
+    const int kb1 = 2 * (a.D / kGk);
+    const int lstart[4] = {0, kb1, kb1 + 8, kb1 + 16};
     const CUtensorMap* maps[3] = {&mapW1, &mapW2, &mapW3};
     const float* biases[3] = {a.b1, a.b2, a.b3};
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(kFusedRows, kH);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kFusedRows, kH / 2);
     int issued = 0;   // producer (warp 0 lane 0): weight blocks issued so far
     bool ok = true;
     const int qd = warp & 3, ch = warp >> 2;   // TMEM lane quadrant, column half of the epilogue
@@ -337,19 +341,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             while (issued < upto) {
                 const int q = issued, st = q & 1, lq = q < lstart[1] ? 0 : (q < lstart[2] ? 1 : 2);
                 if (q >= 2 && !tc::mbar_wait(&empty[st], ((q >> 1) - 1) & 1, a.err)) break;
+                const int u = q - lstart[lq];   // input block u / 2, output half u % 2
                 tc::mbar_arrive_expect_tx(&full[st], kFusedWStage);
-                tc::tma_load_2d(sW + st * kFusedWStage, maps[lq], &full[st], (q - lstart[lq]) * kGk, 0);
+                tc::tma_load_2d(sW + st * kFusedWStage, maps[lq], &full[st], (u >> 1) * kGk, (u & 1) * (kH / 2));
                 ++issued;
             }
         } else if (warp == 1 && lane == 0) {
             for (int q = lstart[L]; q < lstart[L + 1]; ++q) {
-                const int st = q & 1, kb = q - lstart[L];
+                const int st = q & 1, u = q - lstart[L], kb = u >> 1;
                 if (!tc::mbar_wait(&full[st], (q >> 1) & 1, a.err)) break;
                 tc::fence_after_sync();
                 const uint32_t aa = tc::smem_u32(sAct + kb * kFusedKBlock), bb = tc::smem_u32(sW + st * kFusedWStage);
+                const uint32_t dst = tmem + (uint32_t)((u & 1) * (kH / 2));   // the output half's TMEM columns
 #pragma unroll
                 for (int j = 0; j < kGk / 16; ++j)
-                    tc::mma_bf16(tmem, tc::sdesc_kmajor_sw128(aa + 32 * j), tc::sdesc_kmajor_sw128(bb + 32 * j), idesc,
+                    tc::mma_bf16(dst, tc::sdesc_kmajor_sw128(aa + 32 * j), tc::sdesc_kmajor_sw128(bb + 32 * j), idesc,
                                  (kb | j) != 0);
                 tc::mma_commit(&empty[st]);
             }
@@ -528,8 +534,8 @@ __global__ void k_surrogate_value(int n, const float* __restrict__ out, double m
 __global__ void k_train_batch(int B, int M, int D, int ldt, int n, int spe, const int* __restrict__ step,
                               const int32_t* __restrict__ perm, const double* __restrict__ xi,
                               const float* __restrict__ tt, __nv_bfloat16* __restrict__ X,
-                              __nv_bfloat16* __restrict__ XT, float* __restrict__ t) {    pdl_wait_then_release();
-
+                              __nv_bfloat16* __restrict__ XT, float* __restrict__ t) {
+    pdl_wait_then_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * D) return;
     const int b = i / D, k = i % D;
@@ -651,6 +657,7 @@ struct MlpState {
     __nv_bfloat16 *eX = nullptr, *eH[3] = {};
     float* eout = nullptr;
     CUtensorMap meX, meH1, meH2, eW1, eW2, eW3;
+    CUtensorMap fW1, fW2, fW3;         // the weights in 128-row boxes (fused inference)
     double mu = 0.0, sd = 1.0;
     int* err = nullptr;
     int* step = nullptr;               // device step counter of a training run; step[1]: Adam's block count
@@ -662,7 +669,8 @@ struct MlpState {
     // A training run whose steps may still be running on `st` (launched with
     // fm_train_opts.async_run): every use of the network waits for `trained`
     // on its stream, host-side uses wait on the host.  The run's buffers and
-    // graph live until surrogate_train_finish (or the next run) releases them.
+    // graph live until surrogate_train_finish (or the next run) ends the run;
+    // the buffers stay for the next run.
     struct Run {
         bool pending = false;          // steps launched, not yet finished
         cudaEvent_t trained = nullptr; // recorded after the last step
@@ -670,6 +678,10 @@ struct MlpState {
         float* tt = nullptr;           // standardised targets
         int32_t* perm = nullptr;       // shuffles of every epoch
         float* sq0 = nullptr;          // squared errors of the first step's batch
+        // capacities (elements) of the buffers above and of the training
+        // solves' fields and outputs: kept across runs, grown when short
+        size_t xi_cap = 0, tt_cap = 0, perm_cap = 0, sq0_cap = 0, K_cap = 0, q_cap = 0;
+        double *K = nullptr, *q = nullptr;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         std::vector<double> hq;        // targets Q_0 on the host
@@ -838,7 +850,9 @@ static fm_status mlp_alloc(fm_ctx* ctx) {
          map_bf16(&S->tH1T, S->HT[0], kH, L, bn) && map_bf16(&S->tH2T, S->HT[1], kH, L, bn) &&
          map_bf16(&S->meX, S->eX, kEvalChunk, D, kGm) && map_bf16(&S->meH1, S->eH[0], kEvalChunk, kH, kGm) &&
          map_bf16(&S->meH2, S->eH[1], kEvalChunk, kH, kGm) && map_bf16(&S->eW1, S->W1b, kH, D, kEvalBN) &&
-         map_bf16(&S->eW2, S->W2b, kH, kH, kEvalBN) && map_bf16(&S->eW3, S->W3b, kH, kH, kEvalBN);
+         map_bf16(&S->eW2, S->W2b, kH, kH, kEvalBN) && map_bf16(&S->eW3, S->W3b, kH, kH, kEvalBN) &&
+         map_bf16(&S->fW1, S->W1b, kH, D, kH / 2) && map_bf16(&S->fW2, S->W2b, kH, kH, kH / 2) &&
+         map_bf16(&S->fW3, S->W3b, kH, kH, kH / 2);
     if (!ok) {
         set_error(ctx, "surrogate: cuTensorMapEncodeTiled failed");
         return FM_ECUDA;
@@ -956,7 +970,7 @@ fm_status surrogate_eval_mc_impl(fm_ctx* ctx, uint32_t level, uint64_t first, ui
         const double flops = 2.0 * n * ((double)S->D * kH + 2.0 * kH * kH + kH);
         FM_TIMED(ctx, kFamMlp, st, 8.0 * n, flops,
                  k_mlp_infer_mc<<<(unsigned)((n + kFusedRows - 1) / kFusedRows), kFusedThreads, fused_smem_bytes(),
-                                  st>>>(S->eW1, S->eW2, S->eW3, fa));
+                                  st>>>(S->fW1, S->fW2, S->fW3, fa));
         FM_CUDA_TRY(ctx, cudaGetLastError());
         return FM_OK;
     }
@@ -989,6 +1003,9 @@ void mlp_free(fm_ctx* ctx) {
     if (!S) return;
     train_finish(ctx, nullptr);
     if (S->run.trained) cudaEventDestroy(S->run.trained);
+    for (void* p : {(void*)S->run.xi, (void*)S->run.tt, (void*)S->run.perm, (void*)S->run.sq0, (void*)S->run.K,
+                    (void*)S->run.q})
+        cudaFree(p);
     void* ptrs[] = {S->P, S->G, S->Am, S->Av, S->W1b, S->W2b, S->W3b, S->W2T, S->W3T, S->w4b, S->X, S->XT,
                     S->t, S->out, S->dout, S->sq, S->eX, S->eout, S->err, S->step};
     if (S->st) cudaStreamDestroy(S->st);
@@ -1068,8 +1085,9 @@ extern "C" fm_status surrogate_loss_grad(fm_ctx* ctx, const double* d_xi, const 
 namespace fm {
 
 // The end of a training run: wait for its steps, read the first and last
-// mini-batch losses, evaluate the fit on the training set, release the run's
-// buffers and graph.  rep (nullable) receives the whole report.
+// mini-batch losses, evaluate the fit on the training set, destroy the run's
+// graph (its buffers stay for the next run).  rep (nullable) receives the
+// whole report.
 static fm_status train_finish(fm_ctx* ctx, fm_train_report* rep) {
     MlpState* S = state(ctx);
     if (!S || !S->run.pending) return FM_OK;
@@ -1133,16 +1151,8 @@ static fm_status train_finish(fm_ctx* ctx, fm_train_report* rep) {
     }
     if (R.exec) cudaGraphExecDestroy(R.exec);
     if (R.graph) cudaGraphDestroy(R.graph);
-    cudaFree(R.xi);
-    cudaFree(R.tt);
-    cudaFree(R.perm);
-    cudaFree(R.sq0);
     R.exec = nullptr;
     R.graph = nullptr;
-    R.xi = nullptr;
-    R.tt = nullptr;
-    R.perm = nullptr;
-    R.sq0 = nullptr;
     R.hq.clear();
     return stt;
 }
@@ -1164,18 +1174,14 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     MlpState::Run& R = S->run;
     const int n = opts->n_train, M = ctx->cfg.M;
     // training pairs (xi, Q_0) from the method: level-0 FMG solves on a stream of their own
-    double *xi = nullptr, *q = nullptr, *K = nullptr;
     const int N0 = grid_of_level(ctx, 0);
-    FM_CUDA_TRY(ctx, cudaMalloc((void**)&xi, (size_t)n * M * 8));
-    if (cudaMalloc((void**)&q, (size_t)n * 8) != cudaSuccess) {
-        cudaFree(xi);
-        set_error(ctx, "surrogate_train: device allocation failed");
-        return FM_ENOMEM;
-    }
+    const uint32_t chunk = 65536;
+    FM_TRY(ensure(ctx, &R.xi, &R.xi_cap, (size_t)n * M));
+    FM_TRY(ensure(ctx, &R.q, &R.q_cap, (size_t)n));
+    FM_TRY(ensure(ctx, &R.K, &R.K_cap, (size_t)std::min<uint32_t>(chunk, (uint32_t)n) * N0 * N0));
+    double *xi = R.xi, *q = R.q, *K = R.K;
     fm_status stt = FM_OK;
     {
-        const uint32_t chunk = 65536;
-        if (cudaMalloc((void**)&K, (size_t)chunk * N0 * N0 * 8) != cudaSuccess) stt = FM_ENOMEM;
         const fm_solve_params prm = solve_params(ctx);
         for (uint32_t o = 0; stt == FM_OK && o < (uint32_t)n; o += chunk) {
             const uint32_t c = std::min<uint32_t>(chunk, n - o);
@@ -1186,12 +1192,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     }
     std::vector<double> hq(n);
     if (stt == FM_OK && cudaMemcpy(hq.data(), q, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) stt = FM_ECUDA;
-    cudaFree(K);
-    cudaFree(q);
-    if (stt != FM_OK) {
-        cudaFree(xi);
-        return stt;
-    }
+    if (stt != FM_OK) return stt;
     double mu = 0.0, var = 0.0;
     for (double v : hq) mu += v;
     mu /= n;
@@ -1220,8 +1221,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         std::iota(pe, pe + n, 0);
         std::shuffle(pe, pe + n, gen);
     }
-    // the run's state: from here on train_finish releases it
-    R.xi = xi;
+    // the run's state: from here on train_finish ends it
     R.hq = std::move(hq);
     R.n = n;
     R.batch = batch;
@@ -1234,9 +1234,9 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     if (!R.trained) FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&R.trained, cudaEventDisableTiming));
     cudaStream_t ts = S->st;
     auto launch_run = [&]() -> fm_status {
-        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.tt, (size_t)n * 4));
-        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.perm, perm.size() * 4));
-        FM_CUDA_TRY(ctx, cudaMalloc((void**)&R.sq0, (size_t)batch * 4));
+        FM_TRY(ensure(ctx, &R.tt, &R.tt_cap, (size_t)n));
+        FM_TRY(ensure(ctx, &R.perm, &R.perm_cap, perm.size()));
+        FM_TRY(ensure(ctx, &R.sq0, &R.sq0_cap, (size_t)batch));
         FM_CUDA_TRY(ctx, cudaMemcpy(R.tt, ht.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
         FM_CUDA_TRY(ctx, cudaMemcpy(R.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
         FM_CUDA_TRY(ctx, cudaMemcpy(S->P, hp.data(), S->np * 4, cudaMemcpyHostToDevice));
@@ -1275,7 +1275,7 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         FM_CUDA_TRY(ctx, cudaEventRecord(R.trained, ts));
         return FM_OK;
     };
-    R.pending = true;   // train_finish releases whatever launch_run allocated
+    R.pending = true;   // train_finish ends the run whatever launch_run got to
     S->ready = true;    // users of the network wait for R.trained
     stt = launch_run();
     if (stt != FM_OK) {

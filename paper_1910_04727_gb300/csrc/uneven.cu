@@ -11,9 +11,12 @@
 // residual tests overlap another group's bandwidth-bound fine grids, and
 // the graph removes the gaps between the thousands of small launches.
 //
-// The executable graph is kept in the context: a later call with the same
-// shape (groups, grids, schedule) only updates the kernel parameters
-// (cudaGraphExecUpdate), otherwise it is instantiated anew.
+// Executable graphs are kept in the context by shape (groups, grids,
+// schedule), a few of them: a later call with a kept shape only updates the
+// kernel parameters (cudaGraphExecUpdate), a new shape is instantiated.  An
+// estimator's rounds alternate between shapes (the pilot round solves every
+// level, later rounds a few), so keeping one graph per shape saves an
+// instantiation per round.
 #include <algorithm>
 #include <vector>
 
@@ -27,9 +30,17 @@ struct UnevenState {
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
     cudaStream_t cap = nullptr;       // capture origin
-    cudaGraphExec_t exec = nullptr;
+    struct Kept {
+        std::vector<int64_t> key;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<Kept> kept;           // at most kKeptGraphs, the least recently used replaced
+    uint64_t tick = 0;
     int64_t instantiations = 0, updates = 0, launches = 0;
 };
+
+constexpr size_t kKeptGraphs = 8;
 
 static UnevenState* uneven_state(fm_ctx* ctx) { return static_cast<UnevenState*>(ctx->uneven); }
 
@@ -41,7 +52,7 @@ void uneven_free(fm_ctx* ctx) {
     for (cudaEvent_t e : U->join) cudaEventDestroy(e);
     if (U->fork) cudaEventDestroy(U->fork);
     if (U->cap) cudaStreamDestroy(U->cap);
-    if (U->exec) cudaGraphExecDestroy(U->exec);
+    for (UnevenState::Kept& k : U->kept) cudaGraphExecDestroy(k.exec);
     delete U;
     ctx->uneven = nullptr;
 }
@@ -140,34 +151,46 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
         cudaGetLastError();
         return FM_ECUDA;
     }
-    // same shape as the kept graph: update its parameters; otherwise instantiate
-    bool updated = false;
-    if (U->exec) {
+    // a kept graph of the same shape: update its parameters; otherwise instantiate
+    std::vector<int64_t> key = {n_groups, prm->precision, prm->converged, prm->energy_step, prm->nu0, prm->nu1,
+                                prm->nu2, prm->n_coarsest, prm->bc_case, prm->kernel, prm->ir_cycles};
+    for (int g = 0; g < n_groups; ++g)
+        key.insert(key.end(), {groups[g].n_fine, groups[g].count > 0, resident_grid(groups[g].n_fine, *prm)});
+    cudaGraphExec_t exec = nullptr;
+    for (size_t i = 0; i < U->kept.size() && !exec; ++i) {
+        if (U->kept[i].key != key) continue;
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(U->exec, graph, &info) == cudaSuccess) {
-            updated = true;
+        if (cudaGraphExecUpdate(U->kept[i].exec, graph, &info) == cudaSuccess) {
+            exec = U->kept[i].exec;
+            U->kept[i].used = ++U->tick;
             ++U->updates;
-        } else {
+        } else {   // same key, other topology (a changed smoother shape, say): replace it
             cudaGetLastError();
-            cudaGraphExecDestroy(U->exec);
-            U->exec = nullptr;
+            cudaGraphExecDestroy(U->kept[i].exec);
+            U->kept.erase(U->kept.begin() + (long)i);
         }
     }
-    if (!updated) {
-        const cudaError_t ie = cudaGraphInstantiate(&U->exec, graph, 0);
+    if (!exec) {
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         if (ie != cudaSuccess) {
             cudaGraphDestroy(graph);
-            U->exec = nullptr;
             set_error(ctx, std::string("fmg_solve_uneven: graph instantiation failed: ") + cudaGetErrorString(ie));
             return FM_ECUDA;
         }
         ++U->instantiations;
+        if (U->kept.size() >= kKeptGraphs) {
+            auto lru = std::min_element(U->kept.begin(), U->kept.end(),
+                                        [](const UnevenState::Kept& a, const UnevenState::Kept& b) { return a.used < b.used; });
+            cudaGraphExecDestroy(lru->exec);
+            U->kept.erase(lru);
+        }
+        U->kept.push_back(UnevenState::Kept{key, exec, ++U->tick});
     }
     cudaGraphDestroy(graph);
     cudaStream_t s = as_stream(stream);
     double cells = 0.0;
     for (int g = 0; g < n_groups; ++g) cells += (double)groups[g].count * groups[g].n_fine * groups[g].n_fine;
-    FM_TIMED(ctx, kFamUnevenGraph, s, 8.0 * cells, 0.0, cudaGraphLaunch(U->exec, s));
+    FM_TIMED(ctx, kFamUnevenGraph, s, 8.0 * cells, 0.0, cudaGraphLaunch(exec, s));
     ++U->launches;
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
