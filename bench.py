@@ -392,8 +392,25 @@ def _case_levelwise(torch, fm, level, S):
     ctx.close()
 
 
+def _case_surrogate_mc(torch, fm, n):
+    """S for n MC samples by the fused inference kernel (a network of the
+    five-level workload's size with seeded random parameters), three times."""
+    wl = W.WORKLOADS["fmg_mlmc5"]
+    ctx = make_ctx(fm, wl, 0, "mixed_surrogate")
+    ctx.kl_basis_build(q=wl.kl_q)
+    r = np.random.default_rng(5)
+    ctx.surrogate_set_params((r.random(ctx.surrogate_param_count()) - 0.5).astype(np.float32) * 0.1, mu=1.0, sd=0.5)
+    for k in range(3):
+        s = ctx.surrogate_eval_mc(12, k * n, n)
+    torch.cuda.synchronize()
+    ctx.sync()
+    print("kernel case: %d surrogate evaluations, mean %.6f" % (n, float(s.mean())))
+    ctx.close()
+
+
 # one small isolated launch pattern per case, for a profiler (-k/-c select it)
 KERNEL_CASES = {
+    "surrogate_mc_fused": lambda torch, fm: _case_surrogate_mc(torch, fm, 1 << 20),
     "fmg_levelwise_mixed256": lambda torch, fm: _case_levelwise(torch, fm, 4, 300),
     "fmg_resident_mixed16": lambda torch, fm: _case_resident(torch, fm, 0, 65536),
     "fmg_resident_mixed32": lambda torch, fm: _case_resident(torch, fm, 1, 16384),
