@@ -237,11 +237,11 @@ FORMS = {
     "fp64_fmg2": dict(precision=0, converged=False, surrogate=False),
 }
 
-# surrogate training: 20480 (xi, Q_0) pairs, batch 1024, 12 epochs (240 steps),
-# Adam 4e-3 cosine.  Measured on GB300 (chosen form, seconds per estimate):
-# 24 epochs 0.226, 16 epochs 0.212, 12 epochs 0.207 -- training time falls
-# faster than the level-0 sample count grows (corr 0.9987 -> 0.9969)
-SURROGATE_TRAIN = dict(n_train=20480, epochs=12, lr=4e-3, seed=7, batch=1024)
+# surrogate training: 20480 (xi, Q_0) pairs, batch 1024, 20 epochs (400 steps),
+# Adam 4e-3 cosine.  Measured on GB300 (headline form, 6 FP32 V-cycles per
+# test, seconds per estimate): 12 epochs 0.1322 (corr 0.9969), 16 epochs
+# 0.1316 (0.9979), 20 epochs 0.1312 (0.9983), 24 epochs 0.1325 (0.9987)
+SURROGATE_TRAIN = dict(n_train=20480, epochs=20, lr=4e-3, seed=7, batch=1024)
 # kernels in one captured training step (batch gather, three forward GEMMs,
 # output layer with its gradient, five backward GEMMs, four row sums, Adam)
 TRAIN_STEP_KERNELS = 15
@@ -274,9 +274,11 @@ def surrogate_cost(torch, ctx):
 
 
 # FP32 V-cycles per FP64 residual test in the mixed forms' refinement loops:
-# measured on GB300 (five-level workload, chosen form) 0.238 s per estimate
-# with 2, 0.226 s with 3, 0.223 s with 4 (fewer FP64 residual tests)
-MIXED_IR_CYCLES = 4
+# measured on GB300 (headline form, 12 training epochs, seconds per
+# estimate) 0.1368 with 3, 0.1336-0.1342 with 4, 0.1337 with 5, 0.1322-0.1324
+# with 6; with 16 epochs 0.1316 with 6 and 0.1401 with 8 (fewer FP64
+# residual tests against FP32 cycles spent on samples already converged)
+MIXED_IR_CYCLES = 6
 IR_CYCLES = [MIXED_IR_CYCLES]
 
 
