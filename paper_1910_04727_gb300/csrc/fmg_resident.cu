@@ -727,7 +727,11 @@ static bool launch_resident(fm_ctx* ctx, const ResidentArgs& a, cudaStream_t st)
     const int groups = WARP ? 4 : 1;
     const size_t smem = groups * (resident_slot_bytes<T>() + resident_smem_bytes(a.n_fine, a.n0, MIXED, WARP));
     if (smem > kResidentSmemMax) return false;
-    const int threads = WARP ? 32 * groups : (a.n_fine >= 64 ? 512 : (a.n_fine >= 32 ? 256 : 128));
+    // a 32 x 32 sample on 128 threads: four CTAs per SM (shared memory
+    // allows four, registers four at 128 threads); measured 1.45x the
+    // samples per second of 256 threads (two CTAs per SM), the half-sweeps
+    // being latency-bound
+    const int threads = WARP ? 32 * groups : (a.n_fine >= 64 ? 512 : 128);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fmg_resident<T, MIXED, WARP>, threads, smem);
     int sms = 0;
