@@ -1,4 +1,5 @@
 // Context lifetime and error reporting of the C ABI.
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -86,10 +87,15 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
         }
         ctx->h_lattice_z = *z;
     }
-    if (cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        fm_destroy(ctx);
-        set_error(nullptr, "fm_create: stream creation failed");
-        return FM_ECUDA;
+    cudaDeviceGetStreamPriorityRange(&ctx->prio_lo, &ctx->prio_hi);
+    ctx->prio_lo = std::min(ctx->prio_lo, ctx->prio_hi + fm_ctx::kPrioLevels - 1);
+    for (int p = ctx->prio_hi; p <= ctx->prio_lo; ++p) {
+        if (cudaStreamCreateWithPriority(&ctx->body_stream[p - ctx->prio_hi], cudaStreamNonBlocking, p) !=
+            cudaSuccess) {
+            fm_destroy(ctx);
+            set_error(nullptr, "fm_create: stream creation failed");
+            return FM_ECUDA;
+        }
     }
     fmg_init_attributes();
     resident_init_attributes();
@@ -113,7 +119,8 @@ extern "C" void fm_destroy(fm_ctx* ctx) {
     mlp_free(ctx);
     uneven_free(ctx);
     batched_free(ctx);
-    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
+    for (cudaStream_t s : ctx->body_stream)
+        if (s) cudaStreamDestroy(s);
     for (int l = 0; l < FM_MAX_LEVELS; ++l) cudaFree(ctx->tc.basis[l]);
     cudaFree(ctx->tc.xi);
     cudaFree(ctx->tc.err);

@@ -280,7 +280,12 @@ struct fm_ctx {
     fm::TcState tc;
     void* mlp = nullptr;             // surrogate network state (mlp.cu)
     int surrogate_on = 0;            // level -1 = S(xi), level 0 = Q_0 - S(xi)
-    cudaStream_t body_stream = nullptr;  // captures the bodies of device-side refinement loops
+    // Streams that capture the bodies of device-side refinement loops, one
+    // per stream priority (index: priority - prio_hi), so that a loop body's
+    // kernel nodes carry the priority of the branch that captured it.
+    static constexpr int kPrioLevels = 8;
+    cudaStream_t body_stream[kPrioLevels] = {};
+    int prio_hi = 0, prio_lo = 0;   // greatest (numerically lowest) and least stream priority
     fm::TuneTable tune;              // smoother launch shapes (fm_autotune)
     void* uneven = nullptr;          // uneven-batch executor state (uneven.cu)
     void* batched = nullptr;         // buffers of batched estimator rounds, kept across estimates (mlmc.cu)

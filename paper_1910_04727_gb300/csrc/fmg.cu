@@ -1808,7 +1808,11 @@ static fm_status refine_stage_graph(const Hierarchy<T>& H, int k, const fm_solve
     cudaGraphNode_t node;
     FM_CUDA_TRY(ctx, cudaGraphAddNode(&node, graph, deps, nullptr, nd, &np));
     FM_CUDA_TRY(ctx, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaStream_t bs = ctx->body_stream;
+    // the body is captured on a stream of the branch's own priority
+    int prio = 0;
+    FM_CUDA_TRY(ctx, cudaStreamGetPriority(st, &prio));
+    prio = std::min(std::max(prio, ctx->prio_hi), ctx->prio_lo);
+    cudaStream_t bs = ctx->body_stream[prio - ctx->prio_hi];
     FM_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
     // the body's strips enumerate the samples the last test listed

@@ -18,6 +18,7 @@
 // level, later rounds a few), so keeping one graph per shape saves an
 // instantiation per round.
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -26,8 +27,9 @@ namespace fm {
 
 struct UnevenState {
     std::vector<Arena> arenas;        // level-wise scratch, one per group
-    std::vector<cudaStream_t> side;   // one branch stream per group
-    std::vector<cudaEvent_t> join;
+    // branch streams by priority (index: priority - prio_hi), a branch per group
+    std::vector<cudaStream_t> side[fm_ctx::kPrioLevels];
+    std::vector<cudaEvent_t> join;    // one per group
     cudaEvent_t fork = nullptr;
     cudaStream_t cap = nullptr;       // capture origin
     struct Kept {
@@ -48,7 +50,8 @@ void uneven_free(fm_ctx* ctx) {
     UnevenState* U = uneven_state(ctx);
     if (!U) return;
     for (Arena& a : U->arenas) cudaFree(a.base);
-    for (cudaStream_t s : U->side) cudaStreamDestroy(s);
+    for (const std::vector<cudaStream_t>& v : U->side)
+        for (cudaStream_t s : v) cudaStreamDestroy(s);
     for (cudaEvent_t e : U->join) cudaEventDestroy(e);
     if (U->fork) cudaEventDestroy(U->fork);
     if (U->cap) cudaStreamDestroy(U->cap);
@@ -57,21 +60,53 @@ void uneven_free(fm_ctx* ctx) {
     ctx->uneven = nullptr;
 }
 
-static fm_status uneven_prepare(fm_ctx* ctx, int groups) {
+// Branch priorities: the group of the largest grid (the batch's longest
+// chain of launches) one below the device's greatest priority (the greatest
+// is the surrogate's training stream), the next grid size one lower, and so
+// on to the least priority.  A branch's kernel nodes, its refinement loops'
+// bodies included, carry its priority, so the longest branch's launches are
+// scheduled first and the shorter branches fill the SMs around them.
+static std::vector<int> branch_priorities(const fm_ctx* ctx, int n_groups, const fm_batch_group* groups) {
+    std::vector<int> sizes;
+    for (int g = 0; g < n_groups; ++g) sizes.push_back(groups[g].n_fine);
+    std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    std::vector<int> prio(n_groups);
+    for (int g = 0; g < n_groups; ++g) {
+        const int r = (int)(std::find(sizes.begin(), sizes.end(), groups[g].n_fine) - sizes.begin());
+        prio[g] = std::min(ctx->prio_hi + 1 + r, ctx->prio_lo);
+    }
+    return prio;
+}
+
+// Streams and events for n_groups branches of the given priorities: side
+// stream of group g = the j-th stream of its priority, j counting the
+// groups of that priority before g.
+static fm_status uneven_prepare(fm_ctx* ctx, int n_groups, const std::vector<int>& prio,
+                                std::vector<cudaStream_t>* branch) {
     if (!ctx->uneven) ctx->uneven = new UnevenState();
     UnevenState* U = uneven_state(ctx);
     if (!U->cap) {
         FM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&U->cap, cudaStreamNonBlocking));
         FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&U->fork, cudaEventDisableTiming));
     }
-    while ((int)U->side.size() < groups) {
-        cudaStream_t s;
+    while ((int)U->join.size() < n_groups) {
         cudaEvent_t e;
-        FM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
         FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        U->side.push_back(s);
         U->join.push_back(e);
         U->arenas.emplace_back();
+    }
+    int used[fm_ctx::kPrioLevels] = {};
+    branch->assign(n_groups, nullptr);
+    for (int g = 0; g < n_groups; ++g) {
+        const int pi = prio[g] - ctx->prio_hi;
+        std::vector<cudaStream_t>& pool = U->side[pi];
+        if (used[pi] == (int)pool.size()) {
+            cudaStream_t s;
+            FM_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio[g]));
+            pool.push_back(s);
+        }
+        (*branch)[g] = pool[used[pi]++];
     }
     return FM_OK;
 }
@@ -101,7 +136,9 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
         FM_CHECK_ARG(ctx, G.count == 0 || (G.d_K && G.d_qf),
                      "fmg_solve_uneven: group " + std::to_string(g) + ": null input or output");
     }
-    FM_TRY(uneven_prepare(ctx, n_groups));
+    const std::vector<int> prio = branch_priorities(ctx, n_groups, groups);
+    std::vector<cudaStream_t> branch;
+    FM_TRY(uneven_prepare(ctx, n_groups, prio, &branch));
     UnevenState* U = uneven_state(ctx);
     // level-wise scratch is sized before the capture (no allocation inside it)
     for (int g = 0; g < n_groups; ++g) {
@@ -131,12 +168,12 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
     for (int g = 0; g < n_groups && st == FM_OK; ++g) {
         const fm_batch_group& G = groups[g];
         if (G.count == 0) continue;
-        cudaStreamWaitEvent(U->side[g], U->fork, 0);
+        cudaStreamWaitEvent(branch[g], U->fork, 0);
         fm_solve_params p = *prm;
         p.kernel = resident_grid(G.n_fine, *prm) ? FM_KERNEL_AUTO : FM_KERNEL_LEVELWISE;
         st = fmg_solve_with(ctx, U->arenas[g], G.n_fine, G.count, G.d_K, p, G.d_qf, G.d_qc, nullptr, G.d_status,
-                            U->side[g]);
-        cudaEventRecord(U->join[g], U->side[g]);
+                            branch[g]);
+        cudaEventRecord(U->join[g], branch[g]);
         cudaStreamWaitEvent(U->cap, U->join[g], 0);
     }
     const cudaError_t ce = cudaStreamEndCapture(U->cap, &graph);
@@ -171,7 +208,7 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
         }
     }
     if (!exec) {
-        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         if (ie != cudaSuccess) {
             cudaGraphDestroy(graph);
             set_error(ctx, std::string("fmg_solve_uneven: graph instantiation failed: ") + cudaGetErrorString(ie));
