@@ -379,11 +379,18 @@ fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, doubl
 fm_status surrogate_eval_mc_impl(fm_ctx* ctx, uint32_t level, uint64_t first, uint32_t n, double* d_s,
                                  cudaStream_t st);
 int surrogate_err_flag(const fm_ctx* ctx);
+// surrogate_eval_mc_impl runs the fused inference kernel (no scratch shared
+// with the context's other surrogate evaluations).
+bool surrogate_mc_fused(const fm_ctx* ctx);
 void mlp_free(fm_ctx* ctx);
 
 // Level sums of a batch (mlmc.cu).
 fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc,
                          int coarse, fm_level_sums* d_sums, cudaStream_t stream);
+// The same with partial-sum scratch of the caller's (*partials, grown when
+// short), for sums that run beside others on another stream.
+fm_status level_sums_add_to(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc, int coarse,
+                            fm_level_sums* d_sums, cudaStream_t stream, double** partials, size_t* capacity);
 
 // Host-side Sobol' direction numbers (points.cu).
 int sobol_direction_numbers_host(uint32_t dim, std::vector<uint32_t>& V);

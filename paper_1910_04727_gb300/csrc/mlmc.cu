@@ -85,16 +85,22 @@ __global__ void k_level_fold(int nblocks, size_t S, const double* __restrict__ p
     sums->count += (double)S;
 }
 
-fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc, int coarse,
-                         fm_level_sums* d_sums, cudaStream_t st) {
+fm_status level_sums_add_to(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc, int coarse,
+                            fm_level_sums* d_sums, cudaStream_t st, double** partials, size_t* capacity) {
     if (S == 0) return FM_OK;
     const int nb = (int)((S + kSumItems - 1) / kSumItems);
-    FM_TRY(ensure(ctx, &ctx->d_partials, &ctx->partial_capacity, (size_t)nb * 8));
+    FM_TRY(ensure(ctx, partials, capacity, (size_t)nb * 8));
+    double* part = *partials;
     FM_TIMED(ctx, kFamLevelSums, st, 16.0 * S, 8.0 * S,
-             k_level_partials<<<nb, kSumBlock, 0, st>>>(S, d_qf, d_qc, coarse, ctx->d_partials);
-             k_level_fold<<<1, 32, 0, st>>>(nb, S, ctx->d_partials, d_sums));
+             k_level_partials<<<nb, kSumBlock, 0, st>>>(S, d_qf, d_qc, coarse, part);
+             k_level_fold<<<1, 32, 0, st>>>(nb, S, part, d_sums));
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
+}
+
+fm_status level_sums_add(fm_ctx* ctx, uint32_t S, const double* d_qf, const double* d_qc, int coarse,
+                         fm_level_sums* d_sums, cudaStream_t st) {
+    return level_sums_add_to(ctx, S, d_qf, d_qc, coarse, d_sums, st, &ctx->d_partials, &ctx->partial_capacity);
 }
 
 fm_solve_params solve_params(const fm_ctx* ctx) {
@@ -210,12 +216,26 @@ struct LevelBuf {
 };
 struct BatchedBufs {
     LevelBuf lb[FM_MAX_LEVELS];
+    // the surrogate level's MC requests on a stream of their own: S values,
+    // partial sums, the stream and its fork and join events
+    double* s_q = nullptr;
+    size_t s_cap = 0;
+    double* s_part = nullptr;
+    size_t s_pcap = 0;
+    cudaStream_t s_st = nullptr;
+    cudaEvent_t s_fork = nullptr, s_join = nullptr;
 };
 
-LevelBuf* batched_bufs(fm_ctx* ctx) {
+BatchedBufs* batched_state(fm_ctx* ctx) {
     if (!ctx->batched) ctx->batched = new BatchedBufs();
-    return static_cast<BatchedBufs*>(ctx->batched)->lb;
+    return static_cast<BatchedBufs*>(ctx->batched);
 }
+
+LevelBuf* batched_bufs(fm_ctx* ctx) { return batched_state(ctx)->lb; }
+
+// Chunk of the surrogate level's samples per evaluation (the one
+// mlmc_sample_level uses, so the sums are the same whichever path adds them).
+constexpr uint64_t kSChunk = (uint64_t)1 << 22;
 
 // GPU side of the controller: samples go to mlmc_sample_level with the
 // running sums of (level, shift) cell e * R + r in ctx->d_sums; an event pair
@@ -292,6 +312,43 @@ fm_status flush_batched(GpuSampler* g) {
         cudaEventCreate(&g->b1);
     }
     cudaEventRecord(g->b0, nullptr);
+    // The surrogate level's MC requests need only the trained network (the
+    // fused inference kernel, no shared scratch): they run on a stream of
+    // their own beside the round's points, fields and solves.
+    BatchedBufs* B = batched_state(ctx);
+    const bool s_side = surrogate_mc_fused(ctx);
+    bool s_forked = false;
+    if (s_side) {
+        uint64_t need = 0;
+        for (const Request& r : g->pending)
+            if (r.e - g->off < 0 && r.shift < 0) need = std::max<uint64_t>(need, std::min<uint64_t>(r.n, kSChunk));
+        if (need) {
+            if (!B->s_st) {
+                FM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&B->s_st, cudaStreamNonBlocking));
+                FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&B->s_fork, cudaEventDisableTiming));
+                FM_CUDA_TRY(ctx, cudaEventCreateWithFlags(&B->s_join, cudaEventDisableTiming));
+            }
+            FM_TRY(ensure(ctx, &B->s_q, &B->s_cap, (size_t)need));
+            FM_CUDA_TRY(ctx, cudaEventRecord(B->s_fork, nullptr));
+            FM_CUDA_TRY(ctx, cudaStreamWaitEvent(B->s_st, B->s_fork, 0));
+            for (const Request& r : g->pending) {
+                if (r.e - g->off >= 0 || r.shift >= 0) continue;
+                cudaEvent_t e0 = g->event(), e1 = g->event();
+                g->lev.push_back(r.e);
+                cudaEventRecord(e0, B->s_st);
+                fm_level_sums* cell = ctx->d_sums + (size_t)r.e * g->R;
+                for (uint64_t done = 0; done < r.n;) {
+                    const uint32_t cnt = (uint32_t)std::min<uint64_t>(r.n - done, kSChunk);
+                    FM_TRY(surrogate_eval_mc_impl(ctx, kSurrogateLevelStream, r.first + done, cnt, B->s_q, B->s_st));
+                    FM_TRY(level_sums_add_to(ctx, cnt, B->s_q, nullptr, 0, cell, B->s_st, &B->s_part, &B->s_pcap));
+                    done += cnt;
+                }
+                cudaEventRecord(e1, B->s_st);
+            }
+            FM_CUDA_TRY(ctx, cudaEventRecord(B->s_join, B->s_st));
+            s_forked = true;
+        }
+    }
     // points of every request, level by level, requests packed in order;
     // fields and solves in passes of at most batch_limit samples per level,
     // one uneven batch per pass (every level's next chunk)
@@ -383,7 +440,7 @@ fm_status flush_batched(GpuSampler* g) {
         }
     }
     for (const Request& r : g->pending) {
-        if (r.e - g->off >= 0) continue;
+        if (r.e - g->off >= 0 || (s_forked && r.shift < 0)) continue;
         cudaEvent_t e0 = g->event(), e1 = g->event();
         g->lev.push_back(r.e);
         cudaEventRecord(e0, nullptr);
@@ -395,6 +452,7 @@ fm_status flush_batched(GpuSampler* g) {
         }
         cudaEventRecord(e1, nullptr);
     }
+    if (s_forked) FM_CUDA_TRY(ctx, cudaStreamWaitEvent(nullptr, B->s_join, 0));
     cudaEventRecord(g->b1, nullptr);
     g->pending.clear();
     return FM_OK;
@@ -419,12 +477,18 @@ namespace fm {
 
 void batched_free(fm_ctx* ctx) {
     if (!ctx->batched) return;
-    for (LevelBuf& b : static_cast<BatchedBufs*>(ctx->batched)->lb) {
+    BatchedBufs* B = static_cast<BatchedBufs*>(ctx->batched);
+    for (LevelBuf& b : B->lb) {
         cudaFree(b.xi);
         cudaFree(b.K);
         cudaFree(b.q);
     }
-    delete static_cast<BatchedBufs*>(ctx->batched);
+    cudaFree(B->s_q);
+    cudaFree(B->s_part);
+    if (B->s_st) cudaStreamDestroy(B->s_st);
+    if (B->s_fork) cudaEventDestroy(B->s_fork);
+    if (B->s_join) cudaEventDestroy(B->s_join);
+    delete B;
     ctx->batched = nullptr;
 }
 

@@ -991,6 +991,11 @@ fm_status surrogate_eval_impl(fm_ctx* ctx, uint32_t n, const double* d_xi, doubl
     return FM_OK;
 }
 
+bool surrogate_mc_fused(const fm_ctx* ctx) {
+    const MlpState* S = reinterpret_cast<const MlpState*>(ctx->mlp);
+    return S && S->ready && S->D <= kH && ctx->fused_infer;
+}
+
 int surrogate_err_flag(const fm_ctx* ctx) {
     if (!ctx->mlp) return 0;
     int e = 0;
