@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--c5-steps", type=int, default=1, help="timed estimates per form in the large case")
     ap.add_argument("--train-epochs", type=int, default=None,
                     help="epochs of the surrogate's training inside each step (default: SURROGATE_TRAIN)")
+    ap.add_argument("--train-n", type=int, default=None,
+                    help="training pairs of the surrogate (level-0 solves) inside each step (default: SURROGATE_TRAIN)")
     ap.add_argument("--train-batch", type=int, default=None,
                     help="minibatch of the surrogate's training (default: SURROGATE_TRAIN)")
     ap.add_argument("--train-lr", type=float, default=None,
@@ -929,6 +931,8 @@ def main():
         IR_CYCLES[0] = args.ir_cycles
     if args.train_epochs is not None:
         SURROGATE_TRAIN["epochs"] = args.train_epochs
+    if args.train_n is not None:
+        SURROGATE_TRAIN["n_train"] = args.train_n
     if args.train_batch is not None:
         SURROGATE_TRAIN["batch"] = args.train_batch
     if args.train_lr is not None:
