@@ -131,8 +131,9 @@ typedef struct {
 /* Kernel schedule of a batched FMG solve (same arithmetic, same result up
  * to rounding order). */
 #define FM_KERNEL_AUTO 0       /* resident where it is the faster schedule (up to 32 x 32 in
-                                  the mixed form, 16 x 16 in FP64; not with the energy step),
-                                  else levelwise */
+                                  the mixed form, 16 x 16 in FP64, and a converged mixed
+                                  64 x 64 batch of at most two samples per SM; not with the
+                                  energy step), else levelwise */
 #define FM_KERNEL_LEVELWISE 1  /* one kernel per grid operation over all samples */
 #define FM_KERNEL_RESIDENT 2   /* one CTA per sample, hierarchy in shared memory
                                   (n_fine <= 64 in FP64) */

@@ -57,6 +57,7 @@ extern "C" fm_status fm_create(const fm_config* cfg, fm_ctx** out) {
     ctx->cfg = *cfg;
     if (ctx->cfg.lattice_m == 0) ctx->cfg.lattice_m = 16;
     cudaGetDevice(&ctx->device);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (sobol_direction_numbers_host((uint32_t)cfg->M, ctx->h_sobol_V) != 0) {
         delete ctx;
         set_error(nullptr, "fm_create: Sobol' direction numbers unavailable for this M");

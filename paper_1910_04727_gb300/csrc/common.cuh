@@ -87,8 +87,13 @@ struct Ghost {
 // 16 x 16 2.0x (mixed), 1.1x (FP64, two cycles per stage), 1.2x (FP64
 // converged); 64 x 64 0.82x, 0.89x, 1.04x; 32 x 32 0.93x and 0.84x in FP64,
 // level in the mixed form (0.97x alone, ahead inside the five-level estimate).
-inline bool auto_resident(int n_fine, const fm_solve_params& prm) {
+// The resident kernel for grids up to 32 x 32 in the mixed form (16 x 16 in
+// FP64); also for a converged mixed 64 x 64 batch of at most two samples per
+// SM: one CTA per sample then finishes in one or two waves, where the
+// level-wise schedule is a latency-bound chain of small launches.
+inline bool auto_resident(int n_fine, size_t S, int sms, const fm_solve_params& prm) {
     if (prm.energy_step) return false;
+    if (prm.precision == FM_PREC_MIXED && prm.converged && n_fine == 64 && S <= 2 * (size_t)sms) return true;
     return n_fine <= (prm.precision == FM_PREC_MIXED ? 32 : 16);
 }
 
@@ -255,6 +260,7 @@ struct TcState {
 struct fm_ctx {
     fm_config cfg{};
     int device = 0;
+    int sms = 0;   // multiprocessors of the device
     std::string last_error;
     // KL basis per MLMC level: [n_l^2][M] FP64, row-subsets of the finest grid's basis.
     double* d_basis[FM_MAX_LEVELS] = {};

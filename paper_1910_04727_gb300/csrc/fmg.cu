@@ -2025,7 +2025,7 @@ fm_status fmg_solve_with(fm_ctx* ctx, Arena& ar, int n_fine, uint32_t S, const d
                  "fmg_solve_batch: the energy-optimal correction step runs in converged mode on the level-wise "
                  "schedule");
     if (S == 0) return FM_OK;
-    if (prm.kernel == FM_KERNEL_RESIDENT || (prm.kernel == FM_KERNEL_AUTO && auto_resident(n_fine, prm))) {
+    if (prm.kernel == FM_KERNEL_RESIDENT || (prm.kernel == FM_KERNEL_AUTO && auto_resident(n_fine, S, ctx->sms, prm))) {
         if (fmg_resident_launch(ctx, n_fine, n0, S, d_K, prm, d_qf, d_qc, d_p, d_status, st)) {
             FM_CUDA_TRY(ctx, cudaGetLastError());
             return FM_OK;

@@ -1195,19 +1195,8 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
             if (stt == FM_OK) stt = fmg_solve_impl(ctx, N0, c, K, prm, q + o, nullptr, nullptr, nullptr, nullptr);
         }
     }
-    std::vector<double> hq(n);
-    if (stt == FM_OK && cudaMemcpy(hq.data(), q, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) stt = FM_ECUDA;
-    if (stt != FM_OK) return stt;
-    double mu = 0.0, var = 0.0;
-    for (double v : hq) mu += v;
-    mu /= n;
-    for (double v : hq) var += (v - mu) * (v - mu);
-    const double sd = std::sqrt(var / (n - 1));
-    S->mu = mu;
-    S->sd = sd > 0 ? sd : 1.0;
-    std::vector<float> ht(n);
-    for (int i = 0; i < n; ++i) ht[i] = (float)((hq[i] - mu) / S->sd);
-    // initial parameters U(-1/sqrt(fan_in), 1/sqrt(fan_in)), Adam state zero
+    // The host's part while the device forms the pairs: initial parameters
+    // U(-1/sqrt(fan_in), 1/sqrt(fan_in)) (Adam state zero) and the shuffles.
     std::mt19937_64 gen(opts->seed);
     std::uniform_real_distribution<double> uni(0.0, 1.0);
     std::vector<float> hp(S->np);
@@ -1226,6 +1215,18 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
         std::iota(pe, pe + n, 0);
         std::shuffle(pe, pe + n, gen);
     }
+    std::vector<double> hq(n);
+    if (stt == FM_OK && cudaMemcpy(hq.data(), q, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) stt = FM_ECUDA;
+    if (stt != FM_OK) return stt;
+    double mu = 0.0, var = 0.0;
+    for (double v : hq) mu += v;
+    mu /= n;
+    for (double v : hq) var += (v - mu) * (v - mu);
+    const double sd = std::sqrt(var / (n - 1));
+    S->mu = mu;
+    S->sd = sd > 0 ? sd : 1.0;
+    std::vector<float> ht(n);
+    for (int i = 0; i < n; ++i) ht[i] = (float)((hq[i] - mu) / S->sd);
     // the run's state: from here on train_finish ends it
     R.hq = std::move(hq);
     R.n = n;

@@ -112,8 +112,8 @@ static fm_status uneven_prepare(fm_ctx* ctx, int n_groups, const std::vector<int
 }
 
 // Groups on the resident kernel: where FM_KERNEL_AUTO would take it.
-static bool resident_grid(int n, const fm_solve_params& prm) {
-    return prm.kernel != FM_KERNEL_LEVELWISE && auto_resident(n, prm);
+static bool resident_grid(const fm_ctx* ctx, const fm_batch_group& G, const fm_solve_params& prm) {
+    return prm.kernel != FM_KERNEL_LEVELWISE && auto_resident(G.n_fine, G.count, ctx->sms, prm);
 }
 
 }  // namespace fm
@@ -143,7 +143,7 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
     // level-wise scratch is sized before the capture (no allocation inside it)
     for (int g = 0; g < n_groups; ++g) {
         const fm_batch_group& G = groups[g];
-        if (G.count == 0 || resident_grid(G.n_fine, *prm)) continue;
+        if (G.count == 0 || resident_grid(ctx, G, *prm)) continue;
         const size_t need = fmg_levelwise_scratch(ctx, G.n_fine, G.count, *prm);
         Arena& a = U->arenas[g];
         if (a.capacity < need) {
@@ -170,7 +170,7 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
         if (G.count == 0) continue;
         cudaStreamWaitEvent(branch[g], U->fork, 0);
         fm_solve_params p = *prm;
-        p.kernel = resident_grid(G.n_fine, *prm) ? FM_KERNEL_AUTO : FM_KERNEL_LEVELWISE;
+        p.kernel = resident_grid(ctx, G, *prm) ? FM_KERNEL_AUTO : FM_KERNEL_LEVELWISE;
         st = fmg_solve_with(ctx, U->arenas[g], G.n_fine, G.count, G.d_K, p, G.d_qf, G.d_qc, nullptr, G.d_status,
                             branch[g]);
         cudaEventRecord(U->join[g], branch[g]);
@@ -192,7 +192,7 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
     std::vector<int64_t> key = {n_groups, prm->precision, prm->converged, prm->energy_step, prm->nu0, prm->nu1,
                                 prm->nu2, prm->n_coarsest, prm->bc_case, prm->kernel, prm->ir_cycles};
     for (int g = 0; g < n_groups; ++g)
-        key.insert(key.end(), {groups[g].n_fine, groups[g].count > 0, resident_grid(groups[g].n_fine, *prm)});
+        key.insert(key.end(), {groups[g].n_fine, groups[g].count > 0, resident_grid(ctx, groups[g], *prm)});
     cudaGraphExec_t exec = nullptr;
     for (size_t i = 0; i < U->kept.size() && !exec; ++i) {
         if (U->kept[i].key != key) continue;
