@@ -602,6 +602,10 @@ typedef struct {
     uint64_t seed;        /* parameter initialisation and shuffling */
     int32_t batch;        /* mini-batch rows: a multiple of 128, at most 4096 (0: 256) */
     int32_t async_run;    /* 1: return once the training steps are launched (see surrogate_train) */
+    double target_tol;    /* > 0: residual and outflux-change tolerance of the training pairs'
+                             level-0 solves (converged forms); <= 0: the context's own.  Any S
+                             leaves the estimator unbiased, so the targets need no more
+                             accuracy than the network's fit */
 } fm_train_opts;
 
 typedef struct {

@@ -397,10 +397,12 @@ class Context:
                                                 g.ctypes.data_as(C.c_void_p), C.byref(loss)))
         return loss.value, g
 
-    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7, batch=256, async_run=False):
+    def surrogate_train(self, n_train=20000, epochs=200, lr=1e-3, seed=7, batch=256, async_run=False,
+                        target_tol=0.0):
         """async_run: return once the training steps are launched (the report's
-        losses and fit are NaN until surrogate_train_finish)."""
-        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed, batch, int(bool(async_run)))
+        losses and fit are NaN until surrogate_train_finish).  target_tol > 0:
+        tolerance of the training pairs' level-0 solves (else the context's)."""
+        opts = _lib.FmTrainOpts(n_train, epochs, lr, seed, batch, int(bool(async_run)), float(target_tol))
         rep = _lib.FmTrainReport()
         self._check(self._L.surrogate_train(self._h, C.byref(opts), C.byref(rep)))
         return {f: getattr(rep, f) for f, _ in _lib.FmTrainReport._fields_}

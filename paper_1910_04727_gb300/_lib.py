@@ -78,7 +78,7 @@ class FmKernelStat(C.Structure):
 
 class FmTrainOpts(C.Structure):
     _fields_ = [("n_train", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
-                ("batch", C.c_int32), ("async_run", C.c_int32)]
+                ("batch", C.c_int32), ("async_run", C.c_int32), ("target_tol", C.c_double)]
 
 
 class FmTrainReport(C.Structure):

@@ -1187,7 +1187,11 @@ extern "C" fm_status surrogate_train(fm_ctx* ctx, const fm_train_opts* opts, fm_
     double *xi = R.xi, *q = R.q, *K = R.K;
     fm_status stt = FM_OK;
     {
-        const fm_solve_params prm = solve_params(ctx);
+        fm_solve_params prm = solve_params(ctx);
+        if (opts->target_tol > 0 && prm.converged) {
+            prm.tol = opts->target_tol;
+            prm.qtol = opts->target_tol;
+        }
         for (uint32_t o = 0; stt == FM_OK && o < (uint32_t)n; o += chunk) {
             const uint32_t c = std::min<uint32_t>(chunk, n - o);
             stt = mc_points(ctx, kSurrogateTrainStream, o, c, M, xi + (size_t)o * M, nullptr);
