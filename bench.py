@@ -58,6 +58,8 @@ def parse():
                     help="epochs of the surrogate's training inside each step (default: SURROGATE_TRAIN)")
     ap.add_argument("--train-n", type=int, default=None,
                     help="training pairs of the surrogate (level-0 solves) inside each step (default: SURROGATE_TRAIN)")
+    ap.add_argument("--surrogate-cost", type=float, default=None,
+                    help="cost of an S sample relative to a level-0 sample in the allocation (default: SURROGATE_COST)")
     ap.add_argument("--train-tol", type=float, default=None,
                     help="tolerance of the training pairs' level-0 solves (default: SURROGATE_TRAIN)")
     ap.add_argument("--train-batch", type=int, default=None,
@@ -257,9 +259,10 @@ TRAIN_STEP_KERNELS = 15
 
 # cost of one S-level sample relative to one level-0 sample in the optimal
 # allocation: 0.027, the ratio surrogate_cost() below measured on GB300 with
-# earlier inference kernels.  It now measures 0.0103 (reported beside the
-# estimate), but the allocation with 0.0103 moves work onto the S level and
-# the batched estimate takes longer on GB300 (0.159 s against 0.155 s)
+# earlier inference kernels (it now measures about 0.006, reported beside the
+# estimate).  A fixed ratio keeps the schedule independent of timing; with
+# the S level beside the solves the choice barely matters (seconds per
+# estimate on GB300: 0.027 0.1225, 0.015 0.1218, 0.008 0.1222, 0.005 0.1222)
 SURROGATE_COST = 0.027
 
 
@@ -932,6 +935,7 @@ def run_reference(args, wl, eps):
 
 
 def main():
+    global SURROGATE_COST
     args = parse()
     if args.ir_cycles is not None:
         IR_CYCLES[0] = args.ir_cycles
@@ -939,6 +943,8 @@ def main():
         SURROGATE_TRAIN["epochs"] = args.train_epochs
     if args.train_n is not None:
         SURROGATE_TRAIN["n_train"] = args.train_n
+    if args.surrogate_cost is not None:
+        SURROGATE_COST = args.surrogate_cost
     if args.train_tol is not None:
         SURROGATE_TRAIN["target_tol"] = args.train_tol
     if args.train_batch is not None:
