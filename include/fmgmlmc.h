@@ -307,7 +307,10 @@ fm_status kl_field_batch(fm_ctx* ctx, int32_t level, uint32_t n, const double* d
  * restricted by summing the 2x2 children, bilinear cell-centred
  * prolongation).  Outputs: d_qf[s] QoI of the finest stage; d_qc[s]
  * (nullable) QoI of the stage one grid coarser (the Q^c by-product;
- * NaN if n_fine == n_coarsest); d_p (nullable) the finest solution
+ * NaN if n_fine == n_coarsest).  In converged mode that stage is refined
+ * to the tolerance only when d_qc is given; without it the stage only
+ * starts the finest one, and Q^f agrees with the d_qc run to within the
+ * tolerance, not bit for bit.  d_p (nullable) the finest solution
  * [n][n_fine][n_fine]; d_status (nullable) per-sample FM_OK / FM_ENOTCONV.
  * n_fine must be n_coarsest times a power of two.  Scratch is owned by the
  * context.  prm->kernel picks the schedule: the resident one (the whole
@@ -452,7 +455,10 @@ fm_status fm_level_stats(const fm_level_sums* sums, fm_level_stat* out);
  * (surrogate_enable) level -1 is the surrogate level (Y = S(xi), no solve, on
  * a point stream of its own) and level 0 gives Y = Q_0 - S(xi) with S in the
  * Q^c sums.  d_qf / d_qc (nullable, device [n]) receive the per-sample QoIs.
- * Processes the samples in batches of at most the context's max_batch. */
+ * Level 0 needs no Q^c, so its solves leave the coarse stage unrefined
+ * (fmg_solve_batch without d_qc) unless d_qc asks for it without the
+ * surrogate.  Processes the samples in batches of at most the context's
+ * max_batch. */
 fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t first, uint32_t n,
                             int32_t shift, fm_level_sums* d_sums, double* d_qf, double* d_qc,
                             void* stream);

@@ -1918,13 +1918,16 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
                  k_coarse_inverse<T><<<(unsigned)((S + kInvWarps - 1) / kInvWarps), 32 * kInvWarps, 0, st>>>(H.n0, S, H.g[0].K, H.Ainv,
                                                                                                  bd.ns));
     }
+    // the stage one grid coarser is refined only where its QoI is asked for:
+    // otherwise it just gives the finest stage its starting guess
+    const bool refine_c = conv && qc != nullptr;
     for (int k = 0; k <= H.m; ++k) {
         const GridBufs<T>& g = H.g[k];
         const size_t cells = S * (size_t)g.n * g.n;
-        const bool refined = conv && k >= H.m - 1;
+        const bool refined = conv && (k == H.m || (k == H.m - 1 && refine_c));
         if (k > 0) {
             const GridBufs<T>& c = H.g[k - 1];
-            if (mixed && refined && k == H.m && H.m >= 1) {
+            if (mixed && refined && k == H.m && H.m >= 1 && refine_c) {
                 FM_TIMED(ctx, kFamFmgInterp, st, 10.0 * cells, 8.0 * cells,
                          k_prolong<double><<<blocks_for(cells), kBlock, 0, st>>>(
                              c.n, S, c.p64, Ghost<double>{bd.g[0], bd.g[1], bd.g[2], bd.g[3], bd.ns}, 0, g.p64,
@@ -1943,7 +1946,7 @@ static fm_status fmg_batch(const Hierarchy<T>& H, const fm_solve_params& prm, do
             if (k > 0)
                 for (int it = 0; it < prm.nu0; ++it) vcycle(H, k, k, prm, nullptr, st);
         } else {
-            if (mixed && !(k == H.m && H.m >= 1))
+            if (mixed && !(k == H.m && H.m >= 1 && refine_c))
                 k_widen<T><<<blocks_for(cells), kBlock, 0, st>>>(cells, g.p, g.p64);
             FM_TRY(refine_stage(H, k, prm, mixed, status, st));
         }

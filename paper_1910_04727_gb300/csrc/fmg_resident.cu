@@ -604,12 +604,14 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
         double model = 0.0;  // their algorithmic bytes (byte model of the level-wise kernels)
         constexpr int ts = (int)sizeof(T);
 
+        // the stages giving Q^f and (where it is asked for) Q^c are refined
+        // when converged; otherwise stage m - 1 only gives stage m its start
+        const bool refine_c = a.converged && a.qc != nullptr;
         for (int k = 0; k <= m; ++k) {
             const RGrid<T>& g = L.g[k];
-            // the stages giving Q^c and Q^f are refined when converged
-            const bool refined = a.converged && k >= m - 1;
+            const bool refined = a.converged && (k == m || (k == m - 1 && refine_c));
             if (k > 0) {
-                if (MIXED && refined && k == m && m >= 1) {
+                if (MIXED && refined && k == m && m >= 1 && refine_c) {
                     // FP64 interpolation of the refined stage m-1 solution
                     R::resident_prolong(L.h[0].p, L.h[0].n, L.h[1].p, a.bd, false);
                 } else {
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
             } else {
                 // mixed: FP64 residual -> FP32 V-cycle on the correction -> FP64 update
                 const HGrid& h = L.h[k - (m - 1)];
-                if (!(k == m && m >= 1)) {
+                if (!(k == m && m >= 1 && refine_c)) {
                     for (int c = R::rank(); c < h.n * h.n; c += R::size()) h.p[c] = (double)g.p[c];
                     R::sync();
                 }
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(512, 1) k_fmg_resident(ResidentArgs a) {
                 }
             }
             // outflux of the stage (the FP64 iterate in mixed refined stages)
-            if (k >= m - 1) {
+            if (k == m || (k == m - 1 && a.qc)) {
                 double q;
                 if (MIXED && refined) {
                     const HGrid& h = L.h[k - (m - 1)];

@@ -188,7 +188,10 @@ extern "C" fm_status mlmc_sample_level(fm_ctx* ctx, int32_t level, uint64_t firs
             FM_TRY(eval_s(qf));
         } else {
             FM_TRY(kl_field_batch(ctx, level, cnt, ctx->d_xi, ctx->d_K, stream));
-            FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, qc, nullptr, nullptr, st));
+            // level 0 takes no Q^c (Y_0 = Q_0, or Q_0 - S): the solver then
+            // leaves its coarse stage unrefined, unless the caller asks for it
+            double* solve_qc = (level > 0 || (d_qc && !with_s)) ? qc : nullptr;
+            FM_TRY(fmg_solve_impl(ctx, N, cnt, ctx->d_K, prm, qf, solve_qc, nullptr, nullptr, st));
             // level 0 with the surrogate: Y = Q_0 - S, S in the Q^c slot
             if (with_s) FM_TRY(eval_s(qc));
         }
@@ -406,13 +409,15 @@ fm_status flush_batched(GpuSampler* g) {
             // graph): the refinement rounds of one half, latency-bound once
             // few of its samples still iterate, overlap the other half's
             // (measured on a 1000-sample 256 x 256 pilot: 55.9 -> 53.2 ms)
+            // level 0 takes no Q^c (its coarse slot holds S, or nothing)
+            double* qcl = l > 0 ? b.q + total[l] + d0 : nullptr;
             const uint32_t half = (N >= 128 && cnt >= 64) ? cnt / 2 : 0;
             if (half) {
-                groups.push_back(fm_batch_group{N, half, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+                groups.push_back(fm_batch_group{N, half, b.K, b.q + d0, qcl, nullptr});
                 groups.push_back(fm_batch_group{N, cnt - half, b.K + (size_t)half * N * N, b.q + d0 + half,
-                                                b.q + total[l] + d0 + half, nullptr});
+                                                qcl ? qcl + half : nullptr, nullptr});
             } else {
-                groups.push_back(fm_batch_group{N, cnt, b.K, b.q + d0, b.q + total[l] + d0, nullptr});
+                groups.push_back(fm_batch_group{N, cnt, b.K, b.q + d0, qcl, nullptr});
             }
         }
         FM_TRY(fmg_solve_uneven(ctx, (int32_t)groups.size(), groups.data(), &prm, nullptr));
