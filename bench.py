@@ -771,6 +771,12 @@ def run_native(args, wl, eps):
         if k == "rbgs_strip" and FORMS[args.form]["precision"] == 1:
             e["traffic"] = round(v["bytes"] / v["launches"] * STRIP_DRAM_BYTES_PER_CELL_F32
                                  / STRIP_ALG_BYTES_PER_CELL_F32, 1)
+            if fam == k:
+                # DRAM bytes per average launch: the ncu-measured bytes per
+                # cell of a 256 x 256 strip call times the launch's cells
+                roof["traffic"] = e["traffic"]
+                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64 Mi-cell "
+                                          "strip call (25.6 B per cell), scaled to the average launch's cells")
         hbm_kernels[k] = e
     families = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                     "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
