@@ -470,7 +470,8 @@ typedef struct {
     int32_t max_rounds;
     int32_t surrogate;    /* 1: add the surrogate control-variate level below level 0 */
     double surrogate_cost; /* cost of an S-level sample relative to a level-0 sample */
-    int32_t batched;      /* 1: each round's solves of all levels as one uneven batch (fmg_solve_uneven) */
+    int32_t batched;      /* 1: each round's solves of all levels as one uneven batch (fmg_solve_uneven);
+                             the surrogate level's MC samples on a stream of their own beside it */
     int32_t adapt_L;      /* 1: grow the finest level from L_start (bias test of Algorithms 1-3) up to
                              n_levels - 1; 0: use every level of the context */
     int32_t L_start;      /* adapt_L: the first finest level, 1 .. n_levels - 1 (the paper starts at 2) */
