@@ -191,8 +191,11 @@ extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_ba
     // a kept graph of the same shape: update its parameters; otherwise instantiate
     std::vector<int64_t> key = {n_groups, prm->precision, prm->converged, prm->energy_step, prm->nu0, prm->nu1,
                                 prm->nu2, prm->n_coarsest, prm->bc_case, prm->kernel, prm->ir_cycles};
+    // per group: grid, non-empty, schedule, and whether Q^c is asked for (a
+    // converged solve refines its coarse stage only then)
     for (int g = 0; g < n_groups; ++g)
-        key.insert(key.end(), {groups[g].n_fine, groups[g].count > 0, resident_grid(ctx, groups[g], *prm)});
+        key.insert(key.end(), {groups[g].n_fine, groups[g].count > 0, resident_grid(ctx, groups[g], *prm),
+                               groups[g].d_qc != nullptr});
     cudaGraphExec_t exec = nullptr;
     for (size_t i = 0; i < U->kept.size() && !exec; ++i) {
         if (U->kept[i].key != key) continue;

@@ -69,6 +69,26 @@ def test_converged_device_loops_match_host_loops(ctx, precision):
         assert _rel(qf.cpu().numpy(), of) < bar and _rel(qc.cpu().numpy(), oc) < bar
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_converged_solves_without_qc(ctx, precision):
+    """Without Q^c a converged solve leaves its coarse stage unrefined: the
+    graph and the per-group call agree bit for bit, Q^f stays within the
+    tolerance's reach of the solve that refines both stages, and a kept
+    graph of the same grids with Q^c is not reused for it."""
+    Ks = [torch.tensor(K, device="cuda") for K in _fields(450)]
+    kw = dict(precision=precision, converged=1, tol=1e-12, qtol=0.0, max_cycles=400)
+    with_qc = ctx.solve_uneven(Ks, **kw)
+    before = ctx.uneven_stats()
+    outs = ctx.solve_uneven(Ks, want_qc=False, **kw)
+    after = ctx.uneven_stats()
+    assert after["instantiations"] - before["instantiations"] == 1
+    for (n, S), K, (qf, qc, _), (wf, _, _) in zip(GRIDS, Ks, outs, with_qc):
+        assert qc is None
+        rf, rqc, _ = ctx.fmg_solve_batch(K, want_qc=False, **kw)
+        assert rqc is None and _same(qf, rf), n
+        assert _rel(qf.cpu().numpy(), wf.cpu().numpy()) < 10 * n * 1e-12, n
+
+
 def test_device_loop_reports_non_convergence(ctx):
     Ks = [torch.tensor(W.smooth_lognormal_field(n, S=4, tag=500 + n), device="cuda") for n in (32, 128)]
     outs = ctx.solve_uneven(Ks, want_status=True, converged=1, tol=1e-15, qtol=0.0, max_cycles=1)
