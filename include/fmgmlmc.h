@@ -354,7 +354,8 @@ typedef struct {
     uint32_t count;        /* samples */
     const double* d_K;     /* device [count][n_fine][n_fine] coefficients */
     double* d_qf;          /* device [count] outflux of the finest grid */
-    double* d_qc;          /* device [count] outflux of grid n_fine / 2 (nullable) */
+    double* d_qc;          /* device [count] outflux of grid n_fine / 2 (nullable; without it a
+                              converged solve leaves that stage unrefined, as fmg_solve_batch) */
     int32_t* d_status;     /* device [count] per-sample FM_OK / FM_ENOTCONV (nullable) */
 } fm_batch_group;
 
@@ -362,9 +363,12 @@ typedef struct {
  * branch per group, the resident kernel where FM_KERNEL_AUTO takes it and the
  * level-wise schedule above, the refined stages of the converged mode
  * looping on the device (conditional graph nodes), so the graph runs without
- * the host.  Each sample's results are those fmg_solve_batch gives it.  The
- * executable graphs stay in ctx, one per shape (up to 8, the least recently
- * used replaced), and a call with a kept shape updates that graph in place.
+ * the host.  Each sample's results are those fmg_solve_batch gives it.
+ * Branches carry stream priorities by grid size, the largest grid's highest
+ * (below the surrogate's training stream).  The executable graphs stay in
+ * ctx, one per shape (grids, schedules and which groups ask for Q^c; up to
+ * 8, the least recently used replaced), and a call with a kept shape updates
+ * that graph in place.
  * prm->kernel: FM_KERNEL_AUTO or FM_KERNEL_LEVELWISE
  * (every group level-wise).  Asynchronous on `stream`; one call at a time
  * per ctx.  Scratch is allocated before the capture (FM_ENOMEM). */
