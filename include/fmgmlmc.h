@@ -45,7 +45,7 @@ typedef int32_t fm_status;
 #define FM_ECUDA 3         /* a CUDA call failed */
 #define FM_ENOTCONV 4      /* a solve did not reach its tolerance */
 #define FM_ETIMEOUT 5      /* a bounded device wait ran out */
-#define FM_EUNSUPPORTED 6  /* valid request this build does not implement */
+#define FM_EUNSUPPORTED 6  /* valid request the library does not implement */
 
 #define FM_MAX_LEVELS 12
 
