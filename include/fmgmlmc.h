@@ -364,9 +364,6 @@ typedef struct {
  * level-wise schedule above, the refined stages of the converged mode
  * looping on the device (conditional graph nodes), so the graph runs without
  * the host.  Each sample's results are those fmg_solve_batch gives it.
- * Level-wise groups of 128 x 128 and more with at least 64 samples run as
- * two branches (halves), so one half's latency-bound refinement rounds
- * overlap the other's.
  * Branches carry stream priorities by grid size, the largest grid's highest
  * (below the surrogate's training stream).  The executable graphs stay in
  * ctx, one per shape (grids, schedules and which groups ask for Q^c; up to

@@ -116,34 +116,26 @@ static bool resident_grid(const fm_ctx* ctx, const fm_batch_group& G, const fm_s
     return prm.kernel != FM_KERNEL_LEVELWISE && auto_resident(G.n_fine, G.count, ctx->sms, prm);
 }
 
+}  // namespace fm
 
-// Level-wise groups of 128 x 128 and more with at least 64 samples run as
-// two branches (halves): once few samples of one half still iterate, its
-// latency-bound refinement rounds overlap the other half's (a 1000-sample
-// 256 x 256 group: 55.9 -> 53.2 ms).
-static std::vector<fm_batch_group> split_groups(const fm_ctx* ctx, int n_groups, const fm_batch_group* groups,
-                                                const fm_solve_params& prm) {
-    std::vector<fm_batch_group> parts;
+using namespace fm;
+
+extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_batch_group* groups,
+                                      const fm_solve_params* prm, void* stream) {
+    FM_CHECK_ARG(ctx, ctx != nullptr, "fmg_solve_uneven: null context");
+    FM_CHECK_ARG(ctx, prm != nullptr && groups != nullptr, "fmg_solve_uneven: null argument");
+    FM_CHECK_ARG(ctx, n_groups >= 1 && n_groups <= 64, "fmg_solve_uneven: 1 .. 64 groups");
+    FM_CHECK_ARG(ctx, prm->kernel != FM_KERNEL_RESIDENT, "fmg_solve_uneven: the schedule is chosen per group");
+    const int n0 = prm->n_coarsest;
     for (int g = 0; g < n_groups; ++g) {
         const fm_batch_group& G = groups[g];
-        if (G.n_fine < 128 || G.count < 64 || resident_grid(ctx, G, prm)) {
-            parts.push_back(G);
-            continue;
-        }
-        const uint32_t h = G.count / 2;
-        const size_t cells = (size_t)G.n_fine * G.n_fine;
-        parts.push_back(fm_batch_group{G.n_fine, h, G.d_K, G.d_qf, G.d_qc, G.d_status});
-        parts.push_back(fm_batch_group{G.n_fine, G.count - h, G.d_K + h * cells, G.d_qf + h,
-                                       G.d_qc ? G.d_qc + h : nullptr, G.d_status ? G.d_status + h : nullptr});
+        int m = 0;
+        while (m < 16 && (n0 << m) < G.n_fine) ++m;
+        FM_CHECK_ARG(ctx, n0 >= 2 && n0 <= 4 && G.n_fine >= n0 && (n0 << m) == G.n_fine && G.n_fine <= 8192,
+                     "fmg_solve_uneven: group " + std::to_string(g) + ": n_fine must be n_coarsest * 2^m");
+        FM_CHECK_ARG(ctx, G.count == 0 || (G.d_K && G.d_qf),
+                     "fmg_solve_uneven: group " + std::to_string(g) + ": null input or output");
     }
-    return parts;
-}
-
-// The uneven batch of the (split) groups as one captured graph.
-static fm_status uneven_run(fm_ctx* ctx, const std::vector<fm_batch_group>& parts, const fm_solve_params* prm,
-                            void* stream) {
-    const int n_groups = (int)parts.size();
-    const fm_batch_group* groups = parts.data();
     const std::vector<int> prio = branch_priorities(ctx, n_groups, groups);
     std::vector<cudaStream_t> branch;
     FM_TRY(uneven_prepare(ctx, n_groups, prio, &branch));
@@ -242,29 +234,6 @@ static fm_status uneven_run(fm_ctx* ctx, const std::vector<fm_batch_group>& part
     ++U->launches;
     FM_CUDA_TRY(ctx, cudaGetLastError());
     return FM_OK;
-}
-
-}  // namespace fm
-
-using namespace fm;
-
-extern "C" fm_status fmg_solve_uneven(fm_ctx* ctx, int32_t n_groups, const fm_batch_group* groups,
-                                      const fm_solve_params* prm, void* stream) {
-    FM_CHECK_ARG(ctx, ctx != nullptr, "fmg_solve_uneven: null context");
-    FM_CHECK_ARG(ctx, prm != nullptr && groups != nullptr, "fmg_solve_uneven: null argument");
-    FM_CHECK_ARG(ctx, n_groups >= 1 && n_groups <= 64, "fmg_solve_uneven: 1 .. 64 groups");
-    FM_CHECK_ARG(ctx, prm->kernel != FM_KERNEL_RESIDENT, "fmg_solve_uneven: the schedule is chosen per group");
-    const int n0 = prm->n_coarsest;
-    for (int g = 0; g < n_groups; ++g) {
-        const fm_batch_group& G = groups[g];
-        int m = 0;
-        while (m < 16 && (n0 << m) < G.n_fine) ++m;
-        FM_CHECK_ARG(ctx, n0 >= 2 && n0 <= 4 && G.n_fine >= n0 && (n0 << m) == G.n_fine && G.n_fine <= 8192,
-                     "fmg_solve_uneven: group " + std::to_string(g) + ": n_fine must be n_coarsest * 2^m");
-        FM_CHECK_ARG(ctx, G.count == 0 || (G.d_K && G.d_qf),
-                     "fmg_solve_uneven: group " + std::to_string(g) + ": null input or output");
-    }
-    return uneven_run(ctx, split_groups(ctx, n_groups, groups, *prm), prm, stream);
 }
 
 extern "C" fm_status fmg_uneven_stats(const fm_ctx* ctx, int64_t* instantiations, int64_t* updates,
